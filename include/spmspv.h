@@ -1,0 +1,156 @@
+/*
+ * spmspv.h - C ABI of the GB300 (sm_103a) sparse-matrix x sparse-vector
+ * library: y <- A (+).(x) x over a semiring, A in CSC form, x and y in list
+ * (index, value) form.
+ *
+ * Paper: A. Azad, A. Buluc, "A work-efficient parallel sparse matrix-sparse
+ * vector multiplication algorithm", arXiv 1610.07902.
+ *   Operation and notation ........ Sec. II-A
+ *   CSC matrix, list-format vectors, output format = input format ... Sec. II-C
+ *   The bucketed algorithm ......... Sec. III, Algorithm 1 (Steps 1-3), Algorithm 2
+ *   Preallocated buckets and SPA ... Sec. III-A ("Memory allocation")
+ *   Masked SpMSpV .................. Sec. V (GraphBLAS masks, future work there)
+ *   BFS as repeated SpMSpV ......... Sec. IV-D
+ *
+ * Conventions shared by every call:
+ *   - Every function returns an int status: SPMSPV_OK (0) or an SPMSPV_ERR_*
+ *     code.  spmspv_last_error() gives a message owned by the library.
+ *   - Every array argument is a DEVICE pointer owned by the caller unless the
+ *     argument's comment says "host".
+ *   - A handle BORROWS the CSC arrays given at create: they must stay
+ *     allocated and unchanged until spmspv_destroy.  The handle OWNS its
+ *     workspace (buckets, compacted frontier, scan state), allocated once at
+ *     create, as the paper preallocates buckets and the SPA once (Sec. III-A).
+ *   - Calls that take a stream are asynchronous on that stream and make no
+ *     host synchronisation.  A handle runs one product at a time: calls on a
+ *     handle must be ordered (same stream, or externally synchronised).
+ *   - Errors found on the device (output capacity exceeded, a wait that ran
+ *     out) are recorded in a device status word; spmspv_device_status()
+ *     synchronises the handle's last stream and returns and clears it.
+ *   - Index type int32, floating values float32.  nnz(A) < 2^31.
+ */
+#ifndef SPMSPV_H_
+#define SPMSPV_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t without the CUDA headers; NULL is the legacy default stream */
+typedef struct CUstream_st* spmspv_stream_t;
+typedef struct spmspv_handle spmspv_handle;
+
+/* ---- status codes ---- */
+#define SPMSPV_OK 0
+#define SPMSPV_ERR_ARG 1         /* invalid argument (null pointer, size, id) */
+#define SPMSPV_ERR_STATE 2       /* handle not usable (destroyed, wrong device) */
+#define SPMSPV_ERR_OOM 3         /* device allocation failed at create */
+#define SPMSPV_ERR_CUDA 4        /* a CUDA runtime call failed */
+#define SPMSPV_ERR_CAPACITY 5    /* y needs more entries than y_capacity */
+#define SPMSPV_ERR_TIMEOUT 6     /* a bounded device-side wait gave up */
+#define SPMSPV_ERR_INDEX 7       /* index out of range (checked inputs) */
+#define SPMSPV_ERR_UNSUPPORTED 8 /* shape or option outside the supported range */
+
+/* ---- matrix value types (spmspv_create_csc val_type) ---- */
+#define SPMSPV_VAL_NONE 0 /* pattern matrix: every stored A(i,j) is 1 */
+#define SPMSPV_VAL_F32 1  /* float values */
+
+/* ---- create flags ---- */
+#define SPMSPV_CSC_SYMMETRIC 1u /* A == A^T: the CSC doubles as CSR (pull direction) */
+
+/* ---- semirings (spmspv_run semiring) ----
+ * Operand order A(i,j) (x) x(j), the GraphBLAS mxv order.
+ *   PLUS_TIMES_F32   : (x) = a*x, (+) = +, float32.  x_val, y_val: float[].
+ *                      y's index set is structural (a sum that is exactly 0
+ *                      still appears).
+ *   MIN_SELECT2ND_I32: (x) = x(j) (select2nd), (+) = min, int32.
+ *                      x_val, y_val: int32[].  Matrix values are not read.
+ *   OR_AND_BOOL      : (x) = and, (+) = or.  Values are implicit true:
+ *                      x_val and y_val are ignored (may be NULL); y is the
+ *                      index set only.                                       */
+#define SPMSPV_PLUS_TIMES_F32 0
+#define SPMSPV_MIN_SELECT2ND_I32 1
+#define SPMSPV_OR_AND_BOOL 2
+
+/* ---- run options (spmspv_run opts) ---- */
+#define SPMSPV_MASK_COMPLEMENT 1u /* keep row i only where mask bit i is 0 */
+#define SPMSPV_SORTED_OUT 2u      /* y_idx ascending (see note below) */
+#define SPMSPV_SCHED_AUTO 4u      /* let the learned selector pick the schedule */
+#define SPMSPV_SCHED_FORCE 8u     /* use schedule SPMSPV_SCHED_ID(opts) */
+#define SPMSPV_SCHED_SHIFT 8
+#define SPMSPV_SCHED_OPT(s) (SPMSPV_SCHED_FORCE | ((uint32_t)(s) << SPMSPV_SCHED_SHIFT))
+#define SPMSPV_SCHED_ID(opts) (((opts) >> SPMSPV_SCHED_SHIFT) & 0xFFu)
+#define SPMSPV_NUM_SCHEDULES 12
+
+/* ---- device status bits (spmspv_device_status) ---- */
+#define SPMSPV_DEV_CAPACITY 1u /* y did not fit; *d_nnz_y holds the size needed */
+#define SPMSPV_DEV_TIMEOUT 2u  /* a bounded wait gave up; outputs are invalid */
+
+/* Message for the last error returned on this thread (library-owned). */
+const char* spmspv_last_error(void);
+
+/*
+ * Create a handle over an m-by-n CSC matrix (Sec. II-C: colptrs n+1,
+ * rowids nnz, values nnz; row ids inside a column need not be sorted).
+ *   h        host out: the new handle.
+ *   m, n     rows, columns; 1 <= m <= 2^27, 1 <= n < 2^31.
+ *   nnz      colptr[n]; 0 <= nnz < 2^31.
+ *   colptr   device int32[n+1], non-decreasing, colptr[0] = 0.
+ *   rowidx   device int32[nnz], each in [0, m).
+ *   val      device float[nnz] for SPMSPV_VAL_F32, ignored (may be NULL)
+ *            for SPMSPV_VAL_NONE.
+ *   flags    SPMSPV_CSC_SYMMETRIC or 0.
+ * Synchronous: allocates the workspace (about 6 bytes per nonzero for the
+ * buckets plus 16 bytes per column) on the current device, and scans
+ * rowidx once to size the row-range buckets.  Errors: ARG, OOM, CUDA,
+ * UNSUPPORTED (m too large for the bucket row width).
+ */
+int spmspv_create_csc(spmspv_handle** h, int32_t m, int32_t n, int64_t nnz,
+                      const int32_t* colptr, const int32_t* rowidx, const void* val,
+                      int val_type, uint32_t flags);
+
+/* Release the handle and its workspace (synchronises the device). */
+int spmspv_destroy(spmspv_handle* h);
+
+/*
+ * y <- A (+).(x) x  [under mask]  (Algorithm 1; masks: Sec. V).
+ *   semiring    SPMSPV_PLUS_TIMES_F32 | SPMSPV_MIN_SELECT2ND_I32 | SPMSPV_OR_AND_BOOL.
+ *   x_idx       device int32[nnz_x], distinct, each in [0, n) (caller contract;
+ *               duplicates or out-of-range ids give undefined results).
+ *   x_val       device float[] or int32[] per the semiring; may be NULL for
+ *               OR_AND_BOOL.
+ *   nnz_x       host count, 0 <= nnz_x <= n.  0 gives an empty y.
+ *   mask        device uint32[ceil(m/32)] bitmap (bit i%32 of word i/32), or
+ *               NULL for no mask.  Without SPMSPV_MASK_COMPLEMENT row i is kept
+ *               only where its bit is 1; with it only where its bit is 0.
+ *   opts        SPMSPV_MASK_COMPLEMENT | SPMSPV_SORTED_OUT | schedule bits.
+ *   y_idx       device int32[y_capacity] out.
+ *   y_val       device float[]/int32[y_capacity] out (ignored for OR_AND_BOOL).
+ *   y_capacity  entries available in y_idx/y_val.  min(m, nnz(A)) always
+ *               suffices.  If y needs more, nothing past y_capacity is
+ *               written, *d_nnz_y receives the size needed and the device
+ *               status gets SPMSPV_DEV_CAPACITY.
+ *   d_nnz_y     device int32 out: nnz(y).
+ *   stream      CUDA stream.
+ * Output order: y_idx is always produced in ascending order (each
+ * row-range bucket is emitted in row order and buckets are concatenated in
+ * order, Step 3 of Algorithm 1), so SPMSPV_SORTED_OUT costs nothing extra.
+ */
+int spmspv_run(spmspv_handle* h, int semiring, const int32_t* x_idx, const void* x_val,
+               int32_t nnz_x, const uint32_t* mask, uint32_t opts, int32_t* y_idx,
+               void* y_val, int32_t y_capacity, int32_t* d_nnz_y, spmspv_stream_t stream);
+
+/* Device status word of the handle: synchronises the handle's last stream,
+ * returns the SPMSPV_DEV_* bits in *flags (host out) and clears them. */
+int spmspv_device_status(spmspv_handle* h, uint32_t* flags);
+
+/* Multiply count of the last run (host out, synchronises): the sum of the
+ * selected column lengths, the df term of Sec. II-D, before masking. */
+int spmspv_last_work(spmspv_handle* h, int64_t* work);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPMSPV_H_ */
