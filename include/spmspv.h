@@ -58,7 +58,10 @@ typedef struct spmspv_handle spmspv_handle;
 #define SPMSPV_VAL_F32 1  /* float values */
 
 /* ---- create flags ---- */
-#define SPMSPV_CSC_SYMMETRIC 1u /* A == A^T: the CSC doubles as CSR (pull direction) */
+#define SPMSPV_CSC_PATTERN_SYMMETRIC 1u /* A and A^T have the same nonzero pattern: the CSC
+                                           doubles as CSR for the pull direction of the
+                                           (min,select2nd) and (or,and) semirings */
+#define SPMSPV_CSC_SYMMETRIC 3u         /* A == A^T, values included: pull also for (+,*) */
 
 /* ---- semirings (spmspv_run semiring) ----
  * Operand order A(i,j) (x) x(j), the GraphBLAS mxv order.
@@ -87,6 +90,8 @@ typedef struct spmspv_handle spmspv_handle;
 /* ---- device status bits (spmspv_device_status) ---- */
 #define SPMSPV_DEV_CAPACITY 1u /* y did not fit; *d_nnz_y holds the size needed */
 #define SPMSPV_DEV_TIMEOUT 2u  /* a bounded wait gave up; outputs are invalid */
+#define SPMSPV_DEV_INDEX 4u    /* an x index was outside [0, n), or a bucket overflowed
+                                  (duplicate x indices); outputs are invalid */
 
 /* Message for the last error returned on this thread (library-owned). */
 const char* spmspv_last_error(void);
@@ -101,7 +106,8 @@ const char* spmspv_last_error(void);
  *   rowidx   device int32[nnz], each in [0, m).
  *   val      device float[nnz] for SPMSPV_VAL_F32, ignored (may be NULL)
  *            for SPMSPV_VAL_NONE.
- *   flags    SPMSPV_CSC_SYMMETRIC or 0.
+ *   flags    SPMSPV_CSC_PATTERN_SYMMETRIC, SPMSPV_CSC_SYMMETRIC or 0.  The
+ *            flags are trusted, not checked.
  * Synchronous: allocates the workspace (about 6 bytes per nonzero for the
  * buckets plus 16 bytes per column) on the current device, and scans
  * rowidx once to size the row-range buckets.  Errors: ARG, OOM, CUDA,
@@ -149,6 +155,24 @@ int spmspv_device_status(spmspv_handle* h, uint32_t* flags);
 /* Multiply count of the last run (host out, synchronises): the sum of the
  * selected column lengths, the df term of Sec. II-D, before masking. */
 int spmspv_last_work(spmspv_handle* h, int64_t* work);
+
+/* ---- per-stage timing (CUDA events on the launch stream) ----
+ * Stage ids of spmspv_profile_end's stage_ms array. */
+#define SPMSPV_STAGE_SCAN 0    /* K1 work scan (Algorithm 2's role) */
+#define SPMSPV_STAGE_SELECT 1  /* learned schedule selector */
+#define SPMSPV_STAGE_SCATTER 2 /* K2 expand + multiply + bucket (Step 1) */
+#define SPMSPV_STAGE_MERGE 3   /* K3 SPA merge + concatenation (Steps 2-3) */
+#define SPMSPV_STAGE_PULL 4    /* pull direction (matrix-driven) kernels */
+#define SPMSPV_NUM_STAGES 5
+
+/* Start recording a CUDA event before and after every stage of every
+ * following call on this handle (adds a few microseconds per call). */
+int spmspv_profile_begin(spmspv_handle* h);
+
+/* Stop recording; synchronise; stage_ms (host out, n_stages entries) gets
+ * the summed device time of each stage over the recorded calls and
+ * *n_calls (host out, may be NULL) the number of calls. */
+int spmspv_profile_end(spmspv_handle* h, double* stage_ms, int32_t n_stages, int32_t* n_calls);
 
 #ifdef __cplusplus
 }

@@ -80,7 +80,7 @@ class SpMSpVResult:
 
 
 def spmspv(m, colptr, rowidx, val, semiring, x_idx, x_val=None, mask=None,
-           complement=True, lib=None) -> SpMSpVResult:
+           complement=True, lib=None, with_absum=True) -> SpMSpVResult:
     """y <- A (+).(x) x under an optional mask (bool/uint8 array of length m).
 
     colptr/rowidx int32, val float32 or None (pattern matrix), x_idx int32,
@@ -110,7 +110,7 @@ def spmspv(m, colptr, rowidx, val, semiring, x_idx, x_val=None, mask=None,
     y_idx = np.empty(max(cap, 1), dtype=np.int32)
     if semiring == PLUS_TIMES:
         y_val = np.empty(max(cap, 1), dtype=np.float64)
-        absum = np.empty(max(cap, 1), dtype=np.float64)
+        absum = np.empty(max(cap, 1), dtype=np.float64) if with_absum else None
     elif semiring == MIN_SELECT2ND:
         y_val = np.empty(max(cap, 1), dtype=np.int32)
         absum = None

@@ -1,0 +1,401 @@
+// C ABI of the SpMSpV library (include/spmspv.h): handle life cycle,
+// argument checks, schedule choice and the launch sequence of one product.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include <string>
+#include <vector>
+
+#include "handle.cuh"
+#include "spmspv_internal.cuh"
+
+using namespace spmspv;
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+namespace spmspv {
+
+// One profiled call: events[0] before the first stage, events[i+1] after
+// stage stages[i].
+struct ProfileCall {
+  std::vector<cudaEvent_t> events;
+  std::vector<int> stages;
+};
+using ProfileLog = std::vector<ProfileCall>;
+
+void prof_call_begin(spmspv_handle* h, cudaStream_t s) {
+  if (!h->prof) return;
+  ProfileLog* log = (ProfileLog*)h->prof;
+  log->emplace_back();
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  cudaEventRecord(e, s);
+  log->back().events.push_back(e);
+}
+
+void prof_mark(spmspv_handle* h, int stage, cudaStream_t s) {
+  if (!h->prof) return;
+  ProfileLog* log = (ProfileLog*)h->prof;
+  if (log->empty()) return;
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  cudaEventRecord(e, s);
+  log->back().events.push_back(e);
+  log->back().stages.push_back(stage);
+}
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(SPMSPV_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+static int ilog2_ceil(int64_t v) {
+  int l = 0;
+  while (((int64_t)1 << l) < v) ++l;
+  return l;
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+Sched decode_schedule(const spmspv_handle* h, int id) {
+  Sched s;
+  s.dir = id / 6;
+  s.q = ((id / 3) % 2) ? 2 * QF : QF;
+  s.lwb = h->lwb_lo + id % 3;
+  return s;
+}
+
+int check_handle(const spmspv_handle* h) {
+  if (!h || h->magic != kHandleMagic) return fail(SPMSPV_ERR_STATE, "invalid or destroyed handle");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device)
+    return fail(SPMSPV_ERR_STATE, "handle belongs to device %d but device %d is current", h->device,
+                dev);
+  return SPMSPV_OK;
+}
+
+// The push-direction product: K1 -> K2 -> K3 on `s`.
+int run_push(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_val, int f,
+             const int32_t* f_dev, const uint32_t* mask, int mask_comp, const Sched& sc,
+             int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y, bool bfs,
+             uint32_t* mask_update, int32_t* level, int32_t* parent, cudaStream_t s) {
+  int k1_grid = f_dev ? h->k1_grid_max
+                      : (int)std::min<int64_t>(h->k1_grid_max, ((int64_t)f + K1_TILE - 1) / K1_TILE);
+  if (k1_grid < 1) k1_grid = 1;
+  cudaError_t e;
+  prof_call_begin(h, s);
+  if (bfs) {
+    extern cudaError_t launch_k1_bfs(const Matrix& A, const Workspace& ws, int nb_fine,
+                                     const int32_t* x_idx, const int32_t* f_dev, int grid,
+                                     const Sched& sc, cudaStream_t s);
+    e = launch_k1_bfs(h->A, h->ws, h->nb_fine, x_idx, f_dev, k1_grid, sc, s);
+  } else {
+    e = launch_k1(h->A, h->ws, h->nb_fine, x_idx, x_val, f, f_dev, k1_grid, &sc, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "work scan launch");
+  prof_mark(h, SPMSPV_STAGE_SCAN, s);
+  e = launch_k2(sem, h->A, h->ws, h->lwb_lo, h->nb_fine, mask, mask_comp, h->k2_grid, h->k2_smem, s);
+  if (e != cudaSuccess) return cuda_fail(e, "expand/scatter launch");
+  prof_mark(h, SPMSPV_STAGE_SCATTER, s);
+  const size_t k3_smem = k3_smem_bytes(sc.lwb);
+  const int nb = (int)(((int64_t)h->A.m + (1 << sc.lwb) - 1) >> sc.lwb);
+  const int k3_grid = std::max(1, std::min(nb, h->sm_count * h->k3_bps[sc.lwb - h->lwb_lo]));
+  e = launch_k3(sem, bfs, h->A, h->ws, h->lwb_lo, h->nb_fine, y_idx, y_val, y_cap, d_nnz_y,
+                mask_update, level, parent, k3_grid, k3_smem, s);
+  if (e != cudaSuccess) return cuda_fail(e, "bucket merge launch");
+  prof_mark(h, SPMSPV_STAGE_MERGE, s);
+  return SPMSPV_OK;
+}
+
+}  // namespace spmspv
+
+extern "C" {
+
+const char* spmspv_last_error(void) { return g_last_error.c_str(); }
+
+int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
+                      const int32_t* colptr, const int32_t* rowidx, const void* val, int val_type,
+                      uint32_t flags) {
+  if (!out) return fail(SPMSPV_ERR_ARG, "h is NULL");
+  *out = nullptr;
+  if (m < 1 || n < 1) return fail(SPMSPV_ERR_ARG, "m and n must be >= 1 (got %d, %d)", m, n);
+  if (m > (1 << 27))
+    return fail(SPMSPV_ERR_UNSUPPORTED, "m = %d exceeds 2^27 rows (bucket row width limit)", m);
+  if (nnz < 0 || nnz >= ((int64_t)1 << 31)) return fail(SPMSPV_ERR_ARG, "nnz must be in [0, 2^31)");
+  if (!colptr) return fail(SPMSPV_ERR_ARG, "colptr is NULL");
+  if (nnz > 0 && !rowidx) return fail(SPMSPV_ERR_ARG, "rowidx is NULL");
+  if (val_type != SPMSPV_VAL_NONE && val_type != SPMSPV_VAL_F32)
+    return fail(SPMSPV_ERR_ARG, "unknown val_type %d", val_type);
+  if (val_type == SPMSPV_VAL_F32 && nnz > 0 && !val)
+    return fail(SPMSPV_ERR_ARG, "val is NULL for SPMSPV_VAL_F32");
+
+  spmspv_handle* h = new spmspv_handle();
+  memset(h, 0, sizeof(*h));
+  h->magic = kHandleMagic;
+  cudaGetDevice(&h->device);
+  cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+  h->A.m = m;
+  h->A.n = n;
+  h->A.nnz = nnz;
+  h->A.colptr = colptr;
+  h->A.rowidx = rowidx;
+  h->A.val = val_type == SPMSPV_VAL_F32 ? (const float*)val : nullptr;
+  h->flags = flags;
+
+  // bucket row widths: the widest gives about 128 buckets, the schedule
+  // chooses among three widths
+  int lwb_hi = ilog2_ceil(m) - 7;
+  if (lwb_hi < LWB_MIN + 2) lwb_hi = LWB_MIN + 2;
+  if (lwb_hi > LWB_MAX) lwb_hi = LWB_MAX;
+  h->lwb_lo = lwb_hi - 2;
+  h->nb_fine = (int)(((int64_t)m + (1 << h->lwb_lo) - 1) >> h->lwb_lo);
+  if (h->nb_fine > NB_K2_MAX) {
+    delete h;
+    return fail(SPMSPV_ERR_UNSUPPORTED, "too many row-range buckets (%d)", (int)0);
+  }
+
+  // workspace: one allocation, carved in 256-byte aligned pieces
+  const int64_t ntile_fine = nnz / QF + 2;
+  const int64_t nt1 = ((int64_t)n + K1_TILE - 1) / K1_TILE + 1;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  size_t o_st = take(sizeof(DevState));
+  size_t o_cw = take(sizeof(int32_t) * ((size_t)n + 1));
+  size_t o_cb = take(sizeof(int32_t) * (size_t)n);
+  size_t o_cx = take(sizeof(uint32_t) * (size_t)n);
+  size_t o_tk = take(sizeof(int32_t) * (size_t)ntile_fine);
+  size_t o_k1s = take(sizeof(unsigned long long) * (size_t)nt1);
+  size_t o_bf = take(sizeof(int32_t) * (size_t)h->nb_fine);
+  size_t o_k3s = take(sizeof(unsigned long long) * (size_t)h->nb_fine);
+  size_t o_rb = take(sizeof(int32_t) * ((size_t)h->nb_fine + 1));
+  size_t o_br = take(sizeof(uint16_t) * (size_t)(nnz > 0 ? nnz : 1));
+  size_t o_bv = take(sizeof(uint32_t) * (size_t)(nnz > 0 ? nnz : 1));
+  const size_t zero_bytes = o_br;  // everything before the bucket payload starts zeroed
+  h->ws_bytes = off;
+  cudaError_t e = cudaMalloc(&h->ws_base, h->ws_bytes);
+  if (e != cudaSuccess) {
+    delete h;
+    cudaGetLastError();
+    return fail(SPMSPV_ERR_OOM, "workspace of %zu bytes: %s", off, cudaGetErrorString(e));
+  }
+  char* b = (char*)h->ws_base;
+  h->ws.st = (DevState*)(b + o_st);
+  h->ws.cw = (int32_t*)(b + o_cw);
+  h->ws.cb = (int32_t*)(b + o_cb);
+  h->ws.cx = (uint32_t*)(b + o_cx);
+  h->ws.tile_k0 = (int32_t*)(b + o_tk);
+  h->ws.k1_status = (unsigned long long*)(b + o_k1s);
+  h->ws.bfill = (int32_t*)(b + o_bf);
+  h->ws.k3_status = (unsigned long long*)(b + o_k3s);
+  h->ws.rbase = (int32_t*)(b + o_rb);
+  h->ws.brow = (uint16_t*)(b + o_br);
+  h->ws.bval = (uint32_t*)(b + o_bv);
+
+  int rc = SPMSPV_OK;
+  do {
+    if ((e = cudaMemset(h->ws_base, 0, zero_bytes)) != cudaSuccess) { rc = cuda_fail(e, "memset"); break; }
+    // bucket regions: the nonzeros of A in each fine row range, prefix-summed
+    int32_t* d_counts = nullptr;
+    unsigned int* d_bad = nullptr;
+    if ((e = cudaMalloc(&d_counts, sizeof(int32_t) * (size_t)h->nb_fine + 16)) != cudaSuccess) {
+      rc = fail(SPMSPV_ERR_OOM, "bucket count scratch: %s", cudaGetErrorString(e));
+      break;
+    }
+    d_bad = (unsigned int*)(d_counts + h->nb_fine);
+    cudaMemset(d_counts, 0, sizeof(int32_t) * (size_t)h->nb_fine + 16);
+    if (nnz > 0 && (e = launch_bucket_sizes(h->A, h->lwb_lo, h->nb_fine, d_counts, d_bad, 0)) != cudaSuccess) {
+      cudaFree(d_counts);
+      rc = cuda_fail(e, "bucket size launch");
+      break;
+    }
+    std::vector<int32_t> counts((size_t)h->nb_fine + 4, 0);
+    e = cudaMemcpy(counts.data(), d_counts, sizeof(int32_t) * (size_t)h->nb_fine + 16,
+                   cudaMemcpyDeviceToHost);
+    cudaFree(d_counts);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "bucket size copy"); break; }
+    unsigned int bad = 0;
+    memcpy(&bad, counts.data() + h->nb_fine, sizeof(bad));
+    if (bad) { rc = fail(SPMSPV_ERR_INDEX, "%u row ids outside [0, m)", bad); break; }
+    std::vector<int32_t> rbase((size_t)h->nb_fine + 1, 0);
+    int64_t acc = 0;
+    for (int i = 0; i < h->nb_fine; ++i) {
+      rbase[i] = (int32_t)acc;
+      acc += counts[i];
+    }
+    rbase[h->nb_fine] = (int32_t)acc;
+    if (acc != nnz) { rc = fail(SPMSPV_ERR_ARG, "row histogram %lld != nnz %lld", (long long)acc, (long long)nnz); break; }
+    if ((e = cudaMemcpy(h->ws.rbase, rbase.data(), sizeof(int32_t) * rbase.size(),
+                        cudaMemcpyHostToDevice)) != cudaSuccess) { rc = cuda_fail(e, "rbase copy"); break; }
+    // default schedule state
+    DevState st0;
+    memset(&st0, 0, sizeof(st0));
+    st0.q = 2 * QF;
+    st0.lwb = h->lwb_lo + 1;
+    if ((e = cudaMemcpy(h->ws.st, &st0, sizeof(st0), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      rc = cuda_fail(e, "state init");
+      break;
+    }
+    h->k2_smem = k2_smem_bytes(h->nb_fine);
+    h->k3_smem_max = k3_smem_bytes(lwb_hi);
+    if ((e = set_kernel_attributes(h->k2_smem, h->k3_smem_max)) != cudaSuccess) {
+      rc = cuda_fail(e, "kernel attributes");
+      break;
+    }
+    const int k2_bps = k2_blocks_per_sm(kPlusTimes, h->k2_smem);
+    h->k2_grid = h->sm_count * k2_bps;
+    for (int i = 0; i < 3; ++i) h->k3_bps[i] = k3_blocks_per_sm(kPlusTimes, k3_smem_bytes(h->lwb_lo + i));
+    h->k1_grid_max = h->sm_count * 4;
+    h->default_sched = 4;  // push, q = 4096, middle bucket width
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) { rc = cuda_fail(e, "create"); break; }
+  } while (0);
+  if (rc != SPMSPV_OK) {
+    cudaFree(h->ws_base);
+    h->magic = 0;
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return SPMSPV_OK;
+}
+
+int spmspv_destroy(spmspv_handle* h) {
+  if (!h || h->magic != kHandleMagic) return fail(SPMSPV_ERR_STATE, "invalid or destroyed handle");
+  cudaDeviceSynchronize();
+  if (h->prof) {
+    double tmp[SPMSPV_NUM_STAGES];
+    spmspv_profile_end(h, tmp, SPMSPV_NUM_STAGES, nullptr);
+  }
+  release_extras(h);
+  cudaFree(h->ws_base);
+  h->magic = 0;
+  delete h;
+  return SPMSPV_OK;
+}
+
+int spmspv_run(spmspv_handle* h, int semiring, const int32_t* x_idx, const void* x_val,
+               int32_t nnz_x, const uint32_t* mask, uint32_t opts, int32_t* y_idx, void* y_val,
+               int32_t y_capacity, int32_t* d_nnz_y, spmspv_stream_t stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (semiring < 0 || semiring > 2) return fail(SPMSPV_ERR_ARG, "unknown semiring %d", semiring);
+  if (nnz_x < 0 || nnz_x > h->A.n) return fail(SPMSPV_ERR_ARG, "nnz_x = %d outside [0, n]", nnz_x);
+  if (nnz_x > 0 && !x_idx) return fail(SPMSPV_ERR_ARG, "x_idx is NULL");
+  if (nnz_x > 0 && semiring != SPMSPV_OR_AND_BOOL && !x_val)
+    return fail(SPMSPV_ERR_ARG, "x_val is NULL");
+  if (y_capacity < 0) return fail(SPMSPV_ERR_ARG, "y_capacity < 0");
+  if (y_capacity > 0 && !y_idx) return fail(SPMSPV_ERR_ARG, "y_idx is NULL");
+  if (y_capacity > 0 && semiring != SPMSPV_OR_AND_BOOL && !y_val)
+    return fail(SPMSPV_ERR_ARG, "y_val is NULL");
+  if (!d_nnz_y) return fail(SPMSPV_ERR_ARG, "d_nnz_y is NULL");
+  if ((opts & SPMSPV_SCHED_FORCE) && SPMSPV_SCHED_ID(opts) >= SPMSPV_NUM_SCHEDULES)
+    return fail(SPMSPV_ERR_ARG, "schedule id %u out of range", SPMSPV_SCHED_ID(opts));
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  if (nnz_x == 0) {
+    cudaError_t e = cudaMemsetAsync(d_nnz_y, 0, sizeof(int32_t), s);
+    h->last_empty = 1;
+    return e == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "memset nnz_y");
+  }
+  h->last_empty = 0;
+  int sid = h->default_sched;
+  if (opts & SPMSPV_SCHED_FORCE) sid = (int)SPMSPV_SCHED_ID(opts);
+  Sched sc = decode_schedule(h, sid);
+  if (sc.dir == 1) {
+    rc = run_pull_if_available(h, semiring, x_idx, (const uint32_t*)x_val, nnz_x, mask,
+                               (opts & SPMSPV_MASK_COMPLEMENT) ? 1 : 0, sc, y_idx,
+                               (uint32_t*)y_val, y_capacity, d_nnz_y, s);
+    if (rc != -1) return rc;
+    sc.dir = 0;  // no row access to A: fall back to the push form of the same schedule
+  }
+  return run_push(h, semiring, x_idx, (const uint32_t*)x_val, nnz_x, nullptr, mask,
+                  (opts & SPMSPV_MASK_COMPLEMENT) ? 1 : 0, sc, y_idx, (uint32_t*)y_val, y_capacity,
+                  d_nnz_y, false, nullptr, nullptr, nullptr, s);
+}
+
+int spmspv_device_status(spmspv_handle* h, uint32_t* flags) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!flags) return fail(SPMSPV_ERR_ARG, "flags is NULL");
+  cudaError_t e = cudaStreamSynchronize(h->last_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  uint32_t v = 0;
+  e = cudaMemcpy(&v, &h->ws.st->status, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "status copy");
+  uint32_t z = 0;
+  e = cudaMemcpy(&h->ws.st->status, &z, sizeof(z), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "status clear");
+  *flags = v & (SPMSPV_DEV_CAPACITY | SPMSPV_DEV_TIMEOUT | ST_INDEX);
+  return SPMSPV_OK;
+}
+
+int spmspv_last_work(spmspv_handle* h, int64_t* work) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!work) return fail(SPMSPV_ERR_ARG, "work is NULL");
+  cudaError_t e = cudaStreamSynchronize(h->last_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  if (h->last_empty) {
+    *work = 0;
+    return SPMSPV_OK;
+  }
+  int32_t W = 0;
+  e = cudaMemcpy(&W, &h->ws.st->W, sizeof(W), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "work copy");
+  *work = W;
+  return SPMSPV_OK;
+}
+
+int spmspv_profile_begin(spmspv_handle* h) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!h->prof) h->prof = new ProfileLog();
+  return SPMSPV_OK;
+}
+
+int spmspv_profile_end(spmspv_handle* h, double* stage_ms, int32_t n_stages, int32_t* n_calls) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!stage_ms || n_stages < 0) return fail(SPMSPV_ERR_ARG, "stage_ms is NULL");
+  for (int i = 0; i < n_stages; ++i) stage_ms[i] = 0.0;
+  ProfileLog* log = (ProfileLog*)h->prof;
+  if (n_calls) *n_calls = log ? (int32_t)log->size() : 0;
+  if (!log) return SPMSPV_OK;
+  h->prof = nullptr;
+  cudaError_t err = cudaSuccess;
+  for (ProfileCall& c : *log) {
+    for (size_t i = 0; i + 1 < c.events.size(); ++i) {
+      cudaError_t e = cudaEventSynchronize(c.events[i + 1]);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c.events[i], c.events[i + 1]);
+      if (e != cudaSuccess) err = e;
+      const int st = c.stages[i];
+      if (st >= 0 && st < n_stages) stage_ms[st] += ms;
+    }
+    for (cudaEvent_t e : c.events) cudaEventDestroy(e);
+  }
+  delete log;
+  return err == cudaSuccess ? SPMSPV_OK : cuda_fail(err, "profile events");
+}
+
+}  // extern "C"

@@ -1,0 +1,61 @@
+// The handle behind the opaque spmspv_handle of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spmspv_internal.cuh"
+
+constexpr uint32_t kHandleMagic = 0x53704d53u;
+
+struct spmspv_handle {
+  uint32_t magic;
+  int device;
+  int sm_count;
+  spmspv::Matrix A;
+  uint32_t flags;
+  int rows_sorted;      // row ids ascend inside every column
+  int lwb_lo;           // log2 of the narrowest bucket width of the schedules
+  int nb_fine;          // buckets at the narrowest width
+  void* ws_base;
+  size_t ws_bytes;
+  spmspv::Workspace ws;
+  size_t k2_smem;
+  size_t k3_smem_max;
+  int k2_grid;
+  int k3_bps[3];        // K3 CTAs per SM for each of the three bucket widths
+  int k1_grid_max;
+  int default_sched;
+  cudaStream_t last_stream;
+  int last_empty;
+  void* prof;           // std::vector<ProfileCall>* while profiling, else NULL
+  // pull direction (dense frontier) buffers, allocated on first use
+  uint32_t* xbits;      // [ceil(n/32)] frontier bitmap
+  uint32_t* xdense;     // [n] frontier values
+  unsigned long long* pull_status;  // [row tiles] look-back words
+  int pull_tiles;
+  // BFS buffers, allocated on first use
+  int32_t* bfs_front;   // [n] frontier list (x and y of each level)
+  uint32_t* bfs_visited;  // [ceil(n/32)]
+  int32_t* bfs_count;   // [4] device counters
+};
+
+namespace spmspv {
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* where);
+int check_handle(const spmspv_handle* h);
+Sched decode_schedule(const spmspv_handle* h, int id);
+int run_push(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_val, int f,
+             const int32_t* f_dev, const uint32_t* mask, int mask_comp, const Sched& sc,
+             int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y, bool bfs,
+             uint32_t* mask_update, int32_t* level, int32_t* parent, cudaStream_t s);
+// Returns -1 when the pull direction is not available for this handle/semiring.
+int run_pull_if_available(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_val,
+                          int f, const uint32_t* mask, int mask_comp, const Sched& sc,
+                          int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y,
+                          cudaStream_t s);
+void release_extras(spmspv_handle* h);
+// Per-stage event recording (no-ops unless spmspv_profile_begin was called).
+void prof_call_begin(spmspv_handle* h, cudaStream_t s);
+void prof_mark(spmspv_handle* h, int stage, cudaStream_t s);
+}  // namespace spmspv

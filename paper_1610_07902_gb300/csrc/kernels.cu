@@ -1,0 +1,693 @@
+// SpMSpV kernels for sm_103a: y <- A (+).(x) x with A in CSC, x and y sparse.
+//
+// The three steps of Algorithm 1 (Sec. III) and the counting pre-pass of
+// Algorithm 2, re-designed for one GB300:
+//
+//   K1 work_scan      Algorithm 2's role: instead of counting (thread, bucket)
+//                     insertions, one decoupled-look-back prefix sum over the
+//                     selected column lengths gives every product a global
+//                     rank; x entries with an empty column are dropped and the
+//                     first x entry of every QF-product tile is recorded
+//                     (a merge-path split: every K2 tile then holds the same
+//                     number of products, whatever the column lengths).
+//   K2 expand_scatter Step 1: a tile of q products is gathered (coalesced
+//                     loads of row ids and values), multiplied, optionally
+//                     filtered by the mask, counted per row-range bucket in
+//                     shared memory, staged bucket-by-bucket in shared memory
+//                     and written to the buckets in runs; one global atomic
+//                     per (tile, non-empty bucket) reserves each run.
+//   K3 bucket_merge   Steps 2 and 3: a CTA owns one bucket at a time, merges
+//                     it into a shared-memory SPA with the semiring's add,
+//                     marks occupied rows in a bitmap, and writes its rows in
+//                     ascending order at the offset given by a decoupled
+//                     look-back over the buckets (the prefix sum of Step 3).
+//
+// Bucket b holds rows [b*Wb, (b+1)*Wb) with Wb a power of two; the paper's
+// floor(i*nb/m) assignment is the same row-range split with nb = m/Wb.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spmspv_internal.cuh"
+
+namespace spmspv {
+
+// ------------------------------------------------------------------------
+// small device helpers
+// ------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long lb_load(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void lb_store(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Streaming load (evict-first): matrix entries are read once per call.
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+
+// Exclusive look-back prefix for tile `tile`, given this tile's aggregate.
+// Publishes the aggregate, walks predecessors, publishes the inclusive
+// prefix and returns the exclusive one.  Waits are bounded: on give-up the
+// status word gets ST_TIMEOUT and the predecessor is treated as zero.
+__device__ unsigned long long lookback(unsigned long long* status, uint32_t tile,
+                                       unsigned long long agg, DevState* st) {
+  if (tile == 0) {
+    lb_store(status, LB_FLAG_INC | agg);
+    return 0ull;
+  }
+  lb_store(status + tile, LB_FLAG_AGG | agg);
+  unsigned long long excl = 0;
+  int64_t idx = (int64_t)tile - 1;
+  while (idx >= 0) {
+    unsigned long long s;
+    uint32_t spins = 0;
+    while (((s = lb_load(status + idx)) & LB_FLAG_MASK) == 0ull) {
+      if (++spins > SPIN_LIMIT) {
+        atomicOr(&st->status, ST_TIMEOUT);
+        s = LB_FLAG_INC;  // give up: treat as an empty inclusive prefix
+        break;
+      }
+      __nanosleep(32);
+    }
+    excl += s & LB_VAL_MASK;
+    if ((s & LB_FLAG_MASK) == LB_FLAG_INC) break;
+    --idx;
+  }
+  lb_store(status + tile, LB_FLAG_INC | (excl + agg));
+  return excl;
+}
+
+// Exclusive prefix sum over the block.  `sh` holds NT/32 + 1 shared
+// entries; every thread receives the block total in *total.
+template <int NT, typename T>
+__device__ __forceinline__ T block_exclusive_sum(T v, T* sh, T* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    T w = lane < NT / 32 ? sh[lane] : T(0);
+    T wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < NT / 32) sh[lane] = wi - w;
+    if (lane == NT / 32 - 1) sh[NT / 32] = wi;
+  }
+  __syncthreads();
+  const T r = sh[wid] + x - v;
+  *total = sh[NT / 32];
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------------------
+// K1: work scan + compaction + tile starts
+// ------------------------------------------------------------------------
+__host__ __device__ constexpr int k1_pad(int e) { return e + (e >> 5); }
+constexpr int K1_SMEM_WORDS = K1_TILE + K1_TILE / 32;
+
+// Packed scan value: bits [0,31) = products, bits [31,62) = non-empty entries.
+constexpr unsigned long long K1_CNT_ONE = 1ull << 31;
+constexpr unsigned long long K1_SUM_MASK = (1ull << 31) - 1;
+
+__global__ void __launch_bounds__(K1_THREADS)
+k1_work_scan(const int32_t* __restrict__ x_idx, const uint32_t* __restrict__ x_val, int f_host,
+             const int32_t* __restrict__ f_dev, const int32_t* __restrict__ colptr, int32_t n,
+             int64_t nnz, Workspace ws, int nb_fine, int forced, int f_dir, int f_q, int f_lwb, int bfs_level_inc) {
+  __shared__ int32_t s_deg[K1_SMEM_WORDS];
+  __shared__ int32_t s_c0[K1_SMEM_WORDS];
+  __shared__ uint32_t s_xv[K1_SMEM_WORDS];
+  __shared__ unsigned long long s_warp[K1_THREADS / 32 + 1];
+  __shared__ unsigned long long s_prefix;
+  __shared__ uint32_t s_tile;
+  __shared__ int s_maxdeg;
+  __shared__ unsigned long long s_sq;
+
+  DevState* st = ws.st;
+  const int tid = threadIdx.x;
+  const int f = f_dev ? *f_dev : f_host;
+  const uint32_t nt1 = (uint32_t)((f + K1_TILE - 1) / K1_TILE);
+
+  if (blockIdx.x == 0) {
+    // reset the state the later kernels of this call accumulate into
+    for (int b = tid; b < nb_fine; b += K1_THREADS) {
+      ws.bfill[b] = 0;
+      ws.k3_status[b] = 0ull;
+    }
+    if (tid == 0) {
+      st->f = f;
+      st->k3_ticket = 0u;
+      if (forced) {
+        st->dir = f_dir;
+        st->q = f_q;
+        st->lwb = f_lwb;
+      }
+      if (bfs_level_inc) st->level += 1;
+      if (f == 0) {
+        st->fc = 0;
+        st->W = 0;
+        ws.cw[0] = 0;
+        ws.tile_k0[0] = 0;
+      }
+    }
+  }
+  if (tid == 0) {
+    s_maxdeg = 0;
+    s_sq = 0ull;
+  }
+
+  int maxdeg = 0;
+  unsigned long long sq = 0;
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(&st->k1_ticket, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= nt1) break;
+    const int64_t base = (int64_t)tile * K1_TILE;
+
+    // striped, coalesced loads of x and of the two column pointers
+#pragma unroll
+    for (int i = 0; i < K1_ITEMS; ++i) {
+      const int e = i * K1_THREADS + tid;
+      const int64_t k = base + e;
+      int32_t d = 0, c0 = 0;
+      uint32_t xv = 0;
+      if (k < f) {
+        const int32_t j = x_idx[k];
+        if (j >= 0 && j < n) {
+          c0 = colptr[j];
+          d = colptr[j + 1] - c0;
+        } else {
+          atomicOr(&st->status, ST_INDEX);
+        }
+        xv = x_val ? x_val[k] : (uint32_t)j;
+      }
+      s_deg[k1_pad(e)] = d;
+      s_c0[k1_pad(e)] = c0;
+      s_xv[k1_pad(e)] = xv;
+    }
+    __syncthreads();
+
+    // blocked: thread owns entries [tid*8, tid*8+8) of the tile
+    unsigned long long tsum = 0;
+#pragma unroll
+    for (int i = 0; i < K1_ITEMS; ++i) {
+      const int d = s_deg[k1_pad(tid * K1_ITEMS + i)];
+      tsum += (d > 0 ? K1_CNT_ONE : 0ull) + (unsigned long long)d;
+      maxdeg = max(maxdeg, d);
+      sq += (unsigned long long)d * (unsigned long long)d;
+    }
+    unsigned long long btot;
+    unsigned long long texcl = block_exclusive_sum<K1_THREADS>(tsum, s_warp, &btot);
+    if (tid == 0) s_prefix = lookback(ws.k1_status, tile, btot, st);
+    __syncthreads();
+    unsigned long long run = s_prefix + texcl;
+#pragma unroll
+    for (int i = 0; i < K1_ITEMS; ++i) {
+      const int e = tid * K1_ITEMS + i;
+      const int d = s_deg[k1_pad(e)];
+      if (d > 0) {
+        const int32_t q = (int32_t)((run >> 31) & K1_SUM_MASK);
+        const int32_t w = (int32_t)(run & K1_SUM_MASK);
+        if (q < n && (int64_t)w + d <= nnz) {
+          ws.cw[q] = w;
+          ws.cb[q] = s_c0[k1_pad(e)];
+          ws.cx[q] = s_xv[k1_pad(e)];
+          for (int64_t t = ((int64_t)w + QF - 1) / QF; t * QF < (int64_t)w + d; ++t) ws.tile_k0[t] = q;
+        } else {
+          atomicOr(&st->status, ST_INDEX);  // more products than nonzeros: duplicate x indices
+        }
+        run += K1_CNT_ONE + (unsigned long long)d;
+      }
+    }
+    if (tile == nt1 - 1 && tid == 0) {
+      const unsigned long long tot = s_prefix + btot;
+      int32_t fc = (int32_t)((tot >> 31) & K1_SUM_MASK);
+      int32_t W = (int32_t)(tot & K1_SUM_MASK);
+      if (fc > n || (int64_t)W > nnz) {  // only with duplicate x indices
+        atomicOr(&st->status, ST_INDEX);
+        fc = 0;
+        W = 0;
+      }
+      st->fc = fc;
+      st->W = W;
+      ws.cw[fc] = W;
+      ws.tile_k0[(W + QF - 1) / QF] = fc;
+    }
+    __syncthreads();
+  }
+  // selector features
+  atomicMax(&s_maxdeg, maxdeg);
+  atomicAdd(&s_sq, sq);
+  __syncthreads();
+  if (tid == 0 && s_sq != 0ull) {
+    atomicMax(&st->maxdeg, s_maxdeg);
+    atomicAdd(&st->sumdeg2, s_sq);
+  }
+}
+
+cudaError_t launch_k1(const Matrix& A, const Workspace& ws, int nb_fine, const int32_t* x_idx,
+                      const uint32_t* x_val, int f, const int32_t* f_dev, int grid,
+                      const Sched* forced, cudaStream_t s) {
+  k1_work_scan<<<grid, K1_THREADS, 0, s>>>(x_idx, x_val, f, f_dev, A.colptr, A.n, A.nnz, ws, nb_fine,
+                                           forced ? 1 : 0, forced ? forced->dir : 0,
+                                           forced ? forced->q : 0, forced ? forced->lwb : 0, 0);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// K2: expand + multiply + bucket scatter
+// ------------------------------------------------------------------------
+struct K2Smem {
+  uint32_t* bm;      // [QMAX/32] bit s set where a compacted entry starts at tile offset s
+  uint32_t* bmpre;   // [QMAX/32] exclusive prefix of popcounts of bm
+  int32_t* kbase;    // [QMAX+1]  cb[k] - cw[k] per local entry
+  uint32_t* kx;      // [QMAX+1]  x value per local entry
+  int32_t* hist;     // [nb]      per-bucket count, then exclusive offset in the stage
+  int32_t* gd;       // [nb]      global slot minus stage offset
+  uint32_t* srow;    // [QMAX]    staged rows, grouped by bucket
+  uint32_t* sval;    // [QMAX]    staged values
+};
+
+size_t k2_smem_bytes(int nb_fine) {
+  return sizeof(uint32_t) * (QMAX / 32) * 2 + sizeof(int32_t) * (QMAX + 1) * 2 +
+         sizeof(int32_t) * (size_t)nb_fine * 2 + sizeof(uint32_t) * QMAX * 2 + 64;
+}
+
+template <int SEM>
+__global__ void __launch_bounds__(K2_THREADS, 2)
+k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ val, Workspace ws,
+                  int lwb_lo, int nb_fine, int32_t m, int64_t nnz, const uint32_t* __restrict__ mask,
+                  int mask_comp) {
+  extern __shared__ __align__(16) unsigned char k2_smem_raw[];
+  __shared__ int32_t s_scan[K2_THREADS / 32 + 1];
+  __shared__ int32_t s_kept;
+
+  K2Smem sm;
+  {
+    unsigned char* p = k2_smem_raw;
+    sm.bm = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX / 32);
+    sm.bmpre = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX / 32);
+    sm.srow = (uint32_t*)p; p += sizeof(uint32_t) * QMAX;
+    sm.sval = (uint32_t*)p; p += sizeof(uint32_t) * QMAX;
+    sm.kbase = (int32_t*)p; p += sizeof(int32_t) * (QMAX + 1);
+    sm.kx = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX + 1);
+    sm.hist = (int32_t*)p; p += sizeof(int32_t) * nb_fine;
+    sm.gd = (int32_t*)p;
+  }
+  const DevState* st = ws.st;
+  const int tid = threadIdx.x;
+  const int32_t W = st->W, fc = st->fc, q = st->q, lwb = st->lwb;
+  const int sh = lwb - lwb_lo;
+  const int nb = (int)(((int64_t)m + (1 << lwb) - 1) >> lwb);
+  const uint32_t wmask = (1u << lwb) - 1u;
+  const int items = q / K2_THREADS;
+  const int ntiles = (int)(((int64_t)W + q - 1) / q);
+
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int32_t p0 = t * q;
+    const int32_t np = min(q, W - p0);
+    const int32_t k0 = ws.tile_k0[p0 / QF];
+    const int32_t kend = (p0 + np == W) ? fc : ws.tile_k0[(p0 + np) / QF] + 1;
+    const int32_t nk = max(0, min(kend - k0, QMAX + 1));
+
+    for (int i = tid; i < QMAX / 32; i += K2_THREADS) sm.bm[i] = 0u;
+    for (int b = tid; b < nb; b += K2_THREADS) sm.hist[b] = 0;
+    __syncthreads();
+    for (int l = tid; l < nk; l += K2_THREADS) {
+      const int32_t k = k0 + l;
+      const int32_t w = ws.cw[k];
+      sm.kbase[l] = ws.cb[k] - w;
+      sm.kx[l] = ws.cx[k];
+      const int32_t s0 = w - p0;
+      if (s0 > 0 && s0 < np) atomicOr(&sm.bm[s0 >> 5], 1u << (s0 & 31));
+    }
+    __syncthreads();
+    if (tid < 32) {
+      uint32_t c[QMAX / 32 / 32];
+      uint32_t tot = 0;
+#pragma unroll
+      for (int i = 0; i < QMAX / 32 / 32; ++i) {
+        c[i] = __popc(sm.bm[tid * (QMAX / 32 / 32) + i]);
+        tot += c[i];
+      }
+      uint32_t x = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (tid >= o) x += y;
+      }
+      uint32_t run = x - tot;
+#pragma unroll
+      for (int i = 0; i < QMAX / 32 / 32; ++i) {
+        sm.bmpre[tid * (QMAX / 32 / 32) + i] = run;
+        run += c[i];
+      }
+    }
+    __syncthreads();
+
+    uint32_t rrow[K2_IMAX], rval[K2_IMAX];
+    int32_t rank[K2_IMAX];
+#pragma unroll
+    for (int i = 0; i < K2_IMAX; ++i) {
+      const int32_t pl = tid + i * K2_THREADS;
+      rank[i] = -1;
+      rrow[i] = 0u;
+      rval[i] = 0u;
+      if (i < items && pl < np) {
+        const int wd = pl >> 5;
+        const uint32_t kl = sm.bmpre[wd] + __popc(sm.bm[wd] & (0xffffffffu >> (31 - (pl & 31))));
+        const int32_t pos = sm.kbase[kl] + p0 + pl;
+        if ((uint32_t)pos >= (uint32_t)nnz) continue;  // unreachable with valid inputs
+        const int32_t row = ld_stream(rowidx + pos);
+        uint32_t v = 0u;
+        if (SEM == kPlusTimes) {
+          const float xv = __uint_as_float(sm.kx[kl]);
+          v = __float_as_uint(val ? __fmul_rn(ld_stream(val + pos), xv) : xv);
+        } else if (SEM == kMinSelect2nd) {
+          v = sm.kx[kl];
+        }
+        bool keep = true;
+        if (mask) {
+          const uint32_t bit = (__ldg(mask + (row >> 5)) >> (row & 31)) & 1u;
+          keep = mask_comp ? (bit == 0u) : (bit != 0u);
+        }
+        if (keep) rank[i] = atomicAdd(&sm.hist[row >> lwb], 1);
+        rrow[i] = (uint32_t)row;
+        rval[i] = v;
+      }
+    }
+    __syncthreads();
+
+    // exclusive scan of the bucket histogram; reserve one run per non-empty bucket
+    {
+      const int per = (nb + K2_THREADS - 1) / K2_THREADS;
+      const int b0 = tid * per;
+      int32_t sum = 0;
+      for (int b = b0; b < min(b0 + per, nb); ++b) sum += sm.hist[b];
+      int32_t tot;
+      int32_t run = block_exclusive_sum<K2_THREADS>(sum, s_scan, &tot);
+      if (tid == 0) s_kept = tot;
+      for (int b = b0; b < min(b0 + per, nb); ++b) {
+        const int32_t c = sm.hist[b];
+        sm.hist[b] = run;
+        if (c > 0) {
+          const int fb0 = b << sh;
+          const int fb1 = min((b + 1) << sh, nb_fine);
+          const int32_t base = ws.rbase[fb0];
+          const int32_t cap = ws.rbase[fb1] - base;
+          const int32_t g = atomicAdd(&ws.bfill[b], c);
+          if (g + c <= cap) {
+            sm.gd[b] = base + g - run;
+          } else {
+            sm.gd[b] = INT32_MIN;  // only reachable with duplicate x indices
+            atomicOr(&ws.st->status, ST_INDEX);
+          }
+        }
+        run += c;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < K2_IMAX; ++i) {
+      if (rank[i] >= 0) {
+        const int32_t s = sm.hist[rrow[i] >> lwb] + rank[i];
+        sm.srow[s] = rrow[i];
+        if (SEM != kOrAnd) sm.sval[s] = rval[i];
+      }
+    }
+    __syncthreads();
+    const int32_t kept = s_kept;
+    for (int32_t s = tid; s < kept; s += K2_THREADS) {
+      const uint32_t row = sm.srow[s];
+      const int32_t gd = sm.gd[row >> lwb];
+      if (gd == INT32_MIN) continue;
+      const int32_t dst = gd + s;
+      ws.brow[dst] = (uint16_t)(row & wmask);
+      if (SEM != kOrAnd) ws.bval[dst] = sm.sval[s];
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo, int nb_fine,
+                      const uint32_t* mask, int mask_comp, int grid, size_t smem, cudaStream_t s) {
+  switch (sem) {
+    case kPlusTimes:
+      k2_expand_scatter<kPlusTimes><<<grid, K2_THREADS, smem, s>>>(A.rowidx, A.val, ws, lwb_lo,
+                                                                    nb_fine, A.m, A.nnz, mask, mask_comp);
+      break;
+    case kMinSelect2nd:
+      k2_expand_scatter<kMinSelect2nd><<<grid, K2_THREADS, smem, s>>>(
+          A.rowidx, nullptr, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp);
+      break;
+    default:
+      k2_expand_scatter<kOrAnd><<<grid, K2_THREADS, smem, s>>>(A.rowidx, nullptr, ws, lwb_lo,
+                                                                nb_fine, A.m, A.nnz, mask, mask_comp);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// K3: per-bucket SPA merge + ordered compaction (+ BFS update)
+// ------------------------------------------------------------------------
+size_t k3_smem_bytes(int lwb) {
+  const size_t wb = (size_t)1 << lwb;
+  return wb * sizeof(uint32_t) + (wb / 32) * sizeof(uint32_t);
+}
+
+template <int SEM, bool BFS>
+__global__ void __launch_bounds__(K3_THREADS)
+k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __restrict__ y_idx,
+                uint32_t* __restrict__ y_val, int32_t y_cap, int32_t* __restrict__ d_nnz_y,
+                uint32_t* __restrict__ mask_update, int32_t* __restrict__ level,
+                int32_t* __restrict__ parent) {
+  extern __shared__ __align__(16) uint32_t k3_smem[];
+  __shared__ int32_t s_scan[K3_THREADS / 32 + 1];
+  __shared__ uint32_t s_b;
+  __shared__ unsigned long long s_off;
+  __shared__ int32_t s_tot;
+
+  DevState* st = ws.st;
+  const int tid = threadIdx.x;
+  const int lwb = st->lwb;
+  const int sh = lwb - lwb_lo;
+  const int32_t wb = 1 << lwb;
+  const uint32_t wmask = (uint32_t)wb - 1u;
+  const int nw = wb >> 5;
+  const int nb = (int)(((int64_t)m + wb - 1) >> lwb);
+  uint32_t* spa = k3_smem;
+  uint32_t* occ = k3_smem + wb;
+  const uint32_t ident = (SEM == kMinSelect2nd) ? 0x7fffffffu : 0u;  // min: INT32_MAX, plus: +0.0f
+  const int wpt = nw > K3_THREADS ? nw / K3_THREADS : 1;
+  const int32_t lvl = BFS ? st->level : 0;
+
+  if (blockIdx.x == 0 && tid == 0) {
+    // clear K1's per-call state for the next call
+    st->k1_ticket = 0u;
+    st->maxdeg = 0;
+    st->sumdeg2 = 0ull;
+  }
+  if (blockIdx.x == 0) {
+    const int nt1 = (st->f + K1_TILE - 1) / K1_TILE;
+    for (int i = tid; i < nt1; i += K3_THREADS) ws.k1_status[i] = 0ull;
+  }
+
+  for (;;) {
+    if (tid == 0) s_b = atomicAdd(&st->k3_ticket, 1u);
+    __syncthreads();
+    const uint32_t b = s_b;
+    if (b >= (uint32_t)nb) break;
+    const int32_t base = ws.rbase[b << sh];
+    const int32_t cap = ws.rbase[min((int)(b + 1) << sh, nb_fine)] - base;
+    const int32_t cnt = min(ws.bfill[b], cap);
+
+    if (cnt > 0) {
+      for (int w = tid; w < nw; w += K3_THREADS) occ[w] = 0u;
+      if (SEM != kOrAnd) {
+        if ((int64_t)cnt * 16 < wb) {
+          // partial initialisation: only the SPA slots this bucket touches (Sec. II-F)
+          for (int32_t e = tid; e < cnt; e += K3_THREADS) spa[ws.brow[base + e] & wmask] = ident;
+        } else {
+          for (int r = tid; r < wb; r += K3_THREADS) spa[r] = ident;
+        }
+      }
+      __syncthreads();
+      for (int32_t e = tid; e < cnt; e += K3_THREADS) {
+        const uint32_t r = ws.brow[base + e] & wmask;
+        if (SEM == kPlusTimes) {
+          atomicAdd(reinterpret_cast<float*>(spa + r), __uint_as_float(ws.bval[base + e]));
+        } else if (SEM == kMinSelect2nd) {
+          atomicMin(reinterpret_cast<int*>(spa + r), (int)ws.bval[base + e]);
+        }
+        const uint32_t bit = 1u << (r & 31);
+        if (!(occ[r >> 5] & bit)) atomicOr(occ + (r >> 5), bit);
+      }
+      __syncthreads();
+    }
+    // unique rows of this bucket (|uind_k|), then the offset of the bucket in y
+    int32_t c = 0;
+    const int w0 = tid * wpt;
+    if (cnt > 0 && w0 < nw)
+      for (int w = w0; w < w0 + wpt; ++w) c += __popc(occ[w]);
+    int32_t tot;
+    int32_t run = block_exclusive_sum<K3_THREADS>(c, s_scan, &tot);
+    if (tid == 0) {
+      s_off = lookback(ws.k3_status, b, (unsigned long long)tot, st);
+      s_tot = tot;
+    }
+    __syncthreads();
+    if (cnt > 0 && w0 < nw) {
+      int64_t pos = (int64_t)s_off + run;
+      for (int w = w0; w < w0 + wpt; ++w) {
+        uint32_t bits = occ[w];
+        if (BFS && bits) mask_update[(int64_t)b * nw + w] |= bits;
+        while (bits) {
+          const int r = (w << 5) + __ffs(bits) - 1;
+          bits &= bits - 1u;
+          const int32_t i = (int32_t)(b << lwb) + r;
+          if (pos < y_cap) {
+            y_idx[pos] = i;
+            if (SEM != kOrAnd && y_val) y_val[pos] = spa[r];
+          }
+          if (BFS) {
+            level[i] = lvl;
+            parent[i] = (int32_t)spa[r];
+          }
+          ++pos;
+        }
+      }
+    }
+    if (b == (uint32_t)nb - 1u && tid == 0) {
+      const int64_t total = (int64_t)s_off + s_tot;
+      st->nnz_y = (int32_t)total;
+      if (d_nnz_y) *d_nnz_y = (int32_t)total;
+      if (total > y_cap) atomicOr(&st->status, ST_CAPACITY);
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, int lwb_lo,
+                      int nb_fine, int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y,
+                      uint32_t* mask_update, int32_t* level, int32_t* parent, int grid,
+                      size_t smem, cudaStream_t s) {
+#define K3_ARGS ws, lwb_lo, nb_fine, A.m, y_idx, y_val, y_cap, d_nnz_y, mask_update, level, parent
+  if (bfs) {
+    k3_bucket_merge<kMinSelect2nd, true><<<grid, K3_THREADS, smem, s>>>(K3_ARGS);
+  } else if (sem == kPlusTimes) {
+    k3_bucket_merge<kPlusTimes, false><<<grid, K3_THREADS, smem, s>>>(K3_ARGS);
+  } else if (sem == kMinSelect2nd) {
+    k3_bucket_merge<kMinSelect2nd, false><<<grid, K3_THREADS, smem, s>>>(K3_ARGS);
+  } else {
+    k3_bucket_merge<kOrAnd, false><<<grid, K3_THREADS, smem, s>>>(K3_ARGS);
+  }
+#undef K3_ARGS
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// create-time: nonzeros per fine row-range bucket (sizes the bucket regions)
+// ------------------------------------------------------------------------
+__global__ void k_bucket_sizes(const int32_t* __restrict__ rowidx, int64_t nnz, int32_t m,
+                               int lwb_lo, int nb_fine, int32_t* __restrict__ counts,
+                               unsigned int* __restrict__ bad) {
+  extern __shared__ int32_t h[];
+  for (int b = threadIdx.x; b < nb_fine; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  unsigned int nbad = 0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = rowidx[p];
+    if (r < 0 || r >= m) {
+      ++nbad;
+      continue;
+    }
+    atomicAdd(&h[r >> lwb_lo], 1);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb_fine; b += blockDim.x)
+    if (h[b]) atomicAdd(&counts[b], h[b]);
+  if (nbad) atomicAdd(bad, nbad);
+}
+
+cudaError_t launch_bucket_sizes(const Matrix& A, int lwb_lo, int nb_fine, int32_t* counts,
+                                unsigned int* bad, cudaStream_t s) {
+  size_t smem = sizeof(int32_t) * (size_t)nb_fine;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_bucket_sizes, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_bucket_sizes<<<sms * 2, 1024, smem, s>>>(A.rowidx, A.nnz, A.m, lwb_lo, nb_fine, counts, bad);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// attributes and occupancy
+// ------------------------------------------------------------------------
+cudaError_t set_kernel_attributes(size_t k2_smem, size_t k3_smem_max) {
+  cudaError_t e;
+#define SET(fn, bytes)                                                                      \
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes)); \
+  if (e != cudaSuccess) return e;
+  SET(k2_expand_scatter<kPlusTimes>, k2_smem);
+  SET(k2_expand_scatter<kMinSelect2nd>, k2_smem);
+  SET(k2_expand_scatter<kOrAnd>, k2_smem);
+  SET((k3_bucket_merge<kPlusTimes, false>), k3_smem_max);
+  SET((k3_bucket_merge<kMinSelect2nd, false>), k3_smem_max);
+  SET((k3_bucket_merge<kOrAnd, false>), k3_smem_max);
+  SET((k3_bucket_merge<kMinSelect2nd, true>), k3_smem_max);
+#undef SET
+  return cudaSuccess;
+}
+
+int k3_blocks_per_sm(int sem, size_t smem) {
+  int nb = 0;
+  if (sem == kPlusTimes)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k3_bucket_merge<kPlusTimes, false>, K3_THREADS, smem);
+  else if (sem == kMinSelect2nd)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k3_bucket_merge<kMinSelect2nd, false>, K3_THREADS, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k3_bucket_merge<kOrAnd, false>, K3_THREADS, smem);
+  return nb > 0 ? nb : 1;
+}
+
+int k2_blocks_per_sm(int sem, size_t smem) {
+  int nb = 0;
+  if (sem == kPlusTimes)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k2_expand_scatter<kPlusTimes>, K2_THREADS, smem);
+  else if (sem == kMinSelect2nd)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k2_expand_scatter<kMinSelect2nd>, K2_THREADS, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k2_expand_scatter<kOrAnd>, K2_THREADS, smem);
+  return nb > 0 ? nb : 1;
+}
+
+}  // namespace spmspv
+
+namespace spmspv {
+// BFS level: x values are the vertex ids themselves (select2nd passes the
+// parent id), the count comes from the device, and the level advances.
+cudaError_t launch_k1_bfs(const Matrix& A, const Workspace& ws, int nb_fine, const int32_t* x_idx,
+                          const int32_t* f_dev, int grid, const Sched& sc, cudaStream_t s) {
+  k1_work_scan<<<grid, K1_THREADS, 0, s>>>(x_idx, reinterpret_cast<const uint32_t*>(x_idx), 0,
+                                           f_dev, A.colptr, A.n, A.nnz, ws, nb_fine, 1, sc.dir, sc.q,
+                                           sc.lwb, 1);
+  return cudaGetLastError();
+}
+}  // namespace spmspv

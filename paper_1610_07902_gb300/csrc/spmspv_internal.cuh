@@ -1,0 +1,119 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Nothing here is part of the C ABI (include/spmspv.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spmspv.h"
+
+namespace spmspv {
+
+// ---- semirings (same ids as the C ABI) ----
+constexpr int kPlusTimes = SPMSPV_PLUS_TIMES_F32;
+constexpr int kMinSelect2nd = SPMSPV_MIN_SELECT2ND_I32;
+constexpr int kOrAnd = SPMSPV_OR_AND_BOOL;
+
+// ---- K1: work estimation (prefix sum of selected column lengths) ----
+constexpr int K1_THREADS = 256;
+constexpr int K1_ITEMS = 8;
+constexpr int K1_TILE = K1_THREADS * K1_ITEMS;  // x entries per scan tile
+
+// ---- K2: expand + multiply + bucket scatter ----
+// Tile starts are recorded every QF products; a K2 tile covers q = QF or
+// 2*QF products (the "work quantum" of the schedule).
+constexpr int QF = 2048;
+constexpr int K2_THREADS = 512;
+constexpr int K2_IMAX = 8;                   // products per thread at q = 4096
+constexpr int QMAX = K2_THREADS * K2_IMAX;   // 4096
+
+// ---- K3: per-bucket SPA merge + ordered compaction ----
+constexpr int K3_THREADS = 512;
+
+// ---- bucket row widths ----
+constexpr int LWB_MIN = 7;    // 128 rows
+constexpr int LWB_MAX = 15;   // 32768 rows (local row fits in uint16)
+constexpr int NB_K2_MAX = 16384;  // buckets a K2 tile histograms in shared memory
+
+// ---- device status bits ----
+constexpr uint32_t ST_CAPACITY = SPMSPV_DEV_CAPACITY;
+constexpr uint32_t ST_TIMEOUT = SPMSPV_DEV_TIMEOUT;
+constexpr uint32_t ST_INDEX = 4u;     // an x index or bucket fill was out of range
+
+// Bounded waits: iterations of a spin (each with a short sleep) before a
+// wait gives up and records ST_TIMEOUT.
+constexpr uint32_t SPIN_LIMIT = 1u << 22;
+
+// Look-back status word: flag in the two top bits.
+constexpr unsigned long long LB_FLAG_AGG = 1ull << 62;
+constexpr unsigned long long LB_FLAG_INC = 2ull << 62;
+constexpr unsigned long long LB_FLAG_MASK = 3ull << 62;
+constexpr unsigned long long LB_VAL_MASK = ~LB_FLAG_MASK;
+
+// Per-call state kept on the device so that every launch has a fixed
+// configuration and the host never waits for a count.
+struct DevState {
+  int32_t f;           // nnz(x) of the current call
+  int32_t fc;          // x entries whose column is non-empty
+  int32_t W;           // products: sum of the selected column lengths
+  int32_t lwb;         // log2 bucket row width of this call
+  int32_t q;           // work quantum (products per K2 tile)
+  int32_t dir;         // 0 push (bucketed SpMSpV), 1 pull (masked SpMV)
+  uint32_t status;     // sticky SPMSPV_DEV_* / ST_* bits
+  int32_t nnz_y;       // size of y of the last call
+  uint32_t k1_ticket;  // dynamic tile counter of K1
+  uint32_t k3_ticket;  // dynamic bucket counter of K3
+  int32_t maxdeg;      // largest selected column length (selector feature)
+  int32_t prev_f;      // nnz(x) of the previous call (K1 status words to clear)
+  unsigned long long sumdeg2;  // sum of squared selected column lengths
+  int32_t level;       // BFS level written by the BFS-mode merge
+  int32_t pad[3];
+};
+
+struct Workspace {
+  DevState* st;
+  int32_t* cw;          // [n+1] exclusive work offsets of the compacted x entries
+  int32_t* cb;          // [n]   first position of each compacted x entry's column
+  uint32_t* cx;         // [n]   x value (32-bit payload) of each compacted entry
+  int32_t* tile_k0;     // [nnz/QF + 2] compacted entry holding product t*QF
+  unsigned long long* k1_status;  // [ceil(n/K1_TILE)] look-back words of K1
+  int32_t* bfill;       // [nb_fine] fill counters of the buckets
+  unsigned long long* k3_status;  // [nb_fine] look-back words of K3
+  int32_t* rbase;       // [nb_fine+1] first slot of each fine bucket's region
+  uint16_t* brow;       // [nnz] bucket entries: row offset inside the bucket
+  uint32_t* bval;       // [nnz] bucket entries: 32-bit value
+};
+
+struct Matrix {
+  int32_t m, n;
+  int64_t nnz;
+  const int32_t* colptr;
+  const int32_t* rowidx;
+  const float* val;  // NULL for a pattern matrix
+};
+
+struct Sched {
+  int dir;   // 0 push, 1 pull
+  int q;     // QF or 2*QF
+  int lwb;   // log2 bucket width
+};
+
+// Launchers (kernels.cu).  All launches are asynchronous on `s`.
+cudaError_t launch_k1(const Matrix& A, const Workspace& ws, int nb_fine, const int32_t* x_idx,
+                      const uint32_t* x_val, int f, const int32_t* f_dev, int grid,
+                      const Sched* forced, cudaStream_t s);
+cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo, int nb_fine,
+                      const uint32_t* mask, int mask_comp, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, int lwb_lo,
+                      int nb_fine, int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y,
+                      uint32_t* mask_update, int32_t* level, int32_t* parent, int grid,
+                      size_t smem, cudaStream_t s);
+cudaError_t launch_bucket_sizes(const Matrix& A, int lwb_lo, int nb_fine, int32_t* counts,
+                                unsigned int* bad, cudaStream_t s);
+size_t k2_smem_bytes(int nb_fine);
+size_t k3_smem_bytes(int lwb);
+cudaError_t set_kernel_attributes(size_t k2_smem, size_t k3_smem_max);
+int k3_blocks_per_sm(int sem, size_t smem);
+int k2_blocks_per_sm(int sem, size_t smem);
+
+}  // namespace spmspv

@@ -1,0 +1,218 @@
+"""Thin ctypes binding of the C ABI in include/spmspv.h.
+
+Every function here has the name of the C entry point it calls and only
+marshals arguments: torch tensors are passed as raw device pointers, the
+torch stream as a cudaStream_t.  All computation happens in the CUDA
+kernels of libspmspv.so.  If the library cannot be loaded the import fails
+loudly; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import builder as _build
+
+# ---- constants mirrored from include/spmspv.h ----
+SPMSPV_OK = 0
+SPMSPV_ERR_ARG = 1
+SPMSPV_ERR_STATE = 2
+SPMSPV_ERR_OOM = 3
+SPMSPV_ERR_CUDA = 4
+SPMSPV_ERR_CAPACITY = 5
+SPMSPV_ERR_TIMEOUT = 6
+SPMSPV_ERR_INDEX = 7
+SPMSPV_ERR_UNSUPPORTED = 8
+
+SPMSPV_VAL_NONE = 0
+SPMSPV_VAL_F32 = 1
+
+SPMSPV_CSC_PATTERN_SYMMETRIC = 1
+SPMSPV_CSC_SYMMETRIC = 3
+
+SPMSPV_PLUS_TIMES_F32 = 0
+SPMSPV_MIN_SELECT2ND_I32 = 1
+SPMSPV_OR_AND_BOOL = 2
+
+SPMSPV_MASK_COMPLEMENT = 1
+SPMSPV_SORTED_OUT = 2
+SPMSPV_SCHED_AUTO = 4
+SPMSPV_SCHED_FORCE = 8
+SPMSPV_SCHED_SHIFT = 8
+SPMSPV_NUM_SCHEDULES = 12
+
+SPMSPV_STAGE_SCAN = 0
+SPMSPV_STAGE_SELECT = 1
+SPMSPV_STAGE_SCATTER = 2
+SPMSPV_STAGE_MERGE = 3
+SPMSPV_STAGE_PULL = 4
+SPMSPV_NUM_STAGES = 5
+
+SPMSPV_DEV_CAPACITY = 1
+SPMSPV_DEV_TIMEOUT = 2
+SPMSPV_DEV_INDEX = 4
+
+
+def SPMSPV_SCHED_OPT(s: int) -> int:
+    return SPMSPV_SCHED_FORCE | (int(s) << SPMSPV_SCHED_SHIFT)
+
+
+class SpmspvError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s failed with status %d: %s" % (where, code, spmspv_last_error()))
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libspmspv.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise ImportError("libspmspv.so not found at %s; run build()" % _build.LIB)
+        lib = ctypes.CDLL(_build.LIB)
+        lib.spmspv_last_error.restype = ctypes.c_char_p
+        lib.spmspv_last_error.argtypes = []
+        lib.spmspv_create_csc.argtypes = [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int64, _P, _P, _P, ctypes.c_int, ctypes.c_uint32]
+        lib.spmspv_destroy.argtypes = [_P]
+        lib.spmspv_run.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_int32, _P, ctypes.c_uint32,
+                                   _P, _P, ctypes.c_int32, _P, _P]
+        lib.spmspv_device_status.argtypes = [_P, ctypes.POINTER(ctypes.c_uint32)]
+        lib.spmspv_last_work.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
+        lib.spmspv_profile_begin.argtypes = [_P]
+        lib.spmspv_profile_end.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_int32)]
+        _lib = lib
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(rc, where):
+    if rc != SPMSPV_OK:
+        raise SpmspvError(rc, where)
+
+
+def spmspv_last_error() -> str:
+    return load().spmspv_last_error().decode(errors="replace")
+
+
+def spmspv_create_csc(m, n, nnz, colptr, rowidx, val, val_type, flags=0):
+    """Returns an opaque handle (int).  colptr/rowidx/val are CUDA tensors."""
+    h = _P()
+    rc = load().spmspv_create_csc(ctypes.byref(h), int(m), int(n), int(nnz), _ptr(colptr),
+                                  _ptr(rowidx), _ptr(val), int(val_type), int(flags))
+    _check(rc, "spmspv_create_csc")
+    return h.value
+
+
+def spmspv_destroy(h):
+    _check(load().spmspv_destroy(h), "spmspv_destroy")
+
+
+def spmspv_run(h, semiring, x_idx, x_val, nnz_x, mask, opts, y_idx, y_val, y_capacity, d_nnz_y,
+               stream=None):
+    rc = load().spmspv_run(h, int(semiring), _ptr(x_idx), _ptr(x_val), int(nnz_x), _ptr(mask),
+                           int(opts), _ptr(y_idx), _ptr(y_val), int(y_capacity), _ptr(d_nnz_y),
+                           _stream(stream))
+    _check(rc, "spmspv_run")
+
+
+def spmspv_device_status(h) -> int:
+    v = ctypes.c_uint32(0)
+    _check(load().spmspv_device_status(h, ctypes.byref(v)), "spmspv_device_status")
+    return int(v.value)
+
+
+def spmspv_last_work(h) -> int:
+    v = ctypes.c_int64(0)
+    _check(load().spmspv_last_work(h, ctypes.byref(v)), "spmspv_last_work")
+    return int(v.value)
+
+
+def spmspv_profile_begin(h):
+    _check(load().spmspv_profile_begin(h), "spmspv_profile_begin")
+
+
+def spmspv_profile_end(h):
+    """Returns (per-stage summed milliseconds list, number of calls)."""
+    arr = (ctypes.c_double * SPMSPV_NUM_STAGES)()
+    n = ctypes.c_int32(0)
+    _check(load().spmspv_profile_end(h, arr, SPMSPV_NUM_STAGES, ctypes.byref(n)),
+           "spmspv_profile_end")
+    return [float(v) for v in arr], int(n.value)
+
+
+class CscMatrix:
+    """A CSC matrix resident on the GPU plus its library handle.
+
+    Keeps references to the device tensors the handle borrows, so they
+    outlive the handle.
+    """
+
+    def __init__(self, m, n, colptr, rowidx, val=None, flags=0, device="cuda"):
+        dev = torch.device(device)
+        self.m, self.n = int(m), int(n)
+        self.colptr = torch.as_tensor(colptr, dtype=torch.int32).to(dev).contiguous()
+        self.rowidx = torch.as_tensor(rowidx, dtype=torch.int32).to(dev).contiguous()
+        self.val = None if val is None else torch.as_tensor(val, dtype=torch.float32).to(dev).contiguous()
+        self.nnz = int(self.rowidx.numel())
+        self.handle = spmspv_create_csc(self.m, self.n, self.nnz, self.colptr, self.rowidx, self.val,
+                                        SPMSPV_VAL_NONE if self.val is None else SPMSPV_VAL_F32, flags)
+
+    def close(self):
+        if self.handle:
+            spmspv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def multiply(self, semiring, x_idx, x_val=None, mask=None, opts=0, y_capacity=None,
+                 stream=None, out=None):
+        """y = A (+).(x) x; returns (y_idx, y_val or None) as CUDA tensors (synchronises)."""
+        dev = self.colptr.device
+        cap = min(self.m, self.nnz) if y_capacity is None else int(y_capacity)
+        if out is None:
+            y_idx = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+            if semiring == SPMSPV_PLUS_TIMES_F32:
+                y_val = torch.empty(max(cap, 1), dtype=torch.float32, device=dev)
+            elif semiring == SPMSPV_MIN_SELECT2ND_I32:
+                y_val = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+            else:
+                y_val = None
+            nnz_y = torch.zeros(1, dtype=torch.int32, device=dev)
+        else:
+            y_idx, y_val, nnz_y = out
+        spmspv_run(self.handle, semiring, x_idx, x_val, int(x_idx.numel()), mask, opts, y_idx,
+                   y_val, cap, nnz_y, stream)
+        k = int(nnz_y.item())
+        kk = min(k, cap)
+        return y_idx[:kk], (None if y_val is None else y_val[:kk]), k
