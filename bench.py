@@ -44,10 +44,10 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def make_inputs():
+def make_inputs(scale=SCALE, f=F):
     import synth
-    A = synth.rmat(SCALE, EDGE_FACTOR, seed=SEED)
-    x_idx, x_val = synth.frontier(A.n, F, seed=1, stream=2)
+    A = synth.rmat(scale, EDGE_FACTOR, seed=SEED)
+    x_idx, x_val = synth.frontier(A.n, f, seed=1, stream=2)
     return A, x_idx, x_val
 
 
@@ -164,6 +164,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale", type=int, default=SCALE,
+                    help="R-MAT scale (smaller only for profiler captures)")
+    ap.add_argument("--nnz-x", type=int, default=F)
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="warm-up and timed steps only (for profiler captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -183,7 +188,10 @@ def main():
     from paper_1610_07902_gb300 import spmspv as S
     S.load()
 
-    A, x_idx, x_val = make_inputs()
+    F_ = args.nnz_x
+    A, x_idx, x_val = make_inputs(args.scale, F_)
+    workload = WORKLOAD if (args.scale, F_) == (SCALE, F) else "rmat%d_ef16_f%d_plus_times_f32" % (
+        args.scale, F_)
     dev = torch.device("cuda", local)
     Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val, device=dev)
     xi = torch.from_numpy(x_idx).to(dev)
@@ -197,7 +205,7 @@ def main():
     opts = S.SPMSPV_SORTED_OUT
 
     def step():
-        S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, xi, xv, F, None, opts, y_idx, y_val, cap,
+        S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, xi, xv, F_, None, opts, y_idx, y_val, cap,
                      nnz_y, stream)
 
     sampler = ClockSampler(local)
@@ -230,6 +238,13 @@ def main():
         t_ms = float(tt.item())
     ms_per_step = t_ms / args.steps
     gteps = W * args.steps * world / (t_ms * 1e-3) / 1e9
+    if args.kernels_only:
+        sampler.stop()
+        if rank == 0:
+            print(json.dumps({"workload": workload, "ms_per_step": ms_per_step, "value": gteps,
+                              "unit": "GTEPS", "kernels_only": True}), flush=True)
+        Ad.close()
+        return
 
     # per-stage device time (events around every kernel, separate pass)
     S.spmspv_profile_begin(Ad.handle)
@@ -256,7 +271,7 @@ def main():
         t0 = time.perf_counter()
         xi2.copy_(hx_i, non_blocking=True)
         xv2.copy_(hx_v, non_blocking=True)
-        S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, xi2, xv2, F, None, opts, y_idx, y_val,
+        S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, xi2, xv2, F_, None, opts, y_idx, y_val,
                      cap, nnz_y, stream)
         hn.copy_(nnz_y, non_blocking=True)
         hy_i[:ny].copy_(y_idx[:ny], non_blocking=True)
@@ -271,11 +286,11 @@ def main():
     peak, peak_kind = load_peaks()
     names = {S.SPMSPV_STAGE_SCAN: "work_scan", S.SPMSPV_STAGE_SCATTER: "expand_scatter",
              S.SPMSPV_STAGE_MERGE: "bucket_merge"}
-    alg = {S.SPMSPV_STAGE_SCAN: 16 * F, S.SPMSPV_STAGE_SCATTER: 8 * W,
+    alg = {S.SPMSPV_STAGE_SCAN: 16 * F_, S.SPMSPV_STAGE_SCATTER: 8 * W,
            S.SPMSPV_STAGE_MERGE: 8 * ny}
     dom = max(names, key=lambda s: stage_avg[s])
     achieved = alg[dom] / (stage_avg[dom] * 1e-3) / 1e9
-    path_bytes = compulsory_bytes(F, W, ny)
+    path_bytes = compulsory_bytes(F_, W, ny)
     path_gbs = path_bytes / (ms_per_step * 1e-3) / 1e9
 
     cpu = None
@@ -288,8 +303,8 @@ def main():
         "metric": METRIC, "value": gteps, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "graph": "rmat s22 ef16 symmetrised seed 1",
-                   "m": A.m, "nnz": A.nnz, "nnz_x": F, "products": W, "nnz_y": ny,
+        "config": {"workload": workload, "graph": "rmat s%d ef16 symmetrised seed 1" % args.scale,
+                   "m": A.m, "nnz": A.nnz, "nnz_x": F_, "products": W, "nnz_y": ny,
                    "semiring": "plus_times_f32", "l2": "flushed (256 MiB write) before each step",
                    "parallelism": "replicas" if world > 1 else "single_gpu"},
         "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
@@ -300,7 +315,7 @@ def main():
                           "unit": "GB/s", "frac": path_gbs / peak, "peak_kind": peak_kind},
         "stages_ms": {names[s]: stage_avg[s] for s in names},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_gteps, "unit": "GTEPS", "h2d_bytes_per_step": 8 * F,
+        "e2e": {"value": e2e_gteps, "unit": "GTEPS", "h2d_bytes_per_step": 8 * F_,
                 "d2h_bytes_per_step": 4 + 8 * ny},
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,

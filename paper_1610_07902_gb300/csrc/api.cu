@@ -186,7 +186,7 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
   size_t o_cx = take(sizeof(uint32_t) * (size_t)n);
   size_t o_tk = take(sizeof(int32_t) * (size_t)ntile_fine);
   size_t o_k1s = take(sizeof(unsigned long long) * (size_t)nt1);
-  size_t o_bf = take(sizeof(int32_t) * (size_t)h->nb_fine);
+  size_t o_bf = take(sizeof(int32_t) * (size_t)h->nb_fine * BFILL_STRIDE);
   size_t o_k3s = take(sizeof(unsigned long long) * (size_t)h->nb_fine);
   size_t o_rb = take(sizeof(int32_t) * ((size_t)h->nb_fine + 1));
   size_t o_br = take(sizeof(uint16_t) * (size_t)(nnz > 0 ? nnz : 1));

@@ -48,35 +48,54 @@ __device__ __forceinline__ void lb_store(unsigned long long* p, unsigned long lo
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
 __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
 
-// Exclusive look-back prefix for tile `tile`, given this tile's aggregate.
-// Publishes the aggregate, walks predecessors, publishes the inclusive
-// prefix and returns the exclusive one.  Waits are bounded: on give-up the
-// status word gets ST_TIMEOUT and the predecessor is treated as zero.
-__device__ unsigned long long lookback(unsigned long long* status, uint32_t tile,
-                                       unsigned long long agg, DevState* st) {
+// Exclusive look-back prefix for tile `tile`, computed by one full warp:
+// the warp publishes the tile's aggregate, then reads the status words of
+// the 32 nearest predecessors at once and sums back to the nearest one
+// that holds an inclusive prefix, sliding the window by 32 when none does.
+// Waits are bounded: on give-up the status word gets ST_TIMEOUT and the
+// words still missing count as empty inclusive prefixes.
+__device__ unsigned long long warp_lookback(unsigned long long* status, uint32_t tile,
+                                            unsigned long long agg, DevState* st) {
+  const int lane = threadIdx.x & 31;
   if (tile == 0) {
-    lb_store(status, LB_FLAG_INC | agg);
+    if (lane == 0) lb_store(status, LB_FLAG_INC | agg);
     return 0ull;
   }
-  lb_store(status + tile, LB_FLAG_AGG | agg);
+  if (lane == 0) lb_store(status + tile, LB_FLAG_AGG | agg);
   unsigned long long excl = 0;
-  int64_t idx = (int64_t)tile - 1;
-  while (idx >= 0) {
-    unsigned long long s;
+  int64_t base = (int64_t)tile - 1;
+  for (;;) {
+    const int64_t idx = base - lane;
+    unsigned long long s = idx >= 0 ? lb_load(status + idx) : LB_FLAG_INC;
     uint32_t spins = 0;
-    while (((s = lb_load(status + idx)) & LB_FLAG_MASK) == 0ull) {
+    for (;;) {
+      const bool ready = (s & LB_FLAG_MASK) != 0ull;
+      const unsigned rmask = __ballot_sync(0xffffffffu, ready);
+      const unsigned imask = __ballot_sync(0xffffffffu, (s & LB_FLAG_MASK) == LB_FLAG_INC);
+      unsigned need = 0xffffffffu;
+      if (imask) {
+        const int first = __ffs(imask) - 1;
+        need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
+      }
+      if ((rmask & need) == need) break;
       if (++spins > SPIN_LIMIT) {
-        atomicOr(&st->status, ST_TIMEOUT);
-        s = LB_FLAG_INC;  // give up: treat as an empty inclusive prefix
+        if (lane == 0) atomicOr(&st->status, ST_TIMEOUT);
+        if (!ready) s = LB_FLAG_INC;
         break;
       }
       __nanosleep(32);
+      if (!ready) s = lb_load(status + idx);
     }
-    excl += s & LB_VAL_MASK;
-    if ((s & LB_FLAG_MASK) == LB_FLAG_INC) break;
-    --idx;
+    const unsigned imask = __ballot_sync(0xffffffffu, (s & LB_FLAG_MASK) == LB_FLAG_INC);
+    const int stop = imask ? __ffs(imask) - 1 : 31;
+    unsigned long long v = lane <= stop ? (s & LB_VAL_MASK) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    excl += v;
+    if (imask) break;
+    base -= 32;
   }
-  lb_store(status + tile, LB_FLAG_INC | (excl + agg));
+  if (lane == 0) lb_store(status + tile, LB_FLAG_INC | (excl + agg));
   return excl;
 }
 
@@ -142,7 +161,7 @@ k1_work_scan(const int32_t* __restrict__ x_idx, const uint32_t* __restrict__ x_v
   if (blockIdx.x == 0) {
     // reset the state the later kernels of this call accumulate into
     for (int b = tid; b < nb_fine; b += K1_THREADS) {
-      ws.bfill[b] = 0;
+      ws.bfill[(size_t)b * BFILL_STRIDE] = 0;
       ws.k3_status[b] = 0ull;
     }
     if (tid == 0) {
@@ -210,7 +229,10 @@ k1_work_scan(const int32_t* __restrict__ x_idx, const uint32_t* __restrict__ x_v
     }
     unsigned long long btot;
     unsigned long long texcl = block_exclusive_sum<K1_THREADS>(tsum, s_warp, &btot);
-    if (tid == 0) s_prefix = lookback(ws.k1_status, tile, btot, st);
+    if (tid < 32) {
+      const unsigned long long pre = warp_lookback(ws.k1_status, tile, btot, st);
+      if (tid == 0) s_prefix = pre;
+    }
     __syncthreads();
     unsigned long long run = s_prefix + texcl;
 #pragma unroll
@@ -407,7 +429,7 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
           const int fb1 = min((b + 1) << sh, nb_fine);
           const int32_t base = ws.rbase[fb0];
           const int32_t cap = ws.rbase[fb1] - base;
-          const int32_t g = atomicAdd(&ws.bfill[b], c);
+          const int32_t g = atomicAdd(&ws.bfill[(size_t)b * BFILL_STRIDE], c);
           if (g + c <= cap) {
             sm.gd[b] = base + g - run;
           } else {
@@ -462,6 +484,87 @@ cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo,
 // ------------------------------------------------------------------------
 // K3: per-bucket SPA merge + ordered compaction (+ BFS update)
 // ------------------------------------------------------------------------
+template <int SEM>
+__device__ __forceinline__ void spa_apply(uint32_t* spa, uint32_t r, uint32_t v) {
+  if (SEM == kPlusTimes) atomicAdd(reinterpret_cast<float*>(spa + r), __uint_as_float(v));
+  else if (SEM == kMinSelect2nd) atomicMin(reinterpret_cast<int*>(spa + r), (int)v);
+}
+
+template <int SEM>
+__device__ __forceinline__ uint32_t sr_combine(uint32_t a, uint32_t b) {
+  if (SEM == kPlusTimes) return __float_as_uint(__uint_as_float(a) + __uint_as_float(b));
+  return (int)a < (int)b ? a : b;
+}
+
+// Merge `cnt` bucket entries into the SPA (Algorithm 1, Step 2).  Each
+// thread keeps its two most repeated rows in registers and combines their
+// entries there, so rows that receive thousands of products (hubs of
+// scale-free graphs) do not serialise on one shared-memory address; every
+// other entry goes straight to the SPA with a shared-memory atomic.
+template <int SEM>
+__device__ __forceinline__ void merge_bucket(const uint16_t* __restrict__ brow,
+                                             const uint32_t* __restrict__ bval, int32_t cnt,
+                                             uint32_t wmask, uint32_t* spa, uint32_t* occ) {
+  constexpr int U = 4;
+  const uint32_t NONE = 0xffffffffu;
+  uint32_t h0r = NONE, h1r = NONE, h0v = 0u, h1v = 0u, last = NONE;
+  int32_t h0n = 0, h1n = 0;
+  for (int32_t e0 = threadIdx.x; e0 < cnt; e0 += K3_THREADS * U) {
+    uint32_t r[U], v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int32_t e = e0 + u * K3_THREADS;
+      r[u] = NONE;
+      v[u] = 0u;
+      if (e < cnt) {
+        r[u] = __ldcs(brow + e) & wmask;
+        if (SEM != kOrAnd) v[u] = __ldcs(bval + e);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t rr = r[u];
+      if (rr == NONE) continue;
+      if (SEM == kOrAnd) {
+        const uint32_t bit = 1u << (rr & 31);
+        if (!(occ[rr >> 5] & bit)) atomicOr(occ + (rr >> 5), bit);
+        continue;
+      }
+      if (rr == h0r) {
+        h0v = sr_combine<SEM>(h0v, v[u]);
+        ++h0n;
+      } else if (rr == h1r) {
+        h1v = sr_combine<SEM>(h1v, v[u]);
+        ++h1n;
+      } else {
+        const uint32_t bit = 1u << (rr & 31);
+        if (!(occ[rr >> 5] & bit)) atomicOr(occ + (rr >> 5), bit);
+        if (rr == last) {
+          // second sighting: keep this row in the colder register slot
+          if (h1n <= h0n) {
+            if (h1r != NONE) spa_apply<SEM>(spa, h1r, h1v);
+            h1r = rr;
+            h1v = v[u];
+            h1n = 1;
+          } else {
+            if (h0r != NONE) spa_apply<SEM>(spa, h0r, h0v);
+            h0r = rr;
+            h0v = v[u];
+            h0n = 1;
+          }
+        } else {
+          spa_apply<SEM>(spa, rr, v[u]);
+          last = rr;
+        }
+      }
+    }
+  }
+  if (SEM != kOrAnd) {
+    if (h0r != NONE) spa_apply<SEM>(spa, h0r, h0v);
+    if (h1r != NONE) spa_apply<SEM>(spa, h1r, h1v);
+  }
+}
+
 size_t k3_smem_bytes(int lwb) {
   const size_t wb = (size_t)1 << lwb;
   return wb * sizeof(uint32_t) + (wb / 32) * sizeof(uint32_t);
@@ -511,7 +614,7 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __res
     if (b >= (uint32_t)nb) break;
     const int32_t base = ws.rbase[b << sh];
     const int32_t cap = ws.rbase[min((int)(b + 1) << sh, nb_fine)] - base;
-    const int32_t cnt = min(ws.bfill[b], cap);
+    const int32_t cnt = min(ws.bfill[(size_t)b * BFILL_STRIDE], cap);
 
     if (cnt > 0) {
       for (int w = tid; w < nw; w += K3_THREADS) occ[w] = 0u;
@@ -524,16 +627,7 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __res
         }
       }
       __syncthreads();
-      for (int32_t e = tid; e < cnt; e += K3_THREADS) {
-        const uint32_t r = ws.brow[base + e] & wmask;
-        if (SEM == kPlusTimes) {
-          atomicAdd(reinterpret_cast<float*>(spa + r), __uint_as_float(ws.bval[base + e]));
-        } else if (SEM == kMinSelect2nd) {
-          atomicMin(reinterpret_cast<int*>(spa + r), (int)ws.bval[base + e]);
-        }
-        const uint32_t bit = 1u << (r & 31);
-        if (!(occ[r >> 5] & bit)) atomicOr(occ + (r >> 5), bit);
-      }
+      merge_bucket<SEM>(ws.brow + base, ws.bval + base, cnt, wmask, spa, occ);
       __syncthreads();
     }
     // unique rows of this bucket (|uind_k|), then the offset of the bucket in y
@@ -543,9 +637,12 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __res
       for (int w = w0; w < w0 + wpt; ++w) c += __popc(occ[w]);
     int32_t tot;
     int32_t run = block_exclusive_sum<K3_THREADS>(c, s_scan, &tot);
-    if (tid == 0) {
-      s_off = lookback(ws.k3_status, b, (unsigned long long)tot, st);
-      s_tot = tot;
+    if (tid < 32) {
+      const unsigned long long pre = warp_lookback(ws.k3_status, b, (unsigned long long)tot, st);
+      if (tid == 0) {
+        s_off = pre;
+        s_tot = tot;
+      }
     }
     __syncthreads();
     if (cnt > 0 && w0 < nw) {

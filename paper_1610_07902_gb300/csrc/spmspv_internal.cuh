@@ -34,6 +34,7 @@ constexpr int K3_THREADS = 512;
 constexpr int LWB_MIN = 7;    // 128 rows
 constexpr int LWB_MAX = 15;   // 32768 rows (local row fits in uint16)
 constexpr int NB_K2_MAX = 16384;  // buckets a K2 tile histograms in shared memory
+constexpr int BFILL_STRIDE = 32;  // bucket fill counters sit 128 bytes apart (own L2 line)
 
 // ---- device status bits ----
 constexpr uint32_t ST_CAPACITY = SPMSPV_DEV_CAPACITY;
@@ -77,7 +78,7 @@ struct Workspace {
   uint32_t* cx;         // [n]   x value (32-bit payload) of each compacted entry
   int32_t* tile_k0;     // [nnz/QF + 2] compacted entry holding product t*QF
   unsigned long long* k1_status;  // [ceil(n/K1_TILE)] look-back words of K1
-  int32_t* bfill;       // [nb_fine] fill counters of the buckets
+  int32_t* bfill;       // [nb_fine * BFILL_STRIDE] fill counters of the buckets
   unsigned long long* k3_status;  // [nb_fine] look-back words of K3
   int32_t* rbase;       // [nb_fine+1] first slot of each fine bucket's region
   uint16_t* brow;       // [nnz] bucket entries: row offset inside the bucket
