@@ -50,10 +50,12 @@ __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
 
 // Exclusive look-back prefix for tile `tile`, computed by one full warp:
 // the warp publishes the tile's aggregate, then reads the status words of
-// the 32 nearest predecessors at once and sums back to the nearest one
-// that holds an inclusive prefix, sliding the window by 32 when none does.
+// its LB_WIN*32 nearest predecessors at once and sums back to the nearest
+// one that holds an inclusive prefix, sliding the window when none does.
 // Waits are bounded: on give-up the status word gets ST_TIMEOUT and the
 // words still missing count as empty inclusive prefixes.
+constexpr int LB_WIN = 4;
+
 __device__ unsigned long long warp_lookback(unsigned long long* status, uint32_t tile,
                                             unsigned long long agg, DevState* st) {
   const int lane = threadIdx.x & 31;
@@ -65,35 +67,58 @@ __device__ unsigned long long warp_lookback(unsigned long long* status, uint32_t
   unsigned long long excl = 0;
   int64_t base = (int64_t)tile - 1;
   for (;;) {
-    const int64_t idx = base - lane;
-    unsigned long long s = idx >= 0 ? lb_load(status + idx) : LB_FLAG_INC;
+    // word k*32+lane of the window is predecessor base - (k*32 + lane)
+    unsigned long long s[LB_WIN];
+#pragma unroll
+    for (int k = 0; k < LB_WIN; ++k) {
+      const int64_t idx = base - (k * 32 + lane);
+      s[k] = idx >= 0 ? lb_load(status + idx) : LB_FLAG_INC;
+    }
+    int first = -1;  // distance of the nearest inclusive prefix in the window
     uint32_t spins = 0;
     for (;;) {
-      const bool ready = (s & LB_FLAG_MASK) != 0ull;
-      const unsigned rmask = __ballot_sync(0xffffffffu, ready);
-      const unsigned imask = __ballot_sync(0xffffffffu, (s & LB_FLAG_MASK) == LB_FLAG_INC);
-      unsigned need = 0xffffffffu;
-      if (imask) {
-        const int first = __ffs(imask) - 1;
-        need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
+      first = -1;
+      bool all_ready = true;
+#pragma unroll
+      for (int k = 0; k < LB_WIN; ++k) {
+        const unsigned im = __ballot_sync(0xffffffffu, (s[k] & LB_FLAG_MASK) == LB_FLAG_INC);
+        const unsigned rm = __ballot_sync(0xffffffffu, (s[k] & LB_FLAG_MASK) != 0ull);
+        if (first < 0) {
+          if (im) {
+            const int f0 = __ffs(im) - 1;
+            const unsigned need = f0 == 31 ? 0xffffffffu : ((2u << f0) - 1u);
+            if ((rm & need) != need) all_ready = false;
+            first = k * 32 + f0;
+          } else if (rm != 0xffffffffu) {
+            all_ready = false;
+          }
+        }
       }
-      if ((rmask & need) == need) break;
+      if (all_ready) break;
       if (++spins > SPIN_LIMIT) {
         if (lane == 0) atomicOr(&st->status, ST_TIMEOUT);
-        if (!ready) s = LB_FLAG_INC;
-        break;
+#pragma unroll
+        for (int k = 0; k < LB_WIN; ++k)
+          if ((s[k] & LB_FLAG_MASK) == 0ull) s[k] = LB_FLAG_INC;
+        continue;  // recompute `first` with the missing words as empty prefixes
       }
       __nanosleep(32);
-      if (!ready) s = lb_load(status + idx);
+#pragma unroll
+      for (int k = 0; k < LB_WIN; ++k) {
+        const int64_t idx = base - (k * 32 + lane);
+        if ((s[k] & LB_FLAG_MASK) == 0ull && idx >= 0) s[k] = lb_load(status + idx);
+      }
     }
-    const unsigned imask = __ballot_sync(0xffffffffu, (s & LB_FLAG_MASK) == LB_FLAG_INC);
-    const int stop = imask ? __ffs(imask) - 1 : 31;
-    unsigned long long v = lane <= stop ? (s & LB_VAL_MASK) : 0ull;
+    const int stop = first < 0 ? LB_WIN * 32 - 1 : first;
+    unsigned long long v = 0;
+#pragma unroll
+    for (int k = 0; k < LB_WIN; ++k)
+      if (k * 32 + lane <= stop) v += s[k] & LB_VAL_MASK;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     excl += v;
-    if (imask) break;
-    base -= 32;
+    if (first >= 0) break;
+    base -= LB_WIN * 32;
   }
   if (lane == 0) lb_store(status + tile, LB_FLAG_INC | (excl + agg));
   return excl;
@@ -499,17 +524,21 @@ __device__ __forceinline__ uint32_t sr_combine(uint32_t a, uint32_t b) {
 // Merge `cnt` bucket entries into the SPA (Algorithm 1, Step 2).  Each
 // thread keeps its two most repeated rows in registers and combines their
 // entries there, so rows that receive thousands of products (hubs of
-// scale-free graphs) do not serialise on one shared-memory address; every
-// other entry goes straight to the SPA with a shared-memory atomic.
+// scale-free graphs) do not serialise on one shared-memory address.  For
+// (+,*), lanes of a warp that hold the same row are also combined first
+// (one shared-memory update per distinct row per warp step), because a
+// float add to shared memory retries when two lanes race on one word.
 template <int SEM>
 __device__ __forceinline__ void merge_bucket(const uint16_t* __restrict__ brow,
                                              const uint32_t* __restrict__ bval, int32_t cnt,
-                                             uint32_t wmask, uint32_t* spa, uint32_t* occ) {
+                                             uint32_t wmask, uint32_t* spa, uint32_t* occ,
+                                             float* wscratch) {
   constexpr int U = 4;
   const uint32_t NONE = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   uint32_t h0r = NONE, h1r = NONE, h0v = 0u, h1v = 0u, last = NONE;
   int32_t h0n = 0, h1n = 0;
-  for (int32_t e0 = threadIdx.x; e0 < cnt; e0 += K3_THREADS * U) {
+  for (int32_t e0 = threadIdx.x; e0 - lane < cnt; e0 += K3_THREADS * U) {
     uint32_t r[U], v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -524,38 +553,58 @@ __device__ __forceinline__ void merge_bucket(const uint16_t* __restrict__ brow,
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const uint32_t rr = r[u];
-      if (rr == NONE) continue;
       if (SEM == kOrAnd) {
-        const uint32_t bit = 1u << (rr & 31);
-        if (!(occ[rr >> 5] & bit)) atomicOr(occ + (rr >> 5), bit);
+        if (rr != NONE) {
+          const uint32_t bit = 1u << (rr & 31);
+          if (!(occ[rr >> 5] & bit)) atomicOr(occ + (rr >> 5), bit);
+        }
         continue;
       }
-      if (rr == h0r) {
-        h0v = sr_combine<SEM>(h0v, v[u]);
-        ++h0n;
-      } else if (rr == h1r) {
-        h1v = sr_combine<SEM>(h1v, v[u]);
-        ++h1n;
-      } else {
-        const uint32_t bit = 1u << (rr & 31);
-        if (!(occ[rr >> 5] & bit)) atomicOr(occ + (rr >> 5), bit);
-        if (rr == last) {
-          // second sighting: keep this row in the colder register slot
-          if (h1n <= h0n) {
-            if (h1r != NONE) spa_apply<SEM>(spa, h1r, h1v);
-            h1r = rr;
-            h1v = v[u];
-            h1n = 1;
-          } else {
-            if (h0r != NONE) spa_apply<SEM>(spa, h0r, h0v);
-            h0r = rr;
-            h0v = v[u];
-            h0n = 1;
-          }
+      bool direct = false;
+      if (rr != NONE) {
+        if (rr == h0r) {
+          h0v = sr_combine<SEM>(h0v, v[u]);
+          ++h0n;
+        } else if (rr == h1r) {
+          h1v = sr_combine<SEM>(h1v, v[u]);
+          ++h1n;
         } else {
-          spa_apply<SEM>(spa, rr, v[u]);
-          last = rr;
+          const uint32_t bit = 1u << (rr & 31);
+          if (!(occ[rr >> 5] & bit)) atomicOr(occ + (rr >> 5), bit);
+          if (rr == last) {
+            // second sighting in a row: keep this row in the colder register slot
+            if (h1n <= h0n) {
+              if (h1r != NONE) spa_apply<SEM>(spa, h1r, h1v);
+              h1r = rr;
+              h1v = v[u];
+              h1n = 1;
+            } else {
+              if (h0r != NONE) spa_apply<SEM>(spa, h0r, h0v);
+              h0r = rr;
+              h0v = v[u];
+              h0n = 1;
+            }
+          } else {
+            direct = true;
+            last = rr;
+          }
         }
+      }
+      if (SEM == kPlusTimes) {
+        const unsigned act = __ballot_sync(0xffffffffu, direct);
+        if (direct) {
+          const unsigned g = __match_any_sync(act, rr);
+          wscratch[lane] = __uint_as_float(v[u]);
+          __syncwarp(act);
+          if (lane == __ffs(g) - 1) {
+            float sum = __uint_as_float(v[u]);
+            for (unsigned o = g & (g - 1u); o; o &= o - 1u) sum += wscratch[__ffs(o) - 1];
+            atomicAdd(reinterpret_cast<float*>(spa + rr), sum);
+          }
+          __syncwarp(act);
+        }
+      } else if (direct) {
+        spa_apply<SEM>(spa, rr, v[u]);
       }
     }
   }
@@ -563,11 +612,6 @@ __device__ __forceinline__ void merge_bucket(const uint16_t* __restrict__ brow,
     if (h0r != NONE) spa_apply<SEM>(spa, h0r, h0v);
     if (h1r != NONE) spa_apply<SEM>(spa, h1r, h1v);
   }
-}
-
-size_t k3_smem_bytes(int lwb) {
-  const size_t wb = (size_t)1 << lwb;
-  return wb * sizeof(uint32_t) + (wb / 32) * sizeof(uint32_t);
 }
 
 template <int SEM, bool BFS>
@@ -581,6 +625,7 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __res
   __shared__ uint32_t s_b;
   __shared__ unsigned long long s_off;
   __shared__ int32_t s_tot;
+  __shared__ float s_wscratch[K3_THREADS];
 
   DevState* st = ws.st;
   const int tid = threadIdx.x;
@@ -627,7 +672,8 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __res
         }
       }
       __syncthreads();
-      merge_bucket<SEM>(ws.brow + base, ws.bval + base, cnt, wmask, spa, occ);
+      merge_bucket<SEM>(ws.brow + base, ws.bval + base, cnt, wmask, spa, occ,
+                        s_wscratch + (tid & ~31));
       __syncthreads();
     }
     // unique rows of this bucket (|uind_k|), then the offset of the bucket in y
