@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join("%s\n%s" % f for f in failed))
     tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs)
+    subprocess.check_call([nvcc()] + ARCH + ["-shared", "-Xlinker", "--no-undefined", "-o", tmp] + objs)
     os.replace(tmp, LIB)
     return LIB
 

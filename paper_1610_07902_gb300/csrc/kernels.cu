@@ -614,6 +614,11 @@ __device__ __forceinline__ void merge_bucket(const uint16_t* __restrict__ brow,
   }
 }
 
+size_t k3_smem_bytes(int lwb) {
+  const size_t wb = (size_t)1 << lwb;
+  return wb * sizeof(uint32_t) + (wb / 32) * sizeof(uint32_t);
+}
+
 template <int SEM, bool BFS>
 __global__ void __launch_bounds__(K3_THREADS)
 k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __restrict__ y_idx,
