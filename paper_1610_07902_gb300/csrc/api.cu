@@ -73,6 +73,8 @@ static int ilog2_ceil(int64_t v) {
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+int select_hot_rows(spmspv_handle* h);
+
 Sched decode_schedule(const spmspv_handle* h, int id) {
   Sched s;
   s.dir = id / 6;
@@ -107,7 +109,7 @@ int run_push(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_
                                      const Sched& sc, cudaStream_t s);
     e = launch_k1_bfs(h->A, h->ws, h->nb_fine, x_idx, f_dev, k1_grid, sc, s);
   } else {
-    e = launch_k1(h->A, h->ws, h->nb_fine, x_idx, x_val, f, f_dev, k1_grid, &sc, s);
+    e = launch_k1(sem, h->A, h->ws, h->nb_fine, x_idx, x_val, f, f_dev, k1_grid, &sc, s);
   }
   if (e != cudaSuccess) return cuda_fail(e, "work scan launch");
   prof_mark(h, SPMSPV_STAGE_SCAN, s);
@@ -121,6 +123,78 @@ int run_push(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_
                 mask_update, level, parent, k3_grid, k3_smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "bucket merge launch");
   prof_mark(h, SPMSPV_STAGE_MERGE, s);
+  return SPMSPV_OK;
+}
+
+static inline uint32_t hot_hash_bloom(int32_t row) { return ((uint32_t)row * 0x9E3779B1u) >> 16; }
+static inline uint32_t hot_hash_table(int32_t row) {
+  return ((uint32_t)row * 0x85EBCA77u) >> (32 - HOT_HT_LOG2);
+}
+
+int select_hot_rows(spmspv_handle* h) {
+  const int32_t m = h->A.m;
+  int32_t* d_deg = nullptr;
+  cudaError_t e = cudaMalloc(&d_deg, sizeof(int32_t) * ((size_t)m + 1));
+  if (e != cudaSuccess) return fail(SPMSPV_ERR_OOM, "row degree scratch: %s", cudaGetErrorString(e));
+  int32_t* d_max = d_deg + m;
+  cudaMemset(d_deg, 0, sizeof(int32_t) * ((size_t)m + 1));
+  e = launch_row_degrees(h->A, d_deg, d_max, 0);
+  int32_t maxdeg = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&maxdeg, d_max, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    cudaFree(d_deg);
+    return cuda_fail(e, "row degrees");
+  }
+  if (maxdeg < HOT_MIN_DEG) {
+    cudaFree(d_deg);
+    h->ws.nhot = 0;
+    return SPMSPV_OK;
+  }
+  std::vector<int32_t> deg((size_t)m);
+  e = cudaMemcpy(deg.data(), d_deg, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToHost);
+  cudaFree(d_deg);
+  if (e != cudaSuccess) return cuda_fail(e, "row degree copy");
+  std::vector<int32_t> cand;
+  for (int32_t i = 0; i < m; ++i)
+    if (deg[i] >= HOT_MIN_DEG) cand.push_back(i);
+  if ((int)cand.size() > HOT_MAX) {
+    std::nth_element(cand.begin(), cand.begin() + HOT_MAX, cand.end(), [&](int32_t a, int32_t b) {
+      return deg[a] != deg[b] ? deg[a] > deg[b] : a < b;
+    });
+    cand.resize(HOT_MAX);
+  }
+  std::sort(cand.begin(), cand.end());
+  const int nh = (int)cand.size();
+  std::vector<int32_t> rows(HOT_MAX, -1), key(HOT_HT, -1), start((size_t)h->nb_fine + 1, 0);
+  std::vector<uint32_t> bloom(HOT_BLOOM_WORDS, 0u);
+  std::vector<uint16_t> idx(HOT_HT, 0);
+  for (int i = 0; i < nh; ++i) {
+    const int32_t r = cand[i];
+    rows[i] = r;
+    const uint32_t hb = hot_hash_bloom(r);
+    bloom[hb >> 5] |= 1u << (hb & 31);
+    uint32_t t = hot_hash_table(r);
+    while (key[t] >= 0) t = (t + 1) & (HOT_HT - 1);
+    key[t] = r;
+    idx[t] = (uint16_t)i;
+    start[(r >> h->lwb_lo) + 1]++;
+  }
+  for (int i = 0; i < h->nb_fine; ++i) start[i + 1] += start[i];
+  char* b = (char*)h->ws_base;
+  (void)b;
+  e = cudaMemcpy((void*)h->ws.hot_rows, rows.data(), sizeof(int32_t) * HOT_MAX, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy((void*)h->ws.hot_bloom, bloom.data(), sizeof(uint32_t) * HOT_BLOOM_WORDS,
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy((void*)h->ws.hot_key, key.data(), sizeof(int32_t) * HOT_HT, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy((void*)h->ws.hot_idx, idx.data(), sizeof(uint16_t) * HOT_HT, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy((void*)h->ws.hot_start, start.data(), sizeof(int32_t) * start.size(),
+                   cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "hot row tables");
+  h->ws.nhot = nh;
   return SPMSPV_OK;
 }
 
@@ -189,6 +263,13 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
   size_t o_bf = take(sizeof(int32_t) * (size_t)h->nb_fine * BFILL_STRIDE);
   size_t o_k3s = take(sizeof(unsigned long long) * (size_t)h->nb_fine);
   size_t o_rb = take(sizeof(int32_t) * ((size_t)h->nb_fine + 1));
+  size_t o_hr = take(sizeof(int32_t) * HOT_MAX);
+  size_t o_hb = take(sizeof(uint32_t) * HOT_BLOOM_WORDS);
+  size_t o_hk = take(sizeof(int32_t) * HOT_HT);
+  size_t o_hi = take(sizeof(uint16_t) * HOT_HT);
+  size_t o_hs = take(sizeof(int32_t) * ((size_t)h->nb_fine + 1));
+  size_t o_hv = take(sizeof(uint32_t) * HOT_MAX);
+  size_t o_ht = take(sizeof(uint32_t) * HOT_MAX);
   size_t o_br = take(sizeof(uint16_t) * (size_t)(nnz > 0 ? nnz : 1));
   size_t o_bv = take(sizeof(uint32_t) * (size_t)(nnz > 0 ? nnz : 1));
   const size_t zero_bytes = o_br;  // everything before the bucket payload starts zeroed
@@ -211,6 +292,14 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
   h->ws.rbase = (int32_t*)(b + o_rb);
   h->ws.brow = (uint16_t*)(b + o_br);
   h->ws.bval = (uint32_t*)(b + o_bv);
+  h->ws.hot_rows = (const int32_t*)(b + o_hr);
+  h->ws.hot_bloom = (const uint32_t*)(b + o_hb);
+  h->ws.hot_key = (const int32_t*)(b + o_hk);
+  h->ws.hot_idx = (const uint16_t*)(b + o_hi);
+  h->ws.hot_start = (const int32_t*)(b + o_hs);
+  h->ws.hot_val = (uint32_t*)(b + o_hv);
+  h->ws.hot_touch = (uint32_t*)(b + o_ht);
+  h->ws.nhot = 0;
 
   int rc = SPMSPV_OK;
   do {
@@ -247,6 +336,9 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
     if (acc != nnz) { rc = fail(SPMSPV_ERR_ARG, "row histogram %lld != nnz %lld", (long long)acc, (long long)nnz); break; }
     if ((e = cudaMemcpy(h->ws.rbase, rbase.data(), sizeof(int32_t) * rbase.size(),
                         cudaMemcpyHostToDevice)) != cudaSuccess) { rc = cuda_fail(e, "rbase copy"); break; }
+    // hub rows: the (at most HOT_MAX) rows of largest degree with at least
+    // HOT_MIN_DEG nonzeros; their products are combined per K2 tile
+    if ((rc = select_hot_rows(h)) != SPMSPV_OK) break;
     // default schedule state
     DevState st0;
     memset(&st0, 0, sizeof(st0));
@@ -256,7 +348,7 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
       rc = cuda_fail(e, "state init");
       break;
     }
-    h->k2_smem = k2_smem_bytes(h->nb_fine);
+    h->k2_smem = k2_smem_bytes(h->nb_fine, h->ws.nhot > 0);
     h->k3_smem_max = k3_smem_bytes(lwb_hi);
     if ((e = set_kernel_attributes(h->k2_smem, h->k3_smem_max)) != cudaSuccess) {
       rc = cuda_fail(e, "kernel attributes");

@@ -168,7 +168,8 @@ constexpr unsigned long long K1_SUM_MASK = (1ull << 31) - 1;
 __global__ void __launch_bounds__(K1_THREADS)
 k1_work_scan(const int32_t* __restrict__ x_idx, const uint32_t* __restrict__ x_val, int f_host,
              const int32_t* __restrict__ f_dev, const int32_t* __restrict__ colptr, int32_t n,
-             int64_t nnz, Workspace ws, int nb_fine, int forced, int f_dir, int f_q, int f_lwb, int bfs_level_inc) {
+             int64_t nnz, Workspace ws, int nb_fine, int sem, int forced, int f_dir, int f_q,
+             int f_lwb, int bfs_level_inc) {
   __shared__ int32_t s_deg[K1_SMEM_WORDS];
   __shared__ int32_t s_c0[K1_SMEM_WORDS];
   __shared__ uint32_t s_xv[K1_SMEM_WORDS];
@@ -188,6 +189,11 @@ k1_work_scan(const int32_t* __restrict__ x_idx, const uint32_t* __restrict__ x_v
     for (int b = tid; b < nb_fine; b += K1_THREADS) {
       ws.bfill[(size_t)b * BFILL_STRIDE] = 0;
       ws.k3_status[b] = 0ull;
+    }
+    const uint32_t hid = sem == kMinSelect2nd ? 0x7fffffffu : 0u;
+    for (int h = tid; h < ws.nhot; h += K1_THREADS) {
+      ws.hot_val[h] = hid;
+      ws.hot_touch[h] = 0u;
     }
     if (tid == 0) {
       st->f = f;
@@ -304,32 +310,57 @@ k1_work_scan(const int32_t* __restrict__ x_idx, const uint32_t* __restrict__ x_v
   }
 }
 
-cudaError_t launch_k1(const Matrix& A, const Workspace& ws, int nb_fine, const int32_t* x_idx,
-                      const uint32_t* x_val, int f, const int32_t* f_dev, int grid,
-                      const Sched* forced, cudaStream_t s) {
+cudaError_t launch_k1(int sem, const Matrix& A, const Workspace& ws, int nb_fine,
+                      const int32_t* x_idx, const uint32_t* x_val, int f, const int32_t* f_dev,
+                      int grid, const Sched* forced, cudaStream_t s) {
   k1_work_scan<<<grid, K1_THREADS, 0, s>>>(x_idx, x_val, f, f_dev, A.colptr, A.n, A.nnz, ws, nb_fine,
-                                           forced ? 1 : 0, forced ? forced->dir : 0,
+                                           sem, forced ? 1 : 0, forced ? forced->dir : 0,
                                            forced ? forced->q : 0, forced ? forced->lwb : 0, 0);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------
+// Semiring helpers
+// ------------------------------------------------------------------------
+template <int SEM>
+__device__ __forceinline__ uint32_t sr_identity() {
+  return SEM == kMinSelect2nd ? 0x7fffffffu : 0u;  // min: INT32_MAX; plus: +0.0f
+}
+
+// SPA update in shared memory (atomic: other threads may hit the same row)
+template <int SEM>
+__device__ __forceinline__ void spa_apply(uint32_t* spa, uint32_t r, uint32_t v) {
+  if (SEM == kPlusTimes) atomicAdd(reinterpret_cast<float*>(spa + r), __uint_as_float(v));
+  else if (SEM == kMinSelect2nd) atomicMin(reinterpret_cast<int*>(spa + r), (int)v);
+}
+
+// Hot-row lookup: the rows of largest degree (fixed when the handle is
+// created) are listed in a 64 Ki-bit Bloom filter and an open-addressing
+// table in shared memory.  Returns the hot index of `row`, or -1.
+__device__ __forceinline__ int hot_lookup(int32_t row, const uint32_t* bloom, const int32_t* hkey,
+                                          const uint16_t* hidx) {
+  const uint32_t hb = ((uint32_t)row * 0x9E3779B1u) >> 16;
+  if (!((bloom[hb >> 5] >> (hb & 31)) & 1u)) return -1;
+  uint32_t t = ((uint32_t)row * 0x85EBCA77u) >> (32 - HOT_HT_LOG2);
+  for (int probe = 0; probe < HOT_HT; ++probe) {
+    const int32_t k = hkey[t];
+    if (k == row) return hidx[t];
+    if (k < 0) return -1;
+    t = (t + 1) & (HOT_HT - 1);
+  }
+  return -1;
+}
+
+// ------------------------------------------------------------------------
 // K2: expand + multiply + bucket scatter
 // ------------------------------------------------------------------------
-struct K2Smem {
-  uint32_t* bm;      // [QMAX/32] bit s set where a compacted entry starts at tile offset s
-  uint32_t* bmpre;   // [QMAX/32] exclusive prefix of popcounts of bm
-  int32_t* kbase;    // [QMAX+1]  cb[k] - cw[k] per local entry
-  uint32_t* kx;      // [QMAX+1]  x value per local entry
-  int32_t* hist;     // [nb]      per-bucket count, then exclusive offset in the stage
-  int32_t* gd;       // [nb]      global slot minus stage offset
-  uint32_t* srow;    // [QMAX]    staged rows, grouped by bucket
-  uint32_t* sval;    // [QMAX]    staged values
-};
-
-size_t k2_smem_bytes(int nb_fine) {
-  return sizeof(uint32_t) * (QMAX / 32) * 2 + sizeof(int32_t) * (QMAX + 1) * 2 +
-         sizeof(int32_t) * (size_t)nb_fine * 2 + sizeof(uint32_t) * QMAX * 2 + 64;
+size_t k2_smem_bytes(int nb_fine, bool hot) {
+  size_t b = sizeof(uint32_t) * (QMAX / 32) * 2 + sizeof(uint32_t) * QMAX * 2 +
+             sizeof(int32_t) * (QMAX + 1) * 2 + sizeof(int32_t) * (size_t)nb_fine * 2 + 64;
+  if (hot)
+    b += sizeof(uint32_t) * HOT_BLOOM_WORDS + sizeof(int32_t) * HOT_HT + sizeof(uint16_t) * HOT_HT +
+         sizeof(uint32_t) * HOT_MAX + sizeof(uint32_t) * (HOT_MAX / 32) + 64;
+  return b;
 }
 
 template <int SEM>
@@ -341,18 +372,23 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
   __shared__ int32_t s_scan[K2_THREADS / 32 + 1];
   __shared__ int32_t s_kept;
 
-  K2Smem sm;
-  {
-    unsigned char* p = k2_smem_raw;
-    sm.bm = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX / 32);
-    sm.bmpre = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX / 32);
-    sm.srow = (uint32_t*)p; p += sizeof(uint32_t) * QMAX;
-    sm.sval = (uint32_t*)p; p += sizeof(uint32_t) * QMAX;
-    sm.kbase = (int32_t*)p; p += sizeof(int32_t) * (QMAX + 1);
-    sm.kx = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX + 1);
-    sm.hist = (int32_t*)p; p += sizeof(int32_t) * nb_fine;
-    sm.gd = (int32_t*)p;
-  }
+  // shared-memory carve (sizes as in k2_smem_bytes)
+  unsigned char* p = k2_smem_raw;
+  uint32_t* bm = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX / 32);      // entry starts in the tile
+  uint32_t* bmpre = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX / 32);   // prefix popcounts of bm
+  uint32_t* srow = (uint32_t*)p; p += sizeof(uint32_t) * QMAX;           // staged rows by bucket
+  uint32_t* sval = (uint32_t*)p; p += sizeof(uint32_t) * QMAX;           // staged values
+  int32_t* kbase = (int32_t*)p; p += sizeof(int32_t) * (QMAX + 1);       // cb[k] - cw[k]
+  uint32_t* kx = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX + 1);       // x value per entry
+  int32_t* hist = (int32_t*)p; p += sizeof(int32_t) * nb_fine;           // counts, then stage offsets
+  int32_t* gd = (int32_t*)p; p += sizeof(int32_t) * nb_fine;             // bucket slot - stage offset
+  const int nhot = ws.nhot;
+  uint32_t* bloom = (uint32_t*)p;
+  int32_t* hkey = (int32_t*)(bloom + HOT_BLOOM_WORDS);
+  uint16_t* hidx = (uint16_t*)(hkey + HOT_HT);
+  uint32_t* hacc = (uint32_t*)(hidx + HOT_HT);
+  uint32_t* htb = hacc + HOT_MAX;
+
   const DevState* st = ws.st;
   const int tid = threadIdx.x;
   const int32_t W = st->W, fc = st->fc, q = st->q, lwb = st->lwb;
@@ -361,6 +397,17 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
   const uint32_t wmask = (1u << lwb) - 1u;
   const int items = q / K2_THREADS;
   const int ntiles = (int)(((int64_t)W + q - 1) / q);
+  const uint32_t ident = sr_identity<SEM>();
+
+  if (nhot > 0) {
+    for (int i = tid; i < HOT_BLOOM_WORDS; i += K2_THREADS) bloom[i] = ws.hot_bloom[i];
+    for (int i = tid; i < HOT_HT; i += K2_THREADS) {
+      hkey[i] = ws.hot_key[i];
+      hidx[i] = ws.hot_idx[i];
+    }
+    for (int i = tid; i < HOT_MAX; i += K2_THREADS) hacc[i] = ident;
+    for (int i = tid; i < HOT_MAX / 32; i += K2_THREADS) htb[i] = 0u;
+  }
 
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int32_t p0 = t * q;
@@ -369,16 +416,16 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
     const int32_t kend = (p0 + np == W) ? fc : ws.tile_k0[(p0 + np) / QF] + 1;
     const int32_t nk = max(0, min(kend - k0, QMAX + 1));
 
-    for (int i = tid; i < QMAX / 32; i += K2_THREADS) sm.bm[i] = 0u;
-    for (int b = tid; b < nb; b += K2_THREADS) sm.hist[b] = 0;
+    for (int i = tid; i < QMAX / 32; i += K2_THREADS) bm[i] = 0u;
+    for (int b = tid; b < nb; b += K2_THREADS) hist[b] = 0;
     __syncthreads();
     for (int l = tid; l < nk; l += K2_THREADS) {
       const int32_t k = k0 + l;
       const int32_t w = ws.cw[k];
-      sm.kbase[l] = ws.cb[k] - w;
-      sm.kx[l] = ws.cx[k];
+      kbase[l] = ws.cb[k] - w;
+      kx[l] = ws.cx[k];
       const int32_t s0 = w - p0;
-      if (s0 > 0 && s0 < np) atomicOr(&sm.bm[s0 >> 5], 1u << (s0 & 31));
+      if (s0 > 0 && s0 < np) atomicOr(&bm[s0 >> 5], 1u << (s0 & 31));
     }
     __syncthreads();
     if (tid < 32) {
@@ -386,7 +433,7 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
       uint32_t tot = 0;
 #pragma unroll
       for (int i = 0; i < QMAX / 32 / 32; ++i) {
-        c[i] = __popc(sm.bm[tid * (QMAX / 32 / 32) + i]);
+        c[i] = __popc(bm[tid * (QMAX / 32 / 32) + i]);
         tot += c[i];
       }
       uint32_t x = tot;
@@ -398,7 +445,7 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
       uint32_t run = x - tot;
 #pragma unroll
       for (int i = 0; i < QMAX / 32 / 32; ++i) {
-        sm.bmpre[tid * (QMAX / 32 / 32) + i] = run;
+        bmpre[tid * (QMAX / 32 / 32) + i] = run;
         run += c[i];
       }
     }
@@ -414,41 +461,62 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
       rval[i] = 0u;
       if (i < items && pl < np) {
         const int wd = pl >> 5;
-        const uint32_t kl = sm.bmpre[wd] + __popc(sm.bm[wd] & (0xffffffffu >> (31 - (pl & 31))));
-        const int32_t pos = sm.kbase[kl] + p0 + pl;
+        const uint32_t kl = bmpre[wd] + __popc(bm[wd] & (0xffffffffu >> (31 - (pl & 31))));
+        const int32_t pos = kbase[kl] + p0 + pl;
         if ((uint32_t)pos >= (uint32_t)nnz) continue;  // unreachable with valid inputs
         const int32_t row = ld_stream(rowidx + pos);
         uint32_t v = 0u;
         if (SEM == kPlusTimes) {
-          const float xv = __uint_as_float(sm.kx[kl]);
+          const float xv = __uint_as_float(kx[kl]);
           v = __float_as_uint(val ? __fmul_rn(ld_stream(val + pos), xv) : xv);
         } else if (SEM == kMinSelect2nd) {
-          v = sm.kx[kl];
+          v = kx[kl];
         }
         bool keep = true;
         if (mask) {
           const uint32_t bit = (__ldg(mask + (row >> 5)) >> (row & 31)) & 1u;
           keep = mask_comp ? (bit == 0u) : (bit != 0u);
         }
-        if (keep) rank[i] = atomicAdd(&sm.hist[row >> lwb], 1);
+        if (keep) {
+          const int hs = nhot > 0 ? hot_lookup(row, bloom, hkey, hidx) : -1;
+          if (hs >= 0) {
+            // a hub row: combine its products of this tile in shared memory
+            spa_apply<SEM>(hacc, (uint32_t)hs, v);
+            const uint32_t bit = 1u << (hs & 31);
+            if (!(htb[hs >> 5] & bit)) atomicOr(&htb[hs >> 5], bit);
+          } else {
+            rank[i] = atomicAdd(&hist[row >> lwb], 1);
+          }
+        }
         rrow[i] = (uint32_t)row;
         rval[i] = v;
       }
     }
     __syncthreads();
 
+    // flush this tile's hub sums with one global atomic per touched hub row
+    for (int hs = tid; hs < nhot; hs += K2_THREADS) {
+      if ((htb[hs >> 5] >> (hs & 31)) & 1u) {
+        if (SEM == kPlusTimes)
+          atomicAdd(reinterpret_cast<float*>(ws.hot_val + hs), __uint_as_float(hacc[hs]));
+        else if (SEM == kMinSelect2nd)
+          atomicMin(reinterpret_cast<int*>(ws.hot_val + hs), (int)hacc[hs]);
+        ws.hot_touch[hs] = 1u;
+        hacc[hs] = ident;
+      }
+    }
     // exclusive scan of the bucket histogram; reserve one run per non-empty bucket
     {
       const int per = (nb + K2_THREADS - 1) / K2_THREADS;
       const int b0 = tid * per;
       int32_t sum = 0;
-      for (int b = b0; b < min(b0 + per, nb); ++b) sum += sm.hist[b];
+      for (int b = b0; b < min(b0 + per, nb); ++b) sum += hist[b];
       int32_t tot;
       int32_t run = block_exclusive_sum<K2_THREADS>(sum, s_scan, &tot);
       if (tid == 0) s_kept = tot;
       for (int b = b0; b < min(b0 + per, nb); ++b) {
-        const int32_t c = sm.hist[b];
-        sm.hist[b] = run;
+        const int32_t c = hist[b];
+        hist[b] = run;
         if (c > 0) {
           const int fb0 = b << sh;
           const int fb1 = min((b + 1) << sh, nb_fine);
@@ -456,9 +524,9 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
           const int32_t cap = ws.rbase[fb1] - base;
           const int32_t g = atomicAdd(&ws.bfill[(size_t)b * BFILL_STRIDE], c);
           if (g + c <= cap) {
-            sm.gd[b] = base + g - run;
+            gd[b] = base + g - run;
           } else {
-            sm.gd[b] = INT32_MIN;  // only reachable with duplicate x indices
+            gd[b] = INT32_MIN;  // only reachable with duplicate x indices
             atomicOr(&ws.st->status, ST_INDEX);
           }
         }
@@ -466,23 +534,24 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
       }
     }
     __syncthreads();
+    if (nhot > 0 && tid < HOT_MAX / 32) htb[tid] = 0u;
 #pragma unroll
     for (int i = 0; i < K2_IMAX; ++i) {
       if (rank[i] >= 0) {
-        const int32_t s = sm.hist[rrow[i] >> lwb] + rank[i];
-        sm.srow[s] = rrow[i];
-        if (SEM != kOrAnd) sm.sval[s] = rval[i];
+        const int32_t s = hist[rrow[i] >> lwb] + rank[i];
+        srow[s] = rrow[i];
+        if (SEM != kOrAnd) sval[s] = rval[i];
       }
     }
     __syncthreads();
     const int32_t kept = s_kept;
     for (int32_t s = tid; s < kept; s += K2_THREADS) {
-      const uint32_t row = sm.srow[s];
-      const int32_t gd = sm.gd[row >> lwb];
-      if (gd == INT32_MIN) continue;
-      const int32_t dst = gd + s;
+      const uint32_t row = srow[s];
+      const int32_t g = gd[row >> lwb];
+      if (g == INT32_MIN) continue;
+      const int32_t dst = g + s;
       ws.brow[dst] = (uint16_t)(row & wmask);
-      if (SEM != kOrAnd) ws.bval[dst] = sm.sval[s];
+      if (SEM != kOrAnd) ws.bval[dst] = sval[s];
     }
     __syncthreads();
   }
@@ -492,16 +561,16 @@ cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo,
                       const uint32_t* mask, int mask_comp, int grid, size_t smem, cudaStream_t s) {
   switch (sem) {
     case kPlusTimes:
-      k2_expand_scatter<kPlusTimes><<<grid, K2_THREADS, smem, s>>>(A.rowidx, A.val, ws, lwb_lo,
-                                                                    nb_fine, A.m, A.nnz, mask, mask_comp);
+      k2_expand_scatter<kPlusTimes><<<grid, K2_THREADS, smem, s>>>(
+          A.rowidx, A.val, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp);
       break;
     case kMinSelect2nd:
       k2_expand_scatter<kMinSelect2nd><<<grid, K2_THREADS, smem, s>>>(
           A.rowidx, nullptr, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp);
       break;
     default:
-      k2_expand_scatter<kOrAnd><<<grid, K2_THREADS, smem, s>>>(A.rowidx, nullptr, ws, lwb_lo,
-                                                                nb_fine, A.m, A.nnz, mask, mask_comp);
+      k2_expand_scatter<kOrAnd><<<grid, K2_THREADS, smem, s>>>(
+          A.rowidx, nullptr, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp);
   }
   return cudaGetLastError();
 }
@@ -509,111 +578,6 @@ cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo,
 // ------------------------------------------------------------------------
 // K3: per-bucket SPA merge + ordered compaction (+ BFS update)
 // ------------------------------------------------------------------------
-template <int SEM>
-__device__ __forceinline__ void spa_apply(uint32_t* spa, uint32_t r, uint32_t v) {
-  if (SEM == kPlusTimes) atomicAdd(reinterpret_cast<float*>(spa + r), __uint_as_float(v));
-  else if (SEM == kMinSelect2nd) atomicMin(reinterpret_cast<int*>(spa + r), (int)v);
-}
-
-template <int SEM>
-__device__ __forceinline__ uint32_t sr_combine(uint32_t a, uint32_t b) {
-  if (SEM == kPlusTimes) return __float_as_uint(__uint_as_float(a) + __uint_as_float(b));
-  return (int)a < (int)b ? a : b;
-}
-
-// Merge `cnt` bucket entries into the SPA (Algorithm 1, Step 2).  Each
-// thread keeps its two most repeated rows in registers and combines their
-// entries there, so rows that receive thousands of products (hubs of
-// scale-free graphs) do not serialise on one shared-memory address.  For
-// (+,*), lanes of a warp that hold the same row are also combined first
-// (one shared-memory update per distinct row per warp step), because a
-// float add to shared memory retries when two lanes race on one word.
-template <int SEM>
-__device__ __forceinline__ void merge_bucket(const uint16_t* __restrict__ brow,
-                                             const uint32_t* __restrict__ bval, int32_t cnt,
-                                             uint32_t wmask, uint32_t* spa, uint32_t* occ,
-                                             float* wscratch) {
-  constexpr int U = 4;
-  const uint32_t NONE = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  uint32_t h0r = NONE, h1r = NONE, h0v = 0u, h1v = 0u, last = NONE;
-  int32_t h0n = 0, h1n = 0;
-  for (int32_t e0 = threadIdx.x; e0 - lane < cnt; e0 += K3_THREADS * U) {
-    uint32_t r[U], v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int32_t e = e0 + u * K3_THREADS;
-      r[u] = NONE;
-      v[u] = 0u;
-      if (e < cnt) {
-        r[u] = __ldcs(brow + e) & wmask;
-        if (SEM != kOrAnd) v[u] = __ldcs(bval + e);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint32_t rr = r[u];
-      if (SEM == kOrAnd) {
-        if (rr != NONE) {
-          const uint32_t bit = 1u << (rr & 31);
-          if (!(occ[rr >> 5] & bit)) atomicOr(occ + (rr >> 5), bit);
-        }
-        continue;
-      }
-      bool direct = false;
-      if (rr != NONE) {
-        if (rr == h0r) {
-          h0v = sr_combine<SEM>(h0v, v[u]);
-          ++h0n;
-        } else if (rr == h1r) {
-          h1v = sr_combine<SEM>(h1v, v[u]);
-          ++h1n;
-        } else {
-          const uint32_t bit = 1u << (rr & 31);
-          if (!(occ[rr >> 5] & bit)) atomicOr(occ + (rr >> 5), bit);
-          if (rr == last) {
-            // second sighting in a row: keep this row in the colder register slot
-            if (h1n <= h0n) {
-              if (h1r != NONE) spa_apply<SEM>(spa, h1r, h1v);
-              h1r = rr;
-              h1v = v[u];
-              h1n = 1;
-            } else {
-              if (h0r != NONE) spa_apply<SEM>(spa, h0r, h0v);
-              h0r = rr;
-              h0v = v[u];
-              h0n = 1;
-            }
-          } else {
-            direct = true;
-            last = rr;
-          }
-        }
-      }
-      if (SEM == kPlusTimes) {
-        const unsigned act = __ballot_sync(0xffffffffu, direct);
-        if (direct) {
-          const unsigned g = __match_any_sync(act, rr);
-          wscratch[lane] = __uint_as_float(v[u]);
-          __syncwarp(act);
-          if (lane == __ffs(g) - 1) {
-            float sum = __uint_as_float(v[u]);
-            for (unsigned o = g & (g - 1u); o; o &= o - 1u) sum += wscratch[__ffs(o) - 1];
-            atomicAdd(reinterpret_cast<float*>(spa + rr), sum);
-          }
-          __syncwarp(act);
-        }
-      } else if (direct) {
-        spa_apply<SEM>(spa, rr, v[u]);
-      }
-    }
-  }
-  if (SEM != kOrAnd) {
-    if (h0r != NONE) spa_apply<SEM>(spa, h0r, h0v);
-    if (h1r != NONE) spa_apply<SEM>(spa, h1r, h1v);
-  }
-}
-
 size_t k3_smem_bytes(int lwb) {
   const size_t wb = (size_t)1 << lwb;
   return wb * sizeof(uint32_t) + (wb / 32) * sizeof(uint32_t);
@@ -630,7 +594,6 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __res
   __shared__ uint32_t s_b;
   __shared__ unsigned long long s_off;
   __shared__ int32_t s_tot;
-  __shared__ float s_wscratch[K3_THREADS];
 
   DevState* st = ws.st;
   const int tid = threadIdx.x;
@@ -642,9 +605,10 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __res
   const int nb = (int)(((int64_t)m + wb - 1) >> lwb);
   uint32_t* spa = k3_smem;
   uint32_t* occ = k3_smem + wb;
-  const uint32_t ident = (SEM == kMinSelect2nd) ? 0x7fffffffu : 0u;  // min: INT32_MAX, plus: +0.0f
+  const uint32_t ident = sr_identity<SEM>();
   const int wpt = nw > K3_THREADS ? nw / K3_THREADS : 1;
   const int32_t lvl = BFS ? st->level : 0;
+  const int nhot = ws.nhot;
 
   if (blockIdx.x == 0 && tid == 0) {
     // clear K1's per-call state for the next call
@@ -662,29 +626,67 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __res
     __syncthreads();
     const uint32_t b = s_b;
     if (b >= (uint32_t)nb) break;
-    const int32_t base = ws.rbase[b << sh];
-    const int32_t cap = ws.rbase[min((int)(b + 1) << sh, nb_fine)] - base;
+    const int fb0 = (int)(b << sh), fb1 = min((int)(b + 1) << sh, nb_fine);
+    const int32_t base = ws.rbase[fb0];
+    const int32_t cap = ws.rbase[fb1] - base;
     const int32_t cnt = min(ws.bfill[(size_t)b * BFILL_STRIDE], cap);
+    const int hs0 = nhot > 0 ? ws.hot_start[fb0] : 0;
+    const int hs1 = nhot > 0 ? ws.hot_start[fb1] : 0;
+    const int32_t row0 = (int32_t)(b << lwb);
+    int hot_any = 0;
+    for (int hs = hs0 + tid; hs < hs1; hs += K3_THREADS) hot_any |= (int)ws.hot_touch[hs];
+    const int active = __syncthreads_or(cnt > 0 || hot_any);
 
-    if (cnt > 0) {
+    if (active) {
       for (int w = tid; w < nw; w += K3_THREADS) occ[w] = 0u;
       if (SEM != kOrAnd) {
         if ((int64_t)cnt * 16 < wb) {
           // partial initialisation: only the SPA slots this bucket touches (Sec. II-F)
           for (int32_t e = tid; e < cnt; e += K3_THREADS) spa[ws.brow[base + e] & wmask] = ident;
+          for (int hs = hs0 + tid; hs < hs1; hs += K3_THREADS) spa[ws.hot_rows[hs] - row0] = ident;
         } else {
           for (int r = tid; r < wb; r += K3_THREADS) spa[r] = ident;
         }
       }
       __syncthreads();
-      merge_bucket<SEM>(ws.brow + base, ws.bval + base, cnt, wmask, spa, occ,
-                        s_wscratch + (tid & ~31));
+      // Step 2 of Algorithm 1: merge the bucket into the SPA
+      constexpr int U = 4;
+      const uint16_t* brow = ws.brow + base;
+      const uint32_t* bval = ws.bval + base;
+      for (int32_t e0 = tid; e0 < cnt; e0 += K3_THREADS * U) {
+        uint32_t r[U], v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int32_t e = e0 + u * K3_THREADS;
+          r[u] = 0xffffffffu;
+          v[u] = 0u;
+          if (e < cnt) {
+            r[u] = __ldcs(brow + e) & wmask;
+            if (SEM != kOrAnd) v[u] = __ldcs(bval + e);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const uint32_t rr = r[u];
+          if (rr == 0xffffffffu) continue;
+          const uint32_t bit = 1u << (rr & 31);
+          if (!(occ[rr >> 5] & bit)) atomicOr(occ + (rr >> 5), bit);
+          spa_apply<SEM>(spa, rr, v[u]);
+        }
+      }
+      // hub rows of this bucket: their products were combined in K2
+      for (int hs = hs0 + tid; hs < hs1; hs += K3_THREADS) {
+        if (!ws.hot_touch[hs]) continue;
+        const uint32_t rr = (uint32_t)(ws.hot_rows[hs] - row0);
+        atomicOr(occ + (rr >> 5), 1u << (rr & 31));
+        spa_apply<SEM>(spa, rr, ws.hot_val[hs]);
+      }
       __syncthreads();
     }
     // unique rows of this bucket (|uind_k|), then the offset of the bucket in y
     int32_t c = 0;
     const int w0 = tid * wpt;
-    if (cnt > 0 && w0 < nw)
+    if (active && w0 < nw)
       for (int w = w0; w < w0 + wpt; ++w) c += __popc(occ[w]);
     int32_t tot;
     int32_t run = block_exclusive_sum<K3_THREADS>(c, s_scan, &tot);
@@ -696,7 +698,8 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __res
       }
     }
     __syncthreads();
-    if (cnt > 0 && w0 < nw) {
+    // Step 3: this bucket's rows, ascending, at its offset in y
+    if (active && w0 < nw) {
       int64_t pos = (int64_t)s_off + run;
       for (int w = w0; w < w0 + wpt; ++w) {
         uint32_t bits = occ[w];
@@ -704,7 +707,7 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __res
         while (bits) {
           const int r = (w << 5) + __ffs(bits) - 1;
           bits &= bits - 1u;
-          const int32_t i = (int32_t)(b << lwb) + r;
+          const int32_t i = row0 + r;
           if (pos < y_cap) {
             y_idx[pos] = i;
             if (SEM != kOrAnd && y_val) y_val[pos] = spa[r];
@@ -768,6 +771,32 @@ __global__ void k_bucket_sizes(const int32_t* __restrict__ rowidx, int64_t nnz, 
   for (int b = threadIdx.x; b < nb_fine; b += blockDim.x)
     if (h[b]) atomicAdd(&counts[b], h[b]);
   if (nbad) atomicAdd(bad, nbad);
+}
+
+__global__ void k_row_degrees(const int32_t* __restrict__ rowidx, int64_t nnz, int32_t m,
+                              int32_t* __restrict__ deg) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = rowidx[p];
+    if (r >= 0 && r < m) atomicAdd(&deg[r], 1);
+  }
+}
+
+__global__ void k_max_i32(const int32_t* __restrict__ v, int32_t n, int32_t* __restrict__ out) {
+  int32_t mx = 0;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    mx = max(mx, v[i]);
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
+}
+
+cudaError_t launch_row_degrees(const Matrix& A, int32_t* deg, int32_t* maxdeg, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (A.nnz > 0) k_row_degrees<<<sms * 4, 512, 0, s>>>(A.rowidx, A.nnz, A.m, deg);
+  k_max_i32<<<sms, 512, 0, s>>>(deg, A.m, maxdeg);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_bucket_sizes(const Matrix& A, int lwb_lo, int nb_fine, int32_t* counts,
@@ -834,7 +863,8 @@ namespace spmspv {
 cudaError_t launch_k1_bfs(const Matrix& A, const Workspace& ws, int nb_fine, const int32_t* x_idx,
                           const int32_t* f_dev, int grid, const Sched& sc, cudaStream_t s) {
   k1_work_scan<<<grid, K1_THREADS, 0, s>>>(x_idx, reinterpret_cast<const uint32_t*>(x_idx), 0,
-                                           f_dev, A.colptr, A.n, A.nnz, ws, nb_fine, 1, sc.dir, sc.q,
+                                           f_dev, A.colptr, A.n, A.nnz, ws, nb_fine, kMinSelect2nd,
+                                           1, sc.dir, sc.q,
                                            sc.lwb, 1);
   return cudaGetLastError();
 }

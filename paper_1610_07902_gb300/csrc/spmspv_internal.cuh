@@ -36,6 +36,13 @@ constexpr int LWB_MAX = 15;   // 32768 rows (local row fits in uint16)
 constexpr int NB_K2_MAX = 16384;  // buckets a K2 tile histograms in shared memory
 constexpr int BFILL_STRIDE = 32;  // bucket fill counters sit 128 bytes apart (own L2 line)
 
+// ---- hub ("hot") rows: the largest-degree rows, combined per K2 tile ----
+constexpr int HOT_MAX = 1024;          // at most this many hot rows
+constexpr int HOT_MIN_DEG = 512;       // a hot row has at least this many nonzeros
+constexpr int HOT_HT_LOG2 = 11;
+constexpr int HOT_HT = 1 << HOT_HT_LOG2;  // open-addressing table slots
+constexpr int HOT_BLOOM_WORDS = 2048;  // 64 Ki-bit Bloom filter
+
 // ---- device status bits ----
 constexpr uint32_t ST_CAPACITY = SPMSPV_DEV_CAPACITY;
 constexpr uint32_t ST_TIMEOUT = SPMSPV_DEV_TIMEOUT;
@@ -83,6 +90,15 @@ struct Workspace {
   int32_t* rbase;       // [nb_fine+1] first slot of each fine bucket's region
   uint16_t* brow;       // [nnz] bucket entries: row offset inside the bucket
   uint32_t* bval;       // [nnz] bucket entries: 32-bit value
+  // hub rows (nhot of them, 0 when no row has HOT_MIN_DEG nonzeros)
+  int nhot;
+  const int32_t* hot_rows;   // [HOT_MAX] row ids, ascending
+  const uint32_t* hot_bloom; // [HOT_BLOOM_WORDS]
+  const int32_t* hot_key;    // [HOT_HT] row id, or -1 for an empty slot
+  const uint16_t* hot_idx;   // [HOT_HT] index into hot_rows
+  const int32_t* hot_start;  // [nb_fine+1] first hot index of each fine bucket
+  uint32_t* hot_val;         // [HOT_MAX] per-call sums of the hot rows
+  uint32_t* hot_touch;       // [HOT_MAX] 1 when a hot row received a product this call
 };
 
 struct Matrix {
@@ -100,9 +116,10 @@ struct Sched {
 };
 
 // Launchers (kernels.cu).  All launches are asynchronous on `s`.
-cudaError_t launch_k1(const Matrix& A, const Workspace& ws, int nb_fine, const int32_t* x_idx,
-                      const uint32_t* x_val, int f, const int32_t* f_dev, int grid,
-                      const Sched* forced, cudaStream_t s);
+cudaError_t launch_k1(int sem, const Matrix& A, const Workspace& ws, int nb_fine,
+                      const int32_t* x_idx, const uint32_t* x_val, int f, const int32_t* f_dev,
+                      int grid, const Sched* forced, cudaStream_t s);
+cudaError_t launch_row_degrees(const Matrix& A, int32_t* deg, int32_t* maxdeg, cudaStream_t s);
 cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo, int nb_fine,
                       const uint32_t* mask, int mask_comp, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, int lwb_lo,
@@ -111,7 +128,7 @@ cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, i
                       size_t smem, cudaStream_t s);
 cudaError_t launch_bucket_sizes(const Matrix& A, int lwb_lo, int nb_fine, int32_t* counts,
                                 unsigned int* bad, cudaStream_t s);
-size_t k2_smem_bytes(int nb_fine);
+size_t k2_smem_bytes(int nb_fine, bool hot);
 size_t k3_smem_bytes(int lwb);
 cudaError_t set_kernel_attributes(size_t k2_smem, size_t k3_smem_max);
 int k3_blocks_per_sm(int sem, size_t smem);

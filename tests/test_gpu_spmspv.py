@@ -275,3 +275,32 @@ def test_rmat22_full_size(lib, rmat22, f):
     _check(lib, A, Ad, 1, x_idx, xf)
     print("rmat22 f=%d worst ratio %.3g" % (f, w))
     Ad.close()
+
+
+def test_hub_rows_combined_per_tile(lib):
+    """Rows with thousands of nonzeros take the hub path (combined per
+    expand/scatter tile); results must not change."""
+    rng = np.random.default_rng(12)
+    n, m = 30000, 5000
+    hubs = np.array([0, 17, 2500, 4999], np.int32)
+    cols = []
+    for j in range(n):
+        r = rng.choice(m, size=int(rng.integers(0, 6)), replace=False).astype(np.int32)
+        r = np.union1d(r, hubs[rng.random(hubs.shape[0]) < 0.8]).astype(np.int32)
+        cols.append(r)
+    colptr = np.zeros(n + 1, np.int32)
+    colptr[1:] = np.cumsum([c.shape[0] for c in cols])
+    rowidx = np.concatenate(cols).astype(np.int32)
+    val = rng.random(rowidx.shape[0]).astype(np.float32)
+    A = synth.CSC(m, n, colptr, rowidx, val)
+    Ad = _dev_matrix(lib, A)
+    for f in [1, 500, 8000, n]:
+        x_idx, xf = synth.frontier(n, f, seed=f)
+        mask = (rng.random(m) < 0.3).astype(np.uint8)
+        mask[hubs[:2]] = 1
+        for semiring in (0, 1, 2):
+            for sched in (0, 4, 8):
+                _check(lib, A, Ad, semiring, x_idx, xf, None, True, sched)
+            _check(lib, A, Ad, semiring, x_idx, xf, mask, True)
+            _check(lib, A, Ad, semiring, x_idx, xf, mask, False)
+    Ad.close()
