@@ -180,8 +180,6 @@ int select_hot_rows(spmspv_handle* h) {
     start[(r >> h->lwb_lo) + 1]++;
   }
   for (int i = 0; i < h->nb_fine; ++i) start[i + 1] += start[i];
-  char* b = (char*)h->ws_base;
-  (void)b;
   e = cudaMemcpy((void*)h->ws.hot_rows, rows.data(), sizeof(int32_t) * HOT_MAX, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy((void*)h->ws.hot_bloom, bloom.data(), sizeof(uint32_t) * HOT_BLOOM_WORDS,
