@@ -348,7 +348,10 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
     }
     h->k2_smem = k2_smem_bytes(h->nb_fine, h->ws.nhot > 0);
     h->k3_smem_max = k3_smem_bytes(lwb_hi);
-    if ((e = set_kernel_attributes(h->k2_smem, h->k3_smem_max)) != cudaSuccess) {
+    // the attribute is per kernel, not per handle: always allow the largest
+    // layout any handle can need, so that a later handle never lowers it
+    if ((e = set_kernel_attributes(k2_smem_bytes(NB_K2_MAX, true), k3_smem_bytes(LWB_MAX))) !=
+        cudaSuccess) {
       rc = cuda_fail(e, "kernel attributes");
       break;
     }
