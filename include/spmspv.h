@@ -156,6 +156,36 @@ int spmspv_device_status(spmspv_handle* h, uint32_t* flags);
  * selected column lengths, the df term of Sec. II-D, before masking. */
 int spmspv_last_work(spmspv_handle* h, int64_t* work);
 
+/*
+ * y <- A (+).(x) x without a handle and without allocating device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc, such as code that must not stall the device
+ * (cudaMalloc can synchronise it), code running inside a host process whose
+ * allocator owns all device memory, or code with a device-memory budget fixed
+ * at load time.  The caller passes the CSC matrix, x and y (device pointers,
+ * caller-owned, same meaning and layout as spmspv_create_csc + spmspv_run);
+ * the scratch the product needs (buckets, compacted x, scan state) lives in
+ * one file-scope device array of about 7 MB that the library holds on every
+ * GPU that loads it, until the process exits.
+ *   Limits (rejected with SPMSPV_ERR_UNSUPPORTED and a message naming the
+ *   limit): m <= 2^22 rows, nnz(A) <= 2^20, nnz_x <= 2^16.  Only the default
+ *   schedule: SPMSPV_SCHED_* options are rejected the same way.
+ *   val_type: SPMSPV_VAL_F32 or SPMSPV_VAL_NONE, as for spmspv_create_csc.
+ *   Output order, capacity rule and *d_nnz_y: as for spmspv_run (a y that does
+ *   not fit leaves the size it needs in *d_nnz_y).
+ * The first call on a device looks up the array's device address with that
+ * device current (a one-time set-up); make that first call before any stream
+ * capture.  Every call shares the one array and each call clears the part that
+ * must start at zero: calls whose kernels overlap on the GPU (other streams,
+ * or other host threads without ordering) race on it and give undefined
+ * results.  Asynchronous on `stream`; nothing is allocated or freed.
+ */
+int spmspv_run_noalloc(int32_t m, int32_t n, int64_t nnz, const int32_t* colptr,
+                       const int32_t* rowidx, const void* val, int val_type, int semiring,
+                       const int32_t* x_idx, const void* x_val, int32_t nnz_x,
+                       const uint32_t* mask, uint32_t opts, int32_t* y_idx, void* y_val,
+                       int32_t y_capacity, int32_t* d_nnz_y, spmspv_stream_t stream);
+
 /* ---- per-stage timing (CUDA events on the launch stream) ----
  * Stage ids of spmspv_profile_end's stage_ms array. */
 #define SPMSPV_STAGE_SCAN 0    /* K1 work scan (Algorithm 2's role) */

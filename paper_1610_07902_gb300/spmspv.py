@@ -91,6 +91,9 @@ def load(build_if_missing: bool = True):
                                    _P, _P, ctypes.c_int32, _P, _P]
         lib.spmspv_device_status.argtypes = [_P, ctypes.POINTER(ctypes.c_uint32)]
         lib.spmspv_last_work.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
+        lib.spmspv_run_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P,
+                                           _P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int32,
+                                           _P, ctypes.c_uint32, _P, _P, ctypes.c_int32, _P, _P]
         lib.spmspv_profile_begin.argtypes = [_P]
         lib.spmspv_profile_end.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_int32)]
@@ -140,6 +143,16 @@ def spmspv_run(h, semiring, x_idx, x_val, nnz_x, mask, opts, y_idx, y_val, y_cap
                            int(opts), _ptr(y_idx), _ptr(y_val), int(y_capacity), _ptr(d_nnz_y),
                            _stream(stream))
     _check(rc, "spmspv_run")
+
+
+def spmspv_run_noalloc(m, n, nnz, colptr, rowidx, val, val_type, semiring, x_idx, x_val, nnz_x,
+                       mask, opts, y_idx, y_val, y_capacity, d_nnz_y, stream=None):
+    """The handle-free entry point that allocates no device memory."""
+    rc = load().spmspv_run_noalloc(int(m), int(n), int(nnz), _ptr(colptr), _ptr(rowidx), _ptr(val),
+                                   int(val_type), int(semiring), _ptr(x_idx), _ptr(x_val),
+                                   int(nnz_x), _ptr(mask), int(opts), _ptr(y_idx), _ptr(y_val),
+                                   int(y_capacity), _ptr(d_nnz_y), _stream(stream))
+    _check(rc, "spmspv_run_noalloc")
 
 
 def spmspv_device_status(h) -> int:
