@@ -126,11 +126,6 @@ int run_push(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_
   return SPMSPV_OK;
 }
 
-static inline uint32_t hot_hash_bloom(int32_t row) { return ((uint32_t)row * 0x9E3779B1u) >> 16; }
-static inline uint32_t hot_hash_table(int32_t row) {
-  return ((uint32_t)row * 0x85EBCA77u) >> (32 - HOT_HT_LOG2);
-}
-
 int select_hot_rows(spmspv_handle* h) {
   const int32_t m = h->A.m;
   int32_t* d_deg = nullptr;
@@ -165,33 +160,35 @@ int select_hot_rows(spmspv_handle* h) {
   }
   std::sort(cand.begin(), cand.end());
   const int nh = (int)cand.size();
-  std::vector<int32_t> rows(HOT_MAX, -1), key(HOT_HT, -1), start((size_t)h->nb_fine + 1, 0);
-  std::vector<uint32_t> bloom(HOT_BLOOM_WORDS, 0u);
-  std::vector<uint16_t> idx(HOT_HT, 0);
+  std::vector<int32_t> rows(HOT_MAX, -1), start((size_t)h->nb_fine + 1, 0);
+  std::vector<int32_t> hub_of_row((size_t)m, -1);
   for (int i = 0; i < nh; ++i) {
-    const int32_t r = cand[i];
-    rows[i] = r;
-    const uint32_t hb = hot_hash_bloom(r);
-    bloom[hb >> 5] |= 1u << (hb & 31);
-    uint32_t t = hot_hash_table(r);
-    while (key[t] >= 0) t = (t + 1) & (HOT_HT - 1);
-    key[t] = r;
-    idx[t] = (uint16_t)i;
-    start[(r >> h->lwb_lo) + 1]++;
+    rows[i] = cand[i];
+    hub_of_row[cand[i]] = i;
+    start[(cand[i] >> h->lwb_lo) + 1]++;
   }
   for (int i = 0; i < h->nb_fine; ++i) start[i + 1] += start[i];
   e = cudaMemcpy((void*)h->ws.hot_rows, rows.data(), sizeof(int32_t) * HOT_MAX, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
-    e = cudaMemcpy((void*)h->ws.hot_bloom, bloom.data(), sizeof(uint32_t) * HOT_BLOOM_WORDS,
-                   cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy((void*)h->ws.hot_key, key.data(), sizeof(int32_t) * HOT_HT, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy((void*)h->ws.hot_idx, idx.data(), sizeof(uint16_t) * HOT_HT, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
     e = cudaMemcpy((void*)h->ws.hot_start, start.data(), sizeof(int32_t) * start.size(),
                    cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(e, "hot row tables");
+  if (e != cudaSuccess) return cuda_fail(e, "hub row tables");
+  // the row-id copy K2 reads: hub row r becomes m + its hub index
+  int32_t* d_map = nullptr;
+  e = cudaMalloc(&d_map, sizeof(int32_t) * (size_t)m);
+  if (e != cudaSuccess) return fail(SPMSPV_ERR_OOM, "hub map scratch: %s", cudaGetErrorString(e));
+  e = cudaMalloc(&h->rowidx_k2, sizeof(int32_t) * (size_t)(h->A.nnz > 0 ? h->A.nnz : 1));
+  if (e != cudaSuccess) {
+    cudaFree(d_map);
+    h->rowidx_k2 = nullptr;
+    return fail(SPMSPV_ERR_OOM, "hub row-id copy: %s", cudaGetErrorString(e));
+  }
+  e = cudaMemcpy(d_map, hub_of_row.data(), sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_relabel_hubs(h->A, d_map, h->rowidx_k2, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(d_map);
+  if (e != cudaSuccess) return cuda_fail(e, "hub relabel");
+  h->ws.rowidx_k2 = h->rowidx_k2;
   h->ws.nhot = nh;
   return SPMSPV_OK;
 }
@@ -262,9 +259,6 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
   size_t o_k3s = take(sizeof(unsigned long long) * (size_t)h->nb_fine);
   size_t o_rb = take(sizeof(int32_t) * ((size_t)h->nb_fine + 1));
   size_t o_hr = take(sizeof(int32_t) * HOT_MAX);
-  size_t o_hb = take(sizeof(uint32_t) * HOT_BLOOM_WORDS);
-  size_t o_hk = take(sizeof(int32_t) * HOT_HT);
-  size_t o_hi = take(sizeof(uint16_t) * HOT_HT);
   size_t o_hs = take(sizeof(int32_t) * ((size_t)h->nb_fine + 1));
   size_t o_hv = take(sizeof(uint32_t) * HOT_MAX);
   size_t o_ht = take(sizeof(uint32_t) * HOT_MAX);
@@ -291,9 +285,7 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
   h->ws.brow = (uint16_t*)(b + o_br);
   h->ws.bval = (uint32_t*)(b + o_bv);
   h->ws.hot_rows = (const int32_t*)(b + o_hr);
-  h->ws.hot_bloom = (const uint32_t*)(b + o_hb);
-  h->ws.hot_key = (const int32_t*)(b + o_hk);
-  h->ws.hot_idx = (const uint16_t*)(b + o_hi);
+  h->ws.rowidx_k2 = nullptr;
   h->ws.hot_start = (const int32_t*)(b + o_hs);
   h->ws.hot_val = (uint32_t*)(b + o_hv);
   h->ws.hot_touch = (uint32_t*)(b + o_ht);
@@ -363,6 +355,7 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) { rc = cuda_fail(e, "create"); break; }
   } while (0);
   if (rc != SPMSPV_OK) {
+    cudaFree(h->rowidx_k2);
     cudaFree(h->ws_base);
     h->magic = 0;
     delete h;
@@ -380,6 +373,7 @@ int spmspv_destroy(spmspv_handle* h) {
     spmspv_profile_end(h, tmp, SPMSPV_NUM_STAGES, nullptr);
   }
   release_extras(h);
+  cudaFree(h->rowidx_k2);
   cudaFree(h->ws_base);
   h->magic = 0;
   delete h;

@@ -29,6 +29,7 @@ struct spmspv_handle {
   cudaStream_t last_stream;
   int last_empty;
   void* prof;           // std::vector<ProfileCall>* while profiling, else NULL
+  int32_t* rowidx_k2;   // owned row-id copy with hub rows relabelled (NULL without hubs)
   // pull direction (dense frontier) buffers, allocated on first use
   uint32_t* xbits;      // [ceil(n/32)] frontier bitmap
   uint32_t* xdense;     // [n] frontier values

@@ -226,26 +226,43 @@ k1_work_scan(const int32_t* __restrict__ x_idx, const uint32_t* __restrict__ x_v
     if (tile >= nt1) break;
     const int64_t base = (int64_t)tile * K1_TILE;
 
-    // striped, coalesced loads of x and of the two column pointers
+    // striped, coalesced loads of x, then of the two column pointers of
+    // every entry, all issued before any is used
+    int32_t jj[K1_ITEMS];
+    uint32_t xvv[K1_ITEMS];
 #pragma unroll
     for (int i = 0; i < K1_ITEMS; ++i) {
-      const int e = i * K1_THREADS + tid;
-      const int64_t k = base + e;
-      int32_t d = 0, c0 = 0;
-      uint32_t xv = 0;
+      const int64_t k = base + i * K1_THREADS + tid;
+      jj[i] = -1;
+      xvv[i] = 0u;
       if (k < f) {
-        const int32_t j = x_idx[k];
+        jj[i] = x_idx[k];
+        xvv[i] = x_val ? x_val[k] : 0u;
+      }
+    }
+    int32_t c0v[K1_ITEMS], c1v[K1_ITEMS];
+#pragma unroll
+    for (int i = 0; i < K1_ITEMS; ++i) {
+      c0v[i] = 0;
+      c1v[i] = 0;
+      const int64_t k = base + i * K1_THREADS + tid;
+      if (k < f) {
+        const int32_t j = jj[i];
         if (j >= 0 && j < n) {
-          c0 = colptr[j];
-          d = colptr[j + 1] - c0;
+          c0v[i] = colptr[j];
+          c1v[i] = colptr[j + 1];
         } else {
           atomicOr(&st->status, ST_INDEX);
         }
-        xv = x_val ? x_val[k] : (uint32_t)j;
+        if (!x_val) xvv[i] = (uint32_t)j;
       }
-      s_deg[k1_pad(e)] = d;
-      s_c0[k1_pad(e)] = c0;
-      s_xv[k1_pad(e)] = xv;
+    }
+#pragma unroll
+    for (int i = 0; i < K1_ITEMS; ++i) {
+      const int e = i * K1_THREADS + tid;
+      s_deg[k1_pad(e)] = c1v[i] - c0v[i];
+      s_c0[k1_pad(e)] = c0v[i];
+      s_xv[k1_pad(e)] = xvv[i];
     }
     __syncthreads();
 
@@ -334,63 +351,49 @@ __device__ __forceinline__ void spa_apply(uint32_t* spa, uint32_t r, uint32_t v)
   else if (SEM == kMinSelect2nd) atomicMin(reinterpret_cast<int*>(spa + r), (int)v);
 }
 
-// Hot-row lookup: the rows of largest degree (fixed when the handle is
-// created) are listed in a 64 Ki-bit Bloom filter and an open-addressing
-// table in shared memory.  Returns the hot index of `row`, or -1.
-__device__ __forceinline__ int hot_lookup(int32_t row, const uint32_t* bloom, const int32_t* hkey,
-                                          const uint16_t* hidx) {
-  const uint32_t hb = ((uint32_t)row * 0x9E3779B1u) >> 16;
-  if (!((bloom[hb >> 5] >> (hb & 31)) & 1u)) return -1;
-  uint32_t t = ((uint32_t)row * 0x85EBCA77u) >> (32 - HOT_HT_LOG2);
-  for (int probe = 0; probe < HOT_HT; ++probe) {
-    const int32_t k = hkey[t];
-    if (k == row) return hidx[t];
-    if (k < 0) return -1;
-    t = (t + 1) & (HOT_HT - 1);
-  }
-  return -1;
-}
-
 // ------------------------------------------------------------------------
 // K2: expand + multiply + bucket scatter
 // ------------------------------------------------------------------------
 size_t k2_smem_bytes(int nb_fine, bool hot) {
-  size_t b = sizeof(uint32_t) * (QMAX / 32) * 2 + sizeof(uint32_t) * QMAX * 2 +
-             sizeof(int32_t) * (QMAX + 1) * 2 + sizeof(int32_t) * (size_t)nb_fine * 2 + 64;
-  if (hot)
-    b += sizeof(uint32_t) * HOT_BLOOM_WORDS + sizeof(int32_t) * HOT_HT + sizeof(uint16_t) * HOT_HT +
-         sizeof(uint32_t) * HOT_MAX + sizeof(uint32_t) * (HOT_MAX / 32) + 64;
+  size_t b = sizeof(uint2) * QMAX +              // staged (row, value) pairs, grouped by bucket
+             sizeof(int32_t) * (QMAX + 2) +      // local start of each x entry in the tile
+             sizeof(int32_t) * (QMAX + 1) +      // cb[k] - cw[k]
+             sizeof(uint32_t) * (QMAX + 1) +     // x value
+             sizeof(int32_t) * (size_t)nb_fine * 2 + 64;
+  if (hot) b += sizeof(uint32_t) * HOT_MAX * 2 + sizeof(uint32_t) * (HOT_MAX / 32) + 64;
   return b;
 }
 
+// One tile = q consecutive products (a merge-path slice of the selected
+// columns).  Each warp walks a contiguous chunk of 32*items products with
+// its lanes on consecutive products (coalesced row-id and value loads),
+// advancing the x entry it is in as the product index passes entry
+// boundaries.  Products are counted per bucket with shared-memory atomics,
+// one warp scans the counts, every non-empty bucket gets one run reserved
+// with a global atomic, the products are staged in shared memory grouped by
+// bucket and written out in runs.  Hub rows (row ids >= m in the relabelled
+// row-id array) are summed per tile in shared memory instead.
 template <int SEM>
 __global__ void __launch_bounds__(K2_THREADS, 2)
 k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ val, Workspace ws,
                   int lwb_lo, int nb_fine, int32_t m, int64_t nnz, const uint32_t* __restrict__ mask,
                   int mask_comp) {
   extern __shared__ __align__(16) unsigned char k2_smem_raw[];
-  __shared__ int32_t s_scan[K2_THREADS / 32 + 1];
   __shared__ int32_t s_kept;
 
-  // shared-memory carve (sizes as in k2_smem_bytes)
   unsigned char* p = k2_smem_raw;
-  uint32_t* bm = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX / 32);      // entry starts in the tile
-  uint32_t* bmpre = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX / 32);   // prefix popcounts of bm
-  uint32_t* srow = (uint32_t*)p; p += sizeof(uint32_t) * QMAX;           // staged rows by bucket
-  uint32_t* sval = (uint32_t*)p; p += sizeof(uint32_t) * QMAX;           // staged values
-  int32_t* kbase = (int32_t*)p; p += sizeof(int32_t) * (QMAX + 1);       // cb[k] - cw[k]
-  uint32_t* kx = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX + 1);       // x value per entry
-  int32_t* hist = (int32_t*)p; p += sizeof(int32_t) * nb_fine;           // counts, then stage offsets
-  int32_t* gd = (int32_t*)p; p += sizeof(int32_t) * nb_fine;             // bucket slot - stage offset
-  const int nhot = ws.nhot;
-  uint32_t* bloom = (uint32_t*)p;
-  int32_t* hkey = (int32_t*)(bloom + HOT_BLOOM_WORDS);
-  uint16_t* hidx = (uint16_t*)(hkey + HOT_HT);
-  uint32_t* hacc = (uint32_t*)(hidx + HOT_HT);
-  uint32_t* htb = hacc + HOT_MAX;
+  uint2* stage = (uint2*)p; p += sizeof(uint2) * QMAX;
+  int32_t* cws = (int32_t*)p; p += sizeof(int32_t) * (QMAX + 2);
+  int32_t* kbase = (int32_t*)p; p += sizeof(int32_t) * (QMAX + 1);
+  uint32_t* kx = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX + 1);
+  int32_t* hist = (int32_t*)p; p += sizeof(int32_t) * nb_fine;   // counts, then stage offsets
+  int32_t* gd = (int32_t*)p; p += sizeof(int32_t) * nb_fine;     // counts, then slot - stage offset
+  uint32_t* hacc = (uint32_t*)p;                                 // hub sums of this tile
+  int32_t* hrow = (int32_t*)(hacc + HOT_MAX);                    // hub row ids
+  uint32_t* htb = (uint32_t*)(hrow + HOT_MAX);                   // hub touched bits
 
   const DevState* st = ws.st;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int32_t W = st->W, fc = st->fc, q = st->q, lwb = st->lwb;
   const int sh = lwb - lwb_lo;
   const int nb = (int)(((int64_t)m + (1 << lwb) - 1) >> lwb);
@@ -398,14 +401,13 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
   const int items = q / K2_THREADS;
   const int ntiles = (int)(((int64_t)W + q - 1) / q);
   const uint32_t ident = sr_identity<SEM>();
+  const int nhot = ws.nhot;
 
   if (nhot > 0) {
-    for (int i = tid; i < HOT_BLOOM_WORDS; i += K2_THREADS) bloom[i] = ws.hot_bloom[i];
-    for (int i = tid; i < HOT_HT; i += K2_THREADS) {
-      hkey[i] = ws.hot_key[i];
-      hidx[i] = ws.hot_idx[i];
+    for (int i = tid; i < HOT_MAX; i += K2_THREADS) {
+      hacc[i] = ident;
+      hrow[i] = ws.hot_rows[i];
     }
-    for (int i = tid; i < HOT_MAX; i += K2_THREADS) hacc[i] = ident;
     for (int i = tid; i < HOT_MAX / 32; i += K2_THREADS) htb[i] = 0u;
   }
 
@@ -414,144 +416,161 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
     const int32_t np = min(q, W - p0);
     const int32_t k0 = ws.tile_k0[p0 / QF];
     const int32_t kend = (p0 + np == W) ? fc : ws.tile_k0[(p0 + np) / QF] + 1;
-    const int32_t nk = max(0, min(kend - k0, QMAX + 1));
+    const int32_t nk = max(1, min(kend - k0, QMAX + 1));
 
-    for (int i = tid; i < QMAX / 32; i += K2_THREADS) bm[i] = 0u;
-    for (int b = tid; b < nb; b += K2_THREADS) hist[b] = 0;
-    __syncthreads();
     for (int l = tid; l < nk; l += K2_THREADS) {
       const int32_t k = k0 + l;
       const int32_t w = ws.cw[k];
+      cws[l] = max(w - p0, 0);
       kbase[l] = ws.cb[k] - w;
       kx[l] = ws.cx[k];
-      const int32_t s0 = w - p0;
-      if (s0 > 0 && s0 < np) atomicOr(&bm[s0 >> 5], 1u << (s0 & 31));
     }
-    __syncthreads();
-    if (tid < 32) {
-      uint32_t c[QMAX / 32 / 32];
-      uint32_t tot = 0;
-#pragma unroll
-      for (int i = 0; i < QMAX / 32 / 32; ++i) {
-        c[i] = __popc(bm[tid * (QMAX / 32 / 32) + i]);
-        tot += c[i];
-      }
-      uint32_t x = tot;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (tid >= o) x += y;
-      }
-      uint32_t run = x - tot;
-#pragma unroll
-      for (int i = 0; i < QMAX / 32 / 32; ++i) {
-        bmpre[tid * (QMAX / 32 / 32) + i] = run;
-        run += c[i];
-      }
-    }
+    if (tid == 0) cws[nk] = np;
+    for (int b = tid; b < nb; b += K2_THREADS) hist[b] = 0;
     __syncthreads();
 
+    // ---- gather, multiply, filter, count per bucket ----
     uint32_t rrow[K2_IMAX], rval[K2_IMAX];
     int32_t rank[K2_IMAX];
+    {
+      const int32_t pw0 = warp * 32 * items + lane;
+      int l = 0;
+      if (pw0 < np) {  // last entry whose start is <= pw0
+        int lo = 0, hi = nk;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (cws[mid] <= pw0) lo = mid; else hi = mid;
+        }
+        l = lo;
+      }
+      int32_t nextb = cws[l + 1];
+      int32_t kb = kbase[l];
+      uint32_t xv = kx[l];
+      // phase 1: every item's address, then all loads in flight at once
+      uint32_t xi[K2_IMAX];
+      float av[K2_IMAX];
 #pragma unroll
-    for (int i = 0; i < K2_IMAX; ++i) {
-      const int32_t pl = tid + i * K2_THREADS;
-      rank[i] = -1;
-      rrow[i] = 0u;
-      rval[i] = 0u;
-      if (i < items && pl < np) {
-        const int wd = pl >> 5;
-        const uint32_t kl = bmpre[wd] + __popc(bm[wd] & (0xffffffffu >> (31 - (pl & 31))));
-        const int32_t pos = kbase[kl] + p0 + pl;
-        if ((uint32_t)pos >= (uint32_t)nnz) continue;  // unreachable with valid inputs
-        const int32_t row = ld_stream(rowidx + pos);
+      for (int i = 0; i < K2_IMAX; ++i) {
+        const int32_t pl = pw0 + 32 * i;
+        rrow[i] = 0xffffffffu;
+        xi[i] = 0u;
+        av[i] = 1.0f;
+        if (i < items && pl < np) {
+          if (pl >= nextb) {
+            do {
+              ++l;
+              nextb = cws[l + 1];
+            } while (pl >= nextb);
+            kb = kbase[l];
+            xv = kx[l];
+          }
+          const int32_t pos = kb + p0 + pl;
+          xi[i] = xv;
+          if ((uint32_t)pos < (uint32_t)nnz) {  // always true with valid inputs
+            rrow[i] = (uint32_t)ld_stream(rowidx + pos);
+            if (SEM == kPlusTimes && val) av[i] = ld_stream(val + pos);
+          }
+        }
+      }
+      // phase 2: multiply, filter, count per bucket
+#pragma unroll
+      for (int i = 0; i < K2_IMAX; ++i) {
+        rank[i] = -1;
+        const uint32_t row = rrow[i];
         uint32_t v = 0u;
-        if (SEM == kPlusTimes) {
-          const float xv = __uint_as_float(kx[kl]);
-          v = __float_as_uint(val ? __fmul_rn(ld_stream(val + pos), xv) : xv);
-        } else if (SEM == kMinSelect2nd) {
-          v = kx[kl];
-        }
-        bool keep = true;
-        if (mask) {
-          const uint32_t bit = (__ldg(mask + (row >> 5)) >> (row & 31)) & 1u;
-          keep = mask_comp ? (bit == 0u) : (bit != 0u);
-        }
-        if (keep) {
-          const int hs = nhot > 0 ? hot_lookup(row, bloom, hkey, hidx) : -1;
-          if (hs >= 0) {
-            // a hub row: combine its products of this tile in shared memory
+        if (SEM == kPlusTimes) v = __float_as_uint(__fmul_rn(av[i], __uint_as_float(xi[i])));
+        else if (SEM == kMinSelect2nd) v = xi[i];
+        rval[i] = v;
+        if (row == 0xffffffffu) continue;
+        if ((int32_t)row < m) {
+          bool keep = true;
+          if (mask) {
+            const uint32_t bit = (__ldg(mask + (row >> 5)) >> (row & 31)) & 1u;
+            keep = mask_comp ? (bit == 0u) : (bit != 0u);
+          }
+          if (keep) rank[i] = atomicAdd(&hist[row >> lwb], 1);
+        } else {
+          // a hub row: combine its products of this tile in shared memory
+          const int hs = (int)row - m;
+          const int32_t orow = hrow[hs];
+          bool keep = true;
+          if (mask) {
+            const uint32_t bit = (__ldg(mask + (orow >> 5)) >> (orow & 31)) & 1u;
+            keep = mask_comp ? (bit == 0u) : (bit != 0u);
+          }
+          if (keep) {
             spa_apply<SEM>(hacc, (uint32_t)hs, v);
             const uint32_t bit = 1u << (hs & 31);
             if (!(htb[hs >> 5] & bit)) atomicOr(&htb[hs >> 5], bit);
-          } else {
-            rank[i] = atomicAdd(&hist[row >> lwb], 1);
           }
         }
-        rrow[i] = (uint32_t)row;
-        rval[i] = v;
       }
     }
     __syncthreads();
 
-    // flush this tile's hub sums with one global atomic per touched hub row
-    for (int hs = tid; hs < nhot; hs += K2_THREADS) {
-      if ((htb[hs >> 5] >> (hs & 31)) & 1u) {
-        if (SEM == kPlusTimes)
-          atomicAdd(reinterpret_cast<float*>(ws.hot_val + hs), __uint_as_float(hacc[hs]));
-        else if (SEM == kMinSelect2nd)
-          atomicMin(reinterpret_cast<int*>(ws.hot_val + hs), (int)hacc[hs]);
-        ws.hot_touch[hs] = 1u;
-        hacc[hs] = ident;
-      }
-    }
-    // exclusive scan of the bucket histogram; reserve one run per non-empty bucket
-    {
-      const int per = (nb + K2_THREADS - 1) / K2_THREADS;
-      const int b0 = tid * per;
+    // ---- one warp scans the bucket counts; the other warps flush hub sums ----
+    if (warp == 0) {
+      const int per = (nb + 31) >> 5;
+      const int b0 = lane * per, b1 = min(b0 + per, nb);
       int32_t sum = 0;
-      for (int b = b0; b < min(b0 + per, nb); ++b) sum += hist[b];
-      int32_t tot;
-      int32_t run = block_exclusive_sum<K2_THREADS>(sum, s_scan, &tot);
-      if (tid == 0) s_kept = tot;
-      for (int b = b0; b < min(b0 + per, nb); ++b) {
+      for (int b = b0; b < b1; ++b) sum += hist[b];
+      int32_t x = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      int32_t run = x - sum;
+      if (lane == 31) s_kept = x;
+      for (int b = b0; b < b1; ++b) {
         const int32_t c = hist[b];
+        gd[b] = c;
         hist[b] = run;
-        if (c > 0) {
-          const int fb0 = b << sh;
-          const int fb1 = min((b + 1) << sh, nb_fine);
-          const int32_t base = ws.rbase[fb0];
-          const int32_t cap = ws.rbase[fb1] - base;
-          const int32_t g = atomicAdd(&ws.bfill[(size_t)b * BFILL_STRIDE], c);
-          if (g + c <= cap) {
-            gd[b] = base + g - run;
-          } else {
-            gd[b] = INT32_MIN;  // only reachable with duplicate x indices
-            atomicOr(&ws.st->status, ST_INDEX);
-          }
-        }
         run += c;
       }
-    }
-    __syncthreads();
-    if (nhot > 0 && tid < HOT_MAX / 32) htb[tid] = 0u;
-#pragma unroll
-    for (int i = 0; i < K2_IMAX; ++i) {
-      if (rank[i] >= 0) {
-        const int32_t s = hist[rrow[i] >> lwb] + rank[i];
-        srow[s] = rrow[i];
-        if (SEM != kOrAnd) sval[s] = rval[i];
+    } else if (nhot > 0) {
+      for (int hs = tid - 32; hs < nhot; hs += K2_THREADS - 32) {
+        if ((htb[hs >> 5] >> (hs & 31)) & 1u) {
+          if (SEM == kPlusTimes)
+            atomicAdd(reinterpret_cast<float*>(ws.hot_val + hs), __uint_as_float(hacc[hs]));
+          else if (SEM == kMinSelect2nd)
+            atomicMin(reinterpret_cast<int*>(ws.hot_val + hs), (int)hacc[hs]);
+          ws.hot_touch[hs] = 1u;
+          hacc[hs] = ident;
+        }
       }
     }
     __syncthreads();
+    // ---- reserve one run per non-empty bucket (all threads) ----
+    for (int b = tid; b < nb; b += K2_THREADS) {
+      const int32_t c = gd[b];
+      if (c > 0) {
+        const int32_t base = ws.rbase[b << sh];
+        const int32_t cap = ws.rbase[min((b + 1) << sh, nb_fine)] - base;
+        const int32_t g = atomicAdd(&ws.bfill[(size_t)b * BFILL_STRIDE], c);
+        if (g + c <= cap) {
+          gd[b] = base + g - hist[b];
+        } else {
+          gd[b] = INT32_MIN;  // only reachable with duplicate x indices
+          atomicOr(&ws.st->status, ST_INDEX);
+        }
+      }
+    }
+    // ---- stage the products grouped by bucket ----
+#pragma unroll
+    for (int i = 0; i < K2_IMAX; ++i)
+      if (rank[i] >= 0) stage[hist[rrow[i] >> lwb] + rank[i]] = make_uint2(rrow[i], rval[i]);
+    if (nhot > 0 && warp == 1) htb[lane] = 0u;
+    __syncthreads();
+    // ---- write the runs to the buckets ----
     const int32_t kept = s_kept;
     for (int32_t s = tid; s < kept; s += K2_THREADS) {
-      const uint32_t row = srow[s];
-      const int32_t g = gd[row >> lwb];
+      const uint2 e = stage[s];
+      const int32_t g = gd[e.x >> lwb];
       if (g == INT32_MIN) continue;
       const int32_t dst = g + s;
-      ws.brow[dst] = (uint16_t)(row & wmask);
-      if (SEM != kOrAnd) ws.bval[dst] = sval[s];
+      ws.brow[dst] = (uint16_t)(e.x & wmask);
+      if (SEM != kOrAnd) ws.bval[dst] = e.y;
     }
     __syncthreads();
   }
@@ -559,18 +578,19 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
 
 cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo, int nb_fine,
                       const uint32_t* mask, int mask_comp, int grid, size_t smem, cudaStream_t s) {
+  const int32_t* rows = ws.nhot > 0 ? ws.rowidx_k2 : A.rowidx;
   switch (sem) {
     case kPlusTimes:
       k2_expand_scatter<kPlusTimes><<<grid, K2_THREADS, smem, s>>>(
-          A.rowidx, A.val, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp);
+          rows, A.val, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp);
       break;
     case kMinSelect2nd:
       k2_expand_scatter<kMinSelect2nd><<<grid, K2_THREADS, smem, s>>>(
-          A.rowidx, nullptr, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp);
+          rows, nullptr, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp);
       break;
     default:
       k2_expand_scatter<kOrAnd><<<grid, K2_THREADS, smem, s>>>(
-          A.rowidx, nullptr, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp);
+          rows, nullptr, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp);
   }
   return cudaGetLastError();
 }
@@ -650,7 +670,7 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __res
       }
       __syncthreads();
       // Step 2 of Algorithm 1: merge the bucket into the SPA
-      constexpr int U = 4;
+      constexpr int U = 8;
       const uint16_t* brow = ws.brow + base;
       const uint32_t* bval = ws.bval + base;
       for (int32_t e0 = tid; e0 < cnt; e0 += K3_THREADS * U) {
@@ -780,6 +800,27 @@ __global__ void k_row_degrees(const int32_t* __restrict__ rowidx, int64_t nnz, i
     const int32_t r = rowidx[p];
     if (r >= 0 && r < m) atomicAdd(&deg[r], 1);
   }
+}
+
+// Hub rows get the ids m + hub index in the row-id copy K2 reads.
+__global__ void k_relabel_hubs(const int32_t* __restrict__ rowidx, int64_t nnz,
+                               const int32_t* __restrict__ hub_of_row, int32_t m,
+                               int32_t* __restrict__ out) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = rowidx[p];
+    const int32_t h = (r >= 0 && r < m) ? hub_of_row[r] : -1;
+    out[p] = h >= 0 ? m + h : r;
+  }
+}
+
+cudaError_t launch_relabel_hubs(const Matrix& A, const int32_t* hub_of_row, int32_t* out,
+                                cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (A.nnz > 0) k_relabel_hubs<<<sms * 4, 512, 0, s>>>(A.rowidx, A.nnz, hub_of_row, A.m, out);
+  return cudaGetLastError();
 }
 
 __global__ void k_max_i32(const int32_t* __restrict__ v, int32_t n, int32_t* __restrict__ out) {

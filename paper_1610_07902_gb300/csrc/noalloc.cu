@@ -183,9 +183,7 @@ extern "C" int spmspv_run_noalloc(int32_t m, int32_t n, int64_t nnz, const int32
   ws.bval = (uint32_t*)(base + NA_OFF_BV);
   ws.nhot = 0;
   ws.hot_rows = nullptr;
-  ws.hot_bloom = nullptr;
-  ws.hot_key = nullptr;
-  ws.hot_idx = nullptr;
+  ws.rowidx_k2 = nullptr;
   ws.hot_start = nullptr;
   ws.hot_val = nullptr;
   ws.hot_touch = nullptr;

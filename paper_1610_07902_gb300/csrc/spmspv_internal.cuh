@@ -39,9 +39,7 @@ constexpr int BFILL_STRIDE = 32;  // bucket fill counters sit 128 bytes apart (o
 // ---- hub ("hot") rows: the largest-degree rows, combined per K2 tile ----
 constexpr int HOT_MAX = 1024;          // at most this many hot rows
 constexpr int HOT_MIN_DEG = 512;       // a hot row has at least this many nonzeros
-constexpr int HOT_HT_LOG2 = 11;
-constexpr int HOT_HT = 1 << HOT_HT_LOG2;  // open-addressing table slots
-constexpr int HOT_BLOOM_WORDS = 2048;  // 64 Ki-bit Bloom filter
+
 
 // ---- device status bits ----
 constexpr uint32_t ST_CAPACITY = SPMSPV_DEV_CAPACITY;
@@ -93,10 +91,8 @@ struct Workspace {
   // hub rows (nhot of them, 0 when no row has HOT_MIN_DEG nonzeros)
   int nhot;
   const int32_t* hot_rows;   // [HOT_MAX] row ids, ascending
-  const uint32_t* hot_bloom; // [HOT_BLOOM_WORDS]
-  const int32_t* hot_key;    // [HOT_HT] row id, or -1 for an empty slot
-  const uint16_t* hot_idx;   // [HOT_HT] index into hot_rows
   const int32_t* hot_start;  // [nb_fine+1] first hot index of each fine bucket
+  const int32_t* rowidx_k2;  // [nnz] row ids with hub row r replaced by m + its hub index
   uint32_t* hot_val;         // [HOT_MAX] per-call sums of the hot rows
   uint32_t* hot_touch;       // [HOT_MAX] 1 when a hot row received a product this call
 };
@@ -120,6 +116,8 @@ cudaError_t launch_k1(int sem, const Matrix& A, const Workspace& ws, int nb_fine
                       const int32_t* x_idx, const uint32_t* x_val, int f, const int32_t* f_dev,
                       int grid, const Sched* forced, cudaStream_t s);
 cudaError_t launch_row_degrees(const Matrix& A, int32_t* deg, int32_t* maxdeg, cudaStream_t s);
+cudaError_t launch_relabel_hubs(const Matrix& A, const int32_t* hub_of_row, int32_t* out,
+                                cudaStream_t s);
 cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo, int nb_fine,
                       const uint32_t* mask, int mask_comp, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, int lwb_lo,
