@@ -100,7 +100,7 @@ const char* spmspv_last_error(void);
  * Create a handle over an m-by-n CSC matrix (Sec. II-C: colptrs n+1,
  * rowids nnz, values nnz; row ids inside a column need not be sorted).
  *   h        host out: the new handle.
- *   m, n     rows, columns; 1 <= m <= 2^27, 1 <= n < 2^31.
+ *   m, n     rows, columns; 1 <= m <= 2^26, 1 <= n < 2^31.
  *   nnz      colptr[n]; 0 <= nnz < 2^31.
  *   colptr   device int32[n+1], non-decreasing, colptr[0] = 0.
  *   rowidx   device int32[nnz], each in [0, m).

@@ -205,8 +205,8 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
   if (!out) return fail(SPMSPV_ERR_ARG, "h is NULL");
   *out = nullptr;
   if (m < 1 || n < 1) return fail(SPMSPV_ERR_ARG, "m and n must be >= 1 (got %d, %d)", m, n);
-  if (m > (1 << 27))
-    return fail(SPMSPV_ERR_UNSUPPORTED, "m = %d exceeds 2^27 rows (bucket row width limit)", m);
+  if (m > (1 << 26))
+    return fail(SPMSPV_ERR_UNSUPPORTED, "m = %d exceeds 2^26 rows (bucket row width limit)", m);
   if (nnz < 0 || nnz >= ((int64_t)1 << 31)) return fail(SPMSPV_ERR_ARG, "nnz must be in [0, 2^31)");
   if (!colptr) return fail(SPMSPV_ERR_ARG, "colptr is NULL");
   if (nnz > 0 && !rowidx) return fail(SPMSPV_ERR_ARG, "rowidx is NULL");
@@ -237,7 +237,7 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
   h->nb_fine = (int)(((int64_t)m + (1 << h->lwb_lo) - 1) >> h->lwb_lo);
   if (h->nb_fine > NB_K2_MAX) {
     delete h;
-    return fail(SPMSPV_ERR_UNSUPPORTED, "too many row-range buckets (%d)", (int)0);
+    return fail(SPMSPV_ERR_UNSUPPORTED, "too many row-range buckets (%d)", h->nb_fine);
   }
 
   // workspace: one allocation, carved in 256-byte aligned pieces

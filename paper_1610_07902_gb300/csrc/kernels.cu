@@ -354,15 +354,6 @@ __device__ __forceinline__ void spa_apply(uint32_t* spa, uint32_t r, uint32_t v)
 // ------------------------------------------------------------------------
 // K2: expand + multiply + bucket scatter
 // ------------------------------------------------------------------------
-size_t k2_smem_bytes(int nb_fine, bool hot) {
-  size_t b = sizeof(uint2) * QMAX +              // staged (row, value) pairs, grouped by bucket
-             sizeof(int32_t) * (QMAX + 2) +      // local start of each x entry in the tile
-             sizeof(int32_t) * (QMAX + 1) +      // cb[k] - cw[k]
-             sizeof(uint32_t) * (QMAX + 1) +     // x value
-             sizeof(int32_t) * (size_t)nb_fine * 2 + 64;
-  if (hot) b += sizeof(uint32_t) * HOT_MAX * 2 + sizeof(uint32_t) * (HOT_MAX / 32) + 64;
-  return b;
-}
 
 // One tile = q consecutive products (a merge-path slice of the selected
 // columns).  Each warp walks a contiguous chunk of 32*items products with
@@ -598,11 +589,6 @@ cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo,
 // ------------------------------------------------------------------------
 // K3: per-bucket SPA merge + ordered compaction (+ BFS update)
 // ------------------------------------------------------------------------
-size_t k3_smem_bytes(int lwb) {
-  const size_t wb = (size_t)1 << lwb;
-  return wb * sizeof(uint32_t) + (wb / 32) * sizeof(uint32_t);
-}
-
 template <int SEM, bool BFS>
 __global__ void __launch_bounds__(K3_THREADS)
 k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __restrict__ y_idx,

@@ -33,7 +33,7 @@ constexpr int K3_THREADS = 512;
 // ---- bucket row widths ----
 constexpr int LWB_MIN = 7;    // 128 rows
 constexpr int LWB_MAX = 15;   // 32768 rows (local row fits in uint16)
-constexpr int NB_K2_MAX = 16384;  // buckets a K2 tile histograms in shared memory
+constexpr int NB_K2_MAX = 8192;   // buckets a K2 tile histograms in shared memory
 constexpr int BFILL_STRIDE = 32;  // bucket fill counters sit 128 bytes apart (own L2 line)
 
 // ---- hub ("hot") rows: the largest-degree rows, combined per K2 tile ----
@@ -126,8 +126,21 @@ cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, i
                       size_t smem, cudaStream_t s);
 cudaError_t launch_bucket_sizes(const Matrix& A, int lwb_lo, int nb_fine, int32_t* counts,
                                 unsigned int* bad, cudaStream_t s);
-size_t k2_smem_bytes(int nb_fine, bool hot);
-size_t k3_smem_bytes(int lwb);
+// K2 shared memory: staged (row, value) pairs of one tile, the start,
+// cb - cw and x value of the tile's x entries, the bucket histogram and
+// slots, and the hub-row tables.
+__host__ __device__ constexpr size_t k2_smem_bytes(int nb_fine, bool hot) {
+  return sizeof(uint32_t) * 2 * QMAX + sizeof(int32_t) * (QMAX + 2) + sizeof(int32_t) * (QMAX + 1) +
+         sizeof(uint32_t) * (QMAX + 1) + sizeof(int32_t) * (size_t)nb_fine * 2 + 64 +
+         (hot ? sizeof(uint32_t) * HOT_MAX * 2 + sizeof(uint32_t) * (HOT_MAX / 32) + 64 : 0);
+}
+// K3 shared memory: the SPA values and the occupancy bitmap of one bucket
+__host__ __device__ constexpr size_t k3_smem_bytes(int lwb) {
+  return ((size_t)1 << lwb) * sizeof(uint32_t) + (((size_t)1 << lwb) / 32) * sizeof(uint32_t);
+}
+constexpr size_t SMEM_PER_BLOCK_MAX = 227 * 1024;
+static_assert(k2_smem_bytes(NB_K2_MAX, true) + 128 <= SMEM_PER_BLOCK_MAX, "K2 layout too large");
+static_assert(k3_smem_bytes(LWB_MAX) + 4096 <= SMEM_PER_BLOCK_MAX, "K3 layout too large");
 cudaError_t set_kernel_attributes(size_t k2_smem, size_t k3_smem_max);
 int k3_blocks_per_sm(int sem, size_t smem);
 int k2_blocks_per_sm(int sem, size_t smem);
