@@ -148,6 +148,25 @@ int spmspv_run(spmspv_handle* h, int semiring, const int32_t* x_idx, const void*
                int32_t nnz_x, const uint32_t* mask, uint32_t opts, int32_t* y_idx,
                void* y_val, int32_t y_capacity, int32_t* d_nnz_y, spmspv_stream_t stream);
 
+/*
+ * Breadth-first search from `src` by repeated masked (min, select2nd) SpMSpV
+ * (Sec. IV-D; level rule: level[src] = 0, parent[src] = src; every vertex
+ * reached at level L has parent = its smallest-id neighbour at level L-1;
+ * unreached vertices get -1).  A must be square; for an undirected graph it is
+ * symmetric (create with SPMSPV_CSC_PATTERN_SYMMETRIC to allow the pull
+ * direction).  Column j's entries are the vertices reached from j.
+ *   level, parent  device int32[n] out.
+ *   d_nlevels      device int32 out (may be NULL): number of levels (max level + 1).
+ *   opts           schedule: SPMSPV_SCHED_OPT(s) for a fixed schedule, SPMSPV_SCHED_AUTO
+ *                  for the learned selector (weights must be loaded or trained),
+ *                  0 for the default fixed push schedule.
+ * The level loop runs on the device (a CUDA graph with a conditional WHILE node,
+ * built on first use for each schedule mode): no host synchronisation per level.
+ * Allocates the BFS buffers (4 bytes per vertex + a visited bitmap) on first use.
+ */
+int spmspv_bfs(spmspv_handle* h, int32_t src, int32_t* level, int32_t* parent,
+               int32_t* d_nlevels, uint32_t opts, spmspv_stream_t stream);
+
 /* Device status word of the handle: synchronises the handle's last stream,
  * returns the SPMSPV_DEV_* bits in *flags (host out) and clears them. */
 int spmspv_device_status(spmspv_handle* h, uint32_t* flags);

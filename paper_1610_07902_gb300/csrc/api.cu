@@ -97,17 +97,14 @@ int check_handle(const spmspv_handle* h) {
 int run_push(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_val, int f,
              const int32_t* f_dev, const uint32_t* mask, int mask_comp, const Sched& sc,
              int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y, bool bfs,
-             uint32_t* mask_update, int32_t* level, int32_t* parent, cudaStream_t s) {
+             uint32_t* mask_update, cudaStream_t s) {
   int k1_grid = f_dev ? h->k1_grid_max
                       : (int)std::min<int64_t>(h->k1_grid_max, ((int64_t)f + K1_TILE - 1) / K1_TILE);
   if (k1_grid < 1) k1_grid = 1;
   cudaError_t e;
   prof_call_begin(h, s);
   if (bfs) {
-    extern cudaError_t launch_k1_bfs(const Matrix& A, const Workspace& ws, int nb_fine,
-                                     const int32_t* x_idx, const int32_t* f_dev, int grid,
-                                     const Sched& sc, cudaStream_t s);
-    e = launch_k1_bfs(h->A, h->ws, h->nb_fine, x_idx, f_dev, k1_grid, sc, s);
+    e = launch_k1_bfs(h->A, h->ws, h->nb_fine, x_idx, f_dev, k1_grid, &sc, s);
   } else {
     e = launch_k1(sem, h->A, h->ws, h->nb_fine, x_idx, x_val, f, f_dev, k1_grid, &sc, s);
   }
@@ -120,7 +117,7 @@ int run_push(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_
   const int nb = (int)(((int64_t)h->A.m + (1 << sc.lwb) - 1) >> sc.lwb);
   const int k3_grid = std::max(1, std::min(nb, h->sm_count * h->k3_bps[sc.lwb - h->lwb_lo]));
   e = launch_k3(sem, bfs, h->A, h->ws, h->lwb_lo, h->nb_fine, y_idx, y_val, y_cap, d_nnz_y,
-                mask_update, level, parent, k3_grid, k3_smem, s);
+                mask_update, k3_grid, k3_smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "bucket merge launch");
   prof_mark(h, SPMSPV_STAGE_MERGE, s);
   return SPMSPV_OK;
@@ -329,6 +326,28 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
     // hub rows: the (at most HOT_MAX) rows of largest degree with at least
     // HOT_MIN_DEG nonzeros; their products are combined per K2 tile
     if ((rc = select_hot_rows(h)) != SPMSPV_OK) break;
+    // row ids ascending in every column? (lets the pull BFS stop at the first hit)
+    {
+      int32_t* d_u = nullptr;
+      if ((e = cudaMalloc(&d_u, sizeof(int32_t))) != cudaSuccess) {
+        rc = fail(SPMSPV_ERR_OOM, "scratch: %s", cudaGetErrorString(e));
+        break;
+      }
+      cudaMemset(d_u, 0, sizeof(int32_t));
+      int32_t u = 1;
+      e = launch_rows_unsorted(h->A, d_u, 0);
+      if (e == cudaSuccess) e = cudaMemcpy(&u, d_u, sizeof(int32_t), cudaMemcpyDeviceToHost);
+      cudaFree(d_u);
+      if (e != cudaSuccess) { rc = cuda_fail(e, "row order check"); break; }
+      h->rows_sorted = u == 0;
+    }
+    // pull direction buffers (the CSC doubles as CSR only for a symmetric pattern)
+    if ((flags & SPMSPV_CSC_PATTERN_SYMMETRIC) && m == n) {
+      if ((e = alloc_pull_buffers(h)) != cudaSuccess) {
+        rc = fail(SPMSPV_ERR_OOM, "pull buffers: %s", cudaGetErrorString(e));
+        break;
+      }
+    }
     // default schedule state
     DevState st0;
     memset(&st0, 0, sizeof(st0));
@@ -355,6 +374,7 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) { rc = cuda_fail(e, "create"); break; }
   } while (0);
   if (rc != SPMSPV_OK) {
+    release_extras(h);
     cudaFree(h->rowidx_k2);
     cudaFree(h->ws_base);
     h->magic = 0;
@@ -372,8 +392,10 @@ int spmspv_destroy(spmspv_handle* h) {
     double tmp[SPMSPV_NUM_STAGES];
     spmspv_profile_end(h, tmp, SPMSPV_NUM_STAGES, nullptr);
   }
+  release_bfs_graphs(h);
   release_extras(h);
   cudaFree(h->rowidx_k2);
+  cudaFree(h->sel_w);
   cudaFree(h->ws_base);
   h->magic = 0;
   delete h;
@@ -417,7 +439,7 @@ int spmspv_run(spmspv_handle* h, int semiring, const int32_t* x_idx, const void*
   }
   return run_push(h, semiring, x_idx, (const uint32_t*)x_val, nnz_x, nullptr, mask,
                   (opts & SPMSPV_MASK_COMPLEMENT) ? 1 : 0, sc, y_idx, (uint32_t*)y_val, y_capacity,
-                  d_nnz_y, false, nullptr, nullptr, nullptr, s);
+                  d_nnz_y, false, nullptr, s);
 }
 
 int spmspv_device_status(spmspv_handle* h, uint32_t* flags) {

@@ -1,0 +1,220 @@
+// Breadth-first search as repeated masked (min, select2nd) SpMSpV (Sec. IV-D):
+// frontier x = {(j, j)}, y = A (min.select2nd) x on the unvisited rows, every
+// (i, p) in y gets level L and parent p, joins the visited mask and forms the
+// next frontier; stop at an empty y.
+//
+// The whole level loop runs on the device: a CUDA graph with a conditional
+// WHILE node whose body is one level (work scan -> [selector] -> push kernels
+// | pull kernels -> condition kernel).  The condition kernel keeps the loop
+// going while the last y was non-empty, so a search of thousands of levels
+// never returns to the host.  One graph is built per handle and schedule mode
+// on first use and reused; the per-search arguments (source, output arrays)
+// reach the kernels through the device state.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "handle.cuh"
+#include "spmspv_internal.cuh"
+
+namespace spmspv {
+
+cudaError_t launch_pull(const spmspv_handle* h, int sem, bool bfs, const int32_t* x_idx,
+                        const uint32_t* x_val, int f, const int32_t* f_dev, const uint32_t* mask,
+                        int mask_comp, int early_exit, int32_t* y_idx, uint32_t* y_val,
+                        int32_t y_cap, int32_t* d_nnz_y, uint32_t* visited, int only_pull,
+                        cudaStream_t s);
+int pull_available(const spmspv_handle* h, int sem);
+cudaError_t launch_selector(spmspv_handle* h, int allow_pull, cudaStream_t s);
+
+namespace {
+
+// Start of a search: every vertex unreached, the source at level 0.
+__global__ void k_bfs_init(int32_t n, int32_t src, int32_t* __restrict__ level,
+                           int32_t* __restrict__ parent, uint32_t* __restrict__ visited,
+                           int32_t* __restrict__ front, DevState* st) {
+  const int32_t words = (n + 31) / 32;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    level[i] = i == src ? 0 : -1;
+    parent[i] = i == src ? src : -1;
+    if (i < words) visited[i] = (i == (src >> 5)) ? (1u << (src & 31)) : 0u;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    front[0] = src;
+    st->nnz_y = 1;
+    st->level = 0;
+    st->nvisited = 1;
+    st->bfs_level = level;
+    st->bfs_parent = parent;
+  }
+}
+
+// Loop condition: another level while the last one found vertices.
+__global__ void k_bfs_continue(cudaGraphConditionalHandle cond, const DevState* st, int32_t n) {
+  if (threadIdx.x == 0) cudaGraphSetConditional(cond, (st->nnz_y > 0 && st->level <= n) ? 1u : 0u);
+}
+
+}  // namespace
+
+// One BFS level on `s` (captured into the loop body).
+static int bfs_level_launches(spmspv_handle* h, int sched, cudaGraphConditionalHandle cond,
+                              cudaStream_t s) {
+  const bool autos = sched < 0;
+  const bool can_pull = pull_available(h, kMinSelect2nd) != 0;
+  Sched sc = decode_schedule(h, autos ? h->default_sched : sched);
+  if (!can_pull) sc.dir = 0;
+  cudaError_t e = launch_k1_bfs(h->A, h->ws, h->nb_fine, h->bfs_front, &h->ws.st->nnz_y,
+                                h->k1_grid_max, autos ? nullptr : &sc, s);
+  if (e != cudaSuccess) return cuda_fail(e, "bfs work scan");
+  if (autos) {
+    if ((e = launch_selector(h, can_pull ? 1 : 0, s)) != cudaSuccess) return cuda_fail(e, "bfs selector");
+  }
+  const bool push = autos || sc.dir == 0;
+  const bool pull = can_pull && (autos || sc.dir == 1);
+  if (push) {
+    const int lwb = autos ? h->lwb_lo + 2 : sc.lwb;
+    const size_t k3_smem = k3_smem_bytes(lwb);
+    const int nb_max = (int)(((int64_t)h->A.m + (1 << h->lwb_lo) - 1) >> h->lwb_lo);
+    const int k3_grid = std::max(1, std::min(nb_max, h->sm_count * h->k3_bps[lwb - h->lwb_lo]));
+    e = launch_k2(kMinSelect2nd, h->A, h->ws, h->lwb_lo, h->nb_fine, h->bfs_visited, 1, h->k2_grid,
+                  h->k2_smem, s, pull ? 1 : 0);
+    if (e != cudaSuccess) return cuda_fail(e, "bfs expand/scatter");
+    e = launch_k3(kMinSelect2nd, true, h->A, h->ws, h->lwb_lo, h->nb_fine, h->bfs_front, nullptr,
+                  h->A.n, nullptr, h->bfs_visited, k3_grid, k3_smem, s, pull ? 1 : 0);
+    if (e != cudaSuccess) return cuda_fail(e, "bfs merge");
+  }
+  if (pull) {
+    e = launch_pull(h, kMinSelect2nd, true, h->bfs_front, nullptr, 0, &h->ws.st->nnz_y,
+                    h->bfs_visited, 1, h->rows_sorted, h->bfs_front, nullptr, h->A.n, nullptr,
+                    h->bfs_visited, push ? 1 : 0, s);
+    if (e != cudaSuccess) return cuda_fail(e, "bfs pull");
+  }
+  k_bfs_continue<<<1, 32, 0, s>>>(cond, h->ws.st, h->A.n);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "bfs condition");
+  return SPMSPV_OK;
+}
+
+// Graph with one WHILE node whose body is one level.
+static int build_bfs_graph(spmspv_handle* h, int sched, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
+  int rc = SPMSPV_OK;
+  do {
+    cudaGraphConditionalHandle cond;
+    if ((e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess) {
+      rc = cuda_fail(e, "cudaGraphConditionalHandleCreate");
+      break;
+    }
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np)) != cudaSuccess) {
+      rc = cuda_fail(e, "add while node");
+      break;
+    }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
+      rc = cuda_fail(e, "capture stream");
+      break;
+    }
+    if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+      rc = cuda_fail(e, "begin capture");
+      break;
+    }
+    void* saved_prof = h->prof;
+    h->prof = nullptr;  // no profiling events inside the graph
+    rc = bfs_level_launches(h, sched, cond, cs);
+    h->prof = saved_prof;
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(cs, &captured);
+    if (rc != SPMSPV_OK) break;
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "end capture");
+      break;
+    }
+    if ((e = cudaGraphInstantiate(&exec, g, 0)) != cudaSuccess) {
+      rc = cuda_fail(e, "instantiate bfs graph");
+      break;
+    }
+  } while (0);
+  if (cs) cudaStreamDestroy(cs);
+  cudaGraphDestroy(g);
+  if (rc != SPMSPV_OK) {
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGetLastError();
+    return rc;
+  }
+  *out = exec;
+  return SPMSPV_OK;
+}
+
+int ensure_bfs_buffers(spmspv_handle* h) {
+  if (h->bfs_front) return SPMSPV_OK;
+  const size_t n = (size_t)h->A.n;
+  cudaError_t e = cudaMalloc(&h->bfs_front, sizeof(int32_t) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&h->bfs_visited, sizeof(uint32_t) * ((n + 31) / 32 + 1));
+  if (e != cudaSuccess) {
+    cudaFree(h->bfs_front);
+    h->bfs_front = nullptr;
+    cudaGetLastError();
+    return fail(SPMSPV_ERR_OOM, "BFS buffers: %s", cudaGetErrorString(e));
+  }
+  return SPMSPV_OK;
+}
+
+void release_bfs_graphs(spmspv_handle* h) {
+  for (int i = 0; i < SPMSPV_NUM_SCHEDULES + 1; ++i) {
+    if (h->bfs_graph[i]) cudaGraphExecDestroy((cudaGraphExec_t)h->bfs_graph[i]);
+    h->bfs_graph[i] = nullptr;
+  }
+}
+
+}  // namespace spmspv
+
+using namespace spmspv;
+
+extern "C" int spmspv_bfs(spmspv_handle* h, int32_t src, int32_t* level, int32_t* parent,
+                          int32_t* d_nlevels, uint32_t opts, spmspv_stream_t stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (h->A.m != h->A.n) return fail(SPMSPV_ERR_ARG, "BFS needs a square matrix");
+  if (src < 0 || src >= h->A.n) return fail(SPMSPV_ERR_ARG, "src = %d outside [0, n)", src);
+  if (!level || !parent) return fail(SPMSPV_ERR_ARG, "level or parent is NULL");
+  if ((opts & SPMSPV_SCHED_FORCE) && SPMSPV_SCHED_ID(opts) >= SPMSPV_NUM_SCHEDULES)
+    return fail(SPMSPV_ERR_ARG, "schedule id out of range");
+  int sched = h->default_sched;
+  if (opts & SPMSPV_SCHED_FORCE) sched = (int)SPMSPV_SCHED_ID(opts);
+  if (opts & SPMSPV_SCHED_AUTO) {
+    if (!h->sel_ready) return fail(SPMSPV_ERR_STATE, "no selector weights loaded or trained");
+    sched = -1;
+  }
+  if ((rc = ensure_bfs_buffers(h)) != SPMSPV_OK) return rc;
+  const int slot = sched < 0 ? SPMSPV_NUM_SCHEDULES : sched;
+  if (!h->bfs_graph[slot]) {
+    cudaGraphExec_t exec = nullptr;
+    if ((rc = build_bfs_graph(h, sched, &exec)) != SPMSPV_OK) return rc;
+    h->bfs_graph[slot] = exec;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  h->last_empty = 0;
+  const int grid = std::max(1, std::min(h->sm_count * 8, (h->A.n + 255) / 256));
+  k_bfs_init<<<grid, 256, 0, s>>>(h->A.n, src, level, parent, h->bfs_visited, h->bfs_front, h->ws.st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "bfs init");
+  if ((e = cudaGraphLaunch((cudaGraphExec_t)h->bfs_graph[slot], s)) != cudaSuccess)
+    return cuda_fail(e, "bfs graph launch");
+  if (d_nlevels) {
+    e = cudaMemcpyAsync(d_nlevels, &h->ws.st->level, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "bfs level count");
+  }
+  return SPMSPV_OK;
+}

@@ -30,6 +30,10 @@ struct spmspv_handle {
   int last_empty;
   void* prof;           // std::vector<ProfileCall>* while profiling, else NULL
   int32_t* rowidx_k2;   // owned row-id copy with hub rows relabelled (NULL without hubs)
+  void* bfs_graph[SPMSPV_NUM_SCHEDULES + 1];  // cudaGraphExec_t per schedule (+ auto)
+  // learned schedule selector
+  int sel_ready;        // weights present
+  float* sel_w;         // device weights (layout in selector.cu)
   // pull direction (dense frontier) buffers, allocated on first use
   uint32_t* xbits;      // [ceil(n/32)] frontier bitmap
   uint32_t* xdense;     // [n] frontier values
@@ -49,13 +53,16 @@ Sched decode_schedule(const spmspv_handle* h, int id);
 int run_push(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_val, int f,
              const int32_t* f_dev, const uint32_t* mask, int mask_comp, const Sched& sc,
              int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y, bool bfs,
-             uint32_t* mask_update, int32_t* level, int32_t* parent, cudaStream_t s);
+             uint32_t* mask_update, cudaStream_t s);
 // Returns -1 when the pull direction is not available for this handle/semiring.
 int run_pull_if_available(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_val,
                           int f, const uint32_t* mask, int mask_comp, const Sched& sc,
                           int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y,
                           cudaStream_t s);
 void release_extras(spmspv_handle* h);
+void release_bfs_graphs(spmspv_handle* h);
+cudaError_t alloc_pull_buffers(spmspv_handle* h);
+int ensure_bfs_buffers(spmspv_handle* h);
 // Per-stage event recording (no-ops unless spmspv_profile_begin was called).
 void prof_call_begin(spmspv_handle* h, cudaStream_t s);
 void prof_mark(spmspv_handle* h, int stage, cudaStream_t s);

@@ -27,133 +27,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "device_util.cuh"
 #include "spmspv_internal.cuh"
 
 namespace spmspv {
-
-// ------------------------------------------------------------------------
-// small device helpers
-// ------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long lb_load(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void lb_store(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// Streaming load (evict-first): matrix entries are read once per call.
-__device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
-__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
-
-// Exclusive look-back prefix for tile `tile`, computed by one full warp:
-// the warp publishes the tile's aggregate, then reads the status words of
-// its LB_WIN*32 nearest predecessors at once and sums back to the nearest
-// one that holds an inclusive prefix, sliding the window when none does.
-// Waits are bounded: on give-up the status word gets ST_TIMEOUT and the
-// words still missing count as empty inclusive prefixes.
-constexpr int LB_WIN = 4;
-
-__device__ unsigned long long warp_lookback(unsigned long long* status, uint32_t tile,
-                                            unsigned long long agg, DevState* st) {
-  const int lane = threadIdx.x & 31;
-  if (tile == 0) {
-    if (lane == 0) lb_store(status, LB_FLAG_INC | agg);
-    return 0ull;
-  }
-  if (lane == 0) lb_store(status + tile, LB_FLAG_AGG | agg);
-  unsigned long long excl = 0;
-  int64_t base = (int64_t)tile - 1;
-  for (;;) {
-    // word k*32+lane of the window is predecessor base - (k*32 + lane)
-    unsigned long long s[LB_WIN];
-#pragma unroll
-    for (int k = 0; k < LB_WIN; ++k) {
-      const int64_t idx = base - (k * 32 + lane);
-      s[k] = idx >= 0 ? lb_load(status + idx) : LB_FLAG_INC;
-    }
-    int first = -1;  // distance of the nearest inclusive prefix in the window
-    uint32_t spins = 0;
-    for (;;) {
-      first = -1;
-      bool all_ready = true;
-#pragma unroll
-      for (int k = 0; k < LB_WIN; ++k) {
-        const unsigned im = __ballot_sync(0xffffffffu, (s[k] & LB_FLAG_MASK) == LB_FLAG_INC);
-        const unsigned rm = __ballot_sync(0xffffffffu, (s[k] & LB_FLAG_MASK) != 0ull);
-        if (first < 0) {
-          if (im) {
-            const int f0 = __ffs(im) - 1;
-            const unsigned need = f0 == 31 ? 0xffffffffu : ((2u << f0) - 1u);
-            if ((rm & need) != need) all_ready = false;
-            first = k * 32 + f0;
-          } else if (rm != 0xffffffffu) {
-            all_ready = false;
-          }
-        }
-      }
-      if (all_ready) break;
-      if (++spins > SPIN_LIMIT) {
-        if (lane == 0) atomicOr(&st->status, ST_TIMEOUT);
-#pragma unroll
-        for (int k = 0; k < LB_WIN; ++k)
-          if ((s[k] & LB_FLAG_MASK) == 0ull) s[k] = LB_FLAG_INC;
-        continue;  // recompute `first` with the missing words as empty prefixes
-      }
-      __nanosleep(32);
-#pragma unroll
-      for (int k = 0; k < LB_WIN; ++k) {
-        const int64_t idx = base - (k * 32 + lane);
-        if ((s[k] & LB_FLAG_MASK) == 0ull && idx >= 0) s[k] = lb_load(status + idx);
-      }
-    }
-    const int stop = first < 0 ? LB_WIN * 32 - 1 : first;
-    unsigned long long v = 0;
-#pragma unroll
-    for (int k = 0; k < LB_WIN; ++k)
-      if (k * 32 + lane <= stop) v += s[k] & LB_VAL_MASK;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    excl += v;
-    if (first >= 0) break;
-    base -= LB_WIN * 32;
-  }
-  if (lane == 0) lb_store(status + tile, LB_FLAG_INC | (excl + agg));
-  return excl;
-}
-
-// Exclusive prefix sum over the block.  `sh` holds NT/32 + 1 shared
-// entries; every thread receives the block total in *total.
-template <int NT, typename T>
-__device__ __forceinline__ T block_exclusive_sum(T v, T* sh, T* total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  T x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    T y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) sh[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    T w = lane < NT / 32 ? sh[lane] : T(0);
-    T wi = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      T y = __shfl_up_sync(0xffffffffu, wi, o);
-      if (lane >= o) wi += y;
-    }
-    if (lane < NT / 32) sh[lane] = wi - w;
-    if (lane == NT / 32 - 1) sh[NT / 32] = wi;
-  }
-  __syncthreads();
-  const T r = sh[wid] + x - v;
-  *total = sh[NT / 32];
-  __syncthreads();
-  return r;
-}
 
 // ------------------------------------------------------------------------
 // K1: work scan + compaction + tile starts
@@ -368,7 +245,8 @@ template <int SEM>
 __global__ void __launch_bounds__(K2_THREADS, 2)
 k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ val, Workspace ws,
                   int lwb_lo, int nb_fine, int32_t m, int64_t nnz, const uint32_t* __restrict__ mask,
-                  int mask_comp) {
+                  int mask_comp, int only_push) {
+  if (only_push && ws.st->dir != 0) return;  // this call runs the pull direction
   extern __shared__ __align__(16) unsigned char k2_smem_raw[];
   __shared__ int32_t s_kept;
 
@@ -568,20 +446,21 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
 }
 
 cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo, int nb_fine,
-                      const uint32_t* mask, int mask_comp, int grid, size_t smem, cudaStream_t s) {
+                      const uint32_t* mask, int mask_comp, int grid, size_t smem, cudaStream_t s,
+                      int only_push) {
   const int32_t* rows = ws.nhot > 0 ? ws.rowidx_k2 : A.rowidx;
   switch (sem) {
     case kPlusTimes:
       k2_expand_scatter<kPlusTimes><<<grid, K2_THREADS, smem, s>>>(
-          rows, A.val, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp);
+          rows, A.val, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp, only_push);
       break;
     case kMinSelect2nd:
       k2_expand_scatter<kMinSelect2nd><<<grid, K2_THREADS, smem, s>>>(
-          rows, nullptr, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp);
+          rows, nullptr, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp, only_push);
       break;
     default:
       k2_expand_scatter<kOrAnd><<<grid, K2_THREADS, smem, s>>>(
-          rows, nullptr, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp);
+          rows, nullptr, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp, only_push);
   }
   return cudaGetLastError();
 }
@@ -593,8 +472,8 @@ template <int SEM, bool BFS>
 __global__ void __launch_bounds__(K3_THREADS)
 k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __restrict__ y_idx,
                 uint32_t* __restrict__ y_val, int32_t y_cap, int32_t* __restrict__ d_nnz_y,
-                uint32_t* __restrict__ mask_update, int32_t* __restrict__ level,
-                int32_t* __restrict__ parent) {
+                uint32_t* __restrict__ mask_update, int only_push) {
+  if (only_push && ws.st->dir != 0) return;  // this call runs the pull direction
   extern __shared__ __align__(16) uint32_t k3_smem[];
   __shared__ int32_t s_scan[K3_THREADS / 32 + 1];
   __shared__ uint32_t s_b;
@@ -614,6 +493,8 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __res
   const uint32_t ident = sr_identity<SEM>();
   const int wpt = nw > K3_THREADS ? nw / K3_THREADS : 1;
   const int32_t lvl = BFS ? st->level : 0;
+  int32_t* const level = BFS ? st->bfs_level : nullptr;
+  int32_t* const parent = BFS ? st->bfs_parent : nullptr;
   const int nhot = ws.nhot;
 
   if (blockIdx.x == 0 && tid == 0) {
@@ -729,6 +610,7 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __res
     if (b == (uint32_t)nb - 1u && tid == 0) {
       const int64_t total = (int64_t)s_off + s_tot;
       st->nnz_y = (int32_t)total;
+      if (BFS) st->nvisited += (int32_t)total;
       if (d_nnz_y) *d_nnz_y = (int32_t)total;
       if (total > y_cap) atomicOr(&st->status, ST_CAPACITY);
     }
@@ -738,9 +620,8 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __res
 
 cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, int lwb_lo,
                       int nb_fine, int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y,
-                      uint32_t* mask_update, int32_t* level, int32_t* parent, int grid,
-                      size_t smem, cudaStream_t s) {
-#define K3_ARGS ws, lwb_lo, nb_fine, A.m, y_idx, y_val, y_cap, d_nnz_y, mask_update, level, parent
+                      uint32_t* mask_update, int grid, size_t smem, cudaStream_t s, int only_push) {
+#define K3_ARGS ws, lwb_lo, nb_fine, A.m, y_idx, y_val, y_cap, d_nnz_y, mask_update, only_push
   if (bfs) {
     k3_bucket_merge<kMinSelect2nd, true><<<grid, K3_THREADS, smem, s>>>(K3_ARGS);
   } else if (sem == kPlusTimes) {
@@ -806,6 +687,27 @@ cudaError_t launch_relabel_hubs(const Matrix& A, const int32_t* hub_of_row, int3
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (A.nnz > 0) k_relabel_hubs<<<sms * 4, 512, 0, s>>>(A.rowidx, A.nnz, hub_of_row, A.m, out);
+  return cudaGetLastError();
+}
+
+// Flags a column whose row ids do not strictly ascend.
+__global__ void k_rows_unsorted(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
+                                int32_t n, int32_t* __restrict__ unsorted) {
+  for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const int32_t p1 = colptr[j + 1];
+    for (int32_t p = colptr[j] + 1; p < p1; ++p)
+      if (rowidx[p] <= rowidx[p - 1]) {
+        atomicOr(unsorted, 1);
+        break;
+      }
+  }
+}
+
+cudaError_t launch_rows_unsorted(const Matrix& A, int32_t* unsorted, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_rows_unsorted<<<sms * 4, 256, 0, s>>>(A.colptr, A.rowidx, A.n, unsorted);
   return cudaGetLastError();
 }
 
@@ -888,11 +790,11 @@ namespace spmspv {
 // BFS level: x values are the vertex ids themselves (select2nd passes the
 // parent id), the count comes from the device, and the level advances.
 cudaError_t launch_k1_bfs(const Matrix& A, const Workspace& ws, int nb_fine, const int32_t* x_idx,
-                          const int32_t* f_dev, int grid, const Sched& sc, cudaStream_t s) {
+                          const int32_t* f_dev, int grid, const Sched* sc, cudaStream_t s) {
   k1_work_scan<<<grid, K1_THREADS, 0, s>>>(x_idx, reinterpret_cast<const uint32_t*>(x_idx), 0,
                                            f_dev, A.colptr, A.n, A.nnz, ws, nb_fine, kMinSelect2nd,
-                                           1, sc.dir, sc.q,
-                                           sc.lwb, 1);
+                                           sc ? 1 : 0, sc ? sc->dir : 0, sc ? sc->q : 0,
+                                           sc ? sc->lwb : 0, 1);
   return cudaGetLastError();
 }
 }  // namespace spmspv

@@ -217,7 +217,7 @@ extern "C" int spmspv_run_noalloc(int32_t m, int32_t n, int64_t nnz, const int32
   const size_t k3_smem = k3_smem_bytes(sc.lwb);
   const int k3_grid = std::max(1, std::min(nb, d->sm_count * k3_blocks_per_sm(semiring, k3_smem)));
   e = launch_k3(semiring, false, A, ws, lwb_lo, nb_fine, y_idx, (uint32_t*)y_val, y_capacity,
-                d_nnz_y, nullptr, nullptr, nullptr, k3_grid, k3_smem, s);
+                d_nnz_y, nullptr, k3_grid, k3_smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "bucket merge launch");
   return SPMSPV_OK;
 }

@@ -70,10 +70,14 @@ struct DevState {
   uint32_t k1_ticket;  // dynamic tile counter of K1
   uint32_t k3_ticket;  // dynamic bucket counter of K3
   int32_t maxdeg;      // largest selected column length (selector feature)
-  int32_t prev_f;      // nnz(x) of the previous call (K1 status words to clear)
+  int32_t sched;       // schedule id of the current call
   unsigned long long sumdeg2;  // sum of squared selected column lengths
-  int32_t level;       // BFS level written by the BFS-mode merge
-  int32_t pad[3];
+  int32_t level;       // BFS level being discovered
+  uint32_t pull_ticket;  // dynamic row-tile counter of the pull kernel
+  int32_t nvisited;    // BFS: vertices reached so far
+  int32_t pad0;
+  int32_t* bfs_level;  // BFS outputs of the current search
+  int32_t* bfs_parent;
 };
 
 struct Workspace {
@@ -93,9 +97,14 @@ struct Workspace {
   const int32_t* hot_rows;   // [HOT_MAX] row ids, ascending
   const int32_t* hot_start;  // [nb_fine+1] first hot index of each fine bucket
   const int32_t* rowidx_k2;  // [nnz] row ids with hub row r replaced by m + its hub index
+  unsigned long long* pull_status;  // [pull tiles] look-back words of the pull kernel
   uint32_t* hot_val;         // [HOT_MAX] per-call sums of the hot rows
   uint32_t* hot_touch;       // [HOT_MAX] 1 when a hot row received a product this call
 };
+
+// ---- pull direction (matrix-driven masked SpMV) ----
+constexpr int PULL_THREADS = 256;
+constexpr int PULL_ROWS = PULL_THREADS * 32;  // rows per pull tile: one 32-row word per thread
 
 struct Matrix {
   int32_t m, n;
@@ -115,15 +124,19 @@ struct Sched {
 cudaError_t launch_k1(int sem, const Matrix& A, const Workspace& ws, int nb_fine,
                       const int32_t* x_idx, const uint32_t* x_val, int f, const int32_t* f_dev,
                       int grid, const Sched* forced, cudaStream_t s);
+cudaError_t launch_k1_bfs(const Matrix& A, const Workspace& ws, int nb_fine, const int32_t* x_idx,
+                          const int32_t* f_dev, int grid, const Sched* sc, cudaStream_t s);
 cudaError_t launch_row_degrees(const Matrix& A, int32_t* deg, int32_t* maxdeg, cudaStream_t s);
+cudaError_t launch_rows_unsorted(const Matrix& A, int32_t* unsorted, cudaStream_t s);
 cudaError_t launch_relabel_hubs(const Matrix& A, const int32_t* hub_of_row, int32_t* out,
                                 cudaStream_t s);
 cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo, int nb_fine,
-                      const uint32_t* mask, int mask_comp, int grid, size_t smem, cudaStream_t s);
+                      const uint32_t* mask, int mask_comp, int grid, size_t smem, cudaStream_t s,
+                      int only_push = 0);
 cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, int lwb_lo,
                       int nb_fine, int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y,
-                      uint32_t* mask_update, int32_t* level, int32_t* parent, int grid,
-                      size_t smem, cudaStream_t s);
+                      uint32_t* mask_update, int grid, size_t smem, cudaStream_t s,
+                      int only_push = 0);
 cudaError_t launch_bucket_sizes(const Matrix& A, int lwb_lo, int nb_fine, int32_t* counts,
                                 unsigned int* bad, cudaStream_t s);
 // K2 shared memory: staged (row, value) pairs of one tile, the start,

@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True):
         lib.spmspv_run_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P,
                                            _P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int32,
                                            _P, ctypes.c_uint32, _P, _P, ctypes.c_int32, _P, _P]
+        lib.spmspv_bfs.argtypes = [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_uint32, _P]
         lib.spmspv_profile_begin.argtypes = [_P]
         lib.spmspv_profile_end.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_int32)]
@@ -155,6 +156,11 @@ def spmspv_run_noalloc(m, n, nnz, colptr, rowidx, val, val_type, semiring, x_idx
     _check(rc, "spmspv_run_noalloc")
 
 
+def spmspv_bfs(h, src, level, parent, d_nlevels, opts=0, stream=None):
+    _check(load().spmspv_bfs(h, int(src), _ptr(level), _ptr(parent), _ptr(d_nlevels), int(opts),
+                             _stream(stream)), "spmspv_bfs")
+
+
 def spmspv_device_status(h) -> int:
     v = ctypes.c_uint32(0)
     _check(load().spmspv_device_status(h, ctypes.byref(v)), "spmspv_device_status")
@@ -207,6 +213,15 @@ class CscMatrix:
             self.close()
         except Exception:
             pass
+
+    def bfs(self, src, opts=0, stream=None):
+        """(level, parent, nlevels) of a BFS from src; level/parent are CUDA tensors."""
+        dev = self.colptr.device
+        level = torch.empty(self.n, dtype=torch.int32, device=dev)
+        parent = torch.empty(self.n, dtype=torch.int32, device=dev)
+        nl = torch.zeros(1, dtype=torch.int32, device=dev)
+        spmspv_bfs(self.handle, src, level, parent, nl, opts, stream)
+        return level, parent, int(nl.item())
 
     def multiply(self, semiring, x_idx, x_val=None, mask=None, opts=0, y_capacity=None,
                  stream=None, out=None):

@@ -1,0 +1,108 @@
+"""GPU BFS (device-side level loop) and the pull direction against the oracle.
+
+Levels and parents must match the oracle bit for bit (Sec. IV-D level rule:
+the parent is the smallest-id neighbour one level closer).  Every fixed
+schedule is run: push (bucketed SpMSpV) and, for symmetric patterns, pull
+(matrix-driven masked SpMV).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import SEMIRING_TO_ORACLE, compare, need_gpu, x_values
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = need_gpu()
+    from paper_1610_07902_gb300 import spmspv as S
+    S.load()
+    return torch, S
+
+
+GRAPHS = [
+    ("rmat12", lambda: synth.rmat(12, seed=5), True),
+    ("rmat14", lambda: synth.rmat(14, seed=6), True),
+    ("grid3d", lambda: synth.grid3d(18, 17, 16, 0.05, seed=3), True),
+    ("grid2d_long", lambda: synth.grid3d(300, 9, 1, 0.02, seed=3), True),
+    ("er_directed", lambda: synth.erdos_renyi(5000, d=3, seed=9), False),
+]
+
+
+@pytest.mark.parametrize("name,make,sym", GRAPHS)
+def test_bfs_all_fixed_schedules(lib, name, make, sym):
+    torch, S = lib
+    A = make()
+    flags = S.SPMSPV_CSC_PATTERN_SYMMETRIC if sym else 0
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val, flags=flags)
+    for src in synth.sources(A.colptr, 2, seed=3):
+        ref_level, ref_parent, ref_nl, _, _ = oracle.bfs(A.colptr, A.rowidx, src)
+        for sched in range(12):
+            level, parent, nl = Ad.bfs(int(src), S.SPMSPV_SCHED_OPT(sched))
+            assert S.spmspv_device_status(Ad.handle) == 0
+            np.testing.assert_array_equal(level.cpu().numpy(), ref_level, err_msg="sched %d" % sched)
+            np.testing.assert_array_equal(parent.cpu().numpy(), ref_parent, err_msg="sched %d" % sched)
+            assert nl == ref_nl
+        # default schedule, twice in a row on the same handle
+        for _ in range(2):
+            level, parent, nl = Ad.bfs(int(src))
+            np.testing.assert_array_equal(level.cpu().numpy(), ref_level)
+            assert nl == ref_nl
+    Ad.close()
+
+
+def test_bfs_isolated_source_and_intact_grid(lib):
+    torch, S = lib
+    X, Y, Z = 11, 10, 9
+    A = synth.grid3d(X, Y, Z, 0.0)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
+    c = (5, 5, 4)
+    src = c[0] * Y * Z + c[1] * Z + c[2]
+    level, parent, nl = Ad.bfs(src)
+    v = np.arange(A.n)
+    x, y, z = v // (Y * Z), (v // Z) % Y, v % Z
+    np.testing.assert_array_equal(level.cpu().numpy(),
+                                  np.abs(x - c[0]) + np.abs(y - c[1]) + np.abs(z - c[2]))
+    Ad.close()
+    R = synth.rmat(11, seed=2)
+    iso = int(np.flatnonzero(np.diff(R.colptr) == 0)[0])
+    Rd = S.CscMatrix(R.m, R.n, R.colptr, R.rowidx, R.val, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
+    level, parent, nl = Rd.bfs(iso)
+    lv = level.cpu().numpy()
+    assert nl == 1 and lv[iso] == 0 and (lv >= 0).sum() == 1
+    Rd.close()
+
+
+def symmetric_values(A):
+    """Values with A(i,j) == A(j,i) on a pattern-symmetric matrix."""
+    cols = np.repeat(np.arange(A.n, dtype=np.int64), np.diff(A.colptr))
+    lo = np.minimum(cols, A.rowidx.astype(np.int64))
+    hi = np.maximum(cols, A.rowidx.astype(np.int64))
+    h = (lo * 0x9E3779B1 + hi * 0x85EBCA77) & 0xFFFFFF
+    return (h.astype(np.float64) / float(1 << 24)).astype(np.float32)
+
+
+@pytest.mark.parametrize("scale", [11, 14])
+def test_pull_direction_all_semirings(lib, scale):
+    torch, S = lib
+    A = synth.rmat(scale, seed=scale)
+    A.val = symmetric_values(A)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val, flags=S.SPMSPV_CSC_SYMMETRIC)
+    rng = np.random.default_rng(scale)
+    for f in [1, 300, A.n // 3, A.n]:
+        x_idx, xf = synth.frontier(A.n, f, seed=f)
+        mask = (rng.random(A.m) < 0.4).astype(np.uint8)
+        for semiring in (0, 1, 2):
+            xv = x_values(semiring, x_idx, xf)
+            for msk, comp in ((None, True), (mask, True), (mask, False)):
+                ref = oracle.spmspv(A.m, A.colptr, A.rowidx, A.val, SEMIRING_TO_ORACLE[semiring],
+                                    x_idx, xv, msk, comp)
+                for sched in (6, 10):  # pull schedules
+                    from test_gpu_spmspv import _run
+                    yi, yv, k, st = _run(lib, A, Ad, semiring, x_idx, xv, msk, comp, sched)
+                    assert st == 0 and k == ref.idx.shape[0]
+                    compare(semiring, ref, yi, yv)
+    Ad.close()
