@@ -82,6 +82,8 @@ typedef struct spmspv_handle spmspv_handle;
 #define SPMSPV_SORTED_OUT 2u      /* y_idx ascending (see note below) */
 #define SPMSPV_SCHED_AUTO 4u      /* let the learned selector pick the schedule */
 #define SPMSPV_SCHED_FORCE 8u     /* use schedule SPMSPV_SCHED_ID(opts) */
+#define SPMSPV_WITH_FEATURES 16u  /* also compute the selector features (spmspv_last_features)
+                                     with a fixed schedule; costs a pass over the mask */
 #define SPMSPV_SCHED_SHIFT 8
 #define SPMSPV_SCHED_OPT(s) (SPMSPV_SCHED_FORCE | ((uint32_t)(s) << SPMSPV_SCHED_SHIFT))
 #define SPMSPV_SCHED_ID(opts) (((opts) >> SPMSPV_SCHED_SHIFT) & 0xFFu)
@@ -166,6 +168,46 @@ int spmspv_run(spmspv_handle* h, int semiring, const int32_t* x_idx, const void*
  */
 int spmspv_bfs(spmspv_handle* h, int32_t src, int32_t* level, int32_t* parent,
                int32_t* d_nlevels, uint32_t opts, spmspv_stream_t stream);
+
+/* ---- learned schedule selector ----
+ * No counterpart in the paper, which leaves open when to switch between the
+ * vector-driven (push) and matrix-driven (pull) forms (Sec. V).  A 6->32->32->12
+ * FP32 MLP predicts the log run time of each of the 12 schedules
+ * (SPMSPV_SCHED_ID = dir*6 + quantum*3 + width: 3 bucket widths x 2 work quanta x
+ * {push, pull}) from features of the call (log2(1+nnz(x)), log2(1+work), max/mean
+ * selected column length, fraction of rows set in the mask, log2(m), nnz(A)/n) computed on the
+ * device after the work scan, and picks the fastest predicted allowed schedule
+ * (pull only for symmetric patterns).  It never changes results.
+ * Parameters: SPMSPV_SELECTOR_NPARAM floats = W1[32][6] b1[32] W2[32][32] b2[32]
+ * W3[12][32] b3[12] mean[6] scale[6] (inputs are (feature - mean) * scale). */
+#define SPMSPV_SELECTOR_NPARAM 1688
+
+/* Install / read the selector parameters (host arrays of `n` floats). */
+int spmspv_selector_set(spmspv_handle* h, const float* params, int32_t n);
+int spmspv_selector_get(spmspv_handle* h, float* params, int32_t n);
+
+/* The 6 selector features of the handle's last call (host out; synchronises). */
+int spmspv_last_features(spmspv_handle* h, float* feats);
+
+/* Schedule id the selector chose in the handle's last SPMSPV_SCHED_AUTO call, or
+ * the id of the last forced schedule (host out; synchronises). */
+int spmspv_last_schedule(spmspv_handle* h, int32_t* sched);
+
+/* Train the selector on the device with the library's own forward/backward
+ * kernels and Adam: feats [n][6] raw features, target [n][12] log run times,
+ * valid [n][12] bytes (NULL: all valid), all device pointers.  Starts from the
+ * installed parameters, else a seeded He initialisation; the input
+ * normalisation is taken from the data.  loss (host, `epochs` floats, may be
+ * NULL) receives the mean squared error of each epoch.  Synchronous. */
+int spmspv_selector_train(spmspv_handle* h, const float* feats, const float* target,
+                          const uint8_t* valid, int32_t n, int32_t epochs, int32_t batch,
+                          float lr, uint64_t seed, float* loss);
+
+/* Gradient (host out, 1676 floats: the weights in parameter order) and loss
+ * (host out, may be NULL) of the summed squared error at the installed
+ * parameters, on device arrays as for spmspv_selector_train.  Synchronous. */
+int spmspv_selector_grad(spmspv_handle* h, const float* feats, const float* target,
+                         const uint8_t* valid, int32_t n, float* grad, float* loss);
 
 /* Device status word of the handle: synchronises the handle's last stream,
  * returns the SPMSPV_DEV_* bits in *flags (host out) and clears them. */

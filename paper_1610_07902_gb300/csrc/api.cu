@@ -75,8 +75,15 @@ static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 int select_hot_rows(spmspv_handle* h);
 
+// Work-scan CTAs needed to count the mask's bits in one pass of 4 words per thread.
+static int mask_pass_grid(const spmspv_handle* h) {
+  const int64_t words = ((int64_t)h->A.m + 31) / 32;
+  return (int)std::min<int64_t>(h->k1_grid_max, (words + K1_THREADS * 4 - 1) / (K1_THREADS * 4));
+}
+
 Sched decode_schedule(const spmspv_handle* h, int id) {
   Sched s;
+  s.id = id;
   s.dir = id / 6;
   s.q = ((id / 3) % 2) ? 2 * QF : QF;
   s.lwb = h->lwb_lo + id % 3;
@@ -100,13 +107,15 @@ int run_push(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_
              uint32_t* mask_update, cudaStream_t s) {
   int k1_grid = f_dev ? h->k1_grid_max
                       : (int)std::min<int64_t>(h->k1_grid_max, ((int64_t)f + K1_TILE - 1) / K1_TILE);
+  if (h->k1_mask) k1_grid = std::max(k1_grid, mask_pass_grid(h));
   if (k1_grid < 1) k1_grid = 1;
   cudaError_t e;
   prof_call_begin(h, s);
   if (bfs) {
-    e = launch_k1_bfs(h->A, h->ws, h->nb_fine, x_idx, f_dev, k1_grid, &sc, s);
+    e = launch_k1_bfs(h->A, h->ws, h->nb_fine, x_idx, f_dev, k1_grid, &sc, s, mask);
   } else {
-    e = launch_k1(sem, h->A, h->ws, h->nb_fine, x_idx, x_val, f, f_dev, k1_grid, &sc, s);
+    e = launch_k1(sem, h->A, h->ws, h->nb_fine, x_idx, x_val, f, f_dev, k1_grid, &sc, s,
+                  h->k1_mask);
   }
   if (e != cudaSuccess) return cuda_fail(e, "work scan launch");
   prof_mark(h, SPMSPV_STAGE_SCAN, s);
@@ -187,6 +196,50 @@ int select_hot_rows(spmspv_handle* h) {
   if (e != cudaSuccess) return cuda_fail(e, "hub relabel");
   h->ws.rowidx_k2 = h->rowidx_k2;
   h->ws.nhot = nh;
+  return SPMSPV_OK;
+}
+
+cudaError_t launch_selector(spmspv_handle* h, int allow_pull, cudaStream_t s);
+cudaError_t launch_pull(const spmspv_handle* h, int sem, bool bfs, const int32_t* x_idx,
+                        const uint32_t* x_val, int f, const int32_t* f_dev, const uint32_t* mask,
+                        int mask_comp, int early_exit, int32_t* y_idx, uint32_t* y_val,
+                        int32_t y_cap, int32_t* d_nnz_y, uint32_t* visited, int only_pull,
+                        cudaStream_t s);
+int pull_available(const spmspv_handle* h, int sem);
+
+// Learned schedule: work scan -> selector (on the device) -> the push kernels
+// and, when the pull form is available, the pull kernels; each set runs only
+// if the selector chose its direction.
+int run_auto(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_val, int f,
+             const uint32_t* mask, int mask_comp, int32_t* y_idx, uint32_t* y_val, int32_t y_cap,
+             int32_t* d_nnz_y, cudaStream_t s) {
+  const int can_pull = pull_available(h, sem);
+  int k1_grid = (int)std::max<int64_t>(1, std::min<int64_t>(h->k1_grid_max, ((int64_t)f + K1_TILE - 1) / K1_TILE));
+  if (mask) k1_grid = std::max(k1_grid, mask_pass_grid(h));
+  prof_call_begin(h, s);
+  cudaError_t e = launch_k1(sem, h->A, h->ws, h->nb_fine, x_idx, x_val, f, nullptr, k1_grid, nullptr, s,
+                            mask);
+  if (e != cudaSuccess) return cuda_fail(e, "work scan launch");
+  prof_mark(h, SPMSPV_STAGE_SCAN, s);
+  if ((e = launch_selector(h, can_pull, s)) != cudaSuccess) return cuda_fail(e, "selector launch");
+  prof_mark(h, SPMSPV_STAGE_SELECT, s);
+  e = launch_k2(sem, h->A, h->ws, h->lwb_lo, h->nb_fine, mask, mask_comp, h->k2_grid, h->k2_smem, s,
+                can_pull);
+  if (e != cudaSuccess) return cuda_fail(e, "expand/scatter launch");
+  prof_mark(h, SPMSPV_STAGE_SCATTER, s);
+  const int lwb = h->lwb_lo + 2;  // shared memory for the widest bucket
+  const int nb_max = (int)(((int64_t)h->A.m + (1 << h->lwb_lo) - 1) >> h->lwb_lo);
+  const int k3_grid = std::max(1, std::min(nb_max, h->sm_count * h->k3_bps[2]));
+  e = launch_k3(sem, false, h->A, h->ws, h->lwb_lo, h->nb_fine, y_idx, y_val, y_cap, d_nnz_y,
+                nullptr, k3_grid, k3_smem_bytes(lwb), s, can_pull);
+  if (e != cudaSuccess) return cuda_fail(e, "bucket merge launch");
+  prof_mark(h, SPMSPV_STAGE_MERGE, s);
+  if (can_pull) {
+    e = launch_pull(h, sem, false, x_idx, x_val, f, nullptr, mask, mask_comp, 0, y_idx, y_val, y_cap,
+                    d_nnz_y, nullptr, 1, s);
+    if (e != cudaSuccess) return cuda_fail(e, "pull launch");
+    prof_mark(h, SPMSPV_STAGE_PULL, s);
+  }
   return SPMSPV_OK;
 }
 
@@ -427,19 +480,27 @@ int spmspv_run(spmspv_handle* h, int semiring, const int32_t* x_idx, const void*
     return e == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "memset nnz_y");
   }
   h->last_empty = 0;
+  const int mask_comp = (opts & SPMSPV_MASK_COMPLEMENT) ? 1 : 0;
+  if (opts & SPMSPV_SCHED_AUTO) {
+    if (!h->sel_ready) return fail(SPMSPV_ERR_STATE, "no selector weights loaded or trained");
+    return run_auto(h, semiring, x_idx, (const uint32_t*)x_val, nnz_x, mask, mask_comp, y_idx,
+                    (uint32_t*)y_val, y_capacity, d_nnz_y, s);
+  }
   int sid = h->default_sched;
   if (opts & SPMSPV_SCHED_FORCE) sid = (int)SPMSPV_SCHED_ID(opts);
   Sched sc = decode_schedule(h, sid);
   if (sc.dir == 1) {
-    rc = run_pull_if_available(h, semiring, x_idx, (const uint32_t*)x_val, nnz_x, mask,
-                               (opts & SPMSPV_MASK_COMPLEMENT) ? 1 : 0, sc, y_idx,
-                               (uint32_t*)y_val, y_capacity, d_nnz_y, s);
+    rc = run_pull_if_available(h, semiring, x_idx, (const uint32_t*)x_val, nnz_x, mask, mask_comp,
+                               sc, y_idx, (uint32_t*)y_val, y_capacity, d_nnz_y, s);
     if (rc != -1) return rc;
-    sc.dir = 0;  // no row access to A: fall back to the push form of the same schedule
+    sc.dir = 0;  // no row access to A: the push form of the same schedule
+    sc.id = sc.id % 6;
   }
-  return run_push(h, semiring, x_idx, (const uint32_t*)x_val, nnz_x, nullptr, mask,
-                  (opts & SPMSPV_MASK_COMPLEMENT) ? 1 : 0, sc, y_idx, (uint32_t*)y_val, y_capacity,
-                  d_nnz_y, false, nullptr, s);
+  h->k1_mask = (opts & SPMSPV_WITH_FEATURES) ? mask : nullptr;
+  rc = run_push(h, semiring, x_idx, (const uint32_t*)x_val, nnz_x, nullptr, mask, mask_comp, sc,
+                y_idx, (uint32_t*)y_val, y_capacity, d_nnz_y, false, nullptr, s);
+  h->k1_mask = nullptr;
+  return rc;
 }
 
 int spmspv_device_status(spmspv_handle* h, uint32_t* flags) {

@@ -27,6 +27,8 @@ cudaError_t launch_pull(const spmspv_handle* h, int sem, bool bfs, const int32_t
                         cudaStream_t s);
 int pull_available(const spmspv_handle* h, int sem);
 cudaError_t launch_selector(spmspv_handle* h, int allow_pull, cudaStream_t s);
+cudaError_t launch_selector_cond(spmspv_handle* h, int allow_pull, cudaGraphConditionalHandle c_push,
+                                 cudaGraphConditionalHandle c_pull, cudaStream_t s);
 
 namespace {
 
@@ -57,39 +59,95 @@ __global__ void k_bfs_continue(cudaGraphConditionalHandle cond, const DevState* 
 
 }  // namespace
 
-// One BFS level on `s` (captured into the loop body).
+static int bfs_push_launches(spmspv_handle* h, const Sched& sc, int lwb, cudaStream_t s) {
+  const size_t k3_smem = k3_smem_bytes(lwb);
+  const int nb_max = (int)(((int64_t)h->A.m + (1 << h->lwb_lo) - 1) >> h->lwb_lo);
+  const int k3_grid = std::max(1, std::min(nb_max, h->sm_count * h->k3_bps[lwb - h->lwb_lo]));
+  (void)sc;
+  cudaError_t e = launch_k2(kMinSelect2nd, h->A, h->ws, h->lwb_lo, h->nb_fine, h->bfs_visited, 1,
+                            h->k2_grid, h->k2_smem, s, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "bfs expand/scatter");
+  e = launch_k3(kMinSelect2nd, true, h->A, h->ws, h->lwb_lo, h->nb_fine, h->bfs_front, nullptr,
+                h->A.n, nullptr, h->bfs_visited, k3_grid, k3_smem, s, 0);
+  return e == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "bfs merge");
+}
+
+static int bfs_pull_launches(spmspv_handle* h, cudaStream_t s) {
+  cudaError_t e = launch_pull(h, kMinSelect2nd, true, h->bfs_front, nullptr, 0, &h->ws.st->nnz_y,
+                              h->bfs_visited, 1, h->rows_sorted, h->bfs_front, nullptr, h->A.n,
+                              nullptr, h->bfs_visited, 0, s);
+  return e == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "bfs pull");
+}
+
+// Add an IF node (condition `hc`) after the current capture point of `s` and
+// capture the launches of `fn` into its body on the side stream.
+template <typename Fn>
+static int capture_if_with(cudaStream_t s, cudaStream_t side, cudaGraphConditionalHandle hc, Fn fn) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps);
+  if (e != cudaSuccess || cst != cudaStreamCaptureStatusActive) return cuda_fail(e, "capture info");
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = hc;
+  np.conditional.type = cudaGraphCondTypeIf;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &np)) != cudaSuccess)
+    return cuda_fail(e, "add if node");
+  if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+    return cuda_fail(e, "capture dependencies");
+  if ((e = cudaStreamBeginCaptureToGraph(side, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    return cuda_fail(e, "begin if capture");
+  int rc = fn(side);
+  cudaGraph_t tmp = nullptr;
+  e = cudaStreamEndCapture(side, &tmp);
+  if (rc != SPMSPV_OK) return rc;
+  return e == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "end if capture");
+}
+
+// One BFS level on `s` (captured into the loop body).  A fixed schedule
+// launches its direction's kernels; the learned schedule launches the work
+// scan and the selector, then two IF nodes (push, pull) of which the
+// selector enables one.
 static int bfs_level_launches(spmspv_handle* h, int sched, cudaGraphConditionalHandle cond,
-                              cudaStream_t s) {
+                              cudaStream_t s, cudaStream_t side) {
   const bool autos = sched < 0;
   const bool can_pull = pull_available(h, kMinSelect2nd) != 0;
   Sched sc = decode_schedule(h, autos ? h->default_sched : sched);
-  if (!can_pull) sc.dir = 0;
+  if (!can_pull && sc.dir == 1) {
+    sc.dir = 0;
+    sc.id %= 6;
+  }
   cudaError_t e = launch_k1_bfs(h->A, h->ws, h->nb_fine, h->bfs_front, &h->ws.st->nnz_y,
-                                h->k1_grid_max, autos ? nullptr : &sc, s);
+                                h->k1_grid_max, autos ? nullptr : &sc, s,
+                                autos ? h->bfs_visited : nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "bfs work scan");
-  if (autos) {
-    if ((e = launch_selector(h, can_pull ? 1 : 0, s)) != cudaSuccess) return cuda_fail(e, "bfs selector");
+  int rc = SPMSPV_OK;
+  if (!autos) {
+    rc = sc.dir == 0 ? bfs_push_launches(h, sc, sc.lwb, s) : bfs_pull_launches(h, s);
+  } else if (!can_pull) {
+    if ((e = launch_selector(h, 0, s)) != cudaSuccess) return cuda_fail(e, "bfs selector");
+    rc = bfs_push_launches(h, sc, h->lwb_lo + 2, s);
+  } else {
+    // both IF handles exist before the selector that sets them is captured
+    cudaGraphConditionalHandle c_push = 0, c_pull = 0;
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    if ((e = cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, nullptr, nullptr, nullptr)) != cudaSuccess)
+      return cuda_fail(e, "capture info");
+    if ((e = cudaGraphConditionalHandleCreate(&c_push, cg, 0, cudaGraphCondAssignDefault)) != cudaSuccess ||
+        (e = cudaGraphConditionalHandleCreate(&c_pull, cg, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+      return cuda_fail(e, "if handles");
+    if ((e = launch_selector_cond(h, 1, c_push, c_pull, s)) != cudaSuccess) return cuda_fail(e, "bfs selector");
+    rc = capture_if_with(s, side, c_push, [&](cudaStream_t ss) { return bfs_push_launches(h, sc, h->lwb_lo + 2, ss); });
+    if (rc == SPMSPV_OK)
+      rc = capture_if_with(s, side, c_pull, [&](cudaStream_t ss) { return bfs_pull_launches(h, ss); });
   }
-  const bool push = autos || sc.dir == 0;
-  const bool pull = can_pull && (autos || sc.dir == 1);
-  if (push) {
-    const int lwb = autos ? h->lwb_lo + 2 : sc.lwb;
-    const size_t k3_smem = k3_smem_bytes(lwb);
-    const int nb_max = (int)(((int64_t)h->A.m + (1 << h->lwb_lo) - 1) >> h->lwb_lo);
-    const int k3_grid = std::max(1, std::min(nb_max, h->sm_count * h->k3_bps[lwb - h->lwb_lo]));
-    e = launch_k2(kMinSelect2nd, h->A, h->ws, h->lwb_lo, h->nb_fine, h->bfs_visited, 1, h->k2_grid,
-                  h->k2_smem, s, pull ? 1 : 0);
-    if (e != cudaSuccess) return cuda_fail(e, "bfs expand/scatter");
-    e = launch_k3(kMinSelect2nd, true, h->A, h->ws, h->lwb_lo, h->nb_fine, h->bfs_front, nullptr,
-                  h->A.n, nullptr, h->bfs_visited, k3_grid, k3_smem, s, pull ? 1 : 0);
-    if (e != cudaSuccess) return cuda_fail(e, "bfs merge");
-  }
-  if (pull) {
-    e = launch_pull(h, kMinSelect2nd, true, h->bfs_front, nullptr, 0, &h->ws.st->nnz_y,
-                    h->bfs_visited, 1, h->rows_sorted, h->bfs_front, nullptr, h->A.n, nullptr,
-                    h->bfs_visited, push ? 1 : 0, s);
-    if (e != cudaSuccess) return cuda_fail(e, "bfs pull");
-  }
+  if (rc != SPMSPV_OK) return rc;
   k_bfs_continue<<<1, 32, 0, s>>>(cond, h->ws.st, h->A.n);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "bfs condition");
   return SPMSPV_OK;
@@ -99,7 +157,7 @@ static int bfs_level_launches(spmspv_handle* h, int sched, cudaGraphConditionalH
 static int build_bfs_graph(spmspv_handle* h, int sched, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaStream_t cs = nullptr;
+  cudaStream_t cs = nullptr, side = nullptr;
   cudaError_t e = cudaGraphCreate(&g, 0);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
   int rc = SPMSPV_OK;
@@ -120,7 +178,8 @@ static int build_bfs_graph(spmspv_handle* h, int sched, cudaGraphExec_t* out) {
       break;
     }
     cudaGraph_t body = np.conditional.phGraph_out[0];
-    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking)) != cudaSuccess) {
       rc = cuda_fail(e, "capture stream");
       break;
     }
@@ -131,7 +190,7 @@ static int build_bfs_graph(spmspv_handle* h, int sched, cudaGraphExec_t* out) {
     }
     void* saved_prof = h->prof;
     h->prof = nullptr;  // no profiling events inside the graph
-    rc = bfs_level_launches(h, sched, cond, cs);
+    rc = bfs_level_launches(h, sched, cond, cs, side);
     h->prof = saved_prof;
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(cs, &captured);
@@ -146,6 +205,7 @@ static int build_bfs_graph(spmspv_handle* h, int sched, cudaGraphExec_t* out) {
     }
   } while (0);
   if (cs) cudaStreamDestroy(cs);
+  if (side) cudaStreamDestroy(side);
   cudaGraphDestroy(g);
   if (rc != SPMSPV_OK) {
     if (exec) cudaGraphExecDestroy(exec);

@@ -28,6 +28,7 @@ struct spmspv_handle {
   int default_sched;
   cudaStream_t last_stream;
   int last_empty;
+  const uint32_t* k1_mask;  // mask whose bits the work scan counts (features), or NULL
   void* prof;           // std::vector<ProfileCall>* while profiling, else NULL
   int32_t* rowidx_k2;   // owned row-id copy with hub rows relabelled (NULL without hubs)
   void* bfs_graph[SPMSPV_NUM_SCHEDULES + 1];  // cudaGraphExec_t per schedule (+ auto)

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(K1_THREADS)
 k1_work_scan(const int32_t* __restrict__ x_idx, const uint32_t* __restrict__ x_val, int f_host,
              const int32_t* __restrict__ f_dev, const int32_t* __restrict__ colptr, int32_t n,
              int64_t nnz, Workspace ws, int nb_fine, int sem, int forced, int f_dir, int f_q,
-             int f_lwb, int bfs_level_inc) {
+             int f_lwb, int bfs_level_inc, const uint32_t* __restrict__ mask, int32_t m) {
   __shared__ int32_t s_deg[K1_SMEM_WORDS];
   __shared__ int32_t s_c0[K1_SMEM_WORDS];
   __shared__ uint32_t s_xv[K1_SMEM_WORDS];
@@ -79,8 +79,10 @@ k1_work_scan(const int32_t* __restrict__ x_idx, const uint32_t* __restrict__ x_v
         st->dir = f_dir;
         st->q = f_q;
         st->lwb = f_lwb;
+        st->sched = forced - 1;
       }
       if (bfs_level_inc) st->level += 1;
+      else st->bfs_level = nullptr;  // not a BFS level
       if (f == 0) {
         st->fc = 0;
         st->W = 0;
@@ -194,9 +196,20 @@ k1_work_scan(const int32_t* __restrict__ x_idx, const uint32_t* __restrict__ x_v
     }
     __syncthreads();
   }
-  // selector features
+  // selector features: degree statistics and the number of masked rows
   atomicMax(&s_maxdeg, maxdeg);
   atomicAdd(&s_sq, sq);
+  int32_t mc = 0;
+  if (mask) {
+    const int32_t words = (m + 31) / 32;
+    for (int32_t i = blockIdx.x * K1_THREADS + tid; i < words; i += gridDim.x * K1_THREADS) {
+      uint32_t wv = mask[i];
+      if (i == words - 1 && (m & 31)) wv &= (1u << (m & 31)) - 1u;
+      mc += __popc(wv);
+    }
+    for (int o = 16; o > 0; o >>= 1) mc += __shfl_xor_sync(0xffffffffu, mc, o);
+    if ((tid & 31) == 0 && mc) atomicAdd(&st->maskcnt, mc);
+  }
   __syncthreads();
   if (tid == 0 && s_sq != 0ull) {
     atomicMax(&st->maxdeg, s_maxdeg);
@@ -206,10 +219,11 @@ k1_work_scan(const int32_t* __restrict__ x_idx, const uint32_t* __restrict__ x_v
 
 cudaError_t launch_k1(int sem, const Matrix& A, const Workspace& ws, int nb_fine,
                       const int32_t* x_idx, const uint32_t* x_val, int f, const int32_t* f_dev,
-                      int grid, const Sched* forced, cudaStream_t s) {
+                      int grid, const Sched* forced, cudaStream_t s, const uint32_t* mask) {
   k1_work_scan<<<grid, K1_THREADS, 0, s>>>(x_idx, x_val, f, f_dev, A.colptr, A.n, A.nnz, ws, nb_fine,
-                                           sem, forced ? 1 : 0, forced ? forced->dir : 0,
-                                           forced ? forced->q : 0, forced ? forced->lwb : 0, 0);
+                                           sem, forced ? forced->id + 1 : 0, forced ? forced->dir : 0,
+                                           forced ? forced->q : 0, forced ? forced->lwb : 0, 0,
+                                           mask, A.m);
   return cudaGetLastError();
 }
 
@@ -502,6 +516,7 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __res
     st->k1_ticket = 0u;
     st->maxdeg = 0;
     st->sumdeg2 = 0ull;
+    st->maskcnt = 0;
   }
   if (blockIdx.x == 0) {
     const int nt1 = (st->f + K1_TILE - 1) / K1_TILE;
@@ -790,11 +805,12 @@ namespace spmspv {
 // BFS level: x values are the vertex ids themselves (select2nd passes the
 // parent id), the count comes from the device, and the level advances.
 cudaError_t launch_k1_bfs(const Matrix& A, const Workspace& ws, int nb_fine, const int32_t* x_idx,
-                          const int32_t* f_dev, int grid, const Sched* sc, cudaStream_t s) {
+                          const int32_t* f_dev, int grid, const Sched* sc, cudaStream_t s,
+                          const uint32_t* mask) {
   k1_work_scan<<<grid, K1_THREADS, 0, s>>>(x_idx, reinterpret_cast<const uint32_t*>(x_idx), 0,
                                            f_dev, A.colptr, A.n, A.nnz, ws, nb_fine, kMinSelect2nd,
-                                           sc ? 1 : 0, sc ? sc->dir : 0, sc ? sc->q : 0,
-                                           sc ? sc->lwb : 0, 1);
+                                           sc ? sc->id + 1 : 0, sc ? sc->dir : 0, sc ? sc->q : 0,
+                                           sc ? sc->lwb : 0, 1, mask, A.m);
   return cudaGetLastError();
 }
 }  // namespace spmspv

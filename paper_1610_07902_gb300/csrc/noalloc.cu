@@ -203,6 +203,7 @@ extern "C" int spmspv_run_noalloc(int32_t m, int32_t n, int64_t nnz, const int32
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "region start launch");
 
   Sched sc;
+  sc.id = 4;
   sc.dir = 0;
   sc.q = 2 * QF;
   sc.lwb = lwb_lo + 1;

@@ -86,6 +86,7 @@ k_pull_rows(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowi
       st->k1_ticket = 0u;
       st->maxdeg = 0;
       st->sumdeg2 = 0ull;
+      st->maskcnt = 0;
     }
     const int nt1 = (st->f + K1_TILE - 1) / K1_TILE;
     for (int i = tid; i < nt1; i += PULL_THREADS) ws.k1_status[i] = 0ull;

@@ -75,7 +75,7 @@ struct DevState {
   int32_t level;       // BFS level being discovered
   uint32_t pull_ticket;  // dynamic row-tile counter of the pull kernel
   int32_t nvisited;    // BFS: vertices reached so far
-  int32_t pad0;
+  int32_t maskcnt;     // rows with their mask bit set (selector feature)
   int32_t* bfs_level;  // BFS outputs of the current search
   int32_t* bfs_parent;
 };
@@ -115,6 +115,7 @@ struct Matrix {
 };
 
 struct Sched {
+  int id;    // schedule id: dir * 6 + quantum * 3 + width
   int dir;   // 0 push, 1 pull
   int q;     // QF or 2*QF
   int lwb;   // log2 bucket width
@@ -123,9 +124,10 @@ struct Sched {
 // Launchers (kernels.cu).  All launches are asynchronous on `s`.
 cudaError_t launch_k1(int sem, const Matrix& A, const Workspace& ws, int nb_fine,
                       const int32_t* x_idx, const uint32_t* x_val, int f, const int32_t* f_dev,
-                      int grid, const Sched* forced, cudaStream_t s);
+                      int grid, const Sched* forced, cudaStream_t s, const uint32_t* mask = nullptr);
 cudaError_t launch_k1_bfs(const Matrix& A, const Workspace& ws, int nb_fine, const int32_t* x_idx,
-                          const int32_t* f_dev, int grid, const Sched* sc, cudaStream_t s);
+                          const int32_t* f_dev, int grid, const Sched* sc, cudaStream_t s,
+                          const uint32_t* mask);
 cudaError_t launch_row_degrees(const Matrix& A, int32_t* deg, int32_t* maxdeg, cudaStream_t s);
 cudaError_t launch_rows_unsorted(const Matrix& A, int32_t* unsorted, cudaStream_t s);
 cudaError_t launch_relabel_hubs(const Matrix& A, const int32_t* hub_of_row, int32_t* out,

@@ -50,6 +50,9 @@ SPMSPV_STAGE_MERGE = 3
 SPMSPV_STAGE_PULL = 4
 SPMSPV_NUM_STAGES = 5
 
+SPMSPV_WITH_FEATURES = 16
+SPMSPV_SELECTOR_NPARAM = 1688
+
 SPMSPV_DEV_CAPACITY = 1
 SPMSPV_DEV_TIMEOUT = 2
 SPMSPV_DEV_INDEX = 4
@@ -95,6 +98,13 @@ def load(build_if_missing: bool = True):
                                            _P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int32,
                                            _P, ctypes.c_uint32, _P, _P, ctypes.c_int32, _P, _P]
         lib.spmspv_bfs.argtypes = [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_uint32, _P]
+        lib.spmspv_selector_set.argtypes = [_P, _P, ctypes.c_int32]
+        lib.spmspv_selector_get.argtypes = [_P, _P, ctypes.c_int32]
+        lib.spmspv_last_features.argtypes = [_P, _P]
+        lib.spmspv_last_schedule.argtypes = [_P, ctypes.POINTER(ctypes.c_int32)]
+        lib.spmspv_selector_train.argtypes = [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, _P]
+        lib.spmspv_selector_grad.argtypes = [_P, _P, _P, _P, ctypes.c_int32, _P, _P]
         lib.spmspv_profile_begin.argtypes = [_P]
         lib.spmspv_profile_end.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_int32)]
@@ -161,6 +171,51 @@ def spmspv_bfs(h, src, level, parent, d_nlevels, opts=0, stream=None):
                              _stream(stream)), "spmspv_bfs")
 
 
+def spmspv_selector_set(h, params):
+    import numpy as np
+    arr = np.ascontiguousarray(params, dtype=np.float32)
+    _check(load().spmspv_selector_set(h, arr.ctypes.data, int(arr.size)), "spmspv_selector_set")
+
+
+def spmspv_selector_get(h):
+    import numpy as np
+    arr = np.empty(SPMSPV_SELECTOR_NPARAM, dtype=np.float32)
+    _check(load().spmspv_selector_get(h, arr.ctypes.data, int(arr.size)), "spmspv_selector_get")
+    return arr
+
+
+def spmspv_last_features(h):
+    import numpy as np
+    arr = np.empty(6, dtype=np.float32)
+    _check(load().spmspv_last_features(h, arr.ctypes.data), "spmspv_last_features")
+    return arr
+
+
+def spmspv_last_schedule(h) -> int:
+    v = ctypes.c_int32(0)
+    _check(load().spmspv_last_schedule(h, ctypes.byref(v)), "spmspv_last_schedule")
+    return int(v.value)
+
+
+def spmspv_selector_train(h, feats, target, valid, n, epochs, batch, lr, seed):
+    """feats/target/valid: CUDA tensors.  Returns the per-epoch mean loss."""
+    import numpy as np
+    loss = np.zeros(max(int(epochs), 1), dtype=np.float32)
+    _check(load().spmspv_selector_train(h, _ptr(feats), _ptr(target), _ptr(valid), int(n),
+                                        int(epochs), int(batch), float(lr), int(seed),
+                                        loss.ctypes.data), "spmspv_selector_train")
+    return loss[:int(epochs)]
+
+
+def spmspv_selector_grad(h, feats, target, valid, n):
+    import numpy as np
+    g = np.zeros(1676, dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    _check(load().spmspv_selector_grad(h, _ptr(feats), _ptr(target), _ptr(valid), int(n),
+                                       g.ctypes.data, loss.ctypes.data), "spmspv_selector_grad")
+    return g, float(loss[0])
+
+
 def spmspv_device_status(h) -> int:
     v = ctypes.c_uint32(0)
     _check(load().spmspv_device_status(h, ctypes.byref(v)), "spmspv_device_status")
@@ -196,6 +251,7 @@ class CscMatrix:
     def __init__(self, m, n, colptr, rowidx, val=None, flags=0, device="cuda"):
         dev = torch.device(device)
         self.m, self.n = int(m), int(n)
+        self.flags = int(flags)
         self.colptr = torch.as_tensor(colptr, dtype=torch.int32).to(dev).contiguous()
         self.rowidx = torch.as_tensor(rowidx, dtype=torch.int32).to(dev).contiguous()
         self.val = None if val is None else torch.as_tensor(val, dtype=torch.float32).to(dev).contiguous()

@@ -25,7 +25,7 @@ def lib():
 
 
 def _run(lib, A, Ad, semiring, x_idx, x_val, mask_u8=None, complement=True, sched=None,
-         cap=None):
+         cap=None, auto=False):
     torch, S = lib
     dev = "cuda"
     xi = torch.from_numpy(np.ascontiguousarray(x_idx, np.int32)).to(dev)
@@ -40,6 +40,8 @@ def _run(lib, A, Ad, semiring, x_idx, x_val, mask_u8=None, complement=True, sche
             opts |= S.SPMSPV_MASK_COMPLEMENT
     if sched is not None:
         opts |= S.SPMSPV_SCHED_OPT(sched)
+    if auto:
+        opts |= S.SPMSPV_SCHED_AUTO
     yi, yv, k = Ad.multiply(semiring, xi, xv, mask, opts, y_capacity=cap)
     st = S.spmspv_device_status(Ad.handle)
     return (yi.cpu().numpy(), None if yv is None else yv.cpu().numpy(), k, st)
