@@ -514,6 +514,8 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __res
   if (blockIdx.x == 0 && tid == 0) {
     // clear K1's per-call state for the next call
     st->k1_ticket = 0u;
+    st->last_maxdeg = st->maxdeg;
+    st->last_maskcnt = st->maskcnt;
     st->maxdeg = 0;
     st->sumdeg2 = 0ull;
     st->maskcnt = 0;

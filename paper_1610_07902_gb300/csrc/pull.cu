@@ -84,6 +84,8 @@ k_pull_rows(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowi
     // this kernel ends the call: clear the work scan's per-call state
     if (tid == 0) {
       st->k1_ticket = 0u;
+      st->last_maxdeg = st->maxdeg;
+      st->last_maskcnt = st->maskcnt;
       st->maxdeg = 0;
       st->sumdeg2 = 0ull;
       st->maskcnt = 0;

@@ -254,8 +254,8 @@ extern "C" int spmspv_last_features(spmspv_handle* h, float* feats) {
   const double f = st.f, W = st.W, fc = st.fc > 0 ? st.fc : 1;
   feats[0] = (float)std::log2(1.0 + f);
   feats[1] = (float)std::log2(1.0 + W);
-  feats[2] = W > 0 ? (float)(st.maxdeg * fc / W) : 0.f;
-  feats[3] = (float)st.maskcnt / (float)h->A.m;
+  feats[2] = W > 0 ? (float)(st.last_maxdeg * fc / W) : 0.f;
+  feats[3] = (float)st.last_maskcnt / (float)h->A.m;
   feats[4] = (float)std::log2((double)h->A.m);
   feats[5] = (float)((double)h->A.nnz / (double)h->A.n);
   return SPMSPV_OK;

@@ -76,6 +76,8 @@ struct DevState {
   uint32_t pull_ticket;  // dynamic row-tile counter of the pull kernel
   int32_t nvisited;    // BFS: vertices reached so far
   int32_t maskcnt;     // rows with their mask bit set (selector feature)
+  int32_t last_maxdeg;   // maxdeg and maskcnt of the last finished call
+  int32_t last_maskcnt;
   int32_t* bfs_level;  // BFS outputs of the current search
   int32_t* bfs_parent;
 };
