@@ -169,6 +169,46 @@ int spmspv_run(spmspv_handle* h, int semiring, const int32_t* x_idx, const void*
 int spmspv_bfs(spmspv_handle* h, int32_t src, int32_t* level, int32_t* parent,
                int32_t* d_nlevels, uint32_t opts, spmspv_stream_t stream);
 
+/*
+ * Batched form: B independent products y_b <- A (+).(x) x_b [under mask_b] in
+ * one graph launch (no counterpart in the paper; its Sec. I and III-A note that
+ * repeated small products are dominated by overhead).  The batch runs as
+ * `lanes` concurrent device-side loops that each take the next frontier from a
+ * shared queue and run the three kernels of spmspv_run on it with their own
+ * workspace; every y_b equals what spmspv_run gives for x_b with the same
+ * (push) schedule.  All arrays are device arrays:
+ *   x_off[B], x_cnt[B]   frontier b is x_idx[x_off[b] .. x_off[b]+x_cnt[b]) and the
+ *                        same slice of x_val (ignored for OR_AND_BOOL).
+ *   masks, mask_stride   NULL, or frontier b's complemented mask at
+ *                        masks + b*mask_stride (uint32 words, stride >= ceil(m/32));
+ *                        opts must then contain SPMSPV_MASK_COMPLEMENT.
+ *   y_off[B], y_cap[B]   y_b goes to y_idx/y_val[y_off[b] ..], at most y_cap[b]
+ *                        entries (ascending indices); d_nnz_y[b] receives nnz(y_b)
+ *                        (the size needed when it exceeds y_cap[b]).
+ *   opts                 SPMSPV_SCHED_OPT(s) (pull schedules run as their push
+ *                        form), SPMSPV_MASK_COMPLEMENT.
+ *   lanes                1..16.  Lane workspaces (one per lane, as for a
+ *                        handle) and the graph are created on first use.
+ */
+int spmspv_run_batched(spmspv_handle* h, int semiring, int32_t B, const int32_t* x_off,
+                       const int32_t* x_cnt, const int32_t* x_idx, const void* x_val,
+                       const uint32_t* masks, int64_t mask_stride, uint32_t opts,
+                       const int32_t* y_off, const int32_t* y_cap, int32_t* y_idx, void* y_val,
+                       int32_t* d_nnz_y, int32_t lanes, spmspv_stream_t stream);
+
+/*
+ * Multi-source BFS: B searches (the BFS of spmspv_bfs from each of sources[B],
+ * device array) advanced together, one batched step per level.
+ *   level, parent  device int32[B][n] out (row b = search from sources[b]).
+ *   nlevels        device int32 out (may be NULL): levels of the deepest search.
+ *   opts, lanes    as for spmspv_run_batched (schedule, 1..16 lanes).
+ * Allocates B*(4n + n/8) bytes of frontiers and visited bitmaps for the call;
+ * synchronises the stream once per level to test for termination.
+ */
+int spmspv_msbfs(spmspv_handle* h, int32_t B, const int32_t* sources, int32_t* level,
+                 int32_t* parent, int32_t* nlevels, uint32_t opts, int32_t lanes,
+                 spmspv_stream_t stream);
+
 /* ---- learned schedule selector ----
  * No counterpart in the paper, which leaves open when to switch between the
  * vector-driven (push) and matrix-driven (pull) forms (Sec. V).  A 6->32->32->12

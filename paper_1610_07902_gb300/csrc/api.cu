@@ -446,6 +446,7 @@ int spmspv_destroy(spmspv_handle* h) {
     spmspv_profile_end(h, tmp, SPMSPV_NUM_STAGES, nullptr);
   }
   release_bfs_graphs(h);
+  release_batch(h);
   release_extras(h);
   cudaFree(h->rowidx_k2);
   cudaFree(h->sel_w);

@@ -1,0 +1,459 @@
+// Batched SpMSpV: B independent products y_b <- A (+).(x) x_b in one graph
+// launch.  The paper runs one product per call; repeated small calls are
+// where it notes most time goes to overhead (Sec. I, Sec. III-A), so the
+// batch is run as L concurrent "lanes": each lane is a device-side WHILE
+// loop (a conditional graph node) that pops the next frontier from a queue
+// shared by the lanes and runs the same three kernels (work scan ->
+// expand/scatter -> bucket merge) on it with its own workspace.  No frontier
+// waits for the host, the lanes keep the GPU busy while small frontiers leave
+// most of it idle, and every frontier gets exactly the result of a single
+// spmspv_run call with the same schedule.
+//
+// The graph is built once per (semiring, lanes, schedule, mode) and reused;
+// the per-call arrays reach the kernels through a device batch descriptor
+// and one job descriptor per lane.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "handle.cuh"
+#include "spmspv_internal.cuh"
+
+namespace spmspv {
+
+struct BatchDesc {
+  int32_t B;
+  int32_t head;  // queue head (atomic)
+  int32_t lvl;   // BFS mode: level being discovered
+  int32_t dummy_nnz;
+  const int32_t* x_off;
+  const int32_t* x_cnt;
+  const int32_t* x_idx;
+  const uint32_t* x_val;
+  const uint32_t* masks;
+  int64_t mask_stride;
+  const int32_t* y_off;
+  const int32_t* y_cap;
+  int32_t* y_idx;
+  uint32_t* y_val;
+  int32_t* d_nnz_y;
+  int32_t* level;   // BFS mode: [B][n]
+  int32_t* parent;  // BFS mode: [B][n]
+  int64_t vstride;  // n
+};
+
+struct BatchState {
+  int lanes;
+  spmspv_handle* sub[MAX_LANES];  // one workspace per lane
+  Job* jobs;                      // [MAX_LANES] device
+  BatchDesc* desc;                // device
+  cudaGraphExec_t graphs[3][SPMSPV_NUM_SCHEDULES][2][MAX_LANES + 1];
+};
+
+namespace {
+
+__global__ void k_batch_start(BatchDesc* d, BatchDesc v) {
+  if (threadIdx.x == 0) {
+    v.head = 0;
+    v.dummy_nnz = 0;
+    v.lvl = d->lvl;
+    *d = v;
+  }
+}
+
+__global__ void k_batch_set_level(BatchDesc* d, int32_t lvl) {
+  if (threadIdx.x == 0) d->lvl = lvl;
+}
+
+// Lane step 1: take the next frontier (or an empty job when none is left).
+__global__ void k_batch_pop(BatchDesc* d, Job* job) {
+  if (threadIdx.x != 0) return;
+  const int32_t t = atomicAdd(&d->head, 1);
+  Job j;
+  memset(&j, 0, sizeof(j));
+  j.b = -1;
+  j.d_nnz_y = &d->dummy_nnz;
+  j.x_idx = d->x_idx;
+  if (t < d->B) {
+    const int32_t b = t;
+    const int32_t xo = d->x_off[b];
+    j.b = b;
+    j.f = d->x_cnt[b];
+    j.x_idx = d->x_idx + xo;
+    j.x_val = d->x_val ? d->x_val + xo : nullptr;
+    j.mask = d->masks ? d->masks + (int64_t)b * d->mask_stride : nullptr;
+    j.y_idx = d->y_idx + d->y_off[b];
+    j.y_val = d->y_val ? d->y_val + d->y_off[b] : nullptr;
+    j.y_cap = d->y_cap[b];
+    j.d_nnz_y = d->d_nnz_y + b;
+    if (d->level) {
+      j.level = d->level + (int64_t)b * d->vstride;
+      j.parent = d->parent + (int64_t)b * d->vstride;
+      j.visited = const_cast<uint32_t*>(j.mask);
+      j.lvl = d->lvl;
+    }
+  }
+  *job = j;
+}
+
+// Lane step 4: another round while frontiers are left in the queue.
+__global__ void k_batch_continue(cudaGraphConditionalHandle cond, const BatchDesc* d) {
+  if (threadIdx.x == 0) {
+    const int32_t head = *(volatile const int32_t*)&d->head;
+    cudaGraphSetConditional(cond, head < d->B ? 1u : 0u);
+  }
+}
+
+}  // namespace
+
+static int lane_launches(spmspv_handle* sub, BatchState* bs, int lane, int sem, bool bfs,
+                         const Sched& sc, cudaGraphConditionalHandle cond, cudaStream_t s) {
+  k_batch_pop<<<1, 32, 0, s>>>(bs->desc, bs->jobs + lane);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "batch pop");
+  const int k1_grid = sub->sm_count;
+  if (bfs)
+    e = launch_k1_bfs(sub->A, sub->ws, sub->nb_fine, nullptr, nullptr, k1_grid, &sc, s, nullptr);
+  else
+    e = launch_k1(sem, sub->A, sub->ws, sub->nb_fine, nullptr, nullptr, 0, nullptr, k1_grid, &sc, s,
+                  nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "batch work scan");
+  e = launch_k2(bfs ? kMinSelect2nd : sem, sub->A, sub->ws, sub->lwb_lo, sub->nb_fine, nullptr,
+                1, sub->k2_grid, sub->k2_smem, s, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "batch expand/scatter");
+  const size_t k3_smem = k3_smem_bytes(sc.lwb);
+  const int nb = (int)(((int64_t)sub->A.m + (1 << sc.lwb) - 1) >> sc.lwb);
+  const int k3_grid = std::max(1, std::min(nb, sub->sm_count * sub->k3_bps[sc.lwb - sub->lwb_lo]));
+  e = launch_k3(bfs ? kMinSelect2nd : sem, bfs, sub->A, sub->ws, sub->lwb_lo, sub->nb_fine, nullptr,
+                nullptr, 0, nullptr, nullptr, k3_grid, k3_smem, s, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "batch merge");
+  k_batch_continue<<<1, 32, 0, s>>>(cond, bs->desc);
+  return (e = cudaGetLastError()) == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "batch condition");
+}
+
+static int build_batch_graph(BatchState* bs, int sem, bool bfs, const Sched& sc, int lanes,
+                             cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
+  int rc = SPMSPV_OK;
+  if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) rc = cuda_fail(e, "stream");
+  for (int l = 0; l < lanes && rc == SPMSPV_OK; ++l) {
+    cudaGraphConditionalHandle cond;
+    if ((e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess) {
+      rc = cuda_fail(e, "lane handle");
+      break;
+    }
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np)) != cudaSuccess) {
+      rc = cuda_fail(e, "lane node");
+      break;
+    }
+    if ((e = cudaStreamBeginCaptureToGraph(cs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+      rc = cuda_fail(e, "lane capture");
+      break;
+    }
+    rc = lane_launches(bs->sub[l], bs, l, sem, bfs, sc, cond, cs);
+    cudaGraph_t tmp = nullptr;
+    e = cudaStreamEndCapture(cs, &tmp);
+    if (rc == SPMSPV_OK && e != cudaSuccess) rc = cuda_fail(e, "lane capture end");
+  }
+  if (rc == SPMSPV_OK && (e = cudaGraphInstantiate(&exec, g, 0)) != cudaSuccess)
+    rc = cuda_fail(e, "instantiate batch graph");
+  if (cs) cudaStreamDestroy(cs);
+  cudaGraphDestroy(g);
+  if (rc != SPMSPV_OK) {
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGetLastError();
+    return rc;
+  }
+  *out = exec;
+  return SPMSPV_OK;
+}
+
+static int ensure_batch(spmspv_handle* h, int lanes, BatchState** out) {
+  BatchState* bs = (BatchState*)h->batch;
+  if (!bs) {
+    bs = new BatchState();
+    memset(bs, 0, sizeof(*bs));
+    cudaError_t e = cudaMalloc(&bs->jobs, sizeof(Job) * MAX_LANES);
+    if (e == cudaSuccess) e = cudaMalloc(&bs->desc, sizeof(BatchDesc));
+    if (e == cudaSuccess) e = cudaMemset(bs->desc, 0, sizeof(BatchDesc));
+    if (e != cudaSuccess) {
+      cudaFree(bs->jobs);
+      cudaFree(bs->desc);
+      delete bs;
+      return fail(SPMSPV_ERR_OOM, "batch descriptors: %s", cudaGetErrorString(e));
+    }
+    h->batch = bs;
+  }
+  // one full workspace per lane, created like the parent handle
+  for (int l = bs->lanes; l < lanes; ++l) {
+    spmspv_handle* sub = nullptr;
+    int rc = spmspv_create_csc(&sub, h->A.m, h->A.n, h->A.nnz, h->A.colptr, h->A.rowidx, h->A.val,
+                               h->A.val ? SPMSPV_VAL_F32 : SPMSPV_VAL_NONE, h->flags & ~SPMSPV_CSC_PATTERN_SYMMETRIC);
+    if (rc != SPMSPV_OK) return rc;
+    sub->ws.job = bs->jobs + l;
+    bs->sub[l] = sub;
+    bs->lanes = l + 1;
+  }
+  *out = bs;
+  return SPMSPV_OK;
+}
+
+void release_batch(spmspv_handle* h) {
+  BatchState* bs = (BatchState*)h->batch;
+  if (!bs) return;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < SPMSPV_NUM_SCHEDULES; ++b)
+      for (int c = 0; c < 2; ++c)
+        for (int d = 0; d <= MAX_LANES; ++d)
+          if (bs->graphs[a][b][c][d]) cudaGraphExecDestroy(bs->graphs[a][b][c][d]);
+  for (int l = 0; l < bs->lanes; ++l) spmspv_destroy(bs->sub[l]);
+  cudaFree(bs->jobs);
+  cudaFree(bs->desc);
+  delete bs;
+  h->batch = nullptr;
+}
+
+int run_batched(spmspv_handle* h, int sem, bool bfs, int32_t B, const BatchDesc& v, uint32_t opts,
+                int32_t lanes, cudaStream_t s);
+int batch_set_level(spmspv_handle* h, int32_t lvl, cudaStream_t s);
+int ensure_batch_state(spmspv_handle* h, int lanes);
+
+int run_batched(spmspv_handle* h, int sem, bool bfs, int32_t B, const BatchDesc& v, uint32_t opts,
+                int32_t lanes, cudaStream_t s) {
+  if (lanes < 1 || lanes > MAX_LANES) return fail(SPMSPV_ERR_ARG, "lanes must be in [1, %d]", MAX_LANES);
+  int sid = h->default_sched;
+  if (opts & SPMSPV_SCHED_FORCE) sid = (int)SPMSPV_SCHED_ID(opts);
+  if (sid >= 6) sid -= 6;  // the lanes run the push form
+  BatchState* bs = nullptr;
+  int rc = ensure_batch(h, lanes, &bs);
+  if (rc) return rc;
+  const Sched sc = decode_schedule(h, sid);
+  cudaGraphExec_t& g = bs->graphs[bfs ? 1 : sem][sid][bfs ? 1 : 0][lanes];
+  if (!g) {
+    if ((rc = build_batch_graph(bs, bfs ? kMinSelect2nd : sem, bfs, sc, lanes, &g)) != SPMSPV_OK) return rc;
+  }
+  k_batch_start<<<1, 32, 0, s>>>(bs->desc, v);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "batch start");
+  if ((e = cudaGraphLaunch(g, s)) != cudaSuccess) return cuda_fail(e, "batch graph launch");
+  h->last_stream = s;
+  return SPMSPV_OK;
+}
+
+int batch_set_level(spmspv_handle* h, int32_t lvl, cudaStream_t s) {
+  BatchState* bs = (BatchState*)h->batch;
+  k_batch_set_level<<<1, 32, 0, s>>>(bs->desc, lvl);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "batch level");
+}
+
+int ensure_batch_state(spmspv_handle* h, int lanes) {
+  BatchState* bs = nullptr;
+  return ensure_batch(h, lanes, &bs);
+}
+
+}  // namespace spmspv
+
+using namespace spmspv;
+
+extern "C" int spmspv_run_batched(spmspv_handle* h, int semiring, int32_t B, const int32_t* x_off,
+                                  const int32_t* x_cnt, const int32_t* x_idx, const void* x_val,
+                                  const uint32_t* masks, int64_t mask_stride, uint32_t opts,
+                                  const int32_t* y_off, const int32_t* y_cap, int32_t* y_idx,
+                                  void* y_val, int32_t* d_nnz_y, int32_t lanes,
+                                  spmspv_stream_t stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (semiring < 0 || semiring > 2) return fail(SPMSPV_ERR_ARG, "unknown semiring %d", semiring);
+  if (B < 0) return fail(SPMSPV_ERR_ARG, "B < 0");
+  if (B == 0) return SPMSPV_OK;
+  if (!x_off || !x_cnt || !x_idx || !y_off || !y_cap || !y_idx || !d_nnz_y)
+    return fail(SPMSPV_ERR_ARG, "NULL batch array");
+  if (semiring != SPMSPV_OR_AND_BOOL && (!x_val || !y_val)) return fail(SPMSPV_ERR_ARG, "x_val/y_val NULL");
+  if (masks && mask_stride < ((int64_t)h->A.m + 31) / 32) return fail(SPMSPV_ERR_ARG, "mask_stride too small");
+  BatchDesc v;
+  memset(&v, 0, sizeof(v));
+  v.B = B;
+  v.x_off = x_off;
+  v.x_cnt = x_cnt;
+  v.x_idx = x_idx;
+  v.x_val = (const uint32_t*)x_val;
+  v.masks = masks;
+  v.mask_stride = mask_stride;
+  v.y_off = y_off;
+  v.y_cap = y_cap;
+  v.y_idx = y_idx;
+  v.y_val = (uint32_t*)y_val;
+  v.d_nnz_y = d_nnz_y;
+  (void)(opts & SPMSPV_MASK_COMPLEMENT);
+  if (masks && !(opts & SPMSPV_MASK_COMPLEMENT))
+    return fail(SPMSPV_ERR_UNSUPPORTED, "batched masks are complemented masks");
+  return run_batched(h, semiring, false, B, v, opts, lanes, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// Multi-source BFS: one batched (min, select2nd) step per level, every source
+// with its own frontier, visited bitmap and outputs.
+// ---------------------------------------------------------------------------
+namespace spmspv {
+namespace {
+
+__global__ void k_msbfs_init(int32_t B, int32_t n, const int32_t* __restrict__ sources,
+                             int32_t* __restrict__ level, int32_t* __restrict__ parent,
+                             uint32_t* __restrict__ visited, int64_t vwords,
+                             int32_t* __restrict__ fronts, int32_t* __restrict__ x_off,
+                             int32_t* __restrict__ x_cnt, int32_t* __restrict__ y_off,
+                             int32_t* __restrict__ y_cap) {
+  const int64_t total = (int64_t)B * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    level[i] = -1;
+    parent[i] = -1;
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)B * vwords;
+       i += (int64_t)gridDim.x * blockDim.x)
+    visited[i] = 0u;
+}
+
+__global__ void k_msbfs_seed(int32_t B, int32_t n, const int32_t* __restrict__ sources,
+                             int32_t* __restrict__ level, int32_t* __restrict__ parent,
+                             uint32_t* __restrict__ visited, int64_t vwords,
+                             int32_t* __restrict__ fronts, int32_t* __restrict__ x_off,
+                             int32_t* __restrict__ x_cnt, int32_t* __restrict__ y_off,
+                             int32_t* __restrict__ y_cap, int32_t* __restrict__ status) {
+  for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    const int32_t s = sources[b];
+    x_off[b] = (int32_t)0;
+    y_off[b] = 0;
+    y_cap[b] = n;
+    x_cnt[b] = 0;
+    if (s < 0 || s >= n) {
+      atomicOr(status, 1);
+      continue;
+    }
+    level[(int64_t)b * n + s] = 0;
+    parent[(int64_t)b * n + s] = s;
+    visited[(int64_t)b * vwords + (s >> 5)] |= 1u << (s & 31);
+    fronts[(int64_t)b * n] = s;
+    x_cnt[b] = 1;
+  }
+}
+
+__global__ void k_msbfs_next(int32_t B, const int32_t* __restrict__ nnz, int32_t* __restrict__ x_cnt,
+                             int32_t* __restrict__ total) {
+  int32_t t = 0;
+  for (int32_t b = threadIdx.x; b < B; b += blockDim.x) {
+    x_cnt[b] = nnz[b];
+    t += nnz[b];
+  }
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(total, t);
+}
+
+}  // namespace
+}  // namespace spmspv
+
+extern "C" int spmspv_msbfs(spmspv_handle* h, int32_t B, const int32_t* sources, int32_t* level,
+                            int32_t* parent, int32_t* nlevels, uint32_t opts, int32_t lanes,
+                            spmspv_stream_t stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (h->A.m != h->A.n) return fail(SPMSPV_ERR_ARG, "BFS needs a square matrix");
+  if (B < 1 || !sources || !level || !parent) return fail(SPMSPV_ERR_ARG, "bad multi-source BFS arguments");
+  if (B > (int32_t)(((int64_t)1 << 31) / h->A.n))
+    return fail(SPMSPV_ERR_UNSUPPORTED, "B * n must stay below 2^31");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int32_t n = h->A.n;
+  const int64_t vwords = ((int64_t)n + 31) / 32;
+  // per-source frontiers, visited bitmaps and batch arrays (freed on return)
+  int32_t *fronts = nullptr, *arr = nullptr;
+  uint32_t* visited = nullptr;
+  cudaError_t e = cudaMalloc(&fronts, sizeof(int32_t) * (size_t)B * n);
+  if (e == cudaSuccess) e = cudaMalloc(&visited, sizeof(uint32_t) * (size_t)B * vwords);
+  if (e == cudaSuccess) e = cudaMalloc(&arr, sizeof(int32_t) * ((size_t)B * 6 + 8));
+  if (e != cudaSuccess) {
+    cudaFree(fronts);
+    cudaFree(visited);
+    cudaFree(arr);
+    cudaGetLastError();
+    return fail(SPMSPV_ERR_OOM, "multi-source BFS buffers: %s", cudaGetErrorString(e));
+  }
+  int32_t* x_off = arr;
+  int32_t* x_cnt = arr + B;
+  int32_t* y_off = arr + 2 * B;
+  int32_t* y_cap = arr + 3 * B;
+  int32_t* nnz = arr + 4 * B;
+  int32_t* misc = arr + 6 * B;  // [0] status, [1] frontier total
+  // frontier b lives at fronts + b*n: express the offsets relative to fronts
+  cudaMemsetAsync(misc, 0, sizeof(int32_t) * 8, s);
+  const int grid = h->sm_count * 4;
+  k_msbfs_init<<<grid, 256, 0, s>>>(B, n, sources, level, parent, visited, vwords, fronts, x_off,
+                                    x_cnt, y_off, y_cap);
+  k_msbfs_seed<<<(B + 255) / 256, 256, 0, s>>>(B, n, sources, level, parent, visited, vwords, fronts,
+                                               x_off, x_cnt, y_off, y_cap, misc);
+  // offsets: frontier b starts at b*n
+  {
+    std::vector<int32_t> off(B);
+    for (int32_t b = 0; b < B; ++b) off[b] = b * n;
+    cudaMemcpyAsync(x_off, off.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(y_off, off.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+  }
+  BatchDesc v;
+  memset(&v, 0, sizeof(v));
+  v.B = B;
+  v.x_off = x_off;
+  v.x_cnt = x_cnt;
+  v.x_idx = fronts;
+  v.masks = visited;
+  v.mask_stride = vwords;
+  v.y_off = y_off;
+  v.y_cap = y_cap;
+  v.y_idx = fronts;
+  v.d_nnz_y = nnz;
+  v.level = level;
+  v.parent = parent;
+  v.vstride = n;
+  int32_t L = 0;
+  rc = SPMSPV_OK;
+  if ((rc = ensure_batch_state(h, lanes)) == SPMSPV_OK) {
+    for (L = 1; L <= n; ++L) {
+      if ((rc = batch_set_level(h, L, s)) != SPMSPV_OK) break;
+      if ((rc = run_batched(h, kMinSelect2nd, true, B, v, opts, lanes, s)) != SPMSPV_OK) break;
+      cudaMemsetAsync(misc + 1, 0, sizeof(int32_t), s);
+      k_msbfs_next<<<1, 1024, 0, s>>>(B, nnz, x_cnt, misc + 1);
+      int32_t total = 0;
+      e = cudaMemcpyAsync(&total, misc + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        rc = cuda_fail(e, "multi-source BFS level");
+        break;
+      }
+      if (total == 0) break;
+    }
+  }
+  if (rc == SPMSPV_OK && nlevels) {
+    e = cudaMemcpyAsync(nlevels, &L, sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "level count");
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(fronts);
+  cudaFree(visited);
+  cudaFree(arr);
+  return rc;
+}

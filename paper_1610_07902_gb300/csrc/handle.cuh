@@ -7,6 +7,7 @@
 #include "spmspv_internal.cuh"
 
 constexpr uint32_t kHandleMagic = 0x53704d53u;
+constexpr int MAX_LANES = 16;  // concurrent lanes of the batched form
 
 struct spmspv_handle {
   uint32_t magic;
@@ -35,6 +36,7 @@ struct spmspv_handle {
   // learned schedule selector
   int sel_ready;        // weights present
   float* sel_w;         // device weights (layout in selector.cu)
+  void* batch;          // BatchState* of the batched form (batched.cu), lazily created
   // pull direction (dense frontier) buffers, allocated on first use
   uint32_t* xbits;      // [ceil(n/32)] frontier bitmap
   uint32_t* xdense;     // [n] frontier values
@@ -62,6 +64,7 @@ int run_pull_if_available(spmspv_handle* h, int sem, const int32_t* x_idx, const
                           cudaStream_t s);
 void release_extras(spmspv_handle* h);
 void release_bfs_graphs(spmspv_handle* h);
+void release_batch(spmspv_handle* h);
 cudaError_t alloc_pull_buffers(spmspv_handle* h);
 int ensure_bfs_buffers(spmspv_handle* h);
 // Per-stage event recording (no-ops unless spmspv_profile_begin was called).

@@ -43,8 +43,8 @@ constexpr unsigned long long K1_CNT_ONE = 1ull << 31;
 constexpr unsigned long long K1_SUM_MASK = (1ull << 31) - 1;
 
 __global__ void __launch_bounds__(K1_THREADS)
-k1_work_scan(const int32_t* __restrict__ x_idx, const uint32_t* __restrict__ x_val, int f_host,
-             const int32_t* __restrict__ f_dev, const int32_t* __restrict__ colptr, int32_t n,
+k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int32_t* f_dev,
+             const int32_t* __restrict__ colptr, int32_t n,
              int64_t nnz, Workspace ws, int nb_fine, int sem, int forced, int f_dir, int f_q,
              int f_lwb, int bfs_level_inc, const uint32_t* __restrict__ mask, int32_t m) {
   __shared__ int32_t s_deg[K1_SMEM_WORDS];
@@ -58,6 +58,12 @@ k1_work_scan(const int32_t* __restrict__ x_idx, const uint32_t* __restrict__ x_v
 
   DevState* st = ws.st;
   const int tid = threadIdx.x;
+  if (ws.job) {  // a batched lane: this frontier's x
+    x_idx = ws.job->x_idx;
+    x_val = bfs_level_inc ? reinterpret_cast<const uint32_t*>(ws.job->x_idx) : ws.job->x_val;
+    f_dev = &ws.job->f;
+    bfs_level_inc = 0;
+  }
   const int f = f_dev ? *f_dev : f_host;
   const uint32_t nt1 = (uint32_t)((f + K1_TILE - 1) / K1_TILE);
 
@@ -82,7 +88,7 @@ k1_work_scan(const int32_t* __restrict__ x_idx, const uint32_t* __restrict__ x_v
         st->sched = forced - 1;
       }
       if (bfs_level_inc) st->level += 1;
-      else st->bfs_level = nullptr;  // not a BFS level
+      else if (!ws.job) st->bfs_level = nullptr;  // not a BFS level
       if (f == 0) {
         st->fc = 0;
         st->W = 0;
@@ -258,9 +264,10 @@ __device__ __forceinline__ void spa_apply(uint32_t* spa, uint32_t r, uint32_t v)
 template <int SEM>
 __global__ void __launch_bounds__(K2_THREADS, 2)
 k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ val, Workspace ws,
-                  int lwb_lo, int nb_fine, int32_t m, int64_t nnz, const uint32_t* __restrict__ mask,
+                  int lwb_lo, int nb_fine, int32_t m, int64_t nnz, const uint32_t* mask,
                   int mask_comp, int only_push) {
   if (only_push && ws.st->dir != 0) return;  // this call runs the pull direction
+  if (ws.job) mask = ws.job->mask;
   extern __shared__ __align__(16) unsigned char k2_smem_raw[];
   __shared__ int32_t s_kept;
 
@@ -484,10 +491,16 @@ cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo,
 // ------------------------------------------------------------------------
 template <int SEM, bool BFS>
 __global__ void __launch_bounds__(K3_THREADS)
-k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __restrict__ y_idx,
-                uint32_t* __restrict__ y_val, int32_t y_cap, int32_t* __restrict__ d_nnz_y,
-                uint32_t* __restrict__ mask_update, int only_push) {
+k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx, uint32_t* y_val,
+                int32_t y_cap, int32_t* d_nnz_y, uint32_t* mask_update, int only_push) {
   if (only_push && ws.st->dir != 0) return;  // this call runs the pull direction
+  if (ws.job) {  // a batched lane: this frontier's outputs
+    y_idx = ws.job->y_idx;
+    y_val = ws.job->y_val;
+    y_cap = ws.job->y_cap;
+    d_nnz_y = ws.job->d_nnz_y;
+    if (BFS) mask_update = ws.job->visited;
+  }
   extern __shared__ __align__(16) uint32_t k3_smem[];
   __shared__ int32_t s_scan[K3_THREADS / 32 + 1];
   __shared__ uint32_t s_b;
@@ -506,9 +519,9 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* __res
   uint32_t* occ = k3_smem + wb;
   const uint32_t ident = sr_identity<SEM>();
   const int wpt = nw > K3_THREADS ? nw / K3_THREADS : 1;
-  const int32_t lvl = BFS ? st->level : 0;
-  int32_t* const level = BFS ? st->bfs_level : nullptr;
-  int32_t* const parent = BFS ? st->bfs_parent : nullptr;
+  const int32_t lvl = BFS ? (ws.job ? ws.job->lvl : st->level) : 0;
+  int32_t* const level = BFS ? (ws.job ? ws.job->level : st->bfs_level) : nullptr;
+  int32_t* const parent = BFS ? (ws.job ? ws.job->parent : st->bfs_parent) : nullptr;
   const int nhot = ws.nhot;
 
   if (blockIdx.x == 0 && tid == 0) {

@@ -184,6 +184,8 @@ extern "C" int spmspv_run_noalloc(int32_t m, int32_t n, int64_t nnz, const int32
   ws.nhot = 0;
   ws.hot_rows = nullptr;
   ws.rowidx_k2 = nullptr;
+  ws.pull_status = nullptr;
+  ws.job = nullptr;
   ws.hot_start = nullptr;
   ws.hot_val = nullptr;
   ws.hot_touch = nullptr;

@@ -82,6 +82,24 @@ struct DevState {
   int32_t* bfs_parent;
 };
 
+// One frontier of a batch, as the batched lanes hand it to the kernels
+// (device memory; read at the start of K1, K2 and K3 when present).
+struct Job {
+  const int32_t* x_idx;
+  const uint32_t* x_val;
+  const uint32_t* mask;
+  int32_t* y_idx;
+  uint32_t* y_val;
+  int32_t* d_nnz_y;
+  int32_t* level;      // BFS mode: this source's outputs and visited bitmap
+  int32_t* parent;
+  uint32_t* visited;
+  int32_t f;
+  int32_t y_cap;
+  int32_t b;           // frontier index, -1 when the queue was empty
+  int32_t lvl;         // BFS mode: the level being discovered
+};
+
 struct Workspace {
   DevState* st;
   int32_t* cw;          // [n+1] exclusive work offsets of the compacted x entries
@@ -100,6 +118,7 @@ struct Workspace {
   const int32_t* hot_start;  // [nb_fine+1] first hot index of each fine bucket
   const int32_t* rowidx_k2;  // [nnz] row ids with hub row r replaced by m + its hub index
   unsigned long long* pull_status;  // [pull tiles] look-back words of the pull kernel
+  const Job* job;            // batched lanes: the current frontier (NULL otherwise)
   uint32_t* hot_val;         // [HOT_MAX] per-call sums of the hot rows
   uint32_t* hot_touch;       // [HOT_MAX] 1 when a hot row received a product this call
 };

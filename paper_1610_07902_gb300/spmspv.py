@@ -105,6 +105,11 @@ def load(build_if_missing: bool = True):
         lib.spmspv_selector_train.argtypes = [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, _P]
         lib.spmspv_selector_grad.argtypes = [_P, _P, _P, _P, ctypes.c_int32, _P, _P]
+        lib.spmspv_run_batched.argtypes = [_P, ctypes.c_int, ctypes.c_int32, _P, _P, _P, _P, _P,
+                                           ctypes.c_int64, ctypes.c_uint32, _P, _P, _P, _P, _P,
+                                           ctypes.c_int32, _P]
+        lib.spmspv_msbfs.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_uint32,
+                                     ctypes.c_int32, _P]
         lib.spmspv_profile_begin.argtypes = [_P]
         lib.spmspv_profile_end.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_int32)]
@@ -214,6 +219,20 @@ def spmspv_selector_grad(h, feats, target, valid, n):
     _check(load().spmspv_selector_grad(h, _ptr(feats), _ptr(target), _ptr(valid), int(n),
                                        g.ctypes.data, loss.ctypes.data), "spmspv_selector_grad")
     return g, float(loss[0])
+
+
+def spmspv_run_batched(h, semiring, B, x_off, x_cnt, x_idx, x_val, masks, mask_stride, opts,
+                       y_off, y_cap, y_idx, y_val, d_nnz_y, lanes=4, stream=None):
+    _check(load().spmspv_run_batched(h, int(semiring), int(B), _ptr(x_off), _ptr(x_cnt), _ptr(x_idx),
+                                     _ptr(x_val), _ptr(masks), int(mask_stride), int(opts),
+                                     _ptr(y_off), _ptr(y_cap), _ptr(y_idx), _ptr(y_val),
+                                     _ptr(d_nnz_y), int(lanes), _stream(stream)),
+           "spmspv_run_batched")
+
+
+def spmspv_msbfs(h, B, sources, level, parent, nlevels, opts=0, lanes=8, stream=None):
+    _check(load().spmspv_msbfs(h, int(B), _ptr(sources), _ptr(level), _ptr(parent), _ptr(nlevels),
+                               int(opts), int(lanes), _stream(stream)), "spmspv_msbfs")
 
 
 def spmspv_device_status(h) -> int:

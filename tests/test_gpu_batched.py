@@ -1,0 +1,89 @@
+"""Batched SpMSpV (concurrent lanes over a device-side frontier queue) and
+multi-source BFS against the oracle: every frontier's y must equal the
+single-product result (index sets and integer values bit for bit, FP32 values
+within the parity tolerance)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import SEMIRING_TO_ORACLE, compare, mask_bits, need_gpu, x_values
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = need_gpu()
+    from paper_1610_07902_gb300 import spmspv as S
+    S.load()
+    return torch, S
+
+
+def make_batch(n, B, seed, fmax):
+    rng = np.random.default_rng(seed)
+    sizes = np.maximum(1, np.floor(10 ** rng.uniform(0, np.log10(fmax), B))).astype(np.int64)
+    fronts = [synth.frontier(n, int(min(s, n)), seed=seed * 1000 + b) for b, s in enumerate(sizes)]
+    return fronts
+
+
+@pytest.mark.parametrize("lanes", [1, 3, 8])
+@pytest.mark.parametrize("masked", [False, True])
+def test_batched_matches_oracle(lib, lanes, masked):
+    torch, S = lib
+    A = synth.rmat(14, seed=4)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val)
+    B = 40
+    fronts = make_batch(A.n, B, 7 + lanes, 5000)
+    words = (A.m + 31) // 32
+    rng = np.random.default_rng(lanes)
+    masks_u8 = [(rng.random(A.m) < 0.3).astype(np.uint8) for _ in range(B)]
+    for semiring in (0, 1, 2):
+        xs = [x_values(semiring, xi, xf) for xi, xf in fronts]
+        x_cnt = np.array([xi.shape[0] for xi, _ in fronts], np.int32)
+        x_off = np.concatenate([[0], np.cumsum(x_cnt)[:-1]]).astype(np.int32)
+        x_idx = np.concatenate([xi for xi, _ in fronts]).astype(np.int32)
+        y_cap = np.full(B, A.m, np.int32)
+        y_off = (np.arange(B) * A.m).astype(np.int32)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        xv = None if semiring == 2 else dev(np.concatenate(xs))
+        yi = torch.empty(B * A.m, dtype=torch.int32, device="cuda")
+        yv = None if semiring == 2 else torch.empty(B * A.m, dtype=torch.float32 if semiring == 0 else torch.int32, device="cuda")
+        nz = torch.zeros(B, dtype=torch.int32, device="cuda")
+        msk = dev(np.concatenate([mask_bits(mm) for mm in masks_u8]).view(np.int32)) if masked else None
+        opts = S.SPMSPV_MASK_COMPLEMENT if masked else 0
+        S.spmspv_run_batched(Ad.handle, semiring, B, dev(x_off), dev(x_cnt), dev(x_idx), xv, msk,
+                             words, opts, dev(y_off), dev(y_cap), yi, yv, nz, lanes)
+        nz_h = nz.cpu().numpy()
+        yi_h = yi.cpu().numpy()
+        yv_h = None if yv is None else yv.cpu().numpy()
+        for b in range(B):
+            ref = oracle.spmspv(A.m, A.colptr, A.rowidx, A.val, SEMIRING_TO_ORACLE[semiring],
+                                fronts[b][0], xs[b], masks_u8[b] if masked else None, True)
+            assert nz_h[b] == ref.idx.shape[0], (semiring, b)
+            o = y_off[b]
+            compare(semiring, ref, yi_h[o:o + nz_h[b]], None if yv_h is None else yv_h[o:o + nz_h[b]])
+        assert S.spmspv_device_status(Ad.handle) == 0
+    Ad.close()
+
+
+def test_multisource_bfs_matches_oracle(lib):
+    torch, S = lib
+    A = synth.rmat(12, seed=8)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
+    srcs = synth.sources(A.colptr, 24, seed=4)
+    B = srcs.shape[0]
+    level = torch.empty(B * A.n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(B * A.n, dtype=torch.int32, device="cuda")
+    nl = torch.zeros(1, dtype=torch.int32, device="cuda")
+    S.spmspv_msbfs(Ad.handle, B, torch.from_numpy(srcs).cuda(), level, parent, nl, 0, 4)
+    lv = level.cpu().numpy().reshape(B, A.n)
+    pa = parent.cpu().numpy().reshape(B, A.n)
+    deepest = 0
+    for b in range(B):
+        rl, rp, rn, _, _ = oracle.bfs(A.colptr, A.rowidx, int(srcs[b]))
+        np.testing.assert_array_equal(lv[b], rl)
+        np.testing.assert_array_equal(pa[b], rp)
+        deepest = max(deepest, rn)
+    assert int(nl.item()) == deepest
+    Ad.close()
