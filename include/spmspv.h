@@ -209,6 +209,23 @@ int spmspv_msbfs(spmspv_handle* h, int32_t B, const int32_t* sources, int32_t* l
                  int32_t* parent, int32_t* nlevels, uint32_t opts, int32_t lanes,
                  spmspv_stream_t stream);
 
+/*
+ * Andersen-Chung-Lang push from B seeds (device int32[B]) on the unweighted
+ * graph (handle created with SPMSPV_VAL_NONE; A symmetric), one batched (+,*)
+ * SpMSpV per step (Sec. I lists ACL as a one-SpMSpV-per-step customer; the
+ * paper gives no algorithm, so the synchronous form below is this library's
+ * reading).  Per seed b: r = e_seed, p = 0; each step, with d(u) = column
+ * length and S = {u : r(u) >= eps*d(u)}: x(u) = (1-alpha) r(u) / (2 d(u)) and
+ * p(u) += alpha r(u), r(u) = (1-alpha) r(u) / 2 for u in S, then r += A x.
+ * Stops when every S is empty or after max_steps steps.  sum(p) + sum(r) stays 1.
+ *   p_out, r_out  device float[B][n] out.   steps_out  device int32 out (may be NULL).
+ * Allocates about 20 B*n bytes of work arrays for the call; synchronises the
+ * stream once per step.
+ */
+int spmspv_acl(spmspv_handle* h, int32_t B, const int32_t* seeds, float alpha, float eps,
+               int32_t max_steps, float* p_out, float* r_out, int32_t* steps_out, int32_t lanes,
+               spmspv_stream_t stream);
+
 /* ---- learned schedule selector ----
  * No counterpart in the paper, which leaves open when to switch between the
  * vector-driven (push) and matrix-driven (pull) forms (Sec. V).  A 6->32->32->12

@@ -457,3 +457,212 @@ extern "C" int spmspv_msbfs(spmspv_handle* h, int32_t B, const int32_t* sources,
   cudaFree(arr);
   return rc;
 }
+
+// ---------------------------------------------------------------------------
+// Andersen-Chung-Lang local clustering (Sec. I names it a one-SpMSpV-per-step
+// customer; the paper gives no algorithm).  Synchronous push per seed b with
+// residual r_b and approximate PageRank p_b (dense, n each), unweighted A,
+// degree d(u) = column length:
+//   S = {u : r(u) >= eps * d(u)}; for u in S: x(u) = (1-alpha) r(u) / (2 d(u)),
+//   p(u) += alpha r(u), r(u) = (1-alpha) r(u) / 2; then r += A x.
+// The next S is drawn only from the rows the step touched (y) and the last S.
+// ---------------------------------------------------------------------------
+namespace spmspv {
+namespace {
+
+__global__ void k_acl_init(int64_t total, float* __restrict__ R, float* __restrict__ P) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    R[i] = 0.f;
+    P[i] = 0.f;
+  }
+}
+
+__global__ void k_acl_seed(int32_t B, int32_t n, const int32_t* __restrict__ seeds,
+                           const int32_t* __restrict__ colptr, float eps, float* __restrict__ R,
+                           int32_t* __restrict__ act, int32_t* __restrict__ cnt,
+                           int32_t* __restrict__ status) {
+  for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    const int32_t s = seeds[b];
+    cnt[b] = 0;
+    if (s < 0 || s >= n) {
+      atomicOr(status, 1);
+      continue;
+    }
+    R[(int64_t)b * n + s] = 1.f;
+    const int32_t d = colptr[s + 1] - colptr[s];
+    if (d > 0 && 1.f >= eps * (float)d) {
+      act[(int64_t)b * n] = s;
+      cnt[b] = 1;
+    }
+  }
+}
+
+// Push the active set: x values, p += alpha r, r = (1-alpha) r / 2.
+__global__ void k_acl_push(int32_t B, int32_t n, const int32_t* __restrict__ colptr, float alpha,
+                           const int32_t* __restrict__ act, const int32_t* __restrict__ cnt,
+                           float* __restrict__ xv, float* __restrict__ R, float* __restrict__ P) {
+  const int32_t b = blockIdx.y;
+  const int32_t c = cnt[b];
+  const int64_t base = (int64_t)b * n;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < c; k += gridDim.x * blockDim.x) {
+    const int32_t u = act[base + k];
+    const float r = R[base + u];
+    const float d = (float)(colptr[u + 1] - colptr[u]);
+    xv[base + k] = (1.f - alpha) * r / (2.f * d);
+    P[base + u] += alpha * r;
+    R[base + u] = (1.f - alpha) * r * 0.5f;
+  }
+}
+
+// r += y for every seed's product.
+__global__ void k_acl_add(int32_t B, int32_t n, const int32_t* __restrict__ y_idx,
+                          const float* __restrict__ y_val, const int32_t* __restrict__ ny,
+                          float* __restrict__ R) {
+  const int32_t b = blockIdx.y;
+  const int32_t c = ny[b];
+  const int64_t base = (int64_t)b * n;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < c; k += gridDim.x * blockDim.x)
+    R[base + y_idx[base + k]] += y_val[base + k];
+}
+
+// Next active set from the candidates y_b and the last S_b (deduplicated with
+// a per-seed bitmap that is cleared again by k_acl_unmark).
+__global__ void k_acl_select(int32_t B, int32_t n, int64_t words, const int32_t* __restrict__ colptr,
+                             float eps, const int32_t* __restrict__ y_idx, const int32_t* __restrict__ ny,
+                             const int32_t* __restrict__ act, const int32_t* __restrict__ cnt,
+                             const float* __restrict__ R, uint32_t* __restrict__ mark,
+                             int32_t* __restrict__ nact, int32_t* __restrict__ ncnt) {
+  const int32_t b = blockIdx.y;
+  const int64_t base = (int64_t)b * n;
+  const int32_t c1 = ny[b], c2 = cnt[b];
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < c1 + c2; k += gridDim.x * blockDim.x) {
+    const int32_t u = k < c1 ? y_idx[base + k] : act[base + (k - c1)];
+    const float d = (float)(colptr[u + 1] - colptr[u]);
+    if (!(d > 0.f) || R[base + u] < eps * d) continue;
+    const uint32_t bit = 1u << (u & 31);
+    const uint32_t old = atomicOr(mark + (int64_t)b * words + (u >> 5), bit);
+    if (old & bit) continue;
+    const int32_t pos = atomicAdd(ncnt + b, 1);
+    nact[base + pos] = u;
+  }
+}
+
+__global__ void k_acl_unmark(int32_t B, int32_t n, int64_t words, const int32_t* __restrict__ nact,
+                             const int32_t* __restrict__ ncnt, uint32_t* __restrict__ mark,
+                             int32_t* __restrict__ total) {
+  const int32_t b = blockIdx.y;
+  const int32_t c = ncnt[b];
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < c; k += gridDim.x * blockDim.x) {
+    const int32_t u = nact[(int64_t)b * n + k];
+    mark[(int64_t)b * words + (u >> 5)] = 0u;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && c) atomicAdd(total, c);
+}
+
+}  // namespace
+}  // namespace spmspv
+
+extern "C" int spmspv_acl(spmspv_handle* h, int32_t B, const int32_t* seeds, float alpha, float eps,
+                          int32_t max_steps, float* p_out, float* r_out, int32_t* steps_out,
+                          int32_t lanes, spmspv_stream_t stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (h->A.m != h->A.n) return fail(SPMSPV_ERR_ARG, "ACL needs a square matrix");
+  if (h->A.val) return fail(SPMSPV_ERR_ARG, "ACL uses the unweighted graph: create the handle with SPMSPV_VAL_NONE");
+  if (B < 1 || !seeds || !p_out || !r_out) return fail(SPMSPV_ERR_ARG, "bad ACL arguments");
+  if (!(alpha > 0.f && alpha < 1.f) || !(eps > 0.f) || max_steps < 0)
+    return fail(SPMSPV_ERR_ARG, "need 0 < alpha < 1, eps > 0, max_steps >= 0");
+  if (B > (int32_t)(((int64_t)1 << 31) / h->A.n)) return fail(SPMSPV_ERR_UNSUPPORTED, "B * n must stay below 2^31");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int32_t n = h->A.n;
+  const int64_t words = ((int64_t)n + 31) / 32;
+  const size_t bn = (size_t)B * n;
+  int32_t *act0 = nullptr, *act1 = nullptr, *yi = nullptr, *arr = nullptr;
+  float *xv = nullptr, *yv = nullptr;
+  uint32_t* mark = nullptr;
+  cudaError_t e = cudaMalloc(&act0, sizeof(int32_t) * bn);
+  if (e == cudaSuccess) e = cudaMalloc(&act1, sizeof(int32_t) * bn);
+  if (e == cudaSuccess) e = cudaMalloc(&yi, sizeof(int32_t) * bn);
+  if (e == cudaSuccess) e = cudaMalloc(&xv, sizeof(float) * bn);
+  if (e == cudaSuccess) e = cudaMalloc(&yv, sizeof(float) * bn);
+  if (e == cudaSuccess) e = cudaMalloc(&mark, sizeof(uint32_t) * (size_t)B * words);
+  if (e == cudaSuccess) e = cudaMalloc(&arr, sizeof(int32_t) * ((size_t)B * 8 + 8));
+  auto release = [&]() {
+    cudaFree(act0); cudaFree(act1); cudaFree(yi); cudaFree(xv); cudaFree(yv); cudaFree(mark); cudaFree(arr);
+  };
+  if (e != cudaSuccess) {
+    release();
+    cudaGetLastError();
+    return fail(SPMSPV_ERR_OOM, "ACL buffers: %s", cudaGetErrorString(e));
+  }
+  int32_t* cnt0 = arr;
+  int32_t* cnt1 = arr + B;
+  int32_t* ny = arr + 2 * B;
+  int32_t* x_off = arr + 3 * B;
+  int32_t* y_cap = arr + 4 * B;
+  int32_t* misc = arr + 8 * B;  // [0] status [1] active total
+  cudaMemsetAsync(mark, 0, sizeof(uint32_t) * (size_t)B * words, s);
+  cudaMemsetAsync(misc, 0, sizeof(int32_t) * 8, s);
+  {
+    std::vector<int32_t> off(B), cap(B, n);
+    for (int32_t b = 0; b < B; ++b) off[b] = b * n;
+    cudaMemcpyAsync(x_off, off.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(y_cap, cap.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+  }
+  k_acl_init<<<h->sm_count * 4, 256, 0, s>>>((int64_t)bn, r_out, p_out);
+  k_acl_seed<<<(B + 255) / 256, 256, 0, s>>>(B, n, seeds, h->A.colptr, eps, r_out, act0, cnt0, misc);
+  if ((rc = ensure_batch_state(h, lanes)) != SPMSPV_OK) {
+    release();
+    return rc;
+  }
+  const dim3 g2(16, B);
+  int32_t step = 0;
+  int32_t* act = act0;
+  int32_t* nact = act1;
+  int32_t* cnt = cnt0;
+  int32_t* ncnt = cnt1;
+  for (step = 0; step < max_steps; ++step) {
+    k_acl_push<<<g2, 256, 0, s>>>(B, n, h->A.colptr, alpha, act, cnt, xv, r_out, p_out);
+    BatchDesc v;
+    memset(&v, 0, sizeof(v));
+    v.B = B;
+    v.x_off = x_off;
+    v.x_cnt = cnt;
+    v.x_idx = act;
+    v.x_val = (const uint32_t*)xv;
+    v.y_off = x_off;
+    v.y_cap = y_cap;
+    v.y_idx = yi;
+    v.y_val = (uint32_t*)yv;
+    v.d_nnz_y = ny;
+    if ((rc = run_batched(h, kPlusTimes, false, B, v, SPMSPV_SCHED_OPT(h->default_sched), lanes, s)) != SPMSPV_OK) break;
+    k_acl_add<<<g2, 256, 0, s>>>(B, n, yi, yv, ny, r_out);
+    cudaMemsetAsync(ncnt, 0, sizeof(int32_t) * B, s);
+    cudaMemsetAsync(misc + 1, 0, sizeof(int32_t), s);
+    k_acl_select<<<g2, 256, 0, s>>>(B, n, words, h->A.colptr, eps, yi, ny, act, cnt, r_out, mark, nact, ncnt);
+    k_acl_unmark<<<g2, 256, 0, s>>>(B, n, words, nact, ncnt, mark, misc + 1);
+    int32_t total = 0;
+    e = cudaMemcpyAsync(&total, misc + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "ACL step");
+      break;
+    }
+    std::swap(act, nact);
+    std::swap(cnt, ncnt);
+    if (total == 0) {
+      ++step;
+      break;
+    }
+  }
+  if (rc == SPMSPV_OK && steps_out) {
+    e = cudaMemcpyAsync(steps_out, &step, sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "ACL step count");
+  }
+  cudaStreamSynchronize(s);
+  release();
+  return rc;
+}

@@ -110,6 +110,8 @@ def load(build_if_missing: bool = True):
                                            ctypes.c_int32, _P]
         lib.spmspv_msbfs.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_uint32,
                                      ctypes.c_int32, _P]
+        lib.spmspv_acl.argtypes = [_P, ctypes.c_int32, _P, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_int32, _P, _P, _P, ctypes.c_int32, _P]
         lib.spmspv_profile_begin.argtypes = [_P]
         lib.spmspv_profile_end.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_int32)]
@@ -233,6 +235,12 @@ def spmspv_run_batched(h, semiring, B, x_off, x_cnt, x_idx, x_val, masks, mask_s
 def spmspv_msbfs(h, B, sources, level, parent, nlevels, opts=0, lanes=8, stream=None):
     _check(load().spmspv_msbfs(h, int(B), _ptr(sources), _ptr(level), _ptr(parent), _ptr(nlevels),
                                int(opts), int(lanes), _stream(stream)), "spmspv_msbfs")
+
+
+def spmspv_acl(h, B, seeds, alpha, eps, max_steps, p_out, r_out, steps_out, lanes=8, stream=None):
+    _check(load().spmspv_acl(h, int(B), _ptr(seeds), float(alpha), float(eps), int(max_steps),
+                             _ptr(p_out), _ptr(r_out), _ptr(steps_out), int(lanes), _stream(stream)),
+           "spmspv_acl")
 
 
 def spmspv_device_status(h) -> int:
