@@ -218,6 +218,7 @@ int spmspv_msbfs(spmspv_handle* h, int32_t B, const int32_t* sources, int32_t* l
  * length and S = {u : r(u) >= eps*d(u)}: x(u) = (1-alpha) r(u) / (2 d(u)) and
  * p(u) += alpha r(u), r(u) = (1-alpha) r(u) / 2 for u in S, then r += A x.
  * Stops when every S is empty or after max_steps steps.  sum(p) + sum(r) stays 1.
+ * 1 <= B <= 65535 and B*n < 2^31, else SPMSPV_ERR_UNSUPPORTED.
  *   p_out, r_out  device float[B][n] out.   steps_out  device int32 out (may be NULL).
  * Allocates about 20 B*n bytes of work arrays for the call; synchronises the
  * stream once per step.

@@ -574,6 +574,7 @@ extern "C" int spmspv_acl(spmspv_handle* h, int32_t B, const int32_t* seeds, flo
   if (!(alpha > 0.f && alpha < 1.f) || !(eps > 0.f) || max_steps < 0)
     return fail(SPMSPV_ERR_ARG, "need 0 < alpha < 1, eps > 0, max_steps >= 0");
   if (B > (int32_t)(((int64_t)1 << 31) / h->A.n)) return fail(SPMSPV_ERR_UNSUPPORTED, "B * n must stay below 2^31");
+  if (B > 65535) return fail(SPMSPV_ERR_UNSUPPORTED, "at most 65535 seeds per call");
   cudaStream_t s = (cudaStream_t)stream;
   const int32_t n = h->A.n;
   const int64_t words = ((int64_t)n + 31) / 32;
