@@ -189,6 +189,14 @@ int spmspv_bfs(spmspv_handle* h, int32_t src, int32_t* level, int32_t* parent,
  *                        form), SPMSPV_MASK_COMPLEMENT.
  *   lanes                1..16.  Lane workspaces (one per lane, as for a
  *                        handle) and the graph are created on first use.
+ *                        0 = autotuned: lanes and push schedule are taken from
+ *                        the handle's tuning cache for this batch profile
+ *                        (spmspv_tune_key), or, on the first call with a new
+ *                        profile, found by running the batch under every
+ *                        candidate (lanes 2/4/8/16 x push schedules 0..5, two
+ *                        runs each, the second timed) and cached.  Any schedule
+ *                        in opts is then ignored.  lanes = 0 synchronises the
+ *                        stream (to read x_cnt), so it must not be captured.
  */
 int spmspv_run_batched(spmspv_handle* h, int semiring, int32_t B, const int32_t* x_off,
                        const int32_t* x_cnt, const int32_t* x_idx, const void* x_val,
@@ -201,7 +209,9 @@ int spmspv_run_batched(spmspv_handle* h, int semiring, int32_t B, const int32_t*
  * device array) advanced together, one batched step per level.
  *   level, parent  device int32[B][n] out (row b = search from sources[b]).
  *   nlevels        device int32 out (may be NULL): levels of the deepest search.
- *   opts, lanes    as for spmspv_run_batched (schedule, 1..16 lanes).
+ *   opts, lanes    as for spmspv_run_batched (schedule, 1..16 lanes, or 0 for
+ *                  autotuned: the first call with a new B profile runs the whole
+ *                  search under every candidate, timed, and caches the fastest).
  * Allocates B*(4n + n/8) bytes of frontiers and visited bitmaps for the call;
  * synchronises the stream once per level to test for termination.
  */
@@ -220,12 +230,32 @@ int spmspv_msbfs(spmspv_handle* h, int32_t B, const int32_t* sources, int32_t* l
  * Stops when every S is empty or after max_steps steps.  sum(p) + sum(r) stays 1.
  * 1 <= B <= 65535 and B*n < 2^31, else SPMSPV_ERR_UNSUPPORTED.
  *   p_out, r_out  device float[B][n] out.   steps_out  device int32 out (may be NULL).
+ *   lanes   1..16 concurrent lanes with the handle's default schedule, or 0 for
+ *           autotuned (as for spmspv_msbfs: whole runs timed per candidate).
  * Allocates about 20 B*n bytes of work arrays for the call; synchronises the
  * stream once per step.
  */
 int spmspv_acl(spmspv_handle* h, int32_t B, const int32_t* seeds, float alpha, float eps,
                int32_t max_steps, float* p_out, float* r_out, int32_t* steps_out, int32_t lanes,
                spmspv_stream_t stream);
+
+/* ---- autotuner of the batched form (no counterpart in the paper) ----
+ * The cache lives in the handle (lost at spmspv_destroy).  A profile key packs
+ * kind (0 batched SpMSpV, 1 multi-source BFS, 2 ACL), semiring, whether masks
+ * are given, ceil(log2 B) and ceil(log2(1 + total nnz(x) / B)); calls whose
+ * profiles share a key share one tuning.  spmspv_tune_key is pure host code.
+ */
+uint64_t spmspv_tune_key(int kind, int semiring, int masked, int32_t B, int64_t total_nnz_x);
+/* What the handle's last lanes = 0 call ran with; from_cache = 1 when no
+ * timing was needed.  SPMSPV_ERR_STATE before any such call. */
+int spmspv_last_tuned(spmspv_handle* h, int32_t* lanes, int32_t* sched, int32_t* from_cache);
+/* Copy up to `capacity` cache entries out (host arrays, any may be NULL);
+ * *count receives the number of entries.  ms is the timed run (NaN if set). */
+int spmspv_tune_entries(spmspv_handle* h, uint64_t* keys, int32_t* lanes, int32_t* sched,
+                        float* ms, int32_t capacity, int32_t* count);
+/* Seed or override an entry (lanes 1..16, push schedule 0..5). */
+int spmspv_tune_set(spmspv_handle* h, uint64_t key, int32_t lanes, int32_t sched);
+int spmspv_tune_clear(spmspv_handle* h);
 
 /* ---- learned schedule selector ----
  * No counterpart in the paper, which leaves open when to switch between the

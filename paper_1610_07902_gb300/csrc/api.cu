@@ -447,6 +447,7 @@ int spmspv_destroy(spmspv_handle* h) {
   }
   release_bfs_graphs(h);
   release_batch(h);
+  release_tune(h);
   release_extras(h);
   cudaFree(h->rowidx_k2);
   cudaFree(h->sel_w);

@@ -302,7 +302,18 @@ extern "C" int spmspv_run_batched(spmspv_handle* h, int semiring, int32_t B, con
   (void)(opts & SPMSPV_MASK_COMPLEMENT);
   if (masks && !(opts & SPMSPV_MASK_COMPLEMENT))
     return fail(SPMSPV_ERR_UNSUPPORTED, "batched masks are complemented masks");
-  return run_batched(h, semiring, false, B, v, opts, lanes, (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (lanes != 0) return run_batched(h, semiring, false, B, v, opts, lanes, s);
+  // autotuned: the profile needs the total frontier length
+  std::vector<int32_t> cnt(B);
+  cudaError_t e = cudaMemcpyAsync(cnt.data(), x_cnt, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "batch profile");
+  int64_t total = 0;
+  for (int32_t c : cnt) total += c;
+  const uint32_t base = opts & ~(uint32_t)(SPMSPV_SCHED_FORCE | SPMSPV_SCHED_AUTO | SPMSPV_SCHED_OPT(0xFFu));
+  return tune_and_run(h, tune_key(0, semiring, masks != nullptr, B, total), s,
+                      [&](int32_t ln, uint32_t so) { return run_batched(h, semiring, false, B, v, base | so, ln, s); });
 }
 
 // ---------------------------------------------------------------------------
@@ -367,9 +378,9 @@ __global__ void k_msbfs_next(int32_t B, const int32_t* __restrict__ nnz, int32_t
 }  // namespace
 }  // namespace spmspv
 
-extern "C" int spmspv_msbfs(spmspv_handle* h, int32_t B, const int32_t* sources, int32_t* level,
-                            int32_t* parent, int32_t* nlevels, uint32_t opts, int32_t lanes,
-                            spmspv_stream_t stream) {
+static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_t* level,
+                     int32_t* parent, int32_t* nlevels, uint32_t opts, int32_t lanes,
+                     spmspv_stream_t stream) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (h->A.m != h->A.n) return fail(SPMSPV_ERR_ARG, "BFS needs a square matrix");
@@ -563,9 +574,9 @@ __global__ void k_acl_unmark(int32_t B, int32_t n, int64_t words, const int32_t*
 }  // namespace
 }  // namespace spmspv
 
-extern "C" int spmspv_acl(spmspv_handle* h, int32_t B, const int32_t* seeds, float alpha, float eps,
-                          int32_t max_steps, float* p_out, float* r_out, int32_t* steps_out,
-                          int32_t lanes, spmspv_stream_t stream) {
+static int acl_run(spmspv_handle* h, int32_t B, const int32_t* seeds, float alpha, float eps,
+                   int32_t max_steps, float* p_out, float* r_out, int32_t* steps_out, uint32_t opts,
+                   int32_t lanes, spmspv_stream_t stream) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (h->A.m != h->A.n) return fail(SPMSPV_ERR_ARG, "ACL needs a square matrix");
@@ -638,7 +649,7 @@ extern "C" int spmspv_acl(spmspv_handle* h, int32_t B, const int32_t* seeds, flo
     v.y_idx = yi;
     v.y_val = (uint32_t*)yv;
     v.d_nnz_y = ny;
-    if ((rc = run_batched(h, kPlusTimes, false, B, v, SPMSPV_SCHED_OPT(h->default_sched), lanes, s)) != SPMSPV_OK) break;
+    if ((rc = run_batched(h, kPlusTimes, false, B, v, opts, lanes, s)) != SPMSPV_OK) break;
     k_acl_add<<<g2, 256, 0, s>>>(B, n, yi, yv, ny, r_out);
     cudaMemsetAsync(ncnt, 0, sizeof(int32_t) * B, s);
     cudaMemsetAsync(misc + 1, 0, sizeof(int32_t), s);
@@ -666,4 +677,32 @@ extern "C" int spmspv_acl(spmspv_handle* h, int32_t B, const int32_t* seeds, flo
   cudaStreamSynchronize(s);
   release();
   return rc;
+}
+
+// lanes == 0: the autotuner picks lanes and schedule per (B) profile, timing
+// whole runs (each run starts from its sources/seeds again, so reruns are harmless).
+extern "C" int spmspv_msbfs(spmspv_handle* h, int32_t B, const int32_t* sources, int32_t* level,
+                            int32_t* parent, int32_t* nlevels, uint32_t opts, int32_t lanes,
+                            spmspv_stream_t stream) {
+  if (lanes != 0) return msbfs_run(h, B, sources, level, parent, nlevels, opts, lanes, stream);
+  int rc = check_handle(h);
+  if (rc) return rc;
+  const uint32_t base = opts & ~(uint32_t)(SPMSPV_SCHED_FORCE | SPMSPV_SCHED_AUTO | SPMSPV_SCHED_OPT(0xFFu));
+  return tune_and_run(h, tune_key(1, kMinSelect2nd, 1, B, 0), (cudaStream_t)stream,
+                      [&](int32_t ln, uint32_t so) {
+                        return msbfs_run(h, B, sources, level, parent, nlevels, base | so, ln, stream);
+                      });
+}
+
+extern "C" int spmspv_acl(spmspv_handle* h, int32_t B, const int32_t* seeds, float alpha, float eps,
+                          int32_t max_steps, float* p_out, float* r_out, int32_t* steps_out,
+                          int32_t lanes, spmspv_stream_t stream) {
+  if (lanes != 0)
+    return acl_run(h, B, seeds, alpha, eps, max_steps, p_out, r_out, steps_out, 0, lanes, stream);
+  int rc = check_handle(h);
+  if (rc) return rc;
+  return tune_and_run(h, tune_key(2, kPlusTimes, 0, B, 0), (cudaStream_t)stream,
+                      [&](int32_t ln, uint32_t so) {
+                        return acl_run(h, B, seeds, alpha, eps, max_steps, p_out, r_out, steps_out, so, ln, stream);
+                      });
 }

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+
 #include "spmspv_internal.cuh"
 
 constexpr uint32_t kHandleMagic = 0x53704d53u;
@@ -37,6 +39,7 @@ struct spmspv_handle {
   int sel_ready;        // weights present
   float* sel_w;         // device weights (layout in selector.cu)
   void* batch;          // BatchState* of the batched form (batched.cu), lazily created
+  void* tune;           // TuneCache* of the batched-form autotuner (autotune.cu), lazily created
   // pull direction (dense frontier) buffers, allocated on first use
   uint32_t* xbits;      // [ceil(n/32)] frontier bitmap
   uint32_t* xdense;     // [n] frontier values
@@ -65,6 +68,13 @@ int run_pull_if_available(spmspv_handle* h, int sem, const int32_t* x_idx, const
 void release_extras(spmspv_handle* h);
 void release_bfs_graphs(spmspv_handle* h);
 void release_batch(spmspv_handle* h);
+void release_tune(spmspv_handle* h);
+// Autotuner (autotune.cu).  kind: 0 batched SpMSpV, 1 multi-source BFS, 2 ACL.
+uint64_t tune_key(int kind, int sem, int masked, int32_t B, int64_t total_f);
+// Runs `run(lanes, schedule opts)` with the cached choice for `key`, or times
+// every candidate on `s` (each run twice, the second timed) and caches the best.
+int tune_and_run(spmspv_handle* h, uint64_t key, cudaStream_t s,
+                 const std::function<int(int32_t, uint32_t)>& run);
 cudaError_t alloc_pull_buffers(spmspv_handle* h);
 int ensure_bfs_buffers(spmspv_handle* h);
 // Per-stage event recording (no-ops unless spmspv_profile_begin was called).

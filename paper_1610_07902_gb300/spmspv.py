@@ -112,6 +112,15 @@ def load(build_if_missing: bool = True):
                                      ctypes.c_int32, _P]
         lib.spmspv_acl.argtypes = [_P, ctypes.c_int32, _P, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_int32, _P, _P, _P, ctypes.c_int32, _P]
+        lib.spmspv_tune_key.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int32,
+                                        ctypes.c_int64]
+        lib.spmspv_tune_key.restype = ctypes.c_uint64
+        lib.spmspv_last_tuned.argtypes = [_P, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+        lib.spmspv_tune_entries.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int32,
+                                            ctypes.POINTER(ctypes.c_int32)]
+        lib.spmspv_tune_set.argtypes = [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32]
+        lib.spmspv_tune_clear.argtypes = [_P]
         lib.spmspv_profile_begin.argtypes = [_P]
         lib.spmspv_profile_end.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_int32)]
@@ -202,6 +211,46 @@ def spmspv_last_schedule(h) -> int:
     v = ctypes.c_int32(0)
     _check(load().spmspv_last_schedule(h, ctypes.byref(v)), "spmspv_last_schedule")
     return int(v.value)
+
+
+TUNE_BATCHED, TUNE_MSBFS, TUNE_ACL = 0, 1, 2
+
+
+def spmspv_tune_key(kind, semiring, masked, B, total_nnz_x) -> int:
+    return int(load().spmspv_tune_key(int(kind), int(semiring), 1 if masked else 0, int(B),
+                                      int(total_nnz_x)))
+
+
+def spmspv_last_tuned(h):
+    """(lanes, schedule, from_cache) of the handle's last autotuned call."""
+    a, b, c = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load().spmspv_last_tuned(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "spmspv_last_tuned")
+    return int(a.value), int(b.value), bool(c.value)
+
+
+def spmspv_tune_entries(h):
+    """List of (key, lanes, schedule, ms) in the handle's tuning cache."""
+    import numpy as np
+    cnt = ctypes.c_int32(0)
+    _check(load().spmspv_tune_entries(h, None, None, None, None, 0, ctypes.byref(cnt)),
+           "spmspv_tune_entries")
+    n = int(cnt.value)
+    keys = np.zeros(n, np.uint64)
+    lanes = np.zeros(n, np.int32)
+    sched = np.zeros(n, np.int32)
+    ms = np.zeros(n, np.float32)
+    _check(load().spmspv_tune_entries(h, keys.ctypes.data, lanes.ctypes.data, sched.ctypes.data,
+                                      ms.ctypes.data, n, ctypes.byref(cnt)), "spmspv_tune_entries")
+    return [(int(keys[i]), int(lanes[i]), int(sched[i]), float(ms[i])) for i in range(n)]
+
+
+def spmspv_tune_set(h, key, lanes, sched):
+    _check(load().spmspv_tune_set(h, int(key), int(lanes), int(sched)), "spmspv_tune_set")
+
+
+def spmspv_tune_clear(h):
+    _check(load().spmspv_tune_clear(h), "spmspv_tune_clear")
 
 
 def spmspv_selector_train(h, feats, target, valid, n, epochs, batch, lr, seed):

@@ -45,7 +45,7 @@ def test_acl_matches_reference(lib, graph, lanes):
     for b in range(B):
         assert abs(P[b].sum() + R[b].sum() - 1.0) < 1e-5, b
         assert (P[b] >= 0).all() and (R[b] >= 0).all()
-        assert (R[b] < eps * deg * (1 + 1e-4)).all(), b
+        assert ((R[b] < eps * deg * (1 + 1e-4)) | ((deg == 0) & (R[b] == 0))).all(), b
         p64, r64, _ = oacl.acl(A.colptr, A.rowidx, int(seeds[b]), alpha, eps, 10000)
         assert np.abs(P[b] - p64).sum() < 1e-3, b
         assert np.abs(R[b] - r64).sum() < 1e-3, b

@@ -87,3 +87,73 @@ def test_multisource_bfs_matches_oracle(lib):
         deepest = max(deepest, rn)
     assert int(nl.item()) == deepest
     Ad.close()
+
+
+def test_autotuned_batch_matches_and_caches(lib):
+    torch, S = lib
+    A = synth.rmat(13, seed=9)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val)
+    B = 24
+    fronts = make_batch(A.n, B, 31, 3000)
+    x_cnt = np.array([xi.shape[0] for xi, _ in fronts], np.int32)
+    x_off = np.concatenate([[0], np.cumsum(x_cnt)[:-1]]).astype(np.int32)
+    x_idx = np.concatenate([xi for xi, _ in fronts]).astype(np.int32)
+    x_val = np.concatenate([xf for _, xf in fronts]).astype(np.float32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    y_cap = np.full(B, A.m, np.int32)
+    y_off = (np.arange(B) * A.m).astype(np.int32)
+    args = [dev(x_off), dev(x_cnt), dev(x_idx), dev(x_val)]
+    outs = []
+    for call in range(2):
+        yi = torch.empty(B * A.m, dtype=torch.int32, device="cuda")
+        yv = torch.empty(B * A.m, dtype=torch.float32, device="cuda")
+        nz = torch.zeros(B, dtype=torch.int32, device="cuda")
+        S.spmspv_run_batched(Ad.handle, 0, B, *args, None, 0, 0, dev(y_off), dev(y_cap), yi, yv, nz, 0)
+        lanes, sched, cached = S.spmspv_last_tuned(Ad.handle)
+        assert 2 <= lanes <= 16 and 0 <= sched < 6
+        assert cached == (call == 1)
+        outs.append((nz.cpu().numpy(), yi.cpu().numpy(), yv.cpu().numpy()))
+    nz_h, yi_h, yv_h = outs[1]
+    for b in range(B):
+        ref = oracle.spmspv(A.m, A.colptr, A.rowidx, A.val, SEMIRING_TO_ORACLE[0], fronts[b][0],
+                            fronts[b][1], None, True)
+        o = y_off[b]
+        assert nz_h[b] == ref.idx.shape[0]
+        compare(0, ref, yi_h[o:o + nz_h[b]], yv_h[o:o + nz_h[b]])
+    ent = S.spmspv_tune_entries(Ad.handle)
+    assert len(ent) == 1 and ent[0][0] == S.spmspv_tune_key(0, 0, 0, B, int(x_cnt.sum()))
+    assert ent[0][3] > 0
+    # an override is used as given
+    S.spmspv_tune_set(Ad.handle, ent[0][0], 3, 5)
+    S.spmspv_run_batched(Ad.handle, 0, B, *args, None, 0, 0, dev(y_off), dev(y_cap), yi, yv, nz, 0)
+    assert S.spmspv_last_tuned(Ad.handle) == (3, 5, True)
+    assert (nz.cpu().numpy() == nz_h).all()
+    S.spmspv_tune_clear(Ad.handle)
+    assert S.spmspv_tune_entries(Ad.handle) == []
+    Ad.close()
+
+
+def test_autotuned_msbfs_and_acl_match_fixed(lib):
+    torch, S = lib
+    A = synth.rmat(11, seed=12, values=False)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, flags=S.SPMSPV_CSC_SYMMETRIC)
+    srcs = torch.from_numpy(synth.sources(A.colptr, 16, seed=9).astype(np.int32)).cuda()
+    B = srcs.shape[0]
+    res = []
+    for lanes in (4, 0):
+        level = torch.empty(B * A.n, dtype=torch.int32, device="cuda")
+        parent = torch.empty(B * A.n, dtype=torch.int32, device="cuda")
+        S.spmspv_msbfs(Ad.handle, B, srcs, level, parent, None, 0, lanes)
+        res.append((level.cpu().numpy(), parent.cpu().numpy()))
+    assert (res[0][0] == res[1][0]).all() and (res[0][1] == res[1][1]).all()
+    assert S.spmspv_last_tuned(Ad.handle)[2] is False
+    p = torch.empty(B * A.n, dtype=torch.float32, device="cuda")
+    r = torch.empty(B * A.n, dtype=torch.float32, device="cuda")
+    S.spmspv_acl(Ad.handle, B, srcs, 0.15, 1e-5, 1000, p, r, None, 0)
+    lanes, sched, cached = S.spmspv_last_tuned(Ad.handle)
+    assert not cached and 2 <= lanes <= 16
+    P = p.cpu().numpy().reshape(B, A.n).astype(np.float64)
+    R = r.cpu().numpy().reshape(B, A.n).astype(np.float64)
+    assert np.abs(P.sum(1) + R.sum(1) - 1).max() < 1e-5
+    assert len(S.spmspv_tune_entries(Ad.handle)) == 2
+    Ad.close()
