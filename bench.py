@@ -124,6 +124,204 @@ def time_oracle(A, x_idx, x_val, budget_s=10.0):
     return W_total / t_total / 1e9, calls, t_total
 
 
+def _events_ms(fn, stream, reps=1):
+    import torch
+    best = float("inf")
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def selector_params():
+    from paper_1610_07902_gb300 import selector
+    try:
+        return selector.load()[0]
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def bench_bfs(S, A, dev, stream, name, sources, params, pt_frontiers=False):
+    """BFS under the plain fixed schedule and under the learned selector (AUTO),
+    one graph-captured level loop per search, levels and parents compared."""
+    import torch
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC,
+                     device=dev)
+    deg = torch.diff(Ad.colptr.long())
+    level = torch.empty(A.n, dtype=torch.int32, device=dev)
+    parent = torch.empty(A.n, dtype=torch.int32, device=dev)
+    level2 = torch.empty_like(level)
+    parent2 = torch.empty_like(parent)
+    nl = torch.zeros(1, dtype=torch.int32, device=dev)
+    default = S.spmspv_default_schedule(Ad.handle)
+    fixed = S.SPMSPV_SCHED_OPT(default)
+    if params is not None:
+        S.spmspv_selector_set(Ad.handle, params)
+    t_fixed = t_auto = 0.0
+    work = 0
+    levels = []
+    same = True
+    for src in sources:
+        run = lambda o, lv, pa: S.spmspv_bfs(Ad.handle, int(src), lv, pa, nl, o, stream)
+        run(fixed, level, parent)
+        t_fixed += _events_ms(lambda: run(fixed, level, parent), stream, 2)
+        levels.append(int(nl.item()))
+        work += int(deg[level >= 0].sum().item())
+        if params is not None:
+            run(S.SPMSPV_SCHED_AUTO, level2, parent2)
+            t_auto += _events_ms(lambda: run(S.SPMSPV_SCHED_AUTO, level2, parent2), stream, 2)
+            same &= bool(torch.equal(level, level2) and torch.equal(parent, parent2))
+    out = {"graph": name, "n": A.n, "nnz": A.nnz, "sources": len(sources),
+           "levels_max": max(levels), "products": work, "default_schedule": default,
+           "fixed_ms": t_fixed, "fixed_gteps": work / (t_fixed * 1e-3) / 1e9}
+    if params is not None:
+        out.update({"auto_ms": t_auto, "auto_gteps": work / (t_auto * 1e-3) / 1e9,
+                    "auto_speedup": t_fixed / t_auto, "identical_results": same})
+    if pt_frontiers:
+        # (+,*) float32 SpMSpV on every frontier of the last search (level sets
+        # from the device BFS, host-side split), one call per level
+        lv = level.cpu().numpy()
+        fr = [torch.from_numpy(np.flatnonzero(lv == L).astype(np.int32)).to(dev)
+              for L in range(int(lv.max()) + 1)]
+        xv = [torch.rand(f.shape[0], device=dev) for f in fr]
+        cap = min(A.m, A.nnz)
+        yi = torch.empty(cap, dtype=torch.int32, device=dev)
+        yv = torch.empty(cap, dtype=torch.float32, device=dev)
+        nz = torch.zeros(1, dtype=torch.int32, device=dev)
+        pw = int(sum(deg[f.long()].sum().item() for f in fr))
+
+        def all_levels():
+            for f, v in zip(fr, xv):
+                S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, f, v, f.shape[0], None, 0, yi, yv,
+                             cap, nz, stream)
+        all_levels()
+        t = _events_ms(all_levels, stream, 2)
+        out["plus_times_per_frontier"] = {"calls": len(fr), "products": pw, "ms": t,
+                                          "gteps": pw / (t * 1e-3) / 1e9,
+                                          "us_per_call": 1e3 * t / len(fr)}
+    Ad.close()
+    return out
+
+
+def bench_batched(S, dev, stream, B=256):
+    """256 frontiers on R-MAT s20 in one batched launch (autotuned) against
+    256 sequential plain calls; multi-source BFS and ACL the same way."""
+    import torch
+    import synth
+    A = synth.rmat(20, EDGE_FACTOR, seed=4)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val, device=dev)
+    rng = np.random.default_rng(4)
+    sizes = np.maximum(1, np.floor(10 ** rng.uniform(0, 5, B))).astype(np.int64)
+    fronts = [synth.frontier(A.n, int(f), seed=100 + b, stream=2) for b, f in enumerate(sizes)]
+    x_cnt = sizes.astype(np.int32)
+    x_off = np.concatenate([[0], np.cumsum(x_cnt)[:-1]]).astype(np.int32)
+    td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    xi_all = td(np.concatenate([f[0] for f in fronts]))
+    xv_all = td(np.concatenate([f[1] for f in fronts]))
+    y_off = (np.arange(B, dtype=np.int64) * A.m).astype(np.int64)
+    ycap = A.m
+    yi = torch.empty(B * ycap, dtype=torch.int32, device=dev)
+    yv = torch.empty(B * ycap, dtype=torch.float32, device=dev)
+    nz = torch.zeros(B, dtype=torch.int32, device=dev)
+    d_off, d_cnt = td(x_off), td(x_cnt)
+    d_yoff, d_ycap = td(y_off.astype(np.int32)), td(np.full(B, ycap, np.int32))
+
+    def batched():
+        S.spmspv_run_batched(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, B, d_off, d_cnt, xi_all, xv_all, None,
+                             0, 0, d_yoff, d_ycap, yi, yv, nz, 0, stream)
+    batched()  # tunes on first use
+    t_b = _events_ms(batched, stream, 3)
+    tuned = S.spmspv_last_tuned(Ad.handle)
+    nz_b = nz.cpu().numpy().copy()
+    yi_b = yi.cpu().numpy()
+    yv_b = yv.cpu().numpy()
+    views = [(xi_all[x_off[b]:x_off[b] + x_cnt[b]], xv_all[x_off[b]:x_off[b] + x_cnt[b]],
+              yi[b * ycap:(b + 1) * ycap], yv[b * ycap:(b + 1) * ycap], nz[b:b + 1]) for b in range(B)]
+
+    def sequential():
+        for b in range(B):
+            a, v, oi, ov, on = views[b]
+            S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, a, v, int(x_cnt[b]), None,
+                         S.SPMSPV_SORTED_OUT, oi, ov, ycap, on, stream)
+    sequential()
+    t_s = _events_ms(sequential, stream, 3)
+    nz_s = nz.cpu().numpy()
+    same_idx = bool((nz_s == nz_b).all())
+    rel = 0.0
+    yi_s, yv_s = yi.cpu().numpy(), yv.cpu().numpy()
+    for b in range(B):
+        o, c = b * ycap, int(nz_s[b])
+        same_idx &= bool((yi_s[o:o + c] == yi_b[o:o + c]).all())
+        d = np.abs(yv_s[o:o + c] - yv_b[o:o + c]) / np.maximum(np.abs(yv_s[o:o + c]), 1e-30)
+        rel = max(rel, float(d.max()) if c else 0.0)
+    W = int(sum(int(np.diff(A.colptr)[f[0]].sum()) for f in fronts))
+    out = {"graph": "rmat s20 ef16 seed 4", "B": B, "nnz_x_loguniform": [1, 100000],
+           "products": W,
+           "spmspv": {"batched_ms": t_b, "sequential_ms": t_s, "speedup": t_s / t_b,
+                      "batched_gteps": W / (t_b * 1e-3) / 1e9, "tuned_lanes": tuned[0],
+                      "tuned_schedule": tuned[1], "identical_index_sets": same_idx,
+                      "max_rel_value_diff": rel}}
+    del yi, yv
+    Ad.close()
+
+    # multi-source BFS vs 256 sequential single-source BFS (fixed schedule)
+    Ap = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, flags=S.SPMSPV_CSC_SYMMETRIC, device=dev)
+    srcs = synth.sources(A.colptr, B, seed=5).astype(np.int32)
+    ds = td(srcs)
+    lv = torch.empty(B * A.n, dtype=torch.int32, device=dev)
+    pa = torch.empty(B * A.n, dtype=torch.int32, device=dev)
+    ms = lambda: S.spmspv_msbfs(Ap.handle, B, ds, lv, pa, None, 0, 0, stream)
+    ms()
+    t_ms = _events_ms(ms, stream, 2)
+    tuned = S.spmspv_last_tuned(Ap.handle)
+    lv1 = torch.empty(A.n, dtype=torch.int32, device=dev)
+    pa1 = torch.empty(A.n, dtype=torch.int32, device=dev)
+    nl = torch.zeros(1, dtype=torch.int32, device=dev)
+    same = True
+    t_seq = 0.0
+    for b in range(B):
+        run = lambda: S.spmspv_bfs(Ap.handle, int(srcs[b]), lv1, pa1, nl, 0, stream)
+        if b == 0:
+            run()
+        t_seq += _events_ms(run, stream, 1)
+        same &= bool(torch.equal(lv1, lv[b * A.n:(b + 1) * A.n]) and torch.equal(pa1, pa[b * A.n:(b + 1) * A.n]))
+    out["msbfs"] = {"batched_ms": t_ms, "sequential_ms": t_seq, "speedup": t_seq / t_ms,
+                    "tuned_lanes": tuned[0], "tuned_schedule": tuned[1], "identical_results": same}
+    del lv, pa
+
+    # ACL from 256 seeds vs one seed at a time
+    alpha, eps = 0.15, 1e-6
+    p = torch.empty(B * A.n, dtype=torch.float32, device=dev)
+    r = torch.empty(B * A.n, dtype=torch.float32, device=dev)
+    acl = lambda: S.spmspv_acl(Ap.handle, B, ds, alpha, eps, 100000, p, r, None, 0, stream)
+    acl()
+    t_acl = _events_ms(acl, stream, 2)
+    tuned = S.spmspv_last_tuned(Ap.handle)
+    mass = float((p.view(B, -1).double().sum(1) + r.view(B, -1).double().sum(1) - 1).abs().max())
+    p1 = torch.empty(A.n, dtype=torch.float32, device=dev)
+    r1 = torch.empty(A.n, dtype=torch.float32, device=dev)
+    t_seq = 0.0
+    l1 = 0.0
+    nseq = 32  # one seed at a time on a sample of the seeds, scaled to B
+    for b in range(nseq):
+        one = lambda: S.spmspv_acl(Ap.handle, 1, ds[b:b + 1], alpha, eps, 100000, p1, r1, None, 1, stream)
+        if b == 0:
+            one()
+        t_seq += _events_ms(one, stream, 1)
+        l1 = max(l1, float((p1 - p[b * A.n:(b + 1) * A.n]).abs().sum()))
+    out["acl"] = {"alpha": alpha, "eps": eps, "batched_ms": t_acl,
+                  "sequential_ms_scaled": t_seq * B / nseq, "sequential_sample": nseq,
+                  "speedup": t_seq * B / nseq / t_acl, "tuned_lanes": tuned[0],
+                  "tuned_schedule": tuned[1], "max_mass_error": mass, "max_l1_p_vs_single": l1}
+    Ap.close()
+    return out
+
+
 def reference_arm(args, rank):
     if rank != 0:
         return
@@ -169,6 +367,8 @@ def main():
     ap.add_argument("--nnz-x", type=int, default=F)
     ap.add_argument("--kernels-only", action="store_true",
                     help="warm-up and timed steps only (for profiler captures)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the BFS (fixed vs learned) and batched measurements")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -299,6 +499,20 @@ def main():
         cpu = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                "sample": "%d full calls of the workload (%.1f s)" % (calls, tt)}
 
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        import synth
+        params = selector_params()
+        extras["bfs_rmat"] = bench_bfs(S, A, dev, stream, "rmat s%d ef16 seed 1" % args.scale,
+                                       synth.sources(A.colptr, 64, seed=2), params)
+        del Ad
+        G = synth.grid3d(256, 256, 256, 0.05, seed=3)
+        extras["bfs_grid"] = bench_bfs(S, G, dev, stream, "grid 256^3 7-point, 5% edges removed",
+                                       [128 * 65536 + 128 * 256 + 128], params, pt_frontiers=True)
+        del G
+        extras["batched"] = bench_batched(S, dev, stream)
+        extras["selector_weights"] = "trained" if params is not None else "absent (AUTO not run)"
+
     line = {
         "metric": METRIC, "value": gteps, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -320,9 +534,11 @@ def main():
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
     }
+    line.update(extras)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    Ad.close()
+    if not extras:
+        Ad.close()
     if world > 1:
         dist.destroy_process_group()
 

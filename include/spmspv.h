@@ -277,6 +277,9 @@ int spmspv_selector_get(spmspv_handle* h, float* params, int32_t n);
 /* The 6 selector features of the handle's last call (host out; synchronises). */
 int spmspv_last_features(spmspv_handle* h, float* feats);
 
+/* The plain fixed schedule: what spmspv_run uses without SPMSPV_SCHED_FORCE or
+ * SPMSPV_SCHED_AUTO, and the AUTO fallback before weights are set. */
+int spmspv_default_schedule(spmspv_handle* h, int32_t* sched);
 /* Schedule id the selector chose in the handle's last SPMSPV_SCHED_AUTO call, or
  * the id of the last forced schedule (host out; synchronises). */
 int spmspv_last_schedule(spmspv_handle* h, int32_t* sched);

@@ -720,24 +720,26 @@ cudaError_t launch_relabel_hubs(const Matrix& A, const int32_t* hub_of_row, int3
   return cudaGetLastError();
 }
 
-// Flags a column whose row ids do not strictly ascend.
+// Flags a column whose row ids do not strictly ascend: one warp per column,
+// lanes compare neighbouring entries 32 apart (coalesced).
 __global__ void k_rows_unsorted(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
                                 int32_t n, int32_t* __restrict__ unsorted) {
-  for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  bool bad = false;
+  for (int64_t j = warp; j < n; j += nwarps) {
     const int32_t p1 = colptr[j + 1];
-    for (int32_t p = colptr[j] + 1; p < p1; ++p)
-      if (rowidx[p] <= rowidx[p - 1]) {
-        atomicOr(unsorted, 1);
-        break;
-      }
+    for (int32_t p = colptr[j] + 1 + lane; p < p1; p += 32) bad |= rowidx[p] <= rowidx[p - 1];
   }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(unsorted, 1);
 }
 
 cudaError_t launch_rows_unsorted(const Matrix& A, int32_t* unsorted, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  k_rows_unsorted<<<sms * 4, 256, 0, s>>>(A.colptr, A.rowidx, A.n, unsorted);
+  k_rows_unsorted<<<sms * 8, 256, 0, s>>>(A.colptr, A.rowidx, A.n, unsorted);
   return cudaGetLastError();
 }
 

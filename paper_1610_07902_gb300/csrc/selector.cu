@@ -400,3 +400,11 @@ extern "C" int spmspv_selector_train(spmspv_handle* h, const float* feats, const
   cudaFree(order);
   return e == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "selector training");
 }
+
+extern "C" int spmspv_default_schedule(spmspv_handle* h, int32_t* sched) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!sched) return fail(SPMSPV_ERR_ARG, "sched is NULL");
+  *sched = h->default_sched;
+  return SPMSPV_OK;
+}

@@ -26,14 +26,11 @@ from . import spmspv as S
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_weights.json")
 
 
-def bfs_levels(colptr, rowidx, src):
-    """Levels of a BFS from src (host, for building replay frontiers)."""
-    import scipy.sparse as sp
-    import scipy.sparse.csgraph as csg
-    n = colptr.shape[0] - 1
-    G = sp.csc_matrix((np.ones(rowidx.shape[0], np.int8), rowidx, colptr), shape=(n, n))
-    d = csg.shortest_path(G.T, method="D", unweighted=True, indices=int(src))
-    return np.where(np.isinf(d), -1, d).astype(np.int32)
+def bfs_levels(Ad, src):
+    """Levels of a BFS from src, computed by the library's own BFS (only used
+    to build the frontiers that the timing replays)."""
+    level, _, _ = Ad.bfs(int(src))
+    return level.cpu().numpy()
 
 
 def time_call(fn, reps):
@@ -61,7 +58,7 @@ def collect(Ad, A, sources, reps=3, max_levels=64, rng=None):
     y_val = torch.empty(cap, dtype=torch.int32, device=dev)
     nz = torch.zeros(1, dtype=torch.int32, device=dev)
     for src in sources:
-        lev = bfs_levels(A.colptr, A.rowidx, src)
+        lev = bfs_levels(Ad, src)
         nl = int(lev.max()) + 1
         levels = list(range(nl))
         if len(levels) > max_levels:
@@ -114,19 +111,137 @@ def load(path=WEIGHTS):
 
 
 TRAINING_GRAPHS = [
-    ("rmat16", ("rmat", 16, 11)), ("rmat18", ("rmat", 18, 12)), ("rmat20", ("rmat", 20, 13)),
+    ("rmat16", ("rmat", 16, 11)), ("rmat17", ("rmat", 17, 14)), ("rmat18", ("rmat", 18, 12)),
+    ("rmat19", ("rmat", 19, 15)), ("rmat20", ("rmat", 20, 13)), ("rmat21", ("rmat", 21, 16)),
     ("grid2d_512", ("grid", (512, 512, 1))), ("grid2d_1024", ("grid", (1024, 1024, 1))),
+    ("grid2d_2048", ("grid", (2048, 2048, 1))),
     ("grid3d_64", ("grid", (64, 64, 64))), ("grid3d_128", ("grid", (128, 128, 128))),
+    ("grid3d_161", ("grid", (161, 161, 161))),
 ]
+
+# held out from training: a larger R-MAT and a larger 3D grid
+EVAL_GRAPHS = [("rmat23", ("rmat", 23, 21)), ("grid3d_320", ("grid", (320, 320, 320)))]
+EVAL_GRAPHS_SMALL = [("rmat22", ("rmat", 22, 21)), ("grid3d_256", ("grid", (256, 256, 256)))]
+
+
+def make_graph(spec):
+    import synth
+    if spec[0] == "rmat":
+        return synth.rmat(spec[1], seed=spec[2], values=False)
+    return synth.grid3d(*spec[1], 0.05, seed=3, values=False)
 
 
 def training_graphs():
-    import synth
     for name, spec in TRAINING_GRAPHS:
-        if spec[0] == "rmat":
-            yield name, synth.rmat(spec[1], seed=spec[2])
-        else:
-            yield name, synth.grid3d(*spec[1], 0.05, seed=3)
+        yield name, make_graph(spec)
+
+
+def time_bfs(Ad, src, opts, reps=3):
+    """Device time (ms) of one whole spmspv_bfs (graph-captured level loop)."""
+    dev = Ad.colptr.device
+    level = torch.empty(Ad.n, dtype=torch.int32, device=dev)
+    parent = torch.empty(Ad.n, dtype=torch.int32, device=dev)
+    nl = torch.zeros(1, dtype=torch.int32, device=dev)
+    fn = lambda: S.spmspv_bfs(Ad.handle, int(src), level, parent, nl, opts)
+    fn()
+    return time_call(fn, reps), level, parent
+
+
+def evaluate(Ad, A, sources, params, reps=3, max_levels=48, rng=None):
+    """Held-out evaluation of the trained selector on one graph.
+
+    Per call (replayed BFS levels): regret t/t_best - 1 of the schedule the
+    network picks (t from the same table), of the AUTO call as run (network
+    inference included) and of the fixed default schedule.  Per BFS: total
+    device time under the default schedule, AUTO, and the best single fixed
+    schedule (the autotuned fixed choice), with levels and parents checked
+    identical across all of them.
+    """
+    rng = rng or np.random.default_rng(0)
+    S.spmspv_selector_set(Ad.handle, params)
+    default = S.spmspv_default_schedule(Ad.handle)
+    dev = Ad.colptr.device
+    cap = A.m
+    y_idx = torch.empty(cap, dtype=torch.int32, device=dev)
+    y_val = torch.empty(cap, dtype=torch.int32, device=dev)
+    nz = torch.zeros(1, dtype=torch.int32, device=dev)
+    pick_regret, auto_regret, fixed_regret, picks = [], [], [], []
+    for src in sources:
+        lev = bfs_levels(Ad, src)
+        nl = int(lev.max()) + 1
+        levels = list(range(nl))
+        if len(levels) > max_levels:
+            levels = sorted(rng.choice(nl, size=max_levels, replace=False).tolist())
+        for L in levels:
+            front = np.flatnonzero(lev == L).astype(np.int32)
+            if front.size == 0:
+                continue
+            rng.shuffle(front)
+            visited = ((lev >= 0) & (lev <= L)).astype(np.uint8)
+            bits = np.packbits(np.pad(visited, (0, (-A.m) % 32)), bitorder="little").view("<u4")
+            xi = torch.from_numpy(front).to(dev)
+            mk = torch.from_numpy(bits.astype(np.uint32).view(np.int32)).to(dev)
+            call = lambda o: (lambda: S.spmspv_run(Ad.handle, S.SPMSPV_MIN_SELECT2ND_I32, xi, xi,
+                                                   front.size, mk, S.SPMSPV_MASK_COMPLEMENT | o,
+                                                   y_idx, y_val, cap, nz))
+            t = np.full(12, np.inf)
+            for sched in range(12):
+                fn = call(S.SPMSPV_SCHED_OPT(sched))
+                fn()
+                t[sched] = time_call(fn, reps)
+            fa = call(S.SPMSPV_SCHED_AUTO)
+            fa()
+            ta = time_call(fa, reps)
+            pick = S.spmspv_last_schedule(Ad.handle)
+            best = t.min()
+            picks.append(pick)
+            pick_regret.append(t[pick] / best - 1)
+            auto_regret.append(ta / best - 1)
+            fixed_regret.append(t[default] / best - 1)
+    q = lambda v: {"mean": float(np.mean(v)), "median": float(np.median(v)),
+                   "p90": float(np.percentile(v, 90)), "max": float(np.max(v))}
+    per_call = {"calls": len(picks), "picked_schedule": q(pick_regret),
+                "auto_as_run": q(auto_regret), "fixed_default": q(fixed_regret),
+                "pick_histogram": np.bincount(picks, minlength=12).tolist()}
+    totals = {"fixed_default": 0.0, "auto": 0.0}
+    per_sched = np.zeros(12)
+    identical = True
+    for src in sources:
+        tf, lf, pf = time_bfs(Ad, src, S.SPMSPV_SCHED_OPT(default), reps)
+        ta, la, pa = time_bfs(Ad, src, S.SPMSPV_SCHED_AUTO, reps)
+        identical &= bool(torch.equal(lf, la) and torch.equal(pf, pa))
+        totals["fixed_default"] += tf
+        totals["auto"] += ta
+        for sched in range(12):
+            ts, ls, ps = time_bfs(Ad, src, S.SPMSPV_SCHED_OPT(sched), reps)
+            identical &= bool(torch.equal(lf, ls) and torch.equal(pf, ps))
+            per_sched[sched] += ts
+    best_fixed = int(np.argmin(per_sched))
+    totals.update({"best_fixed_schedule": best_fixed, "best_fixed": float(per_sched[best_fixed]),
+                   "per_schedule": per_sched.tolist(), "sources": len(sources),
+                   "identical_results": identical,
+                   "auto_vs_fixed_default": totals["fixed_default"] / totals["auto"],
+                   "auto_vs_best_fixed": float(per_sched[best_fixed]) / totals["auto"]})
+    return {"per_call_regret": per_call, "bfs_total_ms": totals, "default_schedule": default}
+
+
+def main_evaluate(args):
+    import synth
+    params, meta = load(args.weights)
+    out = {"weights": os.path.basename(args.weights), "trained_on": meta.get("graphs"), "graphs": {}}
+    for name, spec in (EVAL_GRAPHS_SMALL if args.small else EVAL_GRAPHS):
+        t0 = time.time()
+        A = make_graph(spec)
+        Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
+        r = evaluate(Ad, A, synth.sources(A.colptr, args.sources, seed=7), params)
+        r.update({"n": int(A.n), "nnz": int(A.nnz)})
+        out["graphs"][name] = r
+        print("%-12s %s (%.0f s)" % (name, json.dumps(r["bfs_total_ms"]), time.time() - t0),
+              file=sys.stderr)
+        Ad.close()
+        del A
+    with open(args.eval_out, "w") as fh:
+        json.dump(out, fh, indent=1)
 
 
 def main():
@@ -135,8 +250,16 @@ def main():
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--sources", type=int, default=2)
     ap.add_argument("--epochs", type=int, default=400)
+    ap.add_argument("--evaluate", action="store_true",
+                    help="evaluate --weights on the held-out graphs instead of training")
+    ap.add_argument("--weights", default=WEIGHTS)
+    ap.add_argument("--eval-out", default="selector_eval.json")
+    ap.add_argument("--small", action="store_true", help="held-out graphs one size smaller")
     args = ap.parse_args()
     S.load()
+    if args.evaluate:
+        main_evaluate(args)
+        return
     F, T, V = [], [], []
     t0 = time.time()
     last = None

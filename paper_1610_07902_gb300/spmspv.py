@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
         lib.spmspv_selector_get.argtypes = [_P, _P, ctypes.c_int32]
         lib.spmspv_last_features.argtypes = [_P, _P]
         lib.spmspv_last_schedule.argtypes = [_P, ctypes.POINTER(ctypes.c_int32)]
+        lib.spmspv_default_schedule.argtypes = [_P, ctypes.POINTER(ctypes.c_int32)]
         lib.spmspv_selector_train.argtypes = [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, _P]
         lib.spmspv_selector_grad.argtypes = [_P, _P, _P, _P, ctypes.c_int32, _P, _P]
@@ -251,6 +252,12 @@ def spmspv_tune_set(h, key, lanes, sched):
 
 def spmspv_tune_clear(h):
     _check(load().spmspv_tune_clear(h), "spmspv_tune_clear")
+
+
+def spmspv_default_schedule(h) -> int:
+    v = ctypes.c_int32(0)
+    _check(load().spmspv_default_schedule(h, ctypes.byref(v)), "spmspv_default_schedule")
+    return int(v.value)
 
 
 def spmspv_selector_train(h, feats, target, valid, n, epochs, batch, lr, seed):
