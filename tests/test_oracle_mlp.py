@@ -45,3 +45,38 @@ def test_choose_respects_allow_pull():
     p, feats, _, _ = random_problem(4, n=50)
     c = mlp.choose(p, feats, allow_pull=False)
     assert np.all(c < 6)
+
+
+def test_forward_on_hand_worked_weights():
+    # one path through the network: x -> h1[2] = relu(x0) -> h2[1] = relu(2 h1[2] - 1)
+    # -> out[r] = r * h2[1] + b3[r]; the input is normalised as (f - mean) * scale
+    p = np.zeros(mlp.NPARAM)
+    W1 = p[mlp.O_W1:mlp.O_B1].reshape(mlp.H, mlp.IN)
+    W2 = p[mlp.O_W2:mlp.O_B2].reshape(mlp.H, mlp.H)
+    W3 = p[mlp.O_W3:mlp.O_B3].reshape(mlp.OUT, mlp.H)
+    W1[2, 0] = 1.0
+    W2[1, 2] = 2.0
+    p[mlp.O_B2 + 1] = -1.0
+    W3[:, 1] = np.arange(mlp.OUT)
+    p[mlp.O_B3:mlp.NWEIGHT] = 0.5
+    p[mlp.O_MEAN:mlp.O_SCALE] = 1.0
+    p[mlp.O_SCALE:mlp.NPARAM] = 0.5
+    feats = np.array([[4.0, 9, 9, 9, 9, 9],     # x0 = (4-1)*0.5 = 1.5 -> h2[1] = 2
+                      [-5.0, 9, 9, 9, 9, 9]])   # x0 = -3 -> h1 = 0 -> h2 = relu(-1) = 0
+    out, _ = mlp.forward(p, feats)
+    np.testing.assert_allclose(out[0], 2.0 * np.arange(mlp.OUT) + 0.5, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(out[1], np.full(mlp.OUT, 0.5), rtol=0, atol=0)
+    # squared error against target 0 on outputs 0 and 3 only: 0.5^2 + 6.5^2
+    target = np.zeros((1, mlp.OUT))
+    valid = np.zeros((1, mlp.OUT), np.uint8)
+    valid[0, [0, 3]] = 1
+    loss, _ = mlp.loss_and_grad(p, feats[:1], target, valid)
+    assert abs(loss - (0.25 + 42.25)) < 1e-12
+
+
+def test_invalid_outputs_do_not_reach_loss_or_gradient():
+    p, feats, target, valid = random_problem(5)
+    l0, g0 = mlp.loss_and_grad(p, feats, target, valid)
+    t2 = np.where(valid > 0, target, 1e6)
+    l1, g1 = mlp.loss_and_grad(p, feats, t2, valid)
+    assert l0 == l1 and np.array_equal(g0, g1)
