@@ -199,7 +199,6 @@ int select_hot_rows(spmspv_handle* h) {
   return SPMSPV_OK;
 }
 
-cudaError_t launch_selector(spmspv_handle* h, int allow_pull, cudaStream_t s);
 cudaError_t launch_pull(const spmspv_handle* h, int sem, bool bfs, const int32_t* x_idx,
                         const uint32_t* x_val, int f, const int32_t* f_dev, const uint32_t* mask,
                         int mask_comp, int early_exit, int32_t* y_idx, uint32_t* y_val,
@@ -217,11 +216,15 @@ int run_auto(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_
   int k1_grid = (int)std::max<int64_t>(1, std::min<int64_t>(h->k1_grid_max, ((int64_t)f + K1_TILE - 1) / K1_TILE));
   if (mask) k1_grid = std::max(k1_grid, mask_pass_grid(h));
   prof_call_begin(h, s);
+  // the work scan's last CTA runs the selector (no launch of its own)
+  SelArgs sa{};
+  sa.w = h->sel_w;
+  sa.allow_pull = can_pull;
+  sa.lwb_lo = h->lwb_lo;
   cudaError_t e = launch_k1(sem, h->A, h->ws, h->nb_fine, x_idx, x_val, f, nullptr, k1_grid, nullptr, s,
-                            mask);
+                            mask, &sa);
   if (e != cudaSuccess) return cuda_fail(e, "work scan launch");
   prof_mark(h, SPMSPV_STAGE_SCAN, s);
-  if ((e = launch_selector(h, can_pull, s)) != cudaSuccess) return cuda_fail(e, "selector launch");
   prof_mark(h, SPMSPV_STAGE_SELECT, s);
   e = launch_k2(sem, h->A, h->ws, h->lwb_lo, h->nb_fine, mask, mask_comp, h->k2_grid, h->k2_smem, s,
                 can_pull);
@@ -312,8 +315,10 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
   size_t o_hs = take(sizeof(int32_t) * ((size_t)h->nb_fine + 1));
   size_t o_hv = take(sizeof(uint32_t) * HOT_MAX);
   size_t o_ht = take(sizeof(uint32_t) * HOT_MAX);
-  size_t o_br = take(sizeof(uint16_t) * (size_t)(nnz > 0 ? nnz : 1));
-  size_t o_bv = take(sizeof(uint32_t) * (size_t)(nnz > 0 ? nnz : 1));
+  // bucket payload, padded to whole 8-entry chunks (K3 reads it 16 bytes at a time)
+  const size_t nbe = (size_t)((nnz > 0 ? nnz : 1) + 7) / 8 * 8;
+  size_t o_br = take(sizeof(uint16_t) * nbe);
+  size_t o_bv = take(sizeof(uint32_t) * nbe);
   const size_t zero_bytes = o_br;  // everything before the bucket payload starts zeroed
   h->ws_bytes = off;
   cudaError_t e = cudaMalloc(&h->ws_base, h->ws_bytes);

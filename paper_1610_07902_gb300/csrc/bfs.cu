@@ -26,9 +26,6 @@ cudaError_t launch_pull(const spmspv_handle* h, int sem, bool bfs, const int32_t
                         int32_t y_cap, int32_t* d_nnz_y, uint32_t* visited, int only_pull,
                         cudaStream_t s);
 int pull_available(const spmspv_handle* h, int sem);
-cudaError_t launch_selector(spmspv_handle* h, int allow_pull, cudaStream_t s);
-cudaError_t launch_selector_cond(spmspv_handle* h, int allow_pull, cudaGraphConditionalHandle c_push,
-                                 cudaGraphConditionalHandle c_pull, cudaStream_t s);
 
 namespace {
 
@@ -111,8 +108,8 @@ static int capture_if_with(cudaStream_t s, cudaStream_t side, cudaGraphCondition
 
 // One BFS level on `s` (captured into the loop body).  A fixed schedule
 // launches its direction's kernels; the learned schedule launches the work
-// scan and the selector, then two IF nodes (push, pull) of which the
-// selector enables one.
+// scan, whose last CTA runs the selector, then two IF nodes (push, pull) of
+// which the selector enables one.
 static int bfs_level_launches(spmspv_handle* h, int sched, cudaGraphConditionalHandle cond,
                               cudaStream_t s, cudaStream_t side) {
   const bool autos = sched < 0;
@@ -122,30 +119,42 @@ static int bfs_level_launches(spmspv_handle* h, int sched, cudaGraphConditionalH
     sc.dir = 0;
     sc.id %= 6;
   }
-  cudaError_t e = launch_k1_bfs(h->A, h->ws, h->nb_fine, h->bfs_front, &h->ws.st->nnz_y,
-                                h->k1_grid_max, autos ? nullptr : &sc, s,
-                                autos ? h->bfs_visited : nullptr);
-  if (e != cudaSuccess) return cuda_fail(e, "bfs work scan");
+  cudaError_t e;
   int rc = SPMSPV_OK;
   if (!autos) {
+    if ((e = launch_k1_bfs(h->A, h->ws, h->nb_fine, h->bfs_front, &h->ws.st->nnz_y, h->k1_grid_max, &sc,
+                           s, nullptr)) != cudaSuccess)
+      return cuda_fail(e, "bfs work scan");
     rc = sc.dir == 0 ? bfs_push_launches(h, sc, sc.lwb, s) : bfs_pull_launches(h, s);
-  } else if (!can_pull) {
-    if ((e = launch_selector(h, 0, s)) != cudaSuccess) return cuda_fail(e, "bfs selector");
-    rc = bfs_push_launches(h, sc, h->lwb_lo + 2, s);
   } else {
-    // both IF handles exist before the selector that sets them is captured
-    cudaGraphConditionalHandle c_push = 0, c_pull = 0;
-    cudaStreamCaptureStatus cst;
-    cudaGraph_t cg = nullptr;
-    if ((e = cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, nullptr, nullptr, nullptr)) != cudaSuccess)
-      return cuda_fail(e, "capture info");
-    if ((e = cudaGraphConditionalHandleCreate(&c_push, cg, 0, cudaGraphCondAssignDefault)) != cudaSuccess ||
-        (e = cudaGraphConditionalHandleCreate(&c_pull, cg, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
-      return cuda_fail(e, "if handles");
-    if ((e = launch_selector_cond(h, 1, c_push, c_pull, s)) != cudaSuccess) return cuda_fail(e, "bfs selector");
-    rc = capture_if_with(s, side, c_push, [&](cudaStream_t ss) { return bfs_push_launches(h, sc, h->lwb_lo + 2, ss); });
-    if (rc == SPMSPV_OK)
-      rc = capture_if_with(s, side, c_pull, [&](cudaStream_t ss) { return bfs_pull_launches(h, ss); });
+    // the work scan's last CTA runs the selector; the visited count stands
+    // in for a pass over the visited bitmap
+    SelArgs sa{};
+    sa.w = h->sel_w;
+    sa.allow_pull = can_pull;
+    sa.bfs = 1;
+    sa.lwb_lo = h->lwb_lo;
+    if (can_pull) {
+      // both IF handles exist before the kernel that sets them is captured
+      cudaStreamCaptureStatus cst;
+      cudaGraph_t cg = nullptr;
+      if ((e = cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, nullptr, nullptr, nullptr)) != cudaSuccess)
+        return cuda_fail(e, "capture info");
+      if ((e = cudaGraphConditionalHandleCreate(&sa.c_push, cg, 0, cudaGraphCondAssignDefault)) != cudaSuccess ||
+          (e = cudaGraphConditionalHandleCreate(&sa.c_pull, cg, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return cuda_fail(e, "if handles");
+      sa.use_cond = 1;
+    }
+    if ((e = launch_k1_bfs(h->A, h->ws, h->nb_fine, h->bfs_front, &h->ws.st->nnz_y, h->k1_grid_max,
+                           nullptr, s, nullptr, &sa)) != cudaSuccess)
+      return cuda_fail(e, "bfs work scan");
+    if (!can_pull) {
+      rc = bfs_push_launches(h, sc, h->lwb_lo + 2, s);
+    } else {
+      rc = capture_if_with(s, side, sa.c_push, [&](cudaStream_t ss) { return bfs_push_launches(h, sc, h->lwb_lo + 2, ss); });
+      if (rc == SPMSPV_OK)
+        rc = capture_if_with(s, side, sa.c_pull, [&](cudaStream_t ss) { return bfs_pull_launches(h, ss); });
+    }
   }
   if (rc != SPMSPV_OK) return rc;
   k_bfs_continue<<<1, 32, 0, s>>>(cond, h->ws.st, h->A.n);

@@ -28,6 +28,7 @@
 #include <stdint.h>
 
 #include "device_util.cuh"
+#include "selector_dev.cuh"
 #include "spmspv_internal.cuh"
 
 namespace spmspv {
@@ -46,8 +47,10 @@ __global__ void __launch_bounds__(K1_THREADS)
 k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int32_t* f_dev,
              const int32_t* __restrict__ colptr, int32_t n,
              int64_t nnz, Workspace ws, int nb_fine, int sem, int forced, int f_dir, int f_q,
-             int f_lwb, int bfs_level_inc, const uint32_t* __restrict__ mask, int32_t m) {
+             int f_lwb, int bfs_level_inc, const uint32_t* __restrict__ mask, int32_t m,
+             SelArgs sel) {
   __shared__ int32_t s_deg[K1_SMEM_WORDS];
+  __shared__ int s_last;
   __shared__ int32_t s_c0[K1_SMEM_WORDS];
   __shared__ uint32_t s_xv[K1_SMEM_WORDS];
   __shared__ unsigned long long s_warp[K1_THREADS / 32 + 1];
@@ -221,15 +224,30 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
     atomicMax(&st->maxdeg, s_maxdeg);
     atomicAdd(&st->sumdeg2, s_sq);
   }
+  if (sel.w) {
+    // the last CTA to finish sees every CTA's counts and runs the selector
+    if (tid == 0) {
+      __threadfence();
+      s_last = atomicAdd(&st->k1_done, 1u) == gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      if (tid < 32) sel_choose_warp(sel.w, st, m, n, nnz, sel);
+      if (tid == 0) st->k1_done = 0u;
+    }
+  }
 }
 
 cudaError_t launch_k1(int sem, const Matrix& A, const Workspace& ws, int nb_fine,
                       const int32_t* x_idx, const uint32_t* x_val, int f, const int32_t* f_dev,
-                      int grid, const Sched* forced, cudaStream_t s, const uint32_t* mask) {
+                      int grid, const Sched* forced, cudaStream_t s, const uint32_t* mask,
+                      const SelArgs* sel) {
+  SelArgs none{};
   k1_work_scan<<<grid, K1_THREADS, 0, s>>>(x_idx, x_val, f, f_dev, A.colptr, A.n, A.nnz, ws, nb_fine,
                                            sem, forced ? forced->id + 1 : 0, forced ? forced->dir : 0,
                                            forced ? forced->q : 0, forced ? forced->lwb : 0, 0,
-                                           mask, A.m);
+                                           mask, A.m, sel ? *sel : none);
   return cudaGetLastError();
 }
 
@@ -566,29 +584,47 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
         }
       }
       __syncthreads();
-      // Step 2 of Algorithm 1: merge the bucket into the SPA
-      constexpr int U = 8;
-      const uint16_t* brow = ws.brow + base;
-      const uint32_t* bval = ws.bval + base;
-      for (int32_t e0 = tid; e0 < cnt; e0 += K3_THREADS * U) {
-        uint32_t r[U], v[U];
+      // Step 2 of Algorithm 1: merge the bucket into the SPA.  The bucket's
+      // entries [base, base+cnt) are read in aligned 8-entry chunks (one
+      // 16-byte load of row ids, two of values), entries outside the range
+      // masked off; two chunks per thread are in flight at once.
+      {
+        constexpr int U = 2;
+        const int32_t a0 = base, a1 = base + cnt;
+        const int32_t c1 = (a1 + 7) >> 3;
+        const uint4* brow4 = reinterpret_cast<const uint4*>(ws.brow);
+        const uint4* bval4 = reinterpret_cast<const uint4*>(ws.bval);
+        for (int32_t c = (a0 >> 3) + tid; c < c1; c += K3_THREADS * U) {
+          uint4 rv[U], va[U], vb[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int32_t e = e0 + u * K3_THREADS;
-          r[u] = 0xffffffffu;
-          v[u] = 0u;
-          if (e < cnt) {
-            r[u] = __ldcs(brow + e) & wmask;
-            if (SEM != kOrAnd) v[u] = __ldcs(bval + e);
+          for (int u = 0; u < U; ++u) {
+            const int32_t cc = c + u * K3_THREADS;
+            rv[u] = make_uint4(0u, 0u, 0u, 0u);
+            va[u] = rv[u];
+            vb[u] = rv[u];
+            if (cc < c1) {
+              rv[u] = __ldcs(brow4 + cc);
+              if (SEM != kOrAnd) {
+                va[u] = __ldcs(bval4 + 2 * cc);
+                vb[u] = __ldcs(bval4 + 2 * cc + 1);
+              }
+            }
           }
-        }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const uint32_t rr = r[u];
-          if (rr == 0xffffffffu) continue;
-          const uint32_t bit = 1u << (rr & 31);
-          if (!(occ[rr >> 5] & bit)) atomicOr(occ + (rr >> 5), bit);
-          spa_apply<SEM>(spa, rr, v[u]);
+          for (int u = 0; u < U; ++u) {
+            const int32_t e0 = (c + u * K3_THREADS) << 3;
+            const uint32_t rw[4] = {rv[u].x, rv[u].y, rv[u].z, rv[u].w};
+            const uint32_t vw[8] = {va[u].x, va[u].y, va[u].z, va[u].w, vb[u].x, vb[u].y, vb[u].z, vb[u].w};
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int32_t e = e0 + j;
+              if (e < a0 || e >= a1) continue;
+              const uint32_t rr = ((j & 1) ? (rw[j >> 1] >> 16) : (rw[j >> 1] & 0xffffu)) & wmask;
+              const uint32_t bit = 1u << (rr & 31);
+              if (!(occ[rr >> 5] & bit)) atomicOr(occ + (rr >> 5), bit);
+              spa_apply<SEM>(spa, rr, vw[j]);
+            }
+          }
         }
       }
       // hub rows of this bucket: their products were combined in K2
@@ -823,11 +859,12 @@ namespace spmspv {
 // parent id), the count comes from the device, and the level advances.
 cudaError_t launch_k1_bfs(const Matrix& A, const Workspace& ws, int nb_fine, const int32_t* x_idx,
                           const int32_t* f_dev, int grid, const Sched* sc, cudaStream_t s,
-                          const uint32_t* mask) {
+                          const uint32_t* mask, const SelArgs* sel) {
+  SelArgs none{};
   k1_work_scan<<<grid, K1_THREADS, 0, s>>>(x_idx, reinterpret_cast<const uint32_t*>(x_idx), 0,
                                            f_dev, A.colptr, A.n, A.nnz, ws, nb_fine, kMinSelect2nd,
                                            sc ? sc->id + 1 : 0, sc ? sc->dir : 0, sc ? sc->q : 0,
-                                           sc ? sc->lwb : 0, 1, mask, A.m);
+                                           sc ? sc->lwb : 0, 1, mask, A.m, sel ? *sel : none);
   return cudaGetLastError();
 }
 }  // namespace spmspv

@@ -21,88 +21,11 @@
 #include <vector>
 
 #include "handle.cuh"
+#include "selector_dev.cuh"
 #include "spmspv_internal.cuh"
 
 namespace spmspv {
 
-constexpr int SEL_IN = 6, SEL_H = 32, SEL_OUT = 12;
-constexpr int SEL_OW1 = 0, SEL_OB1 = SEL_OW1 + SEL_H * SEL_IN, SEL_OW2 = SEL_OB1 + SEL_H,
-              SEL_OB2 = SEL_OW2 + SEL_H * SEL_H, SEL_OW3 = SEL_OB2 + SEL_H,
-              SEL_OB3 = SEL_OW3 + SEL_OUT * SEL_H, SEL_NWEIGHT = SEL_OB3 + SEL_OUT;  // 1676
-constexpr int SEL_OMEAN = SEL_NWEIGHT, SEL_OSCALE = SEL_OMEAN + SEL_IN, SEL_NPARAM = SEL_OSCALE + SEL_IN;
-static_assert(SEL_NWEIGHT == 1676, "MLP size");
-
-// One warp evaluates the network for one normalised input; lane j holds
-// hidden unit j.  Returns the prediction of output `lane` (lanes < 12).
-__device__ __forceinline__ float sel_forward_warp(const float* __restrict__ w, const float* xin,
-                                                  float* h1o, float* h2o) {
-  const int lane = threadIdx.x & 31;
-  float a1 = w[SEL_OB1 + lane];
-#pragma unroll
-  for (int k = 0; k < SEL_IN; ++k) a1 += w[SEL_OW1 + lane * SEL_IN + k] * xin[k];
-  const float h1 = fmaxf(a1, 0.f);
-  float a2 = w[SEL_OB2 + lane];
-#pragma unroll
-  for (int k = 0; k < SEL_H; ++k) a2 += w[SEL_OW2 + lane * SEL_H + k] * __shfl_sync(0xffffffffu, h1, k);
-  const float h2 = fmaxf(a2, 0.f);
-  float o = 0.f;
-  const int r = lane < SEL_OUT ? lane : 0;
-  o = w[SEL_OB3 + r];
-#pragma unroll
-  for (int k = 0; k < SEL_H; ++k) o += w[SEL_OW3 + r * SEL_H + k] * __shfl_sync(0xffffffffu, h2, k);
-  if (h1o) *h1o = h1;
-  if (h2o) *h2o = h2;
-  return o;
-}
-
-__device__ __forceinline__ void sel_features(const DevState* st, int32_t m, int32_t n, int64_t nnz,
-                                             float* x) {
-  const float f = (float)st->f, W = (float)st->W, fc = (float)max(st->fc, 1);
-  x[0] = log2f(1.f + f);
-  x[1] = log2f(1.f + W);
-  x[2] = W > 0.f ? (float)st->maxdeg * fc / W : 0.f;
-  x[3] = (float)st->maskcnt / (float)m;
-  x[4] = log2f((float)m);
-  x[5] = (float)((double)nnz / (double)n);
-}
-
-// Device-side choice for this call: features -> MLP -> argmin over the
-// allowed schedules -> state (direction, quantum, bucket width).  Inside a
-// graph, the two conditional handles (when given) select the push or the pull
-// branch of the level.
-__global__ void k_selector(const float* __restrict__ w, DevState* st, int32_t m, int32_t n,
-                           int64_t nnz, int lwb_lo, int allow_pull, int use_cond,
-                           cudaGraphConditionalHandle c_push, cudaGraphConditionalHandle c_pull) {
-  float x[SEL_IN];
-  sel_features(st, m, n, nnz, x);
-#pragma unroll
-  for (int k = 0; k < SEL_IN; ++k) x[k] = (x[k] - w[SEL_OMEAN + k]) * w[SEL_OSCALE + k];
-  const float o = sel_forward_warp(w, x, nullptr, nullptr);
-  const int lane = threadIdx.x & 31;
-  const bool ok = lane < SEL_OUT && (allow_pull || lane < 6);
-  float best = ok ? o : INFINITY;
-  int bi = ok ? lane : 64;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const float ob = __shfl_xor_sync(0xffffffffu, best, off);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-    if (ob < best || (ob == best && oi < bi)) {
-      best = ob;
-      bi = oi;
-    }
-  }
-  if (lane == 0) {
-    const int id = bi < SEL_OUT ? bi : 4;
-    st->sched = id;
-    st->dir = id / 6;
-    st->q = ((id / 3) % 2) ? 2 * QF : QF;
-    st->lwb = lwb_lo + id % 3;
-    if (use_cond) {
-      cudaGraphSetConditional(c_push, id / 6 == 0 ? 1u : 0u);
-      cudaGraphSetConditional(c_pull, id / 6 == 1 ? 1u : 0u);
-    }
-  }
-}
 
 // Training: mean squared error over the valid (sample, schedule) targets.
 // One warp per sample; each lane accumulates the gradient of the weights it
@@ -191,21 +114,6 @@ __global__ void k_sel_adam(float* __restrict__ w, const float* __restrict__ grad
   mom[i] = m1;
   vel[i] = v1;
   w[i] -= lr * (m1 / (1.f - b1t)) / (sqrtf(v1 / (1.f - b2t)) + 1e-8f);
-}
-
-cudaError_t launch_selector(spmspv_handle* h, int allow_pull, cudaStream_t s) {
-  if (!h->sel_w) return cudaErrorInvalidValue;
-  k_selector<<<1, 32, 0, s>>>(h->sel_w, h->ws.st, h->A.m, h->A.n, h->A.nnz, h->lwb_lo, allow_pull,
-                              0, 0, 0);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_selector_cond(spmspv_handle* h, int allow_pull, cudaGraphConditionalHandle c_push,
-                                 cudaGraphConditionalHandle c_pull, cudaStream_t s) {
-  if (!h->sel_w) return cudaErrorInvalidValue;
-  k_selector<<<1, 32, 0, s>>>(h->sel_w, h->ws.st, h->A.m, h->A.n, h->A.nnz, h->lwb_lo, allow_pull,
-                              1, c_push, c_pull);
-  return cudaGetLastError();
 }
 
 static int ensure_sel_buffer(spmspv_handle* h) {

@@ -80,6 +80,21 @@ struct DevState {
   int32_t last_maskcnt;
   int32_t* bfs_level;  // BFS outputs of the current search
   int32_t* bfs_parent;
+  uint32_t k1_done;    // K1 CTAs finished; the last one runs the selector (self-resetting)
+};
+
+// Selector run inside the work scan by its last CTA to finish: weights (NULL:
+// no selection in this launch), whether pull may be chosen, whether the mask
+// is the BFS visited set (its population is then the visited count), and the
+// conditional handles of a graph level (use_cond = 0 outside such graphs).
+struct SelArgs {
+  const float* w;
+  int allow_pull;
+  int bfs;
+  int use_cond;
+  int lwb_lo;
+  cudaGraphConditionalHandle c_push;
+  cudaGraphConditionalHandle c_pull;
 };
 
 // One frontier of a batch, as the batched lanes hand it to the kernels
@@ -145,10 +160,11 @@ struct Sched {
 // Launchers (kernels.cu).  All launches are asynchronous on `s`.
 cudaError_t launch_k1(int sem, const Matrix& A, const Workspace& ws, int nb_fine,
                       const int32_t* x_idx, const uint32_t* x_val, int f, const int32_t* f_dev,
-                      int grid, const Sched* forced, cudaStream_t s, const uint32_t* mask = nullptr);
+                      int grid, const Sched* forced, cudaStream_t s, const uint32_t* mask = nullptr,
+                      const SelArgs* sel = nullptr);
 cudaError_t launch_k1_bfs(const Matrix& A, const Workspace& ws, int nb_fine, const int32_t* x_idx,
                           const int32_t* f_dev, int grid, const Sched* sc, cudaStream_t s,
-                          const uint32_t* mask);
+                          const uint32_t* mask, const SelArgs* sel = nullptr);
 cudaError_t launch_row_degrees(const Matrix& A, int32_t* deg, int32_t* maxdeg, cudaStream_t s);
 cudaError_t launch_rows_unsorted(const Matrix& A, int32_t* unsorted, cudaStream_t s);
 cudaError_t launch_relabel_hubs(const Matrix& A, const int32_t* hub_of_row, int32_t* out,
