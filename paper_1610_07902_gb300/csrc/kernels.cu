@@ -57,7 +57,7 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
   __shared__ unsigned long long s_prefix;
   __shared__ uint32_t s_tile;
   __shared__ int s_maxdeg;
-  __shared__ unsigned long long s_sq;
+  __shared__ int s_maskcnt;
 
   DevState* st = ws.st;
   const int tid = threadIdx.x;
@@ -102,11 +102,10 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
   }
   if (tid == 0) {
     s_maxdeg = 0;
-    s_sq = 0ull;
+    s_maskcnt = 0;
   }
 
   int maxdeg = 0;
-  unsigned long long sq = 0;
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(&st->k1_ticket, 1u);
     __syncthreads();
@@ -161,7 +160,6 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
       const int d = s_deg[k1_pad(tid * K1_ITEMS + i)];
       tsum += (d > 0 ? K1_CNT_ONE : 0ull) + (unsigned long long)d;
       maxdeg = max(maxdeg, d);
-      sq += (unsigned long long)d * (unsigned long long)d;
     }
     unsigned long long btot;
     unsigned long long texcl = block_exclusive_sum<K1_THREADS>(tsum, s_warp, &btot);
@@ -206,8 +204,9 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
     __syncthreads();
   }
   // selector features: degree statistics and the number of masked rows
-  atomicMax(&s_maxdeg, maxdeg);
-  atomicAdd(&s_sq, sq);
+  // one shared atomic per warp (all threads of the block share s_maxdeg)
+  maxdeg = __reduce_max_sync(0xffffffffu, maxdeg);
+  if ((tid & 31) == 0 && maxdeg > 0) atomicMax(&s_maxdeg, maxdeg);
   int32_t mc = 0;
   if (mask) {
     const int32_t words = (m + 31) / 32;
@@ -216,14 +215,12 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
       if (i == words - 1 && (m & 31)) wv &= (1u << (m & 31)) - 1u;
       mc += __popc(wv);
     }
-    for (int o = 16; o > 0; o >>= 1) mc += __shfl_xor_sync(0xffffffffu, mc, o);
-    if ((tid & 31) == 0 && mc) atomicAdd(&st->maskcnt, mc);
+    mc = __reduce_add_sync(0xffffffffu, mc);
+    if ((tid & 31) == 0 && mc) atomicAdd(&s_maskcnt, mc);
   }
   __syncthreads();
-  if (tid == 0 && s_sq != 0ull) {
-    atomicMax(&st->maxdeg, s_maxdeg);
-    atomicAdd(&st->sumdeg2, s_sq);
-  }
+  if (tid == 0 && s_maxdeg > 0) atomicMax(&st->maxdeg, s_maxdeg);
+  if (tid == 0 && s_maskcnt > 0) atomicAdd(&st->maskcnt, s_maskcnt);
   if (sel.w) {
     // the last CTA to finish sees every CTA's counts and runs the selector
     if (tid == 0) {
@@ -271,11 +268,13 @@ __device__ __forceinline__ void spa_apply(uint32_t* spa, uint32_t r, uint32_t v)
 // ------------------------------------------------------------------------
 
 // One tile = q consecutive products (a merge-path slice of the selected
-// columns).  Each warp walks a contiguous chunk of 32*items products with
-// its lanes on consecutive products (coalesced row-id and value loads),
-// advancing the x entry it is in as the product index passes entry
-// boundaries.  Products are counted per bucket with shared-memory atomics,
-// one warp scans the counts, every non-empty bucket gets one run reserved
+// columns).  Each warp takes a contiguous chunk of 32*items products with
+// its lanes on consecutive products (coalesced row-id and value loads).  The
+// x entry of a product comes from a bitmap of the tile's entry starts: the
+// 32 products of one warp load are one bitmap word, so a lane's entry is the
+// count of starts before its word plus a popcount inside the word (no
+// search, no divergence).  Products are counted per bucket with
+// shared-memory atomics, one warp scans the counts, every non-empty bucket gets one run reserved
 // with a global atomic, the products are staged in shared memory grouped by
 // bucket and written out in runs.  Hub rows (row ids >= m in the relabelled
 // row-id array) are summed per tile in shared memory instead.
@@ -291,7 +290,7 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
 
   unsigned char* p = k2_smem_raw;
   uint2* stage = (uint2*)p; p += sizeof(uint2) * QMAX;
-  int32_t* cws = (int32_t*)p; p += sizeof(int32_t) * (QMAX + 2);
+  uint32_t* hbits = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX / 32);  // entry starts of the tile
   int32_t* kbase = (int32_t*)p; p += sizeof(int32_t) * (QMAX + 1);
   uint32_t* kx = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX + 1);
   int32_t* hist = (int32_t*)p; p += sizeof(int32_t) * nb_fine;   // counts, then stage offsets
@@ -318,6 +317,8 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
     }
     for (int i = tid; i < HOT_MAX / 32; i += K2_THREADS) htb[i] = 0u;
   }
+  for (int i = tid; i < QMAX / 32; i += K2_THREADS) hbits[i] = 0u;
+  __syncthreads();
 
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int32_t p0 = t * q;
@@ -329,11 +330,11 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
     for (int l = tid; l < nk; l += K2_THREADS) {
       const int32_t k = k0 + l;
       const int32_t w = ws.cw[k];
-      cws[l] = max(w - p0, 0);
       kbase[l] = ws.cb[k] - w;
       kx[l] = ws.cx[k];
+      const int32_t off = w - p0;  // entries after the first start inside the tile
+      if (l > 0 && off > 0 && off < np) atomicOr(&hbits[off >> 5], 1u << (off & 31));
     }
-    if (tid == 0) cws[nk] = np;
     for (int b = tid; b < nb; b += K2_THREADS) hist[b] = 0;
     __syncthreads();
 
@@ -341,19 +342,12 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
     uint32_t rrow[K2_IMAX], rval[K2_IMAX];
     int32_t rank[K2_IMAX];
     {
-      const int32_t pw0 = warp * 32 * items + lane;
-      int l = 0;
-      if (pw0 < np) {  // last entry whose start is <= pw0
-        int lo = 0, hi = nk;
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (cws[mid] <= pw0) lo = mid; else hi = mid;
-        }
-        l = lo;
-      }
-      int32_t nextb = cws[l + 1];
-      int32_t kb = kbase[l];
-      uint32_t xv = kx[l];
+      const int w0 = warp * items;  // bitmap word of this warp's first 32 products
+      const int32_t pw0 = w0 * 32 + lane;
+      int ent = 0;                  // entry starts before word w0
+      for (int j = lane; j < w0; j += 32) ent += __popc(hbits[j]);
+      ent = __reduce_add_sync(0xffffffffu, ent);
+      const uint32_t le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
       // phase 1: every item's address, then all loads in flight at once
       uint32_t xi[K2_IMAX];
       float av[K2_IMAX];
@@ -363,17 +357,12 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
         rrow[i] = 0xffffffffu;
         xi[i] = 0u;
         av[i] = 1.0f;
+        const uint32_t hw = i < items ? hbits[w0 + i] : 0u;
+        const int e = ent + __popc(hw & le);
+        ent += __popc(hw);
         if (i < items && pl < np) {
-          if (pl >= nextb) {
-            do {
-              ++l;
-              nextb = cws[l + 1];
-            } while (pl >= nextb);
-            kb = kbase[l];
-            xv = kx[l];
-          }
-          const int32_t pos = kb + p0 + pl;
-          xi[i] = xv;
+          const int32_t pos = kbase[e] + p0 + pl;
+          xi[i] = kx[e];
           if ((uint32_t)pos < (uint32_t)nnz) {  // always true with valid inputs
             rrow[i] = (uint32_t)ld_stream(rowidx + pos);
             if (SEM == kPlusTimes && val) av[i] = ld_stream(val + pos);
@@ -415,6 +404,7 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
       }
     }
     __syncthreads();
+    for (int j = tid; j < QMAX / 32; j += K2_THREADS) hbits[j] = 0u;  // phase 1 is done
 
     // ---- one warp scans the bucket counts; the other warps flush hub sums ----
     if (warp == 0) {
@@ -548,7 +538,6 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
     st->last_maxdeg = st->maxdeg;
     st->last_maskcnt = st->maskcnt;
     st->maxdeg = 0;
-    st->sumdeg2 = 0ull;
     st->maskcnt = 0;
   }
   if (blockIdx.x == 0) {

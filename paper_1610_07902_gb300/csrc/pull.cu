@@ -87,7 +87,6 @@ k_pull_rows(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowi
       st->last_maxdeg = st->maxdeg;
       st->last_maskcnt = st->maskcnt;
       st->maxdeg = 0;
-      st->sumdeg2 = 0ull;
       st->maskcnt = 0;
     }
     const int nt1 = (st->f + K1_TILE - 1) / K1_TILE;

@@ -71,7 +71,6 @@ struct DevState {
   uint32_t k3_ticket;  // dynamic bucket counter of K3
   int32_t maxdeg;      // largest selected column length (selector feature)
   int32_t sched;       // schedule id of the current call
-  unsigned long long sumdeg2;  // sum of squared selected column lengths
   int32_t level;       // BFS level being discovered
   uint32_t pull_ticket;  // dynamic row-tile counter of the pull kernel
   int32_t nvisited;    // BFS: vertices reached so far
@@ -178,14 +177,15 @@ cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, i
                       int only_push = 0);
 cudaError_t launch_bucket_sizes(const Matrix& A, int lwb_lo, int nb_fine, int32_t* counts,
                                 unsigned int* bad, cudaStream_t s);
-// K2 shared memory: staged (row, value) pairs of one tile, the start,
-// cb - cw and x value of the tile's x entries, the bucket histogram and
-// slots, and the hub-row tables.
+// K2 shared memory: staged (row, value) pairs of one tile, the bitmap of
+// entry starts, cb - cw and x value of the tile's x entries, the bucket
+// histogram and slots, and the hub-row tables.
 __host__ __device__ constexpr size_t k2_smem_bytes(int nb_fine, bool hot) {
-  return sizeof(uint32_t) * 2 * QMAX + sizeof(int32_t) * (QMAX + 2) + sizeof(int32_t) * (QMAX + 1) +
+  return sizeof(uint32_t) * 2 * QMAX + sizeof(uint32_t) * (QMAX / 32) + sizeof(int32_t) * (QMAX + 1) +
          sizeof(uint32_t) * (QMAX + 1) + sizeof(int32_t) * (size_t)nb_fine * 2 + 64 +
          (hot ? sizeof(uint32_t) * HOT_MAX * 2 + sizeof(uint32_t) * (HOT_MAX / 32) + 64 : 0);
 }
+// K3 shared memory: the SPA values and the occupancy bitmap of one bucket
 // K3 shared memory: the SPA values and the occupancy bitmap of one bucket
 __host__ __device__ constexpr size_t k3_smem_bytes(int lwb) {
   return ((size_t)1 << lwb) * sizeof(uint32_t) + (((size_t)1 << lwb) / 32) * sizeof(uint32_t);
