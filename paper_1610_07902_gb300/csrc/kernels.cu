@@ -274,9 +274,9 @@ __device__ __forceinline__ void spa_apply(uint32_t* spa, uint32_t r, uint32_t v)
 // 32 products of one warp load are one bitmap word, so a lane's entry is the
 // count of starts before its word plus a popcount inside the word (no
 // search, no divergence).  Products are counted per bucket with
-// shared-memory atomics, one warp scans the counts, every non-empty bucket gets one run reserved
-// with a global atomic, the products are staged in shared memory grouped by
-// bucket and written out in runs.  Hub rows (row ids >= m in the relabelled
+// shared-memory atomics, one warp scans the counts, every non-empty bucket
+// gets one run reserved with a global atomic, the products are staged in
+// shared memory grouped by bucket and written out in runs.  Hub rows (row ids >= m in the relabelled
 // row-id array) are summed per tile in shared memory instead.
 template <int SEM>
 __global__ void __launch_bounds__(K2_THREADS, 2)
