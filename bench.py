@@ -35,10 +35,11 @@ WORKLOAD = "rmat22_ef16_f1e6_plus_times_f32"
 SCALE, EDGE_FACTOR, SEED, F = 22, 16, 1, 1_000_000
 
 
-# DRAM bytes per product moved by the scatter kernel, from the full ncu capture
-# of the same kernel on R-MAT s21 with nnz(x) = 5e5 (203.9 MB read + written
-# for 15.03 M products); the traffic of a launch grows with its products.
-K2_TRAFFIC_PER_PRODUCT = 203.9e6 / 15.03e6
+# DRAM bytes per product moved by the scatter kernel, from a full ncu capture
+# of the same kernel build on R-MAT s21 with nnz(x) = 5e5, scaled by products
+# (the traffic of a launch grows with its products); None while the kernel
+# differs from the captured one.
+K2_TRAFFIC_PER_PRODUCT = None
 K2_TRAFFIC_SOURCE = "ncu full capture, R-MAT s21 nnz(x)=5e5, scaled by products"
 
 
@@ -531,7 +532,8 @@ def main():
         "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "traffic": (K2_TRAFFIC_PER_PRODUCT * W
-                                 if dom == S.SPMSPV_STAGE_SCATTER else None),
+                                 if dom == S.SPMSPV_STAGE_SCATTER and K2_TRAFFIC_PER_PRODUCT
+                                 else None),
                      "traffic_unit": "bytes per launch", "traffic_source": K2_TRAFFIC_SOURCE,
                      "peak_kind": peak_kind, "alg_bytes_per_launch": alg[dom],
                      "avg_launch_ms": stage_avg[dom]},
