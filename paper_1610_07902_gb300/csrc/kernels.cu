@@ -327,7 +327,9 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
     const int32_t kend = (p0 + np == W) ? fc : ws.tile_k0[(p0 + np) / QF] + 1;
     const int32_t nk = max(1, min(kend - k0, QMAX + 1));
 
-    for (int l = tid; l < nk; l += K2_THREADS) {
+    // the first K2_THREADS entries of every tile but a CTA's first were
+    // loaded during the previous tile (below)
+    for (int l = tid + (t != (int)blockIdx.x ? K2_THREADS : 0); l < nk; l += K2_THREADS) {
       const int32_t k = k0 + l;
       const int32_t w = ws.cw[k];
       kbase[l] = ws.cb[k] - w;
@@ -406,6 +408,24 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
     __syncthreads();
     for (int j = tid; j < QMAX / 32; j += K2_THREADS) hbits[j] = 0u;  // phase 1 is done
 
+    // ---- the next tile's x entries: in flight during this tile's scan,
+    // reservation and stores, written to shared memory before the write-out ----
+    const int tn = t + (int)gridDim.x;
+    int32_t p0n = 0, npn = 0, nkn = 0, pw = 0, pcb = 0;
+    uint32_t pcx = 0u;
+    if (tn < ntiles) {
+      p0n = tn * q;
+      npn = min(q, W - p0n);
+      const int32_t k0n = ws.tile_k0[p0n / QF];
+      const int32_t kendn = (p0n + npn == W) ? fc : ws.tile_k0[(p0n + npn) / QF] + 1;
+      nkn = max(1, min(kendn - k0n, QMAX + 1));
+      if (tid < nkn) {
+        pw = ws.cw[k0n + tid];
+        pcb = ws.cb[k0n + tid];
+        pcx = ws.cx[k0n + tid];
+      }
+    }
+
     // ---- one warp scans the bucket counts; the other warps flush hub sums ----
     if (warp == 0) {
       const int per = (nb + 31) >> 5;
@@ -460,6 +480,12 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
       if (rank[i] >= 0) stage[hist[rrow[i] >> lwb] + rank[i]] = make_uint2(rrow[i], rval[i]);
     if (nhot > 0 && warp == 1) htb[lane] = 0u;
     __syncthreads();
+    if (tid < nkn) {  // the next tile's entries (this tile's are no longer read)
+      kbase[tid] = pcb - pw;
+      kx[tid] = pcx;
+      const int32_t off = pw - p0n;
+      if (tid > 0 && off > 0 && off < npn) atomicOr(&hbits[off >> 5], 1u << (off & 31));
+    }
     // ---- write the runs to the buckets ----
     const int32_t kept = s_kept;
     for (int32_t s = tid; s < kept; s += K2_THREADS) {
@@ -511,7 +537,7 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
   }
   extern __shared__ __align__(16) uint32_t k3_smem[];
   __shared__ int32_t s_scan[K3_THREADS / 32 + 1];
-  __shared__ uint32_t s_b;
+  __shared__ uint32_t s_tk[2];  // this bucket's ticket and the next one's
   __shared__ unsigned long long s_off;
   __shared__ int32_t s_tot;
 
@@ -545,10 +571,15 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
     for (int i = tid; i < nt1; i += K3_THREADS) ws.k1_status[i] = 0ull;
   }
 
-  for (;;) {
-    if (tid == 0) s_b = atomicAdd(&st->k3_ticket, 1u);
-    __syncthreads();
-    const uint32_t b = s_b;
+  // tickets hand out the buckets in order; the next one is taken once this
+  // one is merged, so that it is in hand by the end of the compaction (every
+  // CTA still processes its buckets in ticket order, so the smallest
+  // unfinished bucket can always proceed; taking it only after the merge
+  // leaves none to CTAs that start late)
+  if (tid == 0) s_tk[0] = atomicAdd(&st->k3_ticket, 1u);
+  __syncthreads();
+  for (int it = 0;; ++it) {
+    const uint32_t b = s_tk[it & 1];
     if (b >= (uint32_t)nb) break;
     const int fb0 = (int)(b << sh), fb1 = min((int)(b + 1) << sh, nb_fine);
     const int32_t base = ws.rbase[fb0];
@@ -625,6 +656,7 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
       }
       __syncthreads();
     }
+    if (tid == 0) s_tk[(it + 1) & 1] = atomicAdd(&st->k3_ticket, 1u);
     // unique rows of this bucket (|uind_k|), then the offset of the bucket in y
     int32_t c = 0;
     const int w0 = tid * wpt;
