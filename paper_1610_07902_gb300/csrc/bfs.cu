@@ -25,6 +25,7 @@ cudaError_t launch_pull(const spmspv_handle* h, int sem, bool bfs, const int32_t
                         int mask_comp, int early_exit, int32_t* y_idx, uint32_t* y_val,
                         int32_t y_cap, int32_t* d_nnz_y, uint32_t* visited, int only_pull,
                         cudaStream_t s);
+cudaError_t launch_pull_rows_bfs(const spmspv_handle* h, int early_exit, int only_pull, cudaStream_t s);
 int pull_available(const spmspv_handle* h, int sem);
 
 namespace {
@@ -32,12 +33,17 @@ namespace {
 // Start of a search: every vertex unreached, the source at level 0.
 __global__ void k_bfs_init(int32_t n, int32_t src, int32_t* __restrict__ level,
                            int32_t* __restrict__ parent, uint32_t* __restrict__ visited,
-                           int32_t* __restrict__ front, DevState* st) {
+                           uint32_t* __restrict__ fb, int32_t* __restrict__ front, DevState* st) {
   const int32_t words = (n + 31) / 32;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     level[i] = i == src ? 0 : -1;
     parent[i] = i == src ? src : -1;
-    if (i < words) visited[i] = (i == (src >> 5)) ? (1u << (src & 31)) : 0u;
+    if (i < words) {
+      const uint32_t w = (i == (src >> 5)) ? (1u << (src & 31)) : 0u;
+      visited[i] = w;
+      fb[i] = w;       // level 0's frontier, read by a pull at level 1
+      fb[words + i] = 0u;
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     front[0] = src;
@@ -46,6 +52,7 @@ __global__ void k_bfs_init(int32_t n, int32_t src, int32_t* __restrict__ level,
     st->nvisited = 1;
     st->bfs_level = level;
     st->bfs_parent = parent;
+    st->bfs_fb = fb;
   }
 }
 
@@ -56,62 +63,30 @@ __global__ void k_bfs_continue(cudaGraphConditionalHandle cond, const DevState* 
 
 }  // namespace
 
-static int bfs_push_launches(spmspv_handle* h, const Sched& sc, int lwb, cudaStream_t s) {
+static int bfs_push_launches(spmspv_handle* h, const Sched& sc, int lwb, cudaStream_t s, int only_push) {
   const size_t k3_smem = k3_smem_bytes(lwb);
   const int nb_max = (int)(((int64_t)h->A.m + (1 << h->lwb_lo) - 1) >> h->lwb_lo);
   const int k3_grid = std::max(1, std::min(nb_max, h->sm_count * h->k3_bps[lwb - h->lwb_lo]));
   (void)sc;
   cudaError_t e = launch_k2(kMinSelect2nd, h->A, h->ws, h->lwb_lo, h->nb_fine, h->bfs_visited, 1,
-                            h->k2_grid, h->k2_smem, s, 0);
+                            h->k2_grid, h->k2_smem, s, only_push);
   if (e != cudaSuccess) return cuda_fail(e, "bfs expand/scatter");
   e = launch_k3(kMinSelect2nd, true, h->A, h->ws, h->lwb_lo, h->nb_fine, h->bfs_front, nullptr,
-                h->A.n, nullptr, h->bfs_visited, k3_grid, k3_smem, s, 0);
+                h->A.n, nullptr, h->bfs_visited, k3_grid, k3_smem, s, only_push);
   return e == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "bfs merge");
 }
 
-static int bfs_pull_launches(spmspv_handle* h, cudaStream_t s) {
-  cudaError_t e = launch_pull(h, kMinSelect2nd, true, h->bfs_front, nullptr, 0, &h->ws.st->nnz_y,
-                              h->bfs_visited, 1, h->rows_sorted, h->bfs_front, nullptr, h->A.n,
-                              nullptr, h->bfs_visited, 0, s);
+static int bfs_pull_launches(spmspv_handle* h, int only_pull, cudaStream_t s) {
+  cudaError_t e = launch_pull_rows_bfs(h, h->rows_sorted, only_pull, s);
   return e == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "bfs pull");
-}
-
-// Add an IF node (condition `hc`) after the current capture point of `s` and
-// capture the launches of `fn` into its body on the side stream.
-template <typename Fn>
-static int capture_if_with(cudaStream_t s, cudaStream_t side, cudaGraphConditionalHandle hc, Fn fn) {
-  cudaStreamCaptureStatus cst;
-  cudaGraph_t cg = nullptr;
-  const cudaGraphNode_t* deps = nullptr;
-  size_t ndeps = 0;
-  cudaError_t e = cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps);
-  if (e != cudaSuccess || cst != cudaStreamCaptureStatusActive) return cuda_fail(e, "capture info");
-  cudaGraphNodeParams np = {};
-  np.type = cudaGraphNodeTypeConditional;
-  np.conditional.handle = hc;
-  np.conditional.type = cudaGraphCondTypeIf;
-  np.conditional.size = 1;
-  cudaGraphNode_t node;
-  if ((e = cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &np)) != cudaSuccess)
-    return cuda_fail(e, "add if node");
-  if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
-    return cuda_fail(e, "capture dependencies");
-  if ((e = cudaStreamBeginCaptureToGraph(side, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                         cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-    return cuda_fail(e, "begin if capture");
-  int rc = fn(side);
-  cudaGraph_t tmp = nullptr;
-  e = cudaStreamEndCapture(side, &tmp);
-  if (rc != SPMSPV_OK) return rc;
-  return e == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "end if capture");
 }
 
 // One BFS level on `s` (captured into the loop body).  A fixed schedule
 // launches its direction's kernels; the learned schedule launches the work
-// scan, whose last CTA runs the selector, then two IF nodes (push, pull) of
-// which the selector enables one.
+// scan, whose last CTA runs the selector, then the push and the pull kernels,
+// of which the ones not chosen return at once.
 static int bfs_level_launches(spmspv_handle* h, int sched, cudaGraphConditionalHandle cond,
-                              cudaStream_t s, cudaStream_t side) {
+                              cudaStream_t s) {
   const bool autos = sched < 0;
   const bool can_pull = pull_available(h, kMinSelect2nd) != 0;
   Sched sc = decode_schedule(h, autos ? h->default_sched : sched);
@@ -125,36 +100,22 @@ static int bfs_level_launches(spmspv_handle* h, int sched, cudaGraphConditionalH
     if ((e = launch_k1_bfs(h->A, h->ws, h->nb_fine, h->bfs_front, &h->ws.st->nnz_y, h->k1_grid_max, &sc,
                            s, nullptr)) != cudaSuccess)
       return cuda_fail(e, "bfs work scan");
-    rc = sc.dir == 0 ? bfs_push_launches(h, sc, sc.lwb, s) : bfs_pull_launches(h, s);
+    rc = sc.dir == 0 ? bfs_push_launches(h, sc, sc.lwb, s, 0) : bfs_pull_launches(h, 0, s);
   } else {
-    // the work scan's last CTA runs the selector; the visited count stands
-    // in for a pass over the visited bitmap
+    // the work scan's last CTA runs the selector and sets the direction; the
+    // push kernels and the pull kernel both follow and the one not chosen
+    // returns at once (no conditional nodes); the visited count stands in
+    // for a pass over the visited bitmap
     SelArgs sa{};
     sa.w = h->sel_w;
     sa.allow_pull = can_pull;
     sa.bfs = 1;
     sa.lwb_lo = h->lwb_lo;
-    if (can_pull) {
-      // both IF handles exist before the kernel that sets them is captured
-      cudaStreamCaptureStatus cst;
-      cudaGraph_t cg = nullptr;
-      if ((e = cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, nullptr, nullptr, nullptr)) != cudaSuccess)
-        return cuda_fail(e, "capture info");
-      if ((e = cudaGraphConditionalHandleCreate(&sa.c_push, cg, 0, cudaGraphCondAssignDefault)) != cudaSuccess ||
-          (e = cudaGraphConditionalHandleCreate(&sa.c_pull, cg, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
-        return cuda_fail(e, "if handles");
-      sa.use_cond = 1;
-    }
     if ((e = launch_k1_bfs(h->A, h->ws, h->nb_fine, h->bfs_front, &h->ws.st->nnz_y, h->k1_grid_max,
                            nullptr, s, nullptr, &sa)) != cudaSuccess)
       return cuda_fail(e, "bfs work scan");
-    if (!can_pull) {
-      rc = bfs_push_launches(h, sc, h->lwb_lo + 2, s);
-    } else {
-      rc = capture_if_with(s, side, sa.c_push, [&](cudaStream_t ss) { return bfs_push_launches(h, sc, h->lwb_lo + 2, ss); });
-      if (rc == SPMSPV_OK)
-        rc = capture_if_with(s, side, sa.c_pull, [&](cudaStream_t ss) { return bfs_pull_launches(h, ss); });
-    }
+    rc = bfs_push_launches(h, sc, h->lwb_lo + 2, s, can_pull ? 1 : 0);
+    if (rc == SPMSPV_OK && can_pull) rc = bfs_pull_launches(h, 1, s);
   }
   if (rc != SPMSPV_OK) return rc;
   k_bfs_continue<<<1, 32, 0, s>>>(cond, h->ws.st, h->A.n);
@@ -166,7 +127,7 @@ static int bfs_level_launches(spmspv_handle* h, int sched, cudaGraphConditionalH
 static int build_bfs_graph(spmspv_handle* h, int sched, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaStream_t cs = nullptr, side = nullptr;
+  cudaStream_t cs = nullptr;
   cudaError_t e = cudaGraphCreate(&g, 0);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
   int rc = SPMSPV_OK;
@@ -187,8 +148,7 @@ static int build_bfs_graph(spmspv_handle* h, int sched, cudaGraphExec_t* out) {
       break;
     }
     cudaGraph_t body = np.conditional.phGraph_out[0];
-    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking)) != cudaSuccess) {
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
       rc = cuda_fail(e, "capture stream");
       break;
     }
@@ -199,7 +159,7 @@ static int build_bfs_graph(spmspv_handle* h, int sched, cudaGraphExec_t* out) {
     }
     void* saved_prof = h->prof;
     h->prof = nullptr;  // no profiling events inside the graph
-    rc = bfs_level_launches(h, sched, cond, cs, side);
+    rc = bfs_level_launches(h, sched, cond, cs);
     h->prof = saved_prof;
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(cs, &captured);
@@ -214,7 +174,6 @@ static int build_bfs_graph(spmspv_handle* h, int sched, cudaGraphExec_t* out) {
     }
   } while (0);
   if (cs) cudaStreamDestroy(cs);
-  if (side) cudaStreamDestroy(side);
   cudaGraphDestroy(g);
   if (rc != SPMSPV_OK) {
     if (exec) cudaGraphExecDestroy(exec);
@@ -230,9 +189,12 @@ int ensure_bfs_buffers(spmspv_handle* h) {
   const size_t n = (size_t)h->A.n;
   cudaError_t e = cudaMalloc(&h->bfs_front, sizeof(int32_t) * n);
   if (e == cudaSuccess) e = cudaMalloc(&h->bfs_visited, sizeof(uint32_t) * ((n + 31) / 32 + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&h->bfs_fb, sizeof(uint32_t) * 2 * ((n + 31) / 32));
   if (e != cudaSuccess) {
     cudaFree(h->bfs_front);
+    cudaFree(h->bfs_visited);
     h->bfs_front = nullptr;
+    h->bfs_visited = nullptr;
     cudaGetLastError();
     return fail(SPMSPV_ERR_OOM, "BFS buffers: %s", cudaGetErrorString(e));
   }
@@ -276,7 +238,8 @@ extern "C" int spmspv_bfs(spmspv_handle* h, int32_t src, int32_t* level, int32_t
   h->last_stream = s;
   h->last_empty = 0;
   const int grid = std::max(1, std::min(h->sm_count * 8, (h->A.n + 255) / 256));
-  k_bfs_init<<<grid, 256, 0, s>>>(h->A.n, src, level, parent, h->bfs_visited, h->bfs_front, h->ws.st);
+  k_bfs_init<<<grid, 256, 0, s>>>(h->A.n, src, level, parent, h->bfs_visited, h->bfs_fb, h->bfs_front,
+                                  h->ws.st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "bfs init");
   if ((e = cudaGraphLaunch((cudaGraphExec_t)h->bfs_graph[slot], s)) != cudaSuccess)

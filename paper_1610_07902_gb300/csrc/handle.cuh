@@ -48,6 +48,7 @@ struct spmspv_handle {
   // BFS buffers, allocated on first use
   int32_t* bfs_front;   // [n] frontier list (x and y of each level)
   uint32_t* bfs_visited;  // [ceil(n/32)]
+  uint32_t* bfs_fb;     // [2 * ceil(n/32)] frontier bitmaps (current / next level)
   int32_t* bfs_count;   // [4] device counters
 };
 

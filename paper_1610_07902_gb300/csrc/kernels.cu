@@ -76,6 +76,8 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
       ws.bfill[(size_t)b * BFILL_STRIDE] = 0;
       ws.k3_status[b] = 0ull;
     }
+    if (bfs_level_inc && ws.pull_status)
+      for (int i = tid; i < ws.pull_tiles; i += K1_THREADS) ws.pull_status[i] = 0ull;
     const uint32_t hid = sem == kMinSelect2nd ? 0x7fffffffu : 0u;
     for (int h = tid; h < ws.nhot; h += K1_THREADS) {
       ws.hot_val[h] = hid;
@@ -90,8 +92,12 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
         st->lwb = f_lwb;
         st->sched = forced - 1;
       }
-      if (bfs_level_inc) st->level += 1;
-      else if (!ws.job) st->bfs_level = nullptr;  // not a BFS level
+      if (bfs_level_inc) {
+        st->level += 1;
+        st->pull_ticket = 0u;  // the level may run the pull kernel
+      } else if (!ws.job) {
+        st->bfs_level = nullptr;  // not a BFS level
+      }
       if (f == 0) {
         st->fc = 0;
         st->W = 0;
@@ -557,6 +563,11 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
   int32_t* const level = BFS ? (ws.job ? ws.job->level : st->bfs_level) : nullptr;
   int32_t* const parent = BFS ? (ws.job ? ws.job->parent : st->bfs_parent) : nullptr;
   const int nhot = ws.nhot;
+  // single-source BFS: this level's frontier bitmap (every word is written,
+  // zeros for buckets without rows) for a pull at the next level
+  uint32_t* fbn = nullptr;
+  const int64_t fb_words = ((int64_t)m + 31) / 32;
+  if (BFS && !ws.job && st->bfs_fb) fbn = st->bfs_fb + ((lvl & 1) ? fb_words : 0);
 
   if (blockIdx.x == 0 && tid == 0) {
     // clear K1's per-call state for the next call
@@ -692,6 +703,12 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
           }
           ++pos;
         }
+      }
+    }
+    if (BFS && fbn && w0 < nw) {
+      for (int w = w0; w < w0 + wpt; ++w) {
+        const int64_t gw = (int64_t)b * nw + w;
+        if (gw < fb_words) fbn[gw] = active ? occ[w] : 0u;
       }
     }
     if (b == (uint32_t)nb - 1u && tid == 0) {

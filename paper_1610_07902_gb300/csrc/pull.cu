@@ -80,6 +80,14 @@ k_pull_rows(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowi
   const int32_t lvl = BFS ? st->level : 0;
   int32_t* const level = BFS ? st->bfs_level : nullptr;
   int32_t* const parent = BFS ? st->bfs_parent : nullptr;
+  // BFS: x is the previous level's frontier bitmap, x(j) = j; this level's
+  // discoveries go to the other bitmap (every word is written)
+  uint32_t* fb_next = nullptr;
+  if (BFS) {
+    const size_t words = ((size_t)m + 31) / 32;
+    xbits = st->bfs_fb + (((lvl - 1) & 1) ? words : 0);
+    fb_next = st->bfs_fb + ((lvl & 1) ? words : 0);
+  }
   if (blockIdx.x == 0) {
     // this kernel ends the call: clear the work scan's per-call state
     if (tid == 0) {
@@ -117,7 +125,7 @@ k_pull_rows(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowi
           if (!((xbits[j >> 5] >> (j & 31)) & 1u)) continue;
           hit = true;
           if (SEM == kOrAnd) break;
-          const uint32_t xv = xdense[j];
+          const uint32_t xv = BFS ? (uint32_t)j : xdense[j];
           if (SEM == kMinSelect2nd) {
             if ((int)xv < (int)acc) acc = xv;
             if (early_exit) break;
@@ -172,6 +180,7 @@ k_pull_rows(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowi
     __syncthreads();
     int64_t pos = (int64_t)s_off + run;
     if (BFS && found) visited[w] |= found;
+    if (BFS && r0 < m) fb_next[w] = found;
     for (uint32_t bits = found; bits; bits &= bits - 1u) {
       const int b = __ffs(bits) - 1;
       const int32_t i = r0 + b;
@@ -232,6 +241,17 @@ cudaError_t launch_pull(const spmspv_handle* h, int sem, bool bfs, const int32_t
   return cudaGetLastError();
 }
 
+// BFS level in the pull direction: the frontier is the previous level's
+// bitmap (written by K3 or by this kernel), so only the row kernel runs; the
+// work scan of the level has reset the pull look-back state.
+cudaError_t launch_pull_rows_bfs(const spmspv_handle* h, int early_exit, int only_pull, cudaStream_t s) {
+  const int grid = std::max(1, std::min(h->pull_tiles, h->sm_count * 8));
+  k_pull_rows<kMinSelect2nd, true><<<grid, PULL_THREADS, 0, s>>>(
+      h->A.colptr, h->A.rowidx, h->A.val, h->A.m, nullptr, nullptr, h->bfs_visited, 1, early_exit,
+      h->bfs_front, nullptr, h->A.n, &h->ws.st->nnz_y, h->bfs_visited, h->ws, h->pull_tiles, only_pull);
+  return cudaGetLastError();
+}
+
 int run_pull_if_available(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_val,
                           int f, const uint32_t* mask, int mask_comp, const Sched& sc,
                           int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y,
@@ -253,7 +273,10 @@ cudaError_t alloc_pull_buffers(spmspv_handle* h) {
   if (e == cudaSuccess) e = cudaMalloc(&h->xdense, sizeof(uint32_t) * (size_t)n);
   if (e == cudaSuccess) e = cudaMalloc(&h->pull_status, sizeof(unsigned long long) * (size_t)h->pull_tiles);
   if (e == cudaSuccess) e = cudaMemset(h->xbits, 0, sizeof(uint32_t) * (((size_t)n + 31) / 32));
-  if (e == cudaSuccess) h->ws.pull_status = h->pull_status;
+  if (e == cudaSuccess) {
+    h->ws.pull_status = h->pull_status;
+    h->ws.pull_tiles = h->pull_tiles;
+  }
   return e;
 }
 
@@ -263,12 +286,14 @@ void release_extras(spmspv_handle* h) {
   cudaFree(h->pull_status);
   cudaFree(h->bfs_front);
   cudaFree(h->bfs_visited);
+  cudaFree(h->bfs_fb);
   cudaFree(h->bfs_count);
   h->xbits = nullptr;
   h->xdense = nullptr;
   h->pull_status = nullptr;
   h->bfs_front = nullptr;
   h->bfs_visited = nullptr;
+  h->bfs_fb = nullptr;
   h->bfs_count = nullptr;
 }
 

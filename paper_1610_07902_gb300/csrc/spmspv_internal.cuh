@@ -79,6 +79,8 @@ struct DevState {
   int32_t last_maskcnt;
   int32_t* bfs_level;  // BFS outputs of the current search
   int32_t* bfs_parent;
+  uint32_t* bfs_fb;    // BFS: two frontier bitmaps of ceil(n/32) words; level L reads
+                       // bitmap (L-1)&1 (pull) and writes bitmap L&1 (K3 or pull)
   uint32_t k1_done;    // K1 CTAs finished; the last one runs the selector (self-resetting)
 };
 
@@ -132,6 +134,7 @@ struct Workspace {
   const int32_t* hot_start;  // [nb_fine+1] first hot index of each fine bucket
   const int32_t* rowidx_k2;  // [nnz] row ids with hub row r replaced by m + its hub index
   unsigned long long* pull_status;  // [pull tiles] look-back words of the pull kernel
+  int pull_tiles;
   const Job* job;            // batched lanes: the current frontier (NULL otherwise)
   uint32_t* hot_val;         // [HOT_MAX] per-call sums of the hot rows
   uint32_t* hot_touch;       // [HOT_MAX] 1 when a hot row received a product this call
