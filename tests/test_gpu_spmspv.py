@@ -245,6 +245,39 @@ def test_bad_arguments_return_codes(lib):
     with pytest.raises(S.SpmspvError) as e:
         S.spmspv_create_csc(0, 1, 1, cp, ri, None, S.SPMSPV_VAL_NONE)
     assert e.value.code == S.SPMSPV_ERR_ARG
+    # row ids and values are read 16 bytes at a time: a misaligned array is refused
+    cp2 = torch.tensor([0, 2], dtype=torch.int32, device="cuda")
+    ri2 = torch.tensor([0, 0, 1], dtype=torch.int32, device="cuda")
+    with pytest.raises(S.SpmspvError) as e:
+        S.spmspv_create_csc(2, 1, 2, cp2, ri2[1:], None, S.SPMSPV_VAL_NONE)
+    assert e.value.code == S.SPMSPV_ERR_ARG
+
+
+@pytest.mark.parametrize("tail", [0, 1, 2, 3])
+def test_columns_at_the_end_of_the_arrays(lib, tail):
+    # nnz = 4k + tail: the last column ends inside the arrays' last, partial
+    # 16-byte chunk; every column (the last ones included) is selected
+    torch, S = lib
+    rng = np.random.default_rng(tail)
+    n, m = 37, 50
+    deg = rng.integers(0, 9, size=n)
+    deg[-1] = 5
+    nnz = int(deg.sum())
+    deg[-1] += (tail - nnz) % 4
+    colptr = np.concatenate([[0], np.cumsum(deg)]).astype(np.int32)
+    rowidx = np.concatenate([np.sort(rng.choice(m, size=d, replace=False)) for d in deg]).astype(np.int32)
+    val = rng.random(rowidx.shape[0]).astype(np.float32)
+    assert rowidx.shape[0] % 4 == tail
+    Ad = S.CscMatrix(m, n, colptr, rowidx, val)
+    for x_idx in (np.arange(n, dtype=np.int32), np.array([n - 1], np.int32), np.array([n - 1, 0], np.int32)):
+        xf = rng.random(x_idx.shape[0]).astype(np.float32)
+        for semiring in (0, 1, 2):
+            xv = x_values(semiring, x_idx, xf)
+            ref = oracle.spmspv(m, colptr, rowidx, val, SEMIRING_TO_ORACLE[semiring], x_idx, xv, None, True)
+            yi, yv, k, st = _run(lib, None, Ad, semiring, x_idx, xv, None, True, None)
+            assert st == 0
+            compare(semiring, ref, yi, yv)
+    Ad.close()
 
 
 def test_many_calls_on_one_handle(lib):
