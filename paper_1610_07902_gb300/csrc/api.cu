@@ -105,7 +105,7 @@ int run_push(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_
              const int32_t* f_dev, const uint32_t* mask, int mask_comp, const Sched& sc,
              int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y, bool bfs,
              uint32_t* mask_update, cudaStream_t s) {
-  int k1_grid = f_dev ? h->k1_grid_max
+  int k1_grid = f_dev ? h->k1_grid_dev
                       : (int)std::min<int64_t>(h->k1_grid_max, ((int64_t)f + K1_TILE - 1) / K1_TILE);
   if (h->k1_mask) k1_grid = std::max(k1_grid, mask_pass_grid(h));
   if (k1_grid < 1) k1_grid = 1;
@@ -435,6 +435,7 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
     h->k2_grid = h->sm_count * k2_bps;
     for (int i = 0; i < 3; ++i) h->k3_bps[i] = k3_blocks_per_sm(kPlusTimes, k3_smem_bytes(h->lwb_lo + i));
     h->k1_grid_max = h->sm_count * 4;
+    h->k1_grid_dev = h->sm_count * 2;
     h->default_sched = 5;  // push, larger quantum, widest bucket: the fastest single
                            // schedule at R-MAT s22 with nnz(x) = 10^6
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) { rc = cuda_fail(e, "create"); break; }

@@ -97,7 +97,7 @@ static int bfs_level_launches(spmspv_handle* h, int sched, cudaGraphConditionalH
   cudaError_t e;
   int rc = SPMSPV_OK;
   if (!autos) {
-    if ((e = launch_k1_bfs(h->A, h->ws, h->nb_fine, h->bfs_front, &h->ws.st->nnz_y, h->k1_grid_max, &sc,
+    if ((e = launch_k1_bfs(h->A, h->ws, h->nb_fine, h->bfs_front, &h->ws.st->nnz_y, h->k1_grid_dev, &sc,
                            s, nullptr)) != cudaSuccess)
       return cuda_fail(e, "bfs work scan");
     rc = sc.dir == 0 ? bfs_push_launches(h, sc, sc.lwb, s, 0) : bfs_pull_launches(h, 0, s);
@@ -111,7 +111,7 @@ static int bfs_level_launches(spmspv_handle* h, int sched, cudaGraphConditionalH
     sa.allow_pull = can_pull;
     sa.bfs = 1;
     sa.lwb_lo = h->lwb_lo;
-    if ((e = launch_k1_bfs(h->A, h->ws, h->nb_fine, h->bfs_front, &h->ws.st->nnz_y, h->k1_grid_max,
+    if ((e = launch_k1_bfs(h->A, h->ws, h->nb_fine, h->bfs_front, &h->ws.st->nnz_y, h->k1_grid_dev,
                            nullptr, s, nullptr, &sa)) != cudaSuccess)
       return cuda_fail(e, "bfs work scan");
     rc = bfs_push_launches(h, sc, h->lwb_lo + 2, s, can_pull ? 1 : 0);

@@ -28,6 +28,7 @@ struct spmspv_handle {
   int k2_grid;
   int k3_bps[3];        // K3 CTAs per SM for each of the three bucket widths
   int k1_grid_max;
+  int k1_grid_dev;      // K1 CTAs when nnz(x) is only known on the device (BFS, lanes)
   int default_sched;
   cudaStream_t last_stream;
   int last_empty;

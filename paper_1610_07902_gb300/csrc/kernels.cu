@@ -116,11 +116,13 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
 
   int maxdeg = 0;
   unsigned long long wsum = 0;  // products of this thread's entries
+  uint32_t my_tiles = 0;
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(&st->k1_ticket, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
     if (tile >= nt1) break;
+    ++my_tiles;
     const int64_t base = (int64_t)tile * K1_TILE;
 
     // striped, coalesced loads of x, then of the two column pointers of
@@ -251,9 +253,14 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
   // CTA's sums: it sets W and runs the selector (otherwise the call's last
   // kernel sets W)
   if (!sel.w) return;
+  // the CTA that finishes the last piece of work runs it: with a mask pass
+  // every CTA is a piece, otherwise every tile (CTAs without one add nothing)
+  const uint32_t units = mask ? 1u : my_tiles;
+  const uint32_t total = mask ? gridDim.x : nt1;
+  if (total == 0 ? blockIdx.x != 0 : units == 0) return;
   if (tid == 0) {
     __threadfence();
-    s_last = atomicAdd(&st->k1_done, 1u) == gridDim.x - 1u;
+    s_last = total == 0 || atomicAdd(&st->k1_done, units) + units == total;
   }
   __syncthreads();
   if (s_last) {
