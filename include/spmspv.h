@@ -105,17 +105,15 @@ const char* spmspv_last_error(void);
  *   m, n     rows, columns; 1 <= m <= 2^26, 1 <= n < 2^31.
  *   nnz      colptr[n]; 0 <= nnz < 2^31.
  *   colptr   device int32[n+1], non-decreasing, colptr[0] = 0.
- *   rowidx   device int32[nnz], each in [0, m), 16-byte aligned.
- *   val      device float[nnz] for SPMSPV_VAL_F32, 16-byte aligned; ignored
- *            (may be NULL) for SPMSPV_VAL_NONE.  Both arrays are read 16
- *            bytes at a time (never past their end).
+ *   rowidx   device int32[nnz], each in [0, m).
+ *   val      device float[nnz] for SPMSPV_VAL_F32, ignored (may be NULL)
+ *            for SPMSPV_VAL_NONE.
  *   flags    SPMSPV_CSC_PATTERN_SYMMETRIC, SPMSPV_CSC_SYMMETRIC or 0.  The
  *            flags are trusted, not checked.
  * Synchronous: allocates the workspace (about 6 bytes per nonzero for the
- * buckets plus 24 bytes per column) on the current device, and scans
- * rowidx once to size the row-range buckets.  Errors: ARG (also for a
- * misaligned rowidx or val), OOM, CUDA, UNSUPPORTED (m too large for the
- * bucket row width).
+ * buckets plus 16 bytes per column) on the current device, and scans
+ * rowidx once to size the row-range buckets.  Errors: ARG, OOM, CUDA,
+ * UNSUPPORTED (m too large for the bucket row width).
  */
 int spmspv_create_csc(spmspv_handle** h, int32_t m, int32_t n, int64_t nnz,
                       const int32_t* colptr, const int32_t* rowidx, const void* val,
@@ -324,8 +322,7 @@ int spmspv_last_work(spmspv_handle* h, int64_t* work);
  *   Limits (rejected with SPMSPV_ERR_UNSUPPORTED and a message naming the
  *   limit): m <= 2^22 rows, nnz(A) <= 2^20, nnz_x <= 2^16.  Only the default
  *   schedule: SPMSPV_SCHED_* options are rejected the same way.
- *   val_type: SPMSPV_VAL_F32 or SPMSPV_VAL_NONE, as for spmspv_create_csc
- *   (rowidx and val 16-byte aligned as there).
+ *   val_type: SPMSPV_VAL_F32 or SPMSPV_VAL_NONE, as for spmspv_create_csc.
  *   Output order, capacity rule and *d_nnz_y: as for spmspv_run (a y that does
  *   not fit leaves the size it needs in *d_nnz_y).
  * The first call on a device looks up the array's device address with that

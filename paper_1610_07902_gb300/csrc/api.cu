@@ -85,7 +85,7 @@ Sched decode_schedule(const spmspv_handle* h, int id) {
   Sched s;
   s.id = id;
   s.dir = id / 6;
-  s.q = ((id / 3) % 2) ? 3 * QF : 2 * QF;
+  s.q = ((id / 3) % 2) ? 2 * QF : QF;
   s.lwb = h->lwb_lo + id % 3;
   return s;
 }
@@ -267,8 +267,6 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
     return fail(SPMSPV_ERR_ARG, "unknown val_type %d", val_type);
   if (val_type == SPMSPV_VAL_F32 && nnz > 0 && !val)
     return fail(SPMSPV_ERR_ARG, "val is NULL for SPMSPV_VAL_F32");
-  if (nnz > 0 && (((uintptr_t)rowidx & 15u) || (val && ((uintptr_t)val & 15u))))
-    return fail(SPMSPV_ERR_ARG, "rowidx and val must be 16-byte aligned (read 16 bytes at a time)");
 
   spmspv_handle* h = new spmspv_handle();
   memset(h, 0, sizeof(*h));
@@ -296,9 +294,7 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
   }
 
   // workspace: one allocation, carved in 256-byte aligned pieces
-  // chunks of one call: each selected column covers at most len/4 + 2 chunks
-  const int64_t cmax = (nnz + 3) / 4 + 2 * (int64_t)n;
-  const int64_t ntile_fine = cmax / QF + 2;
+  const int64_t ntile_fine = nnz / QF + 2;
   const int64_t nt1 = ((int64_t)n + K1_TILE - 1) / K1_TILE + 1;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -309,7 +305,6 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
   size_t o_st = take(sizeof(DevState));
   size_t o_cw = take(sizeof(int32_t) * ((size_t)n + 1));
   size_t o_cb = take(sizeof(int32_t) * (size_t)n);
-  size_t o_cd = take(sizeof(int32_t) * (size_t)n);
   size_t o_cx = take(sizeof(uint32_t) * (size_t)n);
   size_t o_tk = take(sizeof(int32_t) * (size_t)ntile_fine);
   size_t o_k1s = take(sizeof(unsigned long long) * (size_t)nt1);
@@ -336,8 +331,6 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
   h->ws.st = (DevState*)(b + o_st);
   h->ws.cw = (int32_t*)(b + o_cw);
   h->ws.cb = (int32_t*)(b + o_cb);
-  h->ws.cd = (int32_t*)(b + o_cd);
-  h->ws.cmax = (int32_t)cmax;
   h->ws.cx = (uint32_t*)(b + o_cx);
   h->ws.tile_k0 = (int32_t*)(b + o_tk);
   h->ws.k1_status = (unsigned long long*)(b + o_k1s);
@@ -416,7 +409,7 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
     // default schedule state
     DevState st0;
     memset(&st0, 0, sizeof(st0));
-    st0.q = 3 * QF;
+    st0.q = 2 * QF;  // schedule 5 (the default)
     st0.lwb = h->lwb_lo + 2;
     if ((e = cudaMemcpy(h->ws.st, &st0, sizeof(st0), cudaMemcpyHostToDevice)) != cudaSuccess) {
       rc = cuda_fail(e, "state init");
@@ -436,8 +429,8 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
     for (int i = 0; i < 3; ++i) h->k3_bps[i] = k3_blocks_per_sm(kPlusTimes, k3_smem_bytes(h->lwb_lo + i));
     h->k1_grid_max = h->sm_count * 4;
     h->k1_grid_dev = h->sm_count * 2;
-    h->default_sched = 5;  // push, larger quantum, widest bucket: the fastest single
-                           // schedule at R-MAT s22 with nnz(x) = 10^6
+    h->default_sched = 5;  // push, 4096-product tiles, widest buckets: the fastest
+                           // single schedule at R-MAT s22 with nnz(x) = 10^6
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) { rc = cuda_fail(e, "create"); break; }
   } while (0);
   if (rc != SPMSPV_OK) {

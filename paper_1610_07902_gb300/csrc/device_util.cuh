@@ -24,8 +24,6 @@ __device__ __forceinline__ void lb_store(unsigned long long* p, unsigned long lo
 // Streaming load (evict-first): matrix entries are read once per call.
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
 __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
-__device__ __forceinline__ uint4 ld_stream(const uint4* p) { return __ldcs(p); }
-__device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
 
 // Exclusive look-back prefix for tile `tile`, computed by one full warp:
 // the warp publishes the tile's aggregate, then reads the status words of

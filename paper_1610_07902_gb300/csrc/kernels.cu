@@ -5,12 +5,11 @@
 //
 //   K1 work_scan      Algorithm 2's role: instead of counting (thread, bucket)
 //                     insertions, one decoupled-look-back prefix sum over the
-//                     16-byte chunks of the selected columns gives every
-//                     chunk a global rank; x entries with an empty column are
-//                     dropped and the first x entry of every QF-chunk tile is
-//                     recorded (a merge-path split: every K2 tile then holds
-//                     the same number of chunks, whatever the column
-//                     lengths).  W (products) is summed alongside.
+//                     selected column lengths gives every product a global
+//                     rank; x entries with an empty column are dropped and the
+//                     first x entry of every QF-product tile is recorded
+//                     (a merge-path split: every K2 tile then holds the same
+//                     number of products, whatever the column lengths).
 //   K2 expand_scatter Step 1: a tile of q products is gathered (coalesced
 //                     loads of row ids and values), multiplied, optionally
 //                     filtered by the mask, counted per row-range bucket in
@@ -59,7 +58,6 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
   __shared__ uint32_t s_tile;
   __shared__ int s_maxdeg;
   __shared__ int s_maskcnt;
-  __shared__ unsigned long long s_wsum[K1_THREADS / 32];
 
   DevState* st = ws.st;
   const int tid = threadIdx.x;
@@ -87,7 +85,6 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
     }
     if (tid == 0) {
       st->f = f;
-      st->W = 0;  // set from Wacc by K1's last CTA (selector) or by the call's last kernel
       st->k3_ticket = 0u;
       if (forced) {
         st->dir = f_dir;
@@ -103,7 +100,7 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
       }
       if (f == 0) {
         st->fc = 0;
-        st->C = 0;
+        st->W = 0;
         ws.cw[0] = 0;
         ws.tile_k0[0] = 0;
       }
@@ -115,7 +112,6 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
   }
 
   int maxdeg = 0;
-  unsigned long long wsum = 0;  // products of this thread's entries
   uint32_t my_tiles = 0;
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(&st->k1_ticket, 1u);
@@ -169,12 +165,8 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
     unsigned long long tsum = 0;
 #pragma unroll
     for (int i = 0; i < K1_ITEMS; ++i) {
-      const int e = tid * K1_ITEMS + i;
-      const int d = s_deg[k1_pad(e)];
-      const int c0 = s_c0[k1_pad(e)];
-      const int nch = d > 0 ? ((c0 + d + 3) >> 2) - (c0 >> 2) : 0;
-      tsum += (d > 0 ? K1_CNT_ONE : 0ull) + (unsigned long long)nch;
-      wsum += (unsigned long long)d;
+      const int d = s_deg[k1_pad(tid * K1_ITEMS + i)];
+      tsum += (d > 0 ? K1_CNT_ONE : 0ull) + (unsigned long long)d;
       maxdeg = max(maxdeg, d);
     }
     unsigned long long btot;
@@ -190,35 +182,32 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
       const int e = tid * K1_ITEMS + i;
       const int d = s_deg[k1_pad(e)];
       if (d > 0) {
-        const int c0 = s_c0[k1_pad(e)];
-        const int nch = ((c0 + d + 3) >> 2) - (c0 >> 2);
         const int32_t q = (int32_t)((run >> 31) & K1_SUM_MASK);
         const int32_t w = (int32_t)(run & K1_SUM_MASK);
-        if (q < n && (int64_t)w + nch <= ws.cmax) {
+        if (q < n && (int64_t)w + d <= nnz) {
           ws.cw[q] = w;
-          ws.cb[q] = c0;
-          ws.cd[q] = d;
+          ws.cb[q] = s_c0[k1_pad(e)];
           ws.cx[q] = s_xv[k1_pad(e)];
-          for (int64_t t = ((int64_t)w + QF - 1) / QF; t * QF < (int64_t)w + nch; ++t) ws.tile_k0[t] = q;
+          for (int64_t t = ((int64_t)w + QF - 1) / QF; t * QF < (int64_t)w + d; ++t) ws.tile_k0[t] = q;
         } else {
-          atomicOr(&st->status, ST_INDEX);  // more work than the matrix holds: duplicate x indices
+          atomicOr(&st->status, ST_INDEX);  // more products than nonzeros: duplicate x indices
         }
-        run += K1_CNT_ONE + (unsigned long long)nch;
+        run += K1_CNT_ONE + (unsigned long long)d;
       }
     }
     if (tile == nt1 - 1 && tid == 0) {
       const unsigned long long tot = s_prefix + btot;
       int32_t fc = (int32_t)((tot >> 31) & K1_SUM_MASK);
-      int32_t C = (int32_t)(tot & K1_SUM_MASK);
-      if (fc > n || (int64_t)C > ws.cmax) {  // only with duplicate x indices
+      int32_t W = (int32_t)(tot & K1_SUM_MASK);
+      if (fc > n || (int64_t)W > nnz) {  // only with duplicate x indices
         atomicOr(&st->status, ST_INDEX);
         fc = 0;
-        C = 0;
+        W = 0;
       }
       st->fc = fc;
-      st->C = C;
-      ws.cw[fc] = C;
-      ws.tile_k0[(C + QF - 1) / QF] = fc;
+      st->W = W;
+      ws.cw[fc] = W;
+      ws.tile_k0[(W + QF - 1) / QF] = fc;
     }
     __syncthreads();
   }
@@ -238,23 +227,12 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
     if ((tid & 31) == 0 && mc) atomicAdd(&s_maskcnt, mc);
   }
   __syncthreads();
-  // products of this CTA's entries
-  for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-  if ((tid & 31) == 0) s_wsum[tid >> 5] = wsum;
-  __syncthreads();
-  if (tid == 0) {
-    unsigned long long bw = 0;
-    for (int i = 0; i < K1_THREADS / 32; ++i) bw += s_wsum[i];
-    if (bw) atomicAdd(&st->Wacc, bw);
-  }
   if (tid == 0 && s_maxdeg > 0) atomicMax(&st->maxdeg, s_maxdeg);
   if (tid == 0 && s_maskcnt > 0) atomicAdd(&st->maskcnt, s_maskcnt);
-  // with the selector in this launch, the last CTA to finish sees every
-  // CTA's sums: it sets W and runs the selector (otherwise the call's last
-  // kernel sets W)
   if (!sel.w) return;
-  // the CTA that finishes the last piece of work runs it: with a mask pass
-  // every CTA is a piece, otherwise every tile (CTAs without one add nothing)
+  // the selector runs in the CTA that finishes the last piece of work, once
+  // every count is in: with a mask pass every CTA is a piece, otherwise every
+  // tile (CTAs without one add nothing and skip the counter)
   const uint32_t units = mask ? 1u : my_tiles;
   const uint32_t total = mask ? gridDim.x : nt1;
   if (total == 0 ? blockIdx.x != 0 : units == 0) return;
@@ -265,16 +243,8 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
   __syncthreads();
   if (s_last) {
     __threadfence();
-    if (tid == 0) {
-      const unsigned long long wt = __ldcg(&st->Wacc);
-      st->Wacc = 0ull;
-      st->k1_done = 0u;
-      if (wt > (unsigned long long)nnz) atomicOr(&st->status, ST_INDEX);  // duplicate x indices
-      st->W = wt > (unsigned long long)nnz ? 0 : (int32_t)wt;
-      __threadfence();  // the selector reads W from L2
-    }
-    __syncthreads();
     if (tid < 32) sel_choose_warp(sel.w, st, m, n, nnz, sel);
+    if (tid == 0) st->k1_done = 0u;
   }
 }
 
@@ -309,14 +279,13 @@ __device__ __forceinline__ void spa_apply(uint32_t* spa, uint32_t r, uint32_t v)
 // K2: expand + multiply + bucket scatter
 // ------------------------------------------------------------------------
 
-// One tile = q consecutive chunks (a merge-path slice of the selected
-// columns; a chunk is 4 aligned entries of the row-id and value arrays, read
-// with one 16-byte load each, entries outside the column masked off).  Each
-// warp takes 32*items consecutive chunks with its lanes on consecutive chunks
-// (coalesced 128-bit loads).  The x entry of a chunk comes from a bitmap of
-// the tile's entry starts: the 32 chunks of one warp load are one bitmap
-// word, so a lane's entry is the count of starts before its word plus a
-// popcount inside the word (no search, no divergence).  Products are counted per bucket with
+// One tile = q consecutive products (a merge-path slice of the selected
+// columns).  Each warp takes a contiguous chunk of 32*items products with
+// its lanes on consecutive products (coalesced row-id and value loads).  The
+// x entry of a product comes from a bitmap of the tile's entry starts: the
+// 32 products of one warp load are one bitmap word, so a lane's entry is the
+// count of starts before its word plus a popcount inside the word (no
+// search, no divergence).  Products are counted per bucket with
 // shared-memory atomics, one warp scans the counts, every non-empty bucket
 // gets one run reserved with a global atomic, the products are staged in
 // shared memory grouped by bucket and written out in runs.  Hub rows (row ids >= m in the relabelled
@@ -333,11 +302,9 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
 
   unsigned char* p = k2_smem_raw;
   uint2* stage = (uint2*)p; p += sizeof(uint2) * QMAX;
-  uint32_t* hbits = (uint32_t*)p; p += sizeof(uint32_t) * (QCMAX / 32);  // entry starts (chunks)
-  int32_t* kbase = (int32_t*)p; p += sizeof(int32_t) * (QCMAX + 1);   // first chunk - chunk offset
-  uint32_t* kx = (uint32_t*)p; p += sizeof(uint32_t) * (QCMAX + 1);   // x value
-  int32_t* klo = (int32_t*)p; p += sizeof(int32_t) * (QCMAX + 1);     // column start
-  int32_t* khi = (int32_t*)p; p += sizeof(int32_t) * (QCMAX + 1);     // column end
+  uint32_t* hbits = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX / 32);  // entry starts of the tile
+  int32_t* kbase = (int32_t*)p; p += sizeof(int32_t) * (QMAX + 1);
+  uint32_t* kx = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX + 1);
   int32_t* hist = (int32_t*)p; p += sizeof(int32_t) * nb_fine;   // counts, then stage offsets
   int32_t* gd = (int32_t*)p; p += sizeof(int32_t) * nb_fine;     // counts, then slot - stage offset
   uint32_t* hacc = (uint32_t*)p;                                 // hub sums of this tile
@@ -346,15 +313,12 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
 
   const DevState* st = ws.st;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int32_t C = st->C, fc = st->fc, q = st->q, lwb = st->lwb;
+  const int32_t W = st->W, fc = st->fc, q = st->q, lwb = st->lwb;
   const int sh = lwb - lwb_lo;
   const int nb = (int)(((int64_t)m + (1 << lwb) - 1) >> lwb);
   const uint32_t wmask = (1u << lwb) - 1u;
-  const int items = q / K2_THREADS;  // chunks per thread
-  const int ntiles = (int)(((int64_t)C + q - 1) / q);
-  const uint4* rowidx4 = reinterpret_cast<const uint4*>(rowidx);
-  const float4* val4 = reinterpret_cast<const float4*>(val);
-  const int64_t nchunk_full = nnz >> 2;  // chunks lying wholly inside the arrays
+  const int items = q / K2_THREADS;
+  const int ntiles = (int)(((int64_t)W + q - 1) / q);
   const uint32_t ident = sr_identity<SEM>();
   const int nhot = ws.nhot;
 
@@ -365,26 +329,23 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
     }
     for (int i = tid; i < HOT_MAX / 32; i += K2_THREADS) htb[i] = 0u;
   }
-  for (int i = tid; i < QCMAX / 32; i += K2_THREADS) hbits[i] = 0u;
+  for (int i = tid; i < QMAX / 32; i += K2_THREADS) hbits[i] = 0u;
   __syncthreads();
 
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int32_t p0 = t * q;  // first chunk of the tile
-    const int32_t np = min(q, C - p0);
+    const int32_t p0 = t * q;
+    const int32_t np = min(q, W - p0);
     const int32_t k0 = ws.tile_k0[p0 / QF];
-    const int32_t kend = (p0 + np == C) ? fc : ws.tile_k0[(p0 + np) / QF] + 1;
-    const int32_t nk = max(1, min(kend - k0, QCMAX + 1));
+    const int32_t kend = (p0 + np == W) ? fc : ws.tile_k0[(p0 + np) / QF] + 1;
+    const int32_t nk = max(1, min(kend - k0, QMAX + 1));
 
     // the first K2_THREADS entries of every tile but a CTA's first were
     // loaded during the previous tile (below)
     for (int l = tid + (t != (int)blockIdx.x ? K2_THREADS : 0); l < nk; l += K2_THREADS) {
       const int32_t k = k0 + l;
       const int32_t w = ws.cw[k];
-      const int32_t c0 = ws.cb[k];
-      kbase[l] = (c0 >> 2) - w;
+      kbase[l] = ws.cb[k] - w;
       kx[l] = ws.cx[k];
-      klo[l] = c0;
-      khi[l] = c0 + ws.cd[k];
       const int32_t off = w - p0;  // entries after the first start inside the tile
       if (l > 0 && off > 0 && off < np) atomicOr(&hbits[off >> 5], 1u << (off & 31));
     }
@@ -401,50 +362,25 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
       for (int j = lane; j < w0; j += 32) ent += __popc(hbits[j]);
       ent = __reduce_add_sync(0xffffffffu, ent);
       const uint32_t le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
-      // phase 1: every chunk's address, then all loads in flight at once;
-      // element 4c+j of chunk c goes to slot 4*ci+j
+      // phase 1: every item's address, then all loads in flight at once
       uint32_t xi[K2_IMAX];
       float av[K2_IMAX];
 #pragma unroll
-      for (int ci = 0; ci < K2_CIMAX; ++ci) {
-        const int32_t pl = pw0 + 32 * ci;
-        const uint32_t hw = ci < items ? hbits[w0 + ci] : 0u;
+      for (int i = 0; i < K2_IMAX; ++i) {
+        const int32_t pl = pw0 + 32 * i;
+        rrow[i] = 0xffffffffu;
+        xi[i] = 0u;
+        av[i] = 1.0f;
+        const uint32_t hw = i < items ? hbits[w0 + i] : 0u;
         const int e = ent + __popc(hw & le);
         ent += __popc(hw);
-        uint4 r4 = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-        float4 v4 = make_float4(1.f, 1.f, 1.f, 1.f);
-        int32_t lo = 0, hi = 0;
-        uint32_t xv = 0u;
-        int64_t g = -1;
-        if (ci < items && pl < np) {
-          g = (int64_t)kbase[e] + p0 + pl;  // chunk index in the arrays
-          xv = kx[e];
-          lo = klo[e];
-          hi = khi[e];
-          if (g >= 0 && g < nchunk_full) {
-            r4 = ld_stream(rowidx4 + g);
-            if (SEM == kPlusTimes && val) v4 = ld_stream(val4 + g);
-          } else if (g >= 0 && 4 * g < nnz) {  // the arrays' last, partial chunk
-            const int64_t e0 = 4 * g;
-            r4.x = (uint32_t)rowidx[e0];
-            if (e0 + 1 < nnz) r4.y = (uint32_t)rowidx[e0 + 1];
-            if (e0 + 2 < nnz) r4.z = (uint32_t)rowidx[e0 + 2];
-            if (SEM == kPlusTimes && val) {
-              v4.x = val[e0];
-              if (e0 + 1 < nnz) v4.y = val[e0 + 1];
-              if (e0 + 2 < nnz) v4.z = val[e0 + 2];
-            }
+        if (i < items && pl < np) {
+          const int32_t pos = kbase[e] + p0 + pl;
+          xi[i] = kx[e];
+          if ((uint32_t)pos < (uint32_t)nnz) {  // always true with valid inputs
+            rrow[i] = (uint32_t)ld_stream(rowidx + pos);
+            if (SEM == kPlusTimes && val) av[i] = ld_stream(val + pos);
           }
-        }
-        const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
-        const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int64_t pe = 4 * g + j;  // array position of this element
-          const bool in = g >= 0 && pe >= lo && pe < hi;
-          rrow[4 * ci + j] = in ? rr[j] : 0xffffffffu;
-          av[4 * ci + j] = vv[j];
-          xi[4 * ci + j] = xv;
         }
       }
       // phase 2: multiply, filter, count per bucket
@@ -482,23 +418,22 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
       }
     }
     __syncthreads();
-    for (int j = tid; j < QCMAX / 32; j += K2_THREADS) hbits[j] = 0u;  // phase 1 is done
+    for (int j = tid; j < QMAX / 32; j += K2_THREADS) hbits[j] = 0u;  // phase 1 is done
 
     // ---- the next tile's x entries: in flight during this tile's scan,
     // reservation and stores, written to shared memory before the write-out ----
     const int tn = t + (int)gridDim.x;
-    int32_t p0n = 0, npn = 0, nkn = 0, pw = 0, pcb = 0, pcd = 0;
+    int32_t p0n = 0, npn = 0, nkn = 0, pw = 0, pcb = 0;
     uint32_t pcx = 0u;
     if (tn < ntiles) {
       p0n = tn * q;
-      npn = min(q, C - p0n);
+      npn = min(q, W - p0n);
       const int32_t k0n = ws.tile_k0[p0n / QF];
-      const int32_t kendn = (p0n + npn == C) ? fc : ws.tile_k0[(p0n + npn) / QF] + 1;
-      nkn = max(1, min(kendn - k0n, QCMAX + 1));
+      const int32_t kendn = (p0n + npn == W) ? fc : ws.tile_k0[(p0n + npn) / QF] + 1;
+      nkn = max(1, min(kendn - k0n, QMAX + 1));
       if (tid < nkn) {
         pw = ws.cw[k0n + tid];
         pcb = ws.cb[k0n + tid];
-        pcd = ws.cd[k0n + tid];
         pcx = ws.cx[k0n + tid];
       }
     }
@@ -558,10 +493,8 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
     if (nhot > 0 && warp == 1) htb[lane] = 0u;
     __syncthreads();
     if (tid < nkn) {  // the next tile's entries (this tile's are no longer read)
-      kbase[tid] = (pcb >> 2) - pw;
+      kbase[tid] = pcb - pw;
       kx[tid] = pcx;
-      klo[tid] = pcb;
-      khi[tid] = pcb + pcd;
       const int32_t off = pw - p0n;
       if (tid > 0 && off > 0 && off < npn) atomicOr(&hbits[off >> 5], 1u << (off & 31));
     }
@@ -643,12 +576,7 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
   if (BFS && !ws.job && st->bfs_fb) fbn = st->bfs_fb + ((lvl & 1) ? fb_words : 0);
 
   if (blockIdx.x == 0 && tid == 0) {
-    // clear K1's per-call state for the next call; W from the work scan's sums
-    const unsigned long long wa = st->Wacc;
-    if (wa) {
-      st->W = (int32_t)min(wa, 0x7fffffffull);
-      st->Wacc = 0ull;
-    }
+    // clear K1's per-call state for the next call
     st->k1_ticket = 0u;
     st->last_maxdeg = st->maxdeg;
     st->last_maskcnt = st->maskcnt;

@@ -29,8 +29,7 @@ constexpr int NA_MAX_X = 1 << 16;          // nnz(x)
 constexpr int64_t NA_MAX_NNZ = 1 << 20;    // nnz(A)
 constexpr int32_t NA_MAX_M = 1 << 22;      // rows of A
 constexpr int NA_NB_MAX = 512;             // fine buckets for m <= NA_MAX_M
-// chunks of one call are at most ceil(nnz/4) + 2 per x entry
-constexpr int NA_TILES = (int)(((NA_MAX_NNZ + 3) / 4 + 2 * NA_MAX_X) / QF) + 2;
+constexpr int NA_TILES = (int)(NA_MAX_NNZ / QF) + 2;
 constexpr int NA_K1_TILES = NA_MAX_X / K1_TILE + 1;
 constexpr int NA_MAX_DEVICES = 64;
 
@@ -46,8 +45,7 @@ constexpr size_t NA_ZERO_BYTES = NA_OFF_CNT + na_align(sizeof(int32_t) * (NA_NB_
 constexpr size_t NA_OFF_RB = NA_ZERO_BYTES;
 constexpr size_t NA_OFF_CW = NA_OFF_RB + na_align(sizeof(int32_t) * (NA_NB_MAX + 1));
 constexpr size_t NA_OFF_CB = NA_OFF_CW + na_align(sizeof(int32_t) * (NA_MAX_X + 1));
-constexpr size_t NA_OFF_CD = NA_OFF_CB + na_align(sizeof(int32_t) * NA_MAX_X);
-constexpr size_t NA_OFF_CX = NA_OFF_CD + na_align(sizeof(int32_t) * NA_MAX_X);
+constexpr size_t NA_OFF_CX = NA_OFF_CB + na_align(sizeof(int32_t) * NA_MAX_X);
 constexpr size_t NA_OFF_TK = NA_OFF_CX + na_align(sizeof(uint32_t) * NA_MAX_X);
 constexpr size_t NA_OFF_BR = NA_OFF_TK + na_align(sizeof(int32_t) * NA_TILES);
 constexpr size_t NA_OFF_BV = NA_OFF_BR + na_align(sizeof(uint16_t) * NA_MAX_NNZ);
@@ -135,8 +133,6 @@ extern "C" int spmspv_run_noalloc(int32_t m, int32_t n, int64_t nnz, const int32
   if (val_type != SPMSPV_VAL_NONE && val_type != SPMSPV_VAL_F32)
     return fail(SPMSPV_ERR_ARG, "unknown val_type %d", val_type);
   if (val_type == SPMSPV_VAL_F32 && nnz > 0 && !val) return fail(SPMSPV_ERR_ARG, "val is NULL");
-  if (nnz > 0 && (((uintptr_t)rowidx & 15u) || (val_type == SPMSPV_VAL_F32 && ((uintptr_t)val & 15u))))
-    return fail(SPMSPV_ERR_ARG, "rowidx and val must be 16-byte aligned (read 16 bytes at a time)");
   if (semiring < 0 || semiring > 2) return fail(SPMSPV_ERR_ARG, "unknown semiring %d", semiring);
   if (nnz_x > 0 && !x_idx) return fail(SPMSPV_ERR_ARG, "x_idx is NULL");
   if (nnz_x > 0 && semiring != SPMSPV_OR_AND_BOOL && !x_val) return fail(SPMSPV_ERR_ARG, "x_val is NULL");
@@ -181,8 +177,6 @@ extern "C" int spmspv_run_noalloc(int32_t m, int32_t n, int64_t nnz, const int32
   ws.rbase = (int32_t*)(base + NA_OFF_RB);
   ws.cw = (int32_t*)(base + NA_OFF_CW);
   ws.cb = (int32_t*)(base + NA_OFF_CB);
-  ws.cd = (int32_t*)(base + NA_OFF_CD);
-  ws.cmax = (int32_t)((nnz + 3) / 4 + 2 * (int64_t)nnz_x);
   ws.cx = (uint32_t*)(base + NA_OFF_CX);
   ws.tile_k0 = (int32_t*)(base + NA_OFF_TK);
   ws.brow = (uint16_t*)(base + NA_OFF_BR);
@@ -191,7 +185,6 @@ extern "C" int spmspv_run_noalloc(int32_t m, int32_t n, int64_t nnz, const int32
   ws.hot_rows = nullptr;
   ws.rowidx_k2 = nullptr;
   ws.pull_status = nullptr;
-  ws.pull_tiles = 0;
   ws.job = nullptr;
   ws.hot_start = nullptr;
   ws.hot_val = nullptr;
@@ -212,9 +205,9 @@ extern "C" int spmspv_run_noalloc(int32_t m, int32_t n, int64_t nnz, const int32
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "region start launch");
 
   Sched sc;
-  sc.id = 5;
+  sc.id = 5;  // the default schedule: 4096-product tiles, widest buckets
   sc.dir = 0;
-  sc.q = 3 * QF;  // schedule 5 (the default): the larger quantum, widest bucket
+  sc.q = 2 * QF;
   sc.lwb = lwb_lo + 2;
   const int k1_grid = (int)((nnz_x + K1_TILE - 1) / K1_TILE);
   e = launch_k1(semiring, A, ws, nb_fine, x_idx, (const uint32_t*)x_val, nnz_x, nullptr, k1_grid,

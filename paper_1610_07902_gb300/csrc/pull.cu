@@ -89,14 +89,8 @@ k_pull_rows(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowi
     fb_next = st->bfs_fb + ((lvl & 1) ? words : 0);
   }
   if (blockIdx.x == 0) {
-    // this kernel ends the call: clear the work scan's per-call state; W
-    // from the work scan's sums
+    // this kernel ends the call: clear the work scan's per-call state
     if (tid == 0) {
-      const unsigned long long wa = st->Wacc;
-      if (wa) {
-        st->W = (int32_t)min(wa, 0x7fffffffull);
-        st->Wacc = 0ull;
-      }
       st->k1_ticket = 0u;
       st->last_maxdeg = st->maxdeg;
       st->last_maskcnt = st->maskcnt;

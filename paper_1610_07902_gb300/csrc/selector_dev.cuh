@@ -83,7 +83,7 @@ __device__ __forceinline__ void sel_choose_warp(const float* __restrict__ w, Dev
     const int id = bi < SEL_OUT ? bi : 4;
     st->sched = id;
     st->dir = id / 6;
-    st->q = ((id / 3) % 2) ? 3 * QF : 2 * QF;
+    st->q = ((id / 3) % 2) ? 2 * QF : QF;
     st->lwb = lwb_lo + id % 3;
     if (a.use_cond) {
       cudaGraphSetConditional(a.c_push, id / 6 == 0 ? 1u : 0u);

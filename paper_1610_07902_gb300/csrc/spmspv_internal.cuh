@@ -20,17 +20,12 @@ constexpr int K1_ITEMS = 8;
 constexpr int K1_TILE = K1_THREADS * K1_ITEMS;  // x entries per scan tile
 
 // ---- K2: expand + multiply + bucket scatter ----
-// The work is counted in chunks: aligned groups of 4 consecutive entries of
-// the row-id (and value) array, read with one 16-byte load each; column
-// segment [c0, c1) covers ceil(c1/4) - floor(c0/4) chunks.  Tile starts are
-// recorded every QF chunks; a K2 tile covers q = 2*QF or 3*QF chunks (the
-// "work quantum" of the schedule), i.e. at most 4096 or 6144 products.
-constexpr int QF = 512;
+// Tile starts are recorded every QF products; a K2 tile covers q = QF or
+// 2*QF products (the "work quantum" of the schedule).
+constexpr int QF = 2048;
 constexpr int K2_THREADS = 512;
-constexpr int K2_CIMAX = 3;                    // chunks per thread at q = 3*QF
-constexpr int K2_IMAX = 4 * K2_CIMAX;          // products per thread
-constexpr int QCMAX = K2_THREADS * K2_CIMAX;   // 1536 chunks
-constexpr int QMAX = 4 * QCMAX;                // 6144 products
+constexpr int K2_IMAX = 8;                   // products per thread at q = 4096
+constexpr int QMAX = K2_THREADS * K2_IMAX;   // 4096
 
 // ---- K3: per-bucket SPA merge + ordered compaction ----
 constexpr int K3_THREADS = 512;
@@ -86,9 +81,7 @@ struct DevState {
   int32_t* bfs_parent;
   uint32_t* bfs_fb;    // BFS: two frontier bitmaps of ceil(n/32) words; level L reads
                        // bitmap (L-1)&1 (pull) and writes bitmap L&1 (K3 or pull)
-  uint32_t k1_done;    // K1 CTAs finished; the last one sets W, runs the selector (self-resetting)
-  int32_t C;           // chunks of the selected columns (K2's work)
-  unsigned long long Wacc;  // products summed by K1's CTAs (reset by the last one)
+  uint32_t k1_done;    // K1 CTAs finished; the last one runs the selector (self-resetting)
 };
 
 // Selector run inside the work scan by its last CTA to finish: weights (NULL:
@@ -127,10 +120,8 @@ struct Workspace {
   DevState* st;
   int32_t* cw;          // [n+1] exclusive work offsets of the compacted x entries
   int32_t* cb;          // [n]   first position of each compacted x entry's column
-  int32_t* cd;          // [n]   length of each compacted x entry's column
-  int32_t cmax;         // bound on the chunks of one call: ceil(nnz/4) + 2 * (x entries)
   uint32_t* cx;         // [n]   x value (32-bit payload) of each compacted entry
-  int32_t* tile_k0;     // [cmax/QF + 2] compacted entry holding chunk t*QF
+  int32_t* tile_k0;     // [nnz/QF + 2] compacted entry holding product t*QF
   unsigned long long* k1_status;  // [ceil(n/K1_TILE)] look-back words of K1
   int32_t* bfill;       // [nb_fine * BFILL_STRIDE] fill counters of the buckets
   unsigned long long* k3_status;  // [nb_fine] look-back words of K3
@@ -164,7 +155,7 @@ struct Matrix {
 struct Sched {
   int id;    // schedule id: dir * 6 + quantum * 3 + width
   int dir;   // 0 push, 1 pull
-  int q;     // 2*QF or 3*QF chunks
+  int q;     // QF or 2*QF
   int lwb;   // log2 bucket width
 };
 
@@ -190,13 +181,14 @@ cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, i
 cudaError_t launch_bucket_sizes(const Matrix& A, int lwb_lo, int nb_fine, int32_t* counts,
                                 unsigned int* bad, cudaStream_t s);
 // K2 shared memory: staged (row, value) pairs of one tile, the bitmap of
-// entry starts (in chunks), the chunk base, x value and column bounds of the
-// tile's x entries, the bucket histogram and slots, and the hub-row tables.
+// entry starts, cb - cw and x value of the tile's x entries, the bucket
+// histogram and slots, and the hub-row tables.
 __host__ __device__ constexpr size_t k2_smem_bytes(int nb_fine, bool hot) {
-  return sizeof(uint32_t) * 2 * QMAX + sizeof(uint32_t) * (QCMAX / 32) + 4 * sizeof(int32_t) * (QCMAX + 1) +
-         sizeof(int32_t) * (size_t)nb_fine * 2 + 64 +
+  return sizeof(uint32_t) * 2 * QMAX + sizeof(uint32_t) * (QMAX / 32) + sizeof(int32_t) * (QMAX + 1) +
+         sizeof(uint32_t) * (QMAX + 1) + sizeof(int32_t) * (size_t)nb_fine * 2 + 64 +
          (hot ? sizeof(uint32_t) * HOT_MAX * 2 + sizeof(uint32_t) * (HOT_MAX / 32) + 64 : 0);
 }
+// K3 shared memory: the SPA values and the occupancy bitmap of one bucket
 // K3 shared memory: the SPA values and the occupancy bitmap of one bucket
 __host__ __device__ constexpr size_t k3_smem_bytes(int lwb) {
   return ((size_t)1 << lwb) * sizeof(uint32_t) + (((size_t)1 << lwb) / 32) * sizeof(uint32_t);
