@@ -213,6 +213,37 @@ def bench_bfs(S, A, dev, stream, name, sources, params, pt_frontiers=False):
         out["plus_times_per_frontier"] = {"calls": len(fr), "products": pw, "ms": t,
                                           "gteps": pw / (t * 1e-3) / 1e9,
                                           "us_per_call": 1e3 * t / len(fr)}
+        # the same products as one batched launch (autotuned lanes)
+        B = len(fr)
+        x_cnt = np.array([f.shape[0] for f in fr], np.int32)
+        x_off = np.concatenate([[0], np.cumsum(x_cnt)[:-1]]).astype(np.int32)
+        y_cap = np.array([max(1, int(deg[f.long()].sum().item())) for f in fr], np.int64)
+        y_off = np.concatenate([[0], np.cumsum(y_cap)[:-1]])
+        td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        xi_all, xv_all = torch.cat(fr), torch.cat(xv)
+        yi_all = torch.empty(int(y_cap.sum()), dtype=torch.int32, device=dev)
+        yv_all = torch.empty(int(y_cap.sum()), dtype=torch.float32, device=dev)
+        nz_all = torch.zeros(B, dtype=torch.int32, device=dev)
+        d_off, d_cnt = td(x_off), td(x_cnt)
+        d_yoff, d_ycap = td(y_off.astype(np.int32)), td(y_cap.astype(np.int32))
+
+        def batched():
+            S.spmspv_run_batched(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, B, d_off, d_cnt, xi_all, xv_all,
+                                 None, 0, 0, d_yoff, d_ycap, yi_all, yv_all, nz_all, 0, stream)
+        batched()  # tunes on first use
+        tb = _events_ms(batched, stream, 2)
+        tuned = S.spmspv_last_tuned(Ad.handle)
+        nzb = nz_all.cpu().numpy()
+        same = True
+        for b in range(0, B, max(1, B // 24)):  # spot check against single calls
+            S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, fr[b], xv[b], fr[b].shape[0], None,
+                         S.SPMSPV_SORTED_OUT, yi, yv, cap, nz, stream)
+            k = int(nz.item())
+            o = int(y_off[b])
+            same &= k == int(nzb[b]) and torch.equal(yi[:k], yi_all[o:o + k])
+        out["plus_times_per_frontier"].update({
+            "batched_ms": tb, "batched_gteps": pw / (tb * 1e-3) / 1e9, "batched_speedup": t / tb,
+            "batched_lanes": tuned[0], "batched_schedule": tuned[1], "batched_identical_index_sets": same})
     Ad.close()
     return out
 
@@ -511,6 +542,22 @@ def main():
     extras = {}
     if rank == 0 and not args.no_extras:
         import synth
+        # the same graph at the smaller frontiers of the sweep (host-launched calls)
+        sweep = {}
+        for fs in (100, 10_000):
+            sxi, sxv = synth.frontier(A.n, fs, seed=1, stream=2)
+            dxi, dxv = torch.from_numpy(sxi).to(dev), torch.from_numpy(sxv).to(dev)
+            run = lambda: S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, dxi, dxv, fs, None, opts,
+                                       y_idx, y_val, cap, nnz_y, stream)
+            for _ in range(5):
+                run()
+            reps = 200
+            tms = _events_ms(lambda: [run() for _ in range(reps)], stream, 1) / reps
+            ws_ = S.spmspv_last_work(Ad.handle)
+            sweep["nnz_x_%d" % fs] = {"us_per_call": 1e3 * tms, "products": ws_,
+                                       "gteps": ws_ / (tms * 1e-3) / 1e9}
+        sweep["note"] = "back-to-back host-launched calls, L2 not flushed between them"
+        extras["sweep_rmat"] = sweep
         params = selector_params()
         extras["bfs_rmat"] = bench_bfs(S, A, dev, stream, "rmat s%d ef16 seed 1" % args.scale,
                                        synth.sources(A.colptr, 64, seed=2), params)
