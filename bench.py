@@ -332,6 +332,21 @@ def bench_batched(S, dev, stream, B=256):
         same &= bool(torch.equal(lv1, lv[b * A.n:(b + 1) * A.n]) and torch.equal(pa1, pa[b * A.n:(b + 1) * A.n]))
     out["msbfs"] = {"batched_ms": t_ms, "sequential_ms": t_seq, "speedup": t_seq / t_ms,
                     "tuned_lanes": tuned[0], "tuned_schedule": tuned[1], "identical_results": same}
+    params = selector_params()
+    if params is not None:
+        # the same searches with the learned schedule (push or pull per source
+        # and level) inside the lanes, against the same sequential searches
+        S.spmspv_selector_set(Ap.handle, params)
+        lv2 = torch.empty_like(lv)
+        pa2 = torch.empty_like(pa)
+        msl = lambda: S.spmspv_msbfs(Ap.handle, B, ds, lv2, pa2, None, S.SPMSPV_SCHED_AUTO, 0, stream)
+        msl()
+        t_msl = _events_ms(msl, stream, 2)
+        tuned = S.spmspv_last_tuned(Ap.handle)
+        out["msbfs"].update({"learned_batched_ms": t_msl, "learned_speedup": t_seq / t_msl,
+                             "learned_lanes": tuned[0],
+                             "learned_identical_results": bool(torch.equal(lv2, lv) and torch.equal(pa2, pa))})
+        del lv2, pa2
     del lv, pa
 
     # ACL from 256 seeds vs one seed at a time

@@ -212,6 +212,10 @@ int spmspv_run_batched(spmspv_handle* h, int semiring, int32_t B, const int32_t*
  *   opts, lanes    as for spmspv_run_batched (schedule, 1..16 lanes, or 0 for
  *                  autotuned: the first call with a new B profile runs the whole
  *                  search under every candidate, timed, and caches the fastest).
+ *                  SPMSPV_SCHED_AUTO (weights set, pattern-symmetric handle): the
+ *                  learned schedule picks push or pull per source and level, as in
+ *                  spmspv_bfs; levels and parents are the same either way.
+ *                  It adds B*n/4 bytes of frontier bitmaps.
  * Allocates B*(4n + n/8) bytes of frontiers and visited bitmaps for the call;
  * synchronises the stream once per level to test for termination.
  */
@@ -241,7 +245,8 @@ int spmspv_acl(spmspv_handle* h, int32_t B, const int32_t* seeds, float alpha, f
 
 /* ---- autotuner of the batched form (no counterpart in the paper) ----
  * The cache lives in the handle (lost at spmspv_destroy).  A profile key packs
- * kind (0 batched SpMSpV, 1 multi-source BFS, 2 ACL), semiring, whether masks
+ * kind (0 batched SpMSpV, 1 multi-source BFS, 2 ACL, 3 multi-source BFS with
+ * the learned schedule: lanes only, schedule entry 0), semiring, whether masks
  * are given, ceil(log2 B) and ceil(log2(1 + total nnz(x) / B)); calls whose
  * profiles share a key share one tuning.  spmspv_tune_key is pure host code.
  */

@@ -56,7 +56,7 @@ uint64_t tune_key(int kind, int sem, int masked, int32_t B, int64_t total_f) {
 }
 
 int tune_and_run(spmspv_handle* h, uint64_t key, cudaStream_t s,
-                 const std::function<int(int32_t, uint32_t)>& run) {
+                 const std::function<int(int32_t, uint32_t)>& run, int nsched) {
   TuneCache* tc = cache_of(h);
   for (const TuneEntry& t : tc->entries) {
     if (t.key != key) continue;
@@ -75,7 +75,7 @@ int tune_and_run(spmspv_handle* h, uint64_t key, cudaStream_t s,
   TuneEntry best{key, 0, -1, INFINITY};
   int rc = SPMSPV_OK;
   for (int32_t lanes : kLaneChoices) {
-    for (int sid = 0; sid < SPMSPV_NUM_SCHEDULES / 2 && rc == SPMSPV_OK; ++sid) {
+    for (int sid = 0; sid < nsched && rc == SPMSPV_OK; ++sid) {
       const uint32_t o = SPMSPV_SCHED_FORCE | SPMSPV_SCHED_OPT(sid);
       // first run: graph instantiation and first touch; second run: timed
       if ((rc = run(lanes, o)) != SPMSPV_OK) break;

@@ -43,6 +43,9 @@ struct BatchDesc {
   int32_t* level;   // BFS mode: [B][n]
   int32_t* parent;  // BFS mode: [B][n]
   int64_t vstride;  // n
+  uint32_t* fb;     // learned BFS: [B][2][ceil(n/32)] frontier bitmaps
+  int64_t fb_stride;
+  const int32_t* nvis;  // learned BFS: [B] vertices reached per source
 };
 
 struct BatchState {
@@ -50,7 +53,8 @@ struct BatchState {
   spmspv_handle* sub[MAX_LANES];  // one workspace per lane
   Job* jobs;                      // [MAX_LANES] device
   BatchDesc* desc;                // device
-  cudaGraphExec_t graphs[3][SPMSPV_NUM_SCHEDULES][2][MAX_LANES + 1];
+  // [semiring][schedule, or SPMSPV_NUM_SCHEDULES for the learned BFS][bfs][lanes]
+  cudaGraphExec_t graphs[3][SPMSPV_NUM_SCHEDULES + 1][2][MAX_LANES + 1];
 };
 
 namespace {
@@ -94,6 +98,8 @@ __global__ void k_batch_pop(BatchDesc* d, Job* job) {
       j.parent = d->parent + (int64_t)b * d->vstride;
       j.visited = const_cast<uint32_t*>(j.mask);
       j.lvl = d->lvl;
+      if (d->fb) j.fb = d->fb + (int64_t)b * d->fb_stride;
+      if (d->nvis) j.nvis = d->nvis[b];
     }
   }
   *job = j;
@@ -109,12 +115,39 @@ __global__ void k_batch_continue(cudaGraphConditionalHandle cond, const BatchDes
 
 }  // namespace
 
+// One lane's loop body.  sel_w != NULL (BFS only): the learned schedule; the
+// work scan's last CTA picks push or pull per source and level, the push
+// kernels and the pull kernel all follow and the ones not chosen return.
 static int lane_launches(spmspv_handle* sub, BatchState* bs, int lane, int sem, bool bfs,
-                         const Sched& sc, cudaGraphConditionalHandle cond, cudaStream_t s) {
+                         const Sched& sc, const float* sel_w, cudaGraphConditionalHandle cond,
+                         cudaStream_t s) {
   k_batch_pop<<<1, 32, 0, s>>>(bs->desc, bs->jobs + lane);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "batch pop");
   const int k1_grid = sub->sm_count;
+  if (bfs && sel_w) {
+    SelArgs sa{};
+    sa.w = sel_w;
+    sa.allow_pull = 1;
+    sa.bfs = 1;
+    sa.lwb_lo = sub->lwb_lo;
+    if ((e = launch_k1_bfs(sub->A, sub->ws, sub->nb_fine, nullptr, nullptr, k1_grid, nullptr, s,
+                           nullptr, &sa)) != cudaSuccess)
+      return cuda_fail(e, "batch work scan");
+    if ((e = launch_k2(kMinSelect2nd, sub->A, sub->ws, sub->lwb_lo, sub->nb_fine, nullptr, 1,
+                       sub->k2_grid, sub->k2_smem, s, 1)) != cudaSuccess)
+      return cuda_fail(e, "batch expand/scatter");
+    const int lwb = sub->lwb_lo + 2;  // shared memory for the widest bucket
+    const int nb_max = (int)(((int64_t)sub->A.m + (1 << sub->lwb_lo) - 1) >> sub->lwb_lo);
+    const int k3_grid = std::max(1, std::min(nb_max, sub->sm_count * sub->k3_bps[2]));
+    if ((e = launch_k3(kMinSelect2nd, true, sub->A, sub->ws, sub->lwb_lo, sub->nb_fine, nullptr,
+                       nullptr, 0, nullptr, nullptr, k3_grid, k3_smem_bytes(lwb), s, 1)) != cudaSuccess)
+      return cuda_fail(e, "batch merge");
+    if ((e = launch_pull_rows_lane(sub, sub->rows_sorted, s)) != cudaSuccess)
+      return cuda_fail(e, "batch pull");
+    k_batch_continue<<<1, 32, 0, s>>>(cond, bs->desc);
+    return (e = cudaGetLastError()) == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "batch condition");
+  }
   if (bfs)
     e = launch_k1_bfs(sub->A, sub->ws, sub->nb_fine, nullptr, nullptr, k1_grid, &sc, s, nullptr);
   else
@@ -134,8 +167,8 @@ static int lane_launches(spmspv_handle* sub, BatchState* bs, int lane, int sem, 
   return (e = cudaGetLastError()) == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "batch condition");
 }
 
-static int build_batch_graph(BatchState* bs, int sem, bool bfs, const Sched& sc, int lanes,
-                             cudaGraphExec_t* out) {
+static int build_batch_graph(BatchState* bs, int sem, bool bfs, const Sched& sc,
+                             const float* sel_w, int lanes, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cs = nullptr;
@@ -164,7 +197,7 @@ static int build_batch_graph(BatchState* bs, int sem, bool bfs, const Sched& sc,
       rc = cuda_fail(e, "lane capture");
       break;
     }
-    rc = lane_launches(bs->sub[l], bs, l, sem, bfs, sc, cond, cs);
+    rc = lane_launches(bs->sub[l], bs, l, sem, bfs, sc, sel_w, cond, cs);
     cudaGraph_t tmp = nullptr;
     e = cudaStreamEndCapture(cs, &tmp);
     if (rc == SPMSPV_OK && e != cudaSuccess) rc = cuda_fail(e, "lane capture end");
@@ -216,7 +249,7 @@ void release_batch(spmspv_handle* h) {
   BatchState* bs = (BatchState*)h->batch;
   if (!bs) return;
   for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < SPMSPV_NUM_SCHEDULES; ++b)
+    for (int b = 0; b <= SPMSPV_NUM_SCHEDULES; ++b)
       for (int c = 0; c < 2; ++c)
         for (int d = 0; d <= MAX_LANES; ++d)
           if (bs->graphs[a][b][c][d]) cudaGraphExecDestroy(bs->graphs[a][b][c][d]);
@@ -237,14 +270,27 @@ int run_batched(spmspv_handle* h, int sem, bool bfs, int32_t B, const BatchDesc&
   if (lanes < 1 || lanes > MAX_LANES) return fail(SPMSPV_ERR_ARG, "lanes must be in [1, %d]", MAX_LANES);
   int sid = h->default_sched;
   if (opts & SPMSPV_SCHED_FORCE) sid = (int)SPMSPV_SCHED_ID(opts);
-  if (sid >= 6) sid -= 6;  // the lanes run the push form
+  if (sid >= 6) sid -= 6;  // the lanes run the push form (the learned BFS may pull)
+  // learned BFS: the selector picks push or pull per source and level
+  const bool learned = bfs && (opts & SPMSPV_SCHED_AUTO) && h->sel_w && h->sel_ready &&
+                       pull_available(h, kMinSelect2nd);
   BatchState* bs = nullptr;
   int rc = ensure_batch(h, lanes, &bs);
   if (rc) return rc;
+  if (learned) {
+    for (int l = 0; l < lanes; ++l) {
+      if (bs->sub[l]->xbits) continue;
+      cudaError_t e = alloc_pull_buffers(bs->sub[l]);
+      if (e != cudaSuccess) return cuda_fail(e, "lane pull buffers");
+    }
+  }
   const Sched sc = decode_schedule(h, sid);
-  cudaGraphExec_t& g = bs->graphs[bfs ? 1 : sem][sid][bfs ? 1 : 0][lanes];
+  const int slot = learned ? SPMSPV_NUM_SCHEDULES : sid;
+  cudaGraphExec_t& g = bs->graphs[bfs ? 1 : sem][slot][bfs ? 1 : 0][lanes];
   if (!g) {
-    if ((rc = build_batch_graph(bs, bfs ? kMinSelect2nd : sem, bfs, sc, lanes, &g)) != SPMSPV_OK) return rc;
+    if ((rc = build_batch_graph(bs, bfs ? kMinSelect2nd : sem, bfs, sc, learned ? h->sel_w : nullptr,
+                                lanes, &g)) != SPMSPV_OK)
+      return rc;
   }
   k_batch_start<<<1, 32, 0, s>>>(bs->desc, v);
   cudaError_t e = cudaGetLastError();
@@ -328,7 +374,7 @@ __global__ void k_msbfs_init(int32_t B, int32_t n, const int32_t* __restrict__ s
                              uint32_t* __restrict__ visited, int64_t vwords,
                              int32_t* __restrict__ fronts, int32_t* __restrict__ x_off,
                              int32_t* __restrict__ x_cnt, int32_t* __restrict__ y_off,
-                             int32_t* __restrict__ y_cap) {
+                             int32_t* __restrict__ y_cap, uint32_t* __restrict__ fb) {
   const int64_t total = (int64_t)B * n;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -338,6 +384,10 @@ __global__ void k_msbfs_init(int32_t B, int32_t n, const int32_t* __restrict__ s
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)B * vwords;
        i += (int64_t)gridDim.x * blockDim.x)
     visited[i] = 0u;
+  if (fb)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * (int64_t)B * vwords;
+         i += (int64_t)gridDim.x * blockDim.x)
+      fb[i] = 0u;
 }
 
 __global__ void k_msbfs_seed(int32_t B, int32_t n, const int32_t* __restrict__ sources,
@@ -345,13 +395,15 @@ __global__ void k_msbfs_seed(int32_t B, int32_t n, const int32_t* __restrict__ s
                              uint32_t* __restrict__ visited, int64_t vwords,
                              int32_t* __restrict__ fronts, int32_t* __restrict__ x_off,
                              int32_t* __restrict__ x_cnt, int32_t* __restrict__ y_off,
-                             int32_t* __restrict__ y_cap, int32_t* __restrict__ status) {
+                             int32_t* __restrict__ y_cap, int32_t* __restrict__ status,
+                             uint32_t* __restrict__ fb, int32_t* __restrict__ nvis) {
   for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
     const int32_t s = sources[b];
     x_off[b] = (int32_t)0;
     y_off[b] = 0;
     y_cap[b] = n;
     x_cnt[b] = 0;
+    if (nvis) nvis[b] = 0;
     if (s < 0 || s >= n) {
       atomicOr(status, 1);
       continue;
@@ -361,14 +413,17 @@ __global__ void k_msbfs_seed(int32_t B, int32_t n, const int32_t* __restrict__ s
     visited[(int64_t)b * vwords + (s >> 5)] |= 1u << (s & 31);
     fronts[(int64_t)b * n] = s;
     x_cnt[b] = 1;
+    if (fb) fb[2 * (int64_t)b * vwords + (s >> 5)] = 1u << (s & 31);  // level 0's frontier
+    if (nvis) nvis[b] = 1;
   }
 }
 
 __global__ void k_msbfs_next(int32_t B, const int32_t* __restrict__ nnz, int32_t* __restrict__ x_cnt,
-                             int32_t* __restrict__ total) {
+                             int32_t* __restrict__ total, int32_t* __restrict__ nvis) {
   int32_t t = 0;
   for (int32_t b = threadIdx.x; b < B; b += blockDim.x) {
     x_cnt[b] = nnz[b];
+    if (nvis) nvis[b] += nnz[b];
     t += nnz[b];
   }
   for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
@@ -390,16 +445,22 @@ static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_
   cudaStream_t s = (cudaStream_t)stream;
   const int32_t n = h->A.n;
   const int64_t vwords = ((int64_t)n + 31) / 32;
+  // the learned schedule (push or pull per source and level) needs the
+  // selector's weights and a pattern-symmetric matrix
+  const bool learned = (opts & SPMSPV_SCHED_AUTO) && h->sel_w && h->sel_ready &&
+                       pull_available(h, kMinSelect2nd);
   // per-source frontiers, visited bitmaps and batch arrays (freed on return)
   int32_t *fronts = nullptr, *arr = nullptr;
-  uint32_t* visited = nullptr;
+  uint32_t *visited = nullptr, *fbs = nullptr;
   cudaError_t e = cudaMalloc(&fronts, sizeof(int32_t) * (size_t)B * n);
   if (e == cudaSuccess) e = cudaMalloc(&visited, sizeof(uint32_t) * (size_t)B * vwords);
   if (e == cudaSuccess) e = cudaMalloc(&arr, sizeof(int32_t) * ((size_t)B * 6 + 8));
+  if (e == cudaSuccess && learned) e = cudaMalloc(&fbs, sizeof(uint32_t) * 2 * (size_t)B * vwords);
   if (e != cudaSuccess) {
     cudaFree(fronts);
     cudaFree(visited);
     cudaFree(arr);
+    cudaFree(fbs);
     cudaGetLastError();
     return fail(SPMSPV_ERR_OOM, "multi-source BFS buffers: %s", cudaGetErrorString(e));
   }
@@ -408,14 +469,15 @@ static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_
   int32_t* y_off = arr + 2 * B;
   int32_t* y_cap = arr + 3 * B;
   int32_t* nnz = arr + 4 * B;
+  int32_t* nvis = learned ? arr + 5 * B : nullptr;
   int32_t* misc = arr + 6 * B;  // [0] status, [1] frontier total
   // frontier b lives at fronts + b*n: express the offsets relative to fronts
   cudaMemsetAsync(misc, 0, sizeof(int32_t) * 8, s);
   const int grid = h->sm_count * 4;
   k_msbfs_init<<<grid, 256, 0, s>>>(B, n, sources, level, parent, visited, vwords, fronts, x_off,
-                                    x_cnt, y_off, y_cap);
+                                    x_cnt, y_off, y_cap, fbs);
   k_msbfs_seed<<<(B + 255) / 256, 256, 0, s>>>(B, n, sources, level, parent, visited, vwords, fronts,
-                                               x_off, x_cnt, y_off, y_cap, misc);
+                                               x_off, x_cnt, y_off, y_cap, misc, fbs, nvis);
   // offsets: frontier b starts at b*n
   {
     std::vector<int32_t> off(B);
@@ -439,6 +501,9 @@ static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_
   v.level = level;
   v.parent = parent;
   v.vstride = n;
+  v.fb = fbs;
+  v.fb_stride = 2 * vwords;
+  v.nvis = nvis;
   int32_t L = 0;
   rc = SPMSPV_OK;
   if ((rc = ensure_batch_state(h, lanes)) == SPMSPV_OK) {
@@ -446,7 +511,7 @@ static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_
       if ((rc = batch_set_level(h, L, s)) != SPMSPV_OK) break;
       if ((rc = run_batched(h, kMinSelect2nd, true, B, v, opts, lanes, s)) != SPMSPV_OK) break;
       cudaMemsetAsync(misc + 1, 0, sizeof(int32_t), s);
-      k_msbfs_next<<<1, 1024, 0, s>>>(B, nnz, x_cnt, misc + 1);
+      k_msbfs_next<<<1, 1024, 0, s>>>(B, nnz, x_cnt, misc + 1, nvis);
       int32_t total = 0;
       e = cudaMemcpyAsync(&total, misc + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -466,6 +531,7 @@ static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_
   cudaFree(fronts);
   cudaFree(visited);
   cudaFree(arr);
+  cudaFree(fbs);
   return rc;
 }
 
@@ -687,6 +753,11 @@ extern "C" int spmspv_msbfs(spmspv_handle* h, int32_t B, const int32_t* sources,
   if (lanes != 0) return msbfs_run(h, B, sources, level, parent, nlevels, opts, lanes, stream);
   int rc = check_handle(h);
   if (rc) return rc;
+  if (opts & SPMSPV_SCHED_AUTO)  // the learned schedule: only the lane count is tuned
+    return tune_and_run(h, tune_key(3, kMinSelect2nd, 1, B, 0), (cudaStream_t)stream,
+                        [&](int32_t ln, uint32_t) {
+                          return msbfs_run(h, B, sources, level, parent, nlevels, opts, ln, stream);
+                        }, 1);
   const uint32_t base = opts & ~(uint32_t)(SPMSPV_SCHED_FORCE | SPMSPV_SCHED_AUTO | SPMSPV_SCHED_OPT(0xFFu));
   return tune_and_run(h, tune_key(1, kMinSelect2nd, 1, B, 0), (cudaStream_t)stream,
                       [&](int32_t ln, uint32_t so) {

@@ -75,9 +75,13 @@ void release_tune(spmspv_handle* h);
 uint64_t tune_key(int kind, int sem, int masked, int32_t B, int64_t total_f);
 // Runs `run(lanes, schedule opts)` with the cached choice for `key`, or times
 // every candidate on `s` (each run twice, the second timed) and caches the best.
+// Candidates: lanes 2/4/8/16 x push schedules 0..nsched-1.
 int tune_and_run(spmspv_handle* h, uint64_t key, cudaStream_t s,
-                 const std::function<int(int32_t, uint32_t)>& run);
+                 const std::function<int(int32_t, uint32_t)>& run, int nsched = 6);
 cudaError_t alloc_pull_buffers(spmspv_handle* h);
+int pull_available(const spmspv_handle* h, int sem);
+// BFS pull kernel of a batched lane (the lane's job names the source's arrays)
+cudaError_t launch_pull_rows_lane(const spmspv_handle* sub, int early_exit, cudaStream_t s);
 int ensure_bfs_buffers(spmspv_handle* h);
 // Per-stage event recording (no-ops unless spmspv_profile_begin was called).
 void prof_call_begin(spmspv_handle* h, cudaStream_t s);

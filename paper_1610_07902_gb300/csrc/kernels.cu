@@ -61,6 +61,7 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
 
   DevState* st = ws.st;
   const int tid = threadIdx.x;
+  const int bfs_mode = bfs_level_inc;  // a BFS level (single source or a batched lane's)
   if (ws.job) {  // a batched lane: this frontier's x
     x_idx = ws.job->x_idx;
     x_val = bfs_level_inc ? reinterpret_cast<const uint32_t*>(ws.job->x_idx) : ws.job->x_val;
@@ -76,7 +77,7 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
       ws.bfill[(size_t)b * BFILL_STRIDE] = 0;
       ws.k3_status[b] = 0ull;
     }
-    if (bfs_level_inc && ws.pull_status)
+    if (bfs_mode && ws.pull_status)
       for (int i = tid; i < ws.pull_tiles; i += K1_THREADS) ws.pull_status[i] = 0ull;
     const uint32_t hid = sem == kMinSelect2nd ? 0x7fffffffu : 0u;
     for (int h = tid; h < ws.nhot; h += K1_THREADS) {
@@ -92,12 +93,13 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
         st->lwb = f_lwb;
         st->sched = forced - 1;
       }
+      if (bfs_mode) st->pull_ticket = 0u;  // the level may run the pull kernel
       if (bfs_level_inc) {
         st->level += 1;
-        st->pull_ticket = 0u;  // the level may run the pull kernel
       } else if (!ws.job) {
         st->bfs_level = nullptr;  // not a BFS level
       }
+      if (bfs_mode && ws.job) st->nvisited = ws.job->nvis;  // this source's, for the selector
       if (f == 0) {
         st->fc = 0;
         st->W = 0;
@@ -232,13 +234,13 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
   if (!sel.w) return;
   // the selector runs in the CTA that finishes the last piece of work, once
   // every count is in: with a mask pass every CTA is a piece, otherwise every
-  // tile (CTAs without one add nothing and skip the counter)
-  const uint32_t units = mask ? 1u : my_tiles;
-  const uint32_t total = mask ? gridDim.x : nt1;
-  if (total == 0 ? blockIdx.x != 0 : units == 0) return;
+  // tile plus block 0's state set-up (CTAs without a piece skip the counter)
+  const uint32_t units = mask ? 1u : my_tiles + (blockIdx.x == 0 ? 1u : 0u);
+  const uint32_t total = mask ? gridDim.x : nt1 + 1u;
+  if (units == 0) return;
   if (tid == 0) {
     __threadfence();
-    s_last = total == 0 || atomicAdd(&st->k1_done, units) + units == total;
+    s_last = atomicAdd(&st->k1_done, units) + units == total;
   }
   __syncthreads();
   if (s_last) {
@@ -574,6 +576,7 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
   uint32_t* fbn = nullptr;
   const int64_t fb_words = ((int64_t)m + 31) / 32;
   if (BFS && !ws.job && st->bfs_fb) fbn = st->bfs_fb + ((lvl & 1) ? fb_words : 0);
+  if (BFS && ws.job && ws.job->fb) fbn = ws.job->fb + ((lvl & 1) ? fb_words : 0);
 
   if (blockIdx.x == 0 && tid == 0) {
     // clear K1's per-call state for the next call

@@ -77,16 +77,27 @@ k_pull_rows(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowi
   DevState* st = ws.st;
   if (!active_dir(st, only_pull)) return;
   const int tid = threadIdx.x;
-  const int32_t lvl = BFS ? st->level : 0;
-  int32_t* const level = BFS ? st->bfs_level : nullptr;
-  int32_t* const parent = BFS ? st->bfs_parent : nullptr;
+  const Job* job = ws.job;  // a batched lane's BFS level (only BFS jobs come here)
+  int32_t lvl = BFS ? (job ? job->lvl : st->level) : 0;
+  int32_t* level = BFS ? (job ? job->level : st->bfs_level) : nullptr;
+  int32_t* parent = BFS ? (job ? job->parent : st->bfs_parent) : nullptr;
+  uint32_t* fbase = BFS ? (job ? job->fb : st->bfs_fb) : nullptr;
+  if (BFS && job) {
+    visited = job->visited;
+    mask = job->visited;
+    mask_comp = 1;
+    y_idx = job->y_idx;
+    y_val = nullptr;
+    y_cap = job->y_cap;
+    d_nnz_y = job->d_nnz_y;
+  }
   // BFS: x is the previous level's frontier bitmap, x(j) = j; this level's
   // discoveries go to the other bitmap (every word is written)
   uint32_t* fb_next = nullptr;
-  if (BFS) {
+  if (BFS && fbase) {
     const size_t words = ((size_t)m + 31) / 32;
-    xbits = st->bfs_fb + (((lvl - 1) & 1) ? words : 0);
-    fb_next = st->bfs_fb + ((lvl & 1) ? words : 0);
+    xbits = fbase + (((lvl - 1) & 1) ? words : 0);
+    fb_next = fbase + ((lvl & 1) ? words : 0);
   }
   if (blockIdx.x == 0) {
     // this kernel ends the call: clear the work scan's per-call state
@@ -100,6 +111,7 @@ k_pull_rows(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowi
     const int nt1 = (st->f + K1_TILE - 1) / K1_TILE;
     for (int i = tid; i < nt1; i += PULL_THREADS) ws.k1_status[i] = 0ull;
   }
+  if (BFS && (!fbase || (job && job->b < 0))) return;  // an empty lane job: nothing to find
   const uint32_t ident = SEM == kMinSelect2nd ? 0x7fffffffu : 0u;
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(&st->pull_ticket, 1u);
@@ -249,6 +261,15 @@ cudaError_t launch_pull_rows_bfs(const spmspv_handle* h, int early_exit, int onl
   k_pull_rows<kMinSelect2nd, true><<<grid, PULL_THREADS, 0, s>>>(
       h->A.colptr, h->A.rowidx, h->A.val, h->A.m, nullptr, nullptr, h->bfs_visited, 1, early_exit,
       h->bfs_front, nullptr, h->A.n, &h->ws.st->nnz_y, h->bfs_visited, h->ws, h->pull_tiles, only_pull);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pull_rows_lane(const spmspv_handle* sub, int early_exit, cudaStream_t s) {
+  // the lanes share the GPU: fewer CTAs per lane than a lone call takes
+  const int grid = std::max(1, std::min(sub->pull_tiles, sub->sm_count * 2));
+  k_pull_rows<kMinSelect2nd, true><<<grid, PULL_THREADS, 0, s>>>(
+      sub->A.colptr, sub->A.rowidx, sub->A.val, sub->A.m, nullptr, nullptr, nullptr, 1, early_exit,
+      nullptr, nullptr, 0, nullptr, nullptr, sub->ws, sub->pull_tiles, 1);
   return cudaGetLastError();
 }
 

@@ -110,10 +110,13 @@ struct Job {
   int32_t* level;      // BFS mode: this source's outputs and visited bitmap
   int32_t* parent;
   uint32_t* visited;
+  uint32_t* fb;        // BFS mode with the learned schedule: this source's two frontier
+                       // bitmaps (level L reads bitmap (L-1)&1 and writes bitmap L&1)
   int32_t f;
   int32_t y_cap;
   int32_t b;           // frontier index, -1 when the queue was empty
   int32_t lvl;         // BFS mode: the level being discovered
+  int32_t nvis;        // BFS mode: vertices this source has reached (selector feature)
 };
 
 struct Workspace {

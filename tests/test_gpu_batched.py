@@ -157,3 +157,40 @@ def test_autotuned_msbfs_and_acl_match_fixed(lib):
     assert np.abs(P.sum(1) + R.sum(1) - 1).max() < 1e-5
     assert len(S.spmspv_tune_entries(Ad.handle)) == 2
     Ad.close()
+
+
+@pytest.mark.parametrize("bias", ["trained", "pull", "push"])
+def test_learned_msbfs_matches_fixed(lib, bias):
+    # the learned multi-source BFS picks push or pull per source and level in
+    # the lanes; forcing pull everywhere (or push) through the output biases
+    # of the network exercises both kernels; levels and parents never change
+    torch, S = lib
+    from oracle import mlp
+    from paper_1610_07902_gb300 import selector
+    params, _ = selector.load()
+    params = params.copy()
+    if bias == "pull":
+        params[mlp.O_B3 + 6:mlp.O_B3 + 12] -= 1e4
+    elif bias == "push":
+        params[mlp.O_B3:mlp.O_B3 + 6] -= 1e4
+    A = synth.rmat(12, seed=21, values=False)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
+    S.spmspv_selector_set(Ad.handle, params)
+    srcs = synth.sources(A.colptr, 20, seed=3).astype(np.int32)
+    B = srcs.shape[0]
+    ds = torch.from_numpy(srcs).cuda()
+    out = []
+    for opts, lanes in ((0, 4), (S.SPMSPV_SCHED_AUTO, 4), (S.SPMSPV_SCHED_AUTO, 0)):
+        level = torch.empty(B * A.n, dtype=torch.int32, device="cuda")
+        parent = torch.empty(B * A.n, dtype=torch.int32, device="cuda")
+        S.spmspv_msbfs(Ad.handle, B, ds, level, parent, None, opts, lanes)
+        out.append((level.cpu().numpy(), parent.cpu().numpy()))
+    for lv, pa in out[1:]:
+        np.testing.assert_array_equal(lv, out[0][0])
+        np.testing.assert_array_equal(pa, out[0][1])
+    for b in (0, B - 1):
+        ref_l, ref_p, _, _, _ = oracle.bfs(A.colptr, A.rowidx, int(srcs[b]))
+        np.testing.assert_array_equal(out[1][0][b * A.n:(b + 1) * A.n], ref_l)
+        np.testing.assert_array_equal(out[1][1][b * A.n:(b + 1) * A.n], ref_p)
+    assert S.spmspv_device_status(Ad.handle) == 0
+    Ad.close()
