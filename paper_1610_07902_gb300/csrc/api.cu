@@ -119,7 +119,8 @@ int run_push(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_
   }
   if (e != cudaSuccess) return cuda_fail(e, "work scan launch");
   prof_mark(h, SPMSPV_STAGE_SCAN, s);
-  e = launch_k2(sem, h->A, h->ws, h->lwb_lo, h->nb_fine, mask, mask_comp, h->k2_grid, h->k2_smem, s);
+  e = launch_k2(sem, h->A, h->ws, h->lwb_lo, h->nb_fine, mask, mask_comp, h->k2_grid, h->k2_smem, s, 0,
+                sc.q);
   if (e != cudaSuccess) return cuda_fail(e, "expand/scatter launch");
   prof_mark(h, SPMSPV_STAGE_SCATTER, s);
   const size_t k3_smem = k3_smem_bytes(sc.lwb);

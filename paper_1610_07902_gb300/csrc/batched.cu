@@ -155,7 +155,7 @@ static int lane_launches(spmspv_handle* sub, BatchState* bs, int lane, int sem, 
                   nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "batch work scan");
   e = launch_k2(bfs ? kMinSelect2nd : sem, sub->A, sub->ws, sub->lwb_lo, sub->nb_fine, nullptr,
-                1, sub->k2_grid, sub->k2_smem, s, 0);
+                1, sub->k2_grid, sub->k2_smem, s, 0, sc.q);
   if (e != cudaSuccess) return cuda_fail(e, "batch expand/scatter");
   const size_t k3_smem = k3_smem_bytes(sc.lwb);
   const int nb = (int)(((int64_t)sub->A.m + (1 << sc.lwb) - 1) >> sc.lwb);

@@ -67,9 +67,8 @@ static int bfs_push_launches(spmspv_handle* h, const Sched& sc, int lwb, cudaStr
   const size_t k3_smem = k3_smem_bytes(lwb);
   const int nb_max = (int)(((int64_t)h->A.m + (1 << h->lwb_lo) - 1) >> h->lwb_lo);
   const int k3_grid = std::max(1, std::min(nb_max, h->sm_count * h->k3_bps[lwb - h->lwb_lo]));
-  (void)sc;
   cudaError_t e = launch_k2(kMinSelect2nd, h->A, h->ws, h->lwb_lo, h->nb_fine, h->bfs_visited, 1,
-                            h->k2_grid, h->k2_smem, s, only_push);
+                            h->k2_grid, h->k2_smem, s, only_push, only_push ? 0 : sc.q);
   if (e != cudaSuccess) return cuda_fail(e, "bfs expand/scatter");
   e = launch_k3(kMinSelect2nd, true, h->A, h->ws, h->lwb_lo, h->nb_fine, h->bfs_front, nullptr,
                 h->A.n, nullptr, h->bfs_visited, k3_grid, k3_smem, s, only_push);

@@ -292,7 +292,9 @@ __device__ __forceinline__ void spa_apply(uint32_t* spa, uint32_t r, uint32_t v)
 // gets one run reserved with a global atomic, the products are staged in
 // shared memory grouped by bucket and written out in runs.  Hub rows (row ids >= m in the relabelled
 // row-id array) are summed per tile in shared memory instead.
-template <int SEM>
+// IT: products per thread when the host knows the work quantum (4 or 8),
+// 0 when the device decides it; MASKED: a mask may be given.
+template <int SEM, int IT, bool MASKED>
 __global__ void __launch_bounds__(K2_THREADS, 2)
 k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ val, Workspace ws,
                   int lwb_lo, int nb_fine, int32_t m, int64_t nnz, const uint32_t* mask,
@@ -319,7 +321,7 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
   const int sh = lwb - lwb_lo;
   const int nb = (int)(((int64_t)m + (1 << lwb) - 1) >> lwb);
   const uint32_t wmask = (1u << lwb) - 1u;
-  const int items = q / K2_THREADS;
+  const int items = IT ? IT : q / K2_THREADS;
   const int ntiles = (int)(((int64_t)W + q - 1) / q);
   const uint32_t ident = sr_identity<SEM>();
   const int nhot = ws.nhot;
@@ -397,7 +399,7 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
         if (row == 0xffffffffu) continue;
         if ((int32_t)row < m) {
           bool keep = true;
-          if (mask) {
+          if (MASKED && mask) {
             const uint32_t bit = (__ldg(mask + (row >> 5)) >> (row & 31)) & 1u;
             keep = mask_comp ? (bit == 0u) : (bit != 0u);
           }
@@ -407,7 +409,7 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
           const int hs = (int)row - m;
           const int32_t orow = hrow[hs];
           bool keep = true;
-          if (mask) {
+          if (MASKED && mask) {
             const uint32_t bit = (__ldg(mask + (orow >> 5)) >> (orow & 31)) & 1u;
             keep = mask_comp ? (bit == 0u) : (bit != 0u);
           }
@@ -514,22 +516,40 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
   }
 }
 
+template <int SEM>
+static void k2_variant(int it, bool masked, int grid, size_t smem, cudaStream_t s, const int32_t* rows,
+                       const float* val, const Workspace& ws, int lwb_lo, int nb_fine, const Matrix& A,
+                       const uint32_t* mask, int mask_comp, int only_push) {
+#define K2_GO(I, M)                                                                              \
+  k2_expand_scatter<SEM, I, M><<<grid, K2_THREADS, smem, s>>>(rows, val, ws, lwb_lo, nb_fine, A.m, \
+                                                              A.nnz, mask, mask_comp, only_push)
+  if (masked) {
+    if (it == 8) K2_GO(8, true); else if (it == 4) K2_GO(4, true); else K2_GO(0, true);
+  } else {
+    if (it == 8) K2_GO(8, false); else if (it == 4) K2_GO(4, false); else K2_GO(0, false);
+  }
+#undef K2_GO
+}
+
 cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo, int nb_fine,
                       const uint32_t* mask, int mask_comp, int grid, size_t smem, cudaStream_t s,
-                      int only_push) {
+                      int only_push, int q_hint) {
   const int32_t* rows = ws.nhot > 0 ? ws.rowidx_k2 : A.rowidx;
+  // the batched lanes take their masks from the job: compile the mask path in
+  const bool masked = mask != nullptr || ws.job != nullptr;
+  const int it = q_hint == K2_IMAX * K2_THREADS ? K2_IMAX : q_hint == (K2_IMAX / 2) * K2_THREADS ? K2_IMAX / 2 : 0;
   switch (sem) {
     case kPlusTimes:
-      k2_expand_scatter<kPlusTimes><<<grid, K2_THREADS, smem, s>>>(
-          rows, A.val, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp, only_push);
+      k2_variant<kPlusTimes>(it, masked, grid, smem, s, rows, A.val, ws, lwb_lo, nb_fine, A, mask,
+                             mask_comp, only_push);
       break;
     case kMinSelect2nd:
-      k2_expand_scatter<kMinSelect2nd><<<grid, K2_THREADS, smem, s>>>(
-          rows, nullptr, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp, only_push);
+      k2_variant<kMinSelect2nd>(it, masked, grid, smem, s, rows, nullptr, ws, lwb_lo, nb_fine, A, mask,
+                                mask_comp, only_push);
       break;
     default:
-      k2_expand_scatter<kOrAnd><<<grid, K2_THREADS, smem, s>>>(
-          rows, nullptr, ws, lwb_lo, nb_fine, A.m, A.nnz, mask, mask_comp, only_push);
+      k2_variant<kOrAnd>(it, masked, grid, smem, s, rows, nullptr, ws, lwb_lo, nb_fine, A, mask,
+                         mask_comp, only_push);
   }
   return cudaGetLastError();
 }
@@ -866,9 +886,17 @@ cudaError_t set_kernel_attributes(size_t k2_smem, size_t k3_smem_max) {
 #define SET(fn, bytes)                                                                      \
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes)); \
   if (e != cudaSuccess) return e;
-  SET(k2_expand_scatter<kPlusTimes>, k2_smem);
-  SET(k2_expand_scatter<kMinSelect2nd>, k2_smem);
-  SET(k2_expand_scatter<kOrAnd>, k2_smem);
+#define SET_K2(S)                                  \
+  SET((k2_expand_scatter<S, 0, false>), k2_smem);  \
+  SET((k2_expand_scatter<S, 4, false>), k2_smem);  \
+  SET((k2_expand_scatter<S, 8, false>), k2_smem);  \
+  SET((k2_expand_scatter<S, 0, true>), k2_smem);   \
+  SET((k2_expand_scatter<S, 4, true>), k2_smem);   \
+  SET((k2_expand_scatter<S, 8, true>), k2_smem);
+  SET_K2(kPlusTimes)
+  SET_K2(kMinSelect2nd)
+  SET_K2(kOrAnd)
+#undef SET_K2
   SET((k3_bucket_merge<kPlusTimes, false>), k3_smem_max);
   SET((k3_bucket_merge<kMinSelect2nd, false>), k3_smem_max);
   SET((k3_bucket_merge<kOrAnd, false>), k3_smem_max);
@@ -891,11 +919,11 @@ int k3_blocks_per_sm(int sem, size_t smem) {
 int k2_blocks_per_sm(int sem, size_t smem) {
   int nb = 0;
   if (sem == kPlusTimes)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k2_expand_scatter<kPlusTimes>, K2_THREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k2_expand_scatter<kPlusTimes, 0, true>, K2_THREADS, smem);
   else if (sem == kMinSelect2nd)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k2_expand_scatter<kMinSelect2nd>, K2_THREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k2_expand_scatter<kMinSelect2nd, 0, true>, K2_THREADS, smem);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k2_expand_scatter<kOrAnd>, K2_THREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k2_expand_scatter<kOrAnd, 0, true>, K2_THREADS, smem);
   return nb > 0 ? nb : 1;
 }
 

@@ -214,7 +214,7 @@ extern "C" int spmspv_run_noalloc(int32_t m, int32_t n, int64_t nnz, const int32
                 &sc, s);
   if (e != cudaSuccess) return cuda_fail(e, "work scan launch");
   e = launch_k2(semiring, A, ws, lwb_lo, nb_fine, mask, (opts & SPMSPV_MASK_COMPLEMENT) ? 1 : 0,
-                d->k2_grid, k2_smem_bytes(nb_fine, false), s);
+                d->k2_grid, k2_smem_bytes(nb_fine, false), s, 0, sc.q);
   if (e != cudaSuccess) return cuda_fail(e, "expand/scatter launch");
   const int nb = (int)(((int64_t)m + (1 << sc.lwb) - 1) >> sc.lwb);
   const size_t k3_smem = k3_smem_bytes(sc.lwb);

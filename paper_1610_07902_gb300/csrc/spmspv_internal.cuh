@@ -174,9 +174,11 @@ cudaError_t launch_row_degrees(const Matrix& A, int32_t* deg, int32_t* maxdeg, c
 cudaError_t launch_rows_unsorted(const Matrix& A, int32_t* unsorted, cudaStream_t s);
 cudaError_t launch_relabel_hubs(const Matrix& A, const int32_t* hub_of_row, int32_t* out,
                                 cudaStream_t s);
+// q_hint: the work quantum when the host knows it (selects a kernel compiled
+// for it), 0 when the device picks it
 cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo, int nb_fine,
                       const uint32_t* mask, int mask_comp, int grid, size_t smem, cudaStream_t s,
-                      int only_push = 0);
+                      int only_push = 0, int q_hint = 0);
 cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, int lwb_lo,
                       int nb_fine, int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y,
                       uint32_t* mask_update, int grid, size_t smem, cudaStream_t s,
