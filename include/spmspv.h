@@ -306,7 +306,8 @@ int spmspv_selector_grad(spmspv_handle* h, const float* feats, const float* targ
                          const uint8_t* valid, int32_t n, float* grad, float* loss);
 
 /* Device status word of the handle: synchronises the handle's last stream,
- * returns the SPMSPV_DEV_* bits in *flags (host out) and clears them. */
+ * returns the SPMSPV_DEV_* bits in *flags (host out) and clears them.  The
+ * bits of the batched form's lanes (their own workspaces) are included. */
 int spmspv_device_status(spmspv_handle* h, uint32_t* flags);
 
 /* Multiply count of the last run (host out, synchronises): the sum of the

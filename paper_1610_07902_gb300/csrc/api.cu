@@ -525,6 +525,8 @@ int spmspv_device_status(spmspv_handle* h, uint32_t* flags) {
   uint32_t z = 0;
   e = cudaMemcpy(&h->ws.st->status, &z, sizeof(z), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "status clear");
+  v |= batch_collect_status(h, &e);  // the batched lanes' own workspaces
+  if (e != cudaSuccess) return cuda_fail(e, "lane status");
   *flags = v & (SPMSPV_DEV_CAPACITY | SPMSPV_DEV_TIMEOUT | ST_INDEX);
   return SPMSPV_OK;
 }

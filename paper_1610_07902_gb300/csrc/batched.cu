@@ -300,6 +300,21 @@ int run_batched(spmspv_handle* h, int sem, bool bfs, int32_t B, const BatchDesc&
   return SPMSPV_OK;
 }
 
+uint32_t batch_collect_status(spmspv_handle* h, cudaError_t* e) {
+  *e = cudaSuccess;
+  BatchState* bs = (BatchState*)h->batch;
+  if (!bs) return 0u;
+  uint32_t all = 0u;
+  for (int l = 0; l < bs->lanes; ++l) {
+    uint32_t v = 0u, z = 0u;
+    if ((*e = cudaMemcpy(&v, &bs->sub[l]->ws.st->status, sizeof(v), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (*e = cudaMemcpy(&bs->sub[l]->ws.st->status, &z, sizeof(z), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return all;
+    all |= v;
+  }
+  return all;
+}
+
 int batch_set_level(spmspv_handle* h, int32_t lvl, cudaStream_t s) {
   BatchState* bs = (BatchState*)h->batch;
   k_batch_set_level<<<1, 32, 0, s>>>(bs->desc, lvl);

@@ -70,6 +70,9 @@ int run_pull_if_available(spmspv_handle* h, int sem, const int32_t* x_idx, const
 void release_extras(spmspv_handle* h);
 void release_bfs_graphs(spmspv_handle* h);
 void release_batch(spmspv_handle* h);
+// Reads and clears the status words of the batched lanes' workspaces (after
+// the caller has synchronised the stream); CUDA errors are returned in *e.
+uint32_t batch_collect_status(spmspv_handle* h, cudaError_t* e);
 void release_tune(spmspv_handle* h);
 // Autotuner (autotune.cu).  kind: 0 batched SpMSpV, 1 multi-source BFS, 2 ACL.
 uint64_t tune_key(int kind, int sem, int masked, int32_t B, int64_t total_f);

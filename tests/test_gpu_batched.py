@@ -194,3 +194,52 @@ def test_learned_msbfs_matches_fixed(lib, bias):
         np.testing.assert_array_equal(out[1][1][b * A.n:(b + 1) * A.n], ref_p)
     assert S.spmspv_device_status(Ad.handle) == 0
     Ad.close()
+
+
+def test_batched_edge_cases(lib):
+    # empty frontiers among full ones, a single-frontier batch, and a frontier
+    # whose y does not fit: it reports the size it needs, the others are exact
+    torch, S = lib
+    A = synth.rmat(11, seed=17)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    fronts = [synth.frontier(A.n, k, seed=40 + i) if k else (np.zeros(0, np.int32), np.zeros(0, np.float32))
+              for i, k in enumerate([0, 50, 0, 300, 1, 0])]
+    B = len(fronts)
+    x_cnt = np.array([f[0].shape[0] for f in fronts], np.int32)
+    x_off = np.concatenate([[0], np.cumsum(x_cnt)[:-1]]).astype(np.int32)
+    x_idx = np.concatenate([f[0] for f in fronts] + [np.zeros(1, np.int32)]).astype(np.int32)
+    x_val = np.concatenate([f[1] for f in fronts] + [np.zeros(1, np.float32)]).astype(np.float32)
+    refs = [oracle.spmspv(A.m, A.colptr, A.rowidx, A.val, SEMIRING_TO_ORACLE[0], f[0], f[1], None, True)
+            for f in fronts]
+    small = 3  # frontier 3's y needs far more
+    assert refs[small].idx.shape[0] > 10
+    y_cap = np.full(B, A.m, np.int32)
+    y_cap[small] = 10
+    y_off = (np.arange(B) * A.m).astype(np.int32)
+    for lanes in (1, 4):
+        yi = torch.full((B * A.m,), -7, dtype=torch.int32, device="cuda")
+        yv = torch.zeros(B * A.m, dtype=torch.float32, device="cuda")
+        nz = torch.full((B,), -1, dtype=torch.int32, device="cuda")
+        S.spmspv_run_batched(Ad.handle, 0, B, dev(x_off), dev(x_cnt), dev(x_idx), dev(x_val), None, 0, 0,
+                             dev(y_off), dev(y_cap), yi, yv, nz, lanes)
+        nz_h, yi_h, yv_h = nz.cpu().numpy(), yi.cpu().numpy(), yv.cpu().numpy()
+        for b in range(B):
+            assert nz_h[b] == refs[b].idx.shape[0], (lanes, b)
+            o = y_off[b]
+            if b == small:
+                np.testing.assert_array_equal(yi_h[o:o + 10], refs[b].idx[:10])
+                assert (yi_h[o + 10:o + 20] == -7).all()  # nothing past the capacity
+            else:
+                compare(0, refs[b], yi_h[o:o + nz_h[b]], yv_h[o:o + nz_h[b]])
+        assert S.spmspv_device_status(Ad.handle) & S.SPMSPV_DEV_CAPACITY
+    # one frontier
+    yi = torch.empty(A.m, dtype=torch.int32, device="cuda")
+    yv = torch.empty(A.m, dtype=torch.float32, device="cuda")
+    nz = torch.zeros(1, dtype=torch.int32, device="cuda")
+    S.spmspv_run_batched(Ad.handle, 0, 1, dev(np.zeros(1, np.int32)), dev(x_cnt[3:4]), dev(fronts[3][0]),
+                         dev(fronts[3][1]), None, 0, 0, dev(np.zeros(1, np.int32)),
+                         dev(np.array([A.m], np.int32)), yi, yv, nz, 2)
+    k = int(nz.item())
+    compare(0, refs[3], yi.cpu().numpy()[:k], yv.cpu().numpy()[:k])
+    Ad.close()
