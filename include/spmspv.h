@@ -305,6 +305,14 @@ int spmspv_selector_train(spmspv_handle* h, const float* feats, const float* tar
 int spmspv_selector_grad(spmspv_handle* h, const float* feats, const float* target,
                          const uint8_t* valid, int32_t n, float* grad, float* loss);
 
+/* Failure-detection self-test (no counterpart in the paper): runs one warp
+ * of the scan's decoupled look-back against a predecessor that never
+ * publishes, with its wait bounded by `spins` iterations (1 .. 2^22), so that
+ * the wait gives up; synchronous on `stream`.  Afterwards
+ * spmspv_device_status() reports SPMSPV_DEV_TIMEOUT and the handle keeps
+ * working: no fault, no trap, no hang. */
+int spmspv_selftest_wait_timeout(spmspv_handle* h, uint32_t spins, spmspv_stream_t stream);
+
 /* Device status word of the handle: synchronises the handle's last stream,
  * returns the SPMSPV_DEV_* bits in *flags (host out) and clears them.  The
  * bits of the batched form's lanes (their own workspaces) are included. */

@@ -34,7 +34,8 @@ __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
 constexpr int LB_WIN = 4;
 
 __device__ __forceinline__ unsigned long long warp_lookback(unsigned long long* status, uint32_t tile,
-                                            unsigned long long agg, DevState* st) {
+                                            unsigned long long agg, DevState* st,
+                                            uint32_t spin_limit = SPIN_LIMIT) {
   const int lane = threadIdx.x & 31;
   if (tile == 0) {
     if (lane == 0) lb_store(status, LB_FLAG_INC | agg);
@@ -72,7 +73,7 @@ __device__ __forceinline__ unsigned long long warp_lookback(unsigned long long* 
         }
       }
       if (all_ready) break;
-      if (++spins > SPIN_LIMIT) {
+      if (++spins > spin_limit) {
         if (lane == 0) atomicOr(&st->status, ST_TIMEOUT);
 #pragma unroll
         for (int k = 0; k < LB_WIN; ++k)

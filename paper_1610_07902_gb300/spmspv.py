@@ -122,6 +122,7 @@ def load(build_if_missing: bool = True):
                                             ctypes.POINTER(ctypes.c_int32)]
         lib.spmspv_tune_set.argtypes = [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32]
         lib.spmspv_tune_clear.argtypes = [_P]
+        lib.spmspv_selftest_wait_timeout.argtypes = [_P, ctypes.c_uint32, _P]
         lib.spmspv_profile_begin.argtypes = [_P]
         lib.spmspv_profile_end.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_int32)]
@@ -297,6 +298,11 @@ def spmspv_acl(h, B, seeds, alpha, eps, max_steps, p_out, r_out, steps_out, lane
     _check(load().spmspv_acl(h, int(B), _ptr(seeds), float(alpha), float(eps), int(max_steps),
                              _ptr(p_out), _ptr(r_out), _ptr(steps_out), int(lanes), _stream(stream)),
            "spmspv_acl")
+
+
+def spmspv_selftest_wait_timeout(h, spins=1000, stream=None):
+    _check(load().spmspv_selftest_wait_timeout(h, int(spins), _stream(stream)),
+           "spmspv_selftest_wait_timeout")
 
 
 def spmspv_device_status(h) -> int:

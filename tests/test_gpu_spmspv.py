@@ -333,3 +333,55 @@ def test_hub_rows_combined_per_tile(lib):
             _check(lib, A, Ad, semiring, x_idx, xf, mask, True)
             _check(lib, A, Ad, semiring, x_idx, xf, mask, False)
     Ad.close()
+
+
+def test_unsorted_output_mode(lib):
+    # the ER configuration in unsorted-output mode (no SPMSPV_SORTED_OUT): the
+    # comparison sorts both sides (the library emits ascending rows anyway)
+    torch, S = lib
+    A = synth.erdos_renyi(65536, d=16, seed=1)
+    Ad = _dev_matrix(lib, A)
+    x_idx, xf = synth.frontier(A.n, 655, seed=1, stream=2)
+    xi = torch.from_numpy(x_idx).cuda()
+    yi, yv, k = Ad.multiply(0, xi, torch.from_numpy(xf).cuda(), None, 0)
+    ref = oracle.spmspv(A.m, A.colptr, A.rowidx, A.val, SEMIRING_TO_ORACLE[0], x_idx, xf, None, True)
+    yi_h, yv_h = yi.cpu().numpy()[:k], yv.cpu().numpy()[:k]
+    order = np.argsort(yi_h, kind="stable")
+    compare(0, ref, yi_h[order], yv_h[order])
+    Ad.close()
+
+
+def test_single_dense_column(lib):
+    # one column holds every row (a product run far longer than a K2 tile)
+    rng = np.random.default_rng(8)
+    m, n = 20000, 12
+    cols = [np.sort(rng.choice(m, size=rng.integers(0, 40), replace=False)) for _ in range(n)]
+    cols[5] = np.arange(m)
+    colptr = np.concatenate([[0], np.cumsum([c.shape[0] for c in cols])]).astype(np.int32)
+    rowidx = np.concatenate(cols).astype(np.int32)
+    val = rng.random(rowidx.shape[0]).astype(np.float32)
+    from types import SimpleNamespace
+    A = SimpleNamespace(m=m, n=n, colptr=colptr, rowidx=rowidx, val=val, nnz=rowidx.shape[0])
+    Ad = _dev_matrix(lib, A)
+    for x_idx in (np.array([5], np.int32), np.arange(n, dtype=np.int32), np.array([11, 5, 0], np.int32)):
+        xf = rng.random(x_idx.shape[0]).astype(np.float32)
+        for semiring in (0, 1, 2):
+            _check(lib, A, Ad, semiring, x_idx, xf)
+    Ad.close()
+
+
+def test_bounded_wait_gives_up_and_reports(lib):
+    # a look-back wait on a word nothing publishes runs out, records
+    # SPMSPV_DEV_TIMEOUT and returns; the handle keeps giving exact results
+    torch, S = lib
+    A = synth.rmat(10, seed=2)
+    Ad = _dev_matrix(lib, A)
+    assert S.spmspv_device_status(Ad.handle) == 0
+    S.spmspv_selftest_wait_timeout(Ad.handle, 2000)
+    assert S.spmspv_device_status(Ad.handle) & S.SPMSPV_DEV_TIMEOUT
+    assert S.spmspv_device_status(Ad.handle) == 0  # read and cleared
+    x_idx, xf = synth.frontier(A.n, 200, seed=3)
+    _check(lib, A, Ad, 0, x_idx, xf)
+    with pytest.raises(S.SpmspvError):
+        S.spmspv_selftest_wait_timeout(Ad.handle, 0)
+    Ad.close()
