@@ -133,6 +133,20 @@ def time_oracle(A, x_idx, x_val, budget_s=10.0):
     return W_total / t_total / 1e9, calls, t_total
 
 
+def replica_summary(t_ms, products_per_step, steps, world, device):
+    """Replicas only: every rank runs the whole workload on its own GPU.  The
+    job time is the slowest rank's (barrier, then the maximum over ranks) and
+    the value is the products of all ranks over that time, in GTEPS."""
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        tt = torch.tensor([t_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    return t_ms, products_per_step * steps * world / (t_ms * 1e-3) / 1e9
+
+
 def _events_ms(fn, stream, reps=1):
     import torch
     best = float("inf")
@@ -486,13 +500,8 @@ def main():
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        dist.barrier()
-        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms, gteps = replica_summary(t_ms, W, args.steps, world, dev)
     ms_per_step = t_ms / args.steps
-    gteps = W * args.steps * world / (t_ms * 1e-3) / 1e9
     if args.kernels_only:
         sampler.stop()
         if rank == 0:
