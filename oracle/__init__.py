@@ -48,6 +48,8 @@ def _bind(lib):
     lib.oracle_bfs.argtypes = [ctypes.c_int32, p, p, ctypes.c_int32, p, p, p, p]
     lib.oracle_bfs_pull.restype = ctypes.c_int32
     lib.oracle_bfs_pull.argtypes = [ctypes.c_int32, p, p, ctypes.c_int32, p, p]
+    lib.oracle_cc.restype = ctypes.c_int32
+    lib.oracle_cc.argtypes = [ctypes.c_int32, p, p, p]
     return lib
 
 
@@ -146,6 +148,20 @@ def bfs(colptr, rowidx, src, lib=None):
     if nl < 0:
         raise ValueError("oracle_bfs failed with code %d" % nl)
     return level, parent, int(nl), int(tm.value), sizes[:nl].copy()
+
+
+def cc(colptr, rowidx, lib=None):
+    """Connected components: (label int32[n], number of components), label[v]
+    the smallest vertex id of v's component (pattern-symmetric A)."""
+    lib = lib or _load()
+    colptr = np.ascontiguousarray(colptr, dtype=np.int32)
+    rowidx = np.ascontiguousarray(rowidx, dtype=np.int32)
+    n = colptr.shape[0] - 1
+    label = np.empty(n, dtype=np.int32)
+    k = lib.oracle_cc(n, _ptr(colptr), _ptr(rowidx), _ptr(label))
+    if k < 0:
+        raise ValueError("oracle_cc failed with code %d" % k)
+    return label, int(k)
 
 
 def bfs_pull(colptr, rowidx, src, lib=None):

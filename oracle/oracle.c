@@ -321,3 +321,53 @@ int32_t oracle_bfs_pull(int32_t n, const int32_t* colptr, const int32_t* rowidx,
   free(next);
   return L + 1;
 }
+
+/*
+ * Connected components of an undirected graph given as a pattern-symmetric
+ * CSC matrix (Sec. I names connected components among the SpMSpV-built graph
+ * algorithms).  The result has a plain definition: label[v] is the smallest
+ * vertex id in the component of v.  Written as that definition: union-find
+ * over every stored edge (i, j), then each vertex takes the smallest id found
+ * in its set.  Returns the number of components, or -1 on a bad row id.
+ */
+static int32_t uf_find(int32_t* up, int32_t v) {
+  while (up[v] != v) {
+    up[v] = up[up[v]];  /* path halving */
+    v = up[v];
+  }
+  return v;
+}
+
+int32_t oracle_cc(int32_t n, const int32_t* colptr, const int32_t* rowidx, int32_t* label) {
+  int32_t* up = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int32_t* low = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  if (!up || !low) {
+    free(up);
+    free(low);
+    return -2;
+  }
+  for (int32_t v = 0; v < n; ++v) up[v] = v;
+  for (int32_t j = 0; j < n; ++j) {
+    for (int32_t p = colptr[j]; p < colptr[j + 1]; ++p) {
+      const int32_t i = rowidx[p];
+      if (i < 0 || i >= n) {
+        free(up);
+        free(low);
+        return -1;
+      }
+      const int32_t a = uf_find(up, i), b = uf_find(up, j);
+      if (a != b) up[a] = b;
+    }
+  }
+  for (int32_t v = 0; v < n; ++v) low[v] = n;
+  int32_t comps = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    const int32_t r = uf_find(up, v);
+    if (low[r] == n) ++comps;
+    if (v < low[r]) low[r] = v;
+  }
+  for (int32_t v = 0; v < n; ++v) label[v] = low[uf_find(up, v)];
+  free(up);
+  free(low);
+  return comps;
+}

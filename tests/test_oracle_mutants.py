@@ -14,6 +14,7 @@ import pytest
 import oracle
 import synth
 import test_oracle_pins as pins
+import test_oracle_cc
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
 
@@ -29,6 +30,10 @@ MUTANTS = {
     "bfs_level_off_by_one": ("      level[i] = L;\n      parent[i] = yv[q];",
                              "      level[i] = L + 1;\n      parent[i] = yv[q];"),
     "bfs_parent_self": ("      parent[i] = yv[q];", "      parent[i] = i;"),
+    "cc_root_not_min": ("  for (int32_t v = 0; v < n; ++v) label[v] = low[uf_find(up, v)];",
+                        "  for (int32_t v = 0; v < n; ++v) label[v] = uf_find(up, v);"),
+    "cc_drops_last_edge": ("    for (int32_t p = colptr[j]; p < colptr[j + 1]; ++p) {\n      const int32_t i = rowidx[p];",
+                           "    for (int32_t p = colptr[j]; p + 1 < colptr[j + 1]; ++p) {\n      const int32_t i = rowidx[p];"),
     "mult_count_after_mask": ("      ++nmult; /* every selected column entry is one multiplication */\n      if (mask) {\n        int in_mask = mask[i] != 0;\n        if (complement ? in_mask : !in_mask) continue;\n      }",
                               "      if (mask) {\n        int in_mask = mask[i] != 0;\n        if (complement ? in_mask : !in_mask) continue;\n      }\n      ++nmult;"),
 }
@@ -57,6 +62,8 @@ def run_pins():
         ("mult_count", pins.test_multiply_count_invariant),
         ("bfs", lambda: pins.test_bfs_against_queue_bfs_and_scipy(*pins.GRAPHS[0])),
         ("grid", pins.test_intact_grid_levels_are_manhattan_distance),
+        ("cc_hand", test_oracle_cc.test_hand_graph),
+        ("cc_scipy", lambda: test_oracle_cc.test_against_scipy_and_invariants(2000, 3000, 5, 2)),
     ]
     for name, fn in checks:
         try:
