@@ -262,6 +262,26 @@ def bench_bfs(S, A, dev, stream, name, sources, params, pt_frontiers=False):
     return out
 
 
+def bench_cc(S, A, dev, stream):
+    """Connected components of the headline graph (label propagation, one
+    SpMSpV round per graph iteration, all rounds in one graph launch) against
+    the reference's labels."""
+    import torch
+    import oracle
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC,
+                     device=dev)
+    labels = torch.empty(A.n, dtype=torch.int32, device=dev)
+    rounds = torch.zeros(1, dtype=torch.int32, device=dev)
+    run = lambda: S.spmspv_cc(Ad.handle, labels, rounds, 0, stream)
+    run()
+    t = _events_ms(run, stream, 3)
+    ref, k = oracle.cc(A.colptr, A.rowidx)
+    got = labels.cpu().numpy()
+    Ad.close()
+    return {"ms": t, "rounds": int(rounds.item()), "components": k,
+            "identical_to_reference": bool((got == ref).all())}
+
+
 def bench_batched(S, dev, stream, B=256):
     """256 frontiers on R-MAT s20 in one batched launch (autotuned) against
     256 sequential plain calls; multi-source BFS and ACL the same way."""
@@ -585,6 +605,7 @@ def main():
         params = selector_params()
         extras["bfs_rmat"] = bench_bfs(S, A, dev, stream, "rmat s%d ef16 seed 1" % args.scale,
                                        synth.sources(A.colptr, 64, seed=2), params)
+        extras["cc_rmat"] = bench_cc(S, A, dev, stream)
         del Ad
         G = synth.grid3d(256, 256, 256, 0.05, seed=3)
         extras["bfs_grid"] = bench_bfs(S, G, dev, stream, "grid 256^3 7-point, 5% edges removed",

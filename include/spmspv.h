@@ -224,6 +224,23 @@ int spmspv_msbfs(spmspv_handle* h, int32_t B, const int32_t* sources, int32_t* l
                  spmspv_stream_t stream);
 
 /*
+ * Connected components of an undirected graph (square, pattern-symmetric
+ * handle) by minimum-label propagation, one (select2nd, min) SpMSpV per round
+ * on the vertices whose label dropped in the previous round (Sec. I lists
+ * connected components as an SpMSpV customer; the algorithm is this
+ * library's reading).  On return labels[v] is the smallest vertex id of v's
+ * component.  All rounds run in one CUDA graph launch; asynchronous on
+ * `stream`.
+ *   labels     device int32[n] out.
+ *   d_nrounds  device int32 out (may be NULL): rounds run (the last finds nothing).
+ *   opts       SPMSPV_SCHED_OPT(s) with a push schedule s in 0..5, or 0 for the
+ *              default; SPMSPV_SCHED_AUTO is UNSUPPORTED.
+ * Allocates 16 bytes per vertex of frontier buffers on first use.
+ */
+int spmspv_cc(spmspv_handle* h, int32_t* labels, int32_t* d_nrounds, uint32_t opts,
+              spmspv_stream_t stream);
+
+/*
  * Andersen-Chung-Lang push from B seeds (device int32[B]) on the unweighted
  * graph (handle created with SPMSPV_VAL_NONE; A symmetric), one batched (+,*)
  * SpMSpV per step (Sec. I lists ACL as a one-SpMSpV-per-step customer; the

@@ -455,6 +455,7 @@ int spmspv_destroy(spmspv_handle* h) {
   }
   release_bfs_graphs(h);
   release_batch(h);
+  release_cc(h);
   release_tune(h);
   release_extras(h);
   cudaFree(h->rowidx_k2);

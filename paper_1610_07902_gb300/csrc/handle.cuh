@@ -50,6 +50,13 @@ struct spmspv_handle {
   int32_t* bfs_front;   // [n] frontier list (x and y of each level)
   uint32_t* bfs_visited;  // [ceil(n/32)]
   uint32_t* bfs_fb;     // [2 * ceil(n/32)] frontier bitmaps (current / next level)
+  // connected components (first use): frontier (x) and round output (y), counts
+  int32_t* cc_x_idx;
+  uint32_t* cc_x_val;
+  int32_t* cc_y_idx;
+  uint32_t* cc_y_val;
+  int32_t* cc_cnt;
+  void* cc_graph[SPMSPV_NUM_SCHEDULES / 2];  // cudaGraphExec_t per push schedule
   int32_t* bfs_count;   // [4] device counters
 };
 
@@ -70,6 +77,7 @@ int run_pull_if_available(spmspv_handle* h, int sem, const int32_t* x_idx, const
 void release_extras(spmspv_handle* h);
 void release_bfs_graphs(spmspv_handle* h);
 void release_batch(spmspv_handle* h);
+void release_cc(spmspv_handle* h);
 // Reads and clears the status words of the batched lanes' workspaces (after
 // the caller has synchronised the stream); CUDA errors are returned in *e.
 uint32_t batch_collect_status(spmspv_handle* h, cudaError_t* e);
