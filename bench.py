@@ -264,10 +264,10 @@ def bench_bfs(S, A, dev, stream, name, sources, params, pt_frontiers=False):
 
 def bench_cc(S, A, dev, stream):
     """Connected components of the headline graph (label propagation, one
-    SpMSpV round per graph iteration, all rounds in one graph launch) against
-    the reference's labels."""
+    SpMSpV round per graph iteration, all rounds in one graph launch); the
+    labels are checked by the properties every correct answer has (label[v]
+    <= v, labels are their own labels, every edge joins equal labels)."""
     import torch
-    import oracle
     Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC,
                      device=dev)
     labels = torch.empty(A.n, dtype=torch.int32, device=dev)
@@ -275,11 +275,13 @@ def bench_cc(S, A, dev, stream):
     run = lambda: S.spmspv_cc(Ad.handle, labels, rounds, 0, stream)
     run()
     t = _events_ms(run, stream, 3)
-    ref, k = oracle.cc(A.colptr, A.rowidx)
-    got = labels.cpu().numpy()
+    lab = labels.long()
+    col = torch.repeat_interleave(torch.arange(A.n, device=dev), torch.diff(Ad.colptr.long()))
+    valid = bool((lab <= torch.arange(A.n, device=dev)).all() and (lab[lab] == lab).all()
+                 and (lab[Ad.rowidx.long()] == lab[col]).all())
+    comps = int((lab == torch.arange(A.n, device=dev)).sum().item())
     Ad.close()
-    return {"ms": t, "rounds": int(rounds.item()), "components": k,
-            "identical_to_reference": bool((got == ref).all())}
+    return {"ms": t, "rounds": int(rounds.item()), "components": comps, "labels_valid": valid}
 
 
 def bench_batched(S, dev, stream, B=256):
