@@ -4,7 +4,10 @@ This package is the plain, sequential statement of what the GPU path
 computes (Azad & Buluc, arXiv 1610.07902): a Gustavson column walk into a
 sparse accumulator (Sec. I, Sec. II-F), BFS as repeated masked
 (min, select2nd) SpMSpV (Sec. IV-D), and the pull (matrix-driven) form of a
-BFS level (Sec. II-B).  The arithmetic lives in ``oracle.c``; this module
+BFS level (Sec. II-B), and the definitions the SpMSpV-built graph algorithms
+of Sec. I reach: connected components (smallest vertex id per component) and
+the maximal independent set of Luby's rounds with fixed priorities (the
+greedy set in priority order).  The arithmetic lives in ``oracle.c``; this module
 only compiles it with gcc and marshals numpy arrays.
 
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
@@ -50,6 +53,8 @@ def _bind(lib):
     lib.oracle_bfs_pull.argtypes = [ctypes.c_int32, p, p, ctypes.c_int32, p, p]
     lib.oracle_cc.restype = ctypes.c_int32
     lib.oracle_cc.argtypes = [ctypes.c_int32, p, p, p]
+    lib.oracle_mis.restype = ctypes.c_int32
+    lib.oracle_mis.argtypes = [ctypes.c_int32, p, p, p, p]
     return lib
 
 
@@ -162,6 +167,21 @@ def cc(colptr, rowidx, lib=None):
     if k < 0:
         raise ValueError("oracle_cc failed with code %d" % k)
     return label, int(k)
+
+
+def mis(colptr, rowidx, prio, lib=None):
+    """Maximal independent set reached by Luby's rounds with these distinct
+    priorities: (in_set int32[n] of 0/1, size)."""
+    lib = lib or _load()
+    colptr = np.ascontiguousarray(colptr, dtype=np.int32)
+    rowidx = np.ascontiguousarray(rowidx, dtype=np.int32)
+    prio = np.ascontiguousarray(prio, dtype=np.int32)
+    n = colptr.shape[0] - 1
+    in_set = np.empty(n, dtype=np.int32)
+    k = lib.oracle_mis(n, _ptr(colptr), _ptr(rowidx), _ptr(prio), _ptr(in_set))
+    if k < 0:
+        raise ValueError("oracle_mis failed with code %d" % k)
+    return in_set, int(k)
 
 
 def bfs_pull(colptr, rowidx, src, lib=None):

@@ -371,3 +371,57 @@ int32_t oracle_cc(int32_t n, const int32_t* colptr, const int32_t* rowidx, int32
   free(low);
   return comps;
 }
+
+/*
+ * Maximal independent set of an undirected graph (pattern-symmetric CSC),
+ * the set Luby's rounds reach with fixed, distinct priorities (Sec. I names
+ * maximal independent sets among the SpMSpV-built graph algorithms).  That
+ * set has a plain definition, written out here: take the vertices in order
+ * of increasing priority and keep each one none of whose neighbours has been
+ * kept (the greedy set in priority order).  in_set[v] = 1 if kept, else 0.
+ * Returns the size of the set, -1 on a bad row id, -3 if priorities repeat.
+ */
+static const int32_t* g_prio_for_sort;
+static int cmp_by_prio(const void* a, const void* b) {
+  const int32_t pa = g_prio_for_sort[*(const int32_t*)a], pb = g_prio_for_sort[*(const int32_t*)b];
+  return (pa > pb) - (pa < pb);
+}
+
+int32_t oracle_mis(int32_t n, const int32_t* colptr, const int32_t* rowidx, const int32_t* prio,
+                   int32_t* in_set) {
+  int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  if (!order) return -2;
+  for (int32_t v = 0; v < n; ++v) {
+    order[v] = v;
+    in_set[v] = 0;
+  }
+  g_prio_for_sort = prio;
+  qsort(order, (size_t)n, sizeof(int32_t), cmp_by_prio);
+  for (int32_t k = 1; k < n; ++k)
+    if (prio[order[k]] == prio[order[k - 1]]) {
+      free(order);
+      return -3;
+    }
+  int32_t size = 0;
+  for (int32_t k = 0; k < n; ++k) {
+    const int32_t v = order[k];
+    int keep = 1;
+    for (int32_t p = colptr[v]; p < colptr[v + 1]; ++p) {
+      const int32_t u = rowidx[p];
+      if (u < 0 || u >= n) {
+        free(order);
+        return -1;
+      }
+      if (u != v && in_set[u]) {
+        keep = 0;
+        break;
+      }
+    }
+    if (keep) {
+      in_set[v] = 1;
+      ++size;
+    }
+  }
+  free(order);
+  return size;
+}

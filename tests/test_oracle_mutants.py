@@ -15,6 +15,7 @@ import oracle
 import synth
 import test_oracle_pins as pins
 import test_oracle_cc
+import test_oracle_mis
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
 
@@ -34,6 +35,10 @@ MUTANTS = {
                         "  for (int32_t v = 0; v < n; ++v) label[v] = uf_find(up, v);"),
     "cc_drops_last_edge": ("    for (int32_t p = colptr[j]; p < colptr[j + 1]; ++p) {\n      const int32_t i = rowidx[p];",
                            "    for (int32_t p = colptr[j]; p + 1 < colptr[j + 1]; ++p) {\n      const int32_t i = rowidx[p];"),
+    "mis_descending_order": ("  return (pa > pb) - (pa < pb);", "  return (pa < pb) - (pa > pb);"),
+    "mis_drops_last_neighbour": ("    for (int32_t p = colptr[v]; p < colptr[v + 1]; ++p) {\n      const int32_t u = rowidx[p];",
+                                 "    for (int32_t p = colptr[v]; p + 1 < colptr[v + 1]; ++p) {\n      const int32_t u = rowidx[p];"),
+    "mis_ignores_members": ("      if (u != v && in_set[u]) {", "      if (u != v && !in_set[u]) {"),
     "mult_count_after_mask": ("      ++nmult; /* every selected column entry is one multiplication */\n      if (mask) {\n        int in_mask = mask[i] != 0;\n        if (complement ? in_mask : !in_mask) continue;\n      }",
                               "      if (mask) {\n        int in_mask = mask[i] != 0;\n        if (complement ? in_mask : !in_mask) continue;\n      }\n      ++nmult;"),
 }
@@ -64,6 +69,8 @@ def run_pins():
         ("grid", pins.test_intact_grid_levels_are_manhattan_distance),
         ("cc_hand", test_oracle_cc.test_hand_graph),
         ("cc_scipy", lambda: test_oracle_cc.test_against_scipy_and_invariants(2000, 3000, 5, 2)),
+        ("mis_path", test_oracle_mis.test_path),
+        ("mis_luby", lambda: test_oracle_mis.test_against_luby_rounds(400, 1600, 2)),
     ]
     for name, fn in checks:
         try:
