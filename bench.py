@@ -284,6 +284,39 @@ def bench_cc(S, A, dev, stream):
     return {"ms": t, "rounds": int(rounds.item()), "components": comps, "labels_valid": valid}
 
 
+def bench_mis(S, A, dev, stream):
+    """Maximal independent set of the headline graph (Luby's rounds with a
+    seeded random permutation as priorities, two SpMSpVs per round, all rounds
+    in one graph launch).  Checked by the properties that single out the
+    greedy set in priority order: no edge joins two members, and every
+    non-member has a member neighbour of smaller priority."""
+    import torch
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC,
+                     device=dev)
+    g = torch.Generator(device="cpu").manual_seed(7)
+    prio = torch.randperm(A.n, generator=g).to(torch.int32).to(dev)
+    in_set = torch.empty(A.n, dtype=torch.int32, device=dev)
+    rounds = torch.zeros(1, dtype=torch.int32, device=dev)
+    run = lambda: S.spmspv_mis(Ad.handle, prio, in_set, rounds, 0, stream)
+    run()
+    t = _events_ms(run, stream, 3)
+    mem = in_set.bool()
+    col = torch.repeat_interleave(torch.arange(A.n, device=dev), torch.diff(Ad.colptr.long()))
+    row = Ad.rowidx.long()
+    off = row != col
+    independent = not bool((mem[row] & mem[col] & off).any())
+    big = torch.iinfo(torch.int64).max
+    p64 = prio.long()
+    src = torch.where(mem[col] & off, p64[col], torch.full_like(p64[col], big))
+    best = torch.full((A.n,), big, dtype=torch.int64, device=dev).scatter_reduce(0, row, src, "amin")
+    dominated = bool(((best < p64) | mem).all())
+    out = {"ms": t, "rounds": int(rounds.item()), "size": int(mem.sum().item()),
+           "independent": independent, "each_nonmember_has_smaller_member_neighbour": dominated}
+    del col, row, off, src, best
+    Ad.close()
+    return out
+
+
 def bench_batched(S, dev, stream, B=256):
     """256 frontiers on R-MAT s20 in one batched launch (autotuned) against
     256 sequential plain calls; multi-source BFS and ACL the same way."""
@@ -608,6 +641,7 @@ def main():
         extras["bfs_rmat"] = bench_bfs(S, A, dev, stream, "rmat s%d ef16 seed 1" % args.scale,
                                        synth.sources(A.colptr, 64, seed=2), params)
         extras["cc_rmat"] = bench_cc(S, A, dev, stream)
+        extras["mis_rmat"] = bench_mis(S, A, dev, stream)
         del Ad
         G = synth.grid3d(256, 256, 256, 0.05, seed=3)
         extras["bfs_grid"] = bench_bfs(S, G, dev, stream, "grid 256^3 7-point, 5% edges removed",

@@ -241,6 +241,28 @@ int spmspv_cc(spmspv_handle* h, int32_t* labels, int32_t* d_nrounds, uint32_t op
               spmspv_stream_t stream);
 
 /*
+ * Maximal independent set of an undirected graph (square, pattern-symmetric
+ * handle) by Luby's rounds with fixed priorities (Sec. I lists maximal
+ * independent sets as an SpMSpV customer; the rounds are this library's
+ * reading).  Per round, with C the undecided vertices: y = A (min.select2nd)
+ * prio|C with rows masked to C; the v in C with v not in y or prio(v) <= y(v)
+ * join; z = A (or.and) joiners with rows masked to the still undecided; z
+ * leaves C.  Until C is empty.  With distinct priorities the set is the
+ * greedy one in priority order (smallest first).  Self loops are ignored.
+ * All rounds run in one CUDA graph launch; asynchronous on `stream`.
+ *   prio       device int32[n] in: priorities, which must be distinct (for
+ *              example a permutation); repeated values end the rounds all the
+ *              same but may put two adjacent vertices in the set.
+ *   in_set     device int32[n] out: 1 for members, 0 otherwise.
+ *   d_nrounds  device int32 out (may be NULL): rounds run.
+ *   opts       SPMSPV_SCHED_OPT(s) with a push schedule s in 0..5, or 0 for the
+ *              default; SPMSPV_SCHED_AUTO is UNSUPPORTED.
+ * Allocates about 24 bytes per vertex of work buffers on first use.
+ */
+int spmspv_mis(spmspv_handle* h, const int32_t* prio, int32_t* in_set, int32_t* d_nrounds,
+               uint32_t opts, spmspv_stream_t stream);
+
+/*
  * Andersen-Chung-Lang push from B seeds (device int32[B]) on the unweighted
  * graph (handle created with SPMSPV_VAL_NONE; A symmetric), one batched (+,*)
  * SpMSpV per step (Sec. I lists ACL as a one-SpMSpV-per-step customer; the

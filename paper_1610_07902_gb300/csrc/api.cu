@@ -456,6 +456,7 @@ int spmspv_destroy(spmspv_handle* h) {
   release_bfs_graphs(h);
   release_batch(h);
   release_cc(h);
+  release_mis(h);
   release_tune(h);
   release_extras(h);
   cudaFree(h->rowidx_k2);

@@ -57,6 +57,17 @@ struct spmspv_handle {
   uint32_t* cc_y_val;
   int32_t* cc_cnt;
   void* cc_graph[SPMSPV_NUM_SCHEDULES / 2];  // cudaGraphExec_t per push schedule
+  // maximal independent set (first use): candidates (x), SpMSpV output (y),
+  // joiners, dense y lookup, decided bitmap, counts
+  int32_t* mis_x_idx;
+  uint32_t* mis_x_val;
+  int32_t* mis_y_idx;
+  uint32_t* mis_y_val;
+  int32_t* mis_j_idx;
+  int32_t* mis_ymin;
+  uint32_t* mis_decided;
+  int32_t* mis_cnt;
+  void* mis_graph[SPMSPV_NUM_SCHEDULES / 2];
   int32_t* bfs_count;   // [4] device counters
 };
 
@@ -78,6 +89,7 @@ void release_extras(spmspv_handle* h);
 void release_bfs_graphs(spmspv_handle* h);
 void release_batch(spmspv_handle* h);
 void release_cc(spmspv_handle* h);
+void release_mis(spmspv_handle* h);
 // Reads and clears the status words of the batched lanes' workspaces (after
 // the caller has synchronised the stream); CUDA errors are returned in *e.
 uint32_t batch_collect_status(spmspv_handle* h, cudaError_t* e);

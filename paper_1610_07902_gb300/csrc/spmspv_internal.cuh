@@ -80,6 +80,7 @@ struct DevState {
   int32_t* bfs_level;  // BFS outputs of the current search
   int32_t* bfs_parent;
   int32_t* cc_labels;  // connected components: the caller's labels
+  int32_t* mis_in;     // maximal independent set: the caller's membership flags
   uint32_t* bfs_fb;    // BFS: two frontier bitmaps of ceil(n/32) words; level L reads
                        // bitmap (L-1)&1 (pull) and writes bitmap L&1 (K3 or pull)
   uint32_t k1_done;    // K1 CTAs finished; the last one runs the selector (self-resetting)

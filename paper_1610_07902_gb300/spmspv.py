@@ -124,6 +124,7 @@ def load(build_if_missing: bool = True):
         lib.spmspv_tune_clear.argtypes = [_P]
         lib.spmspv_selftest_wait_timeout.argtypes = [_P, ctypes.c_uint32, _P]
         lib.spmspv_cc.argtypes = [_P, _P, _P, ctypes.c_uint32, _P]
+        lib.spmspv_mis.argtypes = [_P, _P, _P, _P, ctypes.c_uint32, _P]
         lib.spmspv_profile_begin.argtypes = [_P]
         lib.spmspv_profile_end.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_int32)]
@@ -303,6 +304,11 @@ def spmspv_acl(h, B, seeds, alpha, eps, max_steps, p_out, r_out, steps_out, lane
 
 def spmspv_cc(h, labels, d_nrounds=None, opts=0, stream=None):
     _check(load().spmspv_cc(h, _ptr(labels), _ptr(d_nrounds), int(opts), _stream(stream)), "spmspv_cc")
+
+
+def spmspv_mis(h, prio, in_set, d_nrounds=None, opts=0, stream=None):
+    _check(load().spmspv_mis(h, _ptr(prio), _ptr(in_set), _ptr(d_nrounds), int(opts), _stream(stream)),
+           "spmspv_mis")
 
 
 def spmspv_selftest_wait_timeout(h, spins=1000, stream=None):
