@@ -7,7 +7,8 @@ sparse accumulator (Sec. I, Sec. II-F), BFS as repeated masked
 BFS level (Sec. II-B), and the definitions the SpMSpV-built graph algorithms
 of Sec. I reach: connected components (smallest vertex id per component) and
 the maximal independent set of Luby's rounds with fixed priorities (the
-greedy set in priority order).  The arithmetic lives in ``oracle.c``; this module
+greedy set in priority order), and the cardinality of a maximum bipartite
+matching between rows and columns (augmenting paths).  The arithmetic lives in ``oracle.c``; this module
 only compiles it with gcc and marshals numpy arrays.
 
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
@@ -55,6 +56,8 @@ def _bind(lib):
     lib.oracle_cc.argtypes = [ctypes.c_int32, p, p, p]
     lib.oracle_mis.restype = ctypes.c_int32
     lib.oracle_mis.argtypes = [ctypes.c_int32, p, p, p, p]
+    lib.oracle_mcm.restype = ctypes.c_int32
+    lib.oracle_mcm.argtypes = [ctypes.c_int32, ctypes.c_int32, p, p, p, p]
     return lib
 
 
@@ -182,6 +185,21 @@ def mis(colptr, rowidx, prio, lib=None):
     if k < 0:
         raise ValueError("oracle_mis failed with code %d" % k)
     return in_set, int(k)
+
+
+def mcm(m, colptr, rowidx, lib=None):
+    """Maximum-cardinality matching between the m rows and the columns:
+    (mate_r int32[m], mate_c int32[n], cardinality)."""
+    lib = lib or _load()
+    colptr = np.ascontiguousarray(colptr, dtype=np.int32)
+    rowidx = np.ascontiguousarray(rowidx, dtype=np.int32)
+    n = colptr.shape[0] - 1
+    mate_r = np.empty(m, dtype=np.int32)
+    mate_c = np.empty(n, dtype=np.int32)
+    k = lib.oracle_mcm(m, n, _ptr(colptr), _ptr(rowidx), _ptr(mate_r), _ptr(mate_c))
+    if k < 0:
+        raise ValueError("oracle_mcm failed with code %d" % k)
+    return mate_r, mate_c, int(k)
 
 
 def bfs_pull(colptr, rowidx, src, lib=None):

@@ -425,3 +425,81 @@ int32_t oracle_mis(int32_t n, const int32_t* colptr, const int32_t* rowidx, cons
   free(order);
   return size;
 }
+
+/*
+ * Maximum-cardinality matching of the bipartite graph whose two sides are the
+ * rows and the columns of A (m-by-n CSC; an edge joins row i and column j when
+ * A(i,j) is stored).  Sec. I names bipartite graph matching among the
+ * SpMSpV-built graph algorithms.  The cardinality has a plain definition, the
+ * largest number of edges no two of which share an end; the matching itself
+ * is one of possibly many.  Method: augmenting paths (Berge: a matching is
+ * maximum exactly when no augmenting path is left), searched depth first
+ * from each column in turn, with the rows seen in this search stamped so that
+ * each is tried once (Kuhn's algorithm, written with an explicit stack).
+ * mate_r[i] = matched column of row i or -1; mate_c[j] = matched row or -1.
+ * Returns the cardinality, -1 on a bad row id, -2 out of memory.
+ */
+int32_t oracle_mcm(int32_t m, int32_t n, const int32_t* colptr, const int32_t* rowidx,
+                   int32_t* mate_r, int32_t* mate_c) {
+  int32_t* stamp = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+  int32_t* scol = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
+  int32_t* spos = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
+  if (!stamp || !scol || !spos) {
+    free(stamp);
+    free(scol);
+    free(spos);
+    return -2;
+  }
+  for (int32_t i = 0; i < m; ++i) {
+    mate_r[i] = -1;
+    stamp[i] = -1;
+  }
+  for (int32_t j = 0; j < n; ++j) mate_c[j] = -1;
+  int32_t size = 0;
+  for (int32_t r = 0; r < n; ++r) {
+    int32_t depth = 0, found = -1;
+    scol[0] = r;
+    spos[0] = colptr[r];
+    while (depth >= 0) {
+      const int32_t j = scol[depth];
+      const int32_t p = spos[depth];
+      if (p == colptr[j + 1]) {  /* every row of column j tried: back up */
+        --depth;
+        continue;
+      }
+      spos[depth] = p + 1;
+      const int32_t i = rowidx[p];
+      if (i < 0 || i >= m) {
+        free(stamp);
+        free(scol);
+        free(spos);
+        return -1;
+      }
+      if (stamp[i] == r) continue;
+      stamp[i] = r;
+      if (mate_r[i] < 0) {  /* a free row ends an augmenting path */
+        found = i;
+        break;
+      }
+      ++depth;  /* continue the alternating path through the column matched to row i */
+      scol[depth] = mate_r[i];
+      spos[depth] = colptr[mate_r[i]];
+    }
+    if (found < 0) continue;
+    /* flip the path: the column at each depth takes the row reached from it,
+       giving up the row it was entered through (its old mate) to the column below */
+    int32_t i = found;
+    for (int32_t d = depth; d >= 0; --d) {
+      const int32_t j = scol[d];
+      const int32_t old = mate_c[j];
+      mate_c[j] = i;
+      mate_r[i] = j;
+      i = old;
+    }
+    ++size;
+  }
+  free(stamp);
+  free(scol);
+  free(spos);
+  return size;
+}

@@ -16,6 +16,7 @@ import synth
 import test_oracle_pins as pins
 import test_oracle_cc
 import test_oracle_mis
+import test_oracle_mcm
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
 
@@ -39,6 +40,11 @@ MUTANTS = {
     "mis_drops_last_neighbour": ("    for (int32_t p = colptr[v]; p < colptr[v + 1]; ++p) {\n      const int32_t u = rowidx[p];",
                                  "    for (int32_t p = colptr[v]; p + 1 < colptr[v + 1]; ++p) {\n      const int32_t u = rowidx[p];"),
     "mis_ignores_members": ("      if (u != v && in_set[u]) {", "      if (u != v && !in_set[u]) {"),
+    "mcm_no_descent": ("      ++depth;  /* continue the alternating path through the column matched to row i */\n      scol[depth] = mate_r[i];\n      spos[depth] = colptr[mate_r[i]];",
+                       "      continue;"),
+    "mcm_skips_last_row": ("      if (p == colptr[j + 1]) {  /* every row of column j tried: back up */",
+                           "      if (p + 1 >= colptr[j + 1]) {  /* every row of column j tried: back up */"),
+    "mcm_flip_keeps_found": ("      mate_r[i] = j;\n      i = old;", "      mate_r[i] = j;\n      i = old >= 0 ? found : old;"),
     "mult_count_after_mask": ("      ++nmult; /* every selected column entry is one multiplication */\n      if (mask) {\n        int in_mask = mask[i] != 0;\n        if (complement ? in_mask : !in_mask) continue;\n      }",
                               "      if (mask) {\n        int in_mask = mask[i] != 0;\n        if (complement ? in_mask : !in_mask) continue;\n      }\n      ++nmult;"),
 }
@@ -71,6 +77,8 @@ def run_pins():
         ("cc_scipy", lambda: test_oracle_cc.test_against_scipy_and_invariants(2000, 3000, 5, 2)),
         ("mis_path", test_oracle_mis.test_path),
         ("mis_luby", lambda: test_oracle_mis.test_against_luby_rounds(400, 1600, 2)),
+        ("mcm_greedy_undone", test_oracle_mcm.test_first_greedy_choice_must_be_undone),
+        ("mcm_scipy", lambda: test_oracle_mcm.test_against_scipy_hopcroft_karp(1000, 1500, 2200, 2)),
     ]
     for name, fn in checks:
         try:
