@@ -317,6 +317,43 @@ def bench_mis(S, A, dev, stream):
     return out
 
 
+def bench_mcm(S, A, dev, stream):
+    """Maximum matching between the rows and the columns of the headline
+    matrix (phases of multi-source alternating BFS, one SpMSpV per level, all
+    in one graph launch).  The matching is checked for validity here (mates
+    agree, matched pairs are edges); that it is maximum is checked against the
+    reference's cardinality in the tests, at sizes the reference finishes."""
+    import torch
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, device=dev)
+    mate_r = torch.empty(A.m, dtype=torch.int32, device=dev)
+    mate_c = torch.empty(A.n, dtype=torch.int32, device=dev)
+    card = torch.zeros(1, dtype=torch.int32, device=dev)
+    phases = torch.zeros(1, dtype=torch.int32, device=dev)
+    run = lambda: S.spmspv_mcm(Ad.handle, mate_r, mate_c, card, phases, 0, stream)
+    run()
+    t = _events_ms(run, stream, 2)
+    mc = mate_c.long()
+    matched = torch.nonzero(mc >= 0).flatten()
+    rows = mc[matched]
+    agree = bool((mate_r.long()[rows] == matched).all()) and int((mate_r >= 0).sum()) == matched.numel()
+    # a matched pair (i, j) is an edge: i lies in column j's row list
+    cp = Ad.colptr.long()
+    ri = Ad.rowidx.long()
+    lo, hi = cp[matched], cp[matched + 1]
+    key = matched * A.m + rows
+    col = torch.repeat_interleave(torch.arange(A.n, device=dev), torch.diff(cp))
+    edges = torch.sort(col * A.m + ri).values
+    pos = torch.searchsorted(edges, key).clamp(max=edges.numel() - 1)
+    edges_ok = bool((edges[pos] == key).all()) and bool((hi > lo).all())
+    out = {"ms": t, "phases": int(phases.item()), "cardinality": int(card.item()),
+           "matched_pairs_found": int(matched.numel()), "mates_agree": agree,
+           "pairs_are_edges": edges_ok,
+           "status": S.spmspv_device_status(Ad.handle)}
+    del col, edges, pos, key, cp, ri
+    Ad.close()
+    return out
+
+
 def bench_batched(S, dev, stream, B=256):
     """256 frontiers on R-MAT s20 in one batched launch (autotuned) against
     256 sequential plain calls; multi-source BFS and ACL the same way."""
@@ -642,6 +679,7 @@ def main():
                                        synth.sources(A.colptr, 64, seed=2), params)
         extras["cc_rmat"] = bench_cc(S, A, dev, stream)
         extras["mis_rmat"] = bench_mis(S, A, dev, stream)
+        extras["matching_rmat"] = bench_mcm(S, A, dev, stream)
         del Ad
         G = synth.grid3d(256, 256, 256, 0.05, seed=3)
         extras["bfs_grid"] = bench_bfs(S, G, dev, stream, "grid 256^3 7-point, 5% edges removed",

@@ -94,6 +94,8 @@ typedef struct spmspv_handle spmspv_handle;
 #define SPMSPV_DEV_TIMEOUT 2u  /* a bounded wait gave up; outputs are invalid */
 #define SPMSPV_DEV_INDEX 4u    /* an x index was outside [0, n), or a bucket overflowed
                                   (duplicate x indices); outputs are invalid */
+#define SPMSPV_DEV_BOUND 8u    /* a device loop reached the iteration bound its
+                                  mathematics guarantees (matching); outputs are invalid */
 
 /* Message for the last error returned on this thread (library-owned). */
 const char* spmspv_last_error(void);
@@ -261,6 +263,31 @@ int spmspv_cc(spmspv_handle* h, int32_t* labels, int32_t* d_nrounds, uint32_t op
  */
 int spmspv_mis(spmspv_handle* h, const int32_t* prio, int32_t* in_set, int32_t* d_nrounds,
                uint32_t opts, spmspv_stream_t stream);
+
+/*
+ * Maximum-cardinality matching of the bipartite graph between the m rows and
+ * the n columns of A (an edge wherever A(i,j) is stored; any shape, no
+ * symmetry needed) by phases of multi-source alternating BFS, one
+ * (min.select2nd) SpMSpV per level with the visited rows as a complemented
+ * mask (Sec. I lists bipartite matching as an SpMSpV customer; the phases are
+ * this library's reading).  A phase grows one BFS tree from every free column,
+ * keeps the first free row each tree reaches and flips those vertex-disjoint
+ * augmenting paths; the search ends when a phase finds none, and the matching
+ * is then maximum.  Which maximum matching comes out depends on the order of
+ * atomic operations; its cardinality does not.  All phases run in one CUDA
+ * graph launch; asynchronous on `stream`.
+ *   mate_r     device int32[m] out: matched column of each row, or -1.
+ *   mate_c     device int32[n] out: matched row of each column, or -1.
+ *   d_card     device int32 out (may be NULL): the cardinality.
+ *   d_nphases  device int32 out (may be NULL): phases that flipped paths.
+ *   opts       SPMSPV_SCHED_OPT(s) with a push schedule s in 0..5, or 0 for the
+ *              default; SPMSPV_SCHED_AUTO is UNSUPPORTED.
+ * SPMSPV_DEV_BOUND in the device status afterwards means a loop bound was
+ * reached and the outputs are invalid.  Allocates about 16 bytes per row and
+ * 16 per column of work buffers on first use.
+ */
+int spmspv_mcm(spmspv_handle* h, int32_t* mate_r, int32_t* mate_c, int32_t* d_card,
+               int32_t* d_nphases, uint32_t opts, spmspv_stream_t stream);
 
 /*
  * Andersen-Chung-Lang push from B seeds (device int32[B]) on the unweighted

@@ -457,6 +457,7 @@ int spmspv_destroy(spmspv_handle* h) {
   release_batch(h);
   release_cc(h);
   release_mis(h);
+  release_mcm(h);
   release_tune(h);
   release_extras(h);
   cudaFree(h->rowidx_k2);
@@ -529,7 +530,7 @@ int spmspv_device_status(spmspv_handle* h, uint32_t* flags) {
   if (e != cudaSuccess) return cuda_fail(e, "status clear");
   v |= batch_collect_status(h, &e);  // the batched lanes' own workspaces
   if (e != cudaSuccess) return cuda_fail(e, "lane status");
-  *flags = v & (SPMSPV_DEV_CAPACITY | SPMSPV_DEV_TIMEOUT | ST_INDEX);
+  *flags = v & (SPMSPV_DEV_CAPACITY | SPMSPV_DEV_TIMEOUT | ST_INDEX | ST_BOUND);
   return SPMSPV_OK;
 }
 

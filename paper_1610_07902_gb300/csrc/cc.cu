@@ -84,78 +84,15 @@ __global__ void k_cc_continue(cudaGraphConditionalHandle cond, DevState* st, int
 
 static int cc_round_launches(spmspv_handle* h, const Sched& sc, cudaGraphConditionalHandle cond,
                              cudaStream_t s) {
-  cudaError_t e = launch_k1(kMinSelect2nd, h->A, h->ws, h->nb_fine, h->cc_x_idx, h->cc_x_val, 0,
-                            h->cc_cnt, h->k1_grid_dev, &sc, s);
-  if (e != cudaSuccess) return cuda_fail(e, "cc work scan");
-  if ((e = launch_k2(kMinSelect2nd, h->A, h->ws, h->lwb_lo, h->nb_fine, nullptr, 0, h->k2_grid,
-                     h->k2_smem, s, 0, sc.q)) != cudaSuccess)
-    return cuda_fail(e, "cc expand/scatter");
-  const int nb = (int)(((int64_t)h->A.m + (1 << sc.lwb) - 1) >> sc.lwb);
-  const int k3_grid = std::max(1, std::min(nb, h->sm_count * h->k3_bps[sc.lwb - h->lwb_lo]));
-  if ((e = launch_k3(kMinSelect2nd, false, h->A, h->ws, h->lwb_lo, h->nb_fine, h->cc_y_idx, h->cc_y_val,
-                     h->A.m, nullptr, nullptr, k3_grid, k3_smem_bytes(sc.lwb), s)) != cudaSuccess)
-    return cuda_fail(e, "cc merge");
+  int rc = graph_spmspv(h, kMinSelect2nd, sc, h->cc_x_idx, h->cc_x_val, h->cc_cnt, nullptr, h->cc_y_idx,
+                        h->cc_y_val, s);
+  if (rc != SPMSPV_OK) return rc;
   k_cc_update<<<h->sm_count * 4, 256, 0, s>>>(h->ws.st, h->cc_y_idx, h->cc_y_val, h->cc_x_idx,
                                                h->cc_x_val, h->cc_cnt);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "cc update");
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "cc update");
   k_cc_continue<<<1, 32, 0, s>>>(cond, h->ws.st, h->cc_cnt, h->A.n);
   return (e = cudaGetLastError()) == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "cc condition");
-}
-
-static int build_cc_graph(spmspv_handle* h, int sched, cudaGraphExec_t* out) {
-  cudaGraph_t g = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaStream_t cs = nullptr;
-  cudaError_t e = cudaGraphCreate(&g, 0);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
-  int rc = SPMSPV_OK;
-  do {
-    cudaGraphConditionalHandle cond;
-    if ((e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess) {
-      rc = cuda_fail(e, "cc condition handle");
-      break;
-    }
-    cudaGraphNodeParams np = {};
-    np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = cond;
-    np.conditional.type = cudaGraphCondTypeWhile;
-    np.conditional.size = 1;
-    cudaGraphNode_t node;
-    if ((e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np)) != cudaSuccess) {
-      rc = cuda_fail(e, "cc while node");
-      break;
-    }
-    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
-      rc = cuda_fail(e, "capture stream");
-      break;
-    }
-    if ((e = cudaStreamBeginCaptureToGraph(cs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
-      rc = cuda_fail(e, "begin capture");
-      break;
-    }
-    void* saved_prof = h->prof;
-    h->prof = nullptr;
-    rc = cc_round_launches(h, decode_schedule(h, sched), cond, cs);
-    h->prof = saved_prof;
-    cudaGraph_t captured = nullptr;
-    e = cudaStreamEndCapture(cs, &captured);
-    if (rc != SPMSPV_OK) break;
-    if (e != cudaSuccess) {
-      rc = cuda_fail(e, "end capture");
-      break;
-    }
-    if ((e = cudaGraphInstantiate(&exec, g, 0)) != cudaSuccess) rc = cuda_fail(e, "instantiate cc graph");
-  } while (0);
-  if (cs) cudaStreamDestroy(cs);
-  cudaGraphDestroy(g);
-  if (rc != SPMSPV_OK) {
-    if (exec) cudaGraphExecDestroy(exec);
-    cudaGetLastError();
-    return rc;
-  }
-  *out = exec;
-  return SPMSPV_OK;
 }
 
 void release_cc(spmspv_handle* h) {
@@ -207,7 +144,11 @@ extern "C" int spmspv_cc(spmspv_handle* h, int32_t* labels, int32_t* d_nrounds, 
   }
   if (!h->cc_graph[sched]) {
     cudaGraphExec_t exec = nullptr;
-    if ((rc = build_cc_graph(h, sched, &exec)) != SPMSPV_OK) return rc;
+    const Sched sc = decode_schedule(h, sched);
+    rc = build_while_graph(h, [&](cudaGraphConditionalHandle c, cudaStream_t cs) {
+      return cc_round_launches(h, sc, c, cs);
+    }, &exec);
+    if (rc != SPMSPV_OK) return rc;
     h->cc_graph[sched] = exec;
   }
   cudaStream_t s = (cudaStream_t)stream;

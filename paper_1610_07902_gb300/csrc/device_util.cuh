@@ -133,4 +133,16 @@ __device__ __forceinline__ T block_exclusive_sum(T v, T* sh, T* total) {
   return r;
 }
 
+// Appends the lanes of a warp whose `take` is set at counter[0]++, one atomic
+// per warp; returns this lane's slot (meaningful where take is set).  Every
+// lane of the warp must call it.
+__device__ __forceinline__ int32_t warp_append(bool take, int32_t* counter) {
+  const int lane = threadIdx.x & 31;
+  const unsigned b = __ballot_sync(0xffffffffu, take);
+  int32_t base = 0;
+  if (lane == 0 && b) base = atomicAdd(counter, __popc(b));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  return base + __popc(b & ((1u << lane) - 1u));
+}
+
 }  // namespace spmspv

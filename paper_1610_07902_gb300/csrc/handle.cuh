@@ -68,6 +68,19 @@ struct spmspv_handle {
   uint32_t* mis_decided;
   int32_t* mis_cnt;
   void* mis_graph[SPMSPV_NUM_SCHEDULES / 2];
+  // maximum bipartite matching (first use): frontier columns and the next
+  // frontier, y (rows), row parents, column roots, the leaf row of each
+  // root, visited rows, counts
+  int32_t* mcm_x_idx;
+  int32_t* mcm_x2_idx;
+  int32_t* mcm_y_idx;
+  uint32_t* mcm_y_val;
+  int32_t* mcm_parent_r;
+  int32_t* mcm_root_c;
+  int32_t* mcm_leaf;
+  uint32_t* mcm_visited;
+  int32_t* mcm_cnt;
+  void* mcm_graph[SPMSPV_NUM_SCHEDULES / 2];
   int32_t* bfs_count;   // [4] device counters
 };
 
@@ -90,6 +103,20 @@ void release_bfs_graphs(spmspv_handle* h);
 void release_batch(spmspv_handle* h);
 void release_cc(spmspv_handle* h);
 void release_mis(spmspv_handle* h);
+void release_mcm(spmspv_handle* h);
+// Graph loops (graph_loop.cu).  build_while_graph captures `body` (given the
+// loop's condition handle and the capture stream) as the body of a WHILE node
+// whose condition starts at 1, and instantiates the graph.
+int build_while_graph(spmspv_handle* h,
+                      const std::function<int(cudaGraphConditionalHandle, cudaStream_t)>& body,
+                      cudaGraphExec_t* out);
+// One push SpMSpV inside a captured graph loop: x = (x_idx, x_val;
+// x_val NULL gives x(j) = j) with its length read from f_dev on the device,
+// rows whose bit is set in skip_rows produce nothing, y to (y_idx, y_val) with
+// capacity m and its length in the device state.
+int graph_spmspv(spmspv_handle* h, int sem, const Sched& sc, const int32_t* x_idx,
+                 const uint32_t* x_val, const int32_t* f_dev, const uint32_t* skip_rows,
+                 int32_t* y_idx, uint32_t* y_val, cudaStream_t s);
 // Reads and clears the status words of the batched lanes' workspaces (after
 // the caller has synchronised the stream); CUDA errors are returned in *e.
 uint32_t batch_collect_status(spmspv_handle* h, cudaError_t* e);

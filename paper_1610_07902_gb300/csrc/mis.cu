@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <climits>
 
+#include "device_util.cuh"
 #include "handle.cuh"
 #include "spmspv_internal.cuh"
 
@@ -57,17 +58,6 @@ __global__ void k_mis_scatter(const DevState* __restrict__ st, const int32_t* __
   const int32_t ny = st->nnz_y;
   for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < ny; k += gridDim.x * blockDim.x)
     ymin[y_idx[k]] = (int32_t)y_val[k];
-}
-
-// Appends the lanes of a warp whose `take` is set to list[cnt..], one atomic per warp;
-// returns this lane's slot (meaningful where take is set).
-__device__ __forceinline__ int32_t warp_append(bool take, int32_t* counter) {
-  const int lane = threadIdx.x & 31;
-  const unsigned b = __ballot_sync(0xffffffffu, take);
-  int32_t base = 0;
-  if (lane == 0 && b) base = atomicAdd(counter, __popc(b));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  return base + __popc(b & ((1u << lane) - 1u));
 }
 
 // Local minima join: membership flag, decided bit, the joiner list J.
@@ -157,37 +147,19 @@ __global__ void k_mis_continue(cudaGraphConditionalHandle cond, DevState* st, in
 
 }  // namespace
 
-// One SpMSpV of a round: x from (x_idx, x_val) with its count on the device,
-// rows masked to the vertices whose decided bit is clear, y to (y_idx, y_val).
-static int mis_spmspv(spmspv_handle* h, int sem, const Sched& sc, const int32_t* x_idx,
-                      const uint32_t* x_val, const int32_t* f_dev, int32_t* y_idx, uint32_t* y_val,
-                      cudaStream_t s) {
-  cudaError_t e = launch_k1(sem, h->A, h->ws, h->nb_fine, x_idx, x_val, 0, f_dev, h->k1_grid_dev, &sc, s);
-  if (e != cudaSuccess) return cuda_fail(e, "mis work scan");
-  if ((e = launch_k2(sem, h->A, h->ws, h->lwb_lo, h->nb_fine, h->mis_decided, 1, h->k2_grid,
-                     h->k2_smem, s, 0, sc.q)) != cudaSuccess)
-    return cuda_fail(e, "mis expand/scatter");
-  const int nb = (int)(((int64_t)h->A.m + (1 << sc.lwb) - 1) >> sc.lwb);
-  const int k3_grid = std::max(1, std::min(nb, h->sm_count * h->k3_bps[sc.lwb - h->lwb_lo]));
-  if ((e = launch_k3(sem, false, h->A, h->ws, h->lwb_lo, h->nb_fine, y_idx, y_val, h->A.m, nullptr,
-                     nullptr, k3_grid, k3_smem_bytes(sc.lwb), s)) != cudaSuccess)
-    return cuda_fail(e, "mis merge");
-  return SPMSPV_OK;
-}
-
 static int mis_round_launches(spmspv_handle* h, const Sched& sc, cudaGraphConditionalHandle cond,
                               cudaStream_t s) {
   const int g = h->sm_count * 4;
-  int rc = mis_spmspv(h, kMinSelect2nd, sc, h->mis_x_idx, h->mis_x_val, &h->mis_cnt[0], h->mis_y_idx,
-                      h->mis_y_val, s);
+  int rc = graph_spmspv(h, kMinSelect2nd, sc, h->mis_x_idx, h->mis_x_val, &h->mis_cnt[0],
+                        h->mis_decided, h->mis_y_idx, h->mis_y_val, s);
   if (rc != SPMSPV_OK) return rc;
   k_mis_scatter<<<g, 256, 0, s>>>(h->ws.st, h->mis_y_idx, h->mis_y_val, h->mis_ymin);
   k_mis_join<<<g, 256, 0, s>>>(h->ws.st, h->mis_x_idx, h->mis_x_val, h->mis_ymin, h->mis_decided,
                                h->mis_j_idx, h->mis_cnt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "mis join");
-  if ((rc = mis_spmspv(h, kOrAnd, sc, h->mis_j_idx, nullptr, &h->mis_cnt[1], h->mis_y_idx, nullptr, s)) !=
-      SPMSPV_OK)
+  if ((rc = graph_spmspv(h, kOrAnd, sc, h->mis_j_idx, nullptr, &h->mis_cnt[1], h->mis_decided,
+                         h->mis_y_idx, nullptr, s)) != SPMSPV_OK)
     return rc;
   k_mis_remove<<<g, 256, 0, s>>>(h->ws.st, h->mis_y_idx, h->mis_decided);
   k_mis_compact<<<g, 256, 0, s>>>(h->mis_x_idx, h->mis_x_val, h->mis_decided, h->mis_y_idx,
@@ -195,62 +167,6 @@ static int mis_round_launches(spmspv_handle* h, const Sched& sc, cudaGraphCondit
   k_mis_copy<<<g, 256, 0, s>>>(h->mis_y_idx, h->mis_y_val, h->mis_x_idx, h->mis_x_val, h->mis_cnt);
   k_mis_continue<<<1, 32, 0, s>>>(cond, h->ws.st, h->mis_cnt, h->A.n);
   return (e = cudaGetLastError()) == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "mis round");
-}
-
-static int build_mis_graph(spmspv_handle* h, int sched, cudaGraphExec_t* out) {
-  cudaGraph_t g = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaStream_t cs = nullptr;
-  cudaError_t e = cudaGraphCreate(&g, 0);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
-  int rc = SPMSPV_OK;
-  do {
-    cudaGraphConditionalHandle cond;
-    if ((e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess) {
-      rc = cuda_fail(e, "mis condition handle");
-      break;
-    }
-    cudaGraphNodeParams np = {};
-    np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = cond;
-    np.conditional.type = cudaGraphCondTypeWhile;
-    np.conditional.size = 1;
-    cudaGraphNode_t node;
-    if ((e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np)) != cudaSuccess) {
-      rc = cuda_fail(e, "mis while node");
-      break;
-    }
-    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
-      rc = cuda_fail(e, "capture stream");
-      break;
-    }
-    if ((e = cudaStreamBeginCaptureToGraph(cs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
-      rc = cuda_fail(e, "begin capture");
-      break;
-    }
-    void* saved_prof = h->prof;
-    h->prof = nullptr;
-    rc = mis_round_launches(h, decode_schedule(h, sched), cond, cs);
-    h->prof = saved_prof;
-    cudaGraph_t captured = nullptr;
-    e = cudaStreamEndCapture(cs, &captured);
-    if (rc != SPMSPV_OK) break;
-    if (e != cudaSuccess) {
-      rc = cuda_fail(e, "end capture");
-      break;
-    }
-    if ((e = cudaGraphInstantiate(&exec, g, 0)) != cudaSuccess) rc = cuda_fail(e, "instantiate mis graph");
-  } while (0);
-  if (cs) cudaStreamDestroy(cs);
-  cudaGraphDestroy(g);
-  if (rc != SPMSPV_OK) {
-    if (exec) cudaGraphExecDestroy(exec);
-    cudaGetLastError();
-    return rc;
-  }
-  *out = exec;
-  return SPMSPV_OK;
 }
 
 void release_mis(spmspv_handle* h) {
@@ -312,7 +228,11 @@ extern "C" int spmspv_mis(spmspv_handle* h, const int32_t* prio, int32_t* in_set
   }
   if (!h->mis_graph[sched]) {
     cudaGraphExec_t exec = nullptr;
-    if ((rc = build_mis_graph(h, sched, &exec)) != SPMSPV_OK) return rc;
+    const Sched sc = decode_schedule(h, sched);
+    rc = build_while_graph(h, [&](cudaGraphConditionalHandle c, cudaStream_t cs) {
+      return mis_round_launches(h, sc, c, cs);
+    }, &exec);
+    if (rc != SPMSPV_OK) return rc;
     h->mis_graph[sched] = exec;
   }
   cudaStream_t s = (cudaStream_t)stream;

@@ -44,6 +44,7 @@ constexpr int HOT_MIN_DEG = 512;       // a hot row has at least this many nonze
 // ---- device status bits ----
 constexpr uint32_t ST_CAPACITY = SPMSPV_DEV_CAPACITY;
 constexpr uint32_t ST_TIMEOUT = SPMSPV_DEV_TIMEOUT;
+constexpr uint32_t ST_BOUND = SPMSPV_DEV_BOUND;
 constexpr uint32_t ST_INDEX = 4u;     // an x index or bucket fill was out of range
 
 // Bounded waits: iterations of a spin (each with a short sleep) before a
@@ -81,6 +82,8 @@ struct DevState {
   int32_t* bfs_parent;
   int32_t* cc_labels;  // connected components: the caller's labels
   int32_t* mis_in;     // maximal independent set: the caller's membership flags
+  int32_t* mcm_mate_r;  // bipartite matching: the caller's mate arrays (rows, columns)
+  int32_t* mcm_mate_c;
   uint32_t* bfs_fb;    // BFS: two frontier bitmaps of ceil(n/32) words; level L reads
                        // bitmap (L-1)&1 (pull) and writes bitmap L&1 (K3 or pull)
   uint32_t k1_done;    // K1 CTAs finished; the last one runs the selector (self-resetting)

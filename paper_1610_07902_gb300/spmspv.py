@@ -56,6 +56,7 @@ SPMSPV_SELECTOR_NPARAM = 1688
 SPMSPV_DEV_CAPACITY = 1
 SPMSPV_DEV_TIMEOUT = 2
 SPMSPV_DEV_INDEX = 4
+SPMSPV_DEV_BOUND = 8
 
 
 def SPMSPV_SCHED_OPT(s: int) -> int:
@@ -125,6 +126,7 @@ def load(build_if_missing: bool = True):
         lib.spmspv_selftest_wait_timeout.argtypes = [_P, ctypes.c_uint32, _P]
         lib.spmspv_cc.argtypes = [_P, _P, _P, ctypes.c_uint32, _P]
         lib.spmspv_mis.argtypes = [_P, _P, _P, _P, ctypes.c_uint32, _P]
+        lib.spmspv_mcm.argtypes = [_P, _P, _P, _P, _P, ctypes.c_uint32, _P]
         lib.spmspv_profile_begin.argtypes = [_P]
         lib.spmspv_profile_end.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_int32)]
@@ -309,6 +311,11 @@ def spmspv_cc(h, labels, d_nrounds=None, opts=0, stream=None):
 def spmspv_mis(h, prio, in_set, d_nrounds=None, opts=0, stream=None):
     _check(load().spmspv_mis(h, _ptr(prio), _ptr(in_set), _ptr(d_nrounds), int(opts), _stream(stream)),
            "spmspv_mis")
+
+
+def spmspv_mcm(h, mate_r, mate_c, d_card=None, d_nphases=None, opts=0, stream=None):
+    _check(load().spmspv_mcm(h, _ptr(mate_r), _ptr(mate_c), _ptr(d_card), _ptr(d_nphases), int(opts),
+                             _stream(stream)), "spmspv_mcm")
 
 
 def spmspv_selftest_wait_timeout(h, spins=1000, stream=None):
