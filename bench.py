@@ -354,6 +354,46 @@ def bench_mcm(S, A, dev, stream):
     return out
 
 
+def bench_sorted_x(S, A, Ad, dev, stream, flush, y_idx, y_val, cap, nnz_y):
+    """The sorted-versus-unsorted study of Sec. V (Fig. 2 there: x with 10K
+    and 2.5M nonzeros) on the headline matrix: x in random order, the same x
+    sorted by the caller, and x in random order sorted on the device first
+    (SPMSPV_SORT_X, the sort inside the timed call).  y is ascending in every
+    case (the bucket order gives it for free).  Median of 9 calls, L2 flushed
+    before each."""
+    import torch
+    import synth
+    out = {}
+    for fs in (10_000, 2_500_000):
+        xi, xv = synth.frontier(A.n, fs, seed=5, stream=2)
+        order = np.argsort(xi, kind="stable")
+        variants = {
+            "random_order": (xi, xv, 0),
+            "sorted_by_caller": (xi[order], xv[order], 0),
+            "device_presort": (xi, xv, S.SPMSPV_SORT_X),
+        }
+        res = {}
+        nz = {}
+        for name, (a, v, extra) in variants.items():
+            dxi, dxv = torch.from_numpy(np.ascontiguousarray(a)).to(dev), torch.from_numpy(np.ascontiguousarray(v)).to(dev)
+            run = lambda: S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, dxi, dxv, fs, None,
+                                       S.SPMSPV_SORTED_OUT | extra, y_idx, y_val, cap, nnz_y, stream)
+            run()
+            times = []
+            for _ in range(9):
+                flush.zero_()
+                times.append(_events_ms(run, stream, 1))
+            res[name + "_ms"] = float(np.median(times))
+            nz[name] = int(nnz_y.item())
+        res["products"] = S.spmspv_last_work(Ad.handle)
+        res["same_nnz_y"] = len(set(nz.values())) == 1
+        res["status"] = S.spmspv_device_status(Ad.handle)
+        res["sorted_by_caller_vs_random"] = res["random_order_ms"] / res["sorted_by_caller_ms"]
+        res["device_presort_vs_random"] = res["random_order_ms"] / res["device_presort_ms"]
+        out["nnz_x_%d" % fs] = res
+    return out
+
+
 def bench_batched(S, dev, stream, B=256):
     """256 frontiers on R-MAT s20 in one batched launch (autotuned) against
     256 sequential plain calls; multi-source BFS and ACL the same way."""
@@ -674,6 +714,7 @@ def main():
                                        "gteps": ws_ / (tms * 1e-3) / 1e9}
         sweep["note"] = "back-to-back host-launched calls, L2 not flushed between them"
         extras["sweep_rmat"] = sweep
+        extras["sorted_x_rmat"] = bench_sorted_x(S, A, Ad, dev, stream, flush, y_idx, y_val, cap, nnz_y)
         params = selector_params()
         extras["bfs_rmat"] = bench_bfs(S, A, dev, stream, "rmat s%d ef16 seed 1" % args.scale,
                                        synth.sources(A.colptr, 64, seed=2), params)

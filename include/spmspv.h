@@ -84,6 +84,10 @@ typedef struct spmspv_handle spmspv_handle;
 #define SPMSPV_SCHED_FORCE 8u     /* use schedule SPMSPV_SCHED_ID(opts) */
 #define SPMSPV_WITH_FEATURES 16u  /* also compute the selector features (spmspv_last_features)
                                      with a fixed schedule; costs a pass over the mask */
+#define SPMSPV_SORT_X 32u         /* sort x by index on the device first (Sec. III, cache
+                                     efficiency: more local column accesses for denser x);
+                                     a counting sort over [0, n), about n/8 + 12 nnz(x)
+                                     bytes of traffic; buffers of 16n bytes on first use */
 #define SPMSPV_SCHED_SHIFT 8
 #define SPMSPV_SCHED_OPT(s) (SPMSPV_SCHED_FORCE | ((uint32_t)(s) << SPMSPV_SCHED_SHIFT))
 #define SPMSPV_SCHED_ID(opts) (((opts) >> SPMSPV_SCHED_SHIFT) & 0xFFu)
@@ -135,7 +139,9 @@ int spmspv_destroy(spmspv_handle* h);
  *   mask        device uint32[ceil(m/32)] bitmap (bit i%32 of word i/32), or
  *               NULL for no mask.  Without SPMSPV_MASK_COMPLEMENT row i is kept
  *               only where its bit is 1; with it only where its bit is 0.
- *   opts        SPMSPV_MASK_COMPLEMENT | SPMSPV_SORTED_OUT | schedule bits.
+ *   opts        SPMSPV_MASK_COMPLEMENT | SPMSPV_SORTED_OUT | SPMSPV_SORT_X |
+ *               schedule bits.  With SPMSPV_SORT_X, repeated or out-of-range x
+ *               ids also set SPMSPV_DEV_INDEX.
  *   y_idx       device int32[y_capacity] out.
  *   y_val       device float[]/int32[y_capacity] out (ignored for OR_AND_BOOL).
  *   y_capacity  entries available in y_idx/y_val.  min(m, nnz(A)) always

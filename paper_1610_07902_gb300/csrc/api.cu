@@ -458,6 +458,7 @@ int spmspv_destroy(spmspv_handle* h) {
   release_cc(h);
   release_mis(h);
   release_mcm(h);
+  release_sortx(h);
   release_tune(h);
   release_extras(h);
   cudaFree(h->rowidx_k2);
@@ -493,6 +494,11 @@ int spmspv_run(spmspv_handle* h, int semiring, const int32_t* x_idx, const void*
     return e == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "memset nnz_y");
   }
   h->last_empty = 0;
+  if ((opts & SPMSPV_SORT_X) && nnz_x > 1) {
+    if ((rc = sort_x(h, x_idx, (const uint32_t*)x_val, nnz_x, s)) != SPMSPV_OK) return rc;
+    x_idx = h->sx_idx;
+    x_val = x_val ? (const void*)h->sx_val : nullptr;
+  }
   const int mask_comp = (opts & SPMSPV_MASK_COMPLEMENT) ? 1 : 0;
   if (opts & SPMSPV_SCHED_AUTO) {
     if (!h->sel_ready) return fail(SPMSPV_ERR_STATE, "no selector weights loaded or trained");

@@ -81,6 +81,13 @@ struct spmspv_handle {
   uint32_t* mcm_visited;
   int32_t* mcm_cnt;
   void* mcm_graph[SPMSPV_NUM_SCHEDULES / 2];
+  // presort of x (SPMSPV_SORT_X, first use): id bitmap (kept zero between
+  // calls), parked values, the sorted x, look-back words + ticket
+  uint32_t* sx_bits;
+  uint32_t* sx_dense;
+  int32_t* sx_idx;
+  uint32_t* sx_val;
+  unsigned long long* sx_status;
   int32_t* bfs_count;   // [4] device counters
 };
 
@@ -104,6 +111,9 @@ void release_batch(spmspv_handle* h);
 void release_cc(spmspv_handle* h);
 void release_mis(spmspv_handle* h);
 void release_mcm(spmspv_handle* h);
+// Sorts x by index into h->sx_idx / h->sx_val (sortx.cu); x_val may be NULL.
+int sort_x(spmspv_handle* h, const int32_t* x_idx, const uint32_t* x_val, int32_t f, cudaStream_t s);
+void release_sortx(spmspv_handle* h);
 // Graph loops (graph_loop.cu).  build_while_graph captures `body` (given the
 // loop's condition handle and the capture stream) as the body of a WHILE node
 // whose condition starts at 1, and instantiates the graph.

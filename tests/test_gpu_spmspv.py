@@ -25,7 +25,7 @@ def lib():
 
 
 def _run(lib, A, Ad, semiring, x_idx, x_val, mask_u8=None, complement=True, sched=None,
-         cap=None, auto=False):
+         cap=None, auto=False, extra_opts=0):
     torch, S = lib
     dev = "cuda"
     xi = torch.from_numpy(np.ascontiguousarray(x_idx, np.int32)).to(dev)
@@ -33,7 +33,7 @@ def _run(lib, A, Ad, semiring, x_idx, x_val, mask_u8=None, complement=True, sche
     if x_val is not None:
         xv = torch.from_numpy(np.ascontiguousarray(x_val)).to(dev)
     mask = None
-    opts = S.SPMSPV_SORTED_OUT
+    opts = S.SPMSPV_SORTED_OUT | extra_opts
     if mask_u8 is not None:
         mask = torch.from_numpy(mask_bits(mask_u8).view(np.int32)).to(dev)
         if complement:
@@ -47,11 +47,12 @@ def _run(lib, A, Ad, semiring, x_idx, x_val, mask_u8=None, complement=True, sche
     return (yi.cpu().numpy(), None if yv is None else yv.cpu().numpy(), k, st)
 
 
-def _check(lib, A, Ad, semiring, x_idx, xf, mask_u8=None, complement=True, sched=None):
+def _check(lib, A, Ad, semiring, x_idx, xf, mask_u8=None, complement=True, sched=None, extra_opts=0):
     xv = x_values(semiring, x_idx, xf)
     ref = oracle.spmspv(A.m, A.colptr, A.rowidx, A.val, SEMIRING_TO_ORACLE[semiring], x_idx,
                         xv, mask_u8, complement)
-    yi, yv, k, st = _run(lib, A, Ad, semiring, x_idx, xv, mask_u8, complement, sched)
+    yi, yv, k, st = _run(lib, A, Ad, semiring, x_idx, xv, mask_u8, complement, sched,
+                         extra_opts=extra_opts)
     assert st == 0, "device status %d" % st
     assert k == ref.idx.shape[0]
     worst = compare(semiring, ref, yi, yv)
@@ -286,6 +287,45 @@ def test_many_calls_on_one_handle(lib):
         x_idx, xf = synth.frontier(A.n, f, seed=it)
         mask = (rng.random(A.m) < 0.2).astype(np.uint8) if it % 3 == 0 else None
         _check(lib, A, Ad, semiring, x_idx, xf, mask, True, sched)
+    Ad.close()
+
+
+@pytest.fixture(scope="module")
+def rmat18(lib):
+    return synth.rmat(18, seed=3)
+
+
+@pytest.mark.parametrize("f", [2, 3, 1000, 65537, 200000])
+@pytest.mark.parametrize("semiring", [0, 1, 2])
+def test_presorted_x(lib, rmat18, f, semiring):
+    """SPMSPV_SORT_X: x in random order is sorted on the device (a counting
+    sort over 32 tiles of 8,192 ids here) before the product; y must equal the
+    reference's, unmasked and masked, push and pull."""
+    torch, S = lib
+    A = rmat18
+    Ad = _dev_matrix(lib, A, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
+    x_idx, xf = synth.frontier(A.n, f, seed=f, stream=2)
+    assert f < 3 or (np.diff(x_idx) < 0).any()  # really unsorted
+    _check(lib, A, Ad, semiring, x_idx, xf, extra_opts=S.SPMSPV_SORT_X)
+    mask = (np.random.default_rng(f).random(A.m) < 0.3).astype(np.uint8)
+    _check(lib, A, Ad, semiring, x_idx, xf, mask, True, sched=2, extra_opts=S.SPMSPV_SORT_X)
+    if semiring != 0:  # the pull form needs A == A^T with values for (+,*)
+        _check(lib, A, Ad, semiring, x_idx, xf, mask, False, sched=8, extra_opts=S.SPMSPV_SORT_X)
+    Ad.close()
+
+
+def test_presort_flags_bad_ids(lib, rmat18):
+    torch, S = lib
+    A = rmat18
+    Ad = _dev_matrix(lib, A)
+    y = torch.empty(A.m, dtype=torch.int32, device="cuda")
+    nnz = torch.zeros(1, dtype=torch.int32, device="cuda")
+    bad = torch.tensor([3, A.n + 5, 17], dtype=torch.int32, device="cuda")
+    S.spmspv_run(Ad.handle, 2, bad, None, 3, None, S.SPMSPV_SORT_X, y, None, A.m, nnz)
+    assert S.spmspv_device_status(Ad.handle) & S.SPMSPV_DEV_INDEX
+    # the bitmap was cleared behind the sort: the next sorted call is clean
+    x_idx, xf = synth.frontier(A.n, 5000, seed=9)
+    _check(lib, A, Ad, 0, x_idx, xf, extra_opts=S.SPMSPV_SORT_X)
     Ad.close()
 
 
