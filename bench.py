@@ -394,6 +394,63 @@ def bench_sorted_x(S, A, Ad, dev, stream, flush, y_idx, y_val, cap, nnz_y):
     return out
 
 
+def bench_dcsc(S, dev, stream, flush):
+    """A hypersparse block of the kind a 2D distribution hands each process
+    (Sec. II-C): m = 2^22 rows, n = 2^25 columns of which nzc = 2^20 hold
+    entries (16 on average), stored as DCSC and, for comparison, as CSC.  x
+    with 10^6 ids uniform over all n columns (about 3% stored) and with 10^5
+    ids among the stored columns.  Median of 9 calls, L2 flushed before each."""
+    import torch
+    m, n, nzc = 1 << 22, 1 << 25, 1 << 20
+    rng = np.random.default_rng(17)
+    cols = np.sort(rng.choice(n, size=nzc, replace=False)).astype(np.int64)
+    d = rng.integers(1, 32, size=nzc)
+    key = np.unique(np.repeat(cols, d) * m + rng.integers(0, m, size=int(d.sum())))
+    col, row = key // m, (key % m).astype(np.int32)
+    del key
+    deg = np.bincount(col, minlength=n)
+    del col
+    colptr = np.concatenate([[0], np.cumsum(deg)]).astype(np.int32)
+    jc = np.flatnonzero(deg > 0).astype(np.int32)
+    cp = np.concatenate([[0], np.cumsum(deg[jc])]).astype(np.int32)
+    val = rng.random(row.shape[0], dtype=np.float32)
+    nnz = int(row.shape[0])
+    Ac = S.CscMatrix(m, n, colptr, row, val, device=dev)
+    Ad = S.DcscMatrix(m, n, jc, cp, row, val, device=dev)
+    cap = m
+    yi = torch.empty(cap, dtype=torch.int32, device=dev)
+    yv = torch.empty(cap, dtype=torch.float32, device=dev)
+    nz = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = {"m": m, "n": n, "nzc": int(jc.shape[0]), "nnz": nnz,
+           "column_index_bytes": {"csc_colptr": 4 * (n + 1),
+                                  "dcsc_jc_cp_aux": 4 * (2 * int(jc.shape[0]) + 1) + 4 * (int(jc.shape[0]) + 2)}}
+    for name, xi_, f in (("uniform_over_n", rng.choice(n, size=1_000_000, replace=False), 1_000_000),
+                         ("stored_columns", rng.choice(jc, size=100_000, replace=False), 100_000)):
+        xi = torch.from_numpy(xi_.astype(np.int32)).to(dev)
+        xv = torch.from_numpy(rng.random(f, dtype=np.float32)).to(dev)
+        res = {}
+        ys = []
+        for hname, H in (("csc", Ac), ("dcsc", Ad)):
+            run = lambda: S.spmspv_run(H.handle, S.SPMSPV_PLUS_TIMES_F32, xi, xv, f, None,
+                                       S.SPMSPV_SORTED_OUT, yi, yv, cap, nz, stream)
+            run()
+            times = []
+            for _ in range(9):
+                flush.zero_()
+                times.append(_events_ms(run, stream, 1))
+            res[hname + "_ms"] = float(np.median(times))
+            res["products"] = S.spmspv_last_work(H.handle)
+            k = int(nz.item())
+            ys.append((yi[:k].cpu().numpy().copy(), yv[:k].cpu().numpy().copy()))
+            res[hname + "_status"] = S.spmspv_device_status(H.handle)
+        res["same_y"] = bool(np.array_equal(ys[0][0], ys[1][0]) and
+                             np.allclose(ys[0][1], ys[1][1], rtol=1e-5, atol=0))
+        out[name] = res
+    Ac.close()
+    Ad.close()
+    return out
+
+
 def bench_batched(S, dev, stream, B=256):
     """256 frontiers on R-MAT s20 in one batched launch (autotuned) against
     256 sequential plain calls; multi-source BFS and ACL the same way."""
@@ -727,6 +784,7 @@ def main():
                                        [128 * 65536 + 128 * 256 + 128], params, pt_frontiers=True)
         del G
         extras["batched"] = bench_batched(S, dev, stream)
+        extras["dcsc_hypersparse"] = bench_dcsc(S, dev, stream, flush)
         extras["selector_weights"] = "trained" if params is not None else "absent (AUTO not run)"
 
     line = {

@@ -125,6 +125,24 @@ int spmspv_create_csc(spmspv_handle** h, int32_t m, int32_t n, int64_t nnz,
                       const int32_t* colptr, const int32_t* rowidx, const void* val,
                       int val_type, uint32_t flags);
 
+/*
+ * Same, for a matrix in DCSC (Sec. II-C): only the nzc columns that hold an
+ * entry are stored.  jc: device int32[nzc], their column ids, strictly
+ * ascending in [0, n); cp: device int32[nzc+1], cp[0] = 0, non-decreasing,
+ * cp[nzc] = nnz, the entries of stored column p being rowidx/val[cp[p] ..
+ * cp[p+1]).  Storage is O(nzc + nnz): the library adds an auxiliary column
+ * index of about nzc entries (aux[k] = the first p with jc[p] >= k * 2^s,
+ * 2^s about n / nzc) that finds a column in expected constant time, and
+ * sizes its per-call x compaction by min(n, nzc).  jc and cp are checked on
+ * the host at create time (SPMSPV_ERR_ARG).  x may name any column in [0, n);
+ * columns not stored contribute nothing.  The pull direction (which needs the
+ * CSC to double as CSR) and spmspv_acl (which reads degrees from column
+ * pointers) are not available on a DCSC handle; everything else is.
+ */
+int spmspv_create_dcsc(spmspv_handle** h, int32_t m, int32_t n, int64_t nnz, int32_t nzc,
+                       const int32_t* jc, const int32_t* cp, const int32_t* rowidx, const void* val,
+                       int val_type, uint32_t flags);
+
 /* Release the handle and its workspace (synchronises the device). */
 int spmspv_destroy(spmspv_handle* h);
 

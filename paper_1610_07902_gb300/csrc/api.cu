@@ -253,9 +253,53 @@ extern "C" {
 
 const char* spmspv_last_error(void) { return g_last_error.c_str(); }
 
-int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
-                      const int32_t* colptr, const int32_t* rowidx, const void* val, int val_type,
-                      uint32_t flags) {
+}  // extern "C"
+
+namespace spmspv {
+
+// DCSC set-up (Sec. II-C): checks the stored column ids and pointers and
+// builds the auxiliary column index on the host, O(nzc + n / 2^aux_shift),
+// then copies it to the device.
+static int build_dcsc_index(spmspv_handle* h, int32_t n, int64_t nnz, int32_t nzc, const int32_t* jc,
+                            const int32_t* cp) {
+  std::vector<int32_t> hjc((size_t)nzc), hcp((size_t)nzc + 1);
+  cudaError_t e = cudaMemcpy(hjc.data(), jc, sizeof(int32_t) * (size_t)nzc, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(hcp.data(), cp, sizeof(int32_t) * ((size_t)nzc + 1), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "DCSC arrays copy");
+  for (int32_t p = 0; p < nzc; ++p) {
+    if (hjc[p] < 0 || hjc[p] >= n) return fail(SPMSPV_ERR_ARG, "jc[%d] = %d outside [0, n)", p, hjc[p]);
+    if (p > 0 && hjc[p] <= hjc[p - 1]) return fail(SPMSPV_ERR_ARG, "jc is not strictly ascending at %d", p);
+    if (hcp[p + 1] < hcp[p]) return fail(SPMSPV_ERR_ARG, "cp decreases at %d", p);
+  }
+  if (hcp[0] != 0 || (int64_t)hcp[nzc] != nnz) return fail(SPMSPV_ERR_ARG, "cp must run from 0 to nnz");
+  // chunks of 2^s column ids, about as many as stored columns
+  int s = 0;
+  while (((int64_t)n >> s) > (int64_t)(nzc > 0 ? nzc : 1)) ++s;
+  const int64_t naux = (((int64_t)n - 1) >> s) + 2;
+  std::vector<int32_t> haux((size_t)naux);
+  int32_t p = 0;
+  for (int64_t k = 0; k < naux; ++k) {
+    const int64_t first = k << s;
+    while (p < nzc && (int64_t)hjc[p] < first) ++p;
+    haux[(size_t)k] = p;
+  }
+  if ((e = cudaMalloc(&h->dcsc_aux, sizeof(int32_t) * (size_t)naux)) != cudaSuccess)
+    return fail(SPMSPV_ERR_OOM, "DCSC index: %s", cudaGetErrorString(e));
+  if ((e = cudaMemcpy(h->dcsc_aux, haux.data(), sizeof(int32_t) * (size_t)naux, cudaMemcpyHostToDevice)) !=
+      cudaSuccess)
+    return cuda_fail(e, "DCSC index copy");
+  h->A.jc = jc;
+  h->A.aux = h->dcsc_aux;
+  h->A.nzc = nzc;
+  h->A.aux_shift = s;
+  return SPMSPV_OK;
+}
+
+// Handle creation for CSC (jc == NULL) and DCSC (jc, nzc; colptr = the
+// pointers of the stored columns).
+static int create_impl(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz, const int32_t* colptr,
+                       const int32_t* rowidx, const void* val, int val_type, uint32_t flags,
+                       const int32_t* jc, int32_t nzc) {
   if (!out) return fail(SPMSPV_ERR_ARG, "h is NULL");
   *out = nullptr;
   if (m < 1 || n < 1) return fail(SPMSPV_ERR_ARG, "m and n must be >= 1 (got %d, %d)", m, n);
@@ -281,6 +325,14 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
   h->A.rowidx = rowidx;
   h->A.val = val_type == SPMSPV_VAL_F32 ? (const float*)val : nullptr;
   h->flags = flags;
+  if (jc) {
+    int rc0 = build_dcsc_index(h, n, nnz, nzc, jc, colptr);
+    if (rc0 != SPMSPV_OK) {
+      cudaFree(h->dcsc_aux);
+      delete h;
+      return rc0;
+    }
+  }
 
   // bucket row widths: the widest gives about 128 buckets, the schedule
   // chooses among three widths
@@ -290,6 +342,7 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
   h->lwb_lo = lwb_hi - 2;
   h->nb_fine = (int)(((int64_t)m + (1 << h->lwb_lo) - 1) >> h->lwb_lo);
   if (h->nb_fine > NB_K2_MAX) {
+    cudaFree(h->dcsc_aux);
     delete h;
     return fail(SPMSPV_ERR_UNSUPPORTED, "too many row-range buckets (%d)", h->nb_fine);
   }
@@ -304,9 +357,10 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
     return o;
   };
   size_t o_st = take(sizeof(DevState));
-  size_t o_cw = take(sizeof(int32_t) * ((size_t)n + 1));
-  size_t o_cb = take(sizeof(int32_t) * (size_t)n);
-  size_t o_cx = take(sizeof(uint32_t) * (size_t)n);
+  const size_t ncomp = (size_t)compaction_capacity(h->A);  // x entries with a non-empty column
+  size_t o_cw = take(sizeof(int32_t) * (ncomp + 1));
+  size_t o_cb = take(sizeof(int32_t) * ncomp);
+  size_t o_cx = take(sizeof(uint32_t) * ncomp);
   size_t o_tk = take(sizeof(int32_t) * (size_t)ntile_fine);
   size_t o_k1s = take(sizeof(unsigned long long) * (size_t)nt1);
   size_t o_bf = take(sizeof(int32_t) * (size_t)h->nb_fine * BFILL_STRIDE);
@@ -324,6 +378,7 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
   h->ws_bytes = off;
   cudaError_t e = cudaMalloc(&h->ws_base, h->ws_bytes);
   if (e != cudaSuccess) {
+    cudaFree(h->dcsc_aux);
     delete h;
     cudaGetLastError();
     return fail(SPMSPV_ERR_OOM, "workspace of %zu bytes: %s", off, cudaGetErrorString(e));
@@ -401,7 +456,7 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
       h->rows_sorted = u == 0;
     }
     // pull direction buffers (the CSC doubles as CSR only for a symmetric pattern)
-    if ((flags & SPMSPV_CSC_PATTERN_SYMMETRIC) && m == n) {
+    if ((flags & SPMSPV_CSC_PATTERN_SYMMETRIC) && m == n && !jc) {
       if ((e = alloc_pull_buffers(h)) != cudaSuccess) {
         rc = fail(SPMSPV_ERR_OOM, "pull buffers: %s", cudaGetErrorString(e));
         break;
@@ -438,12 +493,32 @@ int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz,
     release_extras(h);
     cudaFree(h->rowidx_k2);
     cudaFree(h->ws_base);
+    cudaFree(h->dcsc_aux);
     h->magic = 0;
     delete h;
     return rc;
   }
   *out = h;
   return SPMSPV_OK;
+}
+
+}  // namespace spmspv
+
+extern "C" {
+
+int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz, const int32_t* colptr,
+                      const int32_t* rowidx, const void* val, int val_type, uint32_t flags) {
+  return create_impl(out, m, n, nnz, colptr, rowidx, val, val_type, flags, nullptr, 0);
+}
+
+int spmspv_create_dcsc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz, int32_t nzc,
+                       const int32_t* jc, const int32_t* cp, const int32_t* rowidx, const void* val,
+                       int val_type, uint32_t flags) {
+  if (nzc < 0 || nzc > n) return fail(SPMSPV_ERR_ARG, "nzc = %d outside [0, n]", nzc);
+  if (nzc > 0 && !jc) return fail(SPMSPV_ERR_ARG, "jc is NULL");
+  if (!cp) return fail(SPMSPV_ERR_ARG, "cp is NULL");
+  // with nzc = 0 the (never read) jc stays non-NULL so that the handle is a DCSC one
+  return create_impl(out, m, n, nnz, cp, rowidx, val, val_type, flags, jc ? jc : cp, nzc);
 }
 
 int spmspv_destroy(spmspv_handle* h) {
@@ -464,6 +539,7 @@ int spmspv_destroy(spmspv_handle* h) {
   cudaFree(h->rowidx_k2);
   cudaFree(h->sel_w);
   cudaFree(h->ws_base);
+  cudaFree(h->dcsc_aux);
   h->magic = 0;
   delete h;
   return SPMSPV_OK;

@@ -234,8 +234,12 @@ static int ensure_batch(spmspv_handle* h, int lanes, BatchState** out) {
   // one full workspace per lane, created like the parent handle
   for (int l = bs->lanes; l < lanes; ++l) {
     spmspv_handle* sub = nullptr;
-    int rc = spmspv_create_csc(&sub, h->A.m, h->A.n, h->A.nnz, h->A.colptr, h->A.rowidx, h->A.val,
-                               h->A.val ? SPMSPV_VAL_F32 : SPMSPV_VAL_NONE, h->flags & ~SPMSPV_CSC_PATTERN_SYMMETRIC);
+    const int vt = h->A.val ? SPMSPV_VAL_F32 : SPMSPV_VAL_NONE;
+    const uint32_t fl = h->flags & ~SPMSPV_CSC_PATTERN_SYMMETRIC;
+    int rc = h->A.jc ? spmspv_create_dcsc(&sub, h->A.m, h->A.n, h->A.nnz, h->A.nzc, h->A.jc, h->A.colptr,
+                                          h->A.rowidx, h->A.val, vt, fl)
+                     : spmspv_create_csc(&sub, h->A.m, h->A.n, h->A.nnz, h->A.colptr, h->A.rowidx, h->A.val,
+                                         vt, fl);
     if (rc != SPMSPV_OK) return rc;
     sub->ws.job = bs->jobs + l;
     bs->sub[l] = sub;
@@ -661,6 +665,7 @@ static int acl_run(spmspv_handle* h, int32_t B, const int32_t* seeds, float alph
   int rc = check_handle(h);
   if (rc) return rc;
   if (h->A.m != h->A.n) return fail(SPMSPV_ERR_ARG, "ACL needs a square matrix");
+  if (h->A.jc) return fail(SPMSPV_ERR_UNSUPPORTED, "ACL reads vertex degrees from CSC column pointers");
   if (h->A.val) return fail(SPMSPV_ERR_ARG, "ACL uses the unweighted graph: create the handle with SPMSPV_VAL_NONE");
   if (B < 1 || !seeds || !p_out || !r_out) return fail(SPMSPV_ERR_ARG, "bad ACL arguments");
   if (!(alpha > 0.f && alpha < 1.f) || !(eps > 0.f) || max_steps < 0)

@@ -35,6 +35,7 @@ struct spmspv_handle {
   const uint32_t* k1_mask;  // mask whose bits the work scan counts (features), or NULL
   void* prof;           // std::vector<ProfileCall>* while profiling, else NULL
   int32_t* rowidx_k2;   // owned row-id copy with hub rows relabelled (NULL without hubs)
+  int32_t* dcsc_aux;    // owned auxiliary column index of a DCSC matrix (NULL for CSC)
   void* bfs_graph[SPMSPV_NUM_SCHEDULES + 1];  // cudaGraphExec_t per schedule (+ auto)
   // learned schedule selector
   int sel_ready;        // weights present

@@ -45,7 +45,8 @@ constexpr unsigned long long K1_SUM_MASK = (1ull << 31) - 1;
 
 __global__ void __launch_bounds__(K1_THREADS)
 k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int32_t* f_dev,
-             const int32_t* __restrict__ colptr, int32_t n,
+             const int32_t* __restrict__ colptr, const int32_t* __restrict__ jc,
+             const int32_t* __restrict__ aux, int aux_shift, int32_t qcap, int32_t n,
              int64_t nnz, Workspace ws, int nb_fine, int sem, int forced, int f_dir, int f_q,
              int f_lwb, int bfs_level_inc, const uint32_t* __restrict__ mask, int32_t m,
              SelArgs sel) {
@@ -146,8 +147,7 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
       if (k < f) {
         const int32_t j = jj[i];
         if (j >= 0 && j < n) {
-          c0v[i] = colptr[j];
-          c1v[i] = colptr[j + 1];
+          col_range(colptr, jc, aux, aux_shift, j, c0v[i], c1v[i]);
         } else {
           atomicOr(&st->status, ST_INDEX);
         }
@@ -186,7 +186,7 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
       if (d > 0) {
         const int32_t q = (int32_t)((run >> 31) & K1_SUM_MASK);
         const int32_t w = (int32_t)(run & K1_SUM_MASK);
-        if (q < n && (int64_t)w + d <= nnz) {
+        if (q < qcap && (int64_t)w + d <= nnz) {
           ws.cw[q] = w;
           ws.cb[q] = s_c0[k1_pad(e)];
           ws.cx[q] = s_xv[k1_pad(e)];
@@ -201,7 +201,7 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
       const unsigned long long tot = s_prefix + btot;
       int32_t fc = (int32_t)((tot >> 31) & K1_SUM_MASK);
       int32_t W = (int32_t)(tot & K1_SUM_MASK);
-      if (fc > n || (int64_t)W > nnz) {  // only with duplicate x indices
+      if (fc > qcap || (int64_t)W > nnz) {  // only with duplicate x indices
         atomicOr(&st->status, ST_INDEX);
         fc = 0;
         W = 0;
@@ -255,7 +255,8 @@ cudaError_t launch_k1(int sem, const Matrix& A, const Workspace& ws, int nb_fine
                       int grid, const Sched* forced, cudaStream_t s, const uint32_t* mask,
                       const SelArgs* sel) {
   SelArgs none{};
-  k1_work_scan<<<grid, K1_THREADS, 0, s>>>(x_idx, x_val, f, f_dev, A.colptr, A.n, A.nnz, ws, nb_fine,
+  k1_work_scan<<<grid, K1_THREADS, 0, s>>>(x_idx, x_val, f, f_dev, A.colptr, A.jc, A.aux, A.aux_shift,
+                                           compaction_capacity(A), A.n, A.nnz, ws, nb_fine,
                                            sem, forced ? forced->id + 1 : 0, forced ? forced->dir : 0,
                                            forced ? forced->q : 0, forced ? forced->lwb : 0, 0,
                                            mask, A.m, sel ? *sel : none);
@@ -842,7 +843,7 @@ cudaError_t launch_rows_unsorted(const Matrix& A, int32_t* unsorted, cudaStream_
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  k_rows_unsorted<<<sms * 8, 256, 0, s>>>(A.colptr, A.rowidx, A.n, unsorted);
+  k_rows_unsorted<<<sms * 8, 256, 0, s>>>(A.colptr, A.rowidx, A.jc ? A.nzc : A.n, unsorted);
   return cudaGetLastError();
 }
 
@@ -937,7 +938,8 @@ cudaError_t launch_k1_bfs(const Matrix& A, const Workspace& ws, int nb_fine, con
                           const uint32_t* mask, const SelArgs* sel) {
   SelArgs none{};
   k1_work_scan<<<grid, K1_THREADS, 0, s>>>(x_idx, reinterpret_cast<const uint32_t*>(x_idx), 0,
-                                           f_dev, A.colptr, A.n, A.nnz, ws, nb_fine, kMinSelect2nd,
+                                           f_dev, A.colptr, A.jc, A.aux, A.aux_shift,
+                                           compaction_capacity(A), A.n, A.nnz, ws, nb_fine, kMinSelect2nd,
                                            sc ? sc->id + 1 : 0, sc ? sc->dir : 0, sc ? sc->q : 0,
                                            sc ? sc->lwb : 0, 1, mask, A.m, sel ? *sel : none);
   return cudaGetLastError();

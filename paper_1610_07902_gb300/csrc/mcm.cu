@@ -139,8 +139,7 @@ __global__ void k_mcm_augment(DevState* st, int32_t m, int32_t n, const int32_t*
 
 // Start of the next phase: clear the visited rows, the free non-empty
 // columns become the roots and the frontier.
-__global__ void k_mcm_new_phase(int32_t m, int32_t n, const int32_t* __restrict__ colptr,
-                                const DevState* __restrict__ st, int32_t* __restrict__ x_idx,
+__global__ void k_mcm_new_phase(int32_t m, int32_t n, Matrix A, const DevState* __restrict__ st, int32_t* __restrict__ x_idx,
                                 int32_t* __restrict__ root_c, uint32_t* __restrict__ visited,
                                 int32_t* __restrict__ cnt) {
   if (cnt[1] != 0 || cnt[2] == 0) return;
@@ -151,7 +150,12 @@ __global__ void k_mcm_new_phase(int32_t m, int32_t n, const int32_t* __restrict_
   const int lane = threadIdx.x & 31;
   for (int32_t j0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; j0 < n; j0 += gridDim.x * blockDim.x) {
     const int32_t j = j0 + lane;
-    const bool root = j < n && mate_c[j] < 0 && colptr[j + 1] > colptr[j];
+    bool root = j < n && mate_c[j] < 0;
+    if (root) {
+      int32_t c0, c1;
+      col_range(A.colptr, A.jc, A.aux, A.aux_shift, j, c0, c1);
+      root = c1 > c0;
+    }
     const int32_t pos = warp_append(root, &cnt[3]);
     if (root) {
       root_c[j] = j;
@@ -202,7 +206,7 @@ static int mcm_level_launches(spmspv_handle* h, const Sched& sc, cudaGraphCondit
                                 h->mcm_leaf, h->mcm_visited, h->mcm_x2_idx, h->mcm_cnt);
   k_mcm_copy<<<g, 256, 0, s>>>(h->mcm_x2_idx, h->mcm_x_idx, h->mcm_cnt);
   k_mcm_augment<<<g, 256, 0, s>>>(h->ws.st, h->A.m, h->A.n, h->mcm_parent_r, h->mcm_leaf, h->mcm_cnt);
-  k_mcm_new_phase<<<g, 256, 0, s>>>(h->A.m, h->A.n, h->A.colptr, h->ws.st, h->mcm_x_idx, h->mcm_root_c,
+  k_mcm_new_phase<<<g, 256, 0, s>>>(h->A.m, h->A.n, h->A, h->ws.st, h->mcm_x_idx, h->mcm_root_c,
                                     h->mcm_visited, h->mcm_cnt);
   k_mcm_continue<<<1, 32, 0, s>>>(cond, h->ws.st, h->mcm_cnt, h->A.m, h->A.n);
   cudaError_t e = cudaGetLastError();

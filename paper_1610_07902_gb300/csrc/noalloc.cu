@@ -161,7 +161,7 @@ extern "C" int spmspv_run_noalloc(int32_t m, int32_t n, int64_t nnz, const int32
   const int nb_fine = (int)(((int64_t)m + (1 << lwb_lo) - 1) >> lwb_lo);
 
   unsigned char* base = d->scratch;
-  Matrix A;
+  Matrix A{};
   A.m = m;
   A.n = n;
   A.nnz = nnz;

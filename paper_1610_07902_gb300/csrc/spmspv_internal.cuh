@@ -153,12 +153,49 @@ constexpr int PULL_THREADS = 256;
 constexpr int PULL_ROWS = PULL_THREADS * 32;  // rows per pull tile: one 32-row word per thread
 
 struct Matrix {
-  int32_t m, n;
-  int64_t nnz;
-  const int32_t* colptr;
-  const int32_t* rowidx;
-  const float* val;  // NULL for a pattern matrix
+  int32_t m = 0, n = 0;
+  int64_t nnz = 0;
+  const int32_t* colptr = nullptr;  // CSC: [n+1] column pointers; DCSC: [nzc+1] pointers of the stored columns
+  const int32_t* rowidx = nullptr;
+  const float* val = nullptr;  // NULL for a pattern matrix
+  // DCSC (Sec. II-C): only the nzc columns with a stored entry are kept, with
+  // their ids in jc (ascending), plus an auxiliary index for constant
+  // expected-time column lookup: aux[k] = the first position p with
+  // jc[p] >= k << aux_shift.  jc == NULL for CSC.
+  const int32_t* jc = nullptr;
+  const int32_t* aux = nullptr;
+  int32_t nzc = 0;
+  int aux_shift = 0;
 };
+
+// [c0, c1) = the range of column j's entries in rowidx (empty when a DCSC
+// matrix does not store column j): a binary search among the stored columns
+// of j's aux chunk, which holds about one column on average.
+__device__ __forceinline__ void col_range(const int32_t* __restrict__ colptr, const int32_t* __restrict__ jc,
+                                          const int32_t* __restrict__ aux, int aux_shift, int32_t j,
+                                          int32_t& c0, int32_t& c1) {
+  if (!jc) {
+    c0 = colptr[j];
+    c1 = colptr[j + 1];
+    return;
+  }
+  const int32_t k = j >> aux_shift;
+  int32_t lo = aux[k];
+  const int32_t end = aux[k + 1];
+  int32_t hi = end;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    if (jc[mid] < j) lo = mid + 1;
+    else hi = mid;
+  }
+  if (lo < end && jc[lo] == j) {
+    c0 = colptr[lo];
+    c1 = colptr[lo + 1];
+  } else {
+    c0 = 0;
+    c1 = 0;
+  }
+}
 
 struct Sched {
   int id;    // schedule id: dir * 6 + quantum * 3 + width
@@ -166,6 +203,12 @@ struct Sched {
   int q;     // QF or 2*QF
   int lwb;   // log2 bucket width
 };
+
+// Entries the work scan's compaction (cw, cb, cx) can hold: one per x entry
+// whose column has an entry, so at most the number of stored columns.
+inline int32_t compaction_capacity(const Matrix& A) {
+  return A.jc ? (A.nzc < A.n ? A.nzc : A.n) : A.n;
+}
 
 // Launchers (kernels.cu).  All launches are asynchronous on `s`.
 cudaError_t launch_k1(int sem, const Matrix& A, const Workspace& ws, int nb_fine,

@@ -127,6 +127,8 @@ def load(build_if_missing: bool = True):
         lib.spmspv_selftest_wait_timeout.argtypes = [_P, ctypes.c_uint32, _P]
         lib.spmspv_cc.argtypes = [_P, _P, _P, ctypes.c_uint32, _P]
         lib.spmspv_mis.argtypes = [_P, _P, _P, _P, ctypes.c_uint32, _P]
+        lib.spmspv_create_dcsc.argtypes = [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                           ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int, ctypes.c_uint32]
         lib.spmspv_mcm.argtypes = [_P, _P, _P, _P, _P, ctypes.c_uint32, _P]
         lib.spmspv_profile_begin.argtypes = [_P]
         lib.spmspv_profile_end.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
@@ -314,6 +316,15 @@ def spmspv_mis(h, prio, in_set, d_nrounds=None, opts=0, stream=None):
            "spmspv_mis")
 
 
+def spmspv_create_dcsc(m, n, nnz, nzc, jc, cp, rowidx, val=None, val_type=SPMSPV_VAL_F32, flags=0):
+    """Returns an opaque handle (int) of a DCSC matrix.  jc/cp/rowidx/val are CUDA tensors."""
+    h = _P()
+    _check(load().spmspv_create_dcsc(ctypes.byref(h), int(m), int(n), int(nnz), int(nzc), _ptr(jc), _ptr(cp),
+                                     _ptr(rowidx), _ptr(val), int(val_type), int(flags)),
+           "spmspv_create_dcsc")
+    return h.value
+
+
 def spmspv_mcm(h, mate_r, mate_c, d_card=None, d_nphases=None, opts=0, stream=None):
     _check(load().spmspv_mcm(h, _ptr(mate_r), _ptr(mate_c), _ptr(d_card), _ptr(d_nphases), int(opts),
                              _stream(stream)), "spmspv_mcm")
@@ -408,3 +419,23 @@ class CscMatrix:
         k = int(nnz_y.item())
         kk = min(k, cap)
         return y_idx[:kk], (None if y_val is None else y_val[:kk]), k
+
+
+class DcscMatrix(CscMatrix):
+    """A DCSC matrix (only the columns holding entries are stored, with their
+    ids in jc) resident on the GPU plus its library handle."""
+
+    def __init__(self, m, n, jc, cp, rowidx, val=None, flags=0, device="cuda"):
+        dev = torch.device(device)
+        self.m, self.n = int(m), int(n)
+        self.flags = int(flags)
+        self.jc = torch.as_tensor(jc, dtype=torch.int32).to(dev).contiguous()
+        self.cp = torch.as_tensor(cp, dtype=torch.int32).to(dev).contiguous()
+        self.colptr = self.cp  # the device the arrays live on, for the shared helpers
+        self.rowidx = torch.as_tensor(rowidx, dtype=torch.int32).to(dev).contiguous()
+        self.val = None if val is None else torch.as_tensor(val, dtype=torch.float32).to(dev).contiguous()
+        self.nnz = int(self.rowidx.numel())
+        self.nzc = int(self.jc.numel())
+        self.handle = spmspv_create_dcsc(self.m, self.n, self.nnz, self.nzc, self.jc, self.cp, self.rowidx,
+                                         self.val, SPMSPV_VAL_NONE if self.val is None else SPMSPV_VAL_F32,
+                                         flags)
