@@ -588,6 +588,7 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
   uint32_t* occ = k3_smem + wb;
   const uint32_t ident = sr_identity<SEM>();
   const int wpt = nw > K3_THREADS ? nw / K3_THREADS : 1;
+  const bool or_always = wb >= (1 << 15);
   const int32_t lvl = BFS ? (ws.job ? ws.job->lvl : st->level) : 0;
   int32_t* const level = BFS ? (ws.job ? ws.job->level : st->bfs_level) : nullptr;
   int32_t* const parent = BFS ? (ws.job ? ws.job->parent : st->bfs_parent) : nullptr;
@@ -682,7 +683,9 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
               if (e < a0 || e >= a1) continue;
               const uint32_t rr = ((j & 1) ? (rw[j >> 1] >> 16) : (rw[j >> 1] & 0xffffu)) & wmask;
               const uint32_t bit = 1u << (rr & 31);
-              if (!(occ[rr >> 5] & bit)) atomicOr(occ + (rr >> 5), bit);
+              // with one CTA per SM (the 128 KB SPA of 32768-row buckets) the
+              // dependent test costs more than the extra shared OR it saves
+              if (or_always || !(occ[rr >> 5] & bit)) atomicOr(occ + (rr >> 5), bit);
               spa_apply<SEM>(spa, rr, vw[j]);
             }
           }
