@@ -187,6 +187,34 @@ def test_edge_cases(lib):
     Ad.close()
 
 
+@pytest.mark.parametrize("semiring", [0, 1, 2])
+def test_largest_row_count(lib, semiring):
+    """m = 2^26, the most rows the 16-bit bucket offsets allow (8192 fine
+    buckets of 8192 rows, 2048 buckets at the widest width): rows spread over
+    the whole range, the first and the last row included; one more row is
+    refused."""
+    torch, S = lib
+    m, n = 1 << 26, 2000
+    rng = np.random.default_rng(26)
+    cols = [np.unique(rng.integers(0, m, size=50)) for _ in range(n)]
+    cols[0] = np.unique(np.concatenate([cols[0], [0, m - 1]]))
+    cols[n - 1] = np.unique(np.concatenate([cols[n - 1], [m - 1, m - 2]]))
+    colptr = np.concatenate([[0], np.cumsum([c.shape[0] for c in cols])]).astype(np.int32)
+    rowidx = np.concatenate(cols).astype(np.int32)
+    val = rng.random(rowidx.shape[0], dtype=np.float32)
+    from types import SimpleNamespace
+    A = SimpleNamespace(m=m, n=n, colptr=colptr, rowidx=rowidx, val=val, nnz=rowidx.shape[0])
+    Ad = _dev_matrix(lib, A)
+    x_all = np.arange(n, dtype=np.int32)
+    _check(lib, A, Ad, semiring, x_all, rng.random(n, dtype=np.float32), sched=5)
+    x_half = rng.permutation(n)[: n // 2].astype(np.int32)
+    _check(lib, A, Ad, semiring, x_half, rng.random(x_half.shape[0], dtype=np.float32), sched=0)
+    Ad.close()
+    with pytest.raises(S.SpmspvError) as e:
+        S.CscMatrix(m + 1, n, colptr, rowidx, val)
+    assert e.value.code == S.SPMSPV_ERR_UNSUPPORTED
+
+
 def test_capacity_overflow_reports_size_and_stays_in_bounds(lib):
     torch, S = lib
     A = synth.rmat(12, seed=1)
