@@ -44,6 +44,23 @@ K2_TRAFFIC_SOURCE = ("ncu full capture of the same K2 (commit 73e43e3), R-MAT s2
                      "scaled by products")
 
 
+NOMINAL_HBM_GBS = 7900.0  # nominal HBM3e bandwidth of the part, a second denominator
+
+
+def host_cpu():
+    """Host threads and CPU model (for the oracle baseline)."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return os.cpu_count(), model
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -121,15 +138,19 @@ def time_oracle(A, x_idx, x_val, budget_s=10.0):
     """The oracle as it stands, single-threaded, on a bounded sample."""
     import oracle
     W_total, t_total, calls = 0, 0.0, 0
+    per_call = []
     while t_total < budget_s or calls == 0:
         t0 = time.perf_counter()
         r = oracle.spmspv(A.m, A.colptr, A.rowidx, A.val, oracle.PLUS_TIMES, x_idx, x_val,
                           with_absum=False)
-        t_total += time.perf_counter() - t0
+        dt = time.perf_counter() - t0
+        t_total += dt
+        per_call.append(dt)
         W_total += r.nmult
         calls += 1
         if calls >= 20:
             break
+    time_oracle.median_s = float(np.median(per_call))
     return W_total / t_total / 1e9, calls, t_total
 
 
@@ -187,6 +208,7 @@ def bench_bfs(S, A, dev, stream, name, sources, params, pt_frontiers=False):
         S.spmspv_selector_set(Ad.handle, params)
     t_fixed = t_auto = 0.0
     work = 0
+    reached = 0
     levels = []
     same = True
     for src in sources:
@@ -195,13 +217,21 @@ def bench_bfs(S, A, dev, stream, name, sources, params, pt_frontiers=False):
         t_fixed += _events_ms(lambda: run(fixed, level, parent), stream, 2)
         levels.append(int(nl.item()))
         work += int(deg[level >= 0].sum().item())
+        reached += int((level >= 0).sum().item())
         if params is not None:
             run(S.SPMSPV_SCHED_AUTO, level2, parent2)
             t_auto += _events_ms(lambda: run(S.SPMSPV_SCHED_AUTO, level2, parent2), stream, 2)
             same &= bool(torch.equal(level, level2) and torch.equal(parent, parent2))
+    # compulsory bytes of the (select2nd, min) searches, without the mask reads:
+    # every reached vertex is one x entry (8 B) with two column pointers (8 B),
+    # one y entry (8 B) and a level and a parent (8 B); 4 B of row id per product
+    bfs_bytes = 32 * reached + 4 * work
+    peak, _ = load_peaks()
     out = {"graph": name, "n": A.n, "nnz": A.nnz, "sources": len(sources),
            "levels_max": max(levels), "products": work, "default_schedule": default,
-           "fixed_ms": t_fixed, "fixed_gteps": work / (t_fixed * 1e-3) / 1e9}
+           "fixed_ms": t_fixed, "fixed_gteps": work / (t_fixed * 1e-3) / 1e9,
+           "compulsory_bytes_min_semiring": bfs_bytes,
+           "fixed_path_frac": bfs_bytes / (t_fixed * 1e-3) / 1e9 / peak}
     if params is not None:
         out.update({"auto_ms": t_auto, "auto_gteps": work / (t_auto * 1e-3) / 1e9,
                     "auto_speedup": t_fixed / t_auto, "identical_results": same})
@@ -258,6 +288,58 @@ def bench_bfs(S, A, dev, stream, name, sources, params, pt_frontiers=False):
         out["plus_times_per_frontier"].update({
             "batched_ms": tb, "batched_gteps": pw / (tb * 1e-3) / 1e9, "batched_speedup": t / tb,
             "batched_lanes": tuned[0], "batched_schedule": tuned[1], "batched_identical_index_sets": same})
+    Ad.close()
+    return out
+
+
+def graph_us_per_call(call, stream, reps=100):
+    """GPU time per call with the host out of the way: `reps` calls captured
+    into one CUDA graph (call(stream) launches on the capture stream), the
+    graph replayed and timed with events.  None if the capture fails."""
+    import torch
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            cs = torch.cuda.current_stream()
+            for _ in range(reps):
+                call(cs)
+        g.replay()
+        torch.cuda.synchronize()
+        t = _events_ms(g.replay, stream, 3)
+        del g
+        return 1e3 * t / reps
+    except Exception:  # capture not possible here: report the host-launched figure only
+        torch.cuda.synchronize()
+        return None
+
+
+def bench_er(S, dev, stream):
+    """The Sec. II-A model: Erdos-Renyi m = n = 65,536 with 16/65,536 density
+    (directed, self loops allowed, values uniform(0,1), seed 1); x of 655
+    entries (seed 1 stream 2).  Latency-bound: microseconds per call and
+    GTEPS, back-to-back host-launched calls (the whole problem sits in L2)."""
+    import torch
+    import synth
+    A = synth.erdos_renyi(65536, 16.0, seed=1)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val, device=dev)
+    xi_, xv_ = synth.frontier(A.n, 655, seed=1, stream=2)
+    xi, xv = torch.from_numpy(xi_).to(dev), torch.from_numpy(xv_).to(dev)
+    cap = min(A.m, A.nnz)
+    yi = torch.empty(cap, dtype=torch.int32, device=dev)
+    yv = torch.empty(cap, dtype=torch.float32, device=dev)
+    nz = torch.zeros(1, dtype=torch.int32, device=dev)
+    run = lambda: S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, xi, xv, 655, None, S.SPMSPV_SORTED_OUT,
+                               yi, yv, cap, nz, stream)
+    for _ in range(10):
+        run()
+    reps = 500
+    t = _events_ms(lambda: [run() for _ in range(reps)], stream, 1) / reps
+    W = S.spmspv_last_work(Ad.handle)
+    tg = graph_us_per_call(lambda cs: S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, xi, xv, 655, None,
+                                                    S.SPMSPV_SORTED_OUT, yi, yv, cap, nz, cs), stream)
+    out = {"m": A.m, "nnz": int(A.nnz), "nnz_x": 655, "products": W, "nnz_y": int(nz.item()),
+           "us_per_call": 1e3 * t, "gteps": W / (t * 1e-3) / 1e9, "graph_us_per_call": tg,
+           "status": S.spmspv_device_status(Ad.handle)}
     Ad.close()
     return out
 
@@ -688,7 +770,9 @@ def main():
         step()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
-    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms_median = float(np.median(step_ms))
+    t_ms = sum(step_ms)
     t_ms, gteps = replica_summary(t_ms, W, args.steps, world, dev)
     ms_per_step = t_ms / args.steps
     if args.kernels_only:
@@ -749,8 +833,11 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, calls, tt = time_oracle(A, x_idx, x_val)
+        nproc, model = host_cpu()
         cpu = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-               "sample": "%d full calls of the workload (%.1f s)" % (calls, tt)}
+               "sample": "%d full calls of the workload (%.1f s)" % (calls, tt),
+               "median_ms_per_call": 1e3 * time_oracle.median_s, "host_threads": nproc,
+               "host_cpu": model}
 
     extras = {}
     if rank == 0 and not args.no_extras:
@@ -767,10 +854,16 @@ def main():
             reps = 200
             tms = _events_ms(lambda: [run() for _ in range(reps)], stream, 1) / reps
             ws_ = S.spmspv_last_work(Ad.handle)
-            sweep["nnz_x_%d" % fs] = {"us_per_call": 1e3 * tms, "products": ws_,
-                                       "gteps": ws_ / (tms * 1e-3) / 1e9}
-        sweep["note"] = "back-to-back host-launched calls, L2 not flushed between them"
+            cb = compulsory_bytes(fs, ws_, int(nnz_y.item()))
+            tg = graph_us_per_call(lambda cs: S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, dxi, dxv, fs,
+                                                            None, opts, y_idx, y_val, cap, nnz_y, cs), stream)
+            sweep["nnz_x_%d" % fs] = {"us_per_call": 1e3 * tms, "graph_us_per_call": tg, "products": ws_,
+                                       "gteps": ws_ / (tms * 1e-3) / 1e9, "compulsory_bytes": cb,
+                                       "path_frac": cb / (tms * 1e-3) / 1e9 / peak}
+        sweep["note"] = ("back-to-back host-launched calls, L2 not flushed between them; "
+                         "graph_us_per_call: 100 calls captured in one CUDA graph and replayed")
         extras["sweep_rmat"] = sweep
+        extras["er_spmspv"] = bench_er(S, dev, stream)
         extras["sorted_x_rmat"] = bench_sorted_x(S, A, Ad, dev, stream, flush, y_idx, y_val, cap, nnz_y)
         params = selector_params()
         extras["bfs_rmat"] = bench_bfs(S, A, dev, stream, "rmat s%d ef16 seed 1" % args.scale,
@@ -789,7 +882,8 @@ def main():
 
     line = {
         "metric": METRIC, "value": gteps, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "ms_median": ms_median,
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload, "graph": "rmat s%d ef16 symmetrised seed 1" % args.scale,
                    "m": A.m, "nnz": A.nnz, "nnz_x": F_, "products": W, "nnz_y": ny,
@@ -802,9 +896,10 @@ def main():
                                  else None),
                      "traffic_unit": "bytes per launch", "traffic_source": K2_TRAFFIC_SOURCE,
                      "peak_kind": peak_kind, "alg_bytes_per_launch": alg[dom],
-                     "avg_launch_ms": stage_avg[dom]},
+                     "avg_launch_ms": stage_avg[dom], "frac_nominal": achieved / NOMINAL_HBM_GBS},
         "path_roofline": {"compulsory_bytes": path_bytes, "achieved": path_gbs, "peak": peak,
-                          "unit": "GB/s", "frac": path_gbs / peak, "peak_kind": peak_kind},
+                          "unit": "GB/s", "frac": path_gbs / peak, "peak_kind": peak_kind,
+                          "frac_nominal": path_gbs / NOMINAL_HBM_GBS},
         "stages_ms": {names[s]: stage_avg[s] for s in names},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_gteps, "unit": "GTEPS", "h2d_bytes_per_step": 8 * F_,
