@@ -57,3 +57,16 @@ def test_cc_rejects_directed_handles(lib):
     with pytest.raises(S.SpmspvError):
         S.spmspv_cc(Ad.handle, labels)
     Ad.close()
+
+
+def test_cc_headline_graph(lib):
+    """The headline R-MAT s22 graph, bit for bit against the reference."""
+    torch, S = lib
+    A = synth.rmat(22, seed=1, values=False)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
+    labels = torch.empty(A.n, dtype=torch.int32, device="cuda")
+    S.spmspv_cc(Ad.handle, labels)
+    ref, k = oracle.cc(A.colptr, A.rowidx)
+    np.testing.assert_array_equal(labels.cpu().numpy(), ref)
+    assert S.spmspv_device_status(Ad.handle) == 0
+    Ad.close()

@@ -116,3 +116,14 @@ def test_mis_rejects_bad_calls(lib):
     with pytest.raises(S.SpmspvError):
         S.spmspv_mis(Ad.handle, prio, in_set, None, S.SPMSPV_SCHED_OPT(7))
     Ad.close()
+
+
+def test_mis_headline_graph(lib):
+    """The headline R-MAT s22 graph, bit for bit against the reference."""
+    torch, S = lib
+    A = synth.rmat(22, seed=1, values=False)
+    prio = np.random.default_rng(22).permutation(A.n).astype(np.int32)
+    got, _, rounds = _run(torch, S, A, prio, 0)
+    ref, size = oracle.mis(A.colptr, A.rowidx, prio)
+    np.testing.assert_array_equal(got, ref)
+    assert rounds >= 1
