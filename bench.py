@@ -437,7 +437,7 @@ def bench_mcm(S, A, dev, stream):
 
 
 def bench_sorted_x(S, A, Ad, dev, stream, flush, y_idx, y_val, cap, nnz_y):
-    """The sorted-versus-unsorted study of Sec. V (Fig. 2 there: x with 10K
+    """The sorted-versus-unsorted study of Sec. IV-B (Fig. 2 there: x with 10K
     and 2.5M nonzeros) on the headline matrix: x in random order, the same x
     sorted by the caller, and x in random order sorted on the device first
     (SPMSPV_SORT_X, the sort inside the timed call).  y is ascending in every

@@ -84,7 +84,7 @@ typedef struct spmspv_handle spmspv_handle;
 #define SPMSPV_SCHED_FORCE 8u     /* use schedule SPMSPV_SCHED_ID(opts) */
 #define SPMSPV_WITH_FEATURES 16u  /* also compute the selector features (spmspv_last_features)
                                      with a fixed schedule; costs a pass over the mask */
-#define SPMSPV_SORT_X 32u         /* sort x by index on the device first (Sec. III, cache
+#define SPMSPV_SORT_X 32u         /* sort x by index on the device first (Sec. III-A, cache
                                      efficiency: more local column accesses for denser x);
                                      a counting sort over [0, n), about n/8 + 12 nnz(x)
                                      bytes of traffic; buffers of 16n bytes on first use */

@@ -1,7 +1,7 @@
-// Presort of the input vector by index.  Sec. III (cache efficiency) notes
+// Presort of the input vector by index.  Sec. III-A (cache efficiency) notes
 // that sorting x beforehand makes the column accesses of Step 1 more local
 // when x is denser, since consecutive entries then touch nearby columns; the
-// experiments of Sec. V keep x and y sorted for that reason.
+// experiments of Sec. IV keep x and y sorted for that reason (Sec. IV-B).
 //
 // Indices are distinct and below n, so the sort is a counting sort over the
 // index range: one kernel sets a bit per entry in an n-bit bitmap and parks
