@@ -296,7 +296,7 @@ __device__ __forceinline__ void spa_apply(uint32_t* spa, uint32_t r, uint32_t v)
 // IT: products per thread when the host knows the work quantum (4 or 8),
 // 0 when the device decides it; MASKED: a mask may be given.
 template <int SEM, int IT, bool MASKED>
-__global__ void __launch_bounds__(K2_THREADS, 2)
+__global__ void __launch_bounds__(K2_THREADS, 3)
 k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ val, Workspace ws,
                   int lwb_lo, int nb_fine, int32_t m, int64_t nnz, const uint32_t* mask,
                   int mask_comp, int only_push) {
@@ -306,10 +306,12 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
   __shared__ int32_t s_kept;
 
   unsigned char* p = k2_smem_raw;
-  uint2* stage = (uint2*)p; p += sizeof(uint2) * QMAX;
-  uint32_t* hbits = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX / 32);  // entry starts of the tile
+  // the staged products of a tile share their bytes with the tile's x entries
+  // (the entries are no longer read once the products are counted)
+  uint2* stage = (uint2*)p;
   int32_t* kbase = (int32_t*)p; p += sizeof(int32_t) * (QMAX + 1);
   uint32_t* kx = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX + 1);
+  uint32_t* hbits = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX / 32);  // entry starts of the tile
   int32_t* hist = (int32_t*)p; p += sizeof(int32_t) * nb_fine;   // counts, then stage offsets
   int32_t* gd = (int32_t*)p; p += sizeof(int32_t) * nb_fine;     // counts, then slot - stage offset
   uint32_t* hacc = (uint32_t*)p;                                 // hub sums of this tile
@@ -497,12 +499,6 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
       if (rank[i] >= 0) stage[hist[rrow[i] >> lwb] + rank[i]] = make_uint2(rrow[i], rval[i]);
     if (nhot > 0 && warp == 1) htb[lane] = 0u;
     __syncthreads();
-    if (tid < nkn) {  // the next tile's entries (this tile's are no longer read)
-      kbase[tid] = pcb - pw;
-      kx[tid] = pcx;
-      const int32_t off = pw - p0n;
-      if (tid > 0 && off > 0 && off < npn) atomicOr(&hbits[off >> 5], 1u << (off & 31));
-    }
     // ---- write the runs to the buckets ----
     const int32_t kept = s_kept;
     for (int32_t s = tid; s < kept; s += K2_THREADS) {
@@ -513,7 +509,13 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
       ws.brow[dst] = (uint16_t)(e.x & wmask);
       if (SEM != kOrAnd) ws.bval[dst] = e.y;
     }
-    __syncthreads();
+    __syncthreads();  // the staged products are written out: their bytes take the next entries
+    if (tid < nkn) {  // the next tile's first entries (loaded during this tile)
+      kbase[tid] = pcb - pw;
+      kx[tid] = pcx;
+      const int32_t off = pw - p0n;
+      if (tid > 0 && off > 0 && off < npn) atomicOr(&hbits[off >> 5], 1u << (off & 31));
+    }
   }
 }
 

@@ -233,11 +233,11 @@ cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, i
                       int only_push = 0);
 cudaError_t launch_bucket_sizes(const Matrix& A, int lwb_lo, int nb_fine, int32_t* counts,
                                 unsigned int* bad, cudaStream_t s);
-// K2 shared memory: staged (row, value) pairs of one tile, the bitmap of
-// entry starts, cb - cw and x value of the tile's x entries, the bucket
-// histogram and slots, and the hub-row tables.
+// K2 shared memory: cb - cw and x value of the tile's x entries (whose bytes
+// then hold the tile's staged (row, value) pairs), the bitmap of entry starts,
+// the bucket histogram and slots, and the hub-row tables.
 __host__ __device__ constexpr size_t k2_smem_bytes(int nb_fine, bool hot) {
-  return sizeof(uint32_t) * 2 * QMAX + sizeof(uint32_t) * (QMAX / 32) + sizeof(int32_t) * (QMAX + 1) +
+  return sizeof(uint32_t) * (QMAX / 32) + sizeof(int32_t) * (QMAX + 1) +
          sizeof(uint32_t) * (QMAX + 1) + sizeof(int32_t) * (size_t)nb_fine * 2 + 64 +
          (hot ? sizeof(uint32_t) * HOT_MAX * 2 + sizeof(uint32_t) * (HOT_MAX / 32) + 64 : 0);
 }
