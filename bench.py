@@ -39,8 +39,9 @@ SCALE, EDGE_FACTOR, SEED, F = 22, 16, 1, 1_000_000
 # of the same kernel build on R-MAT s21 with nnz(x) = 5e5, scaled by products
 # (the traffic of a launch grows with its products); None while the kernel
 # differs from the captured one.
-K2_TRAFFIC_PER_PRODUCT = None
-K2_TRAFFIC_SOURCE = "no capture of the current K2 yet"
+K2_TRAFFIC_PER_PRODUCT = (180.53e6 + 36.65e6) / 15.03e6
+K2_TRAFFIC_SOURCE = ("ncu full capture of the same K2 (commit 17daac1), R-MAT s21 nnz(x)=5e5, "
+                     "scaled by products")
 
 
 NOMINAL_HBM_GBS = 7900.0  # nominal HBM3e bandwidth of the part, a second denominator
