@@ -313,8 +313,7 @@ static int create_impl(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz, c
   if (val_type == SPMSPV_VAL_F32 && nnz > 0 && !val)
     return fail(SPMSPV_ERR_ARG, "val is NULL for SPMSPV_VAL_F32");
 
-  spmspv_handle* h = new spmspv_handle();
-  memset(h, 0, sizeof(*h));
+  spmspv_handle* h = new spmspv_handle();  // value-initialised: every field zero or its default
   h->magic = kHandleMagic;
   cudaGetDevice(&h->device);
   cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
