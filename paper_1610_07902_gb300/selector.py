@@ -90,6 +90,43 @@ def collect(Ad, A, sources, reps=3, max_levels=64, rng=None):
     return (np.array(feats, np.float32), np.array(targ, np.float32), np.array(valid, np.uint8))
 
 
+def plain_frontiers(n, count, rng):
+    """`count` frontiers of log-uniform size in [1, n] (distinct ids, random order)."""
+    import synth
+    sizes = np.unique(np.maximum(1, np.floor(10 ** rng.uniform(0, np.log10(n), count))).astype(np.int64))
+    return [synth.frontier(n, int(f), seed=int(rng.integers(1 << 30)), stream=2) for f in sizes]
+
+
+def collect_plain(A, count=10, reps=3, rng=None):
+    """(features, log2 ms, valid) from unmasked (+,*) products with values,
+    x of log-uniform size: the calls a BFS level never looks like (no mask,
+    up to every column), timed under every push schedule."""
+    rng = rng or np.random.default_rng(1)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val)
+    dev = Ad.colptr.device
+    cap = A.m
+    y_idx = torch.empty(cap, dtype=torch.int32, device=dev)
+    y_val = torch.empty(cap, dtype=torch.float32, device=dev)
+    nz = torch.zeros(1, dtype=torch.int32, device=dev)
+    feats, targ, valid = [], [], []
+    for xi_h, xv_h in plain_frontiers(A.n, count, rng):
+        xi, xv = torch.from_numpy(xi_h).to(dev), torch.from_numpy(xv_h).to(dev)
+        row = np.full(12, np.nan)
+        for sched in range(6):
+            fn = lambda: S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, xi, xv, xi_h.size, None,
+                                      S.SPMSPV_SCHED_OPT(sched), y_idx, y_val, cap, nz)
+            fn()
+            row[sched] = time_call(fn, reps)
+        S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, xi, xv, xi_h.size, None, S.SPMSPV_WITH_FEATURES,
+                     y_idx, y_val, cap, nz)
+        feats.append(S.spmspv_last_features(Ad.handle))
+        v = ~np.isnan(row)
+        targ.append(np.where(v, np.log2(np.where(v, row, 1.0)), 0.0))
+        valid.append(v.astype(np.uint8))
+    Ad.close()
+    return (np.array(feats, np.float32), np.array(targ, np.float32), np.array(valid, np.uint8))
+
+
 def train(Ad, feats, targ, valid, epochs=300, batch=64, lr=3e-3, seed=1):
     dev = Ad.colptr.device
     f = torch.from_numpy(np.ascontiguousarray(feats)).to(dev)
@@ -124,11 +161,11 @@ EVAL_GRAPHS = [("rmat23", ("rmat", 23, 21)), ("grid3d_320", ("grid", (320, 320, 
 EVAL_GRAPHS_SMALL = [("rmat22", ("rmat", 22, 21)), ("grid3d_256", ("grid", (256, 256, 256)))]
 
 
-def make_graph(spec):
+def make_graph(spec, values=False):
     import synth
     if spec[0] == "rmat":
-        return synth.rmat(spec[1], seed=spec[2], values=False)
-    return synth.grid3d(*spec[1], 0.05, seed=3, values=False)
+        return synth.rmat(spec[1], seed=spec[2], values=values)
+    return synth.grid3d(*spec[1], 0.05, seed=3, values=values)
 
 
 def training_graphs():
@@ -225,6 +262,40 @@ def evaluate(Ad, A, sources, params, reps=3, max_levels=48, rng=None):
     return {"per_call_regret": per_call, "bfs_total_ms": totals, "default_schedule": default}
 
 
+def evaluate_plain(A, params, count=8, reps=3, rng=None):
+    """Held-out evaluation on unmasked (+,*) products with values (x of
+    log-uniform size): per call, the regret of the picked schedule and of the
+    fixed default, and the time of AUTO as run against the fixed default."""
+    rng = rng or np.random.default_rng(3)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val)
+    S.spmspv_selector_set(Ad.handle, params)
+    default = S.spmspv_default_schedule(Ad.handle)
+    dev = Ad.colptr.device
+    cap = A.m
+    y_idx = torch.empty(cap, dtype=torch.int32, device=dev)
+    y_val = torch.empty(cap, dtype=torch.float32, device=dev)
+    nz = torch.zeros(1, dtype=torch.int32, device=dev)
+    rows = []
+    for xi_h, xv_h in plain_frontiers(A.n, count, rng):
+        xi, xv = torch.from_numpy(xi_h).to(dev), torch.from_numpy(xv_h).to(dev)
+        call = lambda o: (lambda: S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, xi, xv, xi_h.size, None,
+                                               o, y_idx, y_val, cap, nz))
+        t = np.full(6, np.inf)
+        for sched in range(6):
+            fn = call(S.SPMSPV_SCHED_OPT(sched))
+            fn()
+            t[sched] = time_call(fn, reps)
+        fa = call(S.SPMSPV_SCHED_AUTO)
+        fa()
+        ta = time_call(fa, reps)
+        pick = S.spmspv_last_schedule(Ad.handle)
+        rows.append({"nnz_x": int(xi_h.size), "pick": pick, "pick_regret": float(t[pick] / t.min() - 1),
+                     "fixed_regret": float(t[default] / t.min() - 1),
+                     "auto_vs_fixed_default": float(t[default] / ta)})
+    Ad.close()
+    return rows
+
+
 def main_evaluate(args):
     import synth
     params, meta = load(args.weights)
@@ -235,11 +306,13 @@ def main_evaluate(args):
         Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
         r = evaluate(Ad, A, synth.sources(A.colptr, args.sources, seed=7), params)
         r.update({"n": int(A.n), "nnz": int(A.nnz)})
+        Ad.close()
+        del A
+        r["plain_plus_times"] = evaluate_plain(make_graph(spec, values=True), params)
         out["graphs"][name] = r
         print("%-12s %s (%.0f s)" % (name, json.dumps(r["bfs_total_ms"]), time.time() - t0),
               file=sys.stderr)
-        Ad.close()
-        del A
+        print("%-12s plain (+,*): %s" % (name, json.dumps(r["plain_plus_times"])), file=sys.stderr)
     with open(args.eval_out, "w") as fh:
         json.dump(out, fh, indent=1)
 
@@ -263,11 +336,15 @@ def main():
     F, T, V = [], [], []
     t0 = time.time()
     last = None
-    for name, A in training_graphs():
+    for (name, spec), (_, A) in zip(TRAINING_GRAPHS, training_graphs()):
         Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
         f, t, v = collect(Ad, A, synth.sources(A.colptr, args.sources, seed=5))
-        print("%-12s levels %4d  (%.0f s)" % (name, f.shape[0], time.time() - t0), file=sys.stderr)
-        F.append(f), T.append(t), V.append(v)
+        fp, tp, vp = collect_plain(make_graph(spec, values=True))
+        print("%-12s levels %4d, plain calls %3d  (%.0f s)" % (name, f.shape[0], fp.shape[0], time.time() - t0),
+              file=sys.stderr)
+        F += [f, fp]
+        T += [t, tp]
+        V += [v, vp]
         if last is not None:
             last.close()
         last = Ad
@@ -275,9 +352,10 @@ def main():
     losses = train(last, F, T, V, epochs=args.epochs)
     params = S.spmspv_selector_get(last.handle)
     save(params, args.out, {"samples": int(F.shape[0]), "final_loss": float(losses[-1]),
+                            "sample_kinds": "BFS level replays and unmasked (+,*) calls",
                             "graphs": [g for g, _ in TRAINING_GRAPHS]})
     np.savez(os.path.splitext(args.out)[0] + "_data.npz", feats=F, target=T, valid=V)
-    print("trained on %d levels, loss %.4f -> %.4f" % (F.shape[0], losses[0], losses[-1]),
+    print("trained on %d calls, loss %.4f -> %.4f" % (F.shape[0], losses[0], losses[-1]),
           file=sys.stderr)
 
 
