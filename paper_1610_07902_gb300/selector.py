@@ -328,6 +328,8 @@ def main():
     ap.add_argument("--weights", default=WEIGHTS)
     ap.add_argument("--eval-out", default="selector_eval.json")
     ap.add_argument("--small", action="store_true", help="held-out graphs one size smaller")
+    ap.add_argument("--plain-calls", type=int, default=0,
+                    help="also train on this many unmasked (+,*) calls per graph (default: BFS levels only)")
     args = ap.parse_args()
     S.load()
     if args.evaluate:
@@ -339,7 +341,8 @@ def main():
     for (name, spec), (_, A) in zip(TRAINING_GRAPHS, training_graphs()):
         Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
         f, t, v = collect(Ad, A, synth.sources(A.colptr, args.sources, seed=5))
-        fp, tp, vp = collect_plain(make_graph(spec, values=True))
+        fp, tp, vp = (collect_plain(make_graph(spec, values=True), count=args.plain_calls) if args.plain_calls
+                      else (np.zeros((0, 6), np.float32), np.zeros((0, 12), np.float32), np.zeros((0, 12), np.uint8)))
         print("%-12s levels %4d, plain calls %3d  (%.0f s)" % (name, f.shape[0], fp.shape[0], time.time() - t0),
               file=sys.stderr)
         F += [f, fp]
@@ -352,7 +355,8 @@ def main():
     losses = train(last, F, T, V, epochs=args.epochs)
     params = S.spmspv_selector_get(last.handle)
     save(params, args.out, {"samples": int(F.shape[0]), "final_loss": float(losses[-1]),
-                            "sample_kinds": "BFS level replays and unmasked (+,*) calls",
+                            "sample_kinds": ("BFS level replays and unmasked (+,*) calls" if args.plain_calls
+                                             else "BFS level replays"),
                             "graphs": [g for g, _ in TRAINING_GRAPHS]})
     np.savez(os.path.splitext(args.out)[0] + "_data.npz", feats=F, target=T, valid=V)
     print("trained on %d calls, loss %.4f -> %.4f" % (F.shape[0], losses[0], losses[-1]),
