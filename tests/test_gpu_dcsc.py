@@ -161,6 +161,33 @@ def test_dcsc_graph_algorithms(lib, graph):
     Ad.close()
 
 
+def test_dcsc_learned_schedule(lib, graph):
+    """The learned selector on a DCSC handle: push schedules only (no CSR view),
+    same results as the reference for a plain product and a BFS."""
+    torch, S = lib
+    from paper_1610_07902_gb300 import selector
+    try:
+        params = selector.load()[0]
+    except (OSError, ValueError, KeyError):
+        pytest.skip("no selector weights")
+    A, jc, cp = graph
+    Ad = S.DcscMatrix(A.m, A.n, jc, cp, A.rowidx, None, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
+    S.spmspv_selector_set(Ad.handle, params)
+    x_idx = np.random.default_rng(3).permutation(jc)[:2000].astype(np.int32)
+    xd = torch.from_numpy(x_idx).cuda()
+    yi, yv, k = Ad.multiply(1, xd, xd, None, S.SPMSPV_SORTED_OUT | S.SPMSPV_SCHED_AUTO)
+    ref = oracle.spmspv(A.m, A.colptr, A.rowidx, None, oracle.MIN_SELECT2ND, x_idx, x_idx, None, True)
+    compare(1, ref, yi.cpu().numpy(), yv.cpu().numpy())
+    assert S.spmspv_last_schedule(Ad.handle) < 6  # a push schedule
+    src = int(jc[11])
+    level, parent, nl = Ad.bfs(src, S.SPMSPV_SCHED_AUTO)
+    rl, rp = oracle.bfs(A.colptr, A.rowidx, src)[:2]
+    np.testing.assert_array_equal(level.cpu().numpy(), rl)
+    np.testing.assert_array_equal(parent.cpu().numpy(), rp)
+    assert S.spmspv_device_status(Ad.handle) == 0
+    Ad.close()
+
+
 def test_dcsc_batched_multi_source_bfs(lib, graph):
     torch, S = lib
     A, jc, cp = graph
