@@ -291,8 +291,10 @@ __device__ __forceinline__ void spa_apply(uint32_t* spa, uint32_t r, uint32_t v)
 // search, no divergence).  Products are counted per bucket with
 // shared-memory atomics, one warp scans the counts, every non-empty bucket
 // gets one run reserved with a global atomic, the products are staged in
-// shared memory grouped by bucket and written out in runs.  Hub rows (row ids >= m in the relabelled
-// row-id array) are summed per tile in shared memory instead.
+// shared memory grouped by bucket (in the bytes that held the tile's x
+// entries, so that three 512-thread CTAs fit per SM) and written out in runs.
+// Hub rows (row ids >= m in the relabelled row-id array) are summed per tile
+// in shared memory instead.
 // IT: products per thread when the host knows the work quantum (4 or 8),
 // 0 when the device decides it; MASKED: a mask may be given.
 template <int SEM, int IT, bool MASKED>
