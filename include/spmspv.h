@@ -143,6 +143,18 @@ int spmspv_create_dcsc(spmspv_handle** h, int32_t m, int32_t n, int64_t nnz, int
                        const int32_t* jc, const int32_t* cp, const int32_t* rowidx, const void* val,
                        int val_type, uint32_t flags);
 
+/*
+ * The auxiliary column index spmspv_create_dcsc builds, computed on HOST
+ * arrays (no device, no handle): jc host int32[nzc], strictly ascending in
+ * [0, n), else SPMSPV_ERR_ARG.  *shift = s, the smallest s >= 0 with
+ * n / 2^s <= max(nzc, 1); *aux_len = (n-1)/2^s + 2; aux (host, may be NULL)
+ * receives min(aux_capacity, *aux_len) entries, aux[k] = the first position p
+ * with jc[p] >= k * 2^s (nzc when there is none).  Column j is stored iff it
+ * lies among jc[aux[j >> s] .. aux[(j >> s) + 1]).
+ */
+int spmspv_dcsc_index(int32_t n, int32_t nzc, const int32_t* jc, int32_t* aux, int64_t aux_capacity,
+                      int64_t* aux_len, int32_t* shift);
+
 /* Release the handle and its workspace (synchronises the device). */
 int spmspv_destroy(spmspv_handle* h);
 

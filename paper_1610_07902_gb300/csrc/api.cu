@@ -260,29 +260,43 @@ namespace spmspv {
 // DCSC set-up (Sec. II-C): checks the stored column ids and pointers and
 // builds the auxiliary column index on the host, O(nzc + n / 2^aux_shift),
 // then copies it to the device.
+// The DCSC checks and auxiliary index on host arrays (no CUDA calls): jc
+// strictly ascending in [0, n), cp from 0 to nnz and non-decreasing; then
+// chunks of 2^s column ids, about as many as stored columns, and aux[k] = the
+// first position whose id is at least k * 2^s, for k in [0, (n-1)/2^s + 1].
+static int dcsc_index_host(int32_t n, int64_t nnz, int32_t nzc, const int32_t* jc, const int32_t* cp,
+                           std::vector<int32_t>& aux, int& shift) {
+  for (int32_t p = 0; p < nzc; ++p) {
+    if (jc[p] < 0 || jc[p] >= n) return fail(SPMSPV_ERR_ARG, "jc[%d] = %d outside [0, n)", p, jc[p]);
+    if (p > 0 && jc[p] <= jc[p - 1]) return fail(SPMSPV_ERR_ARG, "jc is not strictly ascending at %d", p);
+    if (cp && cp[p + 1] < cp[p]) return fail(SPMSPV_ERR_ARG, "cp decreases at %d", p);
+  }
+  if (cp && (cp[0] != 0 || (int64_t)cp[nzc] != nnz)) return fail(SPMSPV_ERR_ARG, "cp must run from 0 to nnz");
+  int s = 0;
+  while (((int64_t)n >> s) > (int64_t)(nzc > 0 ? nzc : 1)) ++s;
+  const int64_t naux = (((int64_t)n - 1) >> s) + 2;
+  aux.assign((size_t)naux, 0);
+  int32_t p = 0;
+  for (int64_t k = 0; k < naux; ++k) {
+    const int64_t first = k << s;
+    while (p < nzc && (int64_t)jc[p] < first) ++p;
+    aux[(size_t)k] = p;
+  }
+  shift = s;
+  return SPMSPV_OK;
+}
+
 static int build_dcsc_index(spmspv_handle* h, int32_t n, int64_t nnz, int32_t nzc, const int32_t* jc,
                             const int32_t* cp) {
   std::vector<int32_t> hjc((size_t)nzc), hcp((size_t)nzc + 1);
   cudaError_t e = cudaMemcpy(hjc.data(), jc, sizeof(int32_t) * (size_t)nzc, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(hcp.data(), cp, sizeof(int32_t) * ((size_t)nzc + 1), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "DCSC arrays copy");
-  for (int32_t p = 0; p < nzc; ++p) {
-    if (hjc[p] < 0 || hjc[p] >= n) return fail(SPMSPV_ERR_ARG, "jc[%d] = %d outside [0, n)", p, hjc[p]);
-    if (p > 0 && hjc[p] <= hjc[p - 1]) return fail(SPMSPV_ERR_ARG, "jc is not strictly ascending at %d", p);
-    if (hcp[p + 1] < hcp[p]) return fail(SPMSPV_ERR_ARG, "cp decreases at %d", p);
-  }
-  if (hcp[0] != 0 || (int64_t)hcp[nzc] != nnz) return fail(SPMSPV_ERR_ARG, "cp must run from 0 to nnz");
-  // chunks of 2^s column ids, about as many as stored columns
+  std::vector<int32_t> haux;
   int s = 0;
-  while (((int64_t)n >> s) > (int64_t)(nzc > 0 ? nzc : 1)) ++s;
-  const int64_t naux = (((int64_t)n - 1) >> s) + 2;
-  std::vector<int32_t> haux((size_t)naux);
-  int32_t p = 0;
-  for (int64_t k = 0; k < naux; ++k) {
-    const int64_t first = k << s;
-    while (p < nzc && (int64_t)hjc[p] < first) ++p;
-    haux[(size_t)k] = p;
-  }
+  int rc = dcsc_index_host(n, nnz, nzc, hjc.data(), hcp.data(), haux, s);
+  if (rc != SPMSPV_OK) return rc;
+  const size_t naux = haux.size();
   if ((e = cudaMalloc(&h->dcsc_aux, sizeof(int32_t) * (size_t)naux)) != cudaSuccess)
     return fail(SPMSPV_ERR_OOM, "DCSC index: %s", cudaGetErrorString(e));
   if ((e = cudaMemcpy(h->dcsc_aux, haux.data(), sizeof(int32_t) * (size_t)naux, cudaMemcpyHostToDevice)) !=
@@ -508,6 +522,21 @@ extern "C" {
 int spmspv_create_csc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz, const int32_t* colptr,
                       const int32_t* rowidx, const void* val, int val_type, uint32_t flags) {
   return create_impl(out, m, n, nnz, colptr, rowidx, val, val_type, flags, nullptr, 0);
+}
+
+int spmspv_dcsc_index(int32_t n, int32_t nzc, const int32_t* jc, int32_t* aux, int64_t aux_capacity,
+                      int64_t* aux_len, int32_t* shift) {
+  if (n < 1 || nzc < 0 || nzc > n) return fail(SPMSPV_ERR_ARG, "need n >= 1 and 0 <= nzc <= n");
+  if (nzc > 0 && !jc) return fail(SPMSPV_ERR_ARG, "jc is NULL");
+  std::vector<int32_t> a;
+  int s = 0;
+  int rc = dcsc_index_host(n, 0, nzc, jc, nullptr, a, s);
+  if (rc != SPMSPV_OK) return rc;
+  if (aux_len) *aux_len = (int64_t)a.size();
+  if (shift) *shift = s;
+  if (aux && aux_capacity > 0)
+    memcpy(aux, a.data(), sizeof(int32_t) * (size_t)std::min<int64_t>(aux_capacity, (int64_t)a.size()));
+  return SPMSPV_OK;
 }
 
 int spmspv_create_dcsc(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz, int32_t nzc,

@@ -129,6 +129,8 @@ def load(build_if_missing: bool = True):
         lib.spmspv_mis.argtypes = [_P, _P, _P, _P, ctypes.c_uint32, _P]
         lib.spmspv_create_dcsc.argtypes = [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                            ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int, ctypes.c_uint32]
+        lib.spmspv_dcsc_index.argtypes = [ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int64,
+                                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
         lib.spmspv_mcm.argtypes = [_P, _P, _P, _P, _P, ctypes.c_uint32, _P]
         lib.spmspv_profile_begin.argtypes = [_P]
         lib.spmspv_profile_end.argtypes = [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
@@ -323,6 +325,22 @@ def spmspv_create_dcsc(m, n, nnz, nzc, jc, cp, rowidx, val=None, val_type=SPMSPV
                                      _ptr(rowidx), _ptr(val), int(val_type), int(flags)),
            "spmspv_create_dcsc")
     return h.value
+
+
+def spmspv_dcsc_index(n, jc):
+    """Host computation of a DCSC matrix's auxiliary column index: (aux
+    int32 numpy array, shift).  jc: host numpy int32 array of stored column ids."""
+    import numpy as np
+    jc = np.ascontiguousarray(jc, dtype=np.int32)
+    length = ctypes.c_int64(0)
+    shift = ctypes.c_int32(0)
+    _check(load().spmspv_dcsc_index(int(n), int(jc.size), jc.ctypes.data if jc.size else None, None, 0,
+                                    ctypes.byref(length), ctypes.byref(shift)), "spmspv_dcsc_index")
+    aux = np.zeros(length.value, dtype=np.int32)
+    _check(load().spmspv_dcsc_index(int(n), int(jc.size), jc.ctypes.data if jc.size else None,
+                                    aux.ctypes.data, int(aux.size), ctypes.byref(length), ctypes.byref(shift)),
+           "spmspv_dcsc_index")
+    return aux, int(shift.value)
 
 
 def spmspv_mcm(h, mate_r, mate_c, d_card=None, d_nphases=None, opts=0, stream=None):
