@@ -355,9 +355,10 @@ static int create_impl(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz, c
   h->lwb_lo = lwb_hi - 2;
   h->nb_fine = (int)(((int64_t)m + (1 << h->lwb_lo) - 1) >> h->lwb_lo);
   if (h->nb_fine > NB_K2_MAX) {
+    const int nb_fine = h->nb_fine;
     cudaFree(h->dcsc_aux);
     delete h;
-    return fail(SPMSPV_ERR_UNSUPPORTED, "too many row-range buckets (%d)", h->nb_fine);
+    return fail(SPMSPV_ERR_UNSUPPORTED, "too many row-range buckets (%d)", nb_fine);
   }
 
   // workspace: one allocation, carved in 256-byte aligned pieces

@@ -65,9 +65,10 @@ template <int SEM, bool BFS>
 __global__ void __launch_bounds__(PULL_THREADS)
 k_pull_rows(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
             const float* __restrict__ val, int32_t m, const uint32_t* __restrict__ xbits,
-            const uint32_t* __restrict__ xdense, const uint32_t* __restrict__ mask, int mask_comp,
+            const uint32_t* __restrict__ xdense, const uint32_t* mask, int mask_comp,
             int early_exit, int32_t* __restrict__ y_idx, uint32_t* __restrict__ y_val,
-            int32_t y_cap, int32_t* __restrict__ d_nnz_y, uint32_t* __restrict__ visited,
+            int32_t y_cap, int32_t* __restrict__ d_nnz_y, uint32_t* visited,  // a BFS passes one
+                                                                            // bitmap as mask and visited
             Workspace ws, int ntiles, int only_pull) {
   __shared__ uint32_t s_val[PULL_THREADS * 33];
   __shared__ int32_t s_scan[PULL_THREADS / 32 + 1];
