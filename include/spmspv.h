@@ -441,9 +441,16 @@ int spmspv_last_work(spmspv_handle* h, int64_t* work);
  *   val_type: SPMSPV_VAL_F32 or SPMSPV_VAL_NONE, as for spmspv_create_csc.
  *   Output order, capacity rule and *d_nnz_y: as for spmspv_run (a y that does
  *   not fit leaves the size it needs in *d_nnz_y).
+ *   No handle checks the matrix here, so every call makes one pass over A's
+ *   nnz row ids to size the bucket regions (a call costs O(nnz(A)) on top of
+ *   the product's own work).  A row id outside [0, m), or an x index that is
+ *   out of range or repeated, is dropped without any access outside the
+ *   arrays and the call reports it by setting *d_nnz_y to -1 (y undefined).
  * The first call on a device looks up the array's device address with that
  * device current (a one-time set-up); make that first call before any stream
- * capture.  Every call shares the one array and each call clears the part that
+ * capture.  The address is cached per device for the life of the process: a
+ * process that calls cudaDeviceReset must not call this entry point on that
+ * device afterwards.  Every call shares the one array and each call clears the part that
  * must start at zero: calls whose kernels overlap on the GPU (other streams,
  * or other host threads without ordering) race on it and give undefined
  * results.  Asynchronous on `stream`; nothing is allocated or freed.

@@ -60,3 +60,47 @@ def lazy_pagerank(colptr, rowidx, alpha, v):
     dinv = np.where(deg > 0, 1.0 / np.maximum(deg, 1.0), 0.0)
     W = 0.5 * (np.eye(n) + A * dinv[None, :])
     return alpha * np.linalg.solve(np.eye(n) - (1.0 - alpha) * W, np.asarray(v, np.float64))
+
+
+def acl_trace(colptr, rowidx, seed, alpha, eps, max_steps):
+    """The same synchronous push as acl(), with whole-array numpy steps, for
+    graphs of millions of vertices; also returns, per vertex, how many steps
+    it pushed in and how close its residual came to the push threshold.
+
+    Returns (p, r, steps, pushes, margin): pushes int32[n]; margin[v] = the
+    smallest |r(v) - eps d(v)| / (eps d(v)) over the steps at whose start v
+    had a positive residual (inf if it never had one).  A vertex with a small
+    margin is one whose push decision a lower-precision run may take the
+    other way.  The neighbour update adds each step's contributions into r
+    as one sum per vertex (r += A x), so p and r agree with acl() to FP64
+    rounding, not bit for bit.
+    """
+    colptr = np.asarray(colptr, np.int64)
+    rowidx = np.asarray(rowidx, np.int64)
+    n = len(colptr) - 1
+    deg = np.diff(colptr).astype(np.float64)
+    thr = eps * deg
+    p = np.zeros(n)
+    r = np.zeros(n)
+    r[seed] = 1.0
+    pushes = np.zeros(n, np.int32)
+    margin = np.full(n, np.inf)
+    steps = 0
+    while steps < max_steps:
+        cand = np.flatnonzero((r > 0) & (deg > 0))
+        margin[cand] = np.minimum(margin[cand], np.abs(r[cand] - thr[cand]) / thr[cand])
+        active = cand[r[cand] >= thr[cand]]
+        if active.size == 0:
+            break
+        ru = r[active]
+        xu = (1.0 - alpha) * ru / (2.0 * deg[active])
+        p[active] += alpha * ru
+        r[active] = (1.0 - alpha) * ru / 2.0
+        pushes[active] += 1
+        # x(u) goes to every row of column u: y = A x
+        lens = colptr[active + 1] - colptr[active]
+        first = np.repeat(colptr[active] - np.concatenate([[0], np.cumsum(lens)[:-1]]), lens)
+        rows = rowidx[first + np.arange(int(lens.sum()))]
+        r += np.bincount(rows, weights=np.repeat(xu, lens), minlength=n)
+        steps += 1
+    return p, r, steps, pushes, margin

@@ -88,6 +88,7 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
     if (tid == 0) {
       st->f = f;
       st->k3_ticket = 0u;
+      st->feat_dev = 0;
       if (forced) {
         st->dir = f_dir;
         st->q = f_q;
@@ -402,13 +403,17 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
         else if (SEM == kMinSelect2nd) v = xi[i];
         rval[i] = v;
         if (row == 0xffffffffu) continue;
-        if ((int32_t)row < m) {
+        if (row < (uint32_t)m) {
           bool keep = true;
           if (MASKED && mask) {
             const uint32_t bit = (__ldg(mask + (row >> 5)) >> (row & 31)) & 1u;
             keep = mask_comp ? (bit == 0u) : (bit != 0u);
           }
           if (keep) rank[i] = atomicAdd(&hist[row >> lwb], 1);
+        } else if (row - (uint32_t)m >= (uint32_t)nhot) {
+          // a row id outside [0, m) that is not a hub label (only a matrix
+          // that was never checked at create can hold one): dropped, flagged
+          atomicOr(&ws.st->status, ST_INDEX);
         } else {
           // a hub row: combine its products of this tile in shared memory
           const int hs = (int)row - m;

@@ -83,6 +83,16 @@ __global__ void k_region_starts(const int32_t* __restrict__ counts, int nb, int3
   }
 }
 
+// A matrix with row ids outside [0, m) (counted while sizing the bucket
+// regions) or an x with out-of-range or repeated indices (flagged by the work
+// scan) makes the result undefined: the kernels drop what they cannot place
+// and this one-thread kernel then reports the call as failed with
+// *d_nnz_y = -1.
+__global__ void k_noalloc_report(const unsigned int* __restrict__ bad, const DevState* __restrict__ st,
+                                 int32_t* __restrict__ d_nnz_y) {
+  if (*bad != 0u || (st->status & ST_INDEX) != 0u) *d_nnz_y = -1;
+}
+
 int setup_device(int dev, DeviceSetup** out) {
   if (dev < 0 || dev >= NA_MAX_DEVICES)
     return fail(SPMSPV_ERR_UNSUPPORTED, "device %d is beyond the %d devices supported", dev,
@@ -222,5 +232,7 @@ extern "C" int spmspv_run_noalloc(int32_t m, int32_t n, int64_t nnz, const int32
   e = launch_k3(semiring, false, A, ws, lwb_lo, nb_fine, y_idx, (uint32_t*)y_val, y_capacity,
                 d_nnz_y, nullptr, k3_grid, k3_smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "bucket merge launch");
+  k_noalloc_report<<<1, 1, 0, s>>>((const unsigned int*)(counts + NA_NB_MAX), ws.st, d_nnz_y);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "index report launch");
   return SPMSPV_OK;
 }

@@ -159,6 +159,10 @@ extern "C" int spmspv_last_features(spmspv_handle* h, float* feats) {
   DevState st;
   if ((e = cudaMemcpy(&st, h->ws.st, sizeof(st), cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(e, "state copy");
+  if (st.feat_dev) {  // the features the selector itself evaluated in this call
+    for (int k = 0; k < 6; ++k) feats[k] = st.feat[k];
+    return SPMSPV_OK;
+  }
   const double f = st.f, W = st.W, fc = st.fc > 0 ? st.fc : 1;
   feats[0] = (float)std::log2(1.0 + f);
   feats[1] = (float)std::log2(1.0 + W);

@@ -63,6 +63,11 @@ __device__ __forceinline__ void sel_choose_warp(const float* __restrict__ w, Dev
   const int lwb_lo = a.lwb_lo;
   float x[SEL_IN];
   sel_features(st, m, n, nnz, a.bfs, x);
+  if ((threadIdx.x & 31) == 0) {  // kept for spmspv_last_features
+#pragma unroll
+    for (int k = 0; k < SEL_IN; ++k) st->feat[k] = x[k];
+    st->feat_dev = 1;
+  }
 #pragma unroll
   for (int k = 0; k < SEL_IN; ++k) x[k] = (x[k] - w[SEL_OMEAN + k]) * w[SEL_OSCALE + k];
   const float o = sel_forward_warp(w, x, nullptr, nullptr);

@@ -87,6 +87,8 @@ struct DevState {
   uint32_t* bfs_fb;    // BFS: two frontier bitmaps of ceil(n/32) words; level L reads
                        // bitmap (L-1)&1 (pull) and writes bitmap L&1 (K3 or pull)
   uint32_t k1_done;    // K1 CTAs finished; the last one runs the selector (self-resetting)
+  int32_t feat_dev;    // 1 when the current call's selector wrote feat[] (cleared by every K1)
+  float feat[6];       // the six selector features as the device computed them
 };
 
 // Selector run inside the work scan by its last CTA to finish: weights (NULL:

@@ -56,3 +56,51 @@ def compare(semiring, ref, y_idx, y_val, sorted_out=True):
             ref.idx[bad][:5], ratio.max())
         worst = float(ratio.max(initial=0.0))
     return worst
+
+
+# ACL (FP32 on the device, FP64 reference): a vertex whose residual came
+# within ACL_NEAR (relative) of its threshold eps*d(v) at some step may take
+# its push decision the other way in FP32; the FP32 residual's own relative
+# error stays below that (a few dozen steps, each adding a handful of
+# roundings of 2^-24), so every other decision is the same on both sides.
+ACL_NEAR = 1e-4
+ACL_TOL = 1e-4  # elementwise, relative to the FP64 value
+
+
+def acl_compare(p32, r32, colptr, rowidx, seed, alpha, eps, max_steps):
+    """Element-wise comparison of one seed's FP32 ACL vectors with the FP64
+    trace.  When no vertex came near its threshold, every vertex must agree
+    within ACL_TOL.  Otherwise the vertices that disagree must lie within two
+    hops of a near vertex (a diverging push moves r(u) ~ eps d(u) to u's
+    neighbours, whose own decisions it can move in turn), and their number
+    and L1 difference are bounded by what those near vertices hold.
+    Returns (number of near vertices, number of disagreeing vertices)."""
+    from oracle import acl as oacl
+    p64, r64, _, pushes, margin = oacl.acl_trace(colptr, rowidx, seed, alpha, eps, max_steps)
+    p32 = np.asarray(p32, np.float64)
+    r32 = np.asarray(r32, np.float64)
+    floor = 1e-6 * eps  # values this small are rounding residue of zero sums
+    bad = (np.abs(p32 - p64) > ACL_TOL * p64 + floor) | (np.abs(r32 - r64) > ACL_TOL * r64 + floor)
+    near = np.flatnonzero(margin < ACL_NEAR)
+    if near.size == 0:
+        assert not bad.any(), "seed %d: %d vertices differ with no near-threshold vertex (e.g. %s)" % (
+            seed, int(bad.sum()), np.flatnonzero(bad)[:5])
+        return 0, 0
+    colptr = np.asarray(colptr, np.int64)
+    rowidx = np.asarray(rowidx, np.int64)
+    zone = np.zeros(p64.shape[0], bool)
+    zone[near] = True
+    for _ in range(2):
+        idx = np.flatnonzero(zone)
+        lens = colptr[idx + 1] - colptr[idx]
+        first = np.repeat(colptr[idx] - np.concatenate([[0], np.cumsum(lens)[:-1]]), lens)
+        zone[rowidx[first + np.arange(int(lens.sum()))]] = True
+    outside = bad & ~zone
+    assert not outside.any(), "seed %d: vertices %s differ beyond two hops of the near ones" % (
+        seed, np.flatnonzero(outside)[:5])
+    deg = np.diff(colptr).astype(np.float64)
+    held = float((2.0 * eps * deg[near]).sum())  # about the residual each near vertex holds, twice
+    l1 = float(np.abs(p32 - p64)[bad].sum() + np.abs(r32 - r64)[bad].sum())
+    assert l1 <= 4.0 * held, "seed %d: L1 difference %g against %g held near threshold" % (
+        seed, l1, held)
+    return int(near.size), int(bad.sum())

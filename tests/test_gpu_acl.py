@@ -4,16 +4,15 @@ The pushing sets are decided in FP32 on the device and in FP64 in the
 reference, so a vertex whose residual sits within rounding of eps*d(u) can
 push on one side only.  What must hold regardless is checked tightly: mass
 conservation, non-negativity and the termination rule.  The vectors are
-compared in L1: a single diverging decision moves at most about 2 eps d(u)
-of mass, so 1e-3 of the unit mass is far above rounding yet catches any
-wrong constant or dropped update.
+compared element by element (gpu_util.acl_compare): every vertex within a
+relative 1e-4 of the FP64 value when no decision came near its threshold,
+and otherwise every vertex beyond two hops of the near ones.
 """
 import numpy as np
 import pytest
 
 import synth
-from gpu_util import need_gpu
-from oracle import acl as oacl
+from gpu_util import acl_compare, need_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -46,9 +45,7 @@ def test_acl_matches_reference(lib, graph, lanes):
         assert abs(P[b].sum() + R[b].sum() - 1.0) < 1e-5, b
         assert (P[b] >= 0).all() and (R[b] >= 0).all()
         assert ((R[b] < eps * deg * (1 + 1e-4)) | ((deg == 0) & (R[b] == 0))).all(), b
-        p64, r64, _ = oacl.acl(A.colptr, A.rowidx, int(seeds[b]), alpha, eps, 10000)
-        assert np.abs(P[b] - p64).sum() < 1e-3, b
-        assert np.abs(R[b] - r64).sum() < 1e-3, b
+        acl_compare(P[b], R[b], A.colptr, A.rowidx, int(seeds[b]), alpha, eps, 10000)
     assert S.spmspv_device_status(Ad.handle) == 0
     Ad.close()
 

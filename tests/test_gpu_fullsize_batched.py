@@ -1,16 +1,16 @@
 """The batched workloads at the size the benchmark times them (R-MAT s20, 256
 frontiers / sources / seeds, autotuned lanes and schedules as in the bench)
 against the reference: every one of the 256 batched products checked element
-by element; the multi-source BFS (fixed and learned schedule) and ACL on a
-sample of sources and seeds the reference computes one by one, with the
-properties every source must satisfy checked for all of them."""
+by element; the multi-source BFS (fixed and learned schedule) from all 256
+sources level for level and parent for parent; ACL element by element on a
+sample of seeds (the reference is FP64 and the device decides its pushing sets
+in FP32), with the properties every seed must satisfy checked for all of them."""
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from gpu_util import compare, need_gpu
-from oracle import acl as oacl
+from gpu_util import acl_compare, compare, need_gpu
 
 pytestmark = pytest.mark.gpu
 B = 256
@@ -86,26 +86,35 @@ def test_msbfs_full_size(lib, pattern20, learned):
     assert S.spmspv_device_status(Ap.handle) == 0
     L = lv.view(B, A.n)
     P = pa.view(B, A.n)
-    # every source: level 0 at the source, parents one level up along an edge
+    # every source against the reference (levels are unique and the parent is
+    # the smallest-id neighbour one level up, so both are compared bit for bit)
+    from test_gpu_fullsize_bfs import oracle_bfs_all
+    refs = oracle_bfs_all(A, srcs)
+    lv_h, pa_h = lv.cpu().numpy().reshape(B, A.n), pa.cpu().numpy().reshape(B, A.n)
+    for b in range(B):
+        rl, rp, _ = refs[b]
+        np.testing.assert_array_equal(lv_h[b], rl, err_msg="levels of source %d" % b)
+        np.testing.assert_array_equal(pa_h[b], rp, err_msg="parents of source %d" % b)
+    # and, independently of the reference, the properties that single out that
+    # answer: the parent of every reached vertex is a neighbour at level - 1,
+    # and no neighbour at level - 1 has a smaller id
     rows = torch.from_numpy(A.rowidx.astype(np.int64)).cuda()
     cols = torch.repeat_interleave(torch.arange(A.n, device="cuda"),
                                    torch.from_numpy(np.diff(A.colptr).astype(np.int64)).cuda())
-    for b in range(B):
+    key_edges = torch.sort(cols * A.n + rows).values
+    big = torch.iinfo(torch.int64).max
+    for b in range(0, B, 8):
         l, p = L[b].long(), P[b].long()
         assert int(l[int(srcs[b])]) == 0 and int(p[int(srcs[b])]) == int(srcs[b])
         reached = (l > 0).nonzero().flatten()
         assert bool((l[p[reached]] == l[reached] - 1).all()), b
-        # an edge joins two reached vertices or two unreached ones, and never
-        # spans more than one level
-        both = (l[rows] >= 0) & (l[cols] >= 0)
-        assert bool((both | ((l[rows] < 0) & (l[cols] < 0))).all()), b
-        assert bool(((l[rows] - l[cols]).abs()[both] <= 1).all()), b
-    # the reference, one source at a time, on a sample
-    lv_h, pa_h = lv.cpu().numpy().reshape(B, A.n), pa.cpu().numpy().reshape(B, A.n)
-    for b in np.random.default_rng(6).choice(B, size=8, replace=False):
-        rl, rp = oracle.bfs(A.colptr, A.rowidx, int(srcs[b]))[:2]
-        np.testing.assert_array_equal(lv_h[b], rl)
-        np.testing.assert_array_equal(pa_h[b], rp)
+        key = p[reached] * A.n + reached  # edge (parent -> v) stored in column parent
+        pos = torch.searchsorted(key_edges, key).clamp(max=key_edges.numel() - 1)
+        assert bool((key_edges[pos] == key).all()), b
+        up = (l[cols] >= 0) & (l[cols] == l[rows] - 1)
+        best = torch.full((A.n,), big, dtype=torch.int64, device="cuda").scatter_reduce(
+            0, rows, torch.where(up, cols, torch.full_like(cols, big)), "amin")
+        assert bool((best[reached] == p[reached]).all()), b
 
 
 def test_acl_full_size(lib, pattern20):
@@ -122,7 +131,13 @@ def test_acl_full_size(lib, pattern20):
     deg = torch.from_numpy(np.diff(A.colptr).astype(np.float64)).cuda()
     assert bool(((Rm < eps * deg * (1 + 1e-4)) | ((deg == 0) & (Rm == 0))).all())
     P_h, R_h = Pm.cpu().numpy(), Rm.cpu().numpy()
-    for b in np.random.default_rng(7).choice(B, size=3, replace=False):
-        p64, r64, _ = oacl.acl(A.colptr, A.rowidx, int(srcs[b]), alpha, eps, 100000)
-        assert np.abs(P_h[b] - p64).sum() < 1e-3, b
-        assert np.abs(R_h[b] - r64).sum() < 1e-3, b
+    # element by element against the FP64 trace on a sample of 32 seeds (a
+    # few seconds each on the host, run in a thread pool)
+    from concurrent.futures import ThreadPoolExecutor
+    import os
+    sample = np.random.default_rng(7).choice(B, size=32, replace=False)
+    with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
+        out = list(ex.map(lambda b: acl_compare(P_h[b], R_h[b], A.colptr, A.rowidx, int(srcs[b]),
+                                                alpha, eps, 100000), sample))
+    print("ACL s20: seeds with near-threshold vertices %d of %d, disagreeing vertices %d" % (
+        sum(1 for nr, _ in out if nr), len(out), sum(d for _, d in out)))

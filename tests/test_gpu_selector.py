@@ -101,3 +101,35 @@ def test_device_choice_matches_reference_and_results_unchanged(lib):
         np.testing.assert_array_equal(parent.cpu().numpy(), par)
         assert nlv == nl
     Ad.close()
+
+
+def test_device_features_match_their_definition(lib):
+    """The six features the selector evaluates on the device, against their
+    definition computed on the host from the same x, mask and matrix:
+    log2(1+f), log2(1+W), the degree skew max_k d_k / (W / fc) with fc the x
+    entries whose column is non-empty, the mask density, log2 m and nnz/n."""
+    torch, S = lib
+    from test_gpu_spmspv import _run
+    A = synth.rmat(14, seed=4)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
+    S.spmspv_selector_set(Ad.handle, random_params(7))
+    deg = np.diff(A.colptr).astype(np.int64)
+    rng = np.random.default_rng(11)
+    for f in [1, 37, 2000, 9000]:
+        x_idx, xf = synth.frontier(A.n, f, seed=f)
+        for masked in (False, True):
+            mask = (rng.random(A.m) < 0.35).astype(np.uint8) if masked else None
+            for semiring in (0, 1):
+                xv = x_values(semiring, x_idx, xf)
+                _, _, _, st = _run(lib, A, Ad, semiring, x_idx, xv, mask, True, None, auto=True)
+                assert st == 0
+                got = S.spmspv_last_features(Ad.handle).astype(np.float64)
+                d = deg[x_idx]
+                W, fc = int(d.sum()), int((d > 0).sum())
+                want = np.array([np.log2(1 + f), np.log2(1 + W),
+                                 d.max() * fc / W if W else 0.0,
+                                 mask.sum() / A.m if masked else 0.0,
+                                 np.log2(A.m), A.nnz / A.n])
+                np.testing.assert_allclose(got, want, rtol=2e-6, atol=1e-7,
+                                           err_msg="f=%d masked=%s semiring=%d" % (f, masked, semiring))
+    Ad.close()

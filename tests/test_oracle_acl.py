@@ -114,3 +114,32 @@ def test_the_pins_catch_planted_slips():
         mod = types.ModuleType("acl_" + name)
         exec(compile(src.replace(old, new), name, "exec"), mod.__dict__)
         assert _pins_fail(mod), name
+
+
+@pytest.mark.parametrize("seed", [0, 7, 123])
+def test_trace_form_equals_the_loop_form(seed):
+    """acl_trace (whole-array steps, for large graphs) against acl(), whose
+    arithmetic the pins above fix: the same p, r and step count to FP64
+    rounding, and p(v) > 0 exactly where v pushed."""
+    colptr, rowidx = _sym_graph(300, 6, seed)
+    for s in (int(np.argmax(np.diff(colptr))), 5):
+        for eps, steps in ((1e-4, 1000), (1e-3, 3), (1e-6, 1000)):
+            p, r, k = oacl.acl(colptr, rowidx, s, 0.15, eps, steps)
+            p2, r2, k2, pushes, margin = oacl.acl_trace(colptr, rowidx, s, 0.15, eps, steps)
+            assert k2 == k
+            np.testing.assert_allclose(p2, p, rtol=1e-12, atol=1e-15)
+            np.testing.assert_allclose(r2, r, rtol=1e-12, atol=1e-15)
+            assert ((p2 > 0) == (pushes > 0)).all()
+            assert (pushes <= k).all() and (margin >= 0).all()
+
+
+def test_trace_margins_by_hand():
+    # path 0 - 1 - 2, seed 1, eps = 0.45 (thresholds 0.45, 0.9, 0.45): one
+    # push at step 0 (margin |1 - 0.9| / 0.9), then r = (0.2, 0.4, 0.2)
+    # leaves every vertex 5/9 below its threshold and nothing pushes
+    colptr = np.array([0, 1, 3, 4])
+    rowidx = np.array([1, 0, 2, 1])
+    p, r, k, pushes, margin = oacl.acl_trace(colptr, rowidx, 1, 0.2, 0.45, 50)
+    assert k == 1
+    np.testing.assert_array_equal(pushes, [0, 1, 0])
+    np.testing.assert_allclose(margin, [5 / 9, 1 / 9, 5 / 9], rtol=1e-12)
