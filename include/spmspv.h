@@ -379,6 +379,13 @@ int spmspv_tune_clear(spmspv_handle* h);
 
 /* Install / read the selector parameters (host arrays of `n` floats). */
 int spmspv_selector_set(spmspv_handle* h, const float* params, int32_t n);
+/* Install the selector parameters from a weights file: a JSON object whose
+ * "params" member is an array of SPMSPV_SELECTOR_NPARAM numbers (the format
+ * paper_1610_07902_gb300/selector_weights.json has; other members are
+ * ignored).  `path` is a host string owned by the caller.  A missing file, a
+ * missing or malformed array or a wrong count returns SPMSPV_ERR_ARG and
+ * leaves the installed parameters as they were.  Synchronous. */
+int spmspv_selector_load(spmspv_handle* h, const char* path);
 int spmspv_selector_get(spmspv_handle* h, float* params, int32_t n);
 
 /* The 6 selector features of the handle's last call (host out; synchronises). */

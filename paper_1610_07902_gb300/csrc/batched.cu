@@ -135,13 +135,14 @@ static int lane_launches(spmspv_handle* sub, BatchState* bs, int lane, int sem, 
                            nullptr, &sa)) != cudaSuccess)
       return cuda_fail(e, "batch work scan");
     if ((e = launch_k2(kMinSelect2nd, sub->A, sub->ws, sub->lwb_lo, sub->nb_fine, nullptr, 1,
-                       sub->k2_grid, sub->k2_smem, s, 1)) != cudaSuccess)
+                       sub->k2_grid, sub->k2_smem, s, 1, 0, BFS_DIRECT_MAX)) != cudaSuccess)
       return cuda_fail(e, "batch expand/scatter");
     const int lwb = sub->lwb_lo + 2;  // shared memory for the widest bucket
     const int nb_max = (int)(((int64_t)sub->A.m + (1 << sub->lwb_lo) - 1) >> sub->lwb_lo);
     const int k3_grid = std::max(1, std::min(nb_max, sub->sm_count * sub->k3_bps[2]));
     if ((e = launch_k3(kMinSelect2nd, true, sub->A, sub->ws, sub->lwb_lo, sub->nb_fine, nullptr,
-                       nullptr, 0, nullptr, nullptr, k3_grid, k3_smem_bytes(lwb), s, 1)) != cudaSuccess)
+                       nullptr, 0, nullptr, nullptr, k3_grid, k3_smem_bytes(lwb), s, 1,
+                       BFS_DIRECT_MAX)) != cudaSuccess)
       return cuda_fail(e, "batch merge");
     if ((e = launch_pull_rows_lane(sub, sub->rows_sorted, s)) != cudaSuccess)
       return cuda_fail(e, "batch pull");
@@ -155,13 +156,13 @@ static int lane_launches(spmspv_handle* sub, BatchState* bs, int lane, int sem, 
                   nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "batch work scan");
   e = launch_k2(bfs ? kMinSelect2nd : sem, sub->A, sub->ws, sub->lwb_lo, sub->nb_fine, nullptr,
-                1, sub->k2_grid, sub->k2_smem, s, 0, sc.q);
+                1, sub->k2_grid, sub->k2_smem, s, 0, sc.q, bfs ? BFS_DIRECT_MAX : 0);
   if (e != cudaSuccess) return cuda_fail(e, "batch expand/scatter");
   const size_t k3_smem = k3_smem_bytes(sc.lwb);
   const int nb = (int)(((int64_t)sub->A.m + (1 << sc.lwb) - 1) >> sc.lwb);
   const int k3_grid = std::max(1, std::min(nb, sub->sm_count * sub->k3_bps[sc.lwb - sub->lwb_lo]));
   e = launch_k3(bfs ? kMinSelect2nd : sem, bfs, sub->A, sub->ws, sub->lwb_lo, sub->nb_fine, nullptr,
-                nullptr, 0, nullptr, nullptr, k3_grid, k3_smem, s, 0);
+                nullptr, 0, nullptr, nullptr, k3_grid, k3_smem, s, 0, bfs ? BFS_DIRECT_MAX : 0);
   if (e != cudaSuccess) return cuda_fail(e, "batch merge");
   k_batch_continue<<<1, 32, 0, s>>>(cond, bs->desc);
   return (e = cudaGetLastError()) == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "batch condition");

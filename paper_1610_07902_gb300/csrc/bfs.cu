@@ -25,15 +25,19 @@ cudaError_t launch_pull(const spmspv_handle* h, int sem, bool bfs, const int32_t
                         int mask_comp, int early_exit, int32_t* y_idx, uint32_t* y_val,
                         int32_t y_cap, int32_t* d_nnz_y, uint32_t* visited, int only_pull,
                         cudaStream_t s);
-cudaError_t launch_pull_rows_bfs(const spmspv_handle* h, int early_exit, int only_pull, cudaStream_t s);
+cudaError_t launch_pull_rows_bfs(const spmspv_handle* h, int early_exit, int only_pull, cudaStream_t s,
+                                 cudaGraphConditionalHandle cond);
 int pull_available(const spmspv_handle* h, int sem);
 
 namespace {
 
 // Start of a search: every vertex unreached, the source at level 0.
+// keep_fb: the search may run pull levels, which read the last level's
+// frontier bitmap (kept only then: the push levels skip its upkeep otherwise).
 __global__ void k_bfs_init(int32_t n, int32_t src, int32_t* __restrict__ level,
                            int32_t* __restrict__ parent, uint32_t* __restrict__ visited,
-                           uint32_t* __restrict__ fb, int32_t* __restrict__ front, DevState* st) {
+                           uint32_t* __restrict__ fb, int32_t* __restrict__ front, DevState* st,
+                           int keep_fb) {
   const int32_t words = (n + 31) / 32;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     level[i] = i == src ? 0 : -1;
@@ -52,31 +56,30 @@ __global__ void k_bfs_init(int32_t n, int32_t src, int32_t* __restrict__ level,
     st->nvisited = 1;
     st->bfs_level = level;
     st->bfs_parent = parent;
-    st->bfs_fb = fb;
+    st->bfs_fb = keep_fb ? fb : nullptr;
+    st->bfs_front = front;
   }
-}
-
-// Loop condition: another level while the last one found vertices.
-__global__ void k_bfs_continue(cudaGraphConditionalHandle cond, const DevState* st, int32_t n) {
-  if (threadIdx.x == 0) cudaGraphSetConditional(cond, (st->nnz_y > 0 && st->level <= n) ? 1u : 0u);
 }
 
 }  // namespace
 
-static int bfs_push_launches(spmspv_handle* h, const Sched& sc, int lwb, cudaStream_t s, int only_push) {
+// device_sched: the work scan picks the schedule, so K2 must not be the
+// variant compiled for one work quantum.
+static int bfs_push_launches(spmspv_handle* h, const Sched& sc, int lwb, cudaStream_t s, int only_push,
+                             bool device_sched, cudaGraphConditionalHandle cond) {
   const size_t k3_smem = k3_smem_bytes(lwb);
   const int nb_max = (int)(((int64_t)h->A.m + (1 << h->lwb_lo) - 1) >> h->lwb_lo);
   const int k3_grid = std::max(1, std::min(nb_max, h->sm_count * h->k3_bps[lwb - h->lwb_lo]));
   cudaError_t e = launch_k2(kMinSelect2nd, h->A, h->ws, h->lwb_lo, h->nb_fine, h->bfs_visited, 1,
-                            h->k2_grid, h->k2_smem, s, only_push, only_push ? 0 : sc.q);
+                            h->k2_grid, h->k2_smem, s, only_push, device_sched ? 0 : sc.q, BFS_DIRECT_MAX);
   if (e != cudaSuccess) return cuda_fail(e, "bfs expand/scatter");
   e = launch_k3(kMinSelect2nd, true, h->A, h->ws, h->lwb_lo, h->nb_fine, h->bfs_front, nullptr,
-                h->A.n, nullptr, h->bfs_visited, k3_grid, k3_smem, s, only_push);
+                h->A.n, nullptr, h->bfs_visited, k3_grid, k3_smem, s, only_push, BFS_DIRECT_MAX, 1, cond);
   return e == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "bfs merge");
 }
 
-static int bfs_pull_launches(spmspv_handle* h, int only_pull, cudaStream_t s) {
-  cudaError_t e = launch_pull_rows_bfs(h, h->rows_sorted, only_pull, s);
+static int bfs_pull_launches(spmspv_handle* h, int only_pull, cudaStream_t s, cudaGraphConditionalHandle cond) {
+  cudaError_t e = launch_pull_rows_bfs(h, h->rows_sorted, only_pull, s, cond);
   return e == cudaSuccess ? SPMSPV_OK : cuda_fail(e, "bfs pull");
 }
 
@@ -99,7 +102,7 @@ static int bfs_level_launches(spmspv_handle* h, int sched, cudaGraphConditionalH
     if ((e = launch_k1_bfs(h->A, h->ws, h->nb_fine, h->bfs_front, &h->ws.st->nnz_y, h->k1_grid_dev, &sc,
                            s, nullptr)) != cudaSuccess)
       return cuda_fail(e, "bfs work scan");
-    rc = sc.dir == 0 ? bfs_push_launches(h, sc, sc.lwb, s, 0) : bfs_pull_launches(h, 0, s);
+    rc = sc.dir == 0 ? bfs_push_launches(h, sc, sc.lwb, s, 0, false, cond) : bfs_pull_launches(h, 0, s, cond);
   } else {
     // the work scan's last CTA runs the selector and sets the direction; the
     // push kernels and the pull kernel both follow and the one not chosen
@@ -113,13 +116,12 @@ static int bfs_level_launches(spmspv_handle* h, int sched, cudaGraphConditionalH
     if ((e = launch_k1_bfs(h->A, h->ws, h->nb_fine, h->bfs_front, &h->ws.st->nnz_y, h->k1_grid_dev,
                            nullptr, s, nullptr, &sa)) != cudaSuccess)
       return cuda_fail(e, "bfs work scan");
-    rc = bfs_push_launches(h, sc, h->lwb_lo + 2, s, can_pull ? 1 : 0);
-    if (rc == SPMSPV_OK && can_pull) rc = bfs_pull_launches(h, 1, s);
+    rc = bfs_push_launches(h, sc, h->lwb_lo + 2, s, can_pull ? 1 : 0, true, cond);
+    if (rc == SPMSPV_OK && can_pull) rc = bfs_pull_launches(h, 1, s, cond);
   }
-  if (rc != SPMSPV_OK) return rc;
-  k_bfs_continue<<<1, 32, 0, s>>>(cond, h->ws.st, h->A.n);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "bfs condition");
-  return SPMSPV_OK;
+  // the kernel that closes the level (K3, or the pull kernel) sets the loop's
+  // condition: no launch of its own
+  return rc;
 }
 
 // Graph with one WHILE node whose body is one level.
@@ -237,8 +239,9 @@ extern "C" int spmspv_bfs(spmspv_handle* h, int32_t src, int32_t* level, int32_t
   h->last_stream = s;
   h->last_empty = 0;
   const int grid = std::max(1, std::min(h->sm_count * 8, (h->A.n + 255) / 256));
+  const bool pulls = pull_available(h, kMinSelect2nd) && (sched < 0 || sched >= SPMSPV_NUM_SCHEDULES / 2);
   k_bfs_init<<<grid, 256, 0, s>>>(h->A.n, src, level, parent, h->bfs_visited, h->bfs_fb, h->bfs_front,
-                                  h->ws.st);
+                                  h->ws.st, pulls ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "bfs init");
   if ((e = cudaGraphLaunch((cudaGraphExec_t)h->bfs_graph[slot], s)) != cudaSuccess)

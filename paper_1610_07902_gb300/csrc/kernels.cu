@@ -89,6 +89,7 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
       st->f = f;
       st->k3_ticket = 0u;
       st->feat_dev = 0;
+      st->bfs_acc = 0;
       if (forced) {
         st->dir = f_dir;
         st->q = f_q;
@@ -110,6 +111,9 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
       }
     }
   }
+  // a CTA beyond the tiles has nothing to do unless it counts mask bits (the
+  // others take every tile: the tickets are dynamic)
+  if (blockIdx.x > 0 && blockIdx.x >= nt1 && !mask) return;
   if (tid == 0) {
     s_maxdeg = 0;
     s_maskcnt = 0;
@@ -293,20 +297,200 @@ __device__ __forceinline__ void spa_apply(uint32_t* spa, uint32_t r, uint32_t v)
 // shared-memory atomics, one warp scans the counts, every non-empty bucket
 // gets one run reserved with a global atomic, the products are staged in
 // shared memory grouped by bucket (in the bytes that held the tile's x
-// entries, so that three 512-thread CTAs fit per SM) and written out in runs.
-// Hub rows (row ids >= m in the relabelled row-id array) are summed per tile
-// in shared memory instead.
+// entries) and written out in runs.  Hub rows (row ids >= m in the
+// relabelled row-id array) are one more bucket of the histogram, the last:
+// they are staged like the others and then summed into a per-CTA table in
+// shared memory that is flushed once, when the CTA has no tile left, so a
+// hub product costs what any product costs and no warp branches on it.
 // IT: products per thread when the host knows the work quantum (4 or 8),
 // 0 when the device decides it; MASKED: a mask may be given.
+
+// The products of one warp's chunk: entry lookup, coalesced loads of row ids
+// and values, the multiply (FULL: the tile holds items*K2_THREADS products,
+// no bounds test).
+template <int SEM, int IT, bool FULL>
+__device__ __forceinline__ void k2_gather(const int32_t* __restrict__ rowidx, const float* __restrict__ val,
+                                          const uint32_t* hbits, const int32_t* kbase, const uint32_t* kx,
+                                          int items, int warp, int lane, int32_t p0, int32_t np, int64_t nnz,
+                                          uint32_t (&rrow)[K2_IMAX], uint32_t (&rval)[K2_IMAX]) {
+  const int w0 = warp * items;  // bitmap word of this warp's first 32 products
+  const int32_t pw0 = w0 * 32 + lane;
+  int ent = 0;                  // entry starts before word w0
+  for (int j = lane; j < w0; j += 32) ent += __popc(hbits[j]);
+  ent = __reduce_add_sync(0xffffffffu, ent);
+  const uint32_t le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+  uint32_t xi[K2_IMAX];
+  float av[K2_IMAX];
+  // every item's address, then all loads in flight at once
+#pragma unroll
+  for (int i = 0; i < K2_IMAX; ++i) {
+    rrow[i] = 0xffffffffu;
+    xi[i] = 0u;
+    av[i] = 1.0f;
+    if (IT ? i < IT : i < items) {
+      const int32_t pl = pw0 + 32 * i;
+      const uint32_t hw = hbits[w0 + i];
+      const int e = ent + __popc(hw & le);
+      ent += __popc(hw);
+      if (FULL || pl < np) {
+        const int32_t pos = kbase[e] + p0 + pl;
+        xi[i] = kx[e];
+        if ((uint32_t)pos < (uint32_t)nnz) {  // always true with valid inputs
+          rrow[i] = (uint32_t)ld_stream(rowidx + pos);
+          if (SEM == kPlusTimes && val) av[i] = ld_stream(val + pos);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < K2_IMAX; ++i) {
+    uint32_t v = 0u;
+    if (SEM == kPlusTimes) {
+      v = __float_as_uint(__fmul_rn(av[i], __uint_as_float(xi[i])));
+      if (v == 0x80000000u) v = 0u;  // -0.0 -> +0.0: K3's dense SPA reserves -0.0 for "empty"
+    } else if (SEM == kMinSelect2nd) {
+      v = xi[i];
+    }
+    rval[i] = v;
+  }
+}
+
+// Bucket of a product row id: its row range, the hub bucket nb, or -1 for
+// "no product" and for an id outside [0, m) that is not a hub label (which
+// only a matrix that was never checked at create can hold).
+__device__ __forceinline__ int k2_bucket(uint32_t row, int32_t m, int nhot, int lwb, int nb) {
+  if (row < (uint32_t)m) return (int)(row >> lwb);
+  if (row - (uint32_t)m < (uint32_t)nhot) return nb;
+  return -1;
+}
+
+// A BFS level in the direct form (few products): for every product (row i,
+// frontier vertex j) with i unreached before this level, parent[i] =
+// min(parent[i], j), and level[i] = L for the first product that finds i
+// (compare-and-swap), which also appends i to the next frontier and sets its
+// visited bit.  The parent array is the SPA: it holds -1 (as unsigned, the
+// largest value) for every vertex not reached yet, so an unsigned min needs
+// no initialisation of its own.  "Unreached before this level" is read from
+// the level array (-1, or L when another product found i in this level), so
+// the visited bits set during the level change nothing and the minimum is
+// exact.  Every item's loads and atomics are issued before any result is
+// used; one global atomic per warp and tile reserves the frontier slots.
+// With the learned schedule this level's frontier bitmap is cleared here and
+// K3 sets it (a later pull level reads it).
+template <int IT>
+__device__ void k2_bfs_direct(const int32_t* __restrict__ rowidx, Workspace ws, int32_t m, int64_t nnz,
+                              uint32_t* __restrict__ visited, unsigned char* smem_raw) {
+  const DevState* st = ws.st;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int32_t W = st->W, fc = st->fc, q = st->q;
+  const int items = IT ? IT : q / K2_THREADS;
+  const int ntiles = (int)(((int64_t)W + q - 1) / q);
+  const int nhot = ws.nhot;
+  const Job* job = ws.job;
+  const int32_t L = job ? job->lvl : st->level;
+  int32_t* level = job ? job->level : st->bfs_level;
+  uint32_t* parent = reinterpret_cast<uint32_t*>(job ? job->parent : st->bfs_parent);
+  int32_t* front = job ? job->y_idx : st->bfs_front;
+  int32_t* acc = &ws.st->bfs_acc;
+  uint32_t* fb = job ? job->fb : st->bfs_fb;
+  if (fb) {  // this level's frontier bitmap, set again by K3
+    const int64_t words = ((int64_t)m + 31) / 32;
+    fb += (L & 1) ? words : 0;
+    for (int64_t w = (int64_t)blockIdx.x * K2_THREADS + tid; w < words; w += (int64_t)gridDim.x * K2_THREADS)
+      fb[w] = 0u;
+  }
+  if ((int)blockIdx.x >= ntiles) return;  // no tile for this CTA (tiles go round-robin)
+  unsigned char* p = smem_raw;
+  int32_t* kbase = (int32_t*)p; p += sizeof(int32_t) * (QMAX + 1);
+  uint32_t* kx = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX + 1);
+  uint32_t* hbits = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX / 32);
+  int32_t* hrow = (int32_t*)p;  // hub row ids
+  for (int i = tid; i < nhot; i += K2_THREADS) hrow[i] = ws.hot_rows[i];
+  for (int i = tid; i < QMAX / 32; i += K2_THREADS) hbits[i] = 0u;
+  __syncthreads();
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int32_t p0 = t * q;
+    const int32_t np = min(q, W - p0);
+    const int32_t k0 = ws.tile_k0[p0 / QF];
+    const int32_t kend = (p0 + np == W) ? fc : ws.tile_k0[(p0 + np) / QF] + 1;
+    const int32_t nk = max(1, min(kend - k0, QMAX + 1));
+    for (int l = tid; l < nk; l += K2_THREADS) {
+      const int32_t w = ws.cw[k0 + l];
+      kbase[l] = ws.cb[k0 + l] - w;
+      kx[l] = ws.cx[k0 + l];
+      const int32_t off = w - p0;
+      if (l > 0 && off > 0 && off < np) atomicOr(&hbits[off >> 5], 1u << (off & 31));
+    }
+    __syncthreads();
+    uint32_t rrow[K2_IMAX], rval[K2_IMAX];
+    if (np == items * K2_THREADS)
+      k2_gather<kMinSelect2nd, IT, true>(rowidx, nullptr, hbits, kbase, kx, items, warp, lane, p0, np, nnz,
+                                         rrow, rval);
+    else
+      k2_gather<kMinSelect2nd, IT, false>(rowidx, nullptr, hbits, kbase, kx, items, warp, lane, p0, np, nnz,
+                                          rrow, rval);
+    // the row of every item (hub labels mapped back), then its level
+    int32_t lv[K2_IMAX];
+#pragma unroll
+    for (int i = 0; i < K2_IMAX; ++i) {
+      uint32_t row = rrow[i];
+      if (row != 0xffffffffu && row >= (uint32_t)m) {
+        if (row - (uint32_t)m < (uint32_t)nhot) {
+          row = (uint32_t)hrow[row - (uint32_t)m];
+        } else {
+          atomicOr(&ws.st->status, ST_INDEX);  // a row id outside [0, m): dropped, flagged
+          row = 0xffffffffu;
+        }
+      }
+      rrow[i] = row;
+      lv[i] = row != 0xffffffffu ? __ldcg(level + row) : 0;
+    }
+    // the semiring's add on the dense parent array, then the first finder
+    uint32_t found = 0u;
+#pragma unroll
+    for (int i = 0; i < K2_IMAX; ++i) {
+      if (rrow[i] == 0xffffffffu || (lv[i] != -1 && lv[i] != L)) continue;
+      atomicMin(parent + rrow[i], rval[i]);
+      if (lv[i] == -1 && atomicCAS(level + rrow[i], -1, L) == -1) found |= 1u << i;
+    }
+    // one frontier reservation per warp, then the new vertices
+    const int32_t c = __popc(found);
+    int32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    int32_t base = 0;
+    if (lane == 31 && incl > 0) base = atomicAdd(acc, incl);
+    base = __shfl_sync(0xffffffffu, base, 31) + incl - c;
+#pragma unroll
+    for (int i = 0; i < K2_IMAX; ++i) {
+      if (!((found >> i) & 1u)) continue;
+      const uint32_t r = rrow[i];
+      front[base++] = (int32_t)r;
+      atomicOr(visited + (r >> 5), 1u << (r & 31));
+    }
+    __syncthreads();  // the entries of the next tile overwrite this one's
+    for (int j = tid; j < QMAX / 32; j += K2_THREADS) hbits[j] = 0u;
+    __syncthreads();
+  }
+}
+
 template <int SEM, int IT, bool MASKED>
-__global__ void __launch_bounds__(K2_THREADS, 3)
+__global__ void __launch_bounds__(K2_THREADS, K2_MIN_BLOCKS)
 k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ val, Workspace ws,
                   int lwb_lo, int nb_fine, int32_t m, int64_t nnz, const uint32_t* mask,
-                  int mask_comp, int only_push) {
+                  int mask_comp, int only_push, int32_t direct_max) {
   if (only_push && ws.st->dir != 0) return;  // this call runs the pull direction
   if (ws.job) mask = ws.job->mask;
   extern __shared__ __align__(16) unsigned char k2_smem_raw[];
-  __shared__ int32_t s_kept;
+  if (SEM == kMinSelect2nd && MASKED && direct_max > 0 && ws.st->W <= direct_max) {
+    if (!ws.job || ws.job->b >= 0)
+      k2_bfs_direct<IT>(rowidx, ws, m, nnz, const_cast<uint32_t*>(mask), k2_smem_raw);
+    return;
+  }
+  __shared__ int32_t s_kept, s_kept_n;
 
   unsigned char* p = k2_smem_raw;
   // the staged products of a tile share their bytes with the tile's x entries
@@ -315,11 +499,11 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
   int32_t* kbase = (int32_t*)p; p += sizeof(int32_t) * (QMAX + 1);
   uint32_t* kx = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX + 1);
   uint32_t* hbits = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX / 32);  // entry starts of the tile
-  int32_t* hist = (int32_t*)p; p += sizeof(int32_t) * nb_fine;   // counts, then stage offsets
-  int32_t* gd = (int32_t*)p; p += sizeof(int32_t) * nb_fine;     // counts, then slot - stage offset
-  uint32_t* hacc = (uint32_t*)p;                                 // hub sums of this tile
-  int32_t* hrow = (int32_t*)(hacc + HOT_MAX);                    // hub row ids
-  uint32_t* htb = (uint32_t*)(hrow + HOT_MAX);                   // hub touched bits
+  int32_t* hist = (int32_t*)p; p += sizeof(int32_t) * (nb_fine + 1);  // counts, then stage offsets
+  int32_t* gd = (int32_t*)p; p += sizeof(int32_t) * (nb_fine + 1);    // counts, then slot - stage offset
+  uint32_t* hacc = (uint32_t*)p;                                      // hub sums of this CTA
+  int32_t* hrow = (int32_t*)(hacc + HOT_MAX);                         // hub row ids
+  uint32_t* htb = (uint32_t*)(hrow + HOT_MAX);                        // hub touched bits
 
   const DevState* st = ws.st;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -331,11 +515,12 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
   const int ntiles = (int)(((int64_t)W + q - 1) / q);
   const uint32_t ident = sr_identity<SEM>();
   const int nhot = ws.nhot;
+  if ((int)blockIdx.x >= ntiles) return;  // no tile for this CTA (tiles go round-robin)
 
   if (nhot > 0) {
     for (int i = tid; i < HOT_MAX; i += K2_THREADS) {
       hacc[i] = ident;
-      hrow[i] = ws.hot_rows[i];
+      if (MASKED) hrow[i] = ws.hot_rows[i];
     }
     for (int i = tid; i < HOT_MAX / 32; i += K2_THREADS) htb[i] = 0u;
   }
@@ -359,80 +544,35 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
       const int32_t off = w - p0;  // entries after the first start inside the tile
       if (l > 0 && off > 0 && off < np) atomicOr(&hbits[off >> 5], 1u << (off & 31));
     }
-    for (int b = tid; b < nb; b += K2_THREADS) hist[b] = 0;
+    for (int b = tid; b <= nb; b += K2_THREADS) hist[b] = 0;
     __syncthreads();
 
     // ---- gather, multiply, filter, count per bucket ----
     uint32_t rrow[K2_IMAX], rval[K2_IMAX];
     int32_t rank[K2_IMAX];
-    {
-      const int w0 = warp * items;  // bitmap word of this warp's first 32 products
-      const int32_t pw0 = w0 * 32 + lane;
-      int ent = 0;                  // entry starts before word w0
-      for (int j = lane; j < w0; j += 32) ent += __popc(hbits[j]);
-      ent = __reduce_add_sync(0xffffffffu, ent);
-      const uint32_t le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
-      // phase 1: every item's address, then all loads in flight at once
-      uint32_t xi[K2_IMAX];
-      float av[K2_IMAX];
+    if (np == items * K2_THREADS)  // every item of every warp holds a product
+      k2_gather<SEM, IT, true>(rowidx, val, hbits, kbase, kx, items, warp, lane, p0, np, nnz, rrow, rval);
+    else
+      k2_gather<SEM, IT, false>(rowidx, val, hbits, kbase, kx, items, warp, lane, p0, np, nnz, rrow, rval);
 #pragma unroll
-      for (int i = 0; i < K2_IMAX; ++i) {
-        const int32_t pl = pw0 + 32 * i;
-        rrow[i] = 0xffffffffu;
-        xi[i] = 0u;
-        av[i] = 1.0f;
-        const uint32_t hw = i < items ? hbits[w0 + i] : 0u;
-        const int e = ent + __popc(hw & le);
-        ent += __popc(hw);
-        if (i < items && pl < np) {
-          const int32_t pos = kbase[e] + p0 + pl;
-          xi[i] = kx[e];
-          if ((uint32_t)pos < (uint32_t)nnz) {  // always true with valid inputs
-            rrow[i] = (uint32_t)ld_stream(rowidx + pos);
-            if (SEM == kPlusTimes && val) av[i] = ld_stream(val + pos);
-          }
-        }
+    for (int i = 0; i < K2_IMAX; ++i) {
+      rank[i] = -1;
+      const uint32_t row = rrow[i];
+      const int b = k2_bucket(row, m, nhot, lwb, nb);
+      if (b < 0) {
+        if (row != 0xffffffffu) atomicOr(&ws.st->status, ST_INDEX);  // dropped, flagged
+        continue;
       }
-      // phase 2: multiply, filter, count per bucket
-#pragma unroll
-      for (int i = 0; i < K2_IMAX; ++i) {
-        rank[i] = -1;
-        const uint32_t row = rrow[i];
-        uint32_t v = 0u;
-        if (SEM == kPlusTimes) v = __float_as_uint(__fmul_rn(av[i], __uint_as_float(xi[i])));
-        else if (SEM == kMinSelect2nd) v = xi[i];
-        rval[i] = v;
-        if (row == 0xffffffffu) continue;
-        if (row < (uint32_t)m) {
-          bool keep = true;
-          if (MASKED && mask) {
-            const uint32_t bit = (__ldg(mask + (row >> 5)) >> (row & 31)) & 1u;
-            keep = mask_comp ? (bit == 0u) : (bit != 0u);
-          }
-          if (keep) rank[i] = atomicAdd(&hist[row >> lwb], 1);
-        } else if (row - (uint32_t)m >= (uint32_t)nhot) {
-          // a row id outside [0, m) that is not a hub label (only a matrix
-          // that was never checked at create can hold one): dropped, flagged
-          atomicOr(&ws.st->status, ST_INDEX);
-        } else {
-          // a hub row: combine its products of this tile in shared memory
-          const int hs = (int)row - m;
-          const int32_t orow = hrow[hs];
-          bool keep = true;
-          if (MASKED && mask) {
-            const uint32_t bit = (__ldg(mask + (orow >> 5)) >> (orow & 31)) & 1u;
-            keep = mask_comp ? (bit == 0u) : (bit != 0u);
-          }
-          if (keep) {
-            spa_apply<SEM>(hacc, (uint32_t)hs, v);
-            const uint32_t bit = 1u << (hs & 31);
-            if (!(htb[hs >> 5] & bit)) atomicOr(&htb[hs >> 5], bit);
-          }
-        }
+      bool keep = true;
+      if (MASKED && mask) {
+        const uint32_t r = b < nb ? row : (uint32_t)hrow[row - (uint32_t)m];
+        const uint32_t bit = (__ldg(mask + (r >> 5)) >> (r & 31)) & 1u;
+        keep = mask_comp ? (bit == 0u) : (bit != 0u);
       }
+      if (keep) rank[i] = atomicAdd(&hist[b], 1);
     }
     __syncthreads();
-    for (int j = tid; j < QMAX / 32; j += K2_THREADS) hbits[j] = 0u;  // phase 1 is done
+    for (int j = tid; j < QMAX / 32; j += K2_THREADS) hbits[j] = 0u;  // the gather is done
 
     // ---- the next tile's x entries: in flight during this tile's scan,
     // reservation and stores, written to shared memory before the write-out ----
@@ -452,10 +592,11 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
       }
     }
 
-    // ---- one warp scans the bucket counts; the other warps flush hub sums ----
+    // ---- one warp scans the bucket counts (the hub bucket last) ----
     if (warp == 0) {
-      const int per = (nb + 31) >> 5;
-      const int b0 = lane * per, b1 = min(b0 + per, nb);
+      const int nbh = nb + 1;
+      const int per = (nbh + 31) >> 5;
+      const int b0 = lane * per, b1 = min(b0 + per, nbh);
       int32_t sum = 0;
       for (int b = b0; b < b1; ++b) sum += hist[b];
       int32_t x = sum;
@@ -468,20 +609,10 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
       if (lane == 31) s_kept = x;
       for (int b = b0; b < b1; ++b) {
         const int32_t c = hist[b];
+        if (b == nb) s_kept_n = run;
         gd[b] = c;
         hist[b] = run;
         run += c;
-      }
-    } else if (nhot > 0) {
-      for (int hs = tid - 32; hs < nhot; hs += K2_THREADS - 32) {
-        if ((htb[hs >> 5] >> (hs & 31)) & 1u) {
-          if (SEM == kPlusTimes)
-            atomicAdd(reinterpret_cast<float*>(ws.hot_val + hs), __uint_as_float(hacc[hs]));
-          else if (SEM == kMinSelect2nd)
-            atomicMin(reinterpret_cast<int*>(ws.hot_val + hs), (int)hacc[hs]);
-          ws.hot_touch[hs] = 1u;
-          hacc[hs] = ident;
-        }
       }
     }
     __syncthreads();
@@ -503,18 +634,25 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
     // ---- stage the products grouped by bucket ----
 #pragma unroll
     for (int i = 0; i < K2_IMAX; ++i)
-      if (rank[i] >= 0) stage[hist[rrow[i] >> lwb] + rank[i]] = make_uint2(rrow[i], rval[i]);
-    if (nhot > 0 && warp == 1) htb[lane] = 0u;
+      if (rank[i] >= 0)
+        stage[hist[k2_bucket(rrow[i], m, nhot, lwb, nb)] + rank[i]] = make_uint2(rrow[i], rval[i]);
     __syncthreads();
-    // ---- write the runs to the buckets ----
-    const int32_t kept = s_kept;
+    // ---- write the runs to the buckets; sum the hub products ----
+    const int32_t kept_n = s_kept_n, kept = s_kept;
     for (int32_t s = tid; s < kept; s += K2_THREADS) {
       const uint2 e = stage[s];
-      const int32_t g = gd[e.x >> lwb];
-      if (g == INT32_MIN) continue;
-      const int32_t dst = g + s;
-      ws.brow[dst] = (uint16_t)(e.x & wmask);
-      if (SEM != kOrAnd) ws.bval[dst] = e.y;
+      if (s < kept_n) {
+        const int32_t g = gd[e.x >> lwb];
+        if (g == INT32_MIN) continue;
+        const int32_t dst = g + s;
+        ws.brow[dst] = (uint16_t)(e.x & wmask);
+        if (SEM != kOrAnd) ws.bval[dst] = e.y;
+      } else {
+        const uint32_t hs = e.x - (uint32_t)m;
+        spa_apply<SEM>(hacc, hs, e.y);
+        const uint32_t bit = 1u << (hs & 31);
+        if (!(htb[hs >> 5] & bit)) atomicOr(&htb[hs >> 5], bit);
+      }
     }
     __syncthreads();  // the staged products are written out: their bytes take the next entries
     if (tid < nkn) {  // the next tile's first entries (loaded during this tile)
@@ -524,26 +662,41 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
       if (tid > 0 && off > 0 && off < npn) atomicOr(&hbits[off >> 5], 1u << (off & 31));
     }
   }
+  // ---- the CTA's hub sums, once ----
+  if (nhot > 0) {
+    __syncthreads();
+    for (int hs = tid; hs < nhot; hs += K2_THREADS) {
+      if ((htb[hs >> 5] >> (hs & 31)) & 1u) {
+        if (SEM == kPlusTimes)
+          atomicAdd(reinterpret_cast<float*>(ws.hot_val + hs), __uint_as_float(hacc[hs]));
+        else if (SEM == kMinSelect2nd)
+          atomicMin(reinterpret_cast<int*>(ws.hot_val + hs), (int)hacc[hs]);
+        ws.hot_touch[hs] = 1u;
+      }
+    }
+  }
 }
 
 template <int SEM>
 static void k2_variant(int it, bool masked, int grid, size_t smem, cudaStream_t s, const int32_t* rows,
                        const float* val, const Workspace& ws, int lwb_lo, int nb_fine, const Matrix& A,
-                       const uint32_t* mask, int mask_comp, int only_push) {
+                       const uint32_t* mask, int mask_comp, int only_push, int32_t direct_max) {
 #define K2_GO(I, M)                                                                              \
   k2_expand_scatter<SEM, I, M><<<grid, K2_THREADS, smem, s>>>(rows, val, ws, lwb_lo, nb_fine, A.m, \
-                                                              A.nnz, mask, mask_comp, only_push)
+                                                              A.nnz, mask, mask_comp, only_push,  \
+                                                              direct_max)
+  constexpr int I1 = K2_IMAX, I2 = K2_IMAX / 2;
   if (masked) {
-    if (it == 8) K2_GO(8, true); else if (it == 4) K2_GO(4, true); else K2_GO(0, true);
+    if (it == I1) K2_GO(I1, true); else if (it == I2) K2_GO(I2, true); else K2_GO(0, true);
   } else {
-    if (it == 8) K2_GO(8, false); else if (it == 4) K2_GO(4, false); else K2_GO(0, false);
+    if (it == I1) K2_GO(I1, false); else if (it == I2) K2_GO(I2, false); else K2_GO(0, false);
   }
 #undef K2_GO
 }
 
 cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo, int nb_fine,
                       const uint32_t* mask, int mask_comp, int grid, size_t smem, cudaStream_t s,
-                      int only_push, int q_hint) {
+                      int only_push, int q_hint, int32_t direct_max) {
   const int32_t* rows = ws.nhot > 0 ? ws.rowidx_k2 : A.rowidx;
   // the batched lanes take their masks from the job: compile the mask path in
   const bool masked = mask != nullptr || ws.job != nullptr;
@@ -551,15 +704,15 @@ cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo,
   switch (sem) {
     case kPlusTimes:
       k2_variant<kPlusTimes>(it, masked, grid, smem, s, rows, A.val, ws, lwb_lo, nb_fine, A, mask,
-                             mask_comp, only_push);
+                             mask_comp, only_push, 0);
       break;
     case kMinSelect2nd:
       k2_variant<kMinSelect2nd>(it, masked, grid, smem, s, rows, nullptr, ws, lwb_lo, nb_fine, A, mask,
-                                mask_comp, only_push);
+                                mask_comp, only_push, masked ? direct_max : 0);
       break;
     default:
       k2_variant<kOrAnd>(it, masked, grid, smem, s, rows, nullptr, ws, lwb_lo, nb_fine, A, mask,
-                         mask_comp, only_push);
+                         mask_comp, only_push, 0);
   }
   return cudaGetLastError();
 }
@@ -567,10 +720,63 @@ cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo,
 // ------------------------------------------------------------------------
 // K3: per-bucket SPA merge + ordered compaction (+ BFS update)
 // ------------------------------------------------------------------------
+// Two merge forms, chosen per bucket (the choice is uniform in the CTA):
+//   dense   (many entries): every SPA slot starts at an "empty" value that no
+//           merge can produce, so the semiring's add is the only shared-memory
+//           update per entry and the occupied rows are read back from the SPA
+//           itself.  (+,*): empty = -0.0f (K2 stores +0.0 for a -0.0 product,
+//           and -0.0 + p == p, so a touched row never holds -0.0);
+//           (min,select2nd) in BFS: empty = INT32_MAX (x values are vertex ids).
+//           The compaction walks the SPA 32 rows per warp step (ballot).
+//   sparse  (few entries, or no free empty value): an occupancy bitmap next to
+//           the SPA, partially initialised (Sec. II-F), compacted per word.
+constexpr int K3_WARPS = K3_THREADS / 32;
+constexpr int K3_DENSE_MIN_WB = 32 * K3_WARPS;  // every warp walks whole 32-row words
+constexpr int K3_DENSE_DIV = 8;                 // dense when entries >= rows / 8
+
+template <int SEM>
+__device__ __forceinline__ uint32_t spa_empty() {
+  return SEM == kPlusTimes ? 0x80000000u : 0x7fffffffu;
+}
+
+// The end of a BFS level that K2 ran in the direct form: the level's count,
+// the per-call state the work scan starts from, and (when a later level may
+// pull) the new frontier's bits in this level's frontier bitmap.
+__device__ void k3_bfs_direct_close(Workspace ws, int32_t m, const int32_t* y_idx, int32_t* d_nnz_y,
+                                    int use_cond, cudaGraphConditionalHandle cond) {
+  DevState* st = ws.st;
+  const int tid = threadIdx.x;
+  const int32_t total = st->bfs_acc;
+  if (blockIdx.x == 0) {
+    if (tid == 0) {
+      if (use_cond) cudaGraphSetConditional(cond, (total > 0 && st->level <= m) ? 1u : 0u);
+      st->k1_ticket = 0u;
+      st->last_maxdeg = st->maxdeg;
+      st->last_maskcnt = st->maskcnt;
+      st->maxdeg = 0;
+      st->maskcnt = 0;
+      st->nnz_y = total;
+      st->nvisited += total;
+      if (d_nnz_y) *d_nnz_y = total;
+    }
+    const int nt1 = (st->f + K1_TILE - 1) / K1_TILE;
+    for (int i = tid; i < nt1; i += K3_THREADS) ws.k1_status[i] = 0ull;
+  }
+  const int32_t lvl = ws.job ? ws.job->lvl : st->level;
+  uint32_t* fb = ws.job ? ws.job->fb : st->bfs_fb;
+  if (!fb) return;
+  fb += (lvl & 1) ? ((int64_t)m + 31) / 32 : 0;
+  for (int32_t k = blockIdx.x * K3_THREADS + tid; k < total; k += gridDim.x * K3_THREADS) {
+    const int32_t r = y_idx[k];
+    atomicOr(fb + (r >> 5), 1u << (r & 31));
+  }
+}
+
 template <int SEM, bool BFS>
-__global__ void __launch_bounds__(K3_THREADS)
+__global__ void __launch_bounds__(K3_THREADS, 2)
 k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx, uint32_t* y_val,
-                int32_t y_cap, int32_t* d_nnz_y, uint32_t* mask_update, int only_push) {
+                int32_t y_cap, int32_t* d_nnz_y, uint32_t* mask_update, int only_push,
+                int32_t direct_max, int use_cond, cudaGraphConditionalHandle cond) {
   if (only_push && ws.st->dir != 0) return;  // this call runs the pull direction
   if (ws.job) {  // a batched lane: this frontier's outputs
     y_idx = ws.job->y_idx;
@@ -579,6 +785,11 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
     d_nnz_y = ws.job->d_nnz_y;
     if (BFS) mask_update = ws.job->visited;
   }
+  if (BFS && direct_max > 0 && ws.st->W <= direct_max) {  // K2 ran the level in the direct form
+    k3_bfs_direct_close(ws, m, y_idx, d_nnz_y, use_cond, cond);
+    return;
+  }
+  constexpr bool kDenseForm = SEM == kPlusTimes || (SEM == kMinSelect2nd && BFS);
   extern __shared__ __align__(16) uint32_t k3_smem[];
   __shared__ int32_t s_scan[K3_THREADS / 32 + 1];
   __shared__ uint32_t s_tk[2];  // this bucket's ticket and the next one's
@@ -586,7 +797,7 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
   __shared__ int32_t s_tot;
 
   DevState* st = ws.st;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int lwb = st->lwb;
   const int sh = lwb - lwb_lo;
   const int32_t wb = 1 << lwb;
@@ -596,8 +807,10 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
   uint32_t* spa = k3_smem;
   uint32_t* occ = k3_smem + wb;
   const uint32_t ident = sr_identity<SEM>();
+  const uint32_t empty = spa_empty<SEM>();
   const int wpt = nw > K3_THREADS ? nw / K3_THREADS : 1;
   const bool or_always = wb >= (1 << 15);
+  const int rpw = wb / K3_WARPS;  // dense form: rows each warp compacts
   const int32_t lvl = BFS ? (ws.job ? ws.job->lvl : st->level) : 0;
   int32_t* const level = BFS ? (ws.job ? ws.job->level : st->bfs_level) : nullptr;
   int32_t* const parent = BFS ? (ws.job ? ws.job->parent : st->bfs_parent) : nullptr;
@@ -642,16 +855,22 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
     int hot_any = 0;
     for (int hs = hs0 + tid; hs < hs1; hs += K3_THREADS) hot_any |= (int)ws.hot_touch[hs];
     const int active = __syncthreads_or(cnt > 0 || hot_any);
+    const bool dense = kDenseForm && wb >= K3_DENSE_MIN_WB && (int64_t)cnt * K3_DENSE_DIV >= wb;
 
     if (active) {
-      for (int w = tid; w < nw; w += K3_THREADS) occ[w] = 0u;
-      if (SEM != kOrAnd) {
-        if ((int64_t)cnt * 16 < wb) {
-          // partial initialisation: only the SPA slots this bucket touches (Sec. II-F)
-          for (int32_t e = tid; e < cnt; e += K3_THREADS) spa[ws.brow[base + e] & wmask] = ident;
-          for (int hs = hs0 + tid; hs < hs1; hs += K3_THREADS) spa[ws.hot_rows[hs] - row0] = ident;
-        } else {
-          for (int r = tid; r < wb; r += K3_THREADS) spa[r] = ident;
+      if (dense) {
+        uint4* s4 = reinterpret_cast<uint4*>(spa);
+        for (int r = tid; r < (wb >> 2); r += K3_THREADS) s4[r] = make_uint4(empty, empty, empty, empty);
+      } else {
+        for (int w = tid; w < nw; w += K3_THREADS) occ[w] = 0u;
+        if (SEM != kOrAnd) {
+          if ((int64_t)cnt * 16 < wb) {
+            // partial initialisation: only the SPA slots this bucket touches (Sec. II-F)
+            for (int32_t e = tid; e < cnt; e += K3_THREADS) spa[ws.brow[base + e] & wmask] = ident;
+            for (int hs = hs0 + tid; hs < hs1; hs += K3_THREADS) spa[ws.hot_rows[hs] - row0] = ident;
+          } else {
+            for (int r = tid; r < wb; r += K3_THREADS) spa[r] = ident;
+          }
         }
       }
       __syncthreads();
@@ -691,10 +910,12 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
               const int32_t e = e0 + j;
               if (e < a0 || e >= a1) continue;
               const uint32_t rr = ((j & 1) ? (rw[j >> 1] >> 16) : (rw[j >> 1] & 0xffffu)) & wmask;
-              const uint32_t bit = 1u << (rr & 31);
-              // with one CTA per SM (the 128 KB SPA of 32768-row buckets) the
-              // dependent test costs more than the extra shared OR it saves
-              if (or_always || !(occ[rr >> 5] & bit)) atomicOr(occ + (rr >> 5), bit);
+              if (!dense) {
+                const uint32_t bit = 1u << (rr & 31);
+                // with one CTA per SM (the 128 KB SPA of 32768-row buckets) the
+                // dependent test costs more than the extra shared OR it saves
+                if (or_always || !(occ[rr >> 5] & bit)) atomicOr(occ + (rr >> 5), bit);
+              }
               spa_apply<SEM>(spa, rr, vw[j]);
             }
           }
@@ -704,7 +925,7 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
       for (int hs = hs0 + tid; hs < hs1; hs += K3_THREADS) {
         if (!ws.hot_touch[hs]) continue;
         const uint32_t rr = (uint32_t)(ws.hot_rows[hs] - row0);
-        atomicOr(occ + (rr >> 5), 1u << (rr & 31));
+        if (!dense) atomicOr(occ + (rr >> 5), 1u << (rr & 31));
         spa_apply<SEM>(spa, rr, ws.hot_val[hs]);
       }
       __syncthreads();
@@ -713,8 +934,15 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
     // unique rows of this bucket (|uind_k|), then the offset of the bucket in y
     int32_t c = 0;
     const int w0 = tid * wpt;
-    if (active && w0 < nw)
+    if (dense) {
+      // each warp counts its own run of rows (lane 0 carries the count)
+      int32_t cw = 0;
+      for (int r = warp * rpw + lane; r < (warp + 1) * rpw; r += 32)
+        cw += __popc(__ballot_sync(0xffffffffu, spa[r] != empty));
+      c = lane == 0 ? cw : 0;
+    } else if (active && w0 < nw) {
       for (int w = w0; w < w0 + wpt; ++w) c += __popc(occ[w]);
+    }
     int32_t tot;
     int32_t run = block_exclusive_sum<K3_THREADS>(c, s_scan, &tot);
     if (tid < 32) {
@@ -726,31 +954,60 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
     }
     __syncthreads();
     // Step 3: this bucket's rows, ascending, at its offset in y
-    if (active && w0 < nw) {
-      int64_t pos = (int64_t)s_off + run;
-      for (int w = w0; w < w0 + wpt; ++w) {
-        uint32_t bits = occ[w];
-        if (BFS && bits) mask_update[(int64_t)b * nw + w] |= bits;
-        while (bits) {
-          const int r = (w << 5) + __ffs(bits) - 1;
-          bits &= bits - 1u;
+    if (dense) {
+      int64_t pos = (int64_t)s_off + __shfl_sync(0xffffffffu, run, 0);
+      const uint32_t lt = (1u << lane) - 1u;
+      for (int r0w = warp * rpw; r0w < (warp + 1) * rpw; r0w += 32) {
+        const int r = r0w + lane;
+        const uint32_t v = spa[r];
+        const bool hit = v != empty;
+        const uint32_t bits = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+          const int64_t p = pos + __popc(bits & lt);
           const int32_t i = row0 + r;
-          if (pos < y_cap) {
-            y_idx[pos] = i;
-            if (SEM != kOrAnd && y_val) y_val[pos] = spa[r];
+          if (p < y_cap) {
+            y_idx[p] = i;
+            if (y_val) y_val[p] = v;
           }
           if (BFS) {
             level[i] = lvl;
-            parent[i] = (int32_t)spa[r];
+            parent[i] = (int32_t)v;
           }
-          ++pos;
+        }
+        if (BFS && lane == 0) {
+          const int64_t gw = (int64_t)b * nw + (r0w >> 5);
+          if (bits) mask_update[gw] |= bits;
+          if (fbn && gw < fb_words) fbn[gw] = bits;
+        }
+        pos += __popc(bits);
+      }
+    } else {
+      if (active && w0 < nw) {
+        int64_t pos = (int64_t)s_off + run;
+        for (int w = w0; w < w0 + wpt; ++w) {
+          uint32_t bits = occ[w];
+          if (BFS && bits) mask_update[(int64_t)b * nw + w] |= bits;
+          while (bits) {
+            const int r = (w << 5) + __ffs(bits) - 1;
+            bits &= bits - 1u;
+            const int32_t i = row0 + r;
+            if (pos < y_cap) {
+              y_idx[pos] = i;
+              if (SEM != kOrAnd && y_val) y_val[pos] = spa[r];
+            }
+            if (BFS) {
+              level[i] = lvl;
+              parent[i] = (int32_t)spa[r];
+            }
+            ++pos;
+          }
         }
       }
-    }
-    if (BFS && fbn && w0 < nw) {
-      for (int w = w0; w < w0 + wpt; ++w) {
-        const int64_t gw = (int64_t)b * nw + w;
-        if (gw < fb_words) fbn[gw] = active ? occ[w] : 0u;
+      if (BFS && fbn && w0 < nw) {
+        for (int w = w0; w < w0 + wpt; ++w) {
+          const int64_t gw = (int64_t)b * nw + w;
+          if (gw < fb_words) fbn[gw] = active ? occ[w] : 0u;
+        }
       }
     }
     if (b == (uint32_t)nb - 1u && tid == 0) {
@@ -759,6 +1016,8 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
       if (BFS) st->nvisited += (int32_t)total;
       if (d_nnz_y) *d_nnz_y = (int32_t)total;
       if (total > y_cap) atomicOr(&st->status, ST_CAPACITY);
+      // a BFS graph's loop: another level while this one found vertices
+      if (BFS && use_cond) cudaGraphSetConditional(cond, (total > 0 && st->level <= m) ? 1u : 0u);
     }
     __syncthreads();
   }
@@ -766,8 +1025,10 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
 
 cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, int lwb_lo,
                       int nb_fine, int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y,
-                      uint32_t* mask_update, int grid, size_t smem, cudaStream_t s, int only_push) {
-#define K3_ARGS ws, lwb_lo, nb_fine, A.m, y_idx, y_val, y_cap, d_nnz_y, mask_update, only_push
+                      uint32_t* mask_update, int grid, size_t smem, cudaStream_t s, int only_push,
+                      int32_t direct_max, int use_cond, cudaGraphConditionalHandle cond) {
+#define K3_ARGS ws, lwb_lo, nb_fine, A.m, y_idx, y_val, y_cap, d_nnz_y, mask_update, only_push, \
+                bfs ? direct_max : 0, bfs ? use_cond : 0, cond
   if (bfs) {
     k3_bucket_merge<kMinSelect2nd, true><<<grid, K3_THREADS, smem, s>>>(K3_ARGS);
   } else if (sem == kPlusTimes) {
@@ -899,13 +1160,13 @@ cudaError_t set_kernel_attributes(size_t k2_smem, size_t k3_smem_max) {
 #define SET(fn, bytes)                                                                      \
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes)); \
   if (e != cudaSuccess) return e;
-#define SET_K2(S)                                  \
-  SET((k2_expand_scatter<S, 0, false>), k2_smem);  \
-  SET((k2_expand_scatter<S, 4, false>), k2_smem);  \
-  SET((k2_expand_scatter<S, 8, false>), k2_smem);  \
-  SET((k2_expand_scatter<S, 0, true>), k2_smem);   \
-  SET((k2_expand_scatter<S, 4, true>), k2_smem);   \
-  SET((k2_expand_scatter<S, 8, true>), k2_smem);
+#define SET_K2(S)                                            \
+  SET((k2_expand_scatter<S, 0, false>), k2_smem);            \
+  SET((k2_expand_scatter<S, K2_IMAX / 2, false>), k2_smem);  \
+  SET((k2_expand_scatter<S, K2_IMAX, false>), k2_smem);      \
+  SET((k2_expand_scatter<S, 0, true>), k2_smem);             \
+  SET((k2_expand_scatter<S, K2_IMAX / 2, true>), k2_smem);   \
+  SET((k2_expand_scatter<S, K2_IMAX, true>), k2_smem);
   SET_K2(kPlusTimes)
   SET_K2(kMinSelect2nd)
   SET_K2(kOrAnd)

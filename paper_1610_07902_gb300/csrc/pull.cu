@@ -69,7 +69,7 @@ k_pull_rows(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowi
             int early_exit, int32_t* __restrict__ y_idx, uint32_t* __restrict__ y_val,
             int32_t y_cap, int32_t* __restrict__ d_nnz_y, uint32_t* visited,  // a BFS passes one
                                                                             // bitmap as mask and visited
-            Workspace ws, int ntiles, int only_pull) {
+            Workspace ws, int ntiles, int only_pull, int use_cond, cudaGraphConditionalHandle cond) {
   __shared__ uint32_t s_val[PULL_THREADS * 33];
   __shared__ int32_t s_scan[PULL_THREADS / 32 + 1];
   __shared__ uint32_t s_tile;
@@ -214,6 +214,8 @@ k_pull_rows(const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowi
       if (BFS) st->nvisited += (int32_t)total;
       if (d_nnz_y) *d_nnz_y = (int32_t)total;
       if (total > y_cap) atomicOr(&st->status, ST_CAPACITY);
+      // a BFS graph's loop: another level while this one found vertices
+      if (BFS && use_cond) cudaGraphSetConditional(cond, (total > 0 && st->level <= m) ? 1u : 0u);
     }
     __syncthreads();
   }
@@ -242,7 +244,7 @@ cudaError_t launch_pull(const spmspv_handle* h, int sem, bool bfs, const int32_t
   if (e != cudaSuccess) return e;
   const int grid = std::max(1, std::min(h->pull_tiles, h->sm_count * 8));
 #define PULL_ARGS h->A.colptr, h->A.rowidx, h->A.val, m, h->xbits, h->xdense, mask, mask_comp, \
-                  early_exit, y_idx, y_val, y_cap, d_nnz_y, visited, h->ws, h->pull_tiles, only_pull
+                  early_exit, y_idx, y_val, y_cap, d_nnz_y, visited, h->ws, h->pull_tiles, only_pull, 0, 0
   if (bfs) k_pull_rows<kMinSelect2nd, true><<<grid, PULL_THREADS, 0, s>>>(PULL_ARGS);
   else if (sem == kPlusTimes) k_pull_rows<kPlusTimes, false><<<grid, PULL_THREADS, 0, s>>>(PULL_ARGS);
   else if (sem == kMinSelect2nd) k_pull_rows<kMinSelect2nd, false><<<grid, PULL_THREADS, 0, s>>>(PULL_ARGS);
@@ -257,11 +259,15 @@ cudaError_t launch_pull(const spmspv_handle* h, int sem, bool bfs, const int32_t
 // BFS level in the pull direction: the frontier is the previous level's
 // bitmap (written by K3 or by this kernel), so only the row kernel runs; the
 // work scan of the level has reset the pull look-back state.
-cudaError_t launch_pull_rows_bfs(const spmspv_handle* h, int early_exit, int only_pull, cudaStream_t s) {
-  const int grid = std::max(1, std::min(h->pull_tiles, h->sm_count * 8));
+cudaError_t launch_pull_rows_bfs(const spmspv_handle* h, int early_exit, int only_pull, cudaStream_t s,
+                                 cudaGraphConditionalHandle cond) {
+  // a persistent grid: the tiles are handed out by a ticket, and when the
+  // learned schedule picks push the kernel's CTAs only start and return
+  const int grid = std::max(1, std::min(h->pull_tiles, h->sm_count * (only_pull ? 2 : 8)));
   k_pull_rows<kMinSelect2nd, true><<<grid, PULL_THREADS, 0, s>>>(
       h->A.colptr, h->A.rowidx, h->A.val, h->A.m, nullptr, nullptr, h->bfs_visited, 1, early_exit,
-      h->bfs_front, nullptr, h->A.n, &h->ws.st->nnz_y, h->bfs_visited, h->ws, h->pull_tiles, only_pull);
+      h->bfs_front, nullptr, h->A.n, &h->ws.st->nnz_y, h->bfs_visited, h->ws, h->pull_tiles, only_pull,
+      1, cond);
   return cudaGetLastError();
 }
 
@@ -270,7 +276,7 @@ cudaError_t launch_pull_rows_lane(const spmspv_handle* sub, int early_exit, cuda
   const int grid = std::max(1, std::min(sub->pull_tiles, sub->sm_count * 2));
   k_pull_rows<kMinSelect2nd, true><<<grid, PULL_THREADS, 0, s>>>(
       sub->A.colptr, sub->A.rowidx, sub->A.val, sub->A.m, nullptr, nullptr, nullptr, 1, early_exit,
-      nullptr, nullptr, 0, nullptr, nullptr, sub->ws, sub->pull_tiles, 1);
+      nullptr, nullptr, 0, nullptr, nullptr, sub->ws, sub->pull_tiles, 1, 0, 0);
   return cudaGetLastError();
 }
 

@@ -14,10 +14,13 @@
 // W3[12][32] b3[12], then the feature normalisation mean[6] and scale[6].
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
 #include <cmath>
+#include <string>
 #include <vector>
 
 #include "handle.cuh"
@@ -139,6 +142,51 @@ extern "C" int spmspv_selector_set(spmspv_handle* h, const float* params, int32_
   if (e != cudaSuccess) return cuda_fail(e, "selector weights copy");
   h->sel_ready = 1;
   return SPMSPV_OK;
+}
+
+// Parameters from a weights file: a JSON object whose "params" member is an
+// array of SPMSPV_SELECTOR_NPARAM numbers (the file selector.py writes; any
+// other members, such as "nparam" and "meta", are ignored here).  The parse
+// is a plain scan: find the "params" key, then read numbers between '[' and
+// ']' with strtod.
+static int read_selector_file(const char* path, std::vector<float>& out) {
+  FILE* fp = fopen(path, "rb");
+  if (!fp) return fail(SPMSPV_ERR_ARG, "cannot open selector weights file %s", path);
+  std::string text;
+  char buf[65536];
+  size_t got;
+  while ((got = fread(buf, 1, sizeof(buf), fp)) > 0) text.append(buf, got);
+  fclose(fp);
+  const size_t key = text.find("\"params\"");
+  if (key == std::string::npos) return fail(SPMSPV_ERR_ARG, "%s has no \"params\" member", path);
+  size_t i = text.find('[', key);
+  if (i == std::string::npos) return fail(SPMSPV_ERR_ARG, "%s: \"params\" is not an array", path);
+  ++i;
+  out.clear();
+  for (;;) {
+    while (i < text.size() && (text[i] == ' ' || text[i] == '\n' || text[i] == '\r' || text[i] == '\t' ||
+                               text[i] == ','))
+      ++i;
+    if (i >= text.size()) return fail(SPMSPV_ERR_ARG, "%s: unterminated \"params\" array", path);
+    if (text[i] == ']') break;
+    char* end = nullptr;
+    const double v = strtod(text.c_str() + i, &end);
+    if (end == text.c_str() + i) return fail(SPMSPV_ERR_ARG, "%s: not a number at byte %zu", path, i);
+    out.push_back((float)v);
+    i = (size_t)(end - text.c_str());
+  }
+  if ((int)out.size() != SEL_NPARAM)
+    return fail(SPMSPV_ERR_ARG, "%s holds %zu selector parameters, expected %d", path, out.size(), SEL_NPARAM);
+  return SPMSPV_OK;
+}
+
+extern "C" int spmspv_selector_load(spmspv_handle* h, const char* path) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!path) return fail(SPMSPV_ERR_ARG, "path is NULL");
+  std::vector<float> p;
+  if ((rc = read_selector_file(path, p)) != SPMSPV_OK) return rc;
+  return spmspv_selector_set(h, p.data(), (int32_t)p.size());
 }
 
 extern "C" int spmspv_selector_get(spmspv_handle* h, float* params, int32_t n) {

@@ -24,6 +24,7 @@ constexpr int K1_TILE = K1_THREADS * K1_ITEMS;  // x entries per scan tile
 // 2*QF products (the "work quantum" of the schedule).
 constexpr int QF = 2048;
 constexpr int K2_THREADS = 512;
+constexpr int K2_MIN_BLOCKS = 2;             // resident CTAs per SM the register budget allows
 constexpr int K2_IMAX = 8;                   // products per thread at q = 4096
 constexpr int QMAX = K2_THREADS * K2_IMAX;   // 4096
 
@@ -34,6 +35,11 @@ constexpr int K3_THREADS = 512;
 constexpr int LWB_MIN = 7;    // 128 rows
 constexpr int LWB_MAX = 15;   // 32768 rows (local row fits in uint16)
 constexpr int NB_K2_MAX = 8192;   // buckets a K2 tile histograms in shared memory
+// A BFS level whose products number at most this many runs in the direct
+// form: K2 applies (min, select2nd) straight to the level and parent arrays
+// with global atomics (the dense output arrays are the SPA) and K3 only
+// closes the level; above it the bucketed form runs.
+constexpr int32_t BFS_DIRECT_MAX = 1 << 21;
 constexpr int BFILL_STRIDE = 32;  // bucket fill counters sit 128 bytes apart (own L2 line)
 
 // ---- hub ("hot") rows: the largest-degree rows, combined per K2 tile ----
@@ -89,6 +95,8 @@ struct DevState {
   uint32_t k1_done;    // K1 CTAs finished; the last one runs the selector (self-resetting)
   int32_t feat_dev;    // 1 when the current call's selector wrote feat[] (cleared by every K1)
   float feat[6];       // the six selector features as the device computed them
+  int32_t bfs_acc;     // BFS level in the direct form: vertices found so far (reset by K1)
+  int32_t* bfs_front;  // single-source BFS: the frontier list (x of a level, then its y)
 };
 
 // Selector run inside the work scan by its last CTA to finish: weights (NULL:
@@ -226,21 +234,28 @@ cudaError_t launch_relabel_hubs(const Matrix& A, const int32_t* hub_of_row, int3
                                 cudaStream_t s);
 // q_hint: the work quantum when the host knows it (selects a kernel compiled
 // for it), 0 when the device picks it
+// direct_max: a BFS level (the (min, select2nd) push of a search) runs in
+// the direct form when its work is at most this many products; 0 for calls
+// that are not BFS levels.  K2 and K3 of one level get the same value.
+// use_cond/cond (BFS levels in a graph loop): K3 sets the loop's condition
+// when it closes the level (another level while this one found vertices).
 cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo, int nb_fine,
                       const uint32_t* mask, int mask_comp, int grid, size_t smem, cudaStream_t s,
-                      int only_push = 0, int q_hint = 0);
+                      int only_push = 0, int q_hint = 0, int32_t direct_max = 0);
 cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, int lwb_lo,
                       int nb_fine, int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y,
                       uint32_t* mask_update, int grid, size_t smem, cudaStream_t s,
-                      int only_push = 0);
+                      int only_push = 0, int32_t direct_max = 0, int use_cond = 0,
+                      cudaGraphConditionalHandle cond = 0);
 cudaError_t launch_bucket_sizes(const Matrix& A, int lwb_lo, int nb_fine, int32_t* counts,
                                 unsigned int* bad, cudaStream_t s);
 // K2 shared memory: cb - cw and x value of the tile's x entries (whose bytes
 // then hold the tile's staged (row, value) pairs), the bitmap of entry starts,
-// the bucket histogram and slots, and the hub-row tables.
+// the bucket histogram and slots (one more for the hub bucket), and the
+// hub-row tables.
 __host__ __device__ constexpr size_t k2_smem_bytes(int nb_fine, bool hot) {
   return sizeof(uint32_t) * (QMAX / 32) + sizeof(int32_t) * (QMAX + 1) +
-         sizeof(uint32_t) * (QMAX + 1) + sizeof(int32_t) * (size_t)nb_fine * 2 + 64 +
+         sizeof(uint32_t) * (QMAX + 1) + sizeof(int32_t) * ((size_t)nb_fine + 1) * 2 + 64 +
          (hot ? sizeof(uint32_t) * HOT_MAX * 2 + sizeof(uint32_t) * (HOT_MAX / 32) + 64 : 0);
 }
 // K3 shared memory: the SPA values and the occupancy bitmap of one bucket

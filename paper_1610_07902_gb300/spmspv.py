@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
         lib.spmspv_bfs.argtypes = [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_uint32, _P]
         lib.spmspv_selector_set.argtypes = [_P, _P, ctypes.c_int32]
         lib.spmspv_selector_get.argtypes = [_P, _P, ctypes.c_int32]
+        lib.spmspv_selector_load.argtypes = [_P, ctypes.c_char_p]
         lib.spmspv_last_features.argtypes = [_P, _P]
         lib.spmspv_last_schedule.argtypes = [_P, ctypes.POINTER(ctypes.c_int32)]
         lib.spmspv_default_schedule.argtypes = [_P, ctypes.POINTER(ctypes.c_int32)]
@@ -202,6 +203,10 @@ def spmspv_selector_set(h, params):
     import numpy as np
     arr = np.ascontiguousarray(params, dtype=np.float32)
     _check(load().spmspv_selector_set(h, arr.ctypes.data, int(arr.size)), "spmspv_selector_set")
+
+
+def spmspv_selector_load(h, path):
+    _check(load().spmspv_selector_load(h, os.fsencode(str(path))), "spmspv_selector_load")
 
 
 def spmspv_selector_get(h):

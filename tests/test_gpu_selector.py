@@ -133,3 +133,24 @@ def test_device_features_match_their_definition(lib):
                 np.testing.assert_allclose(got, want, rtol=2e-6, atol=1e-7,
                                            err_msg="f=%d masked=%s semiring=%d" % (f, masked, semiring))
     Ad.close()
+
+
+def test_selector_load_reads_the_weights_file(lib, tmp_path):
+    """spmspv_selector_load installs the parameters of a weights file, the
+    same ones spmspv_selector_set installs from an array; a malformed file is
+    refused and leaves the installed parameters unchanged."""
+    torch, S = lib
+    from paper_1610_07902_gb300 import selector
+    A = synth.rmat(10, seed=2)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val)
+    S.spmspv_selector_load(Ad.handle, selector.WEIGHTS)
+    np.testing.assert_array_equal(S.spmspv_selector_get(Ad.handle), selector.load()[0])
+    bad = tmp_path / "short.json"
+    bad.write_text('{"nparam": 3, "params": [1.0, 2.0, 3.0]}')
+    with pytest.raises(S.SpmspvError) as e:
+        S.spmspv_selector_load(Ad.handle, bad)
+    assert e.value.code == S.SPMSPV_ERR_ARG
+    with pytest.raises(S.SpmspvError):
+        S.spmspv_selector_load(Ad.handle, tmp_path / "missing.json")
+    np.testing.assert_array_equal(S.spmspv_selector_get(Ad.handle), selector.load()[0])
+    Ad.close()
