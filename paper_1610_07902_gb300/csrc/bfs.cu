@@ -58,6 +58,11 @@ __global__ void k_bfs_init(int32_t n, int32_t src, int32_t* __restrict__ level,
     st->bfs_parent = parent;
     st->bfs_fb = keep_fb ? fb : nullptr;
     st->bfs_front = front;
+    st->fused_count = 0u;
+    st->fused_gen = 0u;
+    st->fused_w[3] = 0;
+    st->fused_fc[3] = 0;
+    st->fused_md[3] = 0;
   }
 }
 
@@ -188,17 +193,28 @@ static int build_bfs_graph(spmspv_handle* h, int sched, cudaGraphExec_t* out) {
 int ensure_bfs_buffers(spmspv_handle* h) {
   if (h->bfs_front) return SPMSPV_OK;
   const size_t n = (size_t)h->A.n;
+  // the persistent kernel of the learned schedule runs on CSC handles
+  const int fg = h->A.jc ? 0 : fused_bfs_grid(h);
   cudaError_t e = cudaMalloc(&h->bfs_front, sizeof(int32_t) * n);
   if (e == cudaSuccess) e = cudaMalloc(&h->bfs_visited, sizeof(uint32_t) * ((n + 31) / 32 + 1));
   if (e == cudaSuccess) e = cudaMalloc(&h->bfs_fb, sizeof(uint32_t) * 2 * ((n + 31) / 32));
+  if (e == cudaSuccess && fg > 0) e = cudaMalloc(&h->bfs_front2, sizeof(int32_t) * n);
+  if (e == cudaSuccess && fg > 0) e = cudaMalloc(&h->bfs_slice, sizeof(int32_t) * 3 * (size_t)fg);
   if (e != cudaSuccess) {
     cudaFree(h->bfs_front);
     cudaFree(h->bfs_visited);
+    cudaFree(h->bfs_fb);
+    cudaFree(h->bfs_front2);
+    cudaFree(h->bfs_slice);
     h->bfs_front = nullptr;
     h->bfs_visited = nullptr;
+    h->bfs_fb = nullptr;
+    h->bfs_front2 = nullptr;
+    h->bfs_slice = nullptr;
     cudaGetLastError();
     return fail(SPMSPV_ERR_OOM, "BFS buffers: %s", cudaGetErrorString(e));
   }
+  h->fused_grid = fg;
   return SPMSPV_OK;
 }
 
@@ -244,6 +260,12 @@ extern "C" int spmspv_bfs(spmspv_handle* h, int32_t src, int32_t* level, int32_t
                                   h->ws.st, pulls ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "bfs init");
+  // the learned schedule: the first levels, as long as they are small push
+  // levels, in one persistent launch (on a high-diameter graph usually the
+  // whole search); it leaves the state of the first level it does not run
+  // to the graph's loop of plain kernels
+  if (sched < 0 && h->fused_grid > 0 && (e = launch_bfs_fused(h, h->fused_grid, s)) != cudaSuccess)
+    return cuda_fail(e, "bfs persistent levels");
   if ((e = cudaGraphLaunch((cudaGraphExec_t)h->bfs_graph[slot], s)) != cudaSuccess)
     return cuda_fail(e, "bfs graph launch");
   if (d_nlevels) {

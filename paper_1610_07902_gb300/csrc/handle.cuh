@@ -51,6 +51,9 @@ struct spmspv_handle {
   int32_t* bfs_front;   // [n] frontier list (x and y of each level)
   uint32_t* bfs_visited;  // [ceil(n/32)]
   uint32_t* bfs_fb;     // [2 * ceil(n/32)] frontier bitmaps (current / next level)
+  int32_t* bfs_front2;  // [n] the persistent BFS kernel's second frontier buffer
+  int32_t* bfs_slice;   // [3 * fused grid] its per-CTA slice sums
+  int fused_grid;       // CTAs of the persistent BFS kernel (0: not available)
   // connected components (first use): frontier (x) and round output (y), counts
   int32_t* cc_x_idx;
   uint32_t* cc_x_val;
@@ -144,6 +147,10 @@ int pull_available(const spmspv_handle* h, int sem);
 // BFS pull kernel of a batched lane (the lane's job names the source's arrays)
 cudaError_t launch_pull_rows_lane(const spmspv_handle* sub, int early_exit, cudaStream_t s);
 int ensure_bfs_buffers(spmspv_handle* h);
+// The persistent BFS kernel of the learned schedule (bfs_fused.cu): its grid
+// (every CTA resident; 0 if it cannot run) and its cooperative launch.
+int fused_bfs_grid(const spmspv_handle* h);
+cudaError_t launch_bfs_fused(const spmspv_handle* h, int grid, cudaStream_t s);
 // Per-stage event recording (no-ops unless spmspv_profile_begin was called).
 void prof_call_begin(spmspv_handle* h, cudaStream_t s);
 void prof_mark(spmspv_handle* h, int stage, cudaStream_t s);

@@ -96,9 +96,16 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
         st->lwb = f_lwb;
         st->sched = forced - 1;
       }
-      if (bfs_mode) st->pull_ticket = 0u;  // the level may run the pull kernel
+      if (bfs_mode) {
+        st->pull_ticket = 0u;  // the level may run the pull kernel
+        st->fused_w[3] = 0;    // the persistent BFS kernel's next launch counts from zero
+        st->fused_fc[3] = 0;
+        st->fused_md[3] = 0;
+      }
       if (bfs_level_inc) {
-        st->level += 1;
+        // (an empty frontier only reaches here after the persistent kernel
+        // of the learned schedule finished the search: no further level)
+        if (f > 0) st->level += 1;
       } else if (!ws.job) {
         st->bfs_level = nullptr;  // not a BFS level
       }

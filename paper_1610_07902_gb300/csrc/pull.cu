@@ -313,6 +313,8 @@ void release_extras(spmspv_handle* h) {
   cudaFree(h->xdense);
   cudaFree(h->pull_status);
   cudaFree(h->bfs_front);
+  cudaFree(h->bfs_front2);
+  cudaFree(h->bfs_slice);
   cudaFree(h->bfs_visited);
   cudaFree(h->bfs_fb);
   cudaFree(h->bfs_count);
@@ -320,6 +322,9 @@ void release_extras(spmspv_handle* h) {
   h->xdense = nullptr;
   h->pull_status = nullptr;
   h->bfs_front = nullptr;
+  h->bfs_front2 = nullptr;
+  h->bfs_slice = nullptr;
+  h->fused_grid = 0;
   h->bfs_visited = nullptr;
   h->bfs_fb = nullptr;
   h->bfs_count = nullptr;

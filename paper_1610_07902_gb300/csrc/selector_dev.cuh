@@ -41,17 +41,51 @@ __device__ __forceinline__ float sel_forward_warp(const float* __restrict__ w, c
 
 // bfs: the mask is the BFS visited set, whose population is the count of
 // vertices reached so far (no pass over the bitmap needed).
+// The six features from the call's counts: f = nnz(x), W = products, fc =
+// x entries with a non-empty column, the largest selected column, and the
+// number of rows set in the mask (in BFS, the vertices reached so far).
+__device__ __forceinline__ void sel_features_of(int32_t f_i, int32_t W_i, int32_t fc_i, int32_t maxdeg,
+                                                int32_t maskcnt, int32_t m, int32_t n, int64_t nnz,
+                                                float* x) {
+  const float f = (float)f_i, W = (float)W_i;
+  const float fc = (float)max(fc_i, 1);
+  x[0] = log2f(1.f + f);
+  x[1] = log2f(1.f + W);
+  x[2] = W > 0.f ? (float)maxdeg * fc / W : 0.f;
+  x[3] = (float)maskcnt / (float)m;
+  x[4] = log2f((float)m);
+  x[5] = (float)((double)nnz / (double)n);
+}
+
 __device__ __forceinline__ void sel_features(const DevState* st, int32_t m, int32_t n, int64_t nnz,
                                              int bfs, float* x) {
   // L2 reads: other CTAs of the same launch may have written these
-  const float f = (float)__ldcg(&st->f), W = (float)__ldcg(&st->W);
-  const float fc = (float)max(__ldcg(&st->fc), 1);
-  x[0] = log2f(1.f + f);
-  x[1] = log2f(1.f + W);
-  x[2] = W > 0.f ? (float)__ldcg(&st->maxdeg) * fc / W : 0.f;
-  x[3] = (float)(bfs ? __ldcg(&st->nvisited) : __ldcg(&st->maskcnt)) / (float)m;
-  x[4] = log2f((float)m);
-  x[5] = (float)((double)nnz / (double)n);
+  sel_features_of(__ldcg(&st->f), __ldcg(&st->W), __ldcg(&st->fc), __ldcg(&st->maxdeg),
+                  bfs ? __ldcg(&st->nvisited) : __ldcg(&st->maskcnt), m, n, nnz, x);
+}
+
+// The schedule the network picks for raw features x (one full warp; every
+// lane gets the id): normalise, evaluate, argmin over the allowed outputs
+// (ties to the smaller id).
+__device__ __forceinline__ int sel_pick_warp(const float* __restrict__ w, const float* xraw, int allow_pull) {
+  float x[SEL_IN];
+#pragma unroll
+  for (int k = 0; k < SEL_IN; ++k) x[k] = (xraw[k] - w[SEL_OMEAN + k]) * w[SEL_OSCALE + k];
+  const float o = sel_forward_warp(w, x, nullptr, nullptr);
+  const int lane = threadIdx.x & 31;
+  const bool ok = lane < SEL_OUT && (allow_pull || lane < 6);
+  float best = ok ? o : INFINITY;
+  int bi = ok ? lane : 64;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+    if (ob < best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  return bi < SEL_OUT ? bi : 4;
 }
 
 // Device-side choice for this call, run by one full warp: features -> MLP ->

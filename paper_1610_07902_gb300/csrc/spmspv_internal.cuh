@@ -97,6 +97,12 @@ struct DevState {
   float feat[6];       // the six selector features as the device computed them
   int32_t bfs_acc;     // BFS level in the direct form: vertices found so far (reset by K1)
   int32_t* bfs_front;  // single-source BFS: the frontier list (x of a level, then its y)
+  uint32_t fused_count;  // persistent BFS kernel: grid barrier arrivals (monotonic in a search)
+  uint32_t fused_gen;    // persistent BFS kernel: barriers passed so far in the search
+  int32_t fused_cnt[3];  // persistent BFS kernel, per level mod 3: vertices found,
+  long long fused_w[4];  //   their products, non-empty columns and largest column; [3]: the
+  int32_t fused_fc[4];   //   counts of the frontier a launch starts from (zeroed by K1)
+  int32_t fused_md[4];
 };
 
 // Selector run inside the work scan by its last CTA to finish: weights (NULL:
