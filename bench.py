@@ -35,13 +35,32 @@ WORKLOAD = "rmat22_ef16_f1e6_plus_times_f32"
 SCALE, EDGE_FACTOR, SEED, F = 22, 16, 1, 1_000_000
 
 
-# DRAM bytes per product moved by the scatter kernel, from a full ncu capture
-# of the same kernel build on R-MAT s21 with nnz(x) = 5e5, scaled by products
-# (the traffic of a launch grows with its products); None while the kernel
-# differs from the captured one.
-K2_TRAFFIC_PER_PRODUCT = (180.53e6 + 36.65e6) / 15.03e6
-K2_TRAFFIC_SOURCE = ("ncu full capture of the same K2 (commit 17daac1), R-MAT s21 nnz(x)=5e5, "
-                     "scaled by products")
+def kernels_hash():
+    """First 16 hex digits of the SHA-256 of the kernel sources the capture
+    covers (kernels.cu and the headers it includes)."""
+    import hashlib
+    h = hashlib.sha256()
+    base = os.path.join(ROOT, "paper_1610_07902_gb300", "csrc")
+    for name in ("kernels.cu", "spmspv_internal.cuh", "device_util.cuh", "selector_dev.cuh"):
+        with open(os.path.join(base, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(kernel):
+    """DRAM bytes per unit of `kernel` from a committed ncu summary under
+    profiles/ whose capture was of these exact kernel sources: a line
+    'traffic: <kernel> <bytes per unit> bytes per <unit> (sources <hash>)'.
+    None when no summary matches the current sources."""
+    import glob
+    import re
+    want = kernels_hash()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            m = re.search(r"traffic: (\S+) ([0-9.]+) bytes per (\w+) \(sources ([0-9a-f]+)\)", line)
+            if m and m.group(1) == kernel and m.group(4) == want:
+                return float(m.group(2)), os.path.basename(path)
+    return None, None
 
 
 NOMINAL_HBM_GBS = 7900.0  # nominal HBM3e bandwidth of the part, a second denominator
@@ -206,7 +225,7 @@ def bench_bfs(S, A, dev, stream, name, sources, params, pt_frontiers=False):
     fixed = S.SPMSPV_SCHED_OPT(default)
     if params is not None:
         S.spmspv_selector_set(Ad.handle, params)
-    t_fixed = t_auto = 0.0
+    t_fixed = t_auto = t_rule = 0.0
     work = 0
     reached = 0
     levels = []
@@ -218,6 +237,10 @@ def bench_bfs(S, A, dev, stream, name, sources, params, pt_frontiers=False):
         levels.append(int(nl.item()))
         work += int(deg[level >= 0].sum().item())
         reached += int((level >= 0).sum().item())
+        # the direction-optimizing rule (two fixed thresholds), the learned selector's baseline
+        run(S.SPMSPV_SCHED_RULE, level2, parent2)
+        t_rule += _events_ms(lambda: run(S.SPMSPV_SCHED_RULE, level2, parent2), stream, 2)
+        same &= bool(torch.equal(level, level2) and torch.equal(parent, parent2))
         if params is not None:
             run(S.SPMSPV_SCHED_AUTO, level2, parent2)
             t_auto += _events_ms(lambda: run(S.SPMSPV_SCHED_AUTO, level2, parent2), stream, 2)
@@ -232,9 +255,10 @@ def bench_bfs(S, A, dev, stream, name, sources, params, pt_frontiers=False):
            "fixed_ms": t_fixed, "fixed_gteps": work / (t_fixed * 1e-3) / 1e9,
            "compulsory_bytes_min_semiring": bfs_bytes,
            "fixed_path_frac": bfs_bytes / (t_fixed * 1e-3) / 1e9 / peak}
+    out.update({"rule_ms": t_rule, "rule_speedup": t_fixed / t_rule, "identical_results": same})
     if params is not None:
         out.update({"auto_ms": t_auto, "auto_gteps": work / (t_auto * 1e-3) / 1e9,
-                    "auto_speedup": t_fixed / t_auto, "identical_results": same})
+                    "auto_speedup": t_fixed / t_auto, "auto_vs_rule": t_rule / t_auto})
     if pt_frontiers:
         # (+,*) float32 SpMSpV on every frontier of the last search (level sets
         # from the device BFS, host-side split), one call per level
@@ -662,6 +686,50 @@ def bench_batched(S, dev, stream, B=256):
     return out
 
 
+def bench_selector_heldout(S, dev):
+    """The learned selector on graphs it was not trained on (R-MAT s23 and the
+    320^3 grid, BASELINE's held-out pair): per replayed BFS level, the regret
+    t/t_best - 1 of the schedule it picks against the best of the 12 (and of
+    the fixed default); per whole search (two sources each), the time of the
+    fixed default, the learned schedule, the direction-optimizing rule and
+    the best single fixed schedule (the autotuned fixed choice), levels and
+    parents checked identical across all of them."""
+    import torch
+    import synth
+    from paper_1610_07902_gb300 import selector
+    params = selector_params()
+    if params is None:
+        return None
+    out = {}
+    for name, spec in selector.EVAL_GRAPHS:
+        A = selector.make_graph(spec)
+        Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC,
+                         device=dev)
+        srcs = synth.sources(A.colptr, 2, seed=7)
+        r = selector.evaluate(Ad, A, srcs, params, reps=2, max_levels=24)
+        lf = torch.empty(A.n, dtype=torch.int32, device=dev)
+        pf = torch.empty_like(lf)
+        nl = torch.zeros(1, dtype=torch.int32, device=dev)
+        t_rule = 0.0
+        same = True
+        for src in srcs:
+            S.spmspv_bfs(Ad.handle, int(src), lf, pf, nl, S.SPMSPV_SCHED_RULE)
+            t_rule += _events_ms(lambda: S.spmspv_bfs(Ad.handle, int(src), lf, pf, nl, S.SPMSPV_SCHED_RULE),
+                                 torch.cuda.current_stream(dev), 2)
+            ts, ls, ps = selector.time_bfs(Ad, src, S.SPMSPV_SCHED_AUTO, 1)
+            same &= bool(torch.equal(lf, ls) and torch.equal(pf, ps))
+        tot = r["bfs_total_ms"]
+        tot.update({"rule": t_rule, "auto_vs_rule": t_rule / tot["auto"],
+                    "identical_results": bool(tot["identical_results"] and same)})
+        tot.pop("per_schedule", None)
+        out[name] = {"n": int(A.n), "nnz": int(A.nnz), "per_call_regret": r["per_call_regret"],
+                     "bfs_total_ms": tot, "default_schedule": r["default_schedule"]}
+        Ad.close()
+        del A, lf, pf
+        torch.cuda.empty_cache()
+    return out
+
+
 def reference_arm(args, rank):
     if rank != 0:
         return
@@ -810,9 +878,12 @@ def main():
         xv2.copy_(hx_v, non_blocking=True)
         S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, xi2, xv2, F_, None, opts, y_idx, y_val,
                      cap, nnz_y, stream)
+        # as a caller must: read the size of y first, then copy that many entries
         hn.copy_(nnz_y, non_blocking=True)
-        hy_i[:ny].copy_(y_idx[:ny], non_blocking=True)
-        hy_v[:ny].copy_(y_val[:ny], non_blocking=True)
+        torch.cuda.synchronize()
+        k = int(hn.item())
+        hy_i[:k].copy_(y_idx[:k], non_blocking=True)
+        hy_v[:k].copy_(y_val[:k], non_blocking=True)
         torch.cuda.synchronize()
         if i >= 2:
             e2e_ms += (time.perf_counter() - t0) * 1e3
@@ -827,6 +898,10 @@ def main():
            S.SPMSPV_STAGE_MERGE: 8 * ny}
     dom = max(names, key=lambda s: stage_avg[s])
     achieved = alg[dom] / (stage_avg[dom] * 1e-3) / 1e9
+    units = {S.SPMSPV_STAGE_SCAN: F_, S.SPMSPV_STAGE_SCATTER: W, S.SPMSPV_STAGE_MERGE: W}
+    kname = {S.SPMSPV_STAGE_SCAN: "k1_work_scan", S.SPMSPV_STAGE_SCATTER: "k2_expand_scatter",
+             S.SPMSPV_STAGE_MERGE: "k3_bucket_merge"}[dom]
+    per_unit, traffic_src = captured_traffic(kname)
     path_bytes = compulsory_bytes(F_, W, ny)
     path_gbs = path_bytes / (ms_per_step * 1e-3) / 1e9
 
@@ -879,6 +954,7 @@ def main():
         extras["batched"] = bench_batched(S, dev, stream)
         extras["dcsc_hypersparse"] = bench_dcsc(S, dev, stream, flush)
         extras["selector_weights"] = "trained" if params is not None else "absent (AUTO not run)"
+        extras["selector_heldout"] = bench_selector_heldout(S, dev)
 
     line = {
         "metric": METRIC, "value": gteps, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
@@ -891,10 +967,11 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single_gpu"},
         "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": (K2_TRAFFIC_PER_PRODUCT * W
-                                 if dom == S.SPMSPV_STAGE_SCATTER and K2_TRAFFIC_PER_PRODUCT
-                                 else None),
-                     "traffic_unit": "bytes per launch", "traffic_source": K2_TRAFFIC_SOURCE,
+                     "traffic": per_unit * units[dom] if per_unit else None,
+                     "traffic_unit": "bytes per launch",
+                     "traffic_source": ("%s (ncu capture of these kernel sources, %s, scaled by the "
+                                        "launch's units)" % (traffic_src, kernels_hash())
+                                        if per_unit else "no capture of the current kernel sources"),
                      "peak_kind": peak_kind, "alg_bytes_per_launch": alg[dom],
                      "avg_launch_ms": stage_avg[dom], "frac_nominal": achieved / NOMINAL_HBM_GBS},
         "path_roofline": {"compulsory_bytes": path_bytes, "achieved": path_gbs, "peak": peak,
@@ -903,7 +980,8 @@ def main():
         "stages_ms": {names[s]: stage_avg[s] for s in names},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_gteps, "unit": "GTEPS", "h2d_bytes_per_step": 8 * F_,
-                "d2h_bytes_per_step": 4 + 8 * ny},
+                "d2h_bytes_per_step": 4 + 8 * ny,
+                "note": "pinned host x in, y out; the size of y is read (one synchronisation) before y is copied"},
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
     }

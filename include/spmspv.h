@@ -88,6 +88,10 @@ typedef struct spmspv_handle spmspv_handle;
                                      efficiency: more local column accesses for denser x);
                                      a counting sort over [0, n), about n/8 + 12 nnz(x)
                                      bytes of traffic; buffers of 16n bytes on first use */
+#define SPMSPV_SCHED_RULE 64u       /* spmspv_bfs only: push or pull per level by the
+                                       direction-optimizing rule of Beamer, Asanovic and
+                                       Patterson (SC 2012; two fixed thresholds, alpha = 14,
+                                       beta = 24), the baseline of the learned selector */
 #define SPMSPV_SCHED_SHIFT 8
 #define SPMSPV_SCHED_OPT(s) (SPMSPV_SCHED_FORCE | ((uint32_t)(s) << SPMSPV_SCHED_SHIFT))
 #define SPMSPV_SCHED_ID(opts) (((opts) >> SPMSPV_SCHED_SHIFT) & 0xFFu)

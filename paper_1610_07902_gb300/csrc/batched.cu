@@ -131,6 +131,7 @@ static int lane_launches(spmspv_handle* sub, BatchState* bs, int lane, int sem, 
     sa.allow_pull = 1;
     sa.bfs = 1;
     sa.lwb_lo = sub->lwb_lo;
+    sa.direct_max = BFS_DIRECT_MAX;
     if ((e = launch_k1_bfs(sub->A, sub->ws, sub->nb_fine, nullptr, nullptr, k1_grid, nullptr, s,
                            nullptr, &sa)) != cudaSuccess)
       return cuda_fail(e, "batch work scan");

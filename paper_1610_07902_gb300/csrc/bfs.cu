@@ -63,6 +63,8 @@ __global__ void k_bfs_init(int32_t n, int32_t src, int32_t* __restrict__ level,
     st->fused_w[3] = 0;
     st->fused_fc[3] = 0;
     st->fused_md[3] = 0;
+    st->edges_seen = 0;
+    st->dir = 0;  // the rule starts in the push direction
   }
 }
 
@@ -94,7 +96,7 @@ static int bfs_pull_launches(spmspv_handle* h, int only_pull, cudaStream_t s, cu
 // of which the ones not chosen return at once.
 static int bfs_level_launches(spmspv_handle* h, int sched, cudaGraphConditionalHandle cond,
                               cudaStream_t s) {
-  const bool autos = sched < 0;
+  const bool autos = sched < 0;  // -1: the learned selector, -2: the direction-optimizing rule
   const bool can_pull = pull_available(h, kMinSelect2nd) != 0;
   Sched sc = decode_schedule(h, autos ? h->default_sched : sched);
   if (!can_pull && sc.dir == 1) {
@@ -114,10 +116,12 @@ static int bfs_level_launches(spmspv_handle* h, int sched, cudaGraphConditionalH
     // returns at once (no conditional nodes); the visited count stands in
     // for a pass over the visited bitmap
     SelArgs sa{};
-    sa.w = h->sel_w;
+    sa.w = sched == -2 ? nullptr : h->sel_w;
+    sa.rule = sched == -2 ? 1 : 0;
     sa.allow_pull = can_pull;
     sa.bfs = 1;
     sa.lwb_lo = h->lwb_lo;
+    sa.direct_max = BFS_DIRECT_MAX;
     if ((e = launch_k1_bfs(h->A, h->ws, h->nb_fine, h->bfs_front, &h->ws.st->nnz_y, h->k1_grid_dev,
                            nullptr, s, nullptr, &sa)) != cudaSuccess)
       return cuda_fail(e, "bfs work scan");
@@ -219,7 +223,7 @@ int ensure_bfs_buffers(spmspv_handle* h) {
 }
 
 void release_bfs_graphs(spmspv_handle* h) {
-  for (int i = 0; i < SPMSPV_NUM_SCHEDULES + 1; ++i) {
+  for (int i = 0; i < SPMSPV_NUM_SCHEDULES + 2; ++i) {
     if (h->bfs_graph[i]) cudaGraphExecDestroy((cudaGraphExec_t)h->bfs_graph[i]);
     h->bfs_graph[i] = nullptr;
   }
@@ -240,12 +244,15 @@ extern "C" int spmspv_bfs(spmspv_handle* h, int32_t src, int32_t* level, int32_t
     return fail(SPMSPV_ERR_ARG, "schedule id out of range");
   int sched = h->default_sched;
   if (opts & SPMSPV_SCHED_FORCE) sched = (int)SPMSPV_SCHED_ID(opts);
+  if ((opts & SPMSPV_SCHED_AUTO) && (opts & SPMSPV_SCHED_RULE))
+    return fail(SPMSPV_ERR_ARG, "SPMSPV_SCHED_AUTO and SPMSPV_SCHED_RULE exclude each other");
   if (opts & SPMSPV_SCHED_AUTO) {
     if (!h->sel_ready) return fail(SPMSPV_ERR_STATE, "no selector weights loaded or trained");
     sched = -1;
   }
+  if (opts & SPMSPV_SCHED_RULE) sched = -2;
   if ((rc = ensure_bfs_buffers(h)) != SPMSPV_OK) return rc;
-  const int slot = sched < 0 ? SPMSPV_NUM_SCHEDULES : sched;
+  const int slot = sched == -1 ? SPMSPV_NUM_SCHEDULES : sched == -2 ? SPMSPV_NUM_SCHEDULES + 1 : sched;
   if (!h->bfs_graph[slot]) {
     cudaGraphExec_t exec = nullptr;
     if ((rc = build_bfs_graph(h, sched, &exec)) != SPMSPV_OK) return rc;
@@ -260,10 +267,10 @@ extern "C" int spmspv_bfs(spmspv_handle* h, int32_t src, int32_t* level, int32_t
                                   h->ws.st, pulls ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "bfs init");
-  // the learned schedule: the first levels, as long as they are small push
-  // levels, in one persistent launch (on a high-diameter graph usually the
-  // whole search); it leaves the state of the first level it does not run
-  // to the graph's loop of plain kernels
+  // the adaptive schedules (learned, rule): the first levels, as long as
+  // they are small push levels, in one persistent launch (on a high-diameter
+  // graph usually the whole search); it leaves the state of the first level
+  // it does not run to the graph's loop of plain kernels
   if (sched < 0 && h->fused_grid > 0 && (e = launch_bfs_fused(h, h->fused_grid, s)) != cudaSuccess)
     return cuda_fail(e, "bfs persistent levels");
   if ((e = cudaGraphLaunch((cudaGraphExec_t)h->bfs_graph[slot], s)) != cudaSuccess)

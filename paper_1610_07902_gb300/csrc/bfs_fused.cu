@@ -1,31 +1,31 @@
-// Persistent BFS levels for the learned schedule (spmspv_bfs with
-// SPMSPV_SCHED_AUTO on a CSC handle).
+// Persistent BFS levels for the adaptive schedules of spmspv_bfs (the
+// learned selector, SPMSPV_SCHED_AUTO, and the direction-optimizing rule,
+// SPMSPV_SCHED_RULE) on a CSC handle.
 //
 // A high-diameter graph makes a BFS of hundreds of levels with small
 // frontiers; run as the plain per-level kernels (work scan -> expand ->
 // merge) each level pays their launches and ramp-up, which is most of its
 // time.  This kernel, launched once when the search starts, before the BFS
 // graph's loop, with every CTA resident (a cooperative launch), runs
-// consecutive levels itself, one grid barrier per level:
-//   - every CTA evaluates the learned selector on the level's features (the
-//     same network and features as the work scan's; the counts come from
-//     the level before) while its warps load an equal slice of the frontier
-//     x and compact its non-empty columns with their first products;
-//   - when the selector picks the push direction and the level is small
-//     enough, the CTA applies the masked (min, select2nd) product to its
-//     slice in the direct form: one compare-and-swap on the level decides
-//     whether a row is new (first finder), found again in this level or
-//     reached before, an unsigned min on the parent follows (the parent
-//     array is the SPA: -1 is the largest value), and the first finder
-//     appends the vertex to the next frontier (one atomic per warp) and adds
-//     its column length to the next level's counts;
+// consecutive levels itself, one grid barrier per level.  Such levels are
+// push levels in the direct form (both schedules keep a level of at most
+// BFS_DIRECT_MAX products on push):
+//   - every CTA loads an equal slice of the frontier x and compacts its
+//     non-empty columns with their first products; the level's counts
+//     (products, non-empty columns, largest column) come from the level
+//     before, summed while its vertices were found;
+//   - the CTA applies the masked (min, select2nd) product to its slice: one
+//     compare-and-swap on the level decides whether a row is new (first
+//     finder), found again in this level or reached before, an unsigned min
+//     on the parent follows (the parent array is the SPA: -1 is the largest
+//     value), and the first finder appends the vertex to the next frontier
+//     (one atomic per warp) and adds its column length to the next counts;
 //   - a grid barrier closes the level.
-// A level that the selector sends to the pull direction (the kernel first
-// builds the frontier bitmap the pull reads), or that is too large or too
-// uneven for the direct form, is left, with all the levels after it, to the
-// loop of plain kernels, its state exactly as at the level's start.  Every wait
-// is bounded; a wait that runs out sets SPMSPV_DEV_TIMEOUT and the kernel
-// returns.
+// The first level that is too large or too uneven for the direct form is
+// left, with all the levels after it, to the graph's loop of plain kernels
+// (where the selector or the rule decides each level), its state exactly as
+// at the level's start.  Every wait is bounded; a wait that runs out sets
+// SPMSPV_DEV_TIMEOUT and the kernel returns.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -55,10 +55,8 @@ struct FusedArgs {
   uint32_t* visited;
   int32_t* front0;      // the frontier list the plain kernels read and write
   int32_t* front1;      // the other buffer of a level's next frontier
-  uint32_t* fb;         // frontier bitmaps [2][ceil(n/32)] (NULL: no pull level follows)
+  uint32_t* fb;         // frontier bitmaps [2][ceil(n/32)] (NULL: no pull level can follow)
   DevState* st;
-  const float* selw;    // selector parameters
-  int allow_pull;
   int32_t direct_max;
 };
 
@@ -116,10 +114,9 @@ __global__ void __launch_bounds__(FB_THREADS, 2) k_bfs_fused(FusedArgs a) {
   __shared__ int32_t s_lo[FB_CH + 1];    // its first product in the slice
   __shared__ uint32_t s_x[FB_CH];        // its vertex id (the value select2nd passes on)
   __shared__ uint32_t s_hb[FB_QT / 32];  // entry starts inside a product tile
-  __shared__ float s_w[SEL_NPARAM];
   __shared__ long long s_red[FB_WARPS];
   __shared__ unsigned long long s_scan[FB_THREADS / 32 + 1];
-  __shared__ int s_ok, s_pick, s_efirst, s_nq;
+  __shared__ int s_ok, s_efirst, s_nq;
   __shared__ int32_t s_S;
 
   DevState* st = a.st;
@@ -127,15 +124,12 @@ __global__ void __launch_bounds__(FB_THREADS, 2) k_bfs_fused(FusedArgs a) {
   const int32_t G = (int32_t)gridDim.x, c = (int32_t)blockIdx.x, n = a.n;
   int32_t* level = st->bfs_level;    // this search's outputs (set when it started)
   uint32_t* parent = reinterpret_cast<uint32_t*>(st->bfs_parent);
-  // the selector's parameters, unless the frontier already rules out this kernel
-  const int32_t f0 = __ldcg(&st->nnz_y);
-  if (a.selw && f0 > 0 && f0 <= FB_F_MAX)
-    for (int i = tid; i < SEL_NPARAM; i += FB_THREADS) s_w[i] = a.selw[i];
   for (int i = tid; i < FB_QT / 32; i += FB_THREADS) s_hb[i] = 0u;
   // the search's state at this launch (written by the kernels before it)
   int32_t f = __ldcg(&st->nnz_y), L = __ldcg(&st->level), nvis = __ldcg(&st->nvisited);
+  const int32_t L0 = L;
   uint32_t epoch = __ldcg(&st->fused_gen);
-  const int64_t words = ((int64_t)n + 31) / 32;
+  long long seen = __ldcg(&st->edges_seen);  // expanded edges (the rule counts them)
   int cur = 0;          // 0: x in front0, 1: x in front1
   bool have = false;    // counts of the current frontier known (from the level before)
   long long W = 0;
@@ -185,6 +179,7 @@ __global__ void __launch_bounds__(FB_THREADS, 2) k_bfs_fused(FusedArgs a) {
       s_S = (int32_t)(tot & 0xffffffffull);
       s_lo[s_nq] = s_S;
     }
+    __syncthreads();  // the slice's entries and sizes, for every thread
     if (!have) {
       // the first level of this launch: its counts from every slice (into the
       // start slot, which K1 zeroes), and this level's counters start at zero
@@ -206,28 +201,8 @@ __global__ void __launch_bounds__(FB_THREADS, 2) k_bfs_fused(FusedArgs a) {
       md = __ldcg(&st->fused_md[3]);
       have = true;
     }
-    // ---- the selector's choice (every CTA alike) ----
-    if (warp == 0) {
-      int pick = 0;
-      if (a.selw) {
-        float xf[SEL_IN];
-        sel_features_of(f, (int32_t)min(W, (long long)INT32_MAX), fc, md, nvis, n, n, a.nnz, xf);
-        pick = sel_pick_warp(s_w, xf, a.allow_pull);
-      }
-      if (lane == 0) s_pick = pick;
-    }
-    __syncthreads();
-    if (s_pick >= 6) {
-      // a pull level follows: the frontier bitmap it reads (the last level's)
-      if (a.fb) {
-        uint32_t* fbx = a.fb + ((L & 1) ? words : 0);
-        for (int64_t w = (int64_t)c * FB_THREADS + tid; w < words; w += (int64_t)G * FB_THREADS) fbx[w] = 0u;
-        if (!fused_barrier(st, ++epoch, &s_ok)) return;
-        for (int q = tid; q < s_nq; q += FB_THREADS) atomicOr(fbx + (s_x[q] >> 5), 1u << (s_x[q] & 31));
-      }
-      break;
-    }
     if (W > a.direct_max || md > FB_COL_MAX) break;  // the plain kernels take this level
+    seen += W;
     // the counters of the level after next start at zero (last read two levels ago)
     if (c == 0 && tid == 0) {
       st->fused_cnt[(Ln + 1) % 3] = 0;
@@ -265,7 +240,7 @@ __global__ void __launch_bounds__(FB_THREADS, 2) k_bfs_fused(FusedArgs a) {
         ent += __popc(hw);
         row[i] = 0xffffffffu;
         val[i] = 0u;
-        if (pl < np) {
+        if (pl < np && e < nq) {  // (e < nq always holds; the test keeps the reads in the arrays)
           const int32_t pos = s_c0[e] + (P0 + pl - s_lo[e]);
           if ((uint64_t)pos < (uint64_t)a.nnz) row[i] = (uint32_t)__ldcs(a.rowidx + pos);
           val[i] = s_x[e];
@@ -331,6 +306,20 @@ __global__ void __launch_bounds__(FB_THREADS, 2) k_bfs_fused(FusedArgs a) {
       st->level = L;
       st->nnz_y = f;
       st->nvisited = nvis;
+      st->edges_seen = seen;
+    }
+  }
+  // a pull level may follow: it reads the frontier bitmap of the last level
+  // this kernel ran (cleared, then set from that level's vertices)
+  if (a.fb && L > L0 && f > 0) {
+    const int64_t words = ((int64_t)n + 31) / 32;
+    uint32_t* fbx = a.fb + ((L & 1) ? words : 0);
+    for (int64_t w = (int64_t)c * FB_THREADS + tid; w < words; w += (int64_t)G * FB_THREADS) fbx[w] = 0u;
+    if (!fused_barrier(st, ++epoch, &s_ok)) return;
+    const int32_t* xl = cur ? a.front1 : a.front0;
+    for (int32_t k = c * FB_THREADS + tid; k < f; k += G * FB_THREADS) {
+      const int32_t v = xl[k];
+      atomicOr(fbx + (v >> 5), 1u << (v & 31));
     }
   }
   if (c == 0 && tid == 0) st->fused_gen = epoch;
@@ -363,8 +352,6 @@ cudaError_t launch_bfs_fused(const spmspv_handle* h, int grid, cudaStream_t s) {
   a.front1 = h->bfs_front2;
   a.fb = pull_available(h, kMinSelect2nd) ? h->bfs_fb : nullptr;
   a.st = h->ws.st;
-  a.selw = h->sel_w;
-  a.allow_pull = pull_available(h, kMinSelect2nd);
   a.direct_max = BFS_DIRECT_MAX;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);

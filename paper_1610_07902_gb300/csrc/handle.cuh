@@ -36,7 +36,7 @@ struct spmspv_handle {
   void* prof;           // std::vector<ProfileCall>* while profiling, else NULL
   int32_t* rowidx_k2;   // owned row-id copy with hub rows relabelled (NULL without hubs)
   int32_t* dcsc_aux;    // owned auxiliary column index of a DCSC matrix (NULL for CSC)
-  void* bfs_graph[SPMSPV_NUM_SCHEDULES + 1];  // cudaGraphExec_t per schedule (+ auto)
+  void* bfs_graph[SPMSPV_NUM_SCHEDULES + 2];  // cudaGraphExec_t per schedule (+ learned, + rule)
   // learned schedule selector
   int sel_ready;        // weights present
   float* sel_w;         // device weights (layout in selector.cu)
@@ -147,7 +147,7 @@ int pull_available(const spmspv_handle* h, int sem);
 // BFS pull kernel of a batched lane (the lane's job names the source's arrays)
 cudaError_t launch_pull_rows_lane(const spmspv_handle* sub, int early_exit, cudaStream_t s);
 int ensure_bfs_buffers(spmspv_handle* h);
-// The persistent BFS kernel of the learned schedule (bfs_fused.cu): its grid
+// The persistent BFS kernel of the adaptive schedules (bfs_fused.cu): its grid
 // (every CTA resident; 0 if it cannot run) and its cooperative launch.
 int fused_bfs_grid(const spmspv_handle* h);
 cudaError_t launch_bfs_fused(const spmspv_handle* h, int grid, cudaStream_t s);

@@ -243,7 +243,7 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
   __syncthreads();
   if (tid == 0 && s_maxdeg > 0) atomicMax(&st->maxdeg, s_maxdeg);
   if (tid == 0 && s_maskcnt > 0) atomicAdd(&st->maskcnt, s_maskcnt);
-  if (!sel.w) return;
+  if (!sel.w && !sel.rule) return;
   // the selector runs in the CTA that finishes the last piece of work, once
   // every count is in: with a mask pass every CTA is a piece, otherwise every
   // tile plus block 0's state set-up (CTAs without a piece skip the counter)
@@ -257,7 +257,7 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
   __syncthreads();
   if (s_last) {
     __threadfence();
-    if (tid < 32) sel_choose_warp(sel.w, st, m, n, nnz, sel);
+    if (tid < 32) sel_choose_warp(sel.w, st, m, n, nnz, sel);  // (sel.rule: the rule instead)
     if (tid == 0) st->k1_done = 0u;
   }
 }

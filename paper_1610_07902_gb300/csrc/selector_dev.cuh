@@ -88,6 +88,20 @@ __device__ __forceinline__ int sel_pick_warp(const float* __restrict__ w, const 
   return bi < SEL_OUT ? bi : 4;
 }
 
+// The direction-optimizing rule with two fixed thresholds (Beamer, Asanovic
+// and Patterson, "Direction-Optimizing Breadth-First Search", SC 2012, with
+// their alpha = 14 and beta = 24), the baseline the learned selector is
+// measured against: from push to pull once the frontier's edges exceed the
+// unvisited vertices' edges / alpha, back to push once the frontier holds
+// fewer than n / beta vertices.  Returns 1 for pull.
+constexpr int RULE_ALPHA = 14, RULE_BETA = 24;
+__device__ __forceinline__ int rule_direction(int prev_dir, int32_t f, long long W, long long edges_unvisited,
+                                              int32_t n, int allow_pull) {
+  if (!allow_pull) return 0;
+  if (prev_dir == 0) return W * RULE_ALPHA > edges_unvisited ? 1 : 0;
+  return (long long)f * RULE_BETA < (long long)n ? 0 : 1;
+}
+
 // Device-side choice for this call, run by one full warp: features -> MLP ->
 // argmin over the allowed schedules -> state (direction, quantum, bucket
 // width).  Inside a graph, the two conditional handles (when given) select
@@ -95,6 +109,23 @@ __device__ __forceinline__ int sel_pick_warp(const float* __restrict__ w, const 
 __device__ __forceinline__ void sel_choose_warp(const float* __restrict__ w, DevState* st, int32_t m,
                                                 int32_t n, int64_t nnz, const SelArgs& a) {
   const int lwb_lo = a.lwb_lo;
+  // a BFS level small enough for the direct form stays push: there it costs
+  // a few microseconds, less than any pull, whatever decides the others
+  const bool small_bfs = a.bfs && a.direct_max > 0 && __ldcg(&st->W) <= a.direct_max;
+  if (a.rule) {  // the baseline rule: the default push schedule, or pull
+    const long long W = __ldcg(&st->W);
+    const long long seen = __ldcg(&st->edges_seen) + W;
+    const int dir = small_bfs ? 0 : rule_direction(__ldcg(&st->dir), __ldcg(&st->f), W, nnz - seen, n, a.allow_pull);
+    if ((threadIdx.x & 31) == 0) {
+      st->edges_seen = seen;
+      const int id = dir ? 11 : 5;
+      st->sched = id;
+      st->dir = dir;
+      st->q = 2 * QF;
+      st->lwb = lwb_lo + 2;
+    }
+    return;
+  }
   float x[SEL_IN];
   sel_features(st, m, n, nnz, a.bfs, x);
   if ((threadIdx.x & 31) == 0) {  // kept for spmspv_last_features
@@ -119,7 +150,8 @@ __device__ __forceinline__ void sel_choose_warp(const float* __restrict__ w, Dev
     }
   }
   if (lane == 0) {
-    const int id = bi < SEL_OUT ? bi : 4;
+    int id = bi < SEL_OUT ? bi : 4;
+    if (small_bfs && id >= 6) id -= 6;  // the push schedule of the same quantum and width
     st->sched = id;
     st->dir = id / 6;
     st->q = ((id / 3) % 2) ? 2 * QF : QF;

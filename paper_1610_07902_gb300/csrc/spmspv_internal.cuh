@@ -103,6 +103,7 @@ struct DevState {
   long long fused_w[4];  //   their products, non-empty columns and largest column; [3]: the
   int32_t fused_fc[4];   //   counts of the frontier a launch starts from (zeroed by K1)
   int32_t fused_md[4];
+  long long edges_seen;  // BFS: column lengths summed over every frontier so far (the rule's m_u)
 };
 
 // Selector run inside the work scan by its last CTA to finish: weights (NULL:
@@ -111,10 +112,12 @@ struct DevState {
 // conditional handles of a graph level (use_cond = 0 outside such graphs).
 struct SelArgs {
   const float* w;
+  int rule;          // 1: the direction-optimizing rule decides instead of the network
   int allow_pull;
   int bfs;
   int use_cond;
   int lwb_lo;
+  int32_t direct_max;  // BFS: a level of at most this many products runs push (direct form)
   cudaGraphConditionalHandle c_push;
   cudaGraphConditionalHandle c_pull;
 };

@@ -58,6 +58,7 @@ SPMSPV_DEV_TIMEOUT = 2
 SPMSPV_DEV_INDEX = 4
 SPMSPV_DEV_BOUND = 8
 SPMSPV_SORT_X = 32
+SPMSPV_SCHED_RULE = 64
 
 
 def SPMSPV_SCHED_OPT(s: int) -> int:

@@ -51,6 +51,39 @@ def test_bfs_all_fixed_schedules(lib, name, make, sym):
             level, parent, nl = Ad.bfs(int(src))
             np.testing.assert_array_equal(level.cpu().numpy(), ref_level)
             assert nl == ref_nl
+        # the direction-optimizing rule (push or pull per level by two thresholds;
+        # push only without a pattern-symmetric handle)
+        level, parent, nl = Ad.bfs(int(src), S.SPMSPV_SCHED_RULE)
+        assert S.spmspv_device_status(Ad.handle) == 0
+        np.testing.assert_array_equal(level.cpu().numpy(), ref_level, err_msg="rule")
+        np.testing.assert_array_equal(parent.cpu().numpy(), ref_parent, err_msg="rule")
+        assert nl == ref_nl
+    Ad.close()
+
+
+def test_direction_rule_switches_to_pull_and_back(lib):
+    """On R-MAT the rule must take the pull direction for the wide middle levels
+    and come back to push for the last ones; the result is the oracle's."""
+    torch, S = lib
+    A = synth.rmat(16, seed=8, values=False)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
+    src = int(synth.sources(A.colptr, 1, seed=4)[0])
+    rl, rp, nl_ref, _, sizes = oracle.bfs(A.colptr, A.rowidx, src)
+    level, parent, nl = Ad.bfs(src, S.SPMSPV_SCHED_RULE)
+    np.testing.assert_array_equal(level.cpu().numpy(), rl)
+    np.testing.assert_array_equal(parent.cpu().numpy(), rp)
+    assert nl == nl_ref and S.spmspv_device_status(Ad.handle) == 0
+    # the rule's thresholds on the oracle's level sizes: some level is wide enough
+    deg = np.diff(A.colptr).astype(np.int64)
+    lv = rl
+    seen, pulls = 0, 0
+    for L in range(1, nl_ref):
+        W = int(deg[lv == L - 1].sum())
+        seen += W
+        pulls += int(W * 14 > A.nnz - seen)
+    assert pulls >= 1
+    with pytest.raises(S.SpmspvError):
+        Ad.bfs(src, S.SPMSPV_SCHED_RULE | S.SPMSPV_SCHED_AUTO)
     Ad.close()
 
 
