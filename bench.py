@@ -730,6 +730,77 @@ def bench_selector_heldout(S, dev):
     return out
 
 
+def profile_case(args, S, dev):
+    """One kernel family on its own, for profiler captures: warm-up and
+    timed steps of that workload only, one short JSON line.  Cases:
+      pull     forced pull schedule (k_pull_scatter, k_pull_rows, k_pull_clear),
+               (+,*) on R-MAT s<scale> with x of --nnz-x entries
+      sortx    presort of x on the device (k_sortx_*) before the product
+      bfs      BFS from one source under the fixed schedule (a graph loop)
+      bfs_auto BFS under the learned schedule (persistent kernel + graph loop)
+      grid_auto the same on the 3D grid of side --grid (persistent kernel)
+      cc, mis, mcm   the graph algorithms (one graph loop each)
+      msbfs    multi-source BFS from 64 sources (batched lanes)"""
+    import torch
+    import synth
+    stream = torch.cuda.current_stream(dev)
+    case = args.case
+    if case == "grid_auto":
+        A = synth.grid3d(args.grid, args.grid, args.grid, 0.05, seed=3, values=False)
+    else:
+        A = synth.rmat(args.scale, EDGE_FACTOR, seed=SEED, values=case in ("pull", "sortx"))
+    sym = S.SPMSPV_CSC_SYMMETRIC if case in ("pull", "sortx") else S.SPMSPV_CSC_PATTERN_SYMMETRIC
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val, flags=sym, device=dev)
+    params = selector_params()
+    if params is not None:
+        S.spmspv_selector_set(Ad.handle, params)
+    if case in ("pull", "sortx"):
+        xi_, xv_ = synth.frontier(A.n, min(args.nnz_x, A.n), seed=1, stream=2)
+        xi, xv = torch.from_numpy(xi_).to(dev), torch.from_numpy(xv_).to(dev)
+        cap = A.m
+        yi = torch.empty(cap, dtype=torch.int32, device=dev)
+        yv = torch.empty(cap, dtype=torch.float32, device=dev)
+        nz = torch.zeros(1, dtype=torch.int32, device=dev)
+        opts = S.SPMSPV_SCHED_OPT(11) if case == "pull" else S.SPMSPV_SORT_X
+        step = lambda: S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, xi, xv, xi_.size, None, opts, yi, yv,
+                                    cap, nz, stream)
+    elif case in ("bfs", "bfs_auto", "grid_auto"):
+        src = int(synth.sources(A.colptr, 1, seed=2)[0]) if case != "grid_auto" else \
+            (args.grid // 2) * args.grid * args.grid + (args.grid // 2) * args.grid + args.grid // 2
+        lv = torch.empty(A.n, dtype=torch.int32, device=dev)
+        pa = torch.empty_like(lv)
+        nl = torch.zeros(1, dtype=torch.int32, device=dev)
+        opts = S.SPMSPV_SCHED_OPT(5) if case == "bfs" else S.SPMSPV_SCHED_AUTO
+        step = lambda: S.spmspv_bfs(Ad.handle, src, lv, pa, nl, opts, stream)
+    elif case == "cc":
+        lab = torch.empty(A.n, dtype=torch.int32, device=dev)
+        step = lambda: S.spmspv_cc(Ad.handle, lab, None, 0, stream)
+    elif case == "mis":
+        g = torch.Generator(device="cpu").manual_seed(7)
+        prio = torch.randperm(A.n, generator=g).to(torch.int32).to(dev)
+        ins = torch.empty(A.n, dtype=torch.int32, device=dev)
+        step = lambda: S.spmspv_mis(Ad.handle, prio, ins, None, 0, stream)
+    elif case == "mcm":
+        mr = torch.empty(A.m, dtype=torch.int32, device=dev)
+        mc = torch.empty(A.n, dtype=torch.int32, device=dev)
+        step = lambda: S.spmspv_mcm(Ad.handle, mr, mc, None, None, 0, stream)
+    elif case == "msbfs":
+        B = 64
+        srcs = torch.from_numpy(synth.sources(A.colptr, B, seed=5).astype(np.int32)).to(dev)
+        lv = torch.empty(B * A.n, dtype=torch.int32, device=dev)
+        pa = torch.empty_like(lv)
+        step = lambda: S.spmspv_msbfs(Ad.handle, B, srcs, lv, pa, None, S.SPMSPV_SCHED_OPT(5), 8, stream)
+    else:
+        raise SystemExit("unknown case %s" % case)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t = _events_ms(lambda: [step() for _ in range(args.steps)], stream, 1) / max(args.steps, 1)
+    print(json.dumps({"case": case, "scale": args.scale, "ms_per_step": t,
+                      "status": S.spmspv_device_status(Ad.handle)}), flush=True)
+    Ad.close()
+
+
 def reference_arm(args, rank):
     if rank != 0:
         return
@@ -777,6 +848,10 @@ def main():
                     help="warm-up and timed steps only (for profiler captures)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the BFS (fixed vs learned) and batched measurements")
+    ap.add_argument("--case", default=None,
+                    choices=["pull", "sortx", "bfs", "bfs_auto", "grid_auto", "cc", "mis", "mcm", "msbfs"],
+                    help="run one kernel family only (for profiler captures)")
+    ap.add_argument("--grid", type=int, default=64, help="grid side of --case grid_auto")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -795,6 +870,9 @@ def main():
     torch.cuda.set_device(local)
     from paper_1610_07902_gb300 import spmspv as S
     S.load()
+    if args.case:
+        profile_case(args, S, torch.device("cuda", local))
+        return
 
     F_ = args.nnz_x
     A, x_idx, x_val = make_inputs(args.scale, F_)
