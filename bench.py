@@ -41,7 +41,8 @@ def kernels_hash():
     import hashlib
     h = hashlib.sha256()
     base = os.path.join(ROOT, "paper_1610_07902_gb300", "csrc")
-    for name in ("kernels.cu", "spmspv_internal.cuh", "device_util.cuh", "selector_dev.cuh"):
+    for name in ("kernels.cu", "expand_dev.cuh", "spmspv_internal.cuh", "device_util.cuh",
+                 "selector_dev.cuh"):
         with open(os.path.join(base, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -740,16 +741,23 @@ def profile_case(args, S, dev):
       bfs_auto BFS under the learned schedule (persistent kernel + graph loop)
       grid_auto the same on the 3D grid of side --grid (persistent kernel)
       cc, mis, mcm   the graph algorithms (one graph loop each)
-      msbfs    multi-source BFS from 64 sources (batched lanes)"""
+      msbfs    multi-source BFS from 64 sources (batched lanes)
+      batched  256 frontiers of log-uniform size in [1, 10^5] (R-MAT seed 4) as
+               one persistent launch under schedule --sched
+      batched_lanes  the same batch on 16 lanes"""
     import torch
     import synth
     stream = torch.cuda.current_stream(dev)
     case = args.case
     if case == "grid_auto":
         A = synth.grid3d(args.grid, args.grid, args.grid, 0.05, seed=3, values=False)
+    elif case in ("batched", "batched_lanes"):
+        A = synth.rmat(args.scale, EDGE_FACTOR, seed=4)
     else:
         A = synth.rmat(args.scale, EDGE_FACTOR, seed=SEED, values=case in ("pull", "sortx"))
-    sym = S.SPMSPV_CSC_SYMMETRIC if case in ("pull", "sortx") else S.SPMSPV_CSC_PATTERN_SYMMETRIC
+    extra = {}
+    sym = S.SPMSPV_CSC_SYMMETRIC if case in ("pull", "sortx", "batched", "batched_lanes") else \
+        S.SPMSPV_CSC_PATTERN_SYMMETRIC
     Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val, flags=sym, device=dev)
     params = selector_params()
     if params is not None:
@@ -784,6 +792,24 @@ def profile_case(args, S, dev):
         mr = torch.empty(A.m, dtype=torch.int32, device=dev)
         mc = torch.empty(A.n, dtype=torch.int32, device=dev)
         step = lambda: S.spmspv_mcm(Ad.handle, mr, mc, None, None, 0, stream)
+    elif case in ("batched", "batched_lanes"):
+        B = 256
+        rng = np.random.default_rng(4)
+        sizes = np.maximum(1, np.floor(10 ** rng.uniform(0, 5, B))).astype(np.int64)
+        fronts = [synth.frontier(A.n, int(min(f, A.n)), seed=100 + b, stream=2) for b, f in enumerate(sizes)]
+        x_cnt = np.array([f[0].shape[0] for f in fronts], np.int32)
+        x_off = np.concatenate([[0], np.cumsum(x_cnt)[:-1]]).astype(np.int32)
+        td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        bx = (td(x_off), td(x_cnt), td(np.concatenate([f[0] for f in fronts])),
+              td(np.concatenate([f[1] for f in fronts])))
+        by = (td((np.arange(B, dtype=np.int64) * A.m).astype(np.int32)), td(np.full(B, A.m, np.int32)))
+        yi = torch.empty(B * A.m, dtype=torch.int32, device=dev)
+        yv = torch.empty(B * A.m, dtype=torch.float32, device=dev)
+        nz = torch.zeros(B, dtype=torch.int32, device=dev)
+        lanes = S.SPMSPV_LANES_PERSISTENT if case == "batched" else 16
+        extra["products"] = int(sum(int(np.diff(A.colptr)[f[0]].sum()) for f in fronts))
+        step = lambda: S.spmspv_run_batched(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, B, *bx, None, 0,
+                                            S.SPMSPV_SCHED_OPT(args.sched), *by, yi, yv, nz, lanes, stream)
     elif case == "msbfs":
         B = 64
         srcs = torch.from_numpy(synth.sources(A.colptr, B, seed=5).astype(np.int32)).to(dev)
@@ -796,8 +822,15 @@ def profile_case(args, S, dev):
         step()
     torch.cuda.synchronize()
     t = _events_ms(lambda: [step() for _ in range(args.steps)], stream, 1) / max(args.steps, 1)
-    print(json.dumps({"case": case, "scale": args.scale, "ms_per_step": t,
-                      "status": S.spmspv_device_status(Ad.handle)}), flush=True)
+    if "products" in extra:
+        extra["gteps"] = extra["products"] / (t * 1e-3) / 1e9
+    if case == "batched":
+        ph, waves = S.spmspv_batched_phase_times(Ad.handle)
+        extra["phases_ms"] = dict(zip(["scan", "plan", "tile_starts", "expand", "merge", "launch"],
+                                      [round(float(v), 4) for v in ph]))
+        extra["waves"] = waves
+    print(json.dumps(dict({"case": case, "scale": args.scale, "ms_per_step": t,
+                           "status": S.spmspv_device_status(Ad.handle)}, **extra)), flush=True)
     Ad.close()
 
 
@@ -849,9 +882,11 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the BFS (fixed vs learned) and batched measurements")
     ap.add_argument("--case", default=None,
-                    choices=["pull", "sortx", "bfs", "bfs_auto", "grid_auto", "cc", "mis", "mcm", "msbfs"],
+                    choices=["pull", "sortx", "bfs", "bfs_auto", "grid_auto", "cc", "mis", "mcm", "msbfs", "batched",
+                             "batched_lanes"],
                     help="run one kernel family only (for profiler captures)")
     ap.add_argument("--grid", type=int, default=64, help="grid side of --case grid_auto")
+    ap.add_argument("--sched", type=int, default=5, help="push schedule of --case batched")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

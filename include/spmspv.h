@@ -212,15 +212,29 @@ int spmspv_bfs(spmspv_handle* h, int32_t src, int32_t* level, int32_t* parent,
                int32_t* d_nlevels, uint32_t opts, spmspv_stream_t stream);
 
 /*
- * Batched form: B independent products y_b <- A (+).(x) x_b [under mask_b] in
- * one graph launch (no counterpart in the paper; its Sec. I and III-A note that
- * repeated small products are dominated by overhead).  The batch runs as
- * `lanes` concurrent device-side loops that each take the next frontier from a
- * shared queue and run the three kernels of spmspv_run on it with their own
- * workspace; every y_b equals what spmspv_run gives for x_b with the same
- * (push) schedule.  All arrays are device arrays:
+ * Batched form: B independent products y_b <- A (+).(x) x_b [under mask_b]
+ * (no counterpart in the paper; its Sec. I and III-A note that repeated small
+ * products are dominated by overhead).  Two forms run it:
+ *   persistent  one cooperative kernel launch for the whole batch: its CTAs
+ *               scan every frontier, sort each frontier of at most 4096
+ *               products in one CTA, and run the expand and merge steps of the
+ *               larger ones with buckets keyed by (frontier, row block), taking
+ *               tiles and buckets of all frontiers from shared device queues.
+ *               x_cnt is read on the host first (one synchronisation of
+ *               `stream`) to size the work arrays; the launch also needs every
+ *               CTA resident (a cooperative launch).  Its buckets hold m/256,
+ *               m/128 or m/64 rows by the schedule's width (at most 2^15 rows;
+ *               m <= 2^26).
+ *   lanes       `lanes` concurrent device-side loops (a graph with conditional
+ *               WHILE nodes) that each take the next frontier from a queue and
+ *               run the three kernels of spmspv_run on it with their own
+ *               workspace (no host synchronisation).
+ * Either way y_b has the index set spmspv_run gives for x_b, ascending, and
+ * the same values up to the order of the float additions.  All arrays are
+ * device arrays:
  *   x_off[B], x_cnt[B]   frontier b is x_idx[x_off[b] .. x_off[b]+x_cnt[b]) and the
- *                        same slice of x_val (ignored for OR_AND_BOOL).
+ *                        same slice of x_val (ignored for OR_AND_BOOL); each
+ *                        0 <= x_cnt[b] <= n, the ids of one frontier distinct.
  *   masks, mask_stride   NULL, or frontier b's complemented mask at
  *                        masks + b*mask_stride (uint32 words, stride >= ceil(m/32));
  *                        opts must then contain SPMSPV_MASK_COMPLEMENT.
@@ -229,22 +243,45 @@ int spmspv_bfs(spmspv_handle* h, int32_t src, int32_t* level, int32_t* parent,
  *                        (the size needed when it exceeds y_cap[b]).
  *   opts                 SPMSPV_SCHED_OPT(s) (pull schedules run as their push
  *                        form), SPMSPV_MASK_COMPLEMENT.
- *   lanes                1..16.  Lane workspaces (one per lane, as for a
- *                        handle) and the graph are created on first use.
- *                        0 = autotuned: lanes and push schedule are taken from
- *                        the handle's tuning cache for this batch profile
+ *   lanes                0: autotuned persistent form: the push schedule is taken
+ *                        from the handle's tuning cache for this batch profile
  *                        (spmspv_tune_key), or, on the first call with a new
- *                        profile, found by running the batch under every
- *                        candidate (lanes 2/4/8/16 x push schedules 0..5, two
- *                        runs each, the second timed) and cached.  Any schedule
- *                        in opts is then ignored.  lanes = 0 synchronises the
- *                        stream (to read x_cnt), so it must not be captured.
+ *                        profile, found by running the batch under every push
+ *                        schedule 0..5 (two runs each, the second timed) and
+ *                        cached (an entry set with spmspv_tune_set to lanes
+ *                        1..16 runs the lanes form instead).  Any schedule in
+ *                        opts is then ignored.
+ *                        SPMSPV_LANES_PERSISTENT: the persistent form with the
+ *                        schedule in opts (or the handle's default).
+ *                        1..16: the lanes form with that many lanes; lane
+ *                        workspaces (one per lane, as for a handle) and the graph
+ *                        are created on first use.
+ *                        Forms 0 and SPMSPV_LANES_PERSISTENT synchronise the
+ *                        stream, so they must not be captured.
+ * Errors: SPMSPV_ERR_ARG for a bad argument (an x_cnt outside [0, n] is found
+ * on the host in the persistent form), SPMSPV_ERR_UNSUPPORTED for a batch of
+ * 2^31 or more x entries or tiles, SPMSPV_ERR_OOM when work arrays cannot
+ * grow.  Device-side problems (y too small, repeated ids) are reported by
+ * spmspv_device_status.
  */
+#define SPMSPV_LANES_PERSISTENT (-1)
 int spmspv_run_batched(spmspv_handle* h, int semiring, int32_t B, const int32_t* x_off,
                        const int32_t* x_cnt, const int32_t* x_idx, const void* x_val,
                        const uint32_t* masks, int64_t mask_stride, uint32_t opts,
                        const int32_t* y_off, const int32_t* y_cap, int32_t* y_idx, void* y_val,
                        int32_t* d_nnz_y, int32_t lanes, spmspv_stream_t stream);
+
+/*
+ * Device-clock durations (ms) of the phases of the handle's last persistent
+ * batched launch (spmspv_run_batched, lanes 0 or SPMSPV_LANES_PERSISTENT):
+ * ms[0] work scan, ms[1] plan, ms[2] tile starts, ms[3] expand (Step 1 and
+ * the one-CTA small frontiers, summed over waves), ms[4] merge (Steps 2-3,
+ * summed over waves), ms[5] the whole launch; min(capacity, 6) entries are
+ * written.  *waves (may be NULL) receives the launch's number of waves.
+ * Synchronises the handle's last stream.  SPMSPV_ERR_STATE before any such
+ * launch.
+ */
+int spmspv_batched_phase_times(spmspv_handle* h, double* ms, int32_t capacity, int32_t* waves);
 
 /*
  * Multi-source BFS: B searches (the BFS of spmspv_bfs from each of sources[B],

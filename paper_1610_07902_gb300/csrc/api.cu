@@ -559,6 +559,7 @@ int spmspv_destroy(spmspv_handle* h) {
   }
   release_bfs_graphs(h);
   release_batch(h);
+  release_k6(h);
   release_cc(h);
   release_mis(h);
   release_mcm(h);

@@ -1,7 +1,9 @@
-// Batched SpMSpV: B independent products y_b <- A (+).(x) x_b in one graph
-// launch.  The paper runs one product per call; repeated small calls are
-// where it notes most time goes to overhead (Sec. I, Sec. III-A), so the
-// batch is run as L concurrent "lanes": each lane is a device-side WHILE
+// Batched SpMSpV, the lanes form: B independent products y_b <- A (+).(x) x_b
+// in one graph launch (the persistent one-launch form is batched_k6.cu; the
+// multi-source BFS and ACL run on the lanes).  The paper runs one product
+// per call; repeated small calls are where it notes most time goes to
+// overhead (Sec. I, Sec. III-A), so the batch is run as L concurrent "lanes":
+// each lane is a device-side WHILE
 // loop (a conditional graph node) that pops the next frontier from a queue
 // shared by the lanes and runs the same three kernels (work scan ->
 // expand/scatter -> bucket merge) on it with its own workspace.  No frontier
@@ -370,8 +372,13 @@ extern "C" int spmspv_run_batched(spmspv_handle* h, int semiring, int32_t B, con
   if (masks && !(opts & SPMSPV_MASK_COMPLEMENT))
     return fail(SPMSPV_ERR_UNSUPPORTED, "batched masks are complemented masks");
   cudaStream_t s = (cudaStream_t)stream;
+  auto persistent = [&](uint32_t o) {
+    return run_batched_k6(h, semiring, B, x_off, x_cnt, x_idx, (const uint32_t*)x_val, masks, mask_stride, o,
+                          y_off, y_cap, y_idx, (uint32_t*)y_val, d_nnz_y, s);
+  };
+  if (lanes == SPMSPV_LANES_PERSISTENT) return persistent(opts);
   if (lanes != 0) return run_batched(h, semiring, false, B, v, opts, lanes, s);
-  // autotuned: the profile needs the total frontier length
+  // autotuned (persistent form): the profile needs the total frontier length
   std::vector<int32_t> cnt(B);
   cudaError_t e = cudaMemcpyAsync(cnt.data(), x_cnt, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -379,8 +386,12 @@ extern "C" int spmspv_run_batched(spmspv_handle* h, int semiring, int32_t B, con
   int64_t total = 0;
   for (int32_t c : cnt) total += c;
   const uint32_t base = opts & ~(uint32_t)(SPMSPV_SCHED_FORCE | SPMSPV_SCHED_AUTO | SPMSPV_SCHED_OPT(0xFFu));
-  return tune_and_run(h, tune_key(0, semiring, masks != nullptr, B, total), s,
-                      [&](int32_t ln, uint32_t so) { return run_batched(h, semiring, false, B, v, base | so, ln, s); });
+  return tune_and_run(
+      h, tune_key(0, semiring, masks != nullptr, B, total), s,
+      [&](int32_t ln, uint32_t so) {
+        return ln == 0 ? persistent(base | so) : run_batched(h, semiring, false, B, v, base | so, ln, s);
+      },
+      SPMSPV_NUM_SCHEDULES / 2, true);
 }
 
 // ---------------------------------------------------------------------------

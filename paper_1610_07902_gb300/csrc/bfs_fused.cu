@@ -60,40 +60,10 @@ struct FusedArgs {
   int32_t direct_max;
 };
 
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void red_release_add_u32(uint32_t* p, uint32_t v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 // Grid barrier (every CTA resident: cooperative launch).  The arrival count
-// only grows during a search (reset when it starts): barrier number `epoch`
-// is passed once the count reaches epoch * gridDim.x.  A CTA's arrival is a
-// release add after its writes; the wait polls with acquire loads, at most
-// SPIN_LIMIT times, after which it records ST_TIMEOUT and returns false.
+// only grows during a search (reset when it starts).
 __device__ bool fused_barrier(DevState* st, uint32_t epoch, int* s_ok) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    red_release_add_u32(&st->fused_count, 1u);
-    const uint32_t target = epoch * gridDim.x;
-    int ok = 1;
-    uint32_t spins = 0;
-    while ((int32_t)(ld_acquire_u32(&st->fused_count) - target) < 0) {
-      if (++spins > SPIN_LIMIT) {
-        atomicOr(&st->status, ST_TIMEOUT);
-        ok = 0;
-        break;
-      }
-      __nanosleep(20);
-    }
-    *s_ok = ok;
-  }
-  __syncthreads();
-  return *s_ok != 0;
+  return grid_barrier(&st->fused_count, epoch, &st->status, s_ok);
 }
 
 template <typename T, typename Op>

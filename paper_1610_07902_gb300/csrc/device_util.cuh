@@ -21,6 +21,43 @@ __device__ __forceinline__ void lb_store(unsigned long long* p, unsigned long lo
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_add_u32(uint32_t* p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier of a kernel whose CTAs are all resident (cooperative launch).
+// `count` only grows during the launch (zero when it starts): barrier number
+// `epoch` (1, 2, ...) is passed once it reaches epoch * gridDim.x.  A CTA's
+// arrival is a release add after its writes; the wait polls with acquire
+// loads, at most SPIN_LIMIT times, after which it sets ST_TIMEOUT in
+// *status and returns false (every CTA then leaves the kernel).
+__device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t epoch, uint32_t* status, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    red_release_add_u32(count, 1u);
+    const uint32_t target = epoch * gridDim.x;
+    int ok = 1;
+    uint32_t spins = 0;
+    while ((int32_t)(ld_acquire_u32(count) - target) < 0) {
+      if (++spins > SPIN_LIMIT) {
+        atomicOr(status, ST_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(20);
+    }
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
 // Streaming load (evict-first): matrix entries are read once per call.
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
 __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
@@ -29,12 +66,12 @@ __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
 // the warp publishes the tile's aggregate, then reads the status words of
 // its LB_WIN*32 nearest predecessors at once and sums back to the nearest
 // one that holds an inclusive prefix, sliding the window when none does.
-// Waits are bounded: on give-up the status word gets ST_TIMEOUT and the
-// words still missing count as empty inclusive prefixes.
+// Waits are bounded: on give-up *err gets ST_TIMEOUT and the words still
+// missing count as empty inclusive prefixes.
 constexpr int LB_WIN = 4;
 
 __device__ __forceinline__ unsigned long long warp_lookback(unsigned long long* status, uint32_t tile,
-                                            unsigned long long agg, DevState* st,
+                                            unsigned long long agg, uint32_t* err,
                                             uint32_t spin_limit = SPIN_LIMIT) {
   const int lane = threadIdx.x & 31;
   if (tile == 0) {
@@ -74,7 +111,7 @@ __device__ __forceinline__ unsigned long long warp_lookback(unsigned long long* 
       }
       if (all_ready) break;
       if (++spins > spin_limit) {
-        if (lane == 0) atomicOr(&st->status, ST_TIMEOUT);
+        if (lane == 0) atomicOr(err, ST_TIMEOUT);
 #pragma unroll
         for (int k = 0; k < LB_WIN; ++k)
           if ((s[k] & LB_FLAG_MASK) == 0ull) s[k] = LB_FLAG_INC;
@@ -100,6 +137,13 @@ __device__ __forceinline__ unsigned long long warp_lookback(unsigned long long* 
   }
   if (lane == 0) lb_store(status + tile, LB_FLAG_INC | (excl + agg));
   return excl;
+}
+
+// The same, recording a timeout in the device state's status word.
+__device__ __forceinline__ unsigned long long warp_lookback(unsigned long long* status, uint32_t tile,
+                                            unsigned long long agg, DevState* st,
+                                            uint32_t spin_limit = SPIN_LIMIT) {
+  return warp_lookback(status, tile, agg, &st->status, spin_limit);
 }
 
 // Exclusive prefix sum over the block.  `sh` holds NT/32 + 1 shared

@@ -40,7 +40,8 @@ struct spmspv_handle {
   // learned schedule selector
   int sel_ready;        // weights present
   float* sel_w;         // device weights (layout in selector.cu)
-  void* batch;          // BatchState* of the batched form (batched.cu), lazily created
+  void* batch;          // BatchState* of the batched lanes (batched.cu), lazily created
+  void* k6;             // K6Buffers* of the persistent batched form (batched_k6.cu), lazily created
   void* tune;           // TuneCache* of the batched-form autotuner (autotune.cu), lazily created
   // pull direction (dense frontier) buffers, allocated on first use
   uint32_t* xbits;      // [ceil(n/32)] frontier bitmap
@@ -112,6 +113,7 @@ int run_pull_if_available(spmspv_handle* h, int sem, const int32_t* x_idx, const
 void release_extras(spmspv_handle* h);
 void release_bfs_graphs(spmspv_handle* h);
 void release_batch(spmspv_handle* h);
+void release_k6(spmspv_handle* h);
 void release_cc(spmspv_handle* h);
 void release_mis(spmspv_handle* h);
 void release_mcm(spmspv_handle* h);
@@ -131,6 +133,12 @@ int build_while_graph(spmspv_handle* h,
 int graph_spmspv(spmspv_handle* h, int sem, const Sched& sc, const int32_t* x_idx,
                  const uint32_t* x_val, const int32_t* f_dev, const uint32_t* skip_rows,
                  int32_t* y_idx, uint32_t* y_val, cudaStream_t s);
+// The batched form as one persistent launch (batched_k6.cu); reads x_cnt on
+// the host first (one synchronisation of `s`).  masks are complemented.
+int run_batched_k6(spmspv_handle* h, int sem, int32_t B, const int32_t* x_off, const int32_t* x_cnt,
+                   const int32_t* x_idx, const uint32_t* x_val, const uint32_t* masks, int64_t mask_stride,
+                   uint32_t opts, const int32_t* y_off, const int32_t* y_cap, int32_t* y_idx, uint32_t* y_val,
+                   int32_t* d_nnz_y, cudaStream_t s);
 // Reads and clears the status words of the batched lanes' workspaces (after
 // the caller has synchronised the stream); CUDA errors are returned in *e.
 uint32_t batch_collect_status(spmspv_handle* h, cudaError_t* e);
@@ -139,9 +147,10 @@ void release_tune(spmspv_handle* h);
 uint64_t tune_key(int kind, int sem, int masked, int32_t B, int64_t total_f);
 // Runs `run(lanes, schedule opts)` with the cached choice for `key`, or times
 // every candidate on `s` (each run twice, the second timed) and caches the best.
-// Candidates: lanes 2/4/8/16 x push schedules 0..nsched-1.
+// Candidates: lanes 2/4/8/16 x push schedules 0..nsched-1; with
+// persistent = true, only the persistent form (lanes 0) x the schedules.
 int tune_and_run(spmspv_handle* h, uint64_t key, cudaStream_t s,
-                 const std::function<int(int32_t, uint32_t)>& run, int nsched = 6);
+                 const std::function<int(int32_t, uint32_t)>& run, int nsched = 6, bool persistent = false);
 cudaError_t alloc_pull_buffers(spmspv_handle* h);
 int pull_available(const spmspv_handle* h, int sem);
 // BFS pull kernel of a batched lane (the lane's job names the source's arrays)

@@ -28,6 +28,7 @@
 #include <stdint.h>
 
 #include "device_util.cuh"
+#include "expand_dev.cuh"
 #include "selector_dev.cuh"
 #include "spmspv_internal.cuh"
 
@@ -276,21 +277,6 @@ cudaError_t launch_k1(int sem, const Matrix& A, const Workspace& ws, int nb_fine
 }
 
 // ------------------------------------------------------------------------
-// Semiring helpers
-// ------------------------------------------------------------------------
-template <int SEM>
-__device__ __forceinline__ uint32_t sr_identity() {
-  return SEM == kMinSelect2nd ? 0x7fffffffu : 0u;  // min: INT32_MAX; plus: +0.0f
-}
-
-// SPA update in shared memory (atomic: other threads may hit the same row)
-template <int SEM>
-__device__ __forceinline__ void spa_apply(uint32_t* spa, uint32_t r, uint32_t v) {
-  if (SEM == kPlusTimes) atomicAdd(reinterpret_cast<float*>(spa + r), __uint_as_float(v));
-  else if (SEM == kMinSelect2nd) atomicMin(reinterpret_cast<int*>(spa + r), (int)v);
-}
-
-// ------------------------------------------------------------------------
 // K2: expand + multiply + bucket scatter
 // ------------------------------------------------------------------------
 
@@ -311,56 +297,6 @@ __device__ __forceinline__ void spa_apply(uint32_t* spa, uint32_t r, uint32_t v)
 // hub product costs what any product costs and no warp branches on it.
 // IT: products per thread when the host knows the work quantum (4 or 8),
 // 0 when the device decides it; MASKED: a mask may be given.
-
-// The products of one warp's chunk: entry lookup, coalesced loads of row ids
-// and values, the multiply (FULL: the tile holds items*K2_THREADS products,
-// no bounds test).
-template <int SEM, int IT, bool FULL>
-__device__ __forceinline__ void k2_gather(const int32_t* __restrict__ rowidx, const float* __restrict__ val,
-                                          const uint32_t* hbits, const int32_t* kbase, const uint32_t* kx,
-                                          int items, int warp, int lane, int32_t p0, int32_t np, int64_t nnz,
-                                          uint32_t (&rrow)[K2_IMAX], uint32_t (&rval)[K2_IMAX]) {
-  const int w0 = warp * items;  // bitmap word of this warp's first 32 products
-  const int32_t pw0 = w0 * 32 + lane;
-  int ent = 0;                  // entry starts before word w0
-  for (int j = lane; j < w0; j += 32) ent += __popc(hbits[j]);
-  ent = __reduce_add_sync(0xffffffffu, ent);
-  const uint32_t le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
-  uint32_t xi[K2_IMAX];
-  float av[K2_IMAX];
-  // every item's address, then all loads in flight at once
-#pragma unroll
-  for (int i = 0; i < K2_IMAX; ++i) {
-    rrow[i] = 0xffffffffu;
-    xi[i] = 0u;
-    av[i] = 1.0f;
-    if (IT ? i < IT : i < items) {
-      const int32_t pl = pw0 + 32 * i;
-      const uint32_t hw = hbits[w0 + i];
-      const int e = ent + __popc(hw & le);
-      ent += __popc(hw);
-      if (FULL || pl < np) {
-        const int32_t pos = kbase[e] + p0 + pl;
-        xi[i] = kx[e];
-        if ((uint32_t)pos < (uint32_t)nnz) {  // always true with valid inputs
-          rrow[i] = (uint32_t)ld_stream(rowidx + pos);
-          if (SEM == kPlusTimes && val) av[i] = ld_stream(val + pos);
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < K2_IMAX; ++i) {
-    uint32_t v = 0u;
-    if (SEM == kPlusTimes) {
-      v = __float_as_uint(__fmul_rn(av[i], __uint_as_float(xi[i])));
-      if (v == 0x80000000u) v = 0u;  // -0.0 -> +0.0: K3's dense SPA reserves -0.0 for "empty"
-    } else if (SEM == kMinSelect2nd) {
-      v = xi[i];
-    }
-    rval[i] = v;
-  }
-}
 
 // Bucket of a product row id: its row range, the hub bucket nb, or -1 for
 // "no product" and for an id outside [0, m) that is not a hub label (which
@@ -741,10 +677,6 @@ constexpr int K3_WARPS = K3_THREADS / 32;
 constexpr int K3_DENSE_MIN_WB = 32 * K3_WARPS;  // every warp walks whole 32-row words
 constexpr int K3_DENSE_DIV = 8;                 // dense when entries >= rows / 8
 
-template <int SEM>
-__device__ __forceinline__ uint32_t spa_empty() {
-  return SEM == kPlusTimes ? 0x80000000u : 0x7fffffffu;
-}
 
 // The end of a BFS level that K2 ran in the direct form: the level's count,
 // the per-call state the work scan starts from, and (when a later level may

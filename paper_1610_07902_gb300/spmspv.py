@@ -59,6 +59,7 @@ SPMSPV_DEV_INDEX = 4
 SPMSPV_DEV_BOUND = 8
 SPMSPV_SORT_X = 32
 SPMSPV_SCHED_RULE = 64
+SPMSPV_LANES_PERSISTENT = -1  # spmspv_run_batched: the persistent one-launch form
 
 
 def SPMSPV_SCHED_OPT(s: int) -> int:
@@ -113,6 +114,7 @@ def load(build_if_missing: bool = True):
         lib.spmspv_run_batched.argtypes = [_P, ctypes.c_int, ctypes.c_int32, _P, _P, _P, _P, _P,
                                            ctypes.c_int64, ctypes.c_uint32, _P, _P, _P, _P, _P,
                                            ctypes.c_int32, _P]
+        lib.spmspv_batched_phase_times.argtypes = [_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         lib.spmspv_msbfs.argtypes = [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_uint32,
                                      ctypes.c_int32, _P]
         lib.spmspv_acl.argtypes = [_P, ctypes.c_int32, _P, ctypes.c_float, ctypes.c_float,
@@ -302,6 +304,17 @@ def spmspv_run_batched(h, semiring, B, x_off, x_cnt, x_idx, x_val, masks, mask_s
                                      _ptr(y_off), _ptr(y_cap), _ptr(y_idx), _ptr(y_val),
                                      _ptr(d_nnz_y), int(lanes), _stream(stream)),
            "spmspv_run_batched")
+
+
+def spmspv_batched_phase_times(h):
+    """(ms[6], waves) of the last persistent batched launch: scan, plan, tile
+    starts, expand, merge, whole launch (device clock)."""
+    import numpy as np
+    ms = np.zeros(6, dtype=np.float64)
+    w = ctypes.c_int32(0)
+    _check(load().spmspv_batched_phase_times(h, ms.ctypes.data, 6, ctypes.byref(w)),
+           "spmspv_batched_phase_times")
+    return ms, int(w.value)
 
 
 def spmspv_msbfs(h, B, sources, level, parent, nlevels, opts=0, lanes=8, stream=None):

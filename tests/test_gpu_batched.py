@@ -1,4 +1,5 @@
-"""Batched SpMSpV (concurrent lanes over a device-side frontier queue) and
+"""Batched SpMSpV (concurrent lanes over a device-side frontier queue, and
+the persistent one-launch form where noted) and
 multi-source BFS against the oracle: every frontier's y must equal the
 single-product result (index sets and integer values bit for bit, FP32 values
 within the parity tolerance)."""
@@ -110,7 +111,7 @@ def test_autotuned_batch_matches_and_caches(lib):
         nz = torch.zeros(B, dtype=torch.int32, device="cuda")
         S.spmspv_run_batched(Ad.handle, 0, B, *args, None, 0, 0, dev(y_off), dev(y_cap), yi, yv, nz, 0)
         lanes, sched, cached = S.spmspv_last_tuned(Ad.handle)
-        assert 2 <= lanes <= 16 and 0 <= sched < 6
+        assert lanes == 0 and 0 <= sched < 6  # the persistent form
         assert cached == (call == 1)
         outs.append((nz.cpu().numpy(), yi.cpu().numpy(), yv.cpu().numpy()))
     nz_h, yi_h, yv_h = outs[1]
@@ -123,7 +124,7 @@ def test_autotuned_batch_matches_and_caches(lib):
     ent = S.spmspv_tune_entries(Ad.handle)
     assert len(ent) == 1 and ent[0][0] == S.spmspv_tune_key(0, 0, 0, B, int(x_cnt.sum()))
     assert ent[0][3] > 0
-    # an override is used as given
+    # an override is used as given (lanes 3: the lanes form)
     S.spmspv_tune_set(Ad.handle, ent[0][0], 3, 5)
     S.spmspv_run_batched(Ad.handle, 0, B, *args, None, 0, 0, dev(y_off), dev(y_cap), yi, yv, nz, 0)
     assert S.spmspv_last_tuned(Ad.handle) == (3, 5, True)
@@ -217,7 +218,7 @@ def test_batched_edge_cases(lib):
     y_cap = np.full(B, A.m, np.int32)
     y_cap[small] = 10
     y_off = (np.arange(B) * A.m).astype(np.int32)
-    for lanes in (1, 4):
+    for lanes in (1, 4, S.SPMSPV_LANES_PERSISTENT):
         yi = torch.full((B * A.m,), -7, dtype=torch.int32, device="cuda")
         yv = torch.zeros(B * A.m, dtype=torch.float32, device="cuda")
         nz = torch.full((B,), -1, dtype=torch.int32, device="cuda")
