@@ -88,6 +88,7 @@ typedef struct spmspv_handle spmspv_handle;
                                      efficiency: more local column accesses for denser x);
                                      a counting sort over [0, n), about n/8 + 12 nnz(x)
                                      bytes of traffic; buffers of 16n bytes on first use */
+#define SPMSPV_BUCKETS_ONLY 128u   /* spmspv_run, (+,*): never the direct form (see below) */
 #define SPMSPV_SCHED_RULE 64u       /* spmspv_bfs only: push or pull per level by the
                                        direction-optimizing rule of Beamer, Asanovic and
                                        Patterson (SC 2012; two fixed thresholds, alpha = 14,
@@ -187,6 +188,14 @@ int spmspv_destroy(spmspv_handle* h);
  * Output order: y_idx is always produced in ascending order (each
  * row-range bucket is emitted in row order and buckets are concatenated in
  * order, Step 3 of Algorithm 1), so SPMSPV_SORTED_OUT costs nothing extra.
+ * Direct form: a (+,*) push product with at least m/2 products (decided on
+ * the device from the work scan) adds every product into a dense accumulator
+ * of m floats that the handle keeps in device memory (4m bytes, allocated at
+ * create when m <= 2^24; at these sizes it stays in L2), then reads the
+ * touched rows back in ascending order and resets them; this replaces the
+ * row-range buckets and the shared-memory SPA, with the same index set and
+ * values up to the order of the float additions.  SPMSPV_BUCKETS_ONLY keeps
+ * the bucketed form for every size.
  */
 int spmspv_run(spmspv_handle* h, int semiring, const int32_t* x_idx, const void* x_val,
                int32_t nnz_x, const uint32_t* mask, uint32_t opts, int32_t* y_idx,

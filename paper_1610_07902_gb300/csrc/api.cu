@@ -100,6 +100,12 @@ int check_handle(const spmspv_handle* h) {
   return SPMSPV_OK;
 }
 
+// Products from which a (+,*) call runs the direct form (0: never).
+static int32_t plus_direct_min(const spmspv_handle* h) {
+  if (!h->plus_direct || !h->ws.ydense) return 0;
+  return std::max<int32_t>(1, h->A.m / PLUS_DIRECT_DIV);
+}
+
 // The push-direction product: K1 -> K2 -> K3 on `s`.
 int run_push(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_val, int f,
              const int32_t* f_dev, const uint32_t* mask, int mask_comp, const Sched& sc,
@@ -119,15 +125,16 @@ int run_push(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_
   }
   if (e != cudaSuccess) return cuda_fail(e, "work scan launch");
   prof_mark(h, SPMSPV_STAGE_SCAN, s);
+  const int32_t pdm = bfs ? 0 : plus_direct_min(h);
   e = launch_k2(sem, h->A, h->ws, h->lwb_lo, h->nb_fine, mask, mask_comp, h->k2_grid, h->k2_smem, s, 0,
-                sc.q);
+                sc.q, 0, pdm);
   if (e != cudaSuccess) return cuda_fail(e, "expand/scatter launch");
   prof_mark(h, SPMSPV_STAGE_SCATTER, s);
   const size_t k3_smem = k3_smem_bytes(sc.lwb);
   const int nb = (int)(((int64_t)h->A.m + (1 << sc.lwb) - 1) >> sc.lwb);
   const int k3_grid = std::max(1, std::min(nb, h->sm_count * h->k3_bps[sc.lwb - h->lwb_lo]));
   e = launch_k3(sem, bfs, h->A, h->ws, h->lwb_lo, h->nb_fine, y_idx, y_val, y_cap, d_nnz_y,
-                mask_update, k3_grid, k3_smem, s);
+                mask_update, k3_grid, k3_smem, s, 0, 0, 0, 0, pdm);
   if (e != cudaSuccess) return cuda_fail(e, "bucket merge launch");
   prof_mark(h, SPMSPV_STAGE_MERGE, s);
   return SPMSPV_OK;
@@ -227,15 +234,16 @@ int run_auto(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_
   if (e != cudaSuccess) return cuda_fail(e, "work scan launch");
   prof_mark(h, SPMSPV_STAGE_SCAN, s);
   prof_mark(h, SPMSPV_STAGE_SELECT, s);
+  const int32_t pdm = plus_direct_min(h);
   e = launch_k2(sem, h->A, h->ws, h->lwb_lo, h->nb_fine, mask, mask_comp, h->k2_grid, h->k2_smem, s,
-                can_pull);
+                can_pull, 0, 0, pdm);
   if (e != cudaSuccess) return cuda_fail(e, "expand/scatter launch");
   prof_mark(h, SPMSPV_STAGE_SCATTER, s);
   const int lwb = h->lwb_lo + 2;  // shared memory for the widest bucket
   const int nb_max = (int)(((int64_t)h->A.m + (1 << h->lwb_lo) - 1) >> h->lwb_lo);
   const int k3_grid = std::max(1, std::min(nb_max, h->sm_count * h->k3_bps[2]));
   e = launch_k3(sem, false, h->A, h->ws, h->lwb_lo, h->nb_fine, y_idx, y_val, y_cap, d_nnz_y,
-                nullptr, k3_grid, k3_smem_bytes(lwb), s, can_pull);
+                nullptr, k3_grid, k3_smem_bytes(lwb), s, can_pull, 0, 0, 0, pdm);
   if (e != cudaSuccess) return cuda_fail(e, "bucket merge launch");
   prof_mark(h, SPMSPV_STAGE_MERGE, s);
   if (can_pull) {
@@ -485,6 +493,18 @@ static int create_impl(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz, c
       rc = cuda_fail(e, "state init");
       break;
     }
+    // dense accumulator of the direct (+,*) form, every row -0.0
+    if (m <= DIRECT_M_MAX) {
+      if ((e = cudaMalloc(&h->ws.ydense, sizeof(float) * (size_t)m)) != cudaSuccess) {
+        rc = fail(SPMSPV_ERR_OOM, "dense accumulator: %s", cudaGetErrorString(e));
+        break;
+      }
+      if ((e = launch_fill_u32(reinterpret_cast<uint32_t*>(h->ws.ydense), m, 0x80000000u, 0)) != cudaSuccess ||
+          (e = cudaDeviceSynchronize()) != cudaSuccess) {
+        rc = cuda_fail(e, "dense accumulator fill");
+        break;
+      }
+    }
     h->k2_smem = k2_smem_bytes(h->nb_fine, h->ws.nhot > 0);
     h->k3_smem_max = k3_smem_bytes(lwb_hi);
     // the attribute is per kernel, not per handle: always allow the largest
@@ -506,6 +526,7 @@ static int create_impl(spmspv_handle** out, int32_t m, int32_t n, int64_t nnz, c
   if (rc != SPMSPV_OK) {
     release_extras(h);
     cudaFree(h->rowidx_k2);
+    cudaFree(h->ws.ydense);
     cudaFree(h->ws_base);
     cudaFree(h->dcsc_aux);
     h->magic = 0;
@@ -568,6 +589,7 @@ int spmspv_destroy(spmspv_handle* h) {
   release_extras(h);
   cudaFree(h->rowidx_k2);
   cudaFree(h->sel_w);
+  cudaFree(h->ws.ydense);
   cudaFree(h->ws_base);
   cudaFree(h->dcsc_aux);
   h->magic = 0;
@@ -606,6 +628,7 @@ int spmspv_run(spmspv_handle* h, int semiring, const int32_t* x_idx, const void*
     x_val = x_val ? (const void*)h->sx_val : nullptr;
   }
   const int mask_comp = (opts & SPMSPV_MASK_COMPLEMENT) ? 1 : 0;
+  h->plus_direct = (opts & SPMSPV_BUCKETS_ONLY) ? 0 : 1;
   if (opts & SPMSPV_SCHED_AUTO) {
     if (!h->sel_ready) return fail(SPMSPV_ERR_STATE, "no selector weights loaded or trained");
     return run_auto(h, semiring, x_idx, (const uint32_t*)x_val, nnz_x, mask, mask_comp, y_idx,

@@ -246,6 +246,8 @@ static int ensure_batch(spmspv_handle* h, int lanes, BatchState** out) {
                                          vt, fl);
     if (rc != SPMSPV_OK) return rc;
     sub->ws.job = bs->jobs + l;
+    cudaFree(sub->ws.ydense);  // the lanes never run the direct (+,*) form
+    sub->ws.ydense = nullptr;
     bs->sub[l] = sub;
     bs->lanes = l + 1;
   }

@@ -32,6 +32,7 @@ struct spmspv_handle {
   int default_sched;
   cudaStream_t last_stream;
   int last_empty;
+  int plus_direct;      // the current (+,*) call may run the direct form (ws.ydense, per call)
   const uint32_t* k1_mask;  // mask whose bits the work scan counts (features), or NULL
   void* prof;           // std::vector<ProfileCall>* while profiling, else NULL
   int32_t* rowidx_k2;   // owned row-id copy with hub rows relabelled (NULL without hubs)

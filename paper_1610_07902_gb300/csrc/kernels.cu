@@ -27,6 +27,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "device_util.cuh"
 #include "expand_dev.cuh"
 #include "selector_dev.cuh"
@@ -420,17 +422,111 @@ __device__ void k2_bfs_direct(const int32_t* __restrict__ rowidx, Workspace ws, 
   }
 }
 
+// A (+,*) call in the direct form (many products): every product is added
+// into the dense accumulator ws.ydense in global memory with a reduction
+// (no result read back), after the mask.  Hub rows (ids >= m in the
+// relabelled row-id array) are summed per CTA in shared memory first and
+// added once, when the CTA has no tile left, so the most contended rows see
+// one global add per CTA.  Rows keep -0.0 until touched (K2 stores +0.0 for
+// a -0.0 product and -0.0 + p == p), so K3 finds them without a bitmap.
+template <int IT, bool MASKED>
+__device__ void k2_plus_direct(const int32_t* __restrict__ rowidx, const float* __restrict__ val, Workspace ws,
+                               int32_t m, int64_t nnz, const uint32_t* mask, int mask_comp,
+                               unsigned char* smem_raw) {
+  const DevState* st = ws.st;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int32_t W = st->W, fc = st->fc, q = st->q;
+  const int items = IT ? IT : q / K2_THREADS;
+  const int ntiles = (int)(((int64_t)W + q - 1) / q);
+  const int nhot = ws.nhot;
+  float* yd = ws.ydense;
+  if ((int)blockIdx.x >= ntiles) return;  // no tile for this CTA (tiles go round-robin)
+  unsigned char* p = smem_raw;
+  int32_t* kbase = (int32_t*)p; p += sizeof(int32_t) * (QMAX + 1);
+  uint32_t* kx = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX + 1);
+  uint32_t* hbits = (uint32_t*)p; p += sizeof(uint32_t) * (QMAX / 32);
+  uint32_t* hacc = (uint32_t*)p;              // hub sums of this CTA
+  int32_t* hrow = (int32_t*)(hacc + HOT_MAX);  // hub row ids
+  uint32_t* htb = (uint32_t*)(hrow + HOT_MAX); // hub touched bits
+  if (nhot > 0) {
+    for (int i = tid; i < HOT_MAX; i += K2_THREADS) {
+      hacc[i] = 0u;
+      hrow[i] = i < nhot ? ws.hot_rows[i] : 0;
+    }
+    for (int i = tid; i < HOT_MAX / 32; i += K2_THREADS) htb[i] = 0u;
+  }
+  for (int i = tid; i < QMAX / 32; i += K2_THREADS) hbits[i] = 0u;
+  __syncthreads();
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int32_t p0 = t * q;
+    const int32_t np = min(q, W - p0);
+    const int32_t k0 = ws.tile_k0[p0 / QF];
+    const int32_t kend = (p0 + np == W) ? fc : ws.tile_k0[(p0 + np) / QF] + 1;
+    const int32_t nk = max(1, min(kend - k0, QMAX + 1));
+    for (int l = tid; l < nk; l += K2_THREADS) {
+      const int32_t w = ws.cw[k0 + l];
+      kbase[l] = ws.cb[k0 + l] - w;
+      kx[l] = ws.cx[k0 + l];
+      const int32_t off = w - p0;
+      if (l > 0 && off > 0 && off < np) atomicOr(&hbits[off >> 5], 1u << (off & 31));
+    }
+    __syncthreads();
+    uint32_t rrow[K2_IMAX], rval[K2_IMAX];
+    if (np == items * K2_THREADS)
+      k2_gather<kPlusTimes, IT, true>(rowidx, val, hbits, kbase, kx, items, warp, lane, p0, np, nnz, rrow, rval);
+    else
+      k2_gather<kPlusTimes, IT, false>(rowidx, val, hbits, kbase, kx, items, warp, lane, p0, np, nnz, rrow, rval);
+#pragma unroll
+    for (int i = 0; i < K2_IMAX; ++i) {
+      const uint32_t row = rrow[i];
+      if (row == 0xffffffffu) continue;
+      uint32_t r = row;
+      int hs = -1;
+      if (row >= (uint32_t)m) {
+        if (row - (uint32_t)m >= (uint32_t)nhot) {
+          atomicOr(&ws.st->status, ST_INDEX);  // a row id outside [0, m): dropped, flagged
+          continue;
+        }
+        hs = (int)(row - (uint32_t)m);
+        r = (uint32_t)hrow[hs];
+      }
+      if (MASKED && mask) {
+        const uint32_t bit = (__ldg(mask + (r >> 5)) >> (r & 31)) & 1u;
+        if (mask_comp ? bit != 0u : bit == 0u) continue;
+      }
+      if (hs >= 0) {
+        spa_apply<kPlusTimes>(hacc, (uint32_t)hs, rval[i]);
+        const uint32_t hb = 1u << (hs & 31);
+        if (!(htb[hs >> 5] & hb)) atomicOr(&htb[hs >> 5], hb);
+      } else {
+        atomicAdd(yd + r, __uint_as_float(rval[i]));
+      }
+    }
+    __syncthreads();  // the entries of the next tile overwrite this one's
+    for (int j = tid; j < QMAX / 32; j += K2_THREADS) hbits[j] = 0u;
+    __syncthreads();
+  }
+  if (nhot > 0) {
+    for (int hs = tid; hs < nhot; hs += K2_THREADS)
+      if ((htb[hs >> 5] >> (hs & 31)) & 1u) atomicAdd(yd + hrow[hs], __uint_as_float(hacc[hs]));
+  }
+}
+
 template <int SEM, int IT, bool MASKED>
 __global__ void __launch_bounds__(K2_THREADS, K2_MIN_BLOCKS)
 k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ val, Workspace ws,
                   int lwb_lo, int nb_fine, int32_t m, int64_t nnz, const uint32_t* mask,
-                  int mask_comp, int only_push, int32_t direct_max) {
+                  int mask_comp, int only_push, int32_t direct_max, int32_t plus_direct_min) {
   if (only_push && ws.st->dir != 0) return;  // this call runs the pull direction
   if (ws.job) mask = ws.job->mask;
   extern __shared__ __align__(16) unsigned char k2_smem_raw[];
   if (SEM == kMinSelect2nd && MASKED && direct_max > 0 && ws.st->W <= direct_max) {
     if (!ws.job || ws.job->b >= 0)
       k2_bfs_direct<IT>(rowidx, ws, m, nnz, const_cast<uint32_t*>(mask), k2_smem_raw);
+    return;
+  }
+  if (SEM == kPlusTimes && plus_direct_min > 0 && ws.st->W >= plus_direct_min) {
+    k2_plus_direct<IT, MASKED>(rowidx, val, ws, m, nnz, mask, mask_comp, k2_smem_raw);
     return;
   }
   __shared__ int32_t s_kept, s_kept_n;
@@ -623,11 +719,12 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
 template <int SEM>
 static void k2_variant(int it, bool masked, int grid, size_t smem, cudaStream_t s, const int32_t* rows,
                        const float* val, const Workspace& ws, int lwb_lo, int nb_fine, const Matrix& A,
-                       const uint32_t* mask, int mask_comp, int only_push, int32_t direct_max) {
+                       const uint32_t* mask, int mask_comp, int only_push, int32_t direct_max,
+                       int32_t plus_direct_min) {
 #define K2_GO(I, M)                                                                              \
   k2_expand_scatter<SEM, I, M><<<grid, K2_THREADS, smem, s>>>(rows, val, ws, lwb_lo, nb_fine, A.m, \
                                                               A.nnz, mask, mask_comp, only_push,  \
-                                                              direct_max)
+                                                              direct_max, plus_direct_min)
   constexpr int I1 = K2_IMAX, I2 = K2_IMAX / 2;
   if (masked) {
     if (it == I1) K2_GO(I1, true); else if (it == I2) K2_GO(I2, true); else K2_GO(0, true);
@@ -639,7 +736,8 @@ static void k2_variant(int it, bool masked, int grid, size_t smem, cudaStream_t 
 
 cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo, int nb_fine,
                       const uint32_t* mask, int mask_comp, int grid, size_t smem, cudaStream_t s,
-                      int only_push, int q_hint, int32_t direct_max) {
+                      int only_push, int q_hint, int32_t direct_max, int32_t plus_direct_min) {
+  if (!ws.ydense) plus_direct_min = 0;
   const int32_t* rows = ws.nhot > 0 ? ws.rowidx_k2 : A.rowidx;
   // the batched lanes take their masks from the job: compile the mask path in
   const bool masked = mask != nullptr || ws.job != nullptr;
@@ -647,15 +745,15 @@ cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo,
   switch (sem) {
     case kPlusTimes:
       k2_variant<kPlusTimes>(it, masked, grid, smem, s, rows, A.val, ws, lwb_lo, nb_fine, A, mask,
-                             mask_comp, only_push, 0);
+                             mask_comp, only_push, 0, plus_direct_min);
       break;
     case kMinSelect2nd:
       k2_variant<kMinSelect2nd>(it, masked, grid, smem, s, rows, nullptr, ws, lwb_lo, nb_fine, A, mask,
-                                mask_comp, only_push, masked ? direct_max : 0);
+                                mask_comp, only_push, masked ? direct_max : 0, 0);
       break;
     default:
       k2_variant<kOrAnd>(it, masked, grid, smem, s, rows, nullptr, ws, lwb_lo, nb_fine, A, mask,
-                         mask_comp, only_push, 0);
+                         mask_comp, only_push, 0, 0);
   }
   return cudaGetLastError();
 }
@@ -711,11 +809,89 @@ __device__ void k3_bfs_direct_close(Workspace ws, int32_t m, const int32_t* y_id
   }
 }
 
+// The end of a (+,*) call in the direct form: the touched rows of the dense
+// accumulator (those not holding -0.0), in ascending order, to y, each reset
+// to -0.0 as it is read.  CTAs take row tiles of K3D_ROWS rows in ticket
+// order; a warp ballots 32 consecutive rows per step (coalesced reads), a
+// block scan and a look-back over the tiles give each tile's offset in y.
+constexpr int K3D_ROWS = K3_THREADS * 32;  // rows per tile (32 ballot steps of each warp)
+
+__device__ void k3_plus_direct(Workspace ws, int32_t m, int32_t* y_idx, uint32_t* y_val, int32_t y_cap,
+                               int32_t* d_nnz_y) {
+  DevState* st = ws.st;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ uint32_t sbits[K3_WARPS * 32];  // the ballots of a tile, 32 per warp
+  __shared__ int32_t s_scan[K3_THREADS / 32 + 1];
+  __shared__ uint32_t s_tk;
+  __shared__ unsigned long long s_off;
+  uint32_t* yd = reinterpret_cast<uint32_t*>(ws.ydense);
+  constexpr uint32_t kEmpty = 0x80000000u;  // -0.0f
+  if (blockIdx.x == 0) {
+    if (tid == 0) {
+      st->k1_ticket = 0u;
+      st->last_maxdeg = st->maxdeg;
+      st->last_maskcnt = st->maskcnt;
+      st->maxdeg = 0;
+      st->maskcnt = 0;
+    }
+    const int nt1 = (st->f + K1_TILE - 1) / K1_TILE;
+    for (int i = tid; i < nt1; i += K3_THREADS) ws.k1_status[i] = 0ull;
+  }
+  const uint32_t ntiles = (uint32_t)(((int64_t)m + K3D_ROWS - 1) / K3D_ROWS);
+  const int rpw = K3D_ROWS / K3_WARPS;  // rows of each warp in a tile
+  for (;;) {
+    if (tid == 0) s_tk = atomicAdd(&st->k3_ticket, 1u);
+    __syncthreads();
+    const uint32_t t = s_tk;
+    if (t >= ntiles) break;
+    const int64_t r0 = (int64_t)t * K3D_ROWS + (int64_t)warp * rpw;
+    int32_t cw = 0;
+    for (int k = 0; k < rpw / 32; ++k) {
+      const int64_t r = r0 + k * 32 + lane;
+      const bool hit = r < m && __ldcg(yd + r) != kEmpty;
+      const uint32_t bits = __ballot_sync(0xffffffffu, hit);
+      if (lane == 0) sbits[warp * 32 + k] = bits;
+      cw += __popc(bits);
+    }
+    int32_t tot;
+    const int32_t run = block_exclusive_sum<K3_THREADS>(lane == 0 ? cw : 0, s_scan, &tot);
+    if (tid < 32) {
+      const unsigned long long pre = warp_lookback(ws.k3_status, t, (unsigned long long)tot, st);
+      if (tid == 0) s_off = pre;
+    }
+    __syncthreads();
+    int64_t pos = (int64_t)s_off + __shfl_sync(0xffffffffu, run, 0);
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int k = 0; k < rpw / 32; ++k) {
+      const uint32_t bits = sbits[warp * 32 + k];
+      if ((bits >> lane) & 1u) {
+        const int64_t r = r0 + k * 32 + lane;
+        const int64_t pp = pos + __popc(bits & lt);
+        const uint32_t v = __ldcg(yd + r);
+        if (pp < y_cap) {
+          y_idx[pp] = (int32_t)r;
+          if (y_val) y_val[pp] = v;
+        }
+        yd[r] = kEmpty;
+      }
+      pos += __popc(bits);
+    }
+    if (t == ntiles - 1 && tid == 0) {
+      const int64_t total = (int64_t)s_off + tot;
+      st->nnz_y = (int32_t)total;
+      if (d_nnz_y) *d_nnz_y = (int32_t)total;
+      if (total > y_cap) atomicOr(&st->status, ST_CAPACITY);
+    }
+    __syncthreads();
+  }
+}
+
 template <int SEM, bool BFS>
 __global__ void __launch_bounds__(K3_THREADS, 2)
 k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx, uint32_t* y_val,
                 int32_t y_cap, int32_t* d_nnz_y, uint32_t* mask_update, int only_push,
-                int32_t direct_max, int use_cond, cudaGraphConditionalHandle cond) {
+                int32_t direct_max, int use_cond, cudaGraphConditionalHandle cond,
+                int32_t plus_direct_min) {
   if (only_push && ws.st->dir != 0) return;  // this call runs the pull direction
   if (ws.job) {  // a batched lane: this frontier's outputs
     y_idx = ws.job->y_idx;
@@ -728,8 +904,12 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
     k3_bfs_direct_close(ws, m, y_idx, d_nnz_y, use_cond, cond);
     return;
   }
-  constexpr bool kDenseForm = SEM == kPlusTimes || (SEM == kMinSelect2nd && BFS);
   extern __shared__ __align__(16) uint32_t k3_smem[];
+  if (SEM == kPlusTimes && !BFS && plus_direct_min > 0 && ws.st->W >= plus_direct_min) {
+    k3_plus_direct(ws, m, y_idx, y_val, y_cap, d_nnz_y);
+    return;
+  }
+  constexpr bool kDenseForm = SEM == kPlusTimes || (SEM == kMinSelect2nd && BFS);
   __shared__ int32_t s_scan[K3_THREADS / 32 + 1];
   __shared__ uint32_t s_tk[2];  // this bucket's ticket and the next one's
   __shared__ unsigned long long s_off;
@@ -965,9 +1145,11 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
 cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, int lwb_lo,
                       int nb_fine, int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y,
                       uint32_t* mask_update, int grid, size_t smem, cudaStream_t s, int only_push,
-                      int32_t direct_max, int use_cond, cudaGraphConditionalHandle cond) {
+                      int32_t direct_max, int use_cond, cudaGraphConditionalHandle cond,
+                      int32_t plus_direct_min) {
+  if (!ws.ydense || bfs || sem != kPlusTimes) plus_direct_min = 0;
 #define K3_ARGS ws, lwb_lo, nb_fine, A.m, y_idx, y_val, y_cap, d_nnz_y, mask_update, only_push, \
-                bfs ? direct_max : 0, bfs ? use_cond : 0, cond
+                bfs ? direct_max : 0, bfs ? use_cond : 0, cond, plus_direct_min
   if (bfs) {
     k3_bucket_merge<kMinSelect2nd, true><<<grid, K3_THREADS, smem, s>>>(K3_ARGS);
   } else if (sem == kPlusTimes) {
@@ -978,6 +1160,18 @@ cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, i
     k3_bucket_merge<kOrAnd, false><<<grid, K3_THREADS, smem, s>>>(K3_ARGS);
   }
 #undef K3_ARGS
+  return cudaGetLastError();
+}
+
+__global__ void k_fill_u32(uint32_t* __restrict__ p, int64_t n, uint32_t value) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = value;
+}
+
+cudaError_t launch_fill_u32(uint32_t* p, int64_t n, uint32_t value, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  k_fill_u32<<<grid, 256, 0, s>>>(p, n, value);
   return cudaGetLastError();
 }
 

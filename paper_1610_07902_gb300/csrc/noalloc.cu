@@ -199,6 +199,7 @@ extern "C" int spmspv_run_noalloc(int32_t m, int32_t n, int64_t nnz, const int32
   ws.hot_start = nullptr;
   ws.hot_val = nullptr;
   ws.hot_touch = nullptr;
+  ws.ydense = nullptr;  // no dense accumulator: every product runs the bucketed form
 
   e = cudaMemsetAsync(base, 0, NA_ZERO_BYTES, s);
   if (e != cudaSuccess) return cuda_fail(e, "clear no-alloc scratch");

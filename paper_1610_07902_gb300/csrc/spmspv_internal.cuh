@@ -40,6 +40,13 @@ constexpr int NB_K2_MAX = 8192;   // buckets a K2 tile histograms in shared memo
 // with global atomics (the dense output arrays are the SPA) and K3 only
 // closes the level; above it the bucketed form runs.
 constexpr int32_t BFS_DIRECT_MAX = 1 << 21;
+// A (+,*) product with at least m / PLUS_DIRECT_DIV products (W) runs in the
+// direct form when the handle has a dense y accumulator (m <= DIRECT_M_MAX):
+// K2 adds every product into the accumulator in global memory (L2-resident
+// at these sizes) and K3 reads the touched rows back in order, resetting
+// them; below that W the bucketed form runs.
+constexpr int PLUS_DIRECT_DIV = 2;
+constexpr int32_t DIRECT_M_MAX = 1 << 24;
 constexpr int BFILL_STRIDE = 32;  // bucket fill counters sit 128 bytes apart (own L2 line)
 
 // ---- hub ("hot") rows: the largest-degree rows, combined per K2 tile ----
@@ -165,6 +172,8 @@ struct Workspace {
   const Job* job;            // batched lanes: the current frontier (NULL otherwise)
   uint32_t* hot_val;         // [HOT_MAX] per-call sums of the hot rows
   uint32_t* hot_touch;       // [HOT_MAX] 1 when a hot row received a product this call
+  float* ydense;             // [m] dense (+,*) accumulator of the direct form, -0.0 in every
+                             // row between calls (NULL when m > DIRECT_M_MAX)
 };
 
 // ---- pull direction (matrix-driven masked SpMV) ----
@@ -248,14 +257,19 @@ cudaError_t launch_relabel_hubs(const Matrix& A, const int32_t* hub_of_row, int3
 // that are not BFS levels.  K2 and K3 of one level get the same value.
 // use_cond/cond (BFS levels in a graph loop): K3 sets the loop's condition
 // when it closes the level (another level while this one found vertices).
+// plus_direct_min: a (+,*) call with at least this many products runs in the
+// direct form (0: never); K2 and K3 of one call get the same value.
 cudaError_t launch_k2(int sem, const Matrix& A, const Workspace& ws, int lwb_lo, int nb_fine,
                       const uint32_t* mask, int mask_comp, int grid, size_t smem, cudaStream_t s,
-                      int only_push = 0, int q_hint = 0, int32_t direct_max = 0);
+                      int only_push = 0, int q_hint = 0, int32_t direct_max = 0,
+                      int32_t plus_direct_min = 0);
 cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, int lwb_lo,
                       int nb_fine, int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y,
                       uint32_t* mask_update, int grid, size_t smem, cudaStream_t s,
                       int only_push = 0, int32_t direct_max = 0, int use_cond = 0,
-                      cudaGraphConditionalHandle cond = 0);
+                      cudaGraphConditionalHandle cond = 0, int32_t plus_direct_min = 0);
+// Sets n 32-bit words to `value`.
+cudaError_t launch_fill_u32(uint32_t* p, int64_t n, uint32_t value, cudaStream_t s);
 cudaError_t launch_bucket_sizes(const Matrix& A, int lwb_lo, int nb_fine, int32_t* counts,
                                 unsigned int* bad, cudaStream_t s);
 // K2 shared memory: cb - cw and x value of the tile's x entries (whose bytes

@@ -59,6 +59,7 @@ SPMSPV_DEV_INDEX = 4
 SPMSPV_DEV_BOUND = 8
 SPMSPV_SORT_X = 32
 SPMSPV_SCHED_RULE = 64
+SPMSPV_BUCKETS_ONLY = 128  # spmspv_run, (+,*): never the direct form
 SPMSPV_LANES_PERSISTENT = -1  # spmspv_run_batched: the persistent one-launch form
 
 

@@ -58,6 +58,10 @@ def _check(lib, A, Ad, semiring, x_idx, xf, mask_u8=None, complement=True, sched
     worst = compare(semiring, ref, yi, yv)
     _, S = lib
     assert S.spmspv_last_work(Ad.handle) == ref.nmult
+    if semiring == 0 and not (extra_opts & S.SPMSPV_BUCKETS_ONLY):
+        # (+,*) calls with many products run the direct form: the bucketed one too
+        worst = max(worst, _check(lib, A, Ad, semiring, x_idx, xf, mask_u8, complement, sched,
+                                  extra_opts | S.SPMSPV_BUCKETS_ONLY))
     return worst
 
 
