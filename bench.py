@@ -558,6 +558,71 @@ def bench_dcsc(S, dev, stream, flush):
     return out
 
 
+def product_form(m, W, buckets_only):
+    """Which form the library runs a (+,*) call in (the device's rule): the
+    direct form from 2m products on (m <= 2^24), else the bucketed one."""
+    return "direct" if not buckets_only and m <= (1 << 24) and W >= 2 * m else "bucketed"
+
+
+def stage_roofline(S, form, F_, W, ny, stage_avg):
+    """Stage names, the dominant stage's kernel, its captured traffic and its
+    algorithmic HBM bytes: 16 B per x entry (scan), 8 B per product (row id and
+    value read by the expand step; in the direct form its adds stay in L2),
+    8 B per y entry (merge / compaction)."""
+    if form == "direct":
+        names = {S.SPMSPV_STAGE_SCAN: "work_scan", S.SPMSPV_STAGE_SCATTER: "expand_reduce",
+                 S.SPMSPV_STAGE_MERGE: "compact"}
+        knames = {S.SPMSPV_STAGE_SCAN: "k1_work_scan", S.SPMSPV_STAGE_SCATTER: "k2_expand_scatter[direct]",
+                  S.SPMSPV_STAGE_MERGE: "k3_bucket_merge[direct]"}
+    else:
+        names = {S.SPMSPV_STAGE_SCAN: "work_scan", S.SPMSPV_STAGE_SCATTER: "expand_scatter",
+                 S.SPMSPV_STAGE_MERGE: "bucket_merge"}
+        knames = {S.SPMSPV_STAGE_SCAN: "k1_work_scan", S.SPMSPV_STAGE_SCATTER: "k2_expand_scatter",
+                  S.SPMSPV_STAGE_MERGE: "k3_bucket_merge"}
+    alg = {S.SPMSPV_STAGE_SCAN: 16 * F_, S.SPMSPV_STAGE_SCATTER: 8 * W, S.SPMSPV_STAGE_MERGE: 8 * ny}
+    units = {S.SPMSPV_STAGE_SCAN: F_, S.SPMSPV_STAGE_SCATTER: W, S.SPMSPV_STAGE_MERGE: W}
+    dom = max(names, key=lambda s: stage_avg[s])
+    achieved = alg[dom] / (stage_avg[dom] * 1e-3) / 1e9
+    per_unit, traffic_src = captured_traffic(knames[dom])
+    return names, knames[dom], per_unit, traffic_src, units, alg, dom, achieved
+
+
+def bench_bucketed_form(S, Ad, xi, xv, F_, y_idx, y_val, cap, nnz_y, stream, flush, peak, steps=100):
+    """The headline product in the bucketed form (SPMSPV_BUCKETS_ONLY): the
+    paper's row-range buckets and shared-memory SPA at every size."""
+    import torch
+    opts = S.SPMSPV_SORTED_OUT | S.SPMSPV_BUCKETS_ONLY
+
+    def step():
+        S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, xi, xv, F_, None, opts, y_idx, y_val, cap, nnz_y,
+                     stream)
+    for _ in range(5):
+        flush.zero_()
+        step()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    W = S.spmspv_last_work(Ad.handle)
+    ny = int(nnz_y.item())
+    S.spmspv_profile_begin(Ad.handle)
+    for _ in range(50):
+        flush.zero_()
+        step()
+    stage_ms, ncalls = S.spmspv_profile_end(Ad.handle)
+    stage_avg = [v / ncalls for v in stage_ms]
+    names, kname, per_unit, src, units, alg, dom, achieved = stage_roofline(S, "bucketed", F_, W, ny, stage_avg)
+    return {"ms_per_step": ms, "gteps": W / (ms * 1e-3) / 1e9,
+            "stages_ms": {names[s]: stage_avg[s] for s in names},
+            "roofline": {"kernel": kname, "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                         "traffic": per_unit * units[dom] if per_unit else None},
+            "path_frac": compulsory_bytes(F_, W, ny) / (ms * 1e-3) / 1e9 / peak}
+
+
 def bench_batched(S, dev, stream, B=256):
     """256 frontiers on R-MAT s20 in one batched launch (autotuned) against
     256 sequential plain calls; multi-source BFS and ACL the same way."""
@@ -584,9 +649,17 @@ def bench_batched(S, dev, stream, B=256):
     def batched():
         S.spmspv_run_batched(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, B, d_off, d_cnt, xi_all, xv_all, None,
                              0, 0, d_yoff, d_ycap, yi, yv, nz, 0, stream)
-    batched()  # tunes on first use
+    batched()  # tunes on first use (the persistent form under every push schedule)
     t_b = _events_ms(batched, stream, 3)
     tuned = S.spmspv_last_tuned(Ad.handle)
+    phases, waves = S.spmspv_batched_phase_times(Ad.handle)
+
+    def lanes16():
+        S.spmspv_run_batched(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, B, d_off, d_cnt, xi_all, xv_all, None,
+                             0, S.SPMSPV_SCHED_OPT(tuned[1]), d_yoff, d_ycap, yi, yv, nz, 16, stream)
+    lanes16()
+    t_l = _events_ms(lanes16, stream, 3)
+    batched()
     nz_b = nz.cpu().numpy().copy()
     yi_b = yi.cpu().numpy()
     yv_b = yv.cpu().numpy()
@@ -614,8 +687,11 @@ def bench_batched(S, dev, stream, B=256):
            "products": W,
            "spmspv": {"batched_ms": t_b, "sequential_ms": t_s, "speedup": t_s / t_b,
                       "batched_gteps": W / (t_b * 1e-3) / 1e9, "tuned_lanes": tuned[0],
-                      "tuned_schedule": tuned[1], "identical_index_sets": same_idx,
-                      "max_rel_value_diff": rel}}
+                      "tuned_schedule": tuned[1], "form": "persistent" if tuned[0] == 0 else "lanes",
+                      "phases_ms": dict(zip(["scan", "plan", "tile_starts", "expand", "merge", "launch"],
+                                            [round(float(v), 4) for v in phases])),
+                      "waves": waves, "lanes16_ms": t_l, "lanes16_gteps": W / (t_l * 1e-3) / 1e9,
+                      "identical_index_sets": same_idx, "max_rel_value_diff": rel}}
     del yi, yv
     Ad.close()
 
@@ -877,6 +953,8 @@ def main():
     ap.add_argument("--scale", type=int, default=SCALE,
                     help="R-MAT scale (smaller only for profiler captures)")
     ap.add_argument("--nnz-x", type=int, default=F)
+    ap.add_argument("--buckets-only", action="store_true",
+                    help="run the headline product in the bucketed form even where the direct form applies")
     ap.add_argument("--kernels-only", action="store_true",
                     help="warm-up and timed steps only (for profiler captures)")
     ap.add_argument("--no-extras", action="store_true",
@@ -923,7 +1001,7 @@ def main():
     nnz_y = torch.zeros(1, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    opts = S.SPMSPV_SORTED_OUT
+    opts = S.SPMSPV_SORTED_OUT | (S.SPMSPV_BUCKETS_ONLY if args.buckets_only else 0)
 
     def step():
         S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, xi, xv, F_, None, opts, y_idx, y_val, cap,
@@ -1005,16 +1083,9 @@ def main():
     clocks = sampler.stop()
 
     peak, peak_kind = load_peaks()
-    names = {S.SPMSPV_STAGE_SCAN: "work_scan", S.SPMSPV_STAGE_SCATTER: "expand_scatter",
-             S.SPMSPV_STAGE_MERGE: "bucket_merge"}
-    alg = {S.SPMSPV_STAGE_SCAN: 16 * F_, S.SPMSPV_STAGE_SCATTER: 8 * W,
-           S.SPMSPV_STAGE_MERGE: 8 * ny}
-    dom = max(names, key=lambda s: stage_avg[s])
-    achieved = alg[dom] / (stage_avg[dom] * 1e-3) / 1e9
-    units = {S.SPMSPV_STAGE_SCAN: F_, S.SPMSPV_STAGE_SCATTER: W, S.SPMSPV_STAGE_MERGE: W}
-    kname = {S.SPMSPV_STAGE_SCAN: "k1_work_scan", S.SPMSPV_STAGE_SCATTER: "k2_expand_scatter",
-             S.SPMSPV_STAGE_MERGE: "k3_bucket_merge"}[dom]
-    per_unit, traffic_src = captured_traffic(kname)
+    form = product_form(A.m, W, args.buckets_only)
+    names, kname, per_unit, traffic_src, units, alg, dom, achieved = stage_roofline(S, form, F_, W, ny,
+                                                                                    stage_avg)
     path_bytes = compulsory_bytes(F_, W, ny)
     path_gbs = path_bytes / (ms_per_step * 1e-3) / 1e9
 
@@ -1030,6 +1101,9 @@ def main():
     extras = {}
     if rank == 0 and not args.no_extras:
         import synth
+        if form == "direct":
+            extras["bucketed_form"] = bench_bucketed_form(S, Ad, xi, xv, F_, y_idx, y_val, cap, nnz_y, stream,
+                                                          flush, peak)
         # the same graph at the smaller frontiers of the sweep (host-launched calls)
         sweep = {}
         for fs in (100, 10_000):
@@ -1075,10 +1149,10 @@ def main():
         "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload, "graph": "rmat s%d ef16 symmetrised seed 1" % args.scale,
-                   "m": A.m, "nnz": A.nnz, "nnz_x": F_, "products": W, "nnz_y": ny,
+                   "m": A.m, "nnz": A.nnz, "nnz_x": F_, "products": W, "nnz_y": ny, "form": form,
                    "semiring": "plus_times_f32", "l2": "flushed (256 MiB write) before each step",
                    "parallelism": "replicas" if world > 1 else "single_gpu"},
-        "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": kname, "stage": names[dom], "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "traffic": per_unit * units[dom] if per_unit else None,
                      "traffic_unit": "bytes per launch",

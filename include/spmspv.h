@@ -188,7 +188,7 @@ int spmspv_destroy(spmspv_handle* h);
  * Output order: y_idx is always produced in ascending order (each
  * row-range bucket is emitted in row order and buckets are concatenated in
  * order, Step 3 of Algorithm 1), so SPMSPV_SORTED_OUT costs nothing extra.
- * Direct form: a (+,*) push product with at least m/2 products (decided on
+ * Direct form: a (+,*) push product with at least 2m products (decided on
  * the device from the work scan) adds every product into a dense accumulator
  * of m floats that the handle keeps in device memory (4m bytes, allocated at
  * create when m <= 2^24; at these sizes it stays in L2), then reads the

@@ -103,7 +103,14 @@ int check_handle(const spmspv_handle* h) {
 // Products from which a (+,*) call runs the direct form (0: never).
 static int32_t plus_direct_min(const spmspv_handle* h) {
   if (!h->plus_direct || !h->ws.ydense) return 0;
-  return std::max<int32_t>(1, h->A.m / PLUS_DIRECT_DIV);
+  return (int32_t)std::min<int64_t>(INT32_MAX, (int64_t)h->A.m * PLUS_DIRECT_PER_ROW);
+}
+
+// K3 CTAs for the direct form's compaction: one per 8192-row tile, at most
+// two per SM.
+static int direct_k3_grid(const spmspv_handle* h) {
+  const int64_t tiles = ((int64_t)h->A.m + 8191) / 8192;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 2 * h->sm_count));
 }
 
 // The push-direction product: K1 -> K2 -> K3 on `s`.
@@ -132,7 +139,8 @@ int run_push(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_
   prof_mark(h, SPMSPV_STAGE_SCATTER, s);
   const size_t k3_smem = k3_smem_bytes(sc.lwb);
   const int nb = (int)(((int64_t)h->A.m + (1 << sc.lwb) - 1) >> sc.lwb);
-  const int k3_grid = std::max(1, std::min(nb, h->sm_count * h->k3_bps[sc.lwb - h->lwb_lo]));
+  int k3_grid = std::max(1, std::min(nb, h->sm_count * h->k3_bps[sc.lwb - h->lwb_lo]));
+  if (pdm > 0) k3_grid = std::max(k3_grid, direct_k3_grid(h));
   e = launch_k3(sem, bfs, h->A, h->ws, h->lwb_lo, h->nb_fine, y_idx, y_val, y_cap, d_nnz_y,
                 mask_update, k3_grid, k3_smem, s, 0, 0, 0, 0, pdm);
   if (e != cudaSuccess) return cuda_fail(e, "bucket merge launch");
@@ -241,7 +249,8 @@ int run_auto(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_
   prof_mark(h, SPMSPV_STAGE_SCATTER, s);
   const int lwb = h->lwb_lo + 2;  // shared memory for the widest bucket
   const int nb_max = (int)(((int64_t)h->A.m + (1 << h->lwb_lo) - 1) >> h->lwb_lo);
-  const int k3_grid = std::max(1, std::min(nb_max, h->sm_count * h->k3_bps[2]));
+  int k3_grid = std::max(1, std::min(nb_max, h->sm_count * h->k3_bps[2]));
+  if (pdm > 0) k3_grid = std::max(k3_grid, direct_k3_grid(h));
   e = launch_k3(sem, false, h->A, h->ws, h->lwb_lo, h->nb_fine, y_idx, y_val, y_cap, d_nnz_y,
                 nullptr, k3_grid, k3_smem_bytes(lwb), s, can_pull, 0, 0, 0, pdm);
   if (e != cudaSuccess) return cuda_fail(e, "bucket merge launch");

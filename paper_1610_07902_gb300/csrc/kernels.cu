@@ -812,15 +812,16 @@ __device__ void k3_bfs_direct_close(Workspace ws, int32_t m, const int32_t* y_id
 // The end of a (+,*) call in the direct form: the touched rows of the dense
 // accumulator (those not holding -0.0), in ascending order, to y, each reset
 // to -0.0 as it is read.  CTAs take row tiles of K3D_ROWS rows in ticket
-// order; a warp ballots 32 consecutive rows per step (coalesced reads), a
-// block scan and a look-back over the tiles give each tile's offset in y.
-constexpr int K3D_ROWS = K3_THREADS * 32;  // rows per tile (32 ballot steps of each warp)
+// order; each warp reads its K3D_STEPS 32-row words of a tile at once
+// (coalesced, kept in registers), ballots them, and a block scan plus a
+// look-back over the tiles give each tile's offset in y.
+constexpr int K3D_STEPS = 16;                          // 32-row words per warp and tile
+constexpr int K3D_ROWS = K3_THREADS * K3D_STEPS;      // rows per tile (8192)
 
 __device__ void k3_plus_direct(Workspace ws, int32_t m, int32_t* y_idx, uint32_t* y_val, int32_t y_cap,
                                int32_t* d_nnz_y) {
   DevState* st = ws.st;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  __shared__ uint32_t sbits[K3_WARPS * 32];  // the ballots of a tile, 32 per warp
   __shared__ int32_t s_scan[K3_THREADS / 32 + 1];
   __shared__ uint32_t s_tk;
   __shared__ unsigned long long s_off;
@@ -838,20 +839,22 @@ __device__ void k3_plus_direct(Workspace ws, int32_t m, int32_t* y_idx, uint32_t
     for (int i = tid; i < nt1; i += K3_THREADS) ws.k1_status[i] = 0ull;
   }
   const uint32_t ntiles = (uint32_t)(((int64_t)m + K3D_ROWS - 1) / K3D_ROWS);
-  const int rpw = K3D_ROWS / K3_WARPS;  // rows of each warp in a tile
+  const uint32_t lt = (1u << lane) - 1u;
   for (;;) {
     if (tid == 0) s_tk = atomicAdd(&st->k3_ticket, 1u);
     __syncthreads();
     const uint32_t t = s_tk;
     if (t >= ntiles) break;
-    const int64_t r0 = (int64_t)t * K3D_ROWS + (int64_t)warp * rpw;
+    const int64_t r0 = (int64_t)t * K3D_ROWS + (int64_t)warp * (K3D_STEPS * 32) + lane;
+    uint32_t v[K3D_STEPS];
+#pragma unroll
+    for (int k = 0; k < K3D_STEPS; ++k) v[k] = r0 + k * 32 < m ? __ldcg(yd + r0 + k * 32) : kEmpty;
+    uint32_t bits[K3D_STEPS];
     int32_t cw = 0;
-    for (int k = 0; k < rpw / 32; ++k) {
-      const int64_t r = r0 + k * 32 + lane;
-      const bool hit = r < m && __ldcg(yd + r) != kEmpty;
-      const uint32_t bits = __ballot_sync(0xffffffffu, hit);
-      if (lane == 0) sbits[warp * 32 + k] = bits;
-      cw += __popc(bits);
+#pragma unroll
+    for (int k = 0; k < K3D_STEPS; ++k) {
+      bits[k] = __ballot_sync(0xffffffffu, v[k] != kEmpty);
+      cw += __popc(bits[k]);
     }
     int32_t tot;
     const int32_t run = block_exclusive_sum<K3_THREADS>(lane == 0 ? cw : 0, s_scan, &tot);
@@ -861,20 +864,18 @@ __device__ void k3_plus_direct(Workspace ws, int32_t m, int32_t* y_idx, uint32_t
     }
     __syncthreads();
     int64_t pos = (int64_t)s_off + __shfl_sync(0xffffffffu, run, 0);
-    const uint32_t lt = (1u << lane) - 1u;
-    for (int k = 0; k < rpw / 32; ++k) {
-      const uint32_t bits = sbits[warp * 32 + k];
-      if ((bits >> lane) & 1u) {
-        const int64_t r = r0 + k * 32 + lane;
-        const int64_t pp = pos + __popc(bits & lt);
-        const uint32_t v = __ldcg(yd + r);
+#pragma unroll
+    for (int k = 0; k < K3D_STEPS; ++k) {
+      if ((bits[k] >> lane) & 1u) {
+        const int64_t r = r0 + k * 32;
+        const int64_t pp = pos + __popc(bits[k] & lt);
         if (pp < y_cap) {
           y_idx[pp] = (int32_t)r;
-          if (y_val) y_val[pp] = v;
+          if (y_val) y_val[pp] = v[k];
         }
         yd[r] = kEmpty;
       }
-      pos += __popc(bits);
+      pos += __popc(bits[k]);
     }
     if (t == ntiles - 1 && tid == 0) {
       const int64_t total = (int64_t)s_off + tot;

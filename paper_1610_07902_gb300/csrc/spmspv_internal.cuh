@@ -40,12 +40,13 @@ constexpr int NB_K2_MAX = 8192;   // buckets a K2 tile histograms in shared memo
 // with global atomics (the dense output arrays are the SPA) and K3 only
 // closes the level; above it the bucketed form runs.
 constexpr int32_t BFS_DIRECT_MAX = 1 << 21;
-// A (+,*) product with at least m / PLUS_DIRECT_DIV products (W) runs in the
-// direct form when the handle has a dense y accumulator (m <= DIRECT_M_MAX):
+// A (+,*) product with at least PLUS_DIRECT_PER_ROW * m products (W) runs in
+// the direct form when the handle has a dense y accumulator (m <= DIRECT_M_MAX):
 // K2 adds every product into the accumulator in global memory (L2-resident
 // at these sizes) and K3 reads the touched rows back in order, resetting
-// them; below that W the bucketed form runs.
-constexpr int PLUS_DIRECT_DIV = 2;
+// them; below that W the bucketed form runs (measured crossover on R-MAT
+// s20 and s22: between 0.7 m and 2.2 m products).
+constexpr int PLUS_DIRECT_PER_ROW = 2;
 constexpr int32_t DIRECT_M_MAX = 1 << 24;
 constexpr int BFILL_STRIDE = 32;  // bucket fill counters sit 128 bytes apart (own L2 line)
 

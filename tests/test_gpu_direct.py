@@ -1,6 +1,6 @@
 """The direct (+,*) form (products added into a dense accumulator in device
 memory, touched rows read back in order and reset) against the oracle: on
-both sides of its threshold (m/2 products), with hub rows, masks, a y that is
+both sides of its threshold (2m products), with hub rows, masks, a y that is
 too small, repeated calls (the accumulator must be clean after every call),
 a DCSC handle and the learned schedule."""
 import numpy as np
@@ -41,9 +41,10 @@ def test_direct_both_sides_of_the_threshold_and_repeats(lib):
     deg = np.diff(A.colptr)
     rng = np.random.default_rng(3)
     order = rng.permutation(A.n)
-    # frontiers whose products sit just below, at and above m/2, then large ones
+    # frontiers whose products sit just below and above 2m, then others
     cum = np.cumsum(deg[order])
-    sizes = [int(np.searchsorted(cum, A.m // 2)) - 2, int(np.searchsorted(cum, A.m // 2)) + 2, 3000, 20000, 64]
+    thr = int(np.searchsorted(cum, 2 * A.m))
+    sizes = [thr - 2, thr + 2, 3000, 20000, 64]
     for f in sizes:
         xi = np.sort(order[:f]).astype(np.int32)
         xf = rng.uniform(-1, 1, f).astype(np.float32)
