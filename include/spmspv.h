@@ -252,14 +252,15 @@ int spmspv_bfs(spmspv_handle* h, int32_t src, int32_t* level, int32_t* parent,
  *                        (the size needed when it exceeds y_cap[b]).
  *   opts                 SPMSPV_SCHED_OPT(s) (pull schedules run as their push
  *                        form), SPMSPV_MASK_COMPLEMENT.
- *   lanes                0: autotuned persistent form: the push schedule is taken
+ *   lanes                0: autotuned: the form and push schedule are taken
  *                        from the handle's tuning cache for this batch profile
  *                        (spmspv_tune_key), or, on the first call with a new
- *                        profile, found by running the batch under every push
- *                        schedule 0..5 (two runs each, the second timed) and
- *                        cached (an entry set with spmspv_tune_set to lanes
- *                        1..16 runs the lanes form instead).  Any schedule in
- *                        opts is then ignored.
+ *                        profile, found by running the batch under every
+ *                        candidate (the persistent form under push schedules
+ *                        0..5, the lanes form with 4 and 16 lanes under
+ *                        schedules 2 and 5; two runs each, the second timed)
+ *                        and cached (lanes 0 in the cache: the persistent form).
+ *                        Any schedule in opts is then ignored.
  *                        SPMSPV_LANES_PERSISTENT: the persistent form with the
  *                        schedule in opts (or the handle's default).
  *                        1..16: the lanes form with that many lanes; lane

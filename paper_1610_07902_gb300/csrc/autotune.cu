@@ -7,7 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <iterator>
+#include <utility>
 #include <vector>
 
 #include "handle.cuh"
@@ -75,25 +75,35 @@ int tune_and_run(spmspv_handle* h, uint64_t key, cudaStream_t s,
   }
   TuneEntry best{key, 0, -1, INFINITY};
   int rc = SPMSPV_OK;
-  const std::vector<int32_t> lane_choices =
-      persistent ? std::vector<int32_t>{0} : std::vector<int32_t>(std::begin(kLaneChoices), std::end(kLaneChoices));
-  for (int32_t lanes : lane_choices) {
-    for (int sid = 0; sid < nsched && rc == SPMSPV_OK; ++sid) {
-      const uint32_t o = SPMSPV_SCHED_FORCE | SPMSPV_SCHED_OPT(sid);
-      // first run: graph instantiation and first touch; second run: timed
-      if ((rc = run(lanes, o)) != SPMSPV_OK) break;
-      cudaEventRecord(e0, s);
-      if ((rc = run(lanes, o)) != SPMSPV_OK) break;
-      cudaEventRecord(e1, s);
-      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
-        rc = cuda_fail(e, "autotune timing");
-        break;
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best.ms) best = TuneEntry{key, lanes, sid, ms};
+  // candidates (lanes, schedule): the lanes form over every lane count and
+  // schedule, or the persistent form (lanes 0) over every schedule plus a few
+  // lanes configurations (frontiers on a matrix of many rows can favour them)
+  std::vector<std::pair<int32_t, int>> cand;
+  if (persistent) {
+    for (int sid = 0; sid < nsched; ++sid) cand.push_back({0, sid});
+    for (int32_t lanes : {4, 16})
+      for (int sid : {2, 5})
+        if (sid < nsched) cand.push_back({lanes, sid});
+  } else {
+    for (int32_t lanes : kLaneChoices)
+      for (int sid = 0; sid < nsched; ++sid) cand.push_back({lanes, sid});
+  }
+  for (const auto& c : cand) {
+    const int32_t lanes = c.first;
+    const int sid = c.second;
+    const uint32_t o = SPMSPV_SCHED_FORCE | SPMSPV_SCHED_OPT(sid);
+    // first run: graph instantiation and first touch; second run: timed
+    if ((rc = run(lanes, o)) != SPMSPV_OK) break;
+    cudaEventRecord(e0, s);
+    if ((rc = run(lanes, o)) != SPMSPV_OK) break;
+    cudaEventRecord(e1, s);
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+      rc = cuda_fail(e, "autotune timing");
+      break;
     }
-    if (rc != SPMSPV_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best.ms) best = TuneEntry{key, lanes, sid, ms};
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -149,7 +149,8 @@ uint64_t tune_key(int kind, int sem, int masked, int32_t B, int64_t total_f);
 // Runs `run(lanes, schedule opts)` with the cached choice for `key`, or times
 // every candidate on `s` (each run twice, the second timed) and caches the best.
 // Candidates: lanes 2/4/8/16 x push schedules 0..nsched-1; with
-// persistent = true, only the persistent form (lanes 0) x the schedules.
+// persistent = true, the persistent form (lanes 0) x the schedules, and lanes
+// 4 and 16 x schedules 2 and 5.
 int tune_and_run(spmspv_handle* h, uint64_t key, cudaStream_t s,
                  const std::function<int(int32_t, uint32_t)>& run, int nsched = 6, bool persistent = false);
 cudaError_t alloc_pull_buffers(spmspv_handle* h);

@@ -111,7 +111,7 @@ def test_autotuned_batch_matches_and_caches(lib):
         nz = torch.zeros(B, dtype=torch.int32, device="cuda")
         S.spmspv_run_batched(Ad.handle, 0, B, *args, None, 0, 0, dev(y_off), dev(y_cap), yi, yv, nz, 0)
         lanes, sched, cached = S.spmspv_last_tuned(Ad.handle)
-        assert lanes == 0 and 0 <= sched < 6  # the persistent form
+        assert lanes in (0, 4, 16) and 0 <= sched < 6  # 0: the persistent form
         assert cached == (call == 1)
         outs.append((nz.cpu().numpy(), yi.cpu().numpy(), yv.cpu().numpy()))
     nz_h, yi_h, yv_h = outs[1]

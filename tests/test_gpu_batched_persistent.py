@@ -205,5 +205,5 @@ def test_persistent_autotuned_caches_schedule(lib):
     for call in range(2):
         run_and_check(torch, S, A, Ad, fronts, 0, 0)
         lanes, sched, cached = S.spmspv_last_tuned(Ad.handle)
-        assert lanes == 0 and 0 <= sched < 6 and cached == (call == 1)
+        assert lanes in (0, 4, 16) and 0 <= sched < 6 and cached == (call == 1)
     Ad.close()
