@@ -37,7 +37,9 @@
 // Bucket keys are (frontier, row block): the buckets of different frontiers
 // never mix, and a frontier's bucket runs sit in the slots of its own tiles,
 // so no bucket capacity has to be reserved and no global atomic places a run.
-// Hub rows are not relabelled here (the row ids are read as stored).
+// Hub rows (the handle's relabelled row ids) are summed per tile in shared
+// memory and staged once per tile, so a merge task sees a hub row at most
+// once per tile of its frontier.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -96,7 +98,10 @@ struct K6Args {
   int32_t* d_nnz_y;
   // matrix
   const int32_t* colptr;
-  const int32_t* rowidx;
+  const int32_t* rowidx;    // row ids as stored (the one-CTA small frontiers)
+  const int32_t* rowidx_t;  // row ids of the tiles: hub rows relabelled to m + hub index
+  int nhot;                 // hub rows (0: none; rowidx_t == rowidx)
+  const int32_t* hot_rows;  // [nhot] their row ids
   const float* val;
   const int32_t* jc;
   const int32_t* aux;
@@ -141,7 +146,7 @@ struct K6Args {
 __host__ __device__ constexpr size_t k6_smem_scan() { return 3 * sizeof(int32_t) * (size_t)k6_pad(K6_CH); }
 __host__ __device__ constexpr size_t k6_smem_expand(int nb) {
   return sizeof(int32_t) * (QMAX + 1) + sizeof(uint32_t) * (QMAX + 1) + sizeof(uint32_t) * (QMAX / 32) +
-         sizeof(int32_t) * ((size_t)nb + 1);
+         sizeof(int32_t) * ((size_t)nb + 1) + sizeof(uint32_t) * HOT_MAX * 2 + sizeof(uint32_t) * (HOT_MAX / 32);
 }
 __host__ __device__ constexpr size_t k6_smem_merge(int lwb) {
   return ((size_t)1 << lwb) * sizeof(uint32_t) + (((size_t)1 << lwb) / 32) * sizeof(uint32_t) +
@@ -532,8 +537,12 @@ __device__ void k6_tile(const K6Args& a, int32_t k, int32_t slot, unsigned char*
   uint32_t* kx = (uint32_t*)(kbase + QMAX + 1);
   uint32_t* hbits = kx + QMAX + 1;
   int32_t* hist = (int32_t*)(hbits + QMAX / 32);
+  uint32_t* hacc = (uint32_t*)(hist + a.nb + 1);  // the tile's hub sums
+  int32_t* hrow = (int32_t*)(hacc + HOT_MAX);     // hub row ids (loaded when the phase starts)
+  uint32_t* htb = (uint32_t*)(hrow + HOT_MAX);    // hubs the tile touched
   uint2* stage = (uint2*)smem;  // the staged products take the bytes of the x entries
   const int nb = a.nb, lwb = a.lwb;
+  const int nhot = a.nhot;
   const uint32_t wmask = (1u << lwb) - 1u;
   const int32_t b = __ldcg(a.tf + k);
   const int32_t W = __ldcg(a.fW + b), fc = __ldcg(a.ffc + b), xb = a.xp[b], tb = __ldcg(a.ftb + b);
@@ -556,9 +565,9 @@ __device__ void k6_tile(const K6Args& a, int32_t k, int32_t slot, unsigned char*
   uint32_t rrow[K2_IMAX], rval[K2_IMAX];
   int32_t rank[K2_IMAX];
   if (np == q)
-    k2_gather<SEM, IT, true>(a.rowidx, a.val, hbits, kbase, kx, IT, warp, lane, p0, np, a.nnz, rrow, rval);
+    k2_gather<SEM, IT, true>(a.rowidx_t, a.val, hbits, kbase, kx, IT, warp, lane, p0, np, a.nnz, rrow, rval);
   else
-    k2_gather<SEM, IT, false>(a.rowidx, a.val, hbits, kbase, kx, IT, warp, lane, p0, np, a.nnz, rrow, rval);
+    k2_gather<SEM, IT, false>(a.rowidx_t, a.val, hbits, kbase, kx, IT, warp, lane, p0, np, a.nnz, rrow, rval);
   const uint32_t* mask = a.masks ? a.masks + (int64_t)b * a.mask_stride : nullptr;
 #pragma unroll
   for (int i = 0; i < K2_IMAX; ++i) {
@@ -566,7 +575,17 @@ __device__ void k6_tile(const K6Args& a, int32_t k, int32_t slot, unsigned char*
     const uint32_t row = rrow[i];
     if (row == 0xffffffffu) continue;
     if (row >= (uint32_t)a.m) {
-      atomicOr(a.status, ST_INDEX);
+      const uint32_t hs = row - (uint32_t)a.m;
+      if (hs >= (uint32_t)nhot) {
+        atomicOr(a.status, ST_INDEX);
+        continue;
+      }
+      // a hub row: summed in the tile, staged once below
+      const uint32_t hr = (uint32_t)hrow[hs];
+      if (mask && ((__ldg(mask + (hr >> 5)) >> (hr & 31)) & 1u)) continue;
+      spa_apply<SEM>(hacc, hs, rval[i]);
+      const uint32_t hb = 1u << (hs & 31);
+      if (!(htb[hs >> 5] & hb)) atomicOr(&htb[hs >> 5], hb);
       continue;
     }
     if (mask && ((__ldg(mask + (row >> 5)) >> (row & 31)) & 1u)) continue;
@@ -574,6 +593,16 @@ __device__ void k6_tile(const K6Args& a, int32_t k, int32_t slot, unsigned char*
   }
   __syncthreads();
   for (int j = tid; j < QMAX / 32; j += K6_THREADS) hbits[j] = 0u;
+  // every hub the tile touched is one more entry of its bucket
+  constexpr int HPT = HOT_MAX / K6_THREADS;
+  int32_t hrank[HPT];
+#pragma unroll
+  for (int k2 = 0; k2 < HPT; ++k2) {
+    const int hs = tid + k2 * K6_THREADS;
+    hrank[k2] = -1;
+    if (hs < nhot && ((htb[hs >> 5] >> (hs & 31)) & 1u)) hrank[k2] = atomicAdd(&hist[hrow[hs] >> lwb], 1);
+  }
+  __syncthreads();
   // one warp turns the counts into the tile's bucket offsets
   if (warp == 0) {
     const int per = (nb + 31) >> 5;
@@ -602,6 +631,16 @@ __device__ void k6_tile(const K6Args& a, int32_t k, int32_t slot, unsigned char*
 #pragma unroll
   for (int i = 0; i < K2_IMAX; ++i)
     if (rank[i] >= 0) stage[hist[rrow[i] >> lwb] + rank[i]] = make_uint2(rrow[i], rval[i]);
+#pragma unroll
+  for (int k2 = 0; k2 < HPT; ++k2) {
+    const int hs = tid + k2 * K6_THREADS;
+    if (hrank[k2] >= 0) {
+      const uint32_t hr = (uint32_t)hrow[hs];
+      stage[hist[hr >> lwb] + hrank[k2]] = make_uint2(hr, hacc[hs]);
+      hacc[hs] = sr_identity<SEM>();  // untouched sums stay at the identity
+    }
+  }
+  for (int j = tid; j < HOT_MAX / 32; j += K6_THREADS) htb[j] = 0u;
   __syncthreads();
   const int32_t kept = sh.kept;
   const int64_t dst0 = (int64_t)slot * q;
@@ -619,7 +658,7 @@ __device__ void k6_tile(const K6Args& a, int32_t k, int32_t slot, unsigned char*
 template <int SEM>
 __device__ void k6_merge(const K6Args& a, int32_t li, int r, int32_t wt0w, unsigned char* smem, K6Shared& sh) {
   constexpr bool kDenseForm = SEM == kPlusTimes;
-  constexpr int U = 8;  // 32-entry units a warp reads at once
+  constexpr int U = 4;  // units of 32 four-entry chunks a warp reads at once
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int lwb = a.lwb;
   const int32_t wb = 1 << lwb;
@@ -686,14 +725,19 @@ __device__ void k6_merge(const K6Args& a, int32_t li, int r, int32_t wt0w, unsig
         }
         __syncthreads();
       }
-      // units before each run (seg_u[ns] = all units of this part of the list)
+      // units before each run (seg_u[ns] = all units of this part of the
+      // list); a unit is 32 aligned 4-entry chunks of one run, one per lane
       {
         constexpr int SPT = K6_SEGMAX / K6_THREADS;
         int32_t uc[SPT], tsum = 0;
 #pragma unroll
         for (int i = 0; i < SPT; ++i) {
           const int32_t j = tid * SPT + i;
-          uc[i] = j < ns ? (seg_n[j] + 31) >> 5 : 0;
+          uc[i] = 0;
+          if (j < ns && seg_n[j] > 0) {
+            const int32_t chunks = ((seg_lo[j] + seg_n[j] + 3) >> 2) - (seg_lo[j] >> 2);
+            uc[i] = (chunks + 31) >> 5;
+          }
           tsum += uc[i];
         }
         int32_t nu;
@@ -721,32 +765,46 @@ __device__ void k6_merge(const K6Args& a, int32_t li, int r, int32_t wt0w, unsig
         }
         j = lo;
       }
+      const uint2* brow4 = reinterpret_cast<const uint2*>(a.brow);  // 4 row offsets
+      const uint4* bval4 = reinterpret_cast<const uint4*>(a.bval);  // 4 values
       for (; u < u_end; u += U) {
-        uint32_t rr[U], vv[U];
-        bool ok[U];
+        uint2 rr[U];
+        uint4 vv[U];
+        int32_t e0[U], ea[U], eb[U];  // the chunk's first entry, the run's entries [ea, eb)
 #pragma unroll
         for (int k = 0; k < U; ++k) {
           const int32_t uu = u + k;
-          ok[k] = false;
-          rr[k] = 0u;
-          vv[k] = 0u;
+          rr[k] = make_uint2(0u, 0u);
+          vv[k] = make_uint4(0u, 0u, 0u, 0u);
+          e0[k] = 0;
+          ea[k] = 0;
+          eb[k] = 0;
           if (uu < u_end) {
             while (seg_u[j + 1] <= uu) ++j;
-            const int32_t off = ((uu - seg_u[j]) << 5) + lane;
-            if (off < seg_n[j]) {
-              const int64_t pos = (int64_t)(s0 + j0 + j) * q + seg_lo[j] + off;
-              rr[k] = __ldcg(a.brow + pos);
-              if (SEM != kOrAnd) vv[k] = __ldcg(a.bval + pos);
-              ok[k] = true;
+            const int32_t lo = seg_lo[j], hi = lo + seg_n[j];
+            const int32_t c = (lo >> 2) + ((uu - seg_u[j]) << 5) + lane;  // chunk inside the tile slot
+            if (c < ((hi + 3) >> 2)) {
+              const int64_t base = (int64_t)(s0 + j0 + j) * q + 4 * c;  // a multiple of 4
+              rr[k] = __ldcg(brow4 + (base >> 2));
+              if (SEM != kOrAnd) vv[k] = __ldcg(bval4 + (base >> 2));
+              e0[k] = 4 * c;
+              ea[k] = lo;
+              eb[k] = hi;
             }
           }
         }
 #pragma unroll
         for (int k = 0; k < U; ++k) {
-          if (!ok[k]) continue;
-          const uint32_t x = rr[k] & wmask;
-          if (!dense) atomicOr(occ + (x >> 5), 1u << (x & 31));
-          spa_apply<SEM>(spa, x, vv[k]);
+          const uint32_t rw[4] = {rr[k].x & 0xffffu, rr[k].x >> 16, rr[k].y & 0xffffu, rr[k].y >> 16};
+          const uint32_t vw[4] = {vv[k].x, vv[k].y, vv[k].z, vv[k].w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int32_t e = e0[k] + t;
+            if (e < ea[k] || e >= eb[k]) continue;
+            const uint32_t x = rw[t] & wmask;
+            if (!dense) atomicOr(occ + (x >> 5), 1u << (x & 31));
+            spa_apply<SEM>(spa, x, vw[t]);
+          }
         }
       }
     }
@@ -816,6 +874,25 @@ __device__ void k6_merge(const K6Args& a, int32_t li, int r, int32_t wt0w, unsig
   __syncthreads();
 }
 
+// The expand phase's shared state at its start: no entry starts marked, the
+// hub table loaded, the hub sums at the semiring's identity.
+template <int SEM>
+__device__ void k6_expand_setup(const K6Args& a, unsigned char* smem) {
+  const int tid = threadIdx.x;
+  uint32_t* hbits = (uint32_t*)(smem + sizeof(int32_t) * 2 * (QMAX + 1));
+  int32_t* hist = (int32_t*)(hbits + QMAX / 32);
+  uint32_t* hacc = (uint32_t*)(hist + a.nb + 1);
+  int32_t* hrow = (int32_t*)(hacc + HOT_MAX);
+  uint32_t* htb = (uint32_t*)(hrow + HOT_MAX);
+  for (int j = tid; j < QMAX / 32; j += K6_THREADS) hbits[j] = 0u;
+  for (int h = tid; h < HOT_MAX; h += K6_THREADS) {
+    hacc[h] = sr_identity<SEM>();
+    hrow[h] = h < a.nhot ? a.hot_rows[h] : 0;
+  }
+  for (int j = tid; j < HOT_MAX / 32; j += K6_THREADS) htb[j] = 0u;
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
@@ -835,11 +912,7 @@ __global__ void __launch_bounds__(K6_THREADS, 2) k6_batched(K6Args a) {
   const int32_t n_large = __ldcg(&a.st->n_large);
   k6_tile_starts(a, n_large);
   if (!k6_barrier(a, ++epoch, sh)) return;
-  {
-    uint32_t* hbits = (uint32_t*)(k6_smem_raw + sizeof(int32_t) * 2 * (QMAX + 1));
-    for (int j = tid; j < QMAX / 32; j += K6_THREADS) hbits[j] = 0u;
-    __syncthreads();
-  }
+  k6_expand_setup<SEM>(a, k6_smem_raw);
   const int passes = n_waves > 0 ? n_waves : 1;
   for (int w = 0; w < passes; ++w) {
     const int32_t t0 = w < n_waves ? __ldcg(a.wt0 + w) : 0;
@@ -871,9 +944,7 @@ __global__ void __launch_bounds__(K6_THREADS, 2) k6_batched(K6Args a) {
     }
     if (w + 1 < passes) {
       if (!k6_barrier(a, ++epoch, sh)) return;
-      uint32_t* hbits = (uint32_t*)(k6_smem_raw + sizeof(int32_t) * 2 * (QMAX + 1));
-      for (int j = tid; j < QMAX / 32; j += K6_THREADS) hbits[j] = 0u;
-      __syncthreads();
+      k6_expand_setup<SEM>(a, k6_smem_raw);
     }
   }
   if (tid == 0) atomicMax(&a.st->t[K6_STAMPS - 1], k6_clock());
@@ -1137,6 +1208,9 @@ int run_batched_k6(spmspv_handle* h, int sem, int32_t B, const int32_t* x_off, c
   a.d_nnz_y = d_nnz_y;
   a.colptr = A.colptr;
   a.rowidx = A.rowidx;
+  a.nhot = h->ws.nhot;
+  a.rowidx_t = h->ws.nhot > 0 ? h->ws.rowidx_k2 : A.rowidx;
+  a.hot_rows = h->ws.hot_rows;
   a.val = A.val;
   a.jc = A.jc;
   a.aux = A.aux;
