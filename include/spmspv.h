@@ -122,9 +122,13 @@ const char* spmspv_last_error(void);
  *   flags    SPMSPV_CSC_PATTERN_SYMMETRIC, SPMSPV_CSC_SYMMETRIC or 0.  The
  *            flags are trusted, not checked.
  * Synchronous: allocates the workspace (about 6 bytes per nonzero for the
- * buckets plus 16 bytes per column) on the current device, and scans
+ * buckets plus 16 bytes per column, and 4 bytes per row for the direct
+ * form's accumulator when m <= 2^24) on the current device, and scans
  * rowidx once to size the row-range buckets.  Errors: ARG, OOM, CUDA,
  * UNSUPPORTED (m too large for the bucket row width).
+ * A handle's calls use its one workspace: calls on the same handle must not
+ * run at the same time on the GPU (issue them on one stream, or order the
+ * streams); different handles are independent.
  */
 int spmspv_create_csc(spmspv_handle** h, int32_t m, int32_t n, int64_t nnz,
                       const int32_t* colptr, const int32_t* rowidx, const void* val,
