@@ -72,12 +72,10 @@ __host__ __device__ constexpr int k6_pad(int e) { return e + (e >> 5); }
 struct K6State {
   uint32_t bar;        // grid barrier arrivals
   uint32_t tk_scan;    // scan chunk tickets
-  uint32_t tk_tiles;   // tile-start pass: not a ticket (static split); spare
   int32_t n_small;
   int32_t n_large;
   int32_t n_tiles;
   int32_t n_waves;
-  int32_t pad;
   long long padded;    // products of the large frontiers with their tiles rounded up
   unsigned long long t[K6_STAMPS];  // device clock (ns): CTA 0 at its start, after each grid
                                     // barrier (slot = the barrier's number) and at its end (last slot)
