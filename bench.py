@@ -688,7 +688,8 @@ def bench_batched(S, dev, stream, B=256):
            "spmspv": {"batched_ms": t_b, "sequential_ms": t_s, "speedup": t_s / t_b,
                       "batched_gteps": W / (t_b * 1e-3) / 1e9, "tuned_lanes": tuned[0],
                       "tuned_schedule": tuned[1], "form": "persistent" if tuned[0] == 0 else "lanes",
-                      "phases_ms": dict(zip(["scan", "plan", "tile_starts", "expand", "merge", "launch"],
+                      "phases_ms": dict(zip(["scan", "plan", "tile_starts", "expand", "merge", "launch",
+                                             "direct_expand", "direct_compact"],
                                             [round(float(v), 4) for v in phases])),
                       "waves": waves, "lanes16_ms": t_l, "lanes16_gteps": W / (t_l * 1e-3) / 1e9,
                       "identical_index_sets": same_idx, "max_rel_value_diff": rel}}
@@ -902,8 +903,8 @@ def profile_case(args, S, dev):
         extra["gteps"] = extra["products"] / (t * 1e-3) / 1e9
     if case == "batched":
         ph, waves = S.spmspv_batched_phase_times(Ad.handle)
-        extra["phases_ms"] = dict(zip(["scan", "plan", "tile_starts", "expand", "merge", "launch"],
-                                      [round(float(v), 4) for v in ph]))
+        extra["phases_ms"] = dict(zip(["scan", "plan", "tile_starts", "expand", "merge", "launch",
+                                       "direct_expand", "direct_compact"], [round(float(v), 4) for v in ph]))
         extra["waves"] = waves
     print(json.dumps(dict({"case": case, "scale": args.scale, "ms_per_step": t,
                            "status": S.spmspv_device_status(Ad.handle)}, **extra)), flush=True)

@@ -230,9 +230,13 @@ int spmspv_bfs(spmspv_handle* h, int32_t src, int32_t* level, int32_t* parent,
  * products are dominated by overhead).  Two forms run it:
  *   persistent  one cooperative kernel launch for the whole batch: its CTAs
  *               scan every frontier, sort each frontier of at most 4096
- *               products in one CTA, and run the expand and merge steps of the
- *               larger ones with buckets keyed by (frontier, row block), taking
- *               tiles and buckets of all frontiers from shared device queues.
+ *               products in one CTA, run (+,*) frontiers of at least m/2
+ *               products in the direct form (products added into dense
+ *               accumulators of m floats in device memory, as many at a time
+ *               as fit in 128 MB; not with SPMSPV_BUCKETS_ONLY), and the expand
+ *               and merge steps of the others with buckets keyed by (frontier,
+ *               row block), taking tiles and buckets of all frontiers from
+ *               shared device queues.
  *               x_cnt is read on the host first (one synchronisation of
  *               `stream`) to size the work arrays; the launch also needs every
  *               CTA resident (a cooperative launch).  Its buckets hold m/256,
@@ -255,7 +259,7 @@ int spmspv_bfs(spmspv_handle* h, int32_t src, int32_t* level, int32_t* parent,
  *                        entries (ascending indices); d_nnz_y[b] receives nnz(y_b)
  *                        (the size needed when it exceeds y_cap[b]).
  *   opts                 SPMSPV_SCHED_OPT(s) (pull schedules run as their push
- *                        form), SPMSPV_MASK_COMPLEMENT.
+ *                        form), SPMSPV_MASK_COMPLEMENT, SPMSPV_BUCKETS_ONLY.
  *   lanes                0: autotuned: the form and push schedule are taken
  *                        from the handle's tuning cache for this batch profile
  *                        (spmspv_tune_key), or, on the first call with a new
@@ -289,9 +293,11 @@ int spmspv_run_batched(spmspv_handle* h, int semiring, int32_t B, const int32_t*
  * Device-clock durations (ms) of the phases of the handle's last persistent
  * batched launch (spmspv_run_batched, lanes 0 or SPMSPV_LANES_PERSISTENT):
  * ms[0] work scan, ms[1] plan, ms[2] tile starts, ms[3] expand (Step 1 and
- * the one-CTA small frontiers, summed over waves), ms[4] merge (Steps 2-3,
- * summed over waves), ms[5] the whole launch; min(capacity, 6) entries are
- * written.  *waves (may be NULL) receives the launch's number of waves.
+ * the one-CTA small frontiers, summed over the bucket waves), ms[4] merge
+ * (Steps 2-3, summed over the bucket waves), ms[5] the whole launch, ms[6]
+ * the direct form's expand and ms[7] its compaction (summed over its waves);
+ * min(capacity, 8) entries are written.  *waves (may be NULL) receives the
+ * launch's number of bucket waves.
  * Synchronises the handle's last stream.  SPMSPV_ERR_STATE before any such
  * launch.
  */

@@ -74,8 +74,10 @@ struct K6State {
   uint32_t tk_scan;    // scan chunk tickets
   int32_t n_small;
   int32_t n_large;
-  int32_t n_tiles;
+  int32_t n_tiles;     // tiles of the large (bucketed) frontiers; the direct ones' follow
   int32_t n_waves;
+  int32_t n_direct;    // frontiers in the direct form
+  int32_t n_dwaves;    // their waves (at most dslots frontiers each)
   long long padded;    // products of the large frontiers with their tiles rounded up
   unsigned long long t[K6_STAMPS];  // device clock (ns): CTA 0 at its start, after each grid
                                     // barrier (slot = the barrier's number) and at its end (last slot)
@@ -115,9 +117,19 @@ struct K6Args {
   int32_t tw;     // row stride of the tile offset table (tile slots of one wave)
   int32_t nw_cap;
   int32_t tiles_cap;
+  // direct form of the frontiers with at least direct_min products ((+,*) only)
+  int32_t direct_min;       // 0: no direct form
+  int32_t dslots;           // accumulators: frontiers of one direct wave
+  float* dacc;              // [dslots][m] dense accumulators, -0.0 in every row between launches
+  unsigned long long* dstat;  // [dslots][nrt] look-back words of the compaction
+  int32_t nrt;              // compaction row tiles per accumulator
+  int32_t* ld;              // [B] direct frontier ids in order
+  int32_t* fdi;             // [B] direct index of each direct frontier
+  int32_t* dwt0;            // [B + 2] first tile of each direct wave
+  int32_t dw_cap;
   // work arrays
   K6State* st;
-  uint32_t* tk;             // [2 * nw_cap] expand and merge tickets per wave
+  uint32_t* tk;             // [2 * (nw_cap + dw_cap)] expand and merge tickets per wave
   int32_t* wt0;             // [nw_cap + 1] first tile of each wave
   int32_t* wl0;             // [nw_cap + 1] first large frontier of each wave
   unsigned long long* cstat;  // [nc] scan look-back words
@@ -311,8 +323,9 @@ __device__ void k6_plan(const K6Args& a, K6Shared& sh) {
         a.ffc[b] = 0;
       }
     }
-    const bool large = W > K6_SMALL_MAX;
-    const bool small = W > 0 && !large;
+    const bool direct = a.direct_min > 0 && W > K6_SMALL_MAX && W >= a.direct_min;
+    const bool large = W > K6_SMALL_MAX && !direct;
+    const bool small = W > 0 && W <= K6_SMALL_MAX;
     const unsigned long long T = large ? (unsigned long long)(((int64_t)W + a.q - 1) / a.q) : 0ull;
     const unsigned long long v = T | ((unsigned long long)(large ? 1 : 0) << 32) |
                                  ((unsigned long long)(small ? 1 : 0) << 48);
@@ -325,7 +338,7 @@ __device__ void k6_plan(const K6Args& a, K6Shared& sh) {
         a.lb[nlarge + (int32_t)((ex >> 32) & 0xffffu)] = b;
       } else if (small) {
         a.sl[nsmall + (int32_t)(ex >> 48)] = b;
-      } else {
+      } else if (!direct) {
         a.d_nnz_y[b] = 0;
       }
     }
@@ -333,11 +346,40 @@ __device__ void k6_plan(const K6Args& a, K6Shared& sh) {
     nlarge += (int32_t)((tot >> 32) & 0xffffu);
     nsmall += (int32_t)(tot >> 48);
   }
-  if (tiles > a.tiles_cap) {  // cannot happen with the host's bound; the large frontiers are dropped
+  // the direct frontiers: their tiles follow the large frontiers' tiles
+  int64_t dtiles = 0;
+  int32_t ndirect = 0;
+  if (a.direct_min > 0) {
+    for (int32_t base = 0; base < a.B; base += K6_THREADS) {
+      const int32_t b = base + tid;
+      const int32_t W = b < a.B ? __ldcg(a.fW + b) : 0;
+      const bool direct = b < a.B && W > K6_SMALL_MAX && W >= a.direct_min;
+      const unsigned long long T = direct ? (unsigned long long)(((int64_t)W + a.q - 1) / a.q) : 0ull;
+      const unsigned long long v = T | ((unsigned long long)(direct ? 1 : 0) << 32);
+      unsigned long long tot;
+      const unsigned long long ex = block_exclusive_sum<K6_THREADS>(v, sh.scan, &tot);
+      if (direct) {
+        const int64_t tb = tiles + dtiles + (int64_t)(ex & 0xffffffffull);
+        const int32_t di = ndirect + (int32_t)(ex >> 32);
+        a.ftb[b] = (int32_t)min(tb, (int64_t)INT32_MAX);
+        a.ld[di] = b;
+        a.fdi[b] = di;
+      }
+      dtiles += (int64_t)(tot & 0xffffffffull);
+      ndirect += (int32_t)(tot >> 32);
+    }
+  }
+  if (tiles + dtiles > a.tiles_cap) {  // cannot happen with the host's bound; those frontiers are dropped
     if (tid == 0) atomicOr(a.status, ST_BOUND);
     tiles = 0;
     nlarge = 0;
+    dtiles = 0;
+    ndirect = 0;
   }
+  const int32_t ndw = (ndirect + a.dslots - 1) / max(a.dslots, 1);
+  __syncthreads();
+  for (int32_t dw = tid; dw <= ndw && dw < a.dw_cap; dw += K6_THREADS)
+    a.dwt0[dw] = dw < ndw ? __ldcg(a.ftb + __ldcg(a.ld + dw * a.dslots)) : (int32_t)(tiles + dtiles);
   __syncthreads();
   // waves: frontier b joins wave floor(first tile * q / win); a frontier's
   // padded products are at most win, so consecutive waves differ by one
@@ -366,6 +408,9 @@ __device__ void k6_plan(const K6Args& a, K6Shared& sh) {
     a.st->n_large = nlarge;
     a.st->n_tiles = (int32_t)tiles;
     a.st->n_waves = nw;
+    a.st->n_direct = ndirect;
+    a.st->n_dwaves = ndw < a.dw_cap ? ndw : 0;
+    if (ndw >= a.dw_cap && ndw > 0) atomicOr(a.status, ST_BOUND);
     a.st->padded = tiles * a.q;
   }
 }
@@ -651,6 +696,133 @@ __device__ void k6_tile(const K6Args& a, int32_t k, int32_t slot, unsigned char*
 }
 
 // ---------------------------------------------------------------------------
+// direct form: one tile of a frontier with many products ((+,*)): every
+// product added into the frontier's accumulator in global memory (L2), hub
+// rows summed in the tile first
+// ---------------------------------------------------------------------------
+template <int IT>
+__device__ void k6_tile_direct(const K6Args& a, int32_t k, float* acc, unsigned char* smem) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int32_t q = IT * K6_THREADS;
+  int32_t* kbase = (int32_t*)smem;
+  uint32_t* kx = (uint32_t*)(kbase + QMAX + 1);
+  uint32_t* hbits = kx + QMAX + 1;
+  int32_t* hist = (int32_t*)(hbits + QMAX / 32);
+  uint32_t* hacc = (uint32_t*)(hist + a.nb + 1);
+  int32_t* hrow = (int32_t*)(hacc + HOT_MAX);
+  uint32_t* htb = (uint32_t*)(hrow + HOT_MAX);
+  const int nhot = a.nhot;
+  const int32_t b = __ldcg(a.tf + k);
+  const int32_t W = __ldcg(a.fW + b), fc = __ldcg(a.ffc + b), xb = a.xp[b], tb = __ldcg(a.ftb + b);
+  const int32_t t = k - tb;
+  const int32_t T = (int32_t)(((int64_t)W + q - 1) / q);
+  const int32_t p0 = t * q;
+  const int32_t np = min(q, W - p0);
+  const int32_t e0 = __ldcg(a.tk0 + k);
+  const int32_t e1 = t + 1 < T ? __ldcg(a.tk0 + k + 1) + 1 : xb + fc;
+  const int32_t nk = max(1, min(e1 - e0, QMAX + 1));
+  for (int32_t l = tid; l < nk; l += K6_THREADS) {
+    const int32_t w = __ldcg(a.cw + e0 + l);
+    kbase[l] = __ldcg(a.cb + e0 + l) - w;
+    kx[l] = __ldcg(a.cx + e0 + l);
+    const int32_t off = w - p0;
+    if (l > 0 && off > 0 && off < np) atomicOr(&hbits[off >> 5], 1u << (off & 31));
+  }
+  __syncthreads();
+  uint32_t rrow[K2_IMAX], rval[K2_IMAX];
+  if (np == q)
+    k2_gather<kPlusTimes, IT, true>(a.rowidx_t, a.val, hbits, kbase, kx, IT, warp, lane, p0, np, a.nnz, rrow, rval);
+  else
+    k2_gather<kPlusTimes, IT, false>(a.rowidx_t, a.val, hbits, kbase, kx, IT, warp, lane, p0, np, a.nnz, rrow,
+                                     rval);
+  const uint32_t* mask = a.masks ? a.masks + (int64_t)b * a.mask_stride : nullptr;
+#pragma unroll
+  for (int i = 0; i < K2_IMAX; ++i) {
+    const uint32_t row = rrow[i];
+    if (row == 0xffffffffu) continue;
+    if (row >= (uint32_t)a.m) {
+      const uint32_t hs = row - (uint32_t)a.m;
+      if (hs >= (uint32_t)nhot) {
+        atomicOr(a.status, ST_INDEX);
+        continue;
+      }
+      const uint32_t hr = (uint32_t)hrow[hs];
+      if (mask && ((__ldg(mask + (hr >> 5)) >> (hr & 31)) & 1u)) continue;
+      spa_apply<kPlusTimes>(hacc, hs, rval[i]);
+      const uint32_t hb = 1u << (hs & 31);
+      if (!(htb[hs >> 5] & hb)) atomicOr(&htb[hs >> 5], hb);
+      continue;
+    }
+    if (mask && ((__ldg(mask + (row >> 5)) >> (row & 31)) & 1u)) continue;
+    atomicAdd(acc + row, __uint_as_float(rval[i]));
+  }
+  __syncthreads();
+  for (int j = tid; j < QMAX / 32; j += K6_THREADS) hbits[j] = 0u;
+  for (int hs = tid; hs < nhot; hs += K6_THREADS) {
+    if ((htb[hs >> 5] >> (hs & 31)) & 1u) {
+      atomicAdd(acc + hrow[hs], __uint_as_float(hacc[hs]));
+      hacc[hs] = 0u;
+    }
+  }
+  __syncthreads();
+  for (int j = tid; j < HOT_MAX / 32; j += K6_THREADS) htb[j] = 0u;
+  __syncthreads();
+}
+
+// The direct form's compaction: row tile rt (K6_DROWS rows) of one
+// frontier's accumulator, its touched rows (not -0.0) to y_b in ascending
+// order, each reset to -0.0; the tile's offset in y_b from a look-back along
+// the frontier's row tiles.
+constexpr int K6_DSTEPS = 16;                           // 32-row words per warp and tile
+constexpr int K6_DROWS = K6_THREADS * K6_DSTEPS;        // rows per tile (8192)
+
+__device__ void k6_dcompact(const K6Args& a, int32_t b, uint32_t* acc, unsigned long long* chain, int32_t rt,
+                            K6Shared& sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr uint32_t kEmpty = 0x80000000u;  // -0.0f
+  const int64_t r0 = (int64_t)rt * K6_DROWS + (int64_t)warp * (K6_DSTEPS * 32) + lane;
+  uint32_t v[K6_DSTEPS], bits[K6_DSTEPS];
+  int32_t cw = 0;
+#pragma unroll
+  for (int k = 0; k < K6_DSTEPS; ++k) v[k] = r0 + k * 32 < a.m ? __ldcg(acc + r0 + k * 32) : kEmpty;
+#pragma unroll
+  for (int k = 0; k < K6_DSTEPS; ++k) {
+    bits[k] = __ballot_sync(0xffffffffu, v[k] != kEmpty);
+    cw += __popc(bits[k]);
+  }
+  int32_t tot;
+  const int32_t run = block_exclusive_sum<K6_THREADS>(lane == 0 ? cw : 0, sh.iscan, &tot);
+  if (tid < 32) {
+    const unsigned long long pre = warp_lookback(chain, (uint32_t)rt, (unsigned long long)tot, a.status);
+    if (tid == 0) sh.off = (long long)pre;
+  }
+  __syncthreads();
+  const int32_t cap = a.y_cap[b];
+  const int64_t yo = a.y_off[b];
+  const uint32_t lt = (1u << lane) - 1u;
+  int64_t pos = sh.off + __shfl_sync(0xffffffffu, run, 0);
+#pragma unroll
+  for (int k = 0; k < K6_DSTEPS; ++k) {
+    if ((bits[k] >> lane) & 1u) {
+      const int64_t r = r0 + k * 32;
+      const int64_t pp = pos + __popc(bits[k] & lt);
+      if (pp < cap) {
+        a.y_idx[yo + pp] = (int32_t)r;
+        if (a.y_val) a.y_val[yo + pp] = v[k];
+      }
+      acc[r] = kEmpty;
+    }
+    pos += __popc(bits[k]);
+  }
+  if (rt == a.nrt - 1 && tid == 0) {
+    const int64_t total = sh.off + tot;
+    a.d_nnz_y[b] = (int32_t)total;
+    if (total > cap) atomicOr(a.status, ST_CAPACITY);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // phase 5: one (frontier, bucket) merge task
 // ---------------------------------------------------------------------------
 template <int SEM>
@@ -911,6 +1083,44 @@ __global__ void __launch_bounds__(K6_THREADS, 2) k6_batched(K6Args a) {
   k6_tile_starts(a, n_large);
   if (!k6_barrier(a, ++epoch, sh)) return;
   k6_expand_setup<SEM>(a, k6_smem_raw);
+  if (SEM == kPlusTimes) {
+    // the direct frontiers, dslots at a time: every tile's products into the
+    // frontier's accumulator, then the accumulators compacted into y
+    const int32_t n_direct = __ldcg(&a.st->n_direct);
+    const int32_t n_dw = __ldcg(&a.st->n_dwaves);
+    for (int dw = 0; dw < n_dw; ++dw) {
+      const int32_t d0 = dw * a.dslots;
+      const int32_t nd = min(a.dslots, n_direct - d0);
+      const int32_t t0 = __ldcg(a.dwt0 + dw), t1 = __ldcg(a.dwt0 + dw + 1);
+      for (int64_t i = (int64_t)blockIdx.x * K6_THREADS + tid; i < (int64_t)nd * a.nrt;
+           i += (int64_t)gridDim.x * K6_THREADS)
+        a.dstat[i] = 0ull;
+      uint32_t* tkd = a.tk + 2 * (a.nw_cap + dw);
+      for (;;) {
+        if (tid == 0) sh.item = atomicAdd(tkd, 1u);
+        __syncthreads();
+        const uint32_t it = sh.item;
+        if (it >= (uint32_t)(t1 - t0)) break;
+        const int32_t k = t0 + (int32_t)it;
+        const int32_t slot = __ldcg(a.fdi + __ldcg(a.tf + k)) - d0;
+        k6_tile_direct<IT>(a, k, a.dacc + (int64_t)slot * a.m, k6_smem_raw);
+      }
+      if (!k6_barrier(a, ++epoch, sh)) return;
+      // compaction tasks go tile-major: row tile rt of every frontier of the wave, then rt+1
+      const uint32_t tasks = (uint32_t)(nd * a.nrt);
+      for (;;) {
+        if (tid == 0) sh.item = atomicAdd(tkd + 1, 1u);
+        __syncthreads();
+        const uint32_t g = sh.item;
+        if (g >= tasks) break;
+        const int32_t slot = (int32_t)(g % (uint32_t)nd), rt = (int32_t)(g / (uint32_t)nd);
+        const int32_t b = __ldcg(a.ld + d0 + slot);
+        k6_dcompact(a, b, reinterpret_cast<uint32_t*>(a.dacc + (int64_t)slot * a.m), a.dstat + (int64_t)slot * a.nrt,
+                    rt, sh);
+      }
+      if (!k6_barrier(a, ++epoch, sh)) return;
+    }
+  }
   const int passes = n_waves > 0 ? n_waves : 1;
   for (int w = 0; w < passes; ++w) {
     const int32_t t0 = w < n_waves ? __ldcg(a.wt0 + w) : 0;
@@ -1001,6 +1211,9 @@ struct K6Buffers {
   DevArr<uint32_t> bval;
   DevArr<int32_t> toff;
   DevArr<unsigned long long> bstat;
+  DevArr<float> dacc;               // direct accumulators, -0.0 in every row between launches
+  DevArr<unsigned long long> dstat;
+  DevArr<int32_t> ld, fdi, dwt0;
   int32_t* h_pin = nullptr;       // pinned: x_cnt[B] | xp[B+1] | cp[B+1]
   size_t cap_pin = 0;
   long long* h_padded = nullptr;  // pinned: the padded products of the last launch
@@ -1070,6 +1283,11 @@ void release_k6(spmspv_handle* h) {
   kb->bval.release();
   kb->toff.release();
   kb->bstat.release();
+  kb->dacc.release();
+  kb->dstat.release();
+  kb->ld.release();
+  kb->fdi.release();
+  kb->dwt0.release();
   cudaFreeHost(kb->h_pin);
   cudaFreeHost(kb->h_padded);
   if (kb->uploaded) cudaEventDestroy(kb->uploaded);
@@ -1169,7 +1387,30 @@ int run_batched_k6(spmspv_handle* h, int sem, int32_t B, const int32_t* x_off, c
   const int64_t tw = capw / QF + 1;
   // a frontier's padded products are at most 2048 * (its 2048-product tiles + 2)
   const int64_t nw_cap = (tiles + 2 * (int64_t)B) * QF / win + 2;
-  if ((e = kb->st.grow(1)) != cudaSuccess || (e = kb->tk.grow((size_t)nw_cap * 2)) != cudaSuccess ||
+  // direct form ((+,*), m <= 2^24): frontiers with at least m/2 products, as
+  // many per wave as accumulators fit in 128 MB (at most 32; measured on the
+  // 256-frontier R-MAT s20 batch: 64 MB 1.116 ms, 128 MB 1.093 ms; a
+  // threshold of m/4 or m instead of m/2: 1.102 / 1.159 ms)
+  const bool direct = sem == kPlusTimes && !(opts & SPMSPV_BUCKETS_ONLY) && A.m <= DIRECT_M_MAX;
+  const int32_t dslots = direct ? (int32_t)std::max<int64_t>(1, std::min<int64_t>(32, ((int64_t)128 << 20) /
+                                                                                   (4 * (int64_t)A.m)))
+                                : 1;
+  const int32_t nrt = (int32_t)(((int64_t)A.m + K6_DROWS - 1) / K6_DROWS);
+  const int64_t dw_cap = (int64_t)B + 2;
+  if (direct && kb->dacc.cap < (size_t)dslots * A.m) {  // new accumulators start at -0.0 in every row
+    if ((e = kb->dacc.grow((size_t)dslots * A.m)) != cudaSuccess ||
+        (e = launch_fill_u32(reinterpret_cast<uint32_t*>(kb->dacc.p), (int64_t)kb->dacc.cap, 0x80000000u, s)) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return fail(SPMSPV_ERR_OOM, "batched accumulators: %s", cudaGetErrorString(e));
+    }
+  }
+  if ((e = kb->dstat.grow((size_t)dslots * nrt)) != cudaSuccess || (e = kb->ld.grow((size_t)B)) != cudaSuccess ||
+      (e = kb->fdi.grow((size_t)B)) != cudaSuccess || (e = kb->dwt0.grow((size_t)dw_cap)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SPMSPV_ERR_OOM, "batched work arrays: %s", cudaGetErrorString(e));
+  }
+  if ((e = kb->st.grow(1)) != cudaSuccess || (e = kb->tk.grow((size_t)(nw_cap + dw_cap) * 2)) != cudaSuccess ||
       (e = kb->wt0.grow((size_t)nw_cap + 1)) != cudaSuccess || (e = kb->wl0.grow((size_t)nw_cap + 1)) != cudaSuccess ||
       (e = kb->cstat.grow((size_t)nc)) != cudaSuccess || (e = kb->xp.grow((size_t)B + 1)) != cudaSuccess ||
       (e = kb->cp.grow((size_t)B + 1)) != cudaSuccess || (e = kb->fW.grow((size_t)B)) != cudaSuccess ||
@@ -1189,7 +1430,7 @@ int run_batched_k6(spmspv_handle* h, int sem, int32_t B, const int32_t* x_off, c
   cudaEventRecord(kb->uploaded, s);
   kb->uploaded_valid = 1;
   cudaMemsetAsync(kb->st.p, 0, sizeof(K6State), s);
-  cudaMemsetAsync(kb->tk.p, 0, sizeof(uint32_t) * nw_cap * 2, s);
+  cudaMemsetAsync(kb->tk.p, 0, sizeof(uint32_t) * (nw_cap + dw_cap) * 2, s);
   cudaMemsetAsync(kb->cstat.p, 0, sizeof(unsigned long long) * nc, s);
   K6Args a;
   memset(&a, 0, sizeof(a));
@@ -1246,6 +1487,15 @@ int run_batched_k6(spmspv_handle* h, int sem, int32_t B, const int32_t* x_off, c
   a.toff = kb->toff.p;
   a.bstat = kb->bstat.p;
   a.status = &h->ws.st->status;
+  a.direct_min = direct ? std::max<int32_t>(K6_SMALL_MAX + 1, A.m / 2) : 0;
+  a.dslots = dslots;
+  a.dacc = direct ? kb->dacc.p : nullptr;
+  a.dstat = kb->dstat.p;
+  a.nrt = nrt;
+  a.ld = kb->ld.p;
+  a.fdi = kb->fdi.p;
+  a.dwt0 = kb->dwt0.p;
+  a.dw_cap = (int32_t)dw_cap;
   const size_t smem = k6_smem(lwb, nb);
   if (smem > SMEM_PER_BLOCK_MAX) return fail(SPMSPV_ERR_UNSUPPORTED, "batched layout too large");
   const bool q8 = q == K2_IMAX * K6_THREADS;
@@ -1284,22 +1534,30 @@ extern "C" int spmspv_batched_phase_times(spmspv_handle* h, double* ms, int32_t 
   const unsigned long long* t = st.t;
   const unsigned long long end = t[K6_STAMPS - 1];
   auto at = [&](int k) { return k < K6_STAMPS - 1 && t[k] ? t[k] : end; };
-  double v[6] = {0, 0, 0, 0, 0, 0};
+  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   v[0] = (double)(at(1) - t[0]) * 1e-6;
   v[1] = (double)(at(2) - at(1)) * 1e-6;
   v[2] = (double)(at(3) - at(2)) * 1e-6;
+  // the direct waves (two barriers each), then the bucket waves
+  const int ndw = st.n_dwaves;
+  for (int dw = 0; dw < ndw; ++dw) {
+    const int b0 = 3 + 2 * dw;
+    v[6] += (double)(at(b0 + 1) - at(b0)) * 1e-6;
+    v[7] += (double)(at(b0 + 2) - at(b0 + 1)) * 1e-6;
+  }
+  const int base = 3 + 2 * ndw;
   const int nw = st.n_waves;
   if (nw == 0) {
-    v[3] = (double)(end - at(3)) * 1e-6;
+    v[3] = (double)(end - at(base)) * 1e-6;
   } else {
     for (int w = 0; w < nw; ++w) {
-      const int b0 = 3 + 2 * w;
+      const int b0 = base + 2 * w;
       v[3] += (double)(at(b0 + 1) - at(b0)) * 1e-6;
       v[4] += (double)((w + 1 < nw ? at(b0 + 2) : end) - at(b0 + 1)) * 1e-6;
     }
   }
   v[5] = (double)(end - t[0]) * 1e-6;
-  for (int i = 0; i < 6 && i < capacity; ++i) ms[i] = v[i];
+  for (int i = 0; i < 8 && i < capacity; ++i) ms[i] = v[i];
   if (waves) *waves = nw;
   return SPMSPV_OK;
 }

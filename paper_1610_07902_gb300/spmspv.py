@@ -308,12 +308,13 @@ def spmspv_run_batched(h, semiring, B, x_off, x_cnt, x_idx, x_val, masks, mask_s
 
 
 def spmspv_batched_phase_times(h):
-    """(ms[6], waves) of the last persistent batched launch: scan, plan, tile
-    starts, expand, merge, whole launch (device clock)."""
+    """(ms[8], waves) of the last persistent batched launch: scan, plan, tile
+    starts, expand, merge, whole launch, direct expand, direct compaction
+    (device clock)."""
     import numpy as np
-    ms = np.zeros(6, dtype=np.float64)
+    ms = np.zeros(8, dtype=np.float64)
     w = ctypes.c_int32(0)
-    _check(load().spmspv_batched_phase_times(h, ms.ctypes.data, 6, ctypes.byref(w)),
+    _check(load().spmspv_batched_phase_times(h, ms.ctypes.data, 8, ctypes.byref(w)),
            "spmspv_batched_phase_times")
     return ms, int(w.value)
 

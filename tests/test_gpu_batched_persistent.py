@@ -84,16 +84,22 @@ def mixed_fronts(n, B, seed, fmax):
 
 @pytest.mark.parametrize("sched", [0, 2, 4, 5])
 @pytest.mark.parametrize("masked", [False, True])
-def test_persistent_matches_oracle(lib, sched, masked):
+@pytest.mark.parametrize("buckets_only", [False, True])
+def test_persistent_matches_oracle(lib, sched, masked, buckets_only):
+    """(+,*) frontiers of at least m/2 products run in the direct form unless
+    SPMSPV_BUCKETS_ONLY is given; both are compared."""
     torch, S = lib
     A = synth.rmat(14, seed=4)
     Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val)
     fronts = mixed_fronts(A.n, 40, 11 + sched, 5000)
+    W = [int(np.diff(A.colptr)[f[0]].sum()) for f in fronts]
+    assert sum(w >= A.m // 2 for w in W) >= 5
     rng = np.random.default_rng(sched)
     masks = [(rng.random(A.m) < 0.3).astype(np.uint8) for _ in fronts] if masked else None
+    extra = S.SPMSPV_BUCKETS_ONLY if buckets_only else 0
     for semiring in (0, 1, 2):
-        run_and_check(torch, S, A, Ad, fronts, semiring, S.SPMSPV_LANES_PERSISTENT, S.SPMSPV_SCHED_OPT(sched),
-                      masks, label="sched %d" % sched)
+        run_and_check(torch, S, A, Ad, fronts, semiring, S.SPMSPV_LANES_PERSISTENT,
+                      S.SPMSPV_SCHED_OPT(sched) | extra, masks, label="sched %d" % sched)
     Ad.close()
 
 
@@ -112,10 +118,11 @@ def test_persistent_waves_and_repeats(lib):
     assert W > 3 * A.nnz  # several waves at the first launch
     waves = []
     for call in range(3):
-        run_and_check(torch, S, A, Ad, fronts, 0, S.SPMSPV_LANES_PERSISTENT, S.SPMSPV_SCHED_OPT(5),
-                      label="call %d" % call)
+        run_and_check(torch, S, A, Ad, fronts, 0, S.SPMSPV_LANES_PERSISTENT,
+                      S.SPMSPV_SCHED_OPT(5) | S.SPMSPV_BUCKETS_ONLY, label="call %d" % call)
         ms, w = S.spmspv_batched_phase_times(Ad.handle)
-        assert (ms >= 0).all() and abs(ms[:5].sum() - ms[5]) <= 1e-3 * ms[5] + 1e-3
+        parts = ms[[0, 1, 2, 3, 4, 6, 7]].sum()
+        assert (ms >= 0).all() and abs(parts - ms[5]) <= 1e-3 * ms[5] + 1e-3
         waves.append(w)
     assert waves[0] > 1 and waves[1] == 1 and waves[2] == 1, waves
     run_and_check(torch, S, A, Ad, fronts, 1, S.SPMSPV_LANES_PERSISTENT, S.SPMSPV_SCHED_OPT(1))
@@ -206,4 +213,31 @@ def test_persistent_autotuned_caches_schedule(lib):
         run_and_check(torch, S, A, Ad, fronts, 0, 0)
         lanes, sched, cached = S.spmspv_last_tuned(Ad.handle)
         assert lanes in (0, 4, 16) and 0 <= sched < 6 and cached == (call == 1)
+    Ad.close()
+
+
+def test_persistent_direct_form_waves_and_reuse(lib):
+    """Many frontiers in the direct form (more than one wave of accumulators
+    on a matrix of 2^20 rows, 32 per wave), mixed with bucketed and sorted
+    ones, twice in a row (the accumulators must be clean after a launch), and
+    with y capacities below nnz(y) in the direct form."""
+    torch, S = lib
+    A = synth.rmat(20, seed=9)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val)
+    deg = np.diff(A.colptr)
+    rng = np.random.default_rng(2)
+    fronts = []
+    for b in range(70):
+        k = [40000, 60000, 50000, 45000, 30, 2000, 1][b % 7]
+        fronts.append(synth.frontier(A.n, k, seed=700 + b))
+    W = [int(deg[f[0]].sum()) for f in fronts]
+    assert sum(w >= A.m // 2 for w in W) > 32
+    for call in range(2):
+        run_and_check(torch, S, A, Ad, fronts, 0, S.SPMSPV_LANES_PERSISTENT, S.SPMSPV_SCHED_OPT(5),
+                      label="call %d" % call)
+    cap = np.full(len(fronts), A.m, np.int32)
+    cap[0] = 5000
+    cap[3] = 17
+    run_and_check(torch, S, A, Ad, fronts, 0, S.SPMSPV_LANES_PERSISTENT, S.SPMSPV_SCHED_OPT(5), y_cap=cap)
+    run_and_check(torch, S, A, Ad, fronts[:6], 0, S.SPMSPV_LANES_PERSISTENT, S.SPMSPV_SCHED_OPT(2))
     Ad.close()
