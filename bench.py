@@ -821,7 +821,11 @@ def profile_case(args, S, dev):
       msbfs    multi-source BFS from 64 sources (batched lanes)
       batched  256 frontiers of log-uniform size in [1, 10^5] (R-MAT seed 4) as
                one persistent launch under schedule --sched
-      batched_lanes  the same batch on 16 lanes"""
+      batched_lanes  the same batch on 16 lanes
+      auto     (+,*) product under the learned schedule (the selector runs in the
+               work scan's last CTA), x of --nnz-x entries
+      masked_min  (select2nd, min) product of x of --nnz-x entries (x(j) = j)
+               under a complemented mask with half of the rows set"""
     import torch
     import synth
     stream = torch.cuda.current_stream(dev)
@@ -831,7 +835,7 @@ def profile_case(args, S, dev):
     elif case in ("batched", "batched_lanes"):
         A = synth.rmat(args.scale, EDGE_FACTOR, seed=4)
     else:
-        A = synth.rmat(args.scale, EDGE_FACTOR, seed=SEED, values=case in ("pull", "sortx"))
+        A = synth.rmat(args.scale, EDGE_FACTOR, seed=SEED, values=case in ("pull", "sortx", "auto"))
     extra = {}
     sym = S.SPMSPV_CSC_SYMMETRIC if case in ("pull", "sortx", "batched", "batched_lanes") else \
         S.SPMSPV_CSC_PATTERN_SYMMETRIC
@@ -839,7 +843,26 @@ def profile_case(args, S, dev):
     params = selector_params()
     if params is not None:
         S.spmspv_selector_set(Ad.handle, params)
-    if case in ("pull", "sortx"):
+    if case in ("auto", "masked_min"):
+        xi_, xv_ = synth.frontier(A.n, min(args.nnz_x, A.n), seed=1, stream=2)
+        xi = torch.from_numpy(xi_).to(dev)
+        cap = A.m
+        yi = torch.empty(cap, dtype=torch.int32, device=dev)
+        nz = torch.zeros(1, dtype=torch.int32, device=dev)
+        if case == "auto":
+            xv = torch.from_numpy(xv_).to(dev)
+            yv = torch.empty(cap, dtype=torch.float32, device=dev)
+            step = lambda: S.spmspv_run(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, xi, xv, xi_.size, None,
+                                        S.SPMSPV_SCHED_AUTO, yi, yv, cap, nz, stream)
+        else:
+            rng = np.random.default_rng(3)
+            bits = np.packbits((rng.random(A.m) < 0.5).astype(np.uint8), bitorder="little")
+            bits = np.concatenate([bits, np.zeros((-len(bits)) % 4, np.uint8)]).view(np.int32)
+            mask = torch.from_numpy(bits).to(dev)
+            yv = torch.empty(cap, dtype=torch.int32, device=dev)
+            step = lambda: S.spmspv_run(Ad.handle, S.SPMSPV_MIN_SELECT2ND_I32, xi, xi, xi_.size, mask,
+                                        S.SPMSPV_MASK_COMPLEMENT, yi, yv, cap, nz, stream)
+    elif case in ("pull", "sortx"):
         xi_, xv_ = synth.frontier(A.n, min(args.nnz_x, A.n), seed=1, stream=2)
         xi, xv = torch.from_numpy(xi_).to(dev), torch.from_numpy(xv_).to(dev)
         cap = A.m
@@ -962,7 +985,7 @@ def main():
                     help="skip the BFS (fixed vs learned) and batched measurements")
     ap.add_argument("--case", default=None,
                     choices=["pull", "sortx", "bfs", "bfs_auto", "grid_auto", "cc", "mis", "mcm", "msbfs", "batched",
-                             "batched_lanes"],
+                             "batched_lanes", "auto", "masked_min"],
                     help="run one kernel family only (for profiler captures)")
     ap.add_argument("--grid", type=int, default=64, help="grid side of --case grid_auto")
     ap.add_argument("--sched", type=int, default=5, help="push schedule of --case batched")
