@@ -80,7 +80,8 @@ typedef struct spmspv_handle spmspv_handle;
 /* ---- run options (spmspv_run opts) ---- */
 #define SPMSPV_MASK_COMPLEMENT 1u /* keep row i only where mask bit i is 0 */
 #define SPMSPV_SORTED_OUT 2u      /* y_idx ascending (see note below) */
-#define SPMSPV_SCHED_AUTO 4u      /* let the learned selector pick the schedule */
+#define SPMSPV_SCHED_AUTO 4u      /* let the learned selector pick the schedule (a call
+                                     without a mask stays push) */
 #define SPMSPV_SCHED_FORCE 8u     /* use schedule SPMSPV_SCHED_ID(opts) */
 #define SPMSPV_WITH_FEATURES 16u  /* also compute the selector features (spmspv_last_features)
                                      with a fixed schedule; costs a pass over the mask */

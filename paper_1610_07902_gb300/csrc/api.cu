@@ -228,7 +228,10 @@ int pull_available(const spmspv_handle* h, int sem);
 int run_auto(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_val, int f,
              const uint32_t* mask, int mask_comp, int32_t* y_idx, uint32_t* y_val, int32_t y_cap,
              int32_t* d_nnz_y, cudaStream_t s) {
-  const int can_pull = pull_available(h, sem);
+  // the selector is trained on masked, BFS-like calls; without a mask a pull
+  // reads every row of A (an R-MAT hub row of 10^5 entries in one thread), so
+  // an unmasked call stays push
+  const int can_pull = mask ? pull_available(h, sem) : 0;
   int k1_grid = (int)std::max<int64_t>(1, std::min<int64_t>(h->k1_grid_max, ((int64_t)f + K1_TILE - 1) / K1_TILE));
   if (mask) k1_grid = std::max(k1_grid, mask_pass_grid(h));
   prof_call_begin(h, s);

@@ -154,3 +154,28 @@ def test_selector_load_reads_the_weights_file(lib, tmp_path):
         S.spmspv_selector_load(Ad.handle, tmp_path / "missing.json")
     np.testing.assert_array_equal(S.spmspv_selector_get(Ad.handle), selector.load()[0])
     Ad.close()
+
+
+def test_unmasked_auto_call_stays_push(lib):
+    """Weights that rate every pull schedule fastest: a masked call pulls, an
+    unmasked one keeps to the push schedules (the network was never trained on
+    unmasked calls, whose pull would read every row), both exact."""
+    torch, S = lib
+    A = synth.rmat(13, seed=5)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
+    p = random_params(7)
+    p[mlp.O_B3 + 6:mlp.O_B3 + 12] = -100.0  # the pull schedules' output biases
+    S.spmspv_selector_set(Ad.handle, p)
+    from test_gpu_spmspv import _run
+    x_idx, xf = synth.frontier(A.n, 500, seed=3)
+    mask = (np.random.default_rng(4).random(A.m) < 0.5).astype(np.uint8)
+    for use_mask in (True, False):
+        yi, yv, k, st = _run(lib, A, Ad, 1, x_idx, x_idx.astype(np.int32), mask if use_mask else None, True,
+                             None, auto=True)
+        assert st == 0
+        ref = oracle.spmspv(A.m, A.colptr, A.rowidx, A.val, SEMIRING_TO_ORACLE[1], x_idx, x_idx.astype(np.int32),
+                            mask if use_mask else None, True)
+        compare(1, ref, yi, yv)
+        chosen = S.spmspv_last_schedule(Ad.handle)
+        assert (chosen >= 6) == use_mask, (use_mask, chosen)
+    Ad.close()
