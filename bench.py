@@ -717,8 +717,21 @@ def bench_batched(S, dev, stream, B=256):
             run()
         t_seq += _events_ms(run, stream, 1)
         same &= bool(torch.equal(lv1, lv[b * A.n:(b + 1) * A.n]) and torch.equal(pa1, pa[b * A.n:(b + 1) * A.n]))
+    # the two forms side by side with the default schedule: every level as one
+    # persistent launch over all sources, and 16 lanes
+    forms = {}
+    lv3 = torch.empty_like(lv)
+    pa3 = torch.empty_like(pa)
+    for name, ln in (("persistent", S.SPMSPV_LANES_PERSISTENT), ("lanes16", 16)):
+        f = lambda: S.spmspv_msbfs(Ap.handle, B, ds, lv3, pa3, None, 0, ln, stream)
+        f()
+        forms[name + "_ms"] = _events_ms(f, stream, 2)
+        forms[name + "_identical_results"] = bool(torch.equal(lv3, lv) and torch.equal(pa3, pa))
+    del lv3, pa3
     out["msbfs"] = {"batched_ms": t_ms, "sequential_ms": t_seq, "speedup": t_seq / t_ms,
-                    "tuned_lanes": tuned[0], "tuned_schedule": tuned[1], "identical_results": same}
+                    "tuned_lanes": tuned[0], "tuned_schedule": tuned[1],
+                    "form": "persistent" if tuned[0] == 0 else "lanes", "identical_results": same}
+    out["msbfs"].update(forms)
     params = selector_params()
     if params is not None:
         # the same searches with the learned schedule (push or pull per source
@@ -759,7 +772,13 @@ def bench_batched(S, dev, stream, B=256):
     out["acl"] = {"alpha": alpha, "eps": eps, "batched_ms": t_acl,
                   "sequential_ms_scaled": t_seq * B / nseq, "sequential_sample": nseq,
                   "speedup": t_seq * B / nseq / t_acl, "tuned_lanes": tuned[0],
-                  "tuned_schedule": tuned[1], "max_mass_error": mass, "max_l1_p_vs_single": l1}
+                  "tuned_schedule": tuned[1], "form": "persistent" if tuned[0] == 0 else "lanes",
+                  "max_mass_error": mass, "max_l1_p_vs_single": l1}
+    # the two forms side by side with the default schedule
+    for name, ln in (("persistent", S.SPMSPV_LANES_PERSISTENT), ("lanes16", 16)):
+        f = lambda: S.spmspv_acl(Ap.handle, B, ds, alpha, eps, 100000, p, r, None, ln, stream)
+        f()
+        out["acl"][name + "_ms"] = _events_ms(f, stream, 2)
     Ap.close()
     return out
 
@@ -818,7 +837,8 @@ def profile_case(args, S, dev):
       bfs_auto BFS under the learned schedule (persistent kernel + graph loop)
       grid_auto the same on the 3D grid of side --grid (persistent kernel)
       cc, mis, mcm   the graph algorithms (one graph loop each)
-      msbfs    multi-source BFS from 64 sources (batched lanes)
+      msbfs    multi-source BFS from 64 sources (8 batched lanes)
+      msbfs_persistent  the same, every level one persistent launch
       batched  256 frontiers of log-uniform size in [1, 10^5] (R-MAT seed 4) as
                one persistent launch under schedule --sched
       batched_lanes  the same batch on 16 lanes
@@ -910,12 +930,14 @@ def profile_case(args, S, dev):
         extra["products"] = int(sum(int(np.diff(A.colptr)[f[0]].sum()) for f in fronts))
         step = lambda: S.spmspv_run_batched(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, B, *bx, None, 0,
                                             S.SPMSPV_SCHED_OPT(args.sched), *by, yi, yv, nz, lanes, stream)
-    elif case == "msbfs":
+    elif case in ("msbfs", "msbfs_persistent"):
         B = 64
         srcs = torch.from_numpy(synth.sources(A.colptr, B, seed=5).astype(np.int32)).to(dev)
         lv = torch.empty(B * A.n, dtype=torch.int32, device=dev)
         pa = torch.empty_like(lv)
-        step = lambda: S.spmspv_msbfs(Ad.handle, B, srcs, lv, pa, None, S.SPMSPV_SCHED_OPT(5), 8, stream)
+        lanes = 8 if case == "msbfs" else S.SPMSPV_LANES_PERSISTENT
+        step = lambda: S.spmspv_msbfs(Ad.handle, B, srcs, lv, pa, None, S.SPMSPV_SCHED_OPT(args.sched), lanes,
+                                      stream)
     else:
         raise SystemExit("unknown case %s" % case)
     for _ in range(args.warmup):
@@ -984,11 +1006,12 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the BFS (fixed vs learned) and batched measurements")
     ap.add_argument("--case", default=None,
-                    choices=["pull", "sortx", "bfs", "bfs_auto", "grid_auto", "cc", "mis", "mcm", "msbfs", "batched",
+                    choices=["pull", "sortx", "bfs", "bfs_auto", "grid_auto", "cc", "mis", "mcm", "msbfs", "msbfs_persistent",
+                             "batched",
                              "batched_lanes", "auto", "masked_min"],
                     help="run one kernel family only (for profiler captures)")
     ap.add_argument("--grid", type=int, default=64, help="grid side of --case grid_auto")
-    ap.add_argument("--sched", type=int, default=5, help="push schedule of --case batched")
+    ap.add_argument("--sched", type=int, default=5, help="push schedule of --case batched / msbfs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

@@ -309,15 +309,23 @@ int spmspv_batched_phase_times(spmspv_handle* h, double* ms, int32_t capacity, i
  * device array) advanced together, one batched step per level.
  *   level, parent  device int32[B][n] out (row b = search from sources[b]).
  *   nlevels        device int32 out (may be NULL): levels of the deepest search.
- *   opts, lanes    as for spmspv_run_batched (schedule, 1..16 lanes, or 0 for
- *                  autotuned: the first call with a new B profile runs the whole
- *                  search under every candidate, timed, and caches the fastest).
- *                  SPMSPV_SCHED_AUTO (weights set, pattern-symmetric handle): the
- *                  learned schedule picks push or pull per source and level, as in
- *                  spmspv_bfs; levels and parents are the same either way.
- *                  It adds B*n/4 bytes of frontier bitmaps.
- * Allocates B*(4n + n/8) bytes of frontiers and visited bitmaps for the call;
- * synchronises the stream once per level to test for termination.
+ *   opts, lanes    as for spmspv_run_batched: a push schedule; 1..16 lanes;
+ *                  SPMSPV_LANES_PERSISTENT, every level one persistent launch
+ *                  over all sources (y_b = A x_b with x_b the frontier carrying
+ *                  its vertex ids, under the complement of visited_b; push only,
+ *                  SPMSPV_SCHED_AUTO is ignored); or 0 for autotuned: the first
+ *                  call with a new B profile runs the whole search under every
+ *                  candidate (lanes 2/4/8/16 and the persistent form, each with
+ *                  every push schedule), timed, and caches the fastest.
+ *                  SPMSPV_SCHED_AUTO with lanes (weights set, pattern-symmetric
+ *                  handle): the learned schedule picks push or pull per source
+ *                  and level, as in spmspv_bfs (lanes 0: only the lane count is
+ *                  tuned); levels and parents are the same either way.  It adds
+ *                  B*n/4 bytes of frontier bitmaps.
+ * Allocates B*(4n + n/8) bytes of frontiers and visited bitmaps for the call
+ * (the persistent form 8*B*n more: the level's product and its parents);
+ * synchronises the stream once per level to test for termination (the
+ * persistent form twice: its launch reads the frontier sizes first).
  */
 int spmspv_msbfs(spmspv_handle* h, int32_t B, const int32_t* sources, int32_t* level,
                  int32_t* parent, int32_t* nlevels, uint32_t opts, int32_t lanes,
@@ -398,10 +406,12 @@ int spmspv_mcm(spmspv_handle* h, int32_t* mate_r, int32_t* mate_c, int32_t* d_ca
  * Stops when every S is empty or after max_steps steps.  sum(p) + sum(r) stays 1.
  * 1 <= B <= 65535 and B*n < 2^31, else SPMSPV_ERR_UNSUPPORTED.
  *   p_out, r_out  device float[B][n] out.   steps_out  device int32 out (may be NULL).
- *   lanes   1..16 concurrent lanes with the handle's default schedule, or 0 for
- *           autotuned (as for spmspv_msbfs: whole runs timed per candidate).
+ *   lanes   1..16 concurrent lanes with the handle's default schedule,
+ *           SPMSPV_LANES_PERSISTENT (each step's products one persistent launch
+ *           over every seed), or 0 for autotuned (as for spmspv_msbfs: whole
+ *           runs timed per candidate, lanes and persistent form).
  * Allocates about 20 B*n bytes of work arrays for the call; synchronises the
- * stream once per step.
+ * stream once per step (the persistent form twice).
  */
 int spmspv_acl(spmspv_handle* h, int32_t B, const int32_t* seeds, float alpha, float eps,
                int32_t max_steps, float* p_out, float* r_out, int32_t* steps_out, int32_t lanes,
@@ -415,14 +425,16 @@ int spmspv_acl(spmspv_handle* h, int32_t B, const int32_t* seeds, float alpha, f
  * profiles share a key share one tuning.  spmspv_tune_key is pure host code.
  */
 uint64_t spmspv_tune_key(int kind, int semiring, int masked, int32_t B, int64_t total_nnz_x);
-/* What the handle's last lanes = 0 call ran with; from_cache = 1 when no
- * timing was needed.  SPMSPV_ERR_STATE before any such call. */
+/* What the handle's last lanes = 0 call ran with (lanes 0: the persistent
+ * form); from_cache = 1 when no timing was needed.  SPMSPV_ERR_STATE before
+ * any such call. */
 int spmspv_last_tuned(spmspv_handle* h, int32_t* lanes, int32_t* sched, int32_t* from_cache);
 /* Copy up to `capacity` cache entries out (host arrays, any may be NULL);
  * *count receives the number of entries.  ms is the timed run (NaN if set). */
 int spmspv_tune_entries(spmspv_handle* h, uint64_t* keys, int32_t* lanes, int32_t* sched,
                         float* ms, int32_t capacity, int32_t* count);
-/* Seed or override an entry (lanes 1..16, push schedule 0..5). */
+/* Seed or override an entry (lanes 1..16, or 0 for the persistent form;
+ * push schedule 0..5). */
 int spmspv_tune_set(spmspv_handle* h, uint64_t key, int32_t lanes, int32_t sched);
 int spmspv_tune_clear(spmspv_handle* h);
 

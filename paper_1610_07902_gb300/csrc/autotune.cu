@@ -57,7 +57,7 @@ uint64_t tune_key(int kind, int sem, int masked, int32_t B, int64_t total_f) {
 }
 
 int tune_and_run(spmspv_handle* h, uint64_t key, cudaStream_t s,
-                 const std::function<int(int32_t, uint32_t)>& run, int nsched, bool persistent) {
+                 const std::function<int(int32_t, uint32_t)>& run, int nsched, int forms) {
   TuneCache* tc = cache_of(h);
   for (const TuneEntry& t : tc->entries) {
     if (t.key != key) continue;
@@ -76,11 +76,13 @@ int tune_and_run(spmspv_handle* h, uint64_t key, cudaStream_t s,
   TuneEntry best{key, 0, -1, INFINITY};
   int rc = SPMSPV_OK;
   // candidates (lanes, schedule): the lanes form over every lane count and
-  // schedule, or the persistent form (lanes 0) over every schedule plus a few
-  // lanes configurations (frontiers on a matrix of many rows can favour them)
+  // schedule, the persistent form (lanes 0) over every schedule plus a few
+  // lanes configurations (frontiers on a matrix of many rows can favour
+  // them), or both lists whole
   std::vector<std::pair<int32_t, int>> cand;
-  if (persistent) {
+  if (forms != kTuneLanes)
     for (int sid = 0; sid < nsched; ++sid) cand.push_back({0, sid});
+  if (forms == kTunePersistent) {
     for (int32_t lanes : {4, 16})
       for (int sid : {2, 5})
         if (sid < nsched) cand.push_back({lanes, sid});

@@ -393,7 +393,7 @@ extern "C" int spmspv_run_batched(spmspv_handle* h, int semiring, int32_t B, con
       [&](int32_t ln, uint32_t so) {
         return ln == 0 ? persistent(base | so) : run_batched(h, semiring, false, B, v, base | so, ln, s);
       },
-      SPMSPV_NUM_SCHEDULES / 2, true);
+      SPMSPV_NUM_SCHEDULES / 2, kTunePersistent);
 }
 
 // ---------------------------------------------------------------------------
@@ -464,6 +464,26 @@ __global__ void k_msbfs_next(int32_t B, const int32_t* __restrict__ nnz, int32_t
   if ((threadIdx.x & 31) == 0) atomicAdd(total, t);
 }
 
+// The persistent form's level update: y_b of the batched product holds the
+// vertices source b reaches first at level L (the unvisited rows), each with
+// its smallest frontier neighbour as value; they get their level, parent and
+// visited bit, and y_b is the next frontier.
+__global__ void k_msbfs_apply(int32_t B, int32_t n, int32_t L, const int32_t* __restrict__ y_idx,
+                              const int32_t* __restrict__ y_par, const int32_t* __restrict__ nnz,
+                              int32_t* __restrict__ level, int32_t* __restrict__ parent,
+                              uint32_t* __restrict__ visited, int64_t vwords) {
+  const int32_t b = blockIdx.y;
+  if (b >= B) return;
+  const int32_t c = nnz[b];
+  const int64_t base = (int64_t)b * n;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < c; k += gridDim.x * blockDim.x) {
+    const int32_t v = y_idx[base + k];
+    level[base + v] = L;
+    parent[base + v] = y_par[base + k];
+    atomicOr(visited + (int64_t)b * vwords + (v >> 5), 1u << (v & 31));
+  }
+}
+
 }  // namespace
 }  // namespace spmspv
 
@@ -481,20 +501,32 @@ static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_
   const int64_t vwords = ((int64_t)n + 31) / 32;
   // the learned schedule (push or pull per source and level) needs the
   // selector's weights and a pattern-symmetric matrix
-  const bool learned = (opts & SPMSPV_SCHED_AUTO) && h->sel_w && h->sel_ready &&
+  // the persistent form (one launch per level over every source) runs push
+  // only; the lanes run the learned schedule when asked
+  const bool persistent = lanes == SPMSPV_LANES_PERSISTENT;
+  const bool learned = !persistent && (opts & SPMSPV_SCHED_AUTO) && h->sel_w && h->sel_ready &&
                        pull_available(h, kMinSelect2nd);
-  // per-source frontiers, visited bitmaps and batch arrays (freed on return)
-  int32_t *fronts = nullptr, *arr = nullptr;
+  // per-source frontiers, visited bitmaps and batch arrays (freed on return);
+  // the persistent form writes each level's product to a second frontier
+  // array with the parents beside it
+  int32_t *fronts = nullptr, *arr = nullptr, *fronts2 = nullptr, *ypar = nullptr;
   uint32_t *visited = nullptr, *fbs = nullptr;
   cudaError_t e = cudaMalloc(&fronts, sizeof(int32_t) * (size_t)B * n);
   if (e == cudaSuccess) e = cudaMalloc(&visited, sizeof(uint32_t) * (size_t)B * vwords);
   if (e == cudaSuccess) e = cudaMalloc(&arr, sizeof(int32_t) * ((size_t)B * 6 + 8));
   if (e == cudaSuccess && learned) e = cudaMalloc(&fbs, sizeof(uint32_t) * 2 * (size_t)B * vwords);
-  if (e != cudaSuccess) {
+  if (e == cudaSuccess && persistent) e = cudaMalloc(&fronts2, sizeof(int32_t) * (size_t)B * n);
+  if (e == cudaSuccess && persistent) e = cudaMalloc(&ypar, sizeof(int32_t) * (size_t)B * n);
+  auto release = [&]() {
     cudaFree(fronts);
     cudaFree(visited);
     cudaFree(arr);
     cudaFree(fbs);
+    cudaFree(fronts2);
+    cudaFree(ypar);
+  };
+  if (e != cudaSuccess) {
+    release();
     cudaGetLastError();
     return fail(SPMSPV_ERR_OOM, "multi-source BFS buffers: %s", cudaGetErrorString(e));
   }
@@ -540,7 +572,33 @@ static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_
   v.nvis = nvis;
   int32_t L = 0;
   rc = SPMSPV_OK;
-  if ((rc = ensure_batch_state(h, lanes)) == SPMSPV_OK) {
+  if (persistent) {
+    // level L: y_b = A x_b under the complement of visited_b, x_b = the
+    // frontier with its vertex ids as values, so y_b(i) is the smallest
+    // frontier neighbour of every vertex first reached at L
+    int32_t* cur = fronts;
+    int32_t* nxt = fronts2;
+    for (L = 1; L <= n; ++L) {
+      if ((rc = run_batched_k6(h, kMinSelect2nd, B, x_off, x_cnt, cur, (const uint32_t*)cur, visited, vwords,
+                               opts, y_off, y_cap, nxt, (uint32_t*)ypar, nnz, s, true)) != SPMSPV_OK)
+        break;
+      for (int32_t b0 = 0; b0 < B; b0 += 65535)
+        k_msbfs_apply<<<dim3(16, (unsigned)std::min<int32_t>(B - b0, 65535)), 256, 0, s>>>(
+            B - b0, n, L, nxt + (int64_t)b0 * n, ypar + (int64_t)b0 * n, nnz + b0, level + (int64_t)b0 * n,
+            parent + (int64_t)b0 * n, visited + (int64_t)b0 * vwords, vwords);
+      cudaMemsetAsync(misc + 1, 0, sizeof(int32_t), s);
+      k_msbfs_next<<<1, 1024, 0, s>>>(B, nnz, x_cnt, misc + 1, nullptr);
+      int32_t total = 0;
+      e = cudaMemcpyAsync(&total, misc + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        rc = cuda_fail(e, "multi-source BFS level");
+        break;
+      }
+      std::swap(cur, nxt);
+      if (total == 0) break;
+    }
+  } else if ((rc = ensure_batch_state(h, lanes)) == SPMSPV_OK) {
     for (L = 1; L <= n; ++L) {
       if ((rc = batch_set_level(h, L, s)) != SPMSPV_OK) break;
       if ((rc = run_batched(h, kMinSelect2nd, true, B, v, opts, lanes, s)) != SPMSPV_OK) break;
@@ -562,10 +620,7 @@ static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_
     if (e != cudaSuccess) rc = cuda_fail(e, "level count");
   }
   cudaStreamSynchronize(s);
-  cudaFree(fronts);
-  cudaFree(visited);
-  cudaFree(arr);
-  cudaFree(fbs);
+  release();
   return rc;
 }
 
@@ -726,7 +781,9 @@ static int acl_run(spmspv_handle* h, int32_t B, const int32_t* seeds, float alph
   }
   k_acl_init<<<h->sm_count * 4, 256, 0, s>>>((int64_t)bn, r_out, p_out);
   k_acl_seed<<<(B + 255) / 256, 256, 0, s>>>(B, n, seeds, h->A.colptr, eps, r_out, act0, cnt0, misc);
-  if ((rc = ensure_batch_state(h, lanes)) != SPMSPV_OK) {
+  // the persistent form: each step's products are one launch over every seed
+  const bool persistent = lanes == SPMSPV_LANES_PERSISTENT;
+  if (!persistent && (rc = ensure_batch_state(h, lanes)) != SPMSPV_OK) {
     release();
     return rc;
   }
@@ -750,7 +807,10 @@ static int acl_run(spmspv_handle* h, int32_t B, const int32_t* seeds, float alph
     v.y_idx = yi;
     v.y_val = (uint32_t*)yv;
     v.d_nnz_y = ny;
-    if ((rc = run_batched(h, kPlusTimes, false, B, v, opts, lanes, s)) != SPMSPV_OK) break;
+    rc = persistent ? run_batched_k6(h, kPlusTimes, B, x_off, cnt, act, (const uint32_t*)xv, nullptr, 0, opts,
+                                     x_off, y_cap, yi, (uint32_t*)yv, ny, s)
+                    : run_batched(h, kPlusTimes, false, B, v, opts, lanes, s);
+    if (rc != SPMSPV_OK) break;
     k_acl_add<<<g2, 256, 0, s>>>(B, n, yi, yv, ny, r_out);
     cudaMemsetAsync(ncnt, 0, sizeof(int32_t) * B, s);
     cudaMemsetAsync(misc + 1, 0, sizeof(int32_t), s);
@@ -780,15 +840,16 @@ static int acl_run(spmspv_handle* h, int32_t B, const int32_t* seeds, float alph
   return rc;
 }
 
-// lanes == 0: the autotuner picks lanes and schedule per (B) profile, timing
-// whole runs (each run starts from its sources/seeds again, so reruns are harmless).
+// lanes == 0: the autotuner picks the form (lanes, or the persistent form,
+// cached as lanes 0) and the schedule per (B) profile, timing whole runs (each
+// run starts from its sources/seeds again, so reruns are harmless).
 extern "C" int spmspv_msbfs(spmspv_handle* h, int32_t B, const int32_t* sources, int32_t* level,
                             int32_t* parent, int32_t* nlevels, uint32_t opts, int32_t lanes,
                             spmspv_stream_t stream) {
   if (lanes != 0) return msbfs_run(h, B, sources, level, parent, nlevels, opts, lanes, stream);
   int rc = check_handle(h);
   if (rc) return rc;
-  if (opts & SPMSPV_SCHED_AUTO)  // the learned schedule: only the lane count is tuned
+  if (opts & SPMSPV_SCHED_AUTO)  // the learned schedule (lanes only): the lane count is tuned
     return tune_and_run(h, tune_key(3, kMinSelect2nd, 1, B, 0), (cudaStream_t)stream,
                         [&](int32_t ln, uint32_t) {
                           return msbfs_run(h, B, sources, level, parent, nlevels, opts, ln, stream);
@@ -796,8 +857,10 @@ extern "C" int spmspv_msbfs(spmspv_handle* h, int32_t B, const int32_t* sources,
   const uint32_t base = opts & ~(uint32_t)(SPMSPV_SCHED_FORCE | SPMSPV_SCHED_AUTO | SPMSPV_SCHED_OPT(0xFFu));
   return tune_and_run(h, tune_key(1, kMinSelect2nd, 1, B, 0), (cudaStream_t)stream,
                       [&](int32_t ln, uint32_t so) {
-                        return msbfs_run(h, B, sources, level, parent, nlevels, base | so, ln, stream);
-                      });
+                        return msbfs_run(h, B, sources, level, parent, nlevels, base | so,
+                                         ln == 0 ? SPMSPV_LANES_PERSISTENT : ln, stream);
+                      },
+                      SPMSPV_NUM_SCHEDULES / 2, kTuneBoth);
 }
 
 extern "C" int spmspv_acl(spmspv_handle* h, int32_t B, const int32_t* seeds, float alpha, float eps,
@@ -809,6 +872,8 @@ extern "C" int spmspv_acl(spmspv_handle* h, int32_t B, const int32_t* seeds, flo
   if (rc) return rc;
   return tune_and_run(h, tune_key(2, kPlusTimes, 0, B, 0), (cudaStream_t)stream,
                       [&](int32_t ln, uint32_t so) {
-                        return acl_run(h, B, seeds, alpha, eps, max_steps, p_out, r_out, steps_out, so, ln, stream);
-                      });
+                        return acl_run(h, B, seeds, alpha, eps, max_steps, p_out, r_out, steps_out, so,
+                                       ln == 0 ? SPMSPV_LANES_PERSISTENT : ln, stream);
+                      },
+                      SPMSPV_NUM_SCHEDULES / 2, kTuneBoth);
 }

@@ -91,6 +91,7 @@ struct K6Args {
   const uint32_t* x_val;
   const uint32_t* masks;  // complemented masks, frontier b's at masks + b*mask_stride
   int64_t mask_stride;
+  int x_ids;              // (min, select2nd): every x value is below INT32_MAX (vertex ids)
   const int32_t* y_off;
   const int32_t* y_cap;
   int32_t* y_idx;
@@ -117,10 +118,11 @@ struct K6Args {
   int32_t tw;     // row stride of the tile offset table (tile slots of one wave)
   int32_t nw_cap;
   int32_t tiles_cap;
-  // direct form of the frontiers with at least direct_min products ((+,*) only)
+  // direct form of the frontiers with at least direct_min products ((+,*);
+  // (min, select2nd) with x_ids)
   int32_t direct_min;       // 0: no direct form
   int32_t dslots;           // accumulators: frontiers of one direct wave
-  float* dacc;              // [dslots][m] dense accumulators, -0.0 in every row between launches
+  uint32_t* dacc;           // [dslots][m] dense accumulators, the empty mark in every row between launches
   unsigned long long* dstat;  // [dslots][nrt] look-back words of the compaction
   int32_t nrt;              // compaction row tiles per accumulator
   int32_t* ld;              // [B] direct frontier ids in order
@@ -612,6 +614,7 @@ __device__ void k6_tile(const K6Args& a, int32_t k, int32_t slot, unsigned char*
   else
     k2_gather<SEM, IT, false>(a.rowidx_t, a.val, hbits, kbase, kx, IT, warp, lane, p0, np, a.nnz, rrow, rval);
   const uint32_t* mask = a.masks ? a.masks + (int64_t)b * a.mask_stride : nullptr;
+  const uint32_t masked = mask ? k2_mask_bits(mask, rrow, (uint32_t)a.m, (uint32_t)nhot, hrow) : 0u;
 #pragma unroll
   for (int i = 0; i < K2_IMAX; ++i) {
     rank[i] = -1;
@@ -624,14 +627,13 @@ __device__ void k6_tile(const K6Args& a, int32_t k, int32_t slot, unsigned char*
         continue;
       }
       // a hub row: summed in the tile, staged once below
-      const uint32_t hr = (uint32_t)hrow[hs];
-      if (mask && ((__ldg(mask + (hr >> 5)) >> (hr & 31)) & 1u)) continue;
+      if ((masked >> i) & 1u) continue;
       spa_apply<SEM>(hacc, hs, rval[i]);
       const uint32_t hb = 1u << (hs & 31);
       if (!(htb[hs >> 5] & hb)) atomicOr(&htb[hs >> 5], hb);
       continue;
     }
-    if (mask && ((__ldg(mask + (row >> 5)) >> (row & 31)) & 1u)) continue;
+    if ((masked >> i) & 1u) continue;
     rank[i] = atomicAdd(&hist[row >> lwb], 1);
   }
   __syncthreads();
@@ -696,12 +698,20 @@ __device__ void k6_tile(const K6Args& a, int32_t k, int32_t slot, unsigned char*
 }
 
 // ---------------------------------------------------------------------------
-// direct form: one tile of a frontier with many products ((+,*)): every
-// product added into the frontier's accumulator in global memory (L2), hub
-// rows summed in the tile first
+// direct form: one tile of a frontier with many products ((+,*), or
+// (min, select2nd) with vertex ids as x values): every product applied to
+// the frontier's accumulator in global memory (L2) with the semiring's add
+// (a float reduction or an integer minimum), hub rows combined in the tile
+// first
 // ---------------------------------------------------------------------------
-template <int IT>
-__device__ void k6_tile_direct(const K6Args& a, int32_t k, float* acc, unsigned char* smem) {
+template <int SEM>
+__device__ __forceinline__ void k6_acc_apply(uint32_t* acc, uint32_t r, uint32_t v) {
+  if (SEM == kPlusTimes) atomicAdd(reinterpret_cast<float*>(acc) + r, __uint_as_float(v));
+  else atomicMin(reinterpret_cast<int*>(acc) + r, (int)v);
+}
+
+template <int SEM, int IT>
+__device__ void k6_tile_direct(const K6Args& a, int32_t k, uint32_t* acc, unsigned char* smem) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int32_t q = IT * K6_THREADS;
   int32_t* kbase = (int32_t*)smem;
@@ -731,11 +741,11 @@ __device__ void k6_tile_direct(const K6Args& a, int32_t k, float* acc, unsigned 
   __syncthreads();
   uint32_t rrow[K2_IMAX], rval[K2_IMAX];
   if (np == q)
-    k2_gather<kPlusTimes, IT, true>(a.rowidx_t, a.val, hbits, kbase, kx, IT, warp, lane, p0, np, a.nnz, rrow, rval);
+    k2_gather<SEM, IT, true>(a.rowidx_t, a.val, hbits, kbase, kx, IT, warp, lane, p0, np, a.nnz, rrow, rval);
   else
-    k2_gather<kPlusTimes, IT, false>(a.rowidx_t, a.val, hbits, kbase, kx, IT, warp, lane, p0, np, a.nnz, rrow,
-                                     rval);
+    k2_gather<SEM, IT, false>(a.rowidx_t, a.val, hbits, kbase, kx, IT, warp, lane, p0, np, a.nnz, rrow, rval);
   const uint32_t* mask = a.masks ? a.masks + (int64_t)b * a.mask_stride : nullptr;
+  const uint32_t masked = mask ? k2_mask_bits(mask, rrow, (uint32_t)a.m, (uint32_t)nhot, hrow) : 0u;
 #pragma unroll
   for (int i = 0; i < K2_IMAX; ++i) {
     const uint32_t row = rrow[i];
@@ -746,22 +756,21 @@ __device__ void k6_tile_direct(const K6Args& a, int32_t k, float* acc, unsigned 
         atomicOr(a.status, ST_INDEX);
         continue;
       }
-      const uint32_t hr = (uint32_t)hrow[hs];
-      if (mask && ((__ldg(mask + (hr >> 5)) >> (hr & 31)) & 1u)) continue;
-      spa_apply<kPlusTimes>(hacc, hs, rval[i]);
+      if ((masked >> i) & 1u) continue;
+      spa_apply<SEM>(hacc, hs, rval[i]);
       const uint32_t hb = 1u << (hs & 31);
       if (!(htb[hs >> 5] & hb)) atomicOr(&htb[hs >> 5], hb);
       continue;
     }
-    if (mask && ((__ldg(mask + (row >> 5)) >> (row & 31)) & 1u)) continue;
-    atomicAdd(acc + row, __uint_as_float(rval[i]));
+    if ((masked >> i) & 1u) continue;
+    k6_acc_apply<SEM>(acc, row, rval[i]);
   }
   __syncthreads();
   for (int j = tid; j < QMAX / 32; j += K6_THREADS) hbits[j] = 0u;
   for (int hs = tid; hs < nhot; hs += K6_THREADS) {
     if ((htb[hs >> 5] >> (hs & 31)) & 1u) {
-      atomicAdd(acc + hrow[hs], __uint_as_float(hacc[hs]));
-      hacc[hs] = 0u;
+      k6_acc_apply<SEM>(acc, (uint32_t)hrow[hs], hacc[hs]);
+      hacc[hs] = sr_identity<SEM>();
     }
   }
   __syncthreads();
@@ -770,16 +779,18 @@ __device__ void k6_tile_direct(const K6Args& a, int32_t k, float* acc, unsigned 
 }
 
 // The direct form's compaction: row tile rt (K6_DROWS rows) of one
-// frontier's accumulator, its touched rows (not -0.0) to y_b in ascending
-// order, each reset to -0.0; the tile's offset in y_b from a look-back along
-// the frontier's row tiles.
+// frontier's accumulator, its touched rows (not the empty mark: -0.0 for
+// (+,*), INT32_MAX for (min, select2nd)) to y_b in ascending order, each
+// reset to the mark; the tile's offset in y_b from a look-back along the
+// frontier's row tiles.
 constexpr int K6_DSTEPS = 16;                           // 32-row words per warp and tile
 constexpr int K6_DROWS = K6_THREADS * K6_DSTEPS;        // rows per tile (8192)
 
+template <int SEM>
 __device__ void k6_dcompact(const K6Args& a, int32_t b, uint32_t* acc, unsigned long long* chain, int32_t rt,
                             K6Shared& sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr uint32_t kEmpty = 0x80000000u;  // -0.0f
+  const uint32_t kEmpty = spa_empty<SEM>();
   const int64_t r0 = (int64_t)rt * K6_DROWS + (int64_t)warp * (K6_DSTEPS * 32) + lane;
   uint32_t v[K6_DSTEPS], bits[K6_DSTEPS];
   int32_t cw = 0;
@@ -827,7 +838,9 @@ __device__ void k6_dcompact(const K6Args& a, int32_t b, uint32_t* acc, unsigned 
 // ---------------------------------------------------------------------------
 template <int SEM>
 __device__ void k6_merge(const K6Args& a, int32_t li, int r, int32_t wt0w, unsigned char* smem, K6Shared& sh) {
-  constexpr bool kDenseForm = SEM == kPlusTimes;
+  // dense SPA: (+,*) marks empty rows with -0.0; (min, select2nd) with
+  // INT32_MAX when the x values are vertex ids (no product can carry it)
+  const bool kDenseForm = SEM == kPlusTimes || (SEM == kMinSelect2nd && a.x_ids);
   constexpr int U = 4;  // units of 32 four-entry chunks a warp reads at once
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int lwb = a.lwb;
@@ -1083,9 +1096,10 @@ __global__ void __launch_bounds__(K6_THREADS, 2) k6_batched(K6Args a) {
   k6_tile_starts(a, n_large);
   if (!k6_barrier(a, ++epoch, sh)) return;
   k6_expand_setup<SEM>(a, k6_smem_raw);
-  if (SEM == kPlusTimes) {
+  if (SEM != kOrAnd) {
     // the direct frontiers, dslots at a time: every tile's products into the
-    // frontier's accumulator, then the accumulators compacted into y
+    // frontier's accumulator, then the accumulators compacted into y (none
+    // unless the host enabled the form)
     const int32_t n_direct = __ldcg(&a.st->n_direct);
     const int32_t n_dw = __ldcg(&a.st->n_dwaves);
     for (int dw = 0; dw < n_dw; ++dw) {
@@ -1103,7 +1117,7 @@ __global__ void __launch_bounds__(K6_THREADS, 2) k6_batched(K6Args a) {
         if (it >= (uint32_t)(t1 - t0)) break;
         const int32_t k = t0 + (int32_t)it;
         const int32_t slot = __ldcg(a.fdi + __ldcg(a.tf + k)) - d0;
-        k6_tile_direct<IT>(a, k, a.dacc + (int64_t)slot * a.m, k6_smem_raw);
+        k6_tile_direct<SEM, IT>(a, k, a.dacc + (int64_t)slot * a.m, k6_smem_raw);
       }
       if (!k6_barrier(a, ++epoch, sh)) return;
       // compaction tasks go tile-major: row tile rt of every frontier of the wave, then rt+1
@@ -1115,8 +1129,7 @@ __global__ void __launch_bounds__(K6_THREADS, 2) k6_batched(K6Args a) {
         if (g >= tasks) break;
         const int32_t slot = (int32_t)(g % (uint32_t)nd), rt = (int32_t)(g / (uint32_t)nd);
         const int32_t b = __ldcg(a.ld + d0 + slot);
-        k6_dcompact(a, b, reinterpret_cast<uint32_t*>(a.dacc + (int64_t)slot * a.m), a.dstat + (int64_t)slot * a.nrt,
-                    rt, sh);
+        k6_dcompact<SEM>(a, b, a.dacc + (int64_t)slot * a.m, a.dstat + (int64_t)slot * a.nrt, rt, sh);
       }
       if (!k6_barrier(a, ++epoch, sh)) return;
     }
@@ -1211,7 +1224,8 @@ struct K6Buffers {
   DevArr<uint32_t> bval;
   DevArr<int32_t> toff;
   DevArr<unsigned long long> bstat;
-  DevArr<float> dacc;               // direct accumulators, -0.0 in every row between launches
+  DevArr<uint32_t> dacc;            // direct accumulators, the mark dacc_empty in every row between launches
+  uint32_t dacc_empty = 0u;
   DevArr<unsigned long long> dstat;
   DevArr<int32_t> ld, fdi, dwt0;
   int32_t* h_pin = nullptr;       // pinned: x_cnt[B] | xp[B+1] | cp[B+1]
@@ -1301,7 +1315,7 @@ void release_k6(spmspv_handle* h) {
 int run_batched_k6(spmspv_handle* h, int sem, int32_t B, const int32_t* x_off, const int32_t* x_cnt,
                    const int32_t* x_idx, const uint32_t* x_val, const uint32_t* masks, int64_t mask_stride,
                    uint32_t opts, const int32_t* y_off, const int32_t* y_cap, int32_t* y_idx, uint32_t* y_val,
-                   int32_t* d_nnz_y, cudaStream_t s) {
+                   int32_t* d_nnz_y, cudaStream_t s, bool x_ids) {
   if (!h->k6) h->k6 = new K6Buffers();
   K6Buffers* kb = (K6Buffers*)h->k6;
   const Matrix& A = h->A;
@@ -1391,18 +1405,29 @@ int run_batched_k6(spmspv_handle* h, int sem, int32_t B, const int32_t* x_off, c
   // many per wave as accumulators fit in 128 MB (at most 32; measured on the
   // 256-frontier R-MAT s20 batch: 64 MB 1.116 ms, 128 MB 1.093 ms; a
   // threshold of m/4 or m instead of m/2: 1.102 / 1.159 ms)
-  const bool direct = sem == kPlusTimes && !(opts & SPMSPV_BUCKETS_ONLY) && A.m <= DIRECT_M_MAX;
+  // (min, select2nd) takes the direct form when the x values are vertex ids
+  // (INT32_MAX then marks an untouched row)
+  const bool direct = (sem == kPlusTimes || (sem == kMinSelect2nd && x_ids)) && !(opts & SPMSPV_BUCKETS_ONLY) &&
+                      A.m <= DIRECT_M_MAX;
   const int32_t dslots = direct ? (int32_t)std::max<int64_t>(1, std::min<int64_t>(32, ((int64_t)128 << 20) /
                                                                                    (4 * (int64_t)A.m)))
                                 : 1;
   const int32_t nrt = (int32_t)(((int64_t)A.m + K6_DROWS - 1) / K6_DROWS);
   const int64_t dw_cap = (int64_t)B + 2;
-  if (direct && kb->dacc.cap < (size_t)dslots * A.m) {  // new accumulators start at -0.0 in every row
-    if ((e = kb->dacc.grow((size_t)dslots * A.m)) != cudaSuccess ||
-        (e = launch_fill_u32(reinterpret_cast<uint32_t*>(kb->dacc.p), (int64_t)kb->dacc.cap, 0x80000000u, s)) !=
-            cudaSuccess) {
+  if (direct) {
+    // every row of the accumulators holds the semiring's empty mark between
+    // launches (the compaction restores it): new accumulators, and those
+    // last used by the other semiring, are filled first
+    const uint32_t empty = sem == kPlusTimes ? 0x80000000u : 0x7fffffffu;
+    const bool grown = kb->dacc.cap < (size_t)dslots * A.m;
+    if (grown && (e = kb->dacc.grow((size_t)dslots * A.m)) != cudaSuccess) {
       cudaGetLastError();
       return fail(SPMSPV_ERR_OOM, "batched accumulators: %s", cudaGetErrorString(e));
+    }
+    if (grown || kb->dacc_empty != empty) {
+      if ((e = launch_fill_u32(kb->dacc.p, (int64_t)kb->dacc.cap, empty, s)) != cudaSuccess)
+        return cuda_fail(e, "batched accumulators");
+      kb->dacc_empty = empty;
     }
   }
   if ((e = kb->dstat.grow((size_t)dslots * nrt)) != cudaSuccess || (e = kb->ld.grow((size_t)B)) != cudaSuccess ||
@@ -1440,6 +1465,7 @@ int run_batched_k6(spmspv_handle* h, int sem, int32_t B, const int32_t* x_off, c
   a.x_val = x_val;
   a.masks = masks;
   a.mask_stride = mask_stride;
+  a.x_ids = x_ids && sem == kMinSelect2nd ? 1 : 0;
   a.y_off = y_off;
   a.y_cap = y_cap;
   a.y_idx = y_idx;

@@ -84,4 +84,23 @@ __device__ __forceinline__ void k2_gather(const int32_t* __restrict__ rowidx, co
   }
 }
 
+// The mask bit of every item's row (bit i of the result for item i; hub
+// labels m + h read the bit of hrow[h]; items without a product read
+// nothing), with every item's load issued before any result is used.
+__device__ __forceinline__ uint32_t k2_mask_bits(const uint32_t* __restrict__ mask,
+                                                 const uint32_t (&rrow)[K2_IMAX], uint32_t m, uint32_t nhot,
+                                                 const int32_t* hrow) {
+  uint32_t w[K2_IMAX], r[K2_IMAX];
+#pragma unroll
+  for (int i = 0; i < K2_IMAX; ++i) {
+    r[i] = rrow[i];
+    if (r[i] != 0xffffffffu && r[i] >= m) r[i] = r[i] - m < nhot ? (uint32_t)hrow[r[i] - m] : 0xffffffffu;
+    w[i] = r[i] != 0xffffffffu ? __ldg(mask + (r[i] >> 5)) : 0u;
+  }
+  uint32_t bits = 0u;
+#pragma unroll
+  for (int i = 0; i < K2_IMAX; ++i) bits |= ((w[i] >> (r[i] & 31)) & 1u) << i;
+  return bits;
+}
+
 }  // namespace spmspv

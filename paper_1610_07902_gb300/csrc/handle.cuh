@@ -136,10 +136,12 @@ int graph_spmspv(spmspv_handle* h, int sem, const Sched& sc, const int32_t* x_id
                  int32_t* y_idx, uint32_t* y_val, cudaStream_t s);
 // The batched form as one persistent launch (batched_k6.cu); reads x_cnt on
 // the host first (one synchronisation of `s`).  masks are complemented.
+// x_ids: (min, select2nd) with every x value below INT32_MAX (vertex ids), so
+// the merge may mark empty rows with INT32_MAX.
 int run_batched_k6(spmspv_handle* h, int sem, int32_t B, const int32_t* x_off, const int32_t* x_cnt,
                    const int32_t* x_idx, const uint32_t* x_val, const uint32_t* masks, int64_t mask_stride,
                    uint32_t opts, const int32_t* y_off, const int32_t* y_cap, int32_t* y_idx, uint32_t* y_val,
-                   int32_t* d_nnz_y, cudaStream_t s);
+                   int32_t* d_nnz_y, cudaStream_t s, bool x_ids = false);
 // Reads and clears the status words of the batched lanes' workspaces (after
 // the caller has synchronised the stream); CUDA errors are returned in *e.
 uint32_t batch_collect_status(spmspv_handle* h, cudaError_t* e);
@@ -148,11 +150,12 @@ void release_tune(spmspv_handle* h);
 uint64_t tune_key(int kind, int sem, int masked, int32_t B, int64_t total_f);
 // Runs `run(lanes, schedule opts)` with the cached choice for `key`, or times
 // every candidate on `s` (each run twice, the second timed) and caches the best.
-// Candidates: lanes 2/4/8/16 x push schedules 0..nsched-1; with
-// persistent = true, the persistent form (lanes 0) x the schedules, and lanes
-// 4 and 16 x schedules 2 and 5.
+// Candidates by `forms`: kTuneLanes, lanes 2/4/8/16 x push schedules
+// 0..nsched-1; kTunePersistent, the persistent form (lanes 0) x the schedules
+// and lanes 4 and 16 x schedules 2 and 5; kTuneBoth, both full lists.
+enum { kTuneLanes = 0, kTunePersistent = 1, kTuneBoth = 2 };
 int tune_and_run(spmspv_handle* h, uint64_t key, cudaStream_t s,
-                 const std::function<int(int32_t, uint32_t)>& run, int nsched = 6, bool persistent = false);
+                 const std::function<int(int32_t, uint32_t)>& run, int nsched = 6, int forms = kTuneLanes);
 cudaError_t alloc_pull_buffers(spmspv_handle* h);
 int pull_available(const spmspv_handle* h, int sem);
 // BFS pull kernel of a batched lane (the lane's job names the source's arrays)

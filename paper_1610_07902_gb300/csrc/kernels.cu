@@ -593,6 +593,7 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
       k2_gather<SEM, IT, true>(rowidx, val, hbits, kbase, kx, items, warp, lane, p0, np, nnz, rrow, rval);
     else
       k2_gather<SEM, IT, false>(rowidx, val, hbits, kbase, kx, items, warp, lane, p0, np, nnz, rrow, rval);
+    const uint32_t mbits = (MASKED && mask) ? k2_mask_bits(mask, rrow, (uint32_t)m, (uint32_t)nhot, hrow) : 0u;
 #pragma unroll
     for (int i = 0; i < K2_IMAX; ++i) {
       rank[i] = -1;
@@ -604,8 +605,7 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
       }
       bool keep = true;
       if (MASKED && mask) {
-        const uint32_t r = b < nb ? row : (uint32_t)hrow[row - (uint32_t)m];
-        const uint32_t bit = (__ldg(mask + (r >> 5)) >> (r & 31)) & 1u;
+        const uint32_t bit = (mbits >> i) & 1u;
         keep = mask_comp ? (bit == 0u) : (bit != 0u);
       }
       if (keep) rank[i] = atomicAdd(&hist[b], 1);

@@ -1,4 +1,5 @@
-"""Andersen-Chung-Lang push on the batched lanes against the FP64 reference.
+"""Andersen-Chung-Lang push (batched lanes and the persistent form) against the
+FP64 reference.
 
 The pushing sets are decided in FP32 on the device and in FP64 in the
 reference, so a vertex whose residual sits within rounding of eps*d(u) can
@@ -25,9 +26,11 @@ def lib():
     return torch, S
 
 
-@pytest.mark.parametrize("graph,lanes", [("rmat", 4), ("grid", 1), ("grid", 8)])
+@pytest.mark.parametrize("graph,lanes", [("rmat", 4), ("grid", 1), ("grid", 8), ("rmat", -1), ("grid", -1)])
 def test_acl_matches_reference(lib, graph, lanes):
+    # lanes -1: the persistent form (SPMSPV_LANES_PERSISTENT)
     torch, S = lib
+    assert S.SPMSPV_LANES_PERSISTENT == -1
     A = synth.rmat(11, seed=5, values=False) if graph == "rmat" else synth.grid3d(12, 12, 8, 0.2, values=False)
     Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, flags=S.SPMSPV_CSC_SYMMETRIC)
     seeds = synth.sources(A.colptr, 12, seed=6).astype(np.int32)

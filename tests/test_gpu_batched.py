@@ -68,7 +68,8 @@ def test_batched_matches_oracle(lib, lanes, masked):
     Ad.close()
 
 
-def test_multisource_bfs_matches_oracle(lib):
+@pytest.mark.parametrize("form", ["lanes", "persistent"])
+def test_multisource_bfs_matches_oracle(lib, form):
     torch, S = lib
     A = synth.rmat(12, seed=8)
     Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
@@ -77,7 +78,8 @@ def test_multisource_bfs_matches_oracle(lib):
     level = torch.empty(B * A.n, dtype=torch.int32, device="cuda")
     parent = torch.empty(B * A.n, dtype=torch.int32, device="cuda")
     nl = torch.zeros(1, dtype=torch.int32, device="cuda")
-    S.spmspv_msbfs(Ad.handle, B, torch.from_numpy(srcs).cuda(), level, parent, nl, 0, 4)
+    lanes = 4 if form == "lanes" else S.SPMSPV_LANES_PERSISTENT
+    S.spmspv_msbfs(Ad.handle, B, torch.from_numpy(srcs).cuda(), level, parent, nl, 0, lanes)
     lv = level.cpu().numpy().reshape(B, A.n)
     pa = parent.cpu().numpy().reshape(B, A.n)
     deepest = 0
@@ -87,6 +89,39 @@ def test_multisource_bfs_matches_oracle(lib):
         np.testing.assert_array_equal(pa[b], rp)
         deepest = max(deepest, rn)
     assert int(nl.item()) == deepest
+    assert S.spmspv_device_status(Ad.handle) == 0
+    Ad.close()
+
+
+@pytest.mark.parametrize("schedule", [0, 2, 5])
+def test_persistent_msbfs_grid_and_isolated_sources(lib, schedule):
+    # a high-diameter grid (searches of different depths: some frontiers empty
+    # while others run on), sources on isolated vertices (empty first
+    # frontier) and a repeated source, every search against the reference
+    torch, S = lib
+    A = synth.grid3d(24, 20, 6, 0.1, seed=3, values=False)
+    deg = np.diff(A.colptr)
+    isolated = np.flatnonzero(deg == 0)
+    srcs = synth.sources(A.colptr, 14, seed=11).astype(np.int32)
+    extra = [int(isolated[0])] if isolated.size else []
+    srcs = np.concatenate([srcs, np.array(extra + [int(srcs[0]), 0, A.n - 1], np.int32)])
+    B = srcs.shape[0]
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, flags=S.SPMSPV_CSC_SYMMETRIC)
+    level = torch.empty(B * A.n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(B * A.n, dtype=torch.int32, device="cuda")
+    nl = torch.zeros(1, dtype=torch.int32, device="cuda")
+    S.spmspv_msbfs(Ad.handle, B, torch.from_numpy(srcs).cuda(), level, parent, nl,
+                   S.SPMSPV_SCHED_OPT(schedule), S.SPMSPV_LANES_PERSISTENT)
+    lv = level.cpu().numpy().reshape(B, A.n)
+    pa = parent.cpu().numpy().reshape(B, A.n)
+    deepest = 0
+    for b in range(B):
+        rl, rp, rn, _, _ = oracle.bfs(A.colptr, A.rowidx, int(srcs[b]))
+        np.testing.assert_array_equal(lv[b], rl, err_msg="levels of source %d" % b)
+        np.testing.assert_array_equal(pa[b], rp, err_msg="parents of source %d" % b)
+        deepest = max(deepest, rn)
+    assert deepest > 20 and int(nl.item()) == deepest
+    assert S.spmspv_device_status(Ad.handle) == 0
     Ad.close()
 
 
@@ -152,7 +187,7 @@ def test_autotuned_msbfs_and_acl_match_fixed(lib):
     r = torch.empty(B * A.n, dtype=torch.float32, device="cuda")
     S.spmspv_acl(Ad.handle, B, srcs, 0.15, 1e-5, 1000, p, r, None, 0)
     lanes, sched, cached = S.spmspv_last_tuned(Ad.handle)
-    assert not cached and 2 <= lanes <= 16
+    assert not cached and lanes in (0, 2, 4, 8, 16)  # 0: the persistent form
     P = p.cpu().numpy().reshape(B, A.n).astype(np.float64)
     R = r.cpu().numpy().reshape(B, A.n).astype(np.float64)
     assert np.abs(P.sum(1) + R.sum(1) - 1).max() < 1e-5

@@ -241,3 +241,33 @@ def test_persistent_direct_form_waves_and_reuse(lib):
     run_and_check(torch, S, A, Ad, fronts, 0, S.SPMSPV_LANES_PERSISTENT, S.SPMSPV_SCHED_OPT(5), y_cap=cap)
     run_and_check(torch, S, A, Ad, fronts[:6], 0, S.SPMSPV_LANES_PERSISTENT, S.SPMSPV_SCHED_OPT(2))
     Ad.close()
+
+
+def test_persistent_msbfs_and_plus_share_accumulators(lib):
+    """The direct form's accumulators hold -0.0 in every row for (+,*) and
+    INT32_MAX for the multi-source BFS ((min, select2nd) with vertex ids):
+    alternating the two on one handle must leave both exact (every search
+    against the reference, more sources than one wave of accumulators)."""
+    torch, S = lib
+    A = synth.rmat(16, seed=13)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, A.val, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
+    deg = np.diff(A.colptr)
+    fronts = [synth.frontier(A.n, [9000, 12000, 40, 1][b % 4], seed=900 + b) for b in range(24)]
+    assert sum(int(deg[f[0]].sum()) >= A.m // 2 for f in fronts) >= 10
+    srcs = synth.sources(A.colptr, 40, seed=17).astype(np.int32)
+    B = srcs.shape[0]
+    refs = [oracle.bfs(A.colptr, A.rowidx, int(s))[:2] for s in srcs]
+    for rep in range(2):
+        run_and_check(torch, S, A, Ad, fronts, 0, S.SPMSPV_LANES_PERSISTENT, S.SPMSPV_SCHED_OPT(5),
+                      label="plus %d" % rep)
+        level = torch.empty(B * A.n, dtype=torch.int32, device="cuda")
+        parent = torch.empty(B * A.n, dtype=torch.int32, device="cuda")
+        S.spmspv_msbfs(Ad.handle, B, torch.from_numpy(srcs).cuda(), level, parent, None,
+                       S.SPMSPV_SCHED_OPT(2 + 3 * rep), S.SPMSPV_LANES_PERSISTENT)
+        lv = level.cpu().numpy().reshape(B, A.n)
+        pa = parent.cpu().numpy().reshape(B, A.n)
+        for b in range(B):
+            np.testing.assert_array_equal(lv[b], refs[b][0], err_msg="levels of source %d" % b)
+            np.testing.assert_array_equal(pa[b], refs[b][1], err_msg="parents of source %d" % b)
+        assert S.spmspv_device_status(Ad.handle) == 0
+    Ad.close()

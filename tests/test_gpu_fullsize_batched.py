@@ -1,10 +1,11 @@
 """The batched workloads at the size the benchmark times them (R-MAT s20, 256
 frontiers / sources / seeds, autotuned lanes and schedules as in the bench)
 against the reference: every one of the 256 batched products checked element
-by element; the multi-source BFS (fixed and learned schedule) from all 256
-sources level for level and parent for parent; ACL element by element on a
-sample of seeds (the reference is FP64 and the device decides its pushing sets
-in FP32), with the properties every seed must satisfy checked for all of them."""
+by element; the multi-source BFS (autotuned, learned schedule and the
+persistent form) from all 256 sources level for level and parent for parent;
+ACL element by element on a sample of seeds (the reference is FP64 and the
+device decides its pushing sets in FP32), with the properties every seed must
+satisfy checked for all of them."""
 import numpy as np
 import pytest
 
@@ -67,12 +68,20 @@ def pattern20(lib, rmat20):
     Ap.close()
 
 
-@pytest.mark.parametrize("learned", [False, True])
-def test_msbfs_full_size(lib, pattern20, learned):
+@pytest.fixture(scope="module")
+def bfs_refs20(pattern20):
+    from test_gpu_fullsize_bfs import oracle_bfs_all
+    A, _, srcs = pattern20
+    return oracle_bfs_all(A, srcs)
+
+
+@pytest.mark.parametrize("form", ["tuned", "learned", "persistent"])
+def test_msbfs_full_size(lib, pattern20, bfs_refs20, form):
     torch, S = lib
     A, Ap, srcs = pattern20
     opts = 0
-    if learned:
+    lanes = S.SPMSPV_LANES_PERSISTENT if form == "persistent" else 0
+    if form == "learned":
         from paper_1610_07902_gb300 import selector
         try:
             params = selector.load()[0]
@@ -82,14 +91,13 @@ def test_msbfs_full_size(lib, pattern20, learned):
         opts = S.SPMSPV_SCHED_AUTO
     lv = torch.empty(B * A.n, dtype=torch.int32, device="cuda")
     pa = torch.empty(B * A.n, dtype=torch.int32, device="cuda")
-    S.spmspv_msbfs(Ap.handle, B, torch.from_numpy(srcs).cuda(), lv, pa, None, opts, 0)
+    S.spmspv_msbfs(Ap.handle, B, torch.from_numpy(srcs).cuda(), lv, pa, None, opts, lanes)
     assert S.spmspv_device_status(Ap.handle) == 0
     L = lv.view(B, A.n)
     P = pa.view(B, A.n)
     # every source against the reference (levels are unique and the parent is
     # the smallest-id neighbour one level up, so both are compared bit for bit)
-    from test_gpu_fullsize_bfs import oracle_bfs_all
-    refs = oracle_bfs_all(A, srcs)
+    refs = bfs_refs20
     lv_h, pa_h = lv.cpu().numpy().reshape(B, A.n), pa.cpu().numpy().reshape(B, A.n)
     for b in range(B):
         rl, rp, _ = refs[b]
