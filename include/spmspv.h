@@ -312,16 +312,18 @@ int spmspv_batched_phase_times(spmspv_handle* h, double* ms, int32_t capacity, i
  *   opts, lanes    as for spmspv_run_batched: a push schedule; 1..16 lanes;
  *                  SPMSPV_LANES_PERSISTENT, every level one persistent launch
  *                  over all sources (y_b = A x_b with x_b the frontier carrying
- *                  its vertex ids, under the complement of visited_b; push only,
- *                  SPMSPV_SCHED_AUTO is ignored); or 0 for autotuned: the first
- *                  call with a new B profile runs the whole search under every
- *                  candidate (lanes 2/4/8/16 and the persistent form, each with
- *                  every push schedule), timed, and caches the fastest.
- *                  SPMSPV_SCHED_AUTO with lanes (weights set, pattern-symmetric
- *                  handle): the learned schedule picks push or pull per source
- *                  and level, as in spmspv_bfs (lanes 0: only the lane count is
- *                  tuned); levels and parents are the same either way.  It adds
- *                  B*n/4 bytes of frontier bitmaps.
+ *                  its vertex ids, under the complement of visited_b); or 0 for
+ *                  autotuned: the first call with a new B profile runs the whole
+ *                  search under every candidate (lanes 2/4/8/16 and the
+ *                  persistent form, each with every push schedule), timed, and
+ *                  caches the fastest.
+ *                  SPMSPV_SCHED_AUTO (weights set, pattern-symmetric handle):
+ *                  the learned schedule picks push or pull per source and level,
+ *                  as in spmspv_bfs (in the persistent form the sources that
+ *                  pull run in one batched pull kernel beside the push launch;
+ *                  lanes 0: only the form and lane count are tuned); levels and
+ *                  parents are the same either way.  It adds B*n/4 bytes of
+ *                  frontier bitmaps (the persistent form B*n/8).
  * Allocates B*(4n + n/8) bytes of frontiers and visited bitmaps for the call
  * (the persistent form 8*B*n more: the level's product and its parents);
  * synchronises the stream once per level to test for termination (the

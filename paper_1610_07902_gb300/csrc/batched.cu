@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "handle.cuh"
+#include "selector_dev.cuh"
 #include "spmspv_internal.cuh"
 
 namespace spmspv {
@@ -484,6 +485,152 @@ __global__ void k_msbfs_apply(int32_t B, int32_t n, int32_t L, const int32_t* __
   }
 }
 
+// The learned schedule of the persistent form, one CTA per source: the
+// level's features as a single call would compute them (frontier size,
+// products, entries with a non-empty column, the largest column, vertices
+// reached) through the network; a level of at most BFS_DIRECT_MAX products
+// stays push.  A pull choice keeps the source out of the batched product
+// (its push count is 0) and sets its frontier in its bitmap for k_msbfs_pull.
+__global__ void __launch_bounds__(256)
+k_msbfs_decide(int32_t B, int32_t n, int64_t nnz, const int32_t* __restrict__ colptr, const float* __restrict__ w,
+               const int32_t* __restrict__ fronts, const int32_t* __restrict__ x_cnt,
+               const int32_t* __restrict__ nvis, int32_t* __restrict__ xc_push, int32_t* __restrict__ dir,
+               int32_t* __restrict__ pcnt, uint32_t* __restrict__ fbits, int64_t vwords) {
+  __shared__ long long s_w[8];
+  __shared__ int32_t s_fc[8], s_md[8];
+  __shared__ int s_dir;
+  const int32_t b = blockIdx.x;
+  if (b >= B) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int32_t f = x_cnt[b];
+  const int32_t* x = fronts + (int64_t)b * n;
+  long long W = 0;
+  int32_t fc = 0, md = 0;
+  for (int32_t k = tid; k < f; k += 256) {
+    const int32_t j = x[k];
+    const int32_t d = colptr[j + 1] - colptr[j];
+    W += d;
+    fc += d > 0;
+    md = max(md, d);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    W += __shfl_xor_sync(0xffffffffu, W, o);
+    fc += __shfl_xor_sync(0xffffffffu, fc, o);
+    md = max(md, __shfl_xor_sync(0xffffffffu, md, o));
+  }
+  if (lane == 0) {
+    s_w[warp] = W;
+    s_fc[warp] = fc;
+    s_md[warp] = md;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    W = lane < 8 ? s_w[lane] : 0;
+    fc = lane < 8 ? s_fc[lane] : 0;
+    md = lane < 8 ? s_md[lane] : 0;
+    for (int o = 16; o > 0; o >>= 1) {  // every lane ends with the totals
+      W += __shfl_xor_sync(0xffffffffu, W, o);
+      fc += __shfl_xor_sync(0xffffffffu, fc, o);
+      md = max(md, __shfl_xor_sync(0xffffffffu, md, o));
+    }
+    int d = 0;
+    if (f > 0 && W > BFS_DIRECT_MAX) {  // warp-uniform
+      float xf[SEL_IN];
+      sel_features_of(f, (int32_t)min(W, (long long)INT32_MAX), fc, md, nvis[b], n, n, nnz, xf);
+      d = sel_pick_warp(w, xf, 1) >= SPMSPV_NUM_SCHEDULES / 2 ? 1 : 0;
+    }
+    if (lane == 0) s_dir = d;
+  }
+  __syncthreads();
+  const int d = s_dir;
+  if (tid == 0) {
+    dir[b] = d;
+    xc_push[b] = d ? 0 : f;
+    pcnt[b] = 0;
+  }
+  if (d) {
+    uint32_t* fb = fbits + (int64_t)b * vwords;
+    for (int32_t k = tid; k < f; k += 256) atomicOr(fb + (x[k] >> 5), 1u << (x[k] & 31));
+  }
+}
+
+// A pull level of the persistent form for every source that chose pull
+// (Sec. II-B's matrix-driven form): a thread owns one 32-vertex word of the
+// source's visited bitmap, every unvisited vertex scans its neighbours (its
+// column: the pattern is symmetric) for members of the source's frontier
+// and takes the smallest (the first when row ids ascend in every column);
+// the vertices found get level, parent and visited bit and are appended to
+// the next frontier, whose order the next level does not depend on.
+__global__ void __launch_bounds__(256)
+k_msbfs_pull(int32_t B, int32_t n, int32_t L, const int32_t* __restrict__ colptr, const int32_t* __restrict__ rowidx,
+             int rows_sorted, const int32_t* __restrict__ dir, const uint32_t* __restrict__ fbits, int64_t vwords,
+             uint32_t* __restrict__ visited, int32_t* __restrict__ level, int32_t* __restrict__ parent,
+             int32_t* __restrict__ nxt, int32_t* __restrict__ pcnt) {
+  const int32_t b = blockIdx.y;
+  if (b >= B || !dir[b]) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t base = (int64_t)b * n;
+  const uint32_t* fb = fbits + (int64_t)b * vwords;
+  uint32_t* vis = visited + (int64_t)b * vwords;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < vwords; w0 += stride) {
+    const int64_t w = w0 + lane;
+    uint32_t allowed = 0u;
+    if (w < vwords) {
+      allowed = ~vis[w];
+      const int32_t r0 = (int32_t)(w * 32);
+      if (n - r0 < 32) allowed &= (1u << (n - r0)) - 1u;
+    }
+    uint32_t found = 0u;
+    while (allowed) {
+      const int k = __ffs(allowed) - 1;
+      allowed &= allowed - 1u;
+      const int32_t r = (int32_t)(w * 32) + k;
+      int32_t best = INT32_MAX;
+      for (int32_t p = colptr[r], p1 = colptr[r + 1]; p < p1; ++p) {
+        const int32_t j = rowidx[p];
+        if (!((fb[j >> 5] >> (j & 31)) & 1u)) continue;
+        best = min(best, j);
+        if (rows_sorted) break;
+      }
+      if (best != INT32_MAX) {
+        found |= 1u << k;
+        level[base + r] = L;
+        parent[base + r] = best;
+      }
+    }
+    if (found) vis[w] |= found;
+    // one reservation per warp, then the new vertices
+    const int32_t c = __popc(found);
+    int32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    int32_t pos = 0;
+    if (lane == 31 && incl > 0) pos = atomicAdd(pcnt + b, incl);
+    pos = __shfl_sync(0xffffffffu, pos, 31) + incl - c;
+    for (uint32_t bits = found; bits; bits &= bits - 1u) nxt[base + pos++] = (int32_t)(w * 32) + __ffs(bits) - 1;
+  }
+}
+
+// After a pull level: the source's frontier bitmap cleared (every word that
+// holds one of the old frontier's vertices) and its count of new vertices
+// moved to nnz.
+__global__ void k_msbfs_pull_done(int32_t B, int32_t n, const int32_t* __restrict__ dir,
+                                  const int32_t* __restrict__ fronts, const int32_t* __restrict__ x_cnt,
+                                  const int32_t* __restrict__ pcnt, uint32_t* __restrict__ fbits, int64_t vwords,
+                                  int32_t* __restrict__ nnz) {
+  const int32_t b = blockIdx.x;
+  if (b >= B || !dir[b]) return;
+  const int32_t f = x_cnt[b];
+  const int32_t* x = fronts + (int64_t)b * n;
+  uint32_t* fb = fbits + (int64_t)b * vwords;
+  for (int32_t k = threadIdx.x; k < f; k += blockDim.x) fb[x[k] >> 5] = 0u;
+  if (threadIdx.x == 0) nnz[b] = pcnt[b];
+}
+
 }  // namespace
 }  // namespace spmspv
 
@@ -501,10 +648,10 @@ static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_
   const int64_t vwords = ((int64_t)n + 31) / 32;
   // the learned schedule (push or pull per source and level) needs the
   // selector's weights and a pattern-symmetric matrix
-  // the persistent form (one launch per level over every source) runs push
-  // only; the lanes run the learned schedule when asked
+  // the learned schedule: push or pull per source and level (in the lanes,
+  // or around the persistent form's push launch)
   const bool persistent = lanes == SPMSPV_LANES_PERSISTENT;
-  const bool learned = !persistent && (opts & SPMSPV_SCHED_AUTO) && h->sel_w && h->sel_ready &&
+  const bool learned = (opts & SPMSPV_SCHED_AUTO) && h->sel_w && h->sel_ready &&
                        pull_available(h, kMinSelect2nd);
   // per-source frontiers, visited bitmaps and batch arrays (freed on return);
   // the persistent form writes each level's product to a second frontier
@@ -513,8 +660,11 @@ static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_
   uint32_t *visited = nullptr, *fbs = nullptr;
   cudaError_t e = cudaMalloc(&fronts, sizeof(int32_t) * (size_t)B * n);
   if (e == cudaSuccess) e = cudaMalloc(&visited, sizeof(uint32_t) * (size_t)B * vwords);
-  if (e == cudaSuccess) e = cudaMalloc(&arr, sizeof(int32_t) * ((size_t)B * 6 + 8));
-  if (e == cudaSuccess && learned) e = cudaMalloc(&fbs, sizeof(uint32_t) * 2 * (size_t)B * vwords);
+  if (e == cudaSuccess) e = cudaMalloc(&arr, sizeof(int32_t) * ((size_t)B * 9 + 8));
+  // frontier bitmaps of the learned schedule: two per source in the lanes
+  // (this level's and the next), one in the persistent form
+  const size_t fb_words = (persistent ? 1 : 2) * (size_t)B * vwords;
+  if (e == cudaSuccess && learned) e = cudaMalloc(&fbs, sizeof(uint32_t) * fb_words);
   if (e == cudaSuccess && persistent) e = cudaMalloc(&fronts2, sizeof(int32_t) * (size_t)B * n);
   if (e == cudaSuccess && persistent) e = cudaMalloc(&ypar, sizeof(int32_t) * (size_t)B * n);
   auto release = [&]() {
@@ -536,14 +686,19 @@ static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_
   int32_t* y_cap = arr + 3 * B;
   int32_t* nnz = arr + 4 * B;
   int32_t* nvis = learned ? arr + 5 * B : nullptr;
-  int32_t* misc = arr + 6 * B;  // [0] status, [1] frontier total
+  int32_t* xc_push = arr + 6 * B;  // persistent + learned: push counts, direction, pull counts
+  int32_t* dir = arr + 7 * B;
+  int32_t* pcnt = arr + 8 * B;
+  int32_t* misc = arr + 9 * B;  // [0] status, [1] frontier total
   // frontier b lives at fronts + b*n: express the offsets relative to fronts
   cudaMemsetAsync(misc, 0, sizeof(int32_t) * 8, s);
   const int grid = h->sm_count * 4;
+  uint32_t* fb_lanes = persistent ? nullptr : fbs;
+  if (persistent && fbs) cudaMemsetAsync(fbs, 0, sizeof(uint32_t) * fb_words, s);
   k_msbfs_init<<<grid, 256, 0, s>>>(B, n, sources, level, parent, visited, vwords, fronts, x_off,
-                                    x_cnt, y_off, y_cap, fbs);
+                                    x_cnt, y_off, y_cap, fb_lanes);
   k_msbfs_seed<<<(B + 255) / 256, 256, 0, s>>>(B, n, sources, level, parent, visited, vwords, fronts,
-                                               x_off, x_cnt, y_off, y_cap, misc, fbs, nvis);
+                                               x_off, x_cnt, y_off, y_cap, misc, fb_lanes, nvis);
   // offsets: frontier b starts at b*n
   {
     std::vector<int32_t> off(B);
@@ -575,19 +730,39 @@ static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_
   if (persistent) {
     // level L: y_b = A x_b under the complement of visited_b, x_b = the
     // frontier with its vertex ids as values, so y_b(i) is the smallest
-    // frontier neighbour of every vertex first reached at L
+    // frontier neighbour of every vertex first reached at L; with the
+    // learned schedule the sources that chose pull leave the batched product
+    // to k_msbfs_pull
     int32_t* cur = fronts;
     int32_t* nxt = fronts2;
+    // pull: one 32-vertex word per thread, up to 64 CTAs per source (more
+    // when there are few sources)
+    const int64_t pull_cap = std::max<int64_t>(64, ((int64_t)h->sm_count * 8 + B - 1) / B);
+    const int pull_grid = (int)std::min<int64_t>((vwords + 255) / 256, pull_cap);
     for (L = 1; L <= n; ++L) {
-      if ((rc = run_batched_k6(h, kMinSelect2nd, B, x_off, x_cnt, cur, (const uint32_t*)cur, visited, vwords,
-                               opts, y_off, y_cap, nxt, (uint32_t*)ypar, nnz, s, true)) != SPMSPV_OK)
+      for (int32_t b0 = 0; learned && b0 < B; b0 += 65535)
+        k_msbfs_decide<<<(unsigned)std::min<int32_t>(B - b0, 65535), 256, 0, s>>>(
+            B - b0, n, h->A.nnz, h->A.colptr, h->sel_w, cur + (int64_t)b0 * n, x_cnt + b0, nvis + b0,
+            xc_push + b0, dir + b0, pcnt + b0, fbs + (int64_t)b0 * vwords, vwords);
+      if ((rc = run_batched_k6(h, kMinSelect2nd, B, x_off, learned ? xc_push : x_cnt, cur, (const uint32_t*)cur,
+                               visited, vwords, opts, y_off, y_cap, nxt, (uint32_t*)ypar, nnz, s, true)) !=
+          SPMSPV_OK)
         break;
       for (int32_t b0 = 0; b0 < B; b0 += 65535)
         k_msbfs_apply<<<dim3(16, (unsigned)std::min<int32_t>(B - b0, 65535)), 256, 0, s>>>(
             B - b0, n, L, nxt + (int64_t)b0 * n, ypar + (int64_t)b0 * n, nnz + b0, level + (int64_t)b0 * n,
             parent + (int64_t)b0 * n, visited + (int64_t)b0 * vwords, vwords);
+      for (int32_t b0 = 0; learned && b0 < B; b0 += 65535) {
+        const unsigned gy = (unsigned)std::min<int32_t>(B - b0, 65535);
+        k_msbfs_pull<<<dim3(pull_grid, gy), 256, 0, s>>>(
+            B - b0, n, L, h->A.colptr, h->A.rowidx, h->rows_sorted, dir + b0, fbs + (int64_t)b0 * vwords, vwords,
+            visited + (int64_t)b0 * vwords, level + (int64_t)b0 * n, parent + (int64_t)b0 * n,
+            nxt + (int64_t)b0 * n, pcnt + b0);
+        k_msbfs_pull_done<<<gy, 256, 0, s>>>(B - b0, n, dir + b0, cur + (int64_t)b0 * n, x_cnt + b0, pcnt + b0,
+                                            fbs + (int64_t)b0 * vwords, vwords, nnz + b0);
+      }
       cudaMemsetAsync(misc + 1, 0, sizeof(int32_t), s);
-      k_msbfs_next<<<1, 1024, 0, s>>>(B, nnz, x_cnt, misc + 1, nullptr);
+      k_msbfs_next<<<1, 1024, 0, s>>>(B, nnz, x_cnt, misc + 1, nvis);
       int32_t total = 0;
       e = cudaMemcpyAsync(&total, misc + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -849,11 +1024,13 @@ extern "C" int spmspv_msbfs(spmspv_handle* h, int32_t B, const int32_t* sources,
   if (lanes != 0) return msbfs_run(h, B, sources, level, parent, nlevels, opts, lanes, stream);
   int rc = check_handle(h);
   if (rc) return rc;
-  if (opts & SPMSPV_SCHED_AUTO)  // the learned schedule (lanes only): the lane count is tuned
+  if (opts & SPMSPV_SCHED_AUTO)  // the learned schedule: the form (lanes or persistent) is tuned
     return tune_and_run(h, tune_key(3, kMinSelect2nd, 1, B, 0), (cudaStream_t)stream,
                         [&](int32_t ln, uint32_t) {
-                          return msbfs_run(h, B, sources, level, parent, nlevels, opts, ln, stream);
-                        }, 1);
+                          return msbfs_run(h, B, sources, level, parent, nlevels, opts,
+                                           ln == 0 ? SPMSPV_LANES_PERSISTENT : ln, stream);
+                        },
+                        1, kTuneBoth);
   const uint32_t base = opts & ~(uint32_t)(SPMSPV_SCHED_FORCE | SPMSPV_SCHED_AUTO | SPMSPV_SCHED_OPT(0xFFu));
   return tune_and_run(h, tune_key(1, kMinSelect2nd, 1, B, 0), (cudaStream_t)stream,
                       [&](int32_t ln, uint32_t so) {

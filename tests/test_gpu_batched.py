@@ -232,6 +232,45 @@ def test_learned_msbfs_matches_fixed(lib, bias):
     Ad.close()
 
 
+@pytest.mark.parametrize("bias", ["trained", "pull", "push"])
+def test_learned_persistent_msbfs_matches_oracle(lib, bias):
+    # the persistent form with the learned schedule: per source and level the
+    # network picks push (the batched launch) or pull (k_msbfs_pull); levels
+    # of more than 2^21 products may pull, so the graph has several such
+    # levels per search; forcing pull (or push) through the output biases
+    # exercises both paths, every search against the reference
+    torch, S = lib
+    from oracle import mlp
+    from paper_1610_07902_gb300 import selector
+    params, _ = selector.load()
+    params = params.copy()
+    if bias == "pull":
+        params[mlp.O_B3 + 6:mlp.O_B3 + 12] -= 1e4
+    elif bias == "push":
+        params[mlp.O_B3:mlp.O_B3 + 6] -= 1e4
+    A = synth.rmat(17, seed=23, values=False)
+    Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
+    S.spmspv_selector_set(Ad.handle, params)
+    srcs = synth.sources(A.colptr, 12, seed=8).astype(np.int32)
+    B = srcs.shape[0]
+    level = torch.empty(B * A.n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(B * A.n, dtype=torch.int32, device="cuda")
+    nl = torch.zeros(1, dtype=torch.int32, device="cuda")
+    S.spmspv_msbfs(Ad.handle, B, torch.from_numpy(srcs).cuda(), level, parent, nl, S.SPMSPV_SCHED_AUTO,
+                   S.SPMSPV_LANES_PERSISTENT)
+    lv = level.cpu().numpy().reshape(B, A.n)
+    pa = parent.cpu().numpy().reshape(B, A.n)
+    deepest = 0
+    for b in range(B):
+        rl, rp, rn, _, _ = oracle.bfs(A.colptr, A.rowidx, int(srcs[b]))
+        np.testing.assert_array_equal(lv[b], rl, err_msg="levels of source %d" % b)
+        np.testing.assert_array_equal(pa[b], rp, err_msg="parents of source %d" % b)
+        deepest = max(deepest, rn)
+    assert int(nl.item()) == deepest
+    assert S.spmspv_device_status(Ad.handle) == 0
+    Ad.close()
+
+
 def test_batched_edge_cases(lib):
     # empty frontiers among full ones, a single-frontier batch, and a frontier
     # whose y does not fit: it reports the size it needs, the others are exact
