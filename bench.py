@@ -839,6 +839,7 @@ def profile_case(args, S, dev):
       cc, mis, mcm   the graph algorithms (one graph loop each)
       msbfs    multi-source BFS from 64 sources (8 batched lanes)
       msbfs_persistent  the same, every level one persistent launch
+      msbfs_learned  the same under the learned schedule (push launch + batched pull)
       batched  256 frontiers of log-uniform size in [1, 10^5] (R-MAT seed 4) as
                one persistent launch under schedule --sched
       batched_lanes  the same batch on 16 lanes
@@ -930,14 +931,14 @@ def profile_case(args, S, dev):
         extra["products"] = int(sum(int(np.diff(A.colptr)[f[0]].sum()) for f in fronts))
         step = lambda: S.spmspv_run_batched(Ad.handle, S.SPMSPV_PLUS_TIMES_F32, B, *bx, None, 0,
                                             S.SPMSPV_SCHED_OPT(args.sched), *by, yi, yv, nz, lanes, stream)
-    elif case in ("msbfs", "msbfs_persistent"):
+    elif case in ("msbfs", "msbfs_persistent", "msbfs_learned"):
         B = 64
         srcs = torch.from_numpy(synth.sources(A.colptr, B, seed=5).astype(np.int32)).to(dev)
         lv = torch.empty(B * A.n, dtype=torch.int32, device=dev)
         pa = torch.empty_like(lv)
         lanes = 8 if case == "msbfs" else S.SPMSPV_LANES_PERSISTENT
-        step = lambda: S.spmspv_msbfs(Ad.handle, B, srcs, lv, pa, None, S.SPMSPV_SCHED_OPT(args.sched), lanes,
-                                      stream)
+        opts = S.SPMSPV_SCHED_AUTO if case == "msbfs_learned" else S.SPMSPV_SCHED_OPT(args.sched)
+        step = lambda: S.spmspv_msbfs(Ad.handle, B, srcs, lv, pa, None, opts, lanes, stream)
     else:
         raise SystemExit("unknown case %s" % case)
     for _ in range(args.warmup):
@@ -1007,7 +1008,7 @@ def main():
                     help="skip the BFS (fixed vs learned) and batched measurements")
     ap.add_argument("--case", default=None,
                     choices=["pull", "sortx", "bfs", "bfs_auto", "grid_auto", "cc", "mis", "mcm", "msbfs", "msbfs_persistent",
-                             "batched",
+                             "msbfs_learned", "batched",
                              "batched_lanes", "auto", "masked_min"],
                     help="run one kernel family only (for profiler captures)")
     ap.add_argument("--grid", type=int, default=64, help="grid side of --case grid_auto")

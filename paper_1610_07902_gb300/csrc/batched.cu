@@ -485,31 +485,28 @@ __global__ void k_msbfs_apply(int32_t B, int32_t n, int32_t L, const int32_t* __
   }
 }
 
-// The learned schedule of the persistent form, one CTA per source: the
-// level's features as a single call would compute them (frontier size,
-// products, entries with a non-empty column, the largest column, vertices
-// reached) through the network; a level of at most BFS_DIRECT_MAX products
-// stays push.  A pull choice keeps the source out of the batched product
-// (its push count is 0) and sets its frontier in its bitmap for k_msbfs_pull.
+// The learned schedule of the persistent form.  k_msbfs_stats gathers each
+// source's level features as a single call would compute them (products,
+// entries with a non-empty column, the largest column; several CTAs per
+// source), k_msbfs_decide (one warp per source) adds the frontier size and
+// the vertices reached, evaluates the network and clears the statistics for
+// the next level; a level of at most BFS_DIRECT_MAX products stays push.  A
+// pull choice keeps the source out of the batched product (its push count
+// is 0); k_msbfs_setbits sets its frontier in its bitmap for k_msbfs_pull.
 __global__ void __launch_bounds__(256)
-k_msbfs_decide(int32_t B, int32_t n, int64_t nnz, const int32_t* __restrict__ colptr, const float* __restrict__ w,
-               const int32_t* __restrict__ fronts, const int32_t* __restrict__ x_cnt,
-               const int32_t* __restrict__ nvis, int32_t* __restrict__ xc_push, int32_t* __restrict__ dir,
-               int32_t* __restrict__ pcnt, uint32_t* __restrict__ fbits, int64_t vwords) {
-  __shared__ long long s_w[8];
-  __shared__ int32_t s_fc[8], s_md[8];
-  __shared__ int s_dir;
-  const int32_t b = blockIdx.x;
+k_msbfs_stats(int32_t B, int32_t n, const int32_t* __restrict__ colptr, const int32_t* __restrict__ fronts,
+              const int32_t* __restrict__ x_cnt, unsigned long long* __restrict__ wsum, int32_t* __restrict__ fcnt,
+              int32_t* __restrict__ mdeg) {
+  const int32_t b = blockIdx.y;
   if (b >= B) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int32_t f = x_cnt[b];
   const int32_t* x = fronts + (int64_t)b * n;
-  long long W = 0;
+  unsigned long long W = 0;
   int32_t fc = 0, md = 0;
-  for (int32_t k = tid; k < f; k += 256) {
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < f; k += gridDim.x * blockDim.x) {
     const int32_t j = x[k];
     const int32_t d = colptr[j + 1] - colptr[j];
-    W += d;
+    W += (unsigned long long)d;
     fc += d > 0;
     md = max(md, d);
   }
@@ -518,40 +515,49 @@ k_msbfs_decide(int32_t B, int32_t n, int64_t nnz, const int32_t* __restrict__ co
     fc += __shfl_xor_sync(0xffffffffu, fc, o);
     md = max(md, __shfl_xor_sync(0xffffffffu, md, o));
   }
+  if ((threadIdx.x & 31) == 0 && W > 0) {
+    atomicAdd(wsum + b, W);
+    atomicAdd(fcnt + b, fc);
+    atomicMax(mdeg + b, md);
+  }
+}
+
+__global__ void k_msbfs_decide(int32_t B, int32_t n, int64_t nnz, const float* __restrict__ w,
+                               const int32_t* __restrict__ x_cnt, const int32_t* __restrict__ nvis,
+                               unsigned long long* __restrict__ wsum, int32_t* __restrict__ fcnt,
+                               int32_t* __restrict__ mdeg, int32_t* __restrict__ xc_push, int32_t* __restrict__ dir,
+                               int32_t* __restrict__ pcnt) {
+  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (b >= B) return;  // the whole warp
+  const int lane = threadIdx.x & 31;
+  const int32_t f = x_cnt[b];
+  const long long W = (long long)wsum[b];
+  int d = 0;
+  if (f > 0 && W > BFS_DIRECT_MAX) {
+    float xf[SEL_IN];
+    sel_features_of(f, (int32_t)min(W, (long long)INT32_MAX), fcnt[b], mdeg[b], nvis[b], n, n, nnz, xf);
+    d = sel_pick_warp(w, xf, 1) >= SPMSPV_NUM_SCHEDULES / 2 ? 1 : 0;
+  }
   if (lane == 0) {
-    s_w[warp] = W;
-    s_fc[warp] = fc;
-    s_md[warp] = md;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    W = lane < 8 ? s_w[lane] : 0;
-    fc = lane < 8 ? s_fc[lane] : 0;
-    md = lane < 8 ? s_md[lane] : 0;
-    for (int o = 16; o > 0; o >>= 1) {  // every lane ends with the totals
-      W += __shfl_xor_sync(0xffffffffu, W, o);
-      fc += __shfl_xor_sync(0xffffffffu, fc, o);
-      md = max(md, __shfl_xor_sync(0xffffffffu, md, o));
-    }
-    int d = 0;
-    if (f > 0 && W > BFS_DIRECT_MAX) {  // warp-uniform
-      float xf[SEL_IN];
-      sel_features_of(f, (int32_t)min(W, (long long)INT32_MAX), fc, md, nvis[b], n, n, nnz, xf);
-      d = sel_pick_warp(w, xf, 1) >= SPMSPV_NUM_SCHEDULES / 2 ? 1 : 0;
-    }
-    if (lane == 0) s_dir = d;
-  }
-  __syncthreads();
-  const int d = s_dir;
-  if (tid == 0) {
     dir[b] = d;
     xc_push[b] = d ? 0 : f;
     pcnt[b] = 0;
+    wsum[b] = 0ull;
+    fcnt[b] = 0;
+    mdeg[b] = 0;
   }
-  if (d) {
-    uint32_t* fb = fbits + (int64_t)b * vwords;
-    for (int32_t k = tid; k < f; k += 256) atomicOr(fb + (x[k] >> 5), 1u << (x[k] & 31));
-  }
+}
+
+__global__ void __launch_bounds__(256)
+k_msbfs_setbits(int32_t B, int32_t n, const int32_t* __restrict__ dir, const int32_t* __restrict__ fronts,
+                const int32_t* __restrict__ x_cnt, uint32_t* __restrict__ fbits, int64_t vwords) {
+  const int32_t b = blockIdx.y;
+  if (b >= B || !dir[b]) return;
+  const int32_t f = x_cnt[b];
+  const int32_t* x = fronts + (int64_t)b * n;
+  uint32_t* fb = fbits + (int64_t)b * vwords;
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < f; k += gridDim.x * blockDim.x)
+    atomicOr(fb + (x[k] >> 5), 1u << (x[k] & 31));
 }
 
 // A pull level of the persistent form for every source that chose pull
@@ -615,20 +621,17 @@ k_msbfs_pull(int32_t B, int32_t n, int32_t L, const int32_t* __restrict__ colptr
   }
 }
 
-// After a pull level: the source's frontier bitmap cleared (every word that
-// holds one of the old frontier's vertices) and its count of new vertices
-// moved to nnz.
-__global__ void k_msbfs_pull_done(int32_t B, int32_t n, const int32_t* __restrict__ dir,
-                                  const int32_t* __restrict__ fronts, const int32_t* __restrict__ x_cnt,
-                                  const int32_t* __restrict__ pcnt, uint32_t* __restrict__ fbits, int64_t vwords,
-                                  int32_t* __restrict__ nnz) {
-  const int32_t b = blockIdx.x;
+// After a pull level: the source's frontier bitmap cleared (all of it,
+// several CTAs per source) and its count of new vertices moved to nnz.
+__global__ void __launch_bounds__(256)
+k_msbfs_pull_done(int32_t B, const int32_t* __restrict__ dir, const int32_t* __restrict__ pcnt,
+                  uint32_t* __restrict__ fbits, int64_t vwords, int32_t* __restrict__ nnz) {
+  const int32_t b = blockIdx.y;
   if (b >= B || !dir[b]) return;
-  const int32_t f = x_cnt[b];
-  const int32_t* x = fronts + (int64_t)b * n;
   uint32_t* fb = fbits + (int64_t)b * vwords;
-  for (int32_t k = threadIdx.x; k < f; k += blockDim.x) fb[x[k] >> 5] = 0u;
-  if (threadIdx.x == 0) nnz[b] = pcnt[b];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vwords; i += (int64_t)gridDim.x * blockDim.x)
+    fb[i] = 0u;
+  if (blockIdx.x == 0 && threadIdx.x == 0) nnz[b] = pcnt[b];
 }
 
 }  // namespace
@@ -658,9 +661,11 @@ static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_
   // array with the parents beside it
   int32_t *fronts = nullptr, *arr = nullptr, *fronts2 = nullptr, *ypar = nullptr;
   uint32_t *visited = nullptr, *fbs = nullptr;
+  unsigned long long* wsum = nullptr;
   cudaError_t e = cudaMalloc(&fronts, sizeof(int32_t) * (size_t)B * n);
   if (e == cudaSuccess) e = cudaMalloc(&visited, sizeof(uint32_t) * (size_t)B * vwords);
-  if (e == cudaSuccess) e = cudaMalloc(&arr, sizeof(int32_t) * ((size_t)B * 9 + 8));
+  if (e == cudaSuccess) e = cudaMalloc(&arr, sizeof(int32_t) * ((size_t)B * 11 + 8));
+  if (e == cudaSuccess && persistent && learned) e = cudaMalloc(&wsum, sizeof(unsigned long long) * (size_t)B);
   // frontier bitmaps of the learned schedule: two per source in the lanes
   // (this level's and the next), one in the persistent form
   const size_t fb_words = (persistent ? 1 : 2) * (size_t)B * vwords;
@@ -674,6 +679,7 @@ static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_
     cudaFree(fbs);
     cudaFree(fronts2);
     cudaFree(ypar);
+    cudaFree(wsum);
   };
   if (e != cudaSuccess) {
     release();
@@ -689,12 +695,18 @@ static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_
   int32_t* xc_push = arr + 6 * B;  // persistent + learned: push counts, direction, pull counts
   int32_t* dir = arr + 7 * B;
   int32_t* pcnt = arr + 8 * B;
-  int32_t* misc = arr + 9 * B;  // [0] status, [1] frontier total
+  int32_t* fcnt = arr + 9 * B;  // persistent + learned: level statistics
+  int32_t* mdeg = arr + 10 * B;
+  int32_t* misc = arr + 11 * B;  // [0] status, [1] frontier total
   // frontier b lives at fronts + b*n: express the offsets relative to fronts
   cudaMemsetAsync(misc, 0, sizeof(int32_t) * 8, s);
   const int grid = h->sm_count * 4;
   uint32_t* fb_lanes = persistent ? nullptr : fbs;
   if (persistent && fbs) cudaMemsetAsync(fbs, 0, sizeof(uint32_t) * fb_words, s);
+  if (wsum) {
+    cudaMemsetAsync(wsum, 0, sizeof(unsigned long long) * B, s);
+    cudaMemsetAsync(fcnt, 0, sizeof(int32_t) * 2 * B, s);
+  }
   k_msbfs_init<<<grid, 256, 0, s>>>(B, n, sources, level, parent, visited, vwords, fronts, x_off,
                                     x_cnt, y_off, y_cap, fb_lanes);
   k_msbfs_seed<<<(B + 255) / 256, 256, 0, s>>>(B, n, sources, level, parent, visited, vwords, fronts,
@@ -739,11 +751,18 @@ static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_
     // when there are few sources)
     const int64_t pull_cap = std::max<int64_t>(64, ((int64_t)h->sm_count * 8 + B - 1) / B);
     const int pull_grid = (int)std::min<int64_t>((vwords + 255) / 256, pull_cap);
+    // the per-source helpers: enough CTAs per source for about 8 per SM
+    const int per_src = (int)std::max<int64_t>(1, std::min<int64_t>(256, ((int64_t)h->sm_count * 8 + B - 1) / B));
     for (L = 1; L <= n; ++L) {
-      for (int32_t b0 = 0; learned && b0 < B; b0 += 65535)
-        k_msbfs_decide<<<(unsigned)std::min<int32_t>(B - b0, 65535), 256, 0, s>>>(
-            B - b0, n, h->A.nnz, h->A.colptr, h->sel_w, cur + (int64_t)b0 * n, x_cnt + b0, nvis + b0,
-            xc_push + b0, dir + b0, pcnt + b0, fbs + (int64_t)b0 * vwords, vwords);
+      for (int32_t b0 = 0; learned && b0 < B; b0 += 65535) {
+        const int32_t bc = std::min<int32_t>(B - b0, 65535);
+        k_msbfs_stats<<<dim3(per_src, bc), 256, 0, s>>>(bc, n, h->A.colptr, cur + (int64_t)b0 * n, x_cnt + b0,
+                                                         wsum + b0, fcnt + b0, mdeg + b0);
+        k_msbfs_decide<<<(bc + 7) / 8, 256, 0, s>>>(bc, n, h->A.nnz, h->sel_w, x_cnt + b0, nvis + b0, wsum + b0,
+                                                    fcnt + b0, mdeg + b0, xc_push + b0, dir + b0, pcnt + b0);
+        k_msbfs_setbits<<<dim3(per_src, bc), 256, 0, s>>>(bc, n, dir + b0, cur + (int64_t)b0 * n, x_cnt + b0,
+                                                           fbs + (int64_t)b0 * vwords, vwords);
+      }
       if ((rc = run_batched_k6(h, kMinSelect2nd, B, x_off, learned ? xc_push : x_cnt, cur, (const uint32_t*)cur,
                                visited, vwords, opts, y_off, y_cap, nxt, (uint32_t*)ypar, nnz, s, true)) !=
           SPMSPV_OK)
@@ -758,8 +777,8 @@ static int msbfs_run(spmspv_handle* h, int32_t B, const int32_t* sources, int32_
             B - b0, n, L, h->A.colptr, h->A.rowidx, h->rows_sorted, dir + b0, fbs + (int64_t)b0 * vwords, vwords,
             visited + (int64_t)b0 * vwords, level + (int64_t)b0 * n, parent + (int64_t)b0 * n,
             nxt + (int64_t)b0 * n, pcnt + b0);
-        k_msbfs_pull_done<<<gy, 256, 0, s>>>(B - b0, n, dir + b0, cur + (int64_t)b0 * n, x_cnt + b0, pcnt + b0,
-                                            fbs + (int64_t)b0 * vwords, vwords, nnz + b0);
+        k_msbfs_pull_done<<<dim3(per_src, gy), 256, 0, s>>>(B - b0, dir + b0, pcnt + b0, fbs + (int64_t)b0 * vwords,
+                                                             vwords, nnz + b0);
       }
       cudaMemsetAsync(misc + 1, 0, sizeof(int32_t), s);
       k_msbfs_next<<<1, 1024, 0, s>>>(B, nnz, x_cnt, misc + 1, nvis);
