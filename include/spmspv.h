@@ -94,6 +94,11 @@ typedef struct spmspv_handle spmspv_handle;
                                        direction-optimizing rule of Beamer, Asanovic and
                                        Patterson (SC 2012; two fixed thresholds, alpha = 14,
                                        beta = 24), the baseline of the learned selector */
+#define SPMSPV_X_IDS 65536u          /* (min, select2nd): the caller states that every x value
+                                       equals its index (a BFS frontier); the pull direction
+                                       then stops at a row's first frontier neighbour when row
+                                       ids ascend in every column (the first is the smallest),
+                                       as the BFS loop does.  Other x values give undefined y */
 #define SPMSPV_SCHED_SHIFT 8
 #define SPMSPV_SCHED_OPT(s) (SPMSPV_SCHED_FORCE | ((uint32_t)(s) << SPMSPV_SCHED_SHIFT))
 #define SPMSPV_SCHED_ID(opts) (((opts) >> SPMSPV_SCHED_SHIFT) & 0xFFu)
@@ -205,6 +210,26 @@ int spmspv_destroy(spmspv_handle* h);
 int spmspv_run(spmspv_handle* h, int semiring, const int32_t* x_idx, const void* x_val,
                int32_t nnz_x, const uint32_t* mask, uint32_t opts, int32_t* y_idx,
                void* y_val, int32_t y_capacity, int32_t* d_nnz_y, spmspv_stream_t stream);
+
+/*
+ * The same product with x and y in HOST memory (the end-to-end form): x is
+ * copied to device buffers the handle keeps (grown on first use: 8 bytes per
+ * x entry and per y entry of capacity), the product runs on `stream` as in
+ * spmspv_run, nnz(y) is read back (one synchronisation), then the first
+ * min(nnz(y), y_capacity) entries of y are copied out and the stream is
+ * synchronised again: on return y and nnz(y) are in host memory.
+ *   x_idx, x_val          host arrays as for spmspv_run (page-locked memory
+ *                         gives full copy speed; pageable memory works).
+ *   mask                  DEVICE bitmap as for spmspv_run, or NULL.
+ *   y_idx, y_val          host arrays of y_capacity entries.
+ *   nnz_y                 host int32 out: nnz(y) (larger than y_capacity when
+ *                         y did not fit, with SPMSPV_DEV_CAPACITY set).
+ * Errors as for spmspv_run; calls of this kind on one handle must not
+ * overlap (they share the staging buffers).
+ */
+int spmspv_run_host(spmspv_handle* h, int semiring, const int32_t* x_idx, const void* x_val,
+                    int32_t nnz_x, const uint32_t* mask, uint32_t opts, int32_t* y_idx,
+                    void* y_val, int32_t y_capacity, int32_t* nnz_y, spmspv_stream_t stream);
 
 /*
  * Breadth-first search from `src` by repeated masked (min, select2nd) SpMSpV

@@ -227,7 +227,7 @@ int pull_available(const spmspv_handle* h, int sem);
 // if the selector chose its direction.
 int run_auto(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_val, int f,
              const uint32_t* mask, int mask_comp, int32_t* y_idx, uint32_t* y_val, int32_t y_cap,
-             int32_t* d_nnz_y, cudaStream_t s) {
+             int32_t* d_nnz_y, cudaStream_t s, int early_exit) {
   // the selector is trained on masked, BFS-like calls; without a mask a pull
   // reads every row of A (an R-MAT hub row of 10^5 entries in one thread), so
   // an unmasked call stays push
@@ -259,7 +259,7 @@ int run_auto(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_
   if (e != cudaSuccess) return cuda_fail(e, "bucket merge launch");
   prof_mark(h, SPMSPV_STAGE_MERGE, s);
   if (can_pull) {
-    e = launch_pull(h, sem, false, x_idx, x_val, f, nullptr, mask, mask_comp, 0, y_idx, y_val, y_cap,
+    e = launch_pull(h, sem, false, x_idx, x_val, f, nullptr, mask, mask_comp, early_exit, y_idx, y_val, y_cap,
                     d_nnz_y, nullptr, 1, s);
     if (e != cudaSuccess) return cuda_fail(e, "pull launch");
     prof_mark(h, SPMSPV_STAGE_PULL, s);
@@ -598,6 +598,7 @@ int spmspv_destroy(spmspv_handle* h) {
   release_mcm(h);
   release_sortx(h);
   release_tune(h);
+  release_hostio(h);
   release_extras(h);
   cudaFree(h->rowidx_k2);
   cudaFree(h->sel_w);
@@ -641,17 +642,20 @@ int spmspv_run(spmspv_handle* h, int semiring, const int32_t* x_idx, const void*
   }
   const int mask_comp = (opts & SPMSPV_MASK_COMPLEMENT) ? 1 : 0;
   h->plus_direct = (opts & SPMSPV_BUCKETS_ONLY) ? 0 : 1;
+  // x(j) = j (a BFS frontier) and ascending row ids: a pull row may stop at
+  // its first frontier neighbour, the smallest
+  const int early_exit = (opts & SPMSPV_X_IDS) && semiring == SPMSPV_MIN_SELECT2ND_I32 && h->rows_sorted ? 1 : 0;
   if (opts & SPMSPV_SCHED_AUTO) {
     if (!h->sel_ready) return fail(SPMSPV_ERR_STATE, "no selector weights loaded or trained");
     return run_auto(h, semiring, x_idx, (const uint32_t*)x_val, nnz_x, mask, mask_comp, y_idx,
-                    (uint32_t*)y_val, y_capacity, d_nnz_y, s);
+                    (uint32_t*)y_val, y_capacity, d_nnz_y, s, early_exit);
   }
   int sid = h->default_sched;
   if (opts & SPMSPV_SCHED_FORCE) sid = (int)SPMSPV_SCHED_ID(opts);
   Sched sc = decode_schedule(h, sid);
   if (sc.dir == 1) {
     rc = run_pull_if_available(h, semiring, x_idx, (const uint32_t*)x_val, nnz_x, mask, mask_comp,
-                               sc, y_idx, (uint32_t*)y_val, y_capacity, d_nnz_y, s);
+                               sc, y_idx, (uint32_t*)y_val, y_capacity, d_nnz_y, s, early_exit);
     if (rc != -1) return rc;
     sc.dir = 0;  // no row access to A: the push form of the same schedule
     sc.id = sc.id % 6;

@@ -44,6 +44,7 @@ struct spmspv_handle {
   void* batch;          // BatchState* of the batched lanes (batched.cu), lazily created
   void* k6;             // K6Buffers* of the persistent batched form (batched_k6.cu), lazily created
   void* tune;           // TuneCache* of the batched-form autotuner (autotune.cu), lazily created
+  void* hostio;         // HostIO* of spmspv_run_host (host_io.cu), lazily created
   // pull direction (dense frontier) buffers, allocated on first use
   uint32_t* xbits;      // [ceil(n/32)] frontier bitmap
   uint32_t* xdense;     // [n] frontier values
@@ -107,14 +108,17 @@ int run_push(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_
              int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y, bool bfs,
              uint32_t* mask_update, cudaStream_t s);
 // Returns -1 when the pull direction is not available for this handle/semiring.
+// early_exit: (min, select2nd) with x(j) = j and ascending row ids: a row
+// stops at its first frontier neighbour.
 int run_pull_if_available(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_val,
                           int f, const uint32_t* mask, int mask_comp, const Sched& sc,
                           int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y,
-                          cudaStream_t s);
+                          cudaStream_t s, int early_exit = 0);
 void release_extras(spmspv_handle* h);
 void release_bfs_graphs(spmspv_handle* h);
 void release_batch(spmspv_handle* h);
 void release_k6(spmspv_handle* h);
+void release_hostio(spmspv_handle* h);
 void release_cc(spmspv_handle* h);
 void release_mis(spmspv_handle* h);
 void release_mcm(spmspv_handle* h);

@@ -283,11 +283,11 @@ cudaError_t launch_pull_rows_lane(const spmspv_handle* sub, int early_exit, cuda
 int run_pull_if_available(spmspv_handle* h, int sem, const int32_t* x_idx, const uint32_t* x_val,
                           int f, const uint32_t* mask, int mask_comp, const Sched& sc,
                           int32_t* y_idx, uint32_t* y_val, int32_t y_cap, int32_t* d_nnz_y,
-                          cudaStream_t s) {
+                          cudaStream_t s, int early_exit) {
   (void)sc;
   if (!pull_available(h, sem)) return -1;
   prof_call_begin(h, s);
-  cudaError_t e = launch_pull(h, sem, false, x_idx, x_val, f, nullptr, mask, mask_comp, 0, y_idx,
+  cudaError_t e = launch_pull(h, sem, false, x_idx, x_val, f, nullptr, mask, mask_comp, early_exit, y_idx,
                               y_val, y_cap, d_nnz_y, nullptr, 0, s);
   if (e != cudaSuccess) return cuda_fail(e, "pull launch");
   prof_mark(h, SPMSPV_STAGE_PULL, s);

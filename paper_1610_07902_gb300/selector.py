@@ -76,13 +76,15 @@ def collect(Ad, A, sources, reps=3, max_levels=64, rng=None):
             for sched in range(12):
                 if sched >= 6 and not can_pull:
                     continue
-                opts = S.SPMSPV_MASK_COMPLEMENT | S.SPMSPV_SCHED_OPT(sched)
+                # x(j) = j: the pull stops at a row's first frontier neighbour,
+                # as inside the BFS loop the network's choices are used in
+                opts = S.SPMSPV_MASK_COMPLEMENT | S.SPMSPV_X_IDS | S.SPMSPV_SCHED_OPT(sched)
                 fn = lambda: S.spmspv_run(Ad.handle, S.SPMSPV_MIN_SELECT2ND_I32, xi, xi, front.size, mk,
                                           opts, y_idx, y_val, cap, nz)
                 fn()
                 row[sched] = time_call(fn, reps)
             S.spmspv_run(Ad.handle, S.SPMSPV_MIN_SELECT2ND_I32, xi, xi, front.size, mk,
-                         S.SPMSPV_MASK_COMPLEMENT | S.SPMSPV_WITH_FEATURES, y_idx, y_val, cap, nz)
+                         S.SPMSPV_MASK_COMPLEMENT | S.SPMSPV_X_IDS | S.SPMSPV_WITH_FEATURES, y_idx, y_val, cap, nz)
             feats.append(S.spmspv_last_features(Ad.handle))
             v = ~np.isnan(row)
             targ.append(np.where(v, np.log2(np.where(v, row, 1.0)), 0.0))
@@ -219,7 +221,8 @@ def evaluate(Ad, A, sources, params, reps=3, max_levels=48, rng=None):
             xi = torch.from_numpy(front).to(dev)
             mk = torch.from_numpy(bits.astype(np.uint32).view(np.int32)).to(dev)
             call = lambda o: (lambda: S.spmspv_run(Ad.handle, S.SPMSPV_MIN_SELECT2ND_I32, xi, xi,
-                                                   front.size, mk, S.SPMSPV_MASK_COMPLEMENT | o,
+                                                   front.size, mk,
+                                                   S.SPMSPV_MASK_COMPLEMENT | S.SPMSPV_X_IDS | o,
                                                    y_idx, y_val, cap, nz))
             t = np.full(12, np.inf)
             for sched in range(12):
@@ -322,6 +325,9 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--sources", type=int, default=2)
+    ap.add_argument("--rmat-sources", type=int, default=0,
+                    help="BFS sources per R-MAT training graph (default: --sources); an R-MAT search has a "
+                         "few levels, a grid search hundreds")
     ap.add_argument("--epochs", type=int, default=400)
     ap.add_argument("--evaluate", action="store_true",
                     help="evaluate --weights on the held-out graphs instead of training")
@@ -340,7 +346,8 @@ def main():
     last = None
     for (name, spec), (_, A) in zip(TRAINING_GRAPHS, training_graphs()):
         Ad = S.CscMatrix(A.m, A.n, A.colptr, A.rowidx, None, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
-        f, t, v = collect(Ad, A, synth.sources(A.colptr, args.sources, seed=5))
+        nsrc = args.rmat_sources if (spec[0] == "rmat" and args.rmat_sources) else args.sources
+        f, t, v = collect(Ad, A, synth.sources(A.colptr, nsrc, seed=5))
         fp, tp, vp = (collect_plain(make_graph(spec, values=True), count=args.plain_calls) if args.plain_calls
                       else (np.zeros((0, 6), np.float32), np.zeros((0, 12), np.float32), np.zeros((0, 12), np.uint8)))
         print("%-12s levels %4d, plain calls %3d  (%.0f s)" % (name, f.shape[0], fp.shape[0], time.time() - t0),
@@ -355,6 +362,7 @@ def main():
     losses = train(last, F, T, V, epochs=args.epochs)
     params = S.spmspv_selector_get(last.handle)
     save(params, args.out, {"samples": int(F.shape[0]), "final_loss": float(losses[-1]),
+                            "sources": args.sources, "rmat_sources": args.rmat_sources or args.sources,
                             "sample_kinds": ("BFS level replays and unmasked (+,*) calls" if args.plain_calls
                                              else "BFS level replays"),
                             "graphs": [g for g, _ in TRAINING_GRAPHS]})

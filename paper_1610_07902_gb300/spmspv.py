@@ -60,6 +60,7 @@ SPMSPV_DEV_BOUND = 8
 SPMSPV_SORT_X = 32
 SPMSPV_SCHED_RULE = 64
 SPMSPV_BUCKETS_ONLY = 128  # spmspv_run, (+,*): never the direct form
+SPMSPV_X_IDS = 65536  # (min, select2nd): x values equal their indices (the pull may stop early)
 SPMSPV_LANES_PERSISTENT = -1  # spmspv_run_batched: the persistent one-launch form
 
 
@@ -97,6 +98,8 @@ def load(build_if_missing: bool = True):
         lib.spmspv_destroy.argtypes = [_P]
         lib.spmspv_run.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_int32, _P, ctypes.c_uint32,
                                    _P, _P, ctypes.c_int32, _P, _P]
+        lib.spmspv_run_host.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_int32, _P, ctypes.c_uint32,
+                                        _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _P]
         lib.spmspv_device_status.argtypes = [_P, ctypes.POINTER(ctypes.c_uint32)]
         lib.spmspv_last_work.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
         lib.spmspv_run_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P,
@@ -296,6 +299,16 @@ def spmspv_selector_grad(h, feats, target, valid, n):
     _check(load().spmspv_selector_grad(h, _ptr(feats), _ptr(target), _ptr(valid), int(n),
                                        g.ctypes.data, loss.ctypes.data), "spmspv_selector_grad")
     return g, float(loss[0])
+
+
+def spmspv_run_host(h, semiring, x_idx, x_val, nnz_x, mask, opts, y_idx, y_val, y_capacity, stream=None):
+    """spmspv_run with x and y in host memory (CPU tensors, ideally pinned);
+    returns nnz(y).  mask stays a device bitmap."""
+    n = ctypes.c_int32(0)
+    _check(load().spmspv_run_host(h, int(semiring), _ptr(x_idx), _ptr(x_val), int(nnz_x), _ptr(mask), int(opts),
+                                  _ptr(y_idx), _ptr(y_val), int(y_capacity), ctypes.byref(n), _stream(stream)),
+           "spmspv_run_host")
+    return int(n.value)
 
 
 def spmspv_run_batched(h, semiring, B, x_off, x_cnt, x_idx, x_val, masks, mask_stride, opts,

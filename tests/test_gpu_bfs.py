@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import SEMIRING_TO_ORACLE, compare, need_gpu, x_values
+from gpu_util import SEMIRING_TO_ORACLE, compare, mask_bits, need_gpu, x_values
 
 pytestmark = pytest.mark.gpu
 
@@ -139,3 +139,35 @@ def test_pull_direction_all_semirings(lib, scale):
                     assert st == 0 and k == ref.idx.shape[0]
                     compare(semiring, ref, yi, yv)
     Ad.close()
+
+
+@pytest.mark.parametrize("scale", [11, 14])
+def test_pull_with_vertex_id_values_stops_early(lib, scale):
+    # SPMSPV_X_IDS: (min, select2nd) with x(j) = j lets the pull stop at a
+    # row's first frontier neighbour (the smallest, row ids ascending); the
+    # result must equal the reference under masks, pull schedules and the
+    # learned schedule, and a matrix whose columns are not sorted must still
+    # give the minimum (no early stop there)
+    torch, S = lib
+    from paper_1610_07902_gb300 import selector
+    A = synth.rmat(scale, seed=scale + 40, values=False)
+    rng = np.random.default_rng(scale)
+    perm_rows = A.rowidx.copy()
+    for j in range(A.n):  # the same pattern with every column's row ids reversed
+        a, b = A.colptr[j], A.colptr[j + 1]
+        perm_rows[a:b] = perm_rows[a:b][::-1]
+    for rows in (A.rowidx, perm_rows):
+        Ad = S.CscMatrix(A.m, A.n, A.colptr, rows, None, flags=S.SPMSPV_CSC_PATTERN_SYMMETRIC)
+        S.spmspv_selector_set(Ad.handle, selector.load()[0])
+        for f in [1, 300, A.n // 3, A.n]:
+            x_idx, _ = synth.frontier(A.n, f, seed=f)
+            mask = (rng.random(A.m) < 0.4).astype(np.uint8)
+            ref = oracle.spmspv(A.m, A.colptr, A.rowidx, None, oracle.MIN_SELECT2ND, x_idx, x_idx, mask, True)
+            xd = torch.from_numpy(x_idx).cuda()
+            md = torch.from_numpy(mask_bits(mask).view(np.int32)).cuda()
+            for opts in (S.SPMSPV_SCHED_OPT(6), S.SPMSPV_SCHED_OPT(11), S.SPMSPV_SCHED_AUTO):
+                yi, yv, k = Ad.multiply(1, xd, xd, md, opts | S.SPMSPV_MASK_COMPLEMENT | S.SPMSPV_X_IDS)
+                assert k == ref.idx.shape[0]
+                compare(1, ref, yi.cpu().numpy(), yv.cpu().numpy())
+        assert S.spmspv_device_status(Ad.handle) == 0
+        Ad.close()
