@@ -85,6 +85,8 @@ __global__ void __launch_bounds__(FB_THREADS, 2) k_bfs_fused(FusedArgs a) {
   __shared__ uint32_t s_x[FB_CH];        // its vertex id (the value select2nd passes on)
   __shared__ uint32_t s_hb[FB_QT / 32];  // entry starts inside a product tile
   __shared__ long long s_red[FB_WARPS];
+  __shared__ long long s_cw[FB_WARPS];   // per-warp counts of the next frontier
+  __shared__ int32_t s_cfc[FB_WARPS], s_cmd[FB_WARPS];
   __shared__ unsigned long long s_scan[FB_THREADS / 32 + 1];
   __shared__ int s_ok, s_efirst, s_nq;
   __shared__ int32_t s_S;
@@ -236,32 +238,58 @@ __global__ void __launch_bounds__(FB_THREADS, 2) k_bfs_fused(FusedArgs a) {
         const int32_t yv = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += yv;
       }
+      // the visited bits and the new vertices' column lengths (the next
+      // level's counts) are issued before the frontier slots are reserved,
+      // so their latency overlaps the reservation's
+      int32_t dnew[FB_IT];
+#pragma unroll
+      for (int i = 0; i < FB_IT; ++i) {
+        dnew[i] = 0;
+        if (!((found >> i) & 1u)) continue;
+        const uint32_t r = row[i];
+        atomicOr(a.visited + (r >> 5), 1u << (r & 31));
+        dnew[i] = __ldg(a.colptr + r + 1) - __ldg(a.colptr + r);
+      }
       int32_t base = 0;
       if (lane == 31 && incl > 0) base = atomicAdd(cnt, incl);
       base = __shfl_sync(0xffffffffu, base, 31) + incl - cf;
 #pragma unroll
       for (int i = 0; i < FB_IT; ++i) {
         if (!((found >> i) & 1u)) continue;
-        const uint32_t r = row[i];
-        y[base++] = (int32_t)r;
-        atomicOr(a.visited + (r >> 5), 1u << (r & 31));
-        const int32_t d = __ldg(a.colptr + r + 1) - __ldg(a.colptr + r);  // the next level's counts
-        nsum += d;
-        nfc += d > 0;
-        nmd = max(nmd, d);
+        y[base++] = (int32_t)row[i];
+        nsum += dnew[i];
+        nfc += dnew[i] > 0;
+        nmd = max(nmd, dnew[i]);
       }
       __syncthreads();
       for (int j = tid; j < FB_QT / 32; j += FB_THREADS) s_hb[j] = 0u;
       __syncthreads();
     }
-    // the next frontier's counts: one atomic of each kind per CTA
-    nsum = block_reduce(nsum, s_red, [](long long p, long long q) { return p + q; });
-    const long long nfcb = block_reduce((long long)nfc, s_red, [](long long p, long long q) { return p + q; });
-    const long long nmdb = block_reduce((long long)nmd, s_red, [](long long p, long long q) { return p > q ? p : q; });
+    // the next frontier's counts, reduced over the CTA in one pass: one
+    // atomic of each kind per CTA
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      nsum += __shfl_xor_sync(0xffffffffu, nsum, o);
+      nfc += __shfl_xor_sync(0xffffffffu, nfc, o);
+      nmd = max(nmd, __shfl_xor_sync(0xffffffffu, nmd, o));
+    }
+    if (lane == 0) {
+      s_cw[warp] = nsum;
+      s_cfc[warp] = nfc;
+      s_cmd[warp] = nmd;
+    }
+    __syncthreads();
     if (tid == 0) {
-      if (nsum) atomicAdd(reinterpret_cast<unsigned long long*>(&st->fused_w[Ln % 3]), (unsigned long long)nsum);
-      if (nfcb) atomicAdd(&st->fused_fc[Ln % 3], (int32_t)nfcb);
-      if (nmdb) atomicMax(&st->fused_md[Ln % 3], (int32_t)nmdb);
+      long long ws = 0;
+      int32_t fs = 0, ms = 0;
+      for (int i = 0; i < FB_WARPS; ++i) {
+        ws += s_cw[i];
+        fs += s_cfc[i];
+        ms = max(ms, s_cmd[i]);
+      }
+      if (ws) atomicAdd(reinterpret_cast<unsigned long long*>(&st->fused_w[Ln % 3]), (unsigned long long)ws);
+      if (fs) atomicAdd(&st->fused_fc[Ln % 3], fs);
+      if (ms) atomicMax(&st->fused_md[Ln % 3], ms);
     }
     if (!fused_barrier(st, ++epoch, &s_ok)) return;
     // ---- the next level: every CTA reads the same counts ----
