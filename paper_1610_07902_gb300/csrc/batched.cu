@@ -1,9 +1,11 @@
 // Batched SpMSpV, the lanes form: B independent products y_b <- A (+).(x) x_b
-// in one graph launch (the persistent one-launch form is batched_k6.cu; the
-// multi-source BFS and ACL run on the lanes).  The paper runs one product
-// per call; repeated small calls are where it notes most time goes to
-// overhead (Sec. I, Sec. III-A), so the batch is run as L concurrent "lanes":
-// each lane is a device-side WHILE
+// in one graph launch (the persistent one-launch form is batched_k6.cu), and
+// the multi-source BFS and ACL drivers, whose level / push steps run on
+// either form (this file holds their per-source kernels: the persistent
+// form's level update, learned push/pull decision and batched pull).  The
+// paper runs one product per call; repeated small calls are where it notes
+// most time goes to overhead (Sec. I, Sec. III-A), so the batch is run as L
+// concurrent "lanes": each lane is a device-side WHILE
 // loop (a conditional graph node) that pops the next frontier from a queue
 // shared by the lanes and runs the same three kernels (work scan ->
 // expand/scatter -> bucket merge) on it with its own workspace.  No frontier
