@@ -185,6 +185,7 @@ int spmspv_destroy(spmspv_handle* h);
  *               NULL for no mask.  Without SPMSPV_MASK_COMPLEMENT row i is kept
  *               only where its bit is 1; with it only where its bit is 0.
  *   opts        SPMSPV_MASK_COMPLEMENT | SPMSPV_SORTED_OUT | SPMSPV_SORT_X |
+ *               SPMSPV_BUCKETS_ONLY | SPMSPV_X_IDS | SPMSPV_WITH_FEATURES |
  *               schedule bits.  With SPMSPV_SORT_X, repeated or out-of-range x
  *               ids also set SPMSPV_DEV_INDEX.
  *   y_idx       device int32[y_capacity] out.
