@@ -58,6 +58,14 @@ __device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t epoch, ui
   return *s_ok != 0;
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may be scheduled before the kernel ahead of it on the stream
+// has finished; pdl_wait() returns once that kernel has completed and its
+// writes are visible (a no-op after a plain launch), pdl_launch_next() lets
+// the next such kernel be scheduled (a no-op when there is none).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Streaming load (evict-first): matrix entries are read once per call.
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
 __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }

@@ -63,6 +63,7 @@ k1_work_scan(const int32_t* x_idx, const uint32_t* x_val, int f_host, const int3
   __shared__ int s_maxdeg;
   __shared__ int s_maskcnt;
 
+  pdl_launch_next();  // the expand step may be scheduled now; it waits for this kernel
   DevState* st = ws.st;
   const int tid = threadIdx.x;
   const int bfs_mode = bfs_level_inc;  // a BFS level (single source or a batched lane's)
@@ -517,6 +518,8 @@ __global__ void __launch_bounds__(K2_THREADS, K2_MIN_BLOCKS)
 k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ val, Workspace ws,
                   int lwb_lo, int nb_fine, int32_t m, int64_t nnz, const uint32_t* mask,
                   int mask_comp, int only_push, int32_t direct_max, int32_t plus_direct_min) {
+  pdl_wait();         // the work scan's outputs are complete and visible
+  pdl_launch_next();  // the merge step may be scheduled now; it waits for this kernel
   if (only_push && ws.st->dir != 0) return;  // this call runs the pull direction
   if (ws.job) mask = ws.job->mask;
   extern __shared__ __align__(16) unsigned char k2_smem_raw[];
@@ -716,15 +719,48 @@ k2_expand_scatter(const int32_t* __restrict__ rowidx, const float* __restrict__ 
   }
 }
 
+// The expand and merge steps follow the step before them with programmatic
+// dependent launch when the stream is not being captured (graph loops keep
+// plain launches): their CTAs are scheduled while the step before drains
+// and wait in pdl_wait() for its results.
+static bool pdl_allowed(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs == cudaStreamCaptureStatusNone;
+}
+
+template <typename... KArgs, typename... Args>
+static void launch_after(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s, bool pdl,
+                         Args... args) {
+  if (!pdl) {
+    kernel<<<grid, block, smem, s>>>(args...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <int SEM>
 static void k2_variant(int it, bool masked, int grid, size_t smem, cudaStream_t s, const int32_t* rows,
                        const float* val, const Workspace& ws, int lwb_lo, int nb_fine, const Matrix& A,
                        const uint32_t* mask, int mask_comp, int only_push, int32_t direct_max,
                        int32_t plus_direct_min) {
-#define K2_GO(I, M)                                                                              \
-  k2_expand_scatter<SEM, I, M><<<grid, K2_THREADS, smem, s>>>(rows, val, ws, lwb_lo, nb_fine, A.m, \
-                                                              A.nnz, mask, mask_comp, only_push,  \
-                                                              direct_max, plus_direct_min)
+  const bool pdl = pdl_allowed(s);
+#define K2_GO(I, M)                                                                                       \
+  launch_after(k2_expand_scatter<SEM, I, M>, grid, K2_THREADS, smem, s, pdl, rows, val, ws, lwb_lo, nb_fine, \
+               A.m, A.nnz, mask, mask_comp, only_push, direct_max, plus_direct_min)
   constexpr int I1 = K2_IMAX, I2 = K2_IMAX / 2;
   if (masked) {
     if (it == I1) K2_GO(I1, true); else if (it == I2) K2_GO(I2, true); else K2_GO(0, true);
@@ -893,6 +929,7 @@ k3_bucket_merge(Workspace ws, int lwb_lo, int nb_fine, int32_t m, int32_t* y_idx
                 int32_t y_cap, int32_t* d_nnz_y, uint32_t* mask_update, int only_push,
                 int32_t direct_max, int use_cond, cudaGraphConditionalHandle cond,
                 int32_t plus_direct_min) {
+  pdl_wait();  // the expand step's outputs are complete and visible
   if (only_push && ws.st->dir != 0) return;  // this call runs the pull direction
   if (ws.job) {  // a batched lane: this frontier's outputs
     y_idx = ws.job->y_idx;
@@ -1149,16 +1186,17 @@ cudaError_t launch_k3(int sem, bool bfs, const Matrix& A, const Workspace& ws, i
                       int32_t direct_max, int use_cond, cudaGraphConditionalHandle cond,
                       int32_t plus_direct_min) {
   if (!ws.ydense || bfs || sem != kPlusTimes) plus_direct_min = 0;
+  const bool pdl = pdl_allowed(s);
 #define K3_ARGS ws, lwb_lo, nb_fine, A.m, y_idx, y_val, y_cap, d_nnz_y, mask_update, only_push, \
                 bfs ? direct_max : 0, bfs ? use_cond : 0, cond, plus_direct_min
   if (bfs) {
-    k3_bucket_merge<kMinSelect2nd, true><<<grid, K3_THREADS, smem, s>>>(K3_ARGS);
+    launch_after(k3_bucket_merge<kMinSelect2nd, true>, grid, K3_THREADS, smem, s, pdl, K3_ARGS);
   } else if (sem == kPlusTimes) {
-    k3_bucket_merge<kPlusTimes, false><<<grid, K3_THREADS, smem, s>>>(K3_ARGS);
+    launch_after(k3_bucket_merge<kPlusTimes, false>, grid, K3_THREADS, smem, s, pdl, K3_ARGS);
   } else if (sem == kMinSelect2nd) {
-    k3_bucket_merge<kMinSelect2nd, false><<<grid, K3_THREADS, smem, s>>>(K3_ARGS);
+    launch_after(k3_bucket_merge<kMinSelect2nd, false>, grid, K3_THREADS, smem, s, pdl, K3_ARGS);
   } else {
-    k3_bucket_merge<kOrAnd, false><<<grid, K3_THREADS, smem, s>>>(K3_ARGS);
+    launch_after(k3_bucket_merge<kOrAnd, false>, grid, K3_THREADS, smem, s, pdl, K3_ARGS);
   }
 #undef K3_ARGS
   return cudaGetLastError();
